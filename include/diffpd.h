@@ -1,0 +1,243 @@
+/*
+ * diffpd.h -- C ABI of a GB300-native differentiable Projective Dynamics solver.
+ *
+ * The library simulates hexahedral voxel meshes with implicit Euler solved by
+ * Projective Dynamics (Sec. 3, Alg. 1 of "DiffPD: Differentiable Projective
+ * Dynamics", arXiv 2101.05917) and back-propagates through the rollout with the
+ * adjoint splitting iteration  A z_{k+1} = Delta A z_k + dL/dx  (Sec. 4, Eqn 23,
+ * Alg. 2), both accelerated by L-BFGS with the constant matrix A as initial
+ * Hessian (Sec. 4, "Further acceleration with quasi-Newton methods").
+ *
+ * Conventions shared by every entry point
+ *   - Pointers named *_host are host memory; every other array pointer is CUDA
+ *     device memory on the mesh's device, owned by the caller.  The library never
+ *     frees caller memory and never keeps a caller pointer past the call.
+ *   - Per-node arrays are node-major (n, 3) FP64 in kept-node order: the nodes
+ *     touched by at least one kept cell, in increasing grid id, where grid node
+ *     (i, j, k) has id (i*(ny+1)+j)*(nz+1)+k and i runs along x.
+ *   - Per-element arrays follow kept-cell order (increasing cell id
+ *     (ci*ny+cj)*nz+ck).
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *     Calls are stream-ordered; entry points that return statistics synchronise
+ *     the stream before returning.
+ *   - Errors: every call returns a pd_status; pd_last_error() gives a
+ *     thread-local message for the last failing call.  Non-convergence returns
+ *     PD_ERR_NOT_CONVERGED with valid (partially converged) outputs and filled
+ *     statistics.
+ *   - Determinism: no floating-point atomics are used on any data path; every
+ *     reduction runs in a fixed order, so identical inputs give bit-identical
+ *     outputs on the same GPU.
+ */
+#ifndef DIFFPD_H
+#define DIFFPD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  PD_OK = 0,
+  PD_ERR_INVALID_ARG = 1,   /* bad size, NULL where required, wrong state */
+  PD_ERR_OOM = 2,           /* device allocation failed / admission refused */
+  PD_ERR_NOT_SPD = 3,       /* non-positive pivot while factoring A */
+  PD_ERR_NOT_CONVERGED = 4, /* iteration cap reached before the tolerance */
+  PD_ERR_INVERTED = 5,      /* an element with det F <= 0 was seen */
+  PD_ERR_NAN = 6,           /* non-finite value in a residual */
+  PD_ERR_TIMEOUT = 7,       /* serving: result not ready yet */
+  PD_ERR_CUDA = 8,          /* CUDA runtime error */
+  PD_ERR_NO_DEVICE = 9      /* mesh created without a device */
+} pd_status;
+
+enum { PD_PREC_FP64 = 0, PD_PREC_MIXED = 1 };
+
+typedef struct pd_mesh_s* pd_mesh;
+
+/* Voxel mesh description.  All pointers are host memory, read during the call. */
+typedef struct {
+  int32_t nx, ny, nz;           /* cells along x, y, z */
+  double dx;                    /* cell edge [m] */
+  double origin[3];             /* position of grid node (0,0,0) [m] */
+  double density;               /* [kg/m^3]; lumped mass rho dx^3/8 per cell corner */
+  const uint8_t* cell_mask;     /* nx*ny*nz in cell-id order (nonzero = kept), NULL = full box */
+  const uint8_t* dirichlet;     /* per kept node: fixed at its rest position, NULL = none */
+  const uint8_t* contact;       /* per kept node: ground-penalty candidate, NULL = none */
+  int32_t leaf_max;             /* nested-dissection leaf size, 0 = 64 */
+  int32_t device;               /* CUDA device ordinal, -1 = host analysis only */
+} pd_mesh_desc;
+
+typedef struct {
+  int64_t n_nodes, n_elems, n_free;
+  int64_t n_snodes, n_levels;
+  int64_t factor_nnz;           /* entries of all supernode panels (rows x cols) */
+  int64_t max_rows, max_cols;   /* largest supernode panel */
+  int64_t front_entries;        /* sum of rows^2 over supernodes (factor workspace) */
+  int64_t update_entries;       /* forward-solve update vector entries */
+  int32_t factorized;           /* pd_factorize succeeded */
+  int32_t precision;            /* precision of the last factorisation */
+} pd_mesh_info;
+
+/* Builds the mesh, its node/element incidence, the nested-dissection ordering
+ * and the supernodal structure of A on the host (C++), and uploads them to
+ * `device`.  Ownership of *out passes to the caller (pd_mesh_destroy). */
+pd_status pd_create_mesh(const pd_mesh_desc* desc, pd_mesh* out);
+void pd_mesh_destroy(pd_mesh m);
+pd_status pd_mesh_query(pd_mesh m, pd_mesh_info* info);
+
+/* Copies one host-side index structure into host_out (capacity in elements).
+ * Integer structures are int64.  Used to check the native index construction
+ * bit for bit against an independent re-derivation. */
+enum {
+  PD_EXPORT_INC_PTR = 0,   /* (n+1): kept-node -> (element, corner) CSR pointers */
+  PD_EXPORT_INC = 1,       /* (8e): entries e*8+corner, ascending per node */
+  PD_EXPORT_PERM = 2,      /* (n_free): column -> free-node index (free nodes in kept order) */
+  PD_EXPORT_SNODE_FIRST = 3, /* (n_snodes+1): first column of each supernode */
+  PD_EXPORT_ROW_PTR = 4,   /* (n_snodes+1) */
+  PD_EXPORT_ROWS = 5,      /* row structure of every supernode, ascending */
+  PD_EXPORT_PARENT = 6,    /* (n_snodes): supernodal etree parent or -1 */
+  PD_EXPORT_LEVEL = 7,     /* (n_snodes) */
+  PD_EXPORT_REL = 8,       /* positions of each supernode's below rows in its parent */
+  PD_EXPORT_LEVEL_PTR = 9, /* (n_levels+1) into PD_EXPORT_LEVEL_LIST */
+  PD_EXPORT_LEVEL_LIST = 10 /* (n_snodes) supernodes grouped by level, ascending ids */
+};
+pd_status pd_mesh_export(pd_mesh m, int32_t what, int64_t* host_out, int64_t capacity,
+                         int64_t* count);
+
+/* Material state and the one-time factorisation of
+ *   A = M/h^2 + sum_c w_c G_c^T G_c   (Sec. 3, Eqn 19).
+ * w_corot, w_vol, w_muscle: (e) stiffness per unit volume [Pa] of the corotated,
+ * volume-preserving and muscle-fibre energies (NULL = energy absent); each
+ * Gauss point of a cell carries w * dx^3/8.  fiber: (e, 3) unit fibre directions
+ * (required when w_muscle is given).  The numeric supernodal Cholesky runs on
+ * the device in FP64; with PD_PREC_MIXED an FP32 copy of the solve panels is kept
+ * for the triangular solves.  Copies of the weights are kept for the local
+ * steps.  Returns PD_ERR_NOT_SPD on a non-positive pivot. */
+typedef struct {
+  double h;                     /* time step [s] */
+  double gravity[3];            /* [m/s^2] */
+  double k_contact;             /* ground penalty stiffness [N/m] on contact candidates */
+  int32_t precision;            /* PD_PREC_FP64 or PD_PREC_MIXED */
+} pd_factor_opts;
+
+pd_status pd_factorize(pd_mesh m, const double* w_corot, const double* w_vol,
+                       const double* w_muscle, const double* fiber,
+                       const pd_factor_opts* opts, void* stream);
+
+typedef struct {
+  double tol_fwd;               /* |grad g| <= tol_fwd * max(|grad g(y)|, |M y/h^2|) */
+  double tol_bwd;               /* |Hess g z - gbar| <= tol_bwd * |gbar| */
+  int32_t max_iter_fwd, max_iter_bwd;
+  int32_t lbfgs_m;              /* history length (0 = plain PD / plain splitting iteration) */
+  int32_t ls_max;               /* Armijo backtracking tries (Sec. 6 uses 10) */
+  int32_t checkpoint_every;     /* 0 = every state stored; K > 0 = store states t % K == 0 */
+  int32_t check_every;          /* iterations between host convergence polls (0 = 4) */
+  double mixed_switch;          /* MIXED: relative residual below which FP64 local steps run */
+} pd_solver_opts;
+
+typedef struct {
+  int64_t fwd_iters, bwd_iters;         /* total iterations over the rollout */
+  int64_t fwd_fp64_iters, bwd_fp64_iters;
+  int64_t fwd_line_search;              /* rejected trial steps */
+  int32_t max_fwd_iters_step, max_bwd_iters_step;
+  double max_fwd_rel_residual, max_bwd_rel_residual;
+  int32_t inverted;                     /* det F <= 0 seen */
+  int32_t not_converged_steps;
+  double fwd_ms, bwd_ms;                /* host wall time of the call */
+} pd_stats;
+
+/* Forward rollout of T implicit-Euler steps (Sec. 3 Eqns 1-4, Alg. 1).
+ * x0, v0: (n,3).  f_ext: (n,3) constant external force added to gravity, or
+ * NULL.  act: (T, e) muscle contraction per step, or NULL.  mu: friction
+ * coefficient of the ground penalty contact (Sec. 5.1).
+ * x_traj, v_traj: ((S, n, 3)) with S = T+1, or with checkpointing
+ * S = T/K + 1 (T must be a multiple of K) holding states 0, K, 2K, ... */
+pd_status pd_forward(pd_mesh m, const double* x0, const double* v0, const double* f_ext,
+                     const double* act, double mu, int32_t T, const pd_solver_opts* opts,
+                     double* x_traj, double* v_traj, pd_stats* stats, void* stream);
+
+/* Backward rollout (Sec. 4, Alg. 2 with L-BFGS; Eqns 10-12 per step).
+ * x_traj, v_traj, f_ext, act, mu, T: exactly as given to / produced by pd_forward
+ * (with checkpointing the missing states are recomputed segment by segment).
+ * dL_dx, dL_dv: direct loss gradients, (T+1, n, 3) when loss_all_steps != 0,
+ * else (n, 3) for the final state only; dL_dv may be NULL.
+ * Outputs (each may be NULL): g_x0, g_v0 (n,3); g_fext (n,3) summed over steps;
+ * g_w_corot, g_w_vol, g_w_muscle (e) = dL/dw per unit volume; g_act (T, e);
+ * g_mu (1). */
+pd_status pd_backward(pd_mesh m, const double* x_traj, const double* v_traj,
+                      const double* f_ext, const double* act, double mu, int32_t T,
+                      const double* dL_dx, const double* dL_dv, int32_t loss_all_steps,
+                      const pd_solver_opts* opts, double* g_x0, double* g_v0,
+                      double* g_fext, double* g_w_corot, double* g_w_vol,
+                      double* g_w_muscle, double* g_act, double* g_mu,
+                      pd_stats* stats, void* stream);
+
+/* Kernel-level entry points (same conventions; used by tests and tools). */
+
+/* Local step (Sec. 3): grad_E = sum_c w_c G_c^T (G_c x - p_c) (Eqn 20, (n,3),
+ * Dirichlet rows included) and energy = sum_c w_c/2 |G_c x - p_c|^2 (1 scalar),
+ * at positions x (n,3) with contraction act (e) or NULL. */
+pd_status pd_local_step(pd_mesh m, const double* x, const double* act, int32_t precision,
+                        double* grad_E, double* energy, void* stream);
+
+/* Hessian-vector product (A - Delta A) v = Hess g(x) v (Eqn 22) on the free
+ * DoFs of v (n,3); Dirichlet rows of Hv are set to zero. */
+pd_status pd_hessian_vector(pd_mesh m, const double* x, const double* act, const double* v,
+                            int32_t precision, double* Hv, void* stream);
+
+/* Global step (Eqn 19): x = A^-1 b on the free DoFs (b, x: (n,3); Dirichlet
+ * rows of x are set to zero) with the prefactorised supernodal factor. */
+pd_status pd_solve_A(pd_mesh m, const double* b, double* x, int32_t precision, void* stream);
+
+/* Continuous-batching server (rollout-plus-gradient requests). */
+typedef struct pd_server_s* pd_server;
+
+typedef struct {
+  int32_t nx, ny, nz;           /* voxel box of the request */
+  double dx, density, h, gravity[3], k_contact, mu;
+  const uint8_t* cell_mask_host;   /* nx*ny*nz or NULL */
+  const uint8_t* dirichlet_host;   /* per kept node or NULL */
+  const uint8_t* contact_host;     /* per kept node or NULL */
+  const double* w_corot_host;      /* (e) */
+  const double* w_vol_host;        /* (e) or NULL */
+  const double* w_muscle_host;     /* (e) or NULL */
+  const double* fiber_host;        /* (e,3) or NULL */
+  const double* x0_host;           /* (n,3) */
+  const double* v0_host;           /* (n,3) */
+  const double* act_host;          /* (T,e) or NULL */
+  const double* loss_w_host;       /* (n,3): loss = sum(loss_w * x_T) */
+  int32_t T;
+  pd_solver_opts opts;
+} pd_request;
+
+typedef struct {
+  pd_status status;
+  double loss;
+  int64_t n_nodes, n_elems, T;
+  double* x_final_host;            /* library-owned until the next poll of this ticket */
+  double* g_v0_host;
+  double* g_act_host;
+  double latency_ms;               /* submit -> completion */
+  int64_t fwd_iters, bwd_iters;
+} pd_result;
+
+pd_status pd_serve_create(int32_t device, size_t mem_budget_bytes, int32_t max_slots,
+                          pd_server* out);
+/* Non-blocking.  Copies the request; admission happens when a slot and device
+ * memory are free.  Returns a ticket. */
+pd_status pd_serve_submit(pd_server s, const pd_request* r, uint64_t* ticket);
+/* PD_OK with *out filled when done, PD_ERR_TIMEOUT while pending, or the
+ * request's error. */
+pd_status pd_serve_poll(pd_server s, uint64_t ticket, pd_result* out);
+/* Blocks until every submitted request has completed. */
+pd_status pd_serve_drain(pd_server s);
+void pd_serve_destroy(pd_server s);
+
+const char* pd_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DIFFPD_H */

@@ -1,0 +1,953 @@
+// C ABI of the differentiable PD solver and the host orchestration of the
+// forward rollout (Alg. 1 + L-BFGS) and the backward rollout (Alg. 2 + L-BFGS).
+// The host only launches kernels and polls one device flag per batch of
+// iterations; every numerical decision is taken on the device.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "pd_internal.cuh"
+#include "pd_vec.cuh"
+
+namespace pd {
+
+namespace {
+thread_local std::string g_last_error;
+
+template <typename T>
+cudaError_t dalloc(MeshImpl* m, T** p, size_t count) {
+  *p = nullptr;
+  if (count == 0) count = 1;
+  cudaError_t e = cudaMalloc((void**)p, sizeof(T) * count);
+  if (e == cudaSuccess) {
+    m->allocations.push_back((void*)*p);
+    m->ws.bytes += sizeof(T) * count;
+  }
+  return e;
+}
+
+template <typename T, typename S>
+cudaError_t upload(MeshImpl* m, T** p, const std::vector<S>& v) {
+  cudaError_t e = dalloc(m, p, v.size());
+  if (e != cudaSuccess) return e;
+  if (v.empty()) return cudaSuccess;
+  std::vector<T> tmp(v.begin(), v.end());
+  return cudaMemcpy(*p, tmp.data(), sizeof(T) * tmp.size(), cudaMemcpyHostToDevice);
+}
+
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    if (dev >= 0) {
+      cudaGetDevice(&prev);
+      if (prev != dev) cudaSetDevice(dev);
+    }
+  }
+  ~DeviceGuard() {
+    int cur = -1;
+    if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+inline int grid_for(int64_t n) {
+  int64_t b = (n + 255) / 256;
+  return (int)std::max<int64_t>(1, std::min<int64_t>(b, 4096));
+}
+
+}  // namespace
+
+void set_error(const std::string& msg) { g_last_error = msg; }
+
+}  // namespace pd
+
+struct pd_mesh_s {
+  pd::MeshImpl impl;
+};
+
+using namespace pd;
+
+namespace {
+
+pd_status ensure_workspace(MeshImpl* m, int lbfgs_m) {
+  Workspace& w = m->ws;
+  const int64_t n3 = 3 * m->h.n, nf3 = 3 * m->h.nf;
+  if (!w.x) {
+    double** vecs[] = {&w.x, &w.xt, &w.y, &w.xprev, &w.vprev, &w.grad, &w.gradt, &w.dir, &w.q, &w.r,
+                       &w.z, &w.gs, &w.Hd, &w.ax, &w.av, &w.gbar, &w.fext, &w.ffric, &w.iox, &w.iov};
+    for (double** v : vecs) {
+      PD_CUDA_TRY(dalloc(m, v, (size_t)n3));
+      PD_CUDA_TRY(cudaMemset(*v, 0, sizeof(double) * n3));
+    }
+    PD_CUDA_TRY(dalloc(m, (double**)&w.elembuf, (size_t)(24 * m->h.e)));
+    const int64_t np = (int64_t)element_blocks(m) + 4 * (int64_t)gather_blocks(m) + 4 * 4096 + 64;
+    PD_CUDA_TRY(dalloc(m, &w.partials, (size_t)np));
+    PD_CUDA_TRY(dalloc(m, &w.counters, 16));
+    PD_CUDA_TRY(cudaMemset(w.counters, 0, 16 * sizeof(unsigned)));
+    PD_CUDA_TRY(dalloc(m, &w.st, 1));
+    PD_CUDA_TRY(cudaMallocHost((void**)&w.st_host, sizeof(IterState)));
+    PD_CUDA_TRY(dalloc(m, &w.flags, 4));
+    PD_CUDA_TRY(cudaMemset(w.flags, 0, 4 * sizeof(int)));
+    PD_CUDA_TRY(dalloc(m, (double**)&w.solve_u, (size_t)nf3));
+    const int64_t wrows = m->h.rel_ptr.empty() ? 0 : m->h.rel_ptr.back();
+    PD_CUDA_TRY(dalloc(m, (double**)&w.solve_W, (size_t)std::max<int64_t>(3 * wrows, 3)));
+  }
+  if (lbfgs_m > w.lbfgs_m) {
+    // history buffers grow monotonically; old ones stay in the allocation list
+    PD_CUDA_TRY(dalloc(m, &w.S, (size_t)lbfgs_m * nf3));
+    PD_CUDA_TRY(dalloc(m, &w.Y, (size_t)lbfgs_m * nf3));
+    w.lbfgs_m = lbfgs_m;
+  }
+  return PD_OK;
+}
+
+pd_solver_opts default_opts() {
+  pd_solver_opts o{};
+  o.tol_fwd = 1e-9;
+  o.tol_bwd = 1e-9;
+  o.max_iter_fwd = 500;
+  o.max_iter_bwd = 500;
+  o.lbfgs_m = 5;
+  o.ls_max = 10;
+  o.checkpoint_every = 0;
+  o.check_every = 4;
+  o.mixed_switch = 1e-5;
+  return o;
+}
+
+pd_solver_opts fill_opts(const pd_solver_opts* o) {
+  pd_solver_opts r = o ? *o : default_opts();
+  const pd_solver_opts d = default_opts();
+  if (!(r.tol_fwd > 0)) r.tol_fwd = d.tol_fwd;
+  if (!(r.tol_bwd > 0)) r.tol_bwd = d.tol_bwd;
+  if (r.max_iter_fwd <= 0) r.max_iter_fwd = d.max_iter_fwd;
+  if (r.max_iter_bwd <= 0) r.max_iter_bwd = d.max_iter_bwd;
+  if (r.lbfgs_m < 0) r.lbfgs_m = 0;
+  if (r.lbfgs_m > kMaxHistory) r.lbfgs_m = kMaxHistory;
+  if (r.ls_max < 0) r.ls_max = 0;
+  if (r.check_every <= 0) r.check_every = d.check_every;
+  if (!(r.mixed_switch > 0)) r.mixed_switch = d.mixed_switch;
+  return r;
+}
+
+struct Ctx {
+  MeshImpl* m;
+  cudaStream_t s;
+  pd_solver_opts o;
+  int64_t n, nf, n3f;
+  int vb;          // vector kernel blocks
+  VecCtx vc;
+  double* pe;      // energy partials
+  double* pg;      // gather partials
+  int nbe, nbg;
+};
+
+Ctx make_ctx(MeshImpl* m, cudaStream_t s, const pd_solver_opts& o) {
+  Ctx c;
+  c.m = m;
+  c.s = s;
+  c.o = o;
+  c.n = m->h.n;
+  c.nf = m->h.nf;
+  c.n3f = 3 * m->h.nf;
+  c.vb = vec_blocks(c.n3f);
+  c.vc.n3 = c.n3f;
+  c.vc.st = m->ws.st;
+  c.vc.partials = m->ws.partials;
+  c.vc.counter = m->ws.counters;
+  c.nbe = element_blocks(m);
+  c.nbg = gather_blocks(m);
+  c.pe = m->ws.partials;
+  c.pg = m->ws.partials + c.nbe;
+  return c;
+}
+
+pd_status poll(Ctx& c) {
+  PD_CUDA_TRY(cudaMemcpyAsync(c.m->ws.st_host, c.m->ws.st, sizeof(IterState), cudaMemcpyDeviceToHost, c.s));
+  PD_CUDA_TRY(cudaStreamSynchronize(c.s));
+  return PD_OK;
+}
+
+// one forward iteration: evaluate the trial point, decide, next direction
+pd_status launch_fwd_iteration(Ctx& c, int prec, const double* act_t) {
+  MeshImpl* m = c.m;
+  Workspace& w = m->ws;
+  IterState* st = w.st;
+  LocalArgs la{m, st, w.xt, nullptr, act_t, prec};
+  PD_CUDA_TRY(launch_element_forces(la, w.elembuf, c.pe, w.flags, c.s));
+  PD_CUDA_TRY(launch_gather_grad(m, st, w.elembuf, prec, w.xt, w.y, w.dir, w.gradt, c.pg, c.s));
+  decide_fwd_kernel<<<1, 256, 0, c.s>>>(st, c.pe, c.nbe, c.pg, c.nbg);
+  accept_fwd_kernel<<<c.vb, 256, 0, c.s>>>(st, c.n3f, w.x, w.xt, w.grad, w.gradt, w.q, w.S, w.Y);
+  const int M = c.o.lbfgs_m;
+  for (int k = 0; k <= M; ++k) lbfgs_loop1_kernel<<<c.vb, 256, 0, c.s>>>(c.vc, k, w.S, w.Y, w.q);
+  PD_CUDA_TRY(solve_A(m, st, w.q, w.r, m->precision, c.s));
+  for (int k = 0; k < M; ++k) lbfgs_loop2_kernel<<<c.vb, 256, 0, c.s>>>(c.vc, k, w.S, w.Y, w.r);
+  lbfgs_final_kernel<<<c.vb, 256, 0, c.s>>>(c.vc, w.S, w.r, w.dir, w.grad, w.x, w.xt, 1);
+  PD_CUDA_TRY(cudaGetLastError());
+  return PD_OK;
+}
+
+// one backward iteration: direction from the two-loop around A^-1, Hessian
+// product, exact quadratic line search, update of z and of grad s
+pd_status launch_bwd_iteration(Ctx& c, int prec, const double* xnext, const double* act_t) {
+  MeshImpl* m = c.m;
+  Workspace& w = m->ws;
+  IterState* st = w.st;
+  const int M = c.o.lbfgs_m;
+  for (int k = 0; k <= M; ++k) lbfgs_loop1_kernel<<<c.vb, 256, 0, c.s>>>(c.vc, k, w.S, w.Y, w.q);
+  PD_CUDA_TRY(solve_A(m, st, w.q, w.r, m->precision, c.s));
+  for (int k = 0; k < M; ++k) lbfgs_loop2_kernel<<<c.vb, 256, 0, c.s>>>(c.vc, k, w.S, w.Y, w.r);
+  lbfgs_final_kernel<<<c.vb, 256, 0, c.s>>>(c.vc, w.S, w.r, w.dir, w.gs, nullptr, nullptr, 0);
+  LocalArgs la{m, st, xnext, w.dir, act_t, prec};
+  PD_CUDA_TRY(launch_element_hvp(la, w.elembuf, w.flags, c.s));
+  PD_CUDA_TRY(launch_gather_hvp(m, st, w.elembuf, prec, xnext, w.dir, w.gs, w.Hd, c.pg, c.s));
+  decide_bwd_kernel<<<1, 256, 0, c.s>>>(st, c.pg, c.nbg);
+  update_bwd_kernel<<<c.vb, 256, 0, c.s>>>(c.vc, w.dir, w.Hd, w.z, w.gs, w.q, w.S, w.Y);
+  PD_CUDA_TRY(cudaGetLastError());
+  return PD_OK;
+}
+
+struct StepInfo {
+  int iters = 0, fp64_iters = 0, ls = 0;
+  double rel = 0;
+  bool converged = true;
+};
+
+// One implicit-Euler step from the internal state (w.xprev, w.vprev): on return
+// w.x holds x_{t+1}; finalize writes the trajectory and advances the state.
+pd_status forward_step(Ctx& c, const double* act_t, const double* fext_int, double mu,
+                       double* traj_x, double* traj_v, StepInfo& info, int& guess) {
+  MeshImpl* m = c.m;
+  Workspace& w = m->ws;
+  StateCfg cfg{c.o.tol_fwd, m->precision == PD_PREC_MIXED ? 1e-6 : 1e-12, c.o.lbfgs_m, c.o.ls_max,
+               c.o.max_iter_fwd, 0};
+  state_reset_kernel<<<1, 1, 0, c.s>>>(w.st, cfg);
+  PredParams pp{};
+  pp.n = c.n;
+  pp.nf = c.nf;
+  pp.xi = w.xprev;
+  pp.vi = w.vprev;
+  pp.fext = fext_int;
+  pp.mass = m->mass;
+  pp.X = m->X;
+  pp.contact = m->k_contact > 0 ? m->contact : nullptr;
+  pp.k = m->k_contact;
+  pp.mu = mu;
+  pp.h = m->h_step;
+  for (int i = 0; i < 3; ++i) pp.grav[i] = m->grav[i];
+  pp.y = w.y;
+  pp.xt = w.xt;
+  pp.x = w.x;
+  pp.partials = w.partials;
+  pp.counter = w.counters;
+  pp.st = w.st;
+  predictor_kernel<<<grid_for(c.n), 256, 0, c.s>>>(pp);
+  PD_CUDA_TRY(cudaGetLastError());
+  int prec = m->precision == PD_PREC_MIXED ? PD_PREC_MIXED : PD_PREC_FP64;
+  bool fp64_phase = prec == PD_PREC_FP64;
+  int launched = 0, fp64_launched = 0;
+  int chunk = std::max(guess, 1);
+  double last_rel = 1e300;
+  const int hard_cap = 3 * c.o.max_iter_fwd + 64;
+  info = StepInfo{};
+  while (true) {
+    for (int k = 0; k < chunk; ++k) {
+      pd_status e = launch_fwd_iteration(c, prec, act_t);
+      if (e != PD_OK) return e;
+    }
+    launched += chunk;
+    if (fp64_phase && prec == PD_PREC_FP64 && m->precision == PD_PREC_MIXED) fp64_launched += chunk;
+    pd_status e = poll(c);
+    if (e != PD_OK) return e;
+    const IterState& sh = *w.st_host;
+    const double rel = sh.ref2 > 0 ? std::sqrt(sh.gn2_acc / sh.ref2) : 0.0;
+    if (sh.status & DEV_ERR_NAN) {
+      info.converged = false;
+      break;
+    }
+    if (sh.converged) {
+      if (!fp64_phase && !sh.hit_max) {
+        // mixed precision: confirm / polish the FP32 solution with FP64 local steps
+        fp64_phase = true;
+        prec = PD_PREC_FP64;
+        force_accept_kernel<<<1, 1, 0, c.s>>>(w.st);
+        copy_kernel<<<c.vb, 256, 0, c.s>>>(c.n3f, w.x, w.xt);
+        chunk = 1;
+        continue;
+      }
+      info.converged = !sh.hit_max;
+      break;
+    }
+    if (!fp64_phase && (rel <= c.o.mixed_switch || rel > 0.9 * last_rel)) {
+      fp64_phase = true;
+      prec = PD_PREC_FP64;
+      force_accept_kernel<<<1, 1, 0, c.s>>>(w.st);
+      copy_kernel<<<c.vb, 256, 0, c.s>>>(c.n3f, w.x, w.xt);
+    }
+    last_rel = rel;
+    if (launched >= hard_cap) {
+      info.converged = false;
+      break;
+    }
+    chunk = c.o.check_every;
+  }
+  const IterState& sh = *w.st_host;
+  info.iters = sh.iters;
+  info.ls = sh.ls_total;
+  info.fp64_iters = fp64_launched;
+  info.rel = sh.ref2 > 0 ? std::sqrt(sh.gn2_acc / sh.ref2) : 0.0;
+  guess = std::max(1, sh.iters - 1);
+  finalize_fwd_kernel<<<grid_for(c.n), 256, 0, c.s>>>(c.n, w.x, w.xprev, w.vprev, 1.0 / m->h_step,
+                                                      m->kept_of_internal, traj_x, traj_v);
+  PD_CUDA_TRY(cudaGetLastError());
+  return PD_OK;
+}
+
+void accumulate(pd_stats* st, const StepInfo& i, bool fwd) {
+  if (!st) return;
+  if (fwd) {
+    st->fwd_iters += i.iters;
+    st->fwd_fp64_iters += i.fp64_iters;
+    st->fwd_line_search += i.ls;
+    st->max_fwd_iters_step = std::max(st->max_fwd_iters_step, i.iters);
+    st->max_fwd_rel_residual = std::max(st->max_fwd_rel_residual, i.rel);
+  } else {
+    st->bwd_iters += i.iters;
+    st->bwd_fp64_iters += i.fp64_iters;
+    st->max_bwd_iters_step = std::max(st->max_bwd_iters_step, i.iters);
+    st->max_bwd_rel_residual = std::max(st->max_bwd_rel_residual, i.rel);
+  }
+  if (!i.converged) st->not_converged_steps += 1;
+}
+
+pd_status check_flags(Ctx& c, pd_stats* stats) {
+  int flags = 0;
+  PD_CUDA_TRY(cudaMemcpyAsync(&flags, c.m->ws.flags, sizeof(int), cudaMemcpyDeviceToHost, c.s));
+  PD_CUDA_TRY(cudaStreamSynchronize(c.s));
+  if (stats && (flags & DEV_ERR_INVERTED)) stats->inverted = 1;
+  return PD_OK;
+}
+
+// Adjoint of one step at x_{t+1} (w.x holds x_{t+1} internal; w.xprev/w.vprev hold x_t, v_t).
+pd_status backward_step(Ctx& c, const double* xnext, const double* xt_, const double* vt_,
+                        const double* act_t, double mu, const double* gx_t, const double* gv_t,
+                        double* gfext_int, double* g_wc, double* g_wv, double* g_wm, double* g_act_t,
+                        double* g_mu, StepInfo& info, int& guess) {
+  MeshImpl* m = c.m;
+  Workspace& w = m->ws;
+  const double inv_h = 1.0 / m->h_step;
+  StateCfg cfg{c.o.tol_bwd, 0.0, c.o.lbfgs_m, c.o.ls_max, c.o.max_iter_bwd, 1};
+  state_reset_kernel<<<1, 1, 0, c.s>>>(w.st, cfg);
+  bwd_step_init_kernel<<<c.vb, 256, 0, c.s>>>(c.vc, w.ax, w.av, inv_h, w.z, w.gs, w.q);
+  int prec = m->precision == PD_PREC_MIXED ? PD_PREC_MIXED : PD_PREC_FP64;
+  bool fp64_phase = prec == PD_PREC_FP64;
+  int launched = 0, fp64_launched = 0, checks = 0;
+  int chunk = std::max(guess, 1);
+  const int hard_cap = 3 * c.o.max_iter_bwd + 64;
+  double last_rel = 1e300;
+  info = StepInfo{};
+  while (true) {
+    for (int k = 0; k < chunk; ++k) {
+      pd_status e = launch_bwd_iteration(c, prec, xnext, act_t);
+      if (e != PD_OK) return e;
+    }
+    launched += chunk;
+    if (fp64_phase && m->precision == PD_PREC_MIXED) fp64_launched += chunk;
+    pd_status e = poll(c);
+    if (e != PD_OK) return e;
+    const IterState* sh = w.st_host;
+    if (sh->status & DEV_ERR_NAN) {
+      info.converged = false;
+      break;
+    }
+    double rel = sh->ref2 > 0 ? std::sqrt(sh->gn2_acc / sh->ref2) : 0.0;
+    if (sh->converged) {
+      if (sh->hit_max) {
+        info.converged = false;
+        break;
+      }
+      // true residual gs = H z - gbar with an FP64 Hessian product
+      LocalArgs la{m, nullptr, xnext, w.z, act_t, PD_PREC_FP64};
+      PD_CUDA_TRY(launch_element_hvp(la, w.elembuf, w.flags, c.s));
+      PD_CUDA_TRY(launch_gather_hvp(m, nullptr, w.elembuf, PD_PREC_FP64, xnext, w.z, nullptr, w.Hd, c.pg, c.s));
+      residual_replace_kernel<<<c.vb, 256, 0, c.s>>>(c.vc, w.Hd, w.ax, w.av, inv_h, w.gs, w.q);
+      e = poll(c);
+      if (e != PD_OK) return e;
+      ++checks;
+      if (w.st_host->converged || checks > 8) {
+        info.converged = w.st_host->converged != 0;
+        break;
+      }
+      if (m->precision == PD_PREC_MIXED) {
+        fp64_phase = true;
+        prec = PD_PREC_FP64;
+      }
+      chunk = c.o.check_every;
+      continue;
+    }
+    if (!fp64_phase && (rel <= c.o.mixed_switch || rel > 0.9 * last_rel)) {
+      fp64_phase = true;
+      prec = PD_PREC_FP64;
+    }
+    last_rel = rel;
+    if (launched >= hard_cap) {
+      info.converged = false;
+      break;
+    }
+    chunk = c.o.check_every;
+  }
+  const IterState* sh = w.st_host;
+  info.iters = sh->iters;
+  info.ls = sh->ls_total;
+  info.fp64_iters = fp64_launched;
+  info.rel = sh->ref2 > 0 ? std::sqrt(sh->gn2_acc / sh->ref2) : 0.0;
+  guess = std::max(1, sh->iters - 1);
+  // parameter gradients at x_{t+1} (FP64), then the state adjoint of step t
+  LocalArgs la{m, nullptr, xnext, w.z, act_t, PD_PREC_FP64};
+  PD_CUDA_TRY(launch_element_param_grads(la, g_wc, g_wv, g_wm, g_act_t, c.s));
+  BwdStateParams bp{};
+  bp.n = c.n;
+  bp.nf = c.nf;
+  bp.z = w.z;
+  bp.mass = m->mass;
+  bp.xi = xt_;
+  bp.vi = vt_;
+  bp.contact = m->k_contact > 0 ? m->contact : nullptr;
+  bp.k = m->k_contact;
+  bp.mu = mu;
+  bp.h = m->h_step;
+  bp.inv_h = inv_h;
+  bp.inv_h2 = inv_h * inv_h;
+  bp.ax = w.ax;
+  bp.av = w.av;
+  bp.gfext = gfext_int;
+  bp.gx_t = gx_t;
+  bp.gv_t = gv_t;
+  bp.kept_of_internal = m->kept_of_internal;
+  bp.gmu = g_mu;
+  bp.partials = w.partials;
+  bp.counter = w.counters;
+  bwd_state_kernel<<<grid_for(c.n), 256, 0, c.s>>>(bp);
+  PD_CUDA_TRY(cudaGetLastError());
+  return PD_OK;
+}
+
+pd_status check_mesh(pd_mesh m, bool need_factor) {
+  if (!m) {
+    set_error("null mesh");
+    return PD_ERR_INVALID_ARG;
+  }
+  if (m->impl.device < 0) {
+    set_error("mesh was created without a device");
+    return PD_ERR_NO_DEVICE;
+  }
+  if (need_factor && !m->impl.factorized) {
+    set_error("pd_factorize has not succeeded on this mesh");
+    return PD_ERR_INVALID_ARG;
+  }
+  return PD_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* pd_last_error(void) { return g_last_error.c_str(); }
+
+pd_status pd_create_mesh(const pd_mesh_desc* desc, pd_mesh* out) {
+  if (!desc || !out) {
+    set_error("pd_create_mesh: null argument");
+    return PD_ERR_INVALID_ARG;
+  }
+  *out = nullptr;
+  pd_mesh m = new (std::nothrow) pd_mesh_s;
+  if (!m) {
+    set_error("pd_create_mesh: host allocation failed");
+    return PD_ERR_OOM;
+  }
+  MeshImpl& I = m->impl;
+  std::string err;
+  try {
+    err = analyse(*desc, I.h);
+  } catch (const std::bad_alloc&) {
+    err = "pd_create_mesh: host allocation failed";
+  }
+  if (!err.empty()) {
+    set_error(err);
+    delete m;
+    return PD_ERR_INVALID_ARG;
+  }
+  I.device = desc->device;
+  if (I.device < 0) {
+    *out = m;
+    return PD_OK;
+  }
+  DeviceGuard g(I.device);
+  const HostMesh& h = I.h;
+  for (int64_t L = 0; L < h.nlev; ++L)
+    if (h.level_ptr[L + 1] - h.level_ptr[L] > 65535) {
+      set_error("pd_create_mesh: a tree level has more than 65535 supernodes");
+      delete m;
+      return PD_ERR_INVALID_ARG;
+    }
+  auto fail = [&](cudaError_t e) {
+    set_error(std::string("pd_create_mesh: ") + cudaGetErrorString(e));
+    pd_mesh_destroy(m);
+    return e == cudaErrorMemoryAllocation ? PD_ERR_OOM : PD_ERR_CUDA;
+  };
+  cudaError_t e;
+#define UP(dst, src) if ((e = upload(&I, &I.dst, h.src)) != cudaSuccess) return fail(e)
+  UP(elems, elems);
+  UP(inc_ptr, inc_ptr);
+  UP(inc, inc);
+  UP(kept_of_internal, kept_of_internal);
+  UP(X, X);
+  UP(mass, mass);
+  UP(contact, contact);
+  UP(snode_first, snode_first);
+  UP(row_ptr, row_ptr);
+  UP(panel_off, panel_off);
+  UP(rel_ptr, rel_ptr);
+  UP(gath_ptr, gath_ptr);
+  UP(front_off, front_off);
+  UP(level_list, level_list);
+  UP(child_ptr, child_ptr);
+  UP(child_list, child_list);
+  UP(rows, rows);
+  UP(gath, gath);
+  UP(rel, rel);
+  UP(la_target, la_target);
+  UP(la_cptr, la_cptr);
+  UP(la_diag_node, la_diag_node);
+  UP(la_contrib, la_contrib);
+#undef UP
+  std::vector<int2> fwd, bwd;
+  build_solve_schedule(h, fwd, bwd, I.slevels);
+  if ((e = dalloc(&I, &I.fwd_tasks, fwd.size())) != cudaSuccess) return fail(e);
+  if ((e = dalloc(&I, &I.bwd_tasks, bwd.size())) != cudaSuccess) return fail(e);
+  if (!fwd.empty() && (e = cudaMemcpy(I.fwd_tasks, fwd.data(), sizeof(int2) * fwd.size(), cudaMemcpyHostToDevice)) != cudaSuccess) return fail(e);
+  if (!bwd.empty() && (e = cudaMemcpy(I.bwd_tasks, bwd.data(), sizeof(int2) * bwd.size(), cudaMemcpyHostToDevice)) != cudaSuccess) return fail(e);
+  I.flevels.assign(h.nlev, FactorLevel{});
+  for (int64_t L = 0; L < h.nlev; ++L) {
+    FactorLevel& f = I.flevels[L];
+    f.list_off = h.level_ptr[L];
+    f.count = h.level_ptr[L + 1] - h.level_ptr[L];
+    for (int64_t i = h.level_ptr[L]; i < h.level_ptr[L + 1]; ++i) {
+      const int64_t s = h.level_list[i];
+      f.max_nc = std::max(f.max_nc, h.nc(s));
+      f.max_nr = std::max(f.max_nr, h.nr(s));
+      f.max_children = std::max(f.max_children, h.child_ptr[s + 1] - h.child_ptr[s]);
+      for (int64_t ci = h.child_ptr[s]; ci < h.child_ptr[s + 1]; ++ci) {
+        const int64_t t = h.child_list[ci];
+        const int64_t nb = h.nr(t) - h.nc(t);
+        f.max_child_nb2 = std::max(f.max_child_nb2, nb * nb);
+      }
+    }
+  }
+  pd_status ws = ensure_workspace(&I, 5);
+  if (ws != PD_OK) {
+    pd_mesh_destroy(m);
+    return ws;
+  }
+  *out = m;
+  return PD_OK;
+}
+
+void pd_mesh_destroy(pd_mesh m) {
+  if (!m) return;
+  MeshImpl& I = m->impl;
+  if (I.device >= 0) {
+    DeviceGuard g(I.device);
+    cudaDeviceSynchronize();
+    for (void* p : I.allocations) cudaFree(p);
+    if (I.ws.st_host) cudaFreeHost(I.ws.st_host);
+  }
+  delete m;
+}
+
+pd_status pd_mesh_query(pd_mesh m, pd_mesh_info* info) {
+  if (!m || !info) {
+    set_error("pd_mesh_query: null argument");
+    return PD_ERR_INVALID_ARG;
+  }
+  const HostMesh& h = m->impl.h;
+  std::memset(info, 0, sizeof(*info));
+  info->n_nodes = h.n;
+  info->n_elems = h.e;
+  info->n_free = h.nf;
+  info->n_snodes = h.ns;
+  info->n_levels = h.nlev;
+  info->factor_nnz = h.factor_nnz();
+  for (int64_t s = 0; s < h.ns; ++s) {
+    info->max_rows = std::max(info->max_rows, h.nr(s));
+    info->max_cols = std::max(info->max_cols, h.nc(s));
+  }
+  info->front_entries = h.front_entries();
+  info->update_entries = h.rel_ptr.empty() ? 0 : h.rel_ptr.back();
+  info->factorized = m->impl.factorized ? 1 : 0;
+  info->precision = m->impl.precision;
+  return PD_OK;
+}
+
+pd_status pd_mesh_export(pd_mesh m, int32_t what, int64_t* host_out, int64_t capacity, int64_t* count) {
+  if (!m) {
+    set_error("pd_mesh_export: null mesh");
+    return PD_ERR_INVALID_ARG;
+  }
+  const HostMesh& h = m->impl.h;
+  std::vector<int64_t> v;
+  switch (what) {
+    case PD_EXPORT_INC_PTR: v = h.inc_ptr_kept; break;
+    case PD_EXPORT_INC: v = h.inc_kept; break;
+    case PD_EXPORT_PERM: v = h.perm; break;
+    case PD_EXPORT_SNODE_FIRST: v = h.snode_first; break;
+    case PD_EXPORT_ROW_PTR: v = h.row_ptr; break;
+    case PD_EXPORT_ROWS: v.assign(h.rows.begin(), h.rows.end()); break;
+    case PD_EXPORT_PARENT: v = h.parent; break;
+    case PD_EXPORT_LEVEL: v = h.level; break;
+    case PD_EXPORT_REL: v.assign(h.rel.begin(), h.rel.end()); break;
+    case PD_EXPORT_LEVEL_PTR: v = h.level_ptr; break;
+    case PD_EXPORT_LEVEL_LIST: v = h.level_list; break;
+    default:
+      set_error("pd_mesh_export: unknown structure");
+      return PD_ERR_INVALID_ARG;
+  }
+  if (count) *count = (int64_t)v.size();
+  if (host_out) {
+    if (capacity < (int64_t)v.size()) {
+      set_error("pd_mesh_export: capacity too small");
+      return PD_ERR_INVALID_ARG;
+    }
+    std::copy(v.begin(), v.end(), host_out);
+  }
+  return PD_OK;
+}
+
+pd_status pd_factorize(pd_mesh mesh, const double* w_corot, const double* w_vol, const double* w_muscle,
+                       const double* fiber, const pd_factor_opts* opts, void* stream) {
+  pd_status ck = check_mesh(mesh, false);
+  if (ck != PD_OK) return ck;
+  if (!opts || !(opts->h > 0)) {
+    set_error("pd_factorize: opts->h must be positive");
+    return PD_ERR_INVALID_ARG;
+  }
+  if (!w_corot && !w_vol && !w_muscle) {
+    set_error("pd_factorize: at least one energy weight array is required");
+    return PD_ERR_INVALID_ARG;
+  }
+  if (w_muscle && !fiber) {
+    set_error("pd_factorize: fiber directions are required with w_muscle");
+    return PD_ERR_INVALID_ARG;
+  }
+  if (opts->precision != PD_PREC_FP64 && opts->precision != PD_PREC_MIXED) {
+    set_error("pd_factorize: unknown precision");
+    return PD_ERR_INVALID_ARG;
+  }
+  MeshImpl& I = mesh->impl;
+  DeviceGuard g(I.device);
+  cudaStream_t s = (cudaStream_t)stream;
+  const int64_t e = I.h.e;
+  // the library keeps its own copies of the material arrays for the local steps
+  auto own = [&](double** buf, double** dst, const double* src, int64_t count) -> pd_status {
+    *dst = nullptr;
+    if (!src) return PD_OK;
+    if (!*buf) PD_CUDA_TRY(dalloc(&I, buf, (size_t)count));
+    PD_CUDA_TRY(cudaMemcpyAsync(*buf, src, sizeof(double) * count, cudaMemcpyDeviceToDevice, s));
+    *dst = *buf;
+    return PD_OK;
+  };
+  pd_status st;
+  if ((st = own(&I.wc_buf, &I.wc, w_corot, e)) != PD_OK) return st;
+  if ((st = own(&I.wv_buf, &I.wv, w_vol, e)) != PD_OK) return st;
+  if ((st = own(&I.wm_buf, &I.wm, w_muscle, e)) != PD_OK) return st;
+  if ((st = own(&I.fiber_buf, &I.fiber, fiber, 3 * e)) != PD_OK) return st;
+  I.h_step = opts->h;
+  for (int i = 0; i < 3; ++i) I.grav[i] = opts->gravity[i];
+  I.k_contact = opts->k_contact;
+  I.precision = opts->precision;
+  const int64_t nnz = I.h.factor_nnz();
+  if (!I.Q64) PD_CUDA_TRY(dalloc(&I, &I.Q64, (size_t)nnz));
+  if (I.precision == PD_PREC_MIXED && !I.Q32) PD_CUDA_TRY(dalloc(&I, &I.Q32, (size_t)nnz));
+  I.factorized = false;
+  pd_status r = factorize_device(&I, s);
+  if (r == PD_OK) I.factorized = true;
+  return r;
+}
+
+pd_status pd_forward(pd_mesh mesh, const double* x0, const double* v0, const double* f_ext, const double* act,
+                     double mu, int32_t T, const pd_solver_opts* opts, double* x_traj, double* v_traj,
+                     pd_stats* stats, void* stream) {
+  pd_status ck = check_mesh(mesh, true);
+  if (ck != PD_OK) return ck;
+  if (!x0 || !v0 || T < 0) {
+    set_error("pd_forward: x0 and v0 are required and T must be >= 0");
+    return PD_ERR_INVALID_ARG;
+  }
+  const pd_solver_opts o = fill_opts(opts);
+  if (o.checkpoint_every > 0 && T % o.checkpoint_every != 0) {
+    set_error("pd_forward: T must be a multiple of checkpoint_every");
+    return PD_ERR_INVALID_ARG;
+  }
+  MeshImpl* m = &mesh->impl;
+  DeviceGuard g(m->device);
+  const auto t0 = std::chrono::steady_clock::now();
+  pd_status ws = ensure_workspace(m, o.lbfgs_m);
+  if (ws != PD_OK) return ws;
+  cudaStream_t s = (cudaStream_t)stream;
+  Ctx c = make_ctx(m, s, o);
+  Workspace& w = m->ws;
+  const int64_t n = m->h.n;
+  if (stats) std::memset(stats, 0, sizeof(*stats));
+  PD_CUDA_TRY(cudaMemsetAsync(w.flags, 0, sizeof(int), s));
+  kept_to_internal_kernel<<<grid_for(n), 256, 0, s>>>(n, m->kept_of_internal, x0, w.xprev);
+  kept_to_internal_kernel<<<grid_for(n), 256, 0, s>>>(n, m->kept_of_internal, v0, w.vprev);
+  const double* fext_int = nullptr;
+  if (f_ext) {
+    kept_to_internal_kernel<<<grid_for(n), 256, 0, s>>>(n, m->kept_of_internal, f_ext, w.fext);
+    fext_int = w.fext;
+  }
+  const int K = o.checkpoint_every;
+  if (x_traj) PD_CUDA_TRY(cudaMemcpyAsync(x_traj, x0, sizeof(double) * 3 * n, cudaMemcpyDeviceToDevice, s));
+  if (v_traj) PD_CUDA_TRY(cudaMemcpyAsync(v_traj, v0, sizeof(double) * 3 * n, cudaMemcpyDeviceToDevice, s));
+  int guess = 4;
+  bool all_ok = true;
+  for (int t = 0; t < T; ++t) {
+    const double* act_t = act ? act + (int64_t)t * m->h.e : nullptr;
+    double* tx = nullptr;
+    double* tv = nullptr;
+    if (K <= 0) {
+      tx = x_traj ? x_traj + (int64_t)(t + 1) * 3 * n : nullptr;
+      tv = v_traj ? v_traj + (int64_t)(t + 1) * 3 * n : nullptr;
+    } else if ((t + 1) % K == 0) {
+      tx = x_traj ? x_traj + (int64_t)((t + 1) / K) * 3 * n : nullptr;
+      tv = v_traj ? v_traj + (int64_t)((t + 1) / K) * 3 * n : nullptr;
+    }
+    StepInfo info;
+    pd_status e = forward_step(c, act_t, fext_int, mu, tx, tv, info, guess);
+    if (e != PD_OK) return e;
+    accumulate(stats, info, true);
+    if (!info.converged) all_ok = false;
+  }
+  PD_CUDA_TRY(cudaStreamSynchronize(s));
+  check_flags(c, stats);
+  if (stats) stats->fwd_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  const int nan = w.st_host->status & DEV_ERR_NAN;
+  if (nan) {
+    set_error("pd_forward: non-finite residual");
+    return PD_ERR_NAN;
+  }
+  if (!all_ok) {
+    set_error("pd_forward: some steps reached the iteration cap");
+    return PD_ERR_NOT_CONVERGED;
+  }
+  return PD_OK;
+}
+
+pd_status pd_backward(pd_mesh mesh, const double* x_traj, const double* v_traj, const double* f_ext,
+                      const double* act, double mu, int32_t T, const double* dL_dx, const double* dL_dv,
+                      int32_t loss_all_steps, const pd_solver_opts* opts, double* g_x0, double* g_v0,
+                      double* g_fext, double* g_w_corot, double* g_w_vol, double* g_w_muscle, double* g_act,
+                      double* g_mu, pd_stats* stats, void* stream) {
+  pd_status ck = check_mesh(mesh, true);
+  if (ck != PD_OK) return ck;
+  if (!x_traj || !v_traj || !dL_dx || T < 0) {
+    set_error("pd_backward: x_traj, v_traj and dL_dx are required");
+    return PD_ERR_INVALID_ARG;
+  }
+  const pd_solver_opts o = fill_opts(opts);
+  const int K = o.checkpoint_every;
+  if (K > 0 && T % K != 0) {
+    set_error("pd_backward: T must be a multiple of checkpoint_every");
+    return PD_ERR_INVALID_ARG;
+  }
+  MeshImpl* m = &mesh->impl;
+  DeviceGuard g(m->device);
+  const auto t0 = std::chrono::steady_clock::now();
+  pd_status ws = ensure_workspace(m, o.lbfgs_m);
+  if (ws != PD_OK) return ws;
+  cudaStream_t s = (cudaStream_t)stream;
+  Ctx c = make_ctx(m, s, o);
+  Workspace& w = m->ws;
+  const int64_t n = m->h.n, e = m->h.e;
+  if (stats) std::memset(stats, 0, sizeof(*stats));
+  PD_CUDA_TRY(cudaMemsetAsync(w.flags, 0, sizeof(int), s));
+  // segment storage for recomputed states (internal order): K+1 states of x and v
+  double* seg = nullptr;
+  if (K > 0) PD_CUDA_TRY(cudaMallocAsync((void**)&seg, sizeof(double) * 6 * n * (size_t)(K + 1), s));
+  double* gfext_int = w.gbar;   // reuse: accumulated dL/df_ext (internal order)
+  PD_CUDA_TRY(cudaMemsetAsync(gfext_int, 0, sizeof(double) * 3 * n, s));
+  if (g_w_corot) PD_CUDA_TRY(cudaMemsetAsync(g_w_corot, 0, sizeof(double) * e, s));
+  if (g_w_vol) PD_CUDA_TRY(cudaMemsetAsync(g_w_vol, 0, sizeof(double) * e, s));
+  if (g_w_muscle) PD_CUDA_TRY(cudaMemsetAsync(g_w_muscle, 0, sizeof(double) * e, s));
+  if (g_mu) PD_CUDA_TRY(cudaMemsetAsync(g_mu, 0, sizeof(double), s));
+  const double* fext_int = nullptr;
+  if (f_ext) {
+    kept_to_internal_kernel<<<grid_for(n), 256, 0, s>>>(n, m->kept_of_internal, f_ext, w.fext);
+    fext_int = w.fext;
+  }
+  auto loss_x = [&](int t) -> const double* {
+    if (loss_all_steps) return dL_dx + (int64_t)t * 3 * n;
+    return t == T ? dL_dx : nullptr;
+  };
+  auto loss_v = [&](int t) -> const double* {
+    if (!dL_dv) return nullptr;
+    if (loss_all_steps) return dL_dv + (int64_t)t * 3 * n;
+    return t == T ? dL_dv : nullptr;
+  };
+  // upstream of the final state
+  kept_to_internal_kernel<<<grid_for(n), 256, 0, s>>>(n, m->kept_of_internal, loss_x(T), w.ax);
+  if (loss_v(T)) kept_to_internal_kernel<<<grid_for(n), 256, 0, s>>>(n, m->kept_of_internal, loss_v(T), w.av);
+  else PD_CUDA_TRY(cudaMemsetAsync(w.av, 0, sizeof(double) * 3 * n, s));
+  int guess_f = 4, guess_b = 4;
+  bool all_ok = true;
+  // scratch for x_{t+1}, x_t, v_t in internal order
+  double* xn_int = w.iox;     // x_{t+1}
+  double* xt_int = w.xprev;   // x_t
+  double* vt_int = w.vprev;   // v_t
+  const int nseg = K > 0 ? T / K : 1;
+  for (int sg = nseg - 1; sg >= 0; --sg) {
+    const int ta = K > 0 ? sg * K : 0;
+    const int tb = K > 0 ? ta + K : T;
+    if (K > 0) {
+      // recompute states ta..tb-1 from the checkpoint (bit-identical to the forward)
+      kept_to_internal_kernel<<<grid_for(n), 256, 0, s>>>(n, m->kept_of_internal, x_traj + (int64_t)sg * 3 * n, w.xprev);
+      kept_to_internal_kernel<<<grid_for(n), 256, 0, s>>>(n, m->kept_of_internal, v_traj + (int64_t)sg * 3 * n, w.vprev);
+      copy_kernel<<<grid_for(3 * n), 256, 0, s>>>(3 * n, w.xprev, seg);
+      copy_kernel<<<grid_for(3 * n), 256, 0, s>>>(3 * n, w.vprev, seg + 3 * n);
+      for (int t = ta; t < tb - 1; ++t) {
+        StepInfo info;
+        const double* act_t = act ? act + (int64_t)t * e : nullptr;
+        pd_status er = forward_step(c, act_t, fext_int, mu, nullptr, nullptr, info, guess_f);
+        if (er != PD_OK) return er;
+        copy_kernel<<<grid_for(3 * n), 256, 0, s>>>(3 * n, w.xprev, seg + (int64_t)(t + 1 - ta) * 6 * n);
+        copy_kernel<<<grid_for(3 * n), 256, 0, s>>>(3 * n, w.vprev, seg + (int64_t)(t + 1 - ta) * 6 * n + 3 * n);
+      }
+    }
+    for (int t = tb - 1; t >= ta; --t) {
+      const double* act_t = act ? act + (int64_t)t * e : nullptr;
+      if (K > 0) {
+        if (t + 1 == tb)
+          kept_to_internal_kernel<<<grid_for(n), 256, 0, s>>>(n, m->kept_of_internal, x_traj + (int64_t)(sg + 1) * 3 * n, xn_int);
+        else
+          copy_kernel<<<grid_for(3 * n), 256, 0, s>>>(3 * n, seg + (int64_t)(t + 1 - ta) * 6 * n, xn_int);
+        copy_kernel<<<grid_for(3 * n), 256, 0, s>>>(3 * n, seg + (int64_t)(t - ta) * 6 * n, xt_int);
+        copy_kernel<<<grid_for(3 * n), 256, 0, s>>>(3 * n, seg + (int64_t)(t - ta) * 6 * n + 3 * n, vt_int);
+      } else {
+        kept_to_internal_kernel<<<grid_for(n), 256, 0, s>>>(n, m->kept_of_internal, x_traj + (int64_t)(t + 1) * 3 * n, xn_int);
+        kept_to_internal_kernel<<<grid_for(n), 256, 0, s>>>(n, m->kept_of_internal, x_traj + (int64_t)t * 3 * n, xt_int);
+        kept_to_internal_kernel<<<grid_for(n), 256, 0, s>>>(n, m->kept_of_internal, v_traj + (int64_t)t * 3 * n, vt_int);
+      }
+      StepInfo info;
+      pd_status er = backward_step(c, xn_int, xt_int, vt_int, act_t, mu, loss_x(t), loss_v(t), gfext_int,
+                                   g_w_corot, g_w_vol, g_w_muscle, g_act ? g_act + (int64_t)t * e : nullptr,
+                                   g_mu, info, guess_b);
+      if (er != PD_OK) return er;
+      accumulate(stats, info, false);
+      if (!info.converged) all_ok = false;
+    }
+  }
+  if (g_x0) internal_to_kept_kernel<<<grid_for(n), 256, 0, s>>>(n, n, m->kept_of_internal, w.ax, g_x0);
+  if (g_v0) internal_to_kept_kernel<<<grid_for(n), 256, 0, s>>>(n, n, m->kept_of_internal, w.av, g_v0);
+  if (g_fext) internal_to_kept_kernel<<<grid_for(n), 256, 0, s>>>(n, n, m->kept_of_internal, gfext_int, g_fext);
+  if (seg) PD_CUDA_TRY(cudaFreeAsync(seg, s));
+  PD_CUDA_TRY(cudaStreamSynchronize(s));
+  check_flags(c, stats);
+  if (stats) stats->bwd_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  if (w.st_host->status & DEV_ERR_NAN) {
+    set_error("pd_backward: non-finite residual");
+    return PD_ERR_NAN;
+  }
+  if (!all_ok) {
+    set_error("pd_backward: some steps reached the iteration cap");
+    return PD_ERR_NOT_CONVERGED;
+  }
+  return PD_OK;
+}
+
+pd_status pd_local_step(pd_mesh mesh, const double* x, const double* act, int32_t precision, double* grad_E,
+                        double* energy, void* stream) {
+  pd_status ck = check_mesh(mesh, true);
+  if (ck != PD_OK) return ck;
+  if (!x) {
+    set_error("pd_local_step: x is required");
+    return PD_ERR_INVALID_ARG;
+  }
+  MeshImpl* m = &mesh->impl;
+  DeviceGuard g(m->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  Workspace& w = m->ws;
+  const int64_t n = m->h.n;
+  kept_to_internal_kernel<<<grid_for(n), 256, 0, s>>>(n, m->kept_of_internal, x, w.iox);
+  LocalArgs la{m, nullptr, w.iox, nullptr, act, precision};
+  double* pe = w.partials;
+  PD_CUDA_TRY(launch_element_forces(la, w.elembuf, pe, w.flags, s));
+  const int nbe = element_blocks(m);
+  double* etot = w.partials + nbe + 8;
+  sum_partials_kernel<<<1, 256, 0, s>>>(pe, nbe, etot);
+  double* gi = w.iov;
+  const int gb = grid_for(n);
+  if (precision == PD_PREC_MIXED)
+    gather_all_kernel<float><<<gb, 256, 0, s>>>(n, m->inc_ptr, m->inc, w.elembuf, w.iox,
+                                                m->k_contact > 0 ? m->contact : nullptr, m->k_contact, gi,
+                                                w.partials + nbe + 16, w.counters + 1, etot);
+  else
+    gather_all_kernel<double><<<gb, 256, 0, s>>>(n, m->inc_ptr, m->inc, w.elembuf, w.iox,
+                                                 m->k_contact > 0 ? m->contact : nullptr, m->k_contact, gi,
+                                                 w.partials + nbe + 16, w.counters + 1, etot);
+  if (grad_E) internal_to_kept_kernel<<<grid_for(n), 256, 0, s>>>(n, n, m->kept_of_internal, gi, grad_E);
+  if (energy) PD_CUDA_TRY(cudaMemcpyAsync(energy, etot, sizeof(double), cudaMemcpyDeviceToDevice, s));
+  PD_CUDA_TRY(cudaGetLastError());
+  return PD_OK;
+}
+
+pd_status pd_hessian_vector(pd_mesh mesh, const double* x, const double* act, const double* v, int32_t precision,
+                            double* Hv, void* stream) {
+  pd_status ck = check_mesh(mesh, true);
+  if (ck != PD_OK) return ck;
+  if (!x || !v || !Hv) {
+    set_error("pd_hessian_vector: x, v and Hv are required");
+    return PD_ERR_INVALID_ARG;
+  }
+  MeshImpl* m = &mesh->impl;
+  DeviceGuard g(m->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  Workspace& w = m->ws;
+  const int64_t n = m->h.n;
+  kept_to_internal_kernel<<<grid_for(n), 256, 0, s>>>(n, m->kept_of_internal, x, w.iox);
+  kept_to_internal_kernel<<<grid_for(n), 256, 0, s>>>(n, m->kept_of_internal, v, w.iov);
+  LocalArgs la{m, nullptr, w.iox, w.iov, act, precision};
+  PD_CUDA_TRY(launch_element_hvp(la, w.elembuf, w.flags, s));
+  PD_CUDA_TRY(launch_gather_hvp(m, nullptr, w.elembuf, precision, w.iox, w.iov, nullptr, w.Hd,
+                                w.partials + element_blocks(m), s));
+  internal_to_kept_kernel<<<grid_for(n), 256, 0, s>>>(n, m->h.nf, m->kept_of_internal, w.Hd, Hv);
+  PD_CUDA_TRY(cudaGetLastError());
+  return PD_OK;
+}
+
+pd_status pd_solve_A(pd_mesh mesh, const double* b, double* x, int32_t precision, void* stream) {
+  pd_status ck = check_mesh(mesh, true);
+  if (ck != PD_OK) return ck;
+  if (!b || !x) {
+    set_error("pd_solve_A: b and x are required");
+    return PD_ERR_INVALID_ARG;
+  }
+  MeshImpl* m = &mesh->impl;
+  if (precision == PD_PREC_MIXED && !m->Q32) {
+    set_error("pd_solve_A: FP32 panels exist only after a PD_PREC_MIXED factorisation");
+    return PD_ERR_INVALID_ARG;
+  }
+  DeviceGuard g(m->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  Workspace& w = m->ws;
+  const int64_t n = m->h.n;
+  kept_to_internal_kernel<<<grid_for(n), 256, 0, s>>>(n, m->kept_of_internal, b, w.iov);
+  PD_CUDA_TRY(solve_A(m, nullptr, w.iov, w.iox, precision, s));
+  internal_to_kept_kernel<<<grid_for(n), 256, 0, s>>>(n, m->h.nf, m->kept_of_internal, w.iox, x);
+  PD_CUDA_TRY(cudaGetLastError());
+  return PD_OK;
+}
+
+}  // extern "C"

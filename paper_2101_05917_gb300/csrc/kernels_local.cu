@@ -1,0 +1,475 @@
+// Local steps of PD forward (Alg. 1) and of the adjoint splitting iteration
+// (Alg. 2), plus the node gathers that turn element contributions into
+// grad g = M (x - y)/h^2 + sum_c w_c G_c^T (G_c x - p_c)      (Eqn 20)
+// and   Hess g v = M v/h^2 + sum_c w_c G_c^T (I - dp_c/dx) G_c v   (Eqns 21-22).
+//
+// Layout: one warp handles 4 hex cells; lane = 8*cell + k.  For loads and
+// stores k is a corner; for the per-Gauss-point math k is the Gauss point
+// (2x2x2 rule).  Corner data moves between the two roles with warp shuffles,
+// so there is no shared memory and no atomics: each cell writes its 8 corner
+// forces to an element buffer, and the gather sums them per node in the fixed
+// incidence order (bit-reproducible).
+#include "pd_internal.cuh"
+#include "pd_math.cuh"
+
+namespace pd {
+
+namespace {
+
+constexpr int kElemThreads = 256;   // 8 warps = 32 cells per block
+constexpr int kGatherThreads = 256;
+
+__device__ __forceinline__ int cbit(int a, int d) { return (a >> (2 - d)) & 1; }
+
+// d N_a / d X at Gauss point q, component d, for a cube of edge dx:
+// (s_ad / dx) * prod_{d' != d} (1 + s_ad' xi_qd') / 2, xi = +-1/sqrt(3).
+template <typename T>
+__device__ __forceinline__ T gradN(int a, int q, int d, T inv_dx) {
+  const T g = T(0.57735026918962576451);
+  const T wp = T(0.5) * (T(1) + g), wm = T(0.5) * (T(1) - g);
+  T prod = inv_dx;
+#pragma unroll
+  for (int dd = 0; dd < 3; ++dd) {
+    if (dd == d) continue;
+    prod *= (cbit(a, dd) == cbit(q, dd)) ? wp : wm;
+  }
+  return cbit(a, d) ? prod : -prod;
+}
+
+enum { MODE_FORCE = 0, MODE_HVP = 1, MODE_PGRAD = 2 };
+
+struct ElemParams {
+  const IterState* gate;
+  int64_t ne;
+  const int32_t* elems;
+  const double* x;
+  const double* v;
+  const double* act;
+  const double *wc, *wv, *wm, *fiber;
+  double dx, Vq;
+  void* out;            // elembuf (T) for FORCE/HVP
+  double* energy;       // block partials (FORCE)
+  double *g_wc, *g_wv, *g_wm, *g_act;   // PGRAD outputs
+  int* flags;
+};
+
+template <typename T, int MODE>
+__global__ void __launch_bounds__(kElemThreads) element_kernel(ElemParams p) {
+  if (p.gate && p.gate->converged) return;
+  const int lane = threadIdx.x & 31;
+  const int base = lane & ~7;
+  const int k = lane & 7;
+  const int64_t e = ((int64_t)blockIdx.x * kElemThreads + threadIdx.x) >> 3;
+  const bool valid = e < p.ne;
+  const T inv_dx = T(1.0 / p.dx);
+  const T Vq = T(p.Vq);
+
+  // ---- corner loads: relative displacement of corner k w.r.t. corner 0
+  int node = valid ? p.elems[e * 8 + k] : 0;
+  double xk[3] = {0, 0, 0};
+  if (valid) {
+    xk[0] = p.x[3 * (int64_t)node + 0];
+    xk[1] = p.x[3 * (int64_t)node + 1];
+    xk[2] = p.x[3 * (int64_t)node + 2];
+  }
+  T dk[3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    const double x0 = __shfl_sync(0xffffffffu, xk[i], base);
+    dk[i] = (T)((xk[i] - x0) - p.dx * (double)cbit(k, i));
+  }
+  T vk[3] = {T(0), T(0), T(0)};
+  if (MODE != MODE_FORCE && valid) {
+    vk[0] = (T)p.v[3 * (int64_t)node + 0];
+    vk[1] = (T)p.v[3 * (int64_t)node + 1];
+    vk[2] = (T)p.v[3 * (int64_t)node + 2];
+  }
+
+  // ---- per Gauss point (q = k): H = F - I and, when needed, dF = G_q v
+  T H[3][3] = {{T(0), T(0), T(0)}, {T(0), T(0), T(0)}, {T(0), T(0), T(0)}};
+  T dF[3][3] = {{T(0), T(0), T(0)}, {T(0), T(0), T(0)}, {T(0), T(0), T(0)}};
+#pragma unroll
+  for (int a = 0; a < 8; ++a) {
+    T da[3], va[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      da[i] = __shfl_sync(0xffffffffu, dk[i], base + a);
+      if (MODE != MODE_FORCE) va[i] = __shfl_sync(0xffffffffu, vk[i], base + a);
+    }
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      const T gN = gradN<T>(a, k, j, inv_dx);
+#pragma unroll
+      for (int i = 0; i < 3; ++i) {
+        H[i][j] += da[i] * gN;
+        if (MODE != MODE_FORCE) dF[i][j] += va[i] * gN;
+      }
+    }
+  }
+
+  const T wc = (valid && p.wc) ? (T)p.wc[e] : T(0);
+  const T wv = (valid && p.wv) ? (T)p.wv[e] : T(0);
+  const T wm = (valid && p.wm) ? (T)p.wm[e] : T(0);
+  const T act = (valid && p.act) ? (T)p.act[e] : T(0);
+
+  T S[3][3] = {{T(0), T(0), T(0)}, {T(0), T(0), T(0)}, {T(0), T(0), T(0)}};
+  T energy = T(0);
+  T gwc = T(0), gwv = T(0), gwm = T(0), gact = T(0);
+
+  SVD3<T> sv;
+  svd3_from_H<T>(H, sv);
+  if (valid && !(sv.sig[2] > T(0))) atomicOr(p.flags, DEV_ERR_INVERTED);
+  T M[3][3];
+  if (MODE != MODE_FORCE) rotate_in<T>(sv.U, dF, sv.V, M);
+
+  if (wc != T(0)) {
+    if (MODE == MODE_FORCE) {
+      add_UdVt<T>(S, sv.U, sv.sm1, sv.V, wc * Vq);
+      energy += T(0.5) * wc * Vq * (sv.sm1[0] * sv.sm1[0] + sv.sm1[1] * sv.sm1[1] + sv.sm1[2] * sv.sm1[2]);
+    } else if (MODE == MODE_HVP) {
+      T K[3][3];
+      corot_hvp_frame<T>(sv, M, K);
+      add_UKVt<T>(S, sv.U, K, sv.V, wc * Vq);
+    } else {
+      gwc = -Vq * (M[0][0] * sv.sm1[0] + M[1][1] * sv.sm1[1] + M[2][2] * sv.sm1[2]);
+    }
+  }
+  if (wv != T(0)) {
+    VolProj<T> vp;
+    if (volume_project<T>(sv, vp)) {
+      if (MODE == MODE_FORCE) {
+        add_UdVt<T>(S, sv.U, vp.gap, sv.V, wv * Vq);
+        energy += T(0.5) * wv * Vq * (vp.gap[0] * vp.gap[0] + vp.gap[1] * vp.gap[1] + vp.gap[2] * vp.gap[2]);
+      } else if (MODE == MODE_HVP) {
+        T K[3][3];
+        vol_hvp_frame<T>(sv, vp, M, K);
+        add_UKVt<T>(S, sv.U, K, sv.V, wv * Vq);
+      } else {
+        gwv = -Vq * (M[0][0] * vp.gap[0] + M[1][1] * vp.gap[1] + M[2][2] * vp.gap[2]);
+      }
+    }
+  }
+  if (wm != T(0)) {
+    const T m0 = (T)p.fiber[3 * e + 0], m1 = (T)p.fiber[3 * e + 1], m2 = (T)p.fiber[3 * e + 2];
+    const T mv[3] = {m0, m1, m2};
+    T f[3], Hm[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      Hm[i] = H[i][0] * m0 + H[i][1] * m1 + H[i][2] * m2;
+      f[i] = mv[i] + Hm[i];
+    }
+    // m^T E m with E = H + H^T + H^T H  ->  2 m.Hm + |Hm|^2
+    const T mEm = T(2) * (m0 * Hm[0] + m1 * Hm[1] + m2 * Hm[2]) + Hm[0] * Hm[0] + Hm[1] * Hm[1] + Hm[2] * Hm[2];
+    const T fn = tsqrt<T>(T(1) + mEm);
+    const T fnm1 = mEm / (T(1) + fn);            // |f| - 1
+    const T fh[3] = {f[0] / fn, f[1] / fn, f[2] / fn};
+    const T ex = fnm1 + act;                     // |f| - (1 - a)
+    if (MODE == MODE_FORCE) {
+      const T c = wm * Vq * ex;
+#pragma unroll
+      for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) S[i][j] += c * fh[i] * mv[j];
+      energy += T(0.5) * wm * Vq * ex * ex;
+    } else {
+      T df[3];
+#pragma unroll
+      for (int i = 0; i < 3; ++i) df[i] = dF[i][0] * m0 + dF[i][1] * m1 + dF[i][2] * m2;
+      const T fd = fh[0] * df[0] + fh[1] * df[1] + fh[2] * df[2];
+      if (MODE == MODE_HVP) {
+        const T c1 = ex / fn, c2 = (T(1) - act) / fn * fd;
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+          const T r = wm * Vq * (c1 * df[i] + c2 * fh[i]);
+#pragma unroll
+          for (int j = 0; j < 3; ++j) S[i][j] += r * mv[j];
+        }
+      } else {
+        gwm = -Vq * ex * fd;
+        gact = -wm * Vq * fd;
+      }
+    }
+  }
+
+  if (MODE == MODE_PGRAD) {
+    // reduce over the 8 Gauss points of the cell (fixed butterfly)
+#pragma unroll
+    for (int off = 4; off >= 1; off >>= 1) {
+      gwc += __shfl_xor_sync(0xffffffffu, gwc, off);
+      gwv += __shfl_xor_sync(0xffffffffu, gwv, off);
+      gwm += __shfl_xor_sync(0xffffffffu, gwm, off);
+      gact += __shfl_xor_sync(0xffffffffu, gact, off);
+    }
+    if (valid && k == 0) {
+      if (p.g_wc) p.g_wc[e] += (double)gwc;
+      if (p.g_wv) p.g_wv[e] += (double)gwv;
+      if (p.g_wm) p.g_wm[e] += (double)gwm;
+      if (p.g_act) p.g_act[e] = (double)gact;
+    }
+    return;
+  }
+
+  // ---- corner forces f_a = sum_q S_q gradN_a(q), lane k acting as corner a = k
+  T fa[3] = {T(0), T(0), T(0)};
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    T Sq[3][3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) Sq[i][j] = __shfl_sync(0xffffffffu, S[i][j], base + q);
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      const T gN = gradN<T>(k, q, j, inv_dx);
+#pragma unroll
+      for (int i = 0; i < 3; ++i) fa[i] += Sq[i][j] * gN;
+    }
+  }
+  if (valid) {
+    T* out = reinterpret_cast<T*>(p.out) + (e * 8 + k) * 3;
+    out[0] = fa[0];
+    out[1] = fa[1];
+    out[2] = fa[2];
+  }
+  if (MODE == MODE_FORCE) {
+    double en = valid ? (double)energy : 0.0;
+#pragma unroll
+    for (int off = 16; off >= 1; off >>= 1) en += __shfl_xor_sync(0xffffffffu, en, off);
+    __shared__ double wsum[kElemThreads / 32];
+    if (lane == 0) wsum[threadIdx.x >> 5] = en;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double t = 0;
+      for (int w = 0; w < kElemThreads / 32; ++w) t += wsum[w];
+      p.energy[blockIdx.x] = t;
+    }
+  }
+}
+
+// Fixed-order block reduction of NV values per thread into partials[blk*4 + i].
+template <int NV>
+__device__ __forceinline__ void block_partials(double (&v)[NV], double* partials) {
+  __shared__ double red[NV][kGatherThreads / 32];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+  for (int i = 0; i < NV; ++i) {
+    double t = v[i];
+#pragma unroll
+    for (int off = 16; off >= 1; off >>= 1) t += __shfl_xor_sync(0xffffffffu, t, off);
+    if (lane == 0) red[i][w] = t;
+  }
+  __syncthreads();
+  if (threadIdx.x < NV) {
+    double t = 0;
+    for (int k = 0; k < kGatherThreads / 32; ++k) t += red[threadIdx.x][k];
+    partials[blockIdx.x * 4 + threadIdx.x] = t;
+  }
+}
+
+struct GatherParams {
+  const IterState* gate;
+  int64_t nf;
+  const int32_t *inc_ptr, *inc;
+  const double* mass;
+  const uint8_t* contact;
+  double inv_h2, k_contact;
+  const void* elembuf;
+  const double* x;      // positions (contact)
+  const double* y;      // predictor (grad mode)
+  const double* v;      // dir (grad mode, for g.dir) / input vector (hvp mode)
+  const double* aux;    // hvp mode: second vector for a dot product (may be null)
+  double* out;
+  double* partials;
+};
+
+// grad g at x: partials = [kinetic + contact energy, |g|^2, g.dir, 0]
+template <typename T>
+__global__ void __launch_bounds__(kGatherThreads) gather_grad_kernel(GatherParams p) {
+  if (p.gate && p.gate->converged) return;
+  const int64_t c = (int64_t)blockIdx.x * kGatherThreads + threadIdx.x;
+  double acc[4] = {0, 0, 0, 0};
+  if (c < p.nf) {
+    const T* eb = reinterpret_cast<const T*>(p.elembuf);
+    double g[3] = {0, 0, 0};
+    for (int32_t q = p.inc_ptr[c]; q < p.inc_ptr[c + 1]; ++q) {
+      const int64_t slot = (int64_t)p.inc[q] * 3;
+      g[0] += (double)eb[slot + 0];
+      g[1] += (double)eb[slot + 1];
+      g[2] += (double)eb[slot + 2];
+    }
+    const double m = p.mass[c];
+    double kin = 0;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      const double d = p.x[3 * c + i] - p.y[3 * c + i];
+      g[i] += m * d * p.inv_h2;
+      kin += 0.5 * m * d * d * p.inv_h2;
+    }
+    if (p.contact && p.contact[c]) {
+      const double z = p.x[3 * c + 2];
+      if (z < 0.0) {
+        g[2] += p.k_contact * z;
+        kin += 0.5 * p.k_contact * z * z;
+      }
+    }
+    double gd = 0, gg = 0;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      p.out[3 * c + i] = g[i];
+      gg += g[i] * g[i];
+      if (p.v) gd += g[i] * p.v[3 * c + i];
+    }
+    acc[0] = kin;
+    acc[1] = gg;
+    acc[2] = gd;
+  }
+  block_partials<4>(acc, p.partials);
+}
+
+// Hv = M v/h^2 + sum elembuf + contact; partials = [v.Hv, aux.Hv, |Hv|^2, 0]
+template <typename T>
+__global__ void __launch_bounds__(kGatherThreads) gather_hvp_kernel(GatherParams p) {
+  if (p.gate && p.gate->converged) return;
+  const int64_t c = (int64_t)blockIdx.x * kGatherThreads + threadIdx.x;
+  double acc[4] = {0, 0, 0, 0};
+  if (c < p.nf) {
+    const T* eb = reinterpret_cast<const T*>(p.elembuf);
+    double g[3] = {0, 0, 0};
+    for (int32_t q = p.inc_ptr[c]; q < p.inc_ptr[c + 1]; ++q) {
+      const int64_t slot = (int64_t)p.inc[q] * 3;
+      g[0] += (double)eb[slot + 0];
+      g[1] += (double)eb[slot + 1];
+      g[2] += (double)eb[slot + 2];
+    }
+    const double m = p.mass[c];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) g[i] += m * p.v[3 * c + i] * p.inv_h2;
+    if (p.contact && p.contact[c] && p.x[3 * c + 2] < 0.0) g[2] += p.k_contact * p.v[3 * c + 2];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      p.out[3 * c + i] = g[i];
+      acc[0] += g[i] * p.v[3 * c + i];
+      if (p.aux) acc[1] += g[i] * p.aux[3 * c + i];
+      acc[2] += g[i] * g[i];
+    }
+  }
+  block_partials<4>(acc, p.partials);
+}
+
+ElemParams make_params(const LocalArgs& a) {
+  ElemParams p{};
+  p.gate = a.gate;
+  p.ne = a.m->h.e;
+  p.elems = a.m->elems;
+  p.x = a.x;
+  p.v = a.v;
+  p.act = a.act;
+  p.wc = a.m->wc;
+  p.wv = a.m->wv;
+  p.wm = a.m->wm;
+  p.fiber = a.m->fiber;
+  p.dx = a.m->h.dx;
+  p.Vq = a.m->h.dx * a.m->h.dx * a.m->h.dx / 8.0;
+  return p;
+}
+
+GatherParams make_gather(const MeshImpl* m) {
+  GatherParams p{};
+  p.nf = m->h.nf;
+  p.inc_ptr = m->inc_ptr;
+  p.inc = m->inc;
+  p.mass = m->mass;
+  p.contact = m->k_contact > 0 ? m->contact : nullptr;
+  p.inv_h2 = 1.0 / (m->h_step * m->h_step);
+  p.k_contact = m->k_contact;
+  return p;
+}
+
+}  // namespace
+
+int element_blocks(const MeshImpl* m) {
+  return (int)((m->h.e * 8 + kElemThreads - 1) / kElemThreads);
+}
+int gather_blocks(const MeshImpl* m) {
+  return (int)((m->h.nf + kGatherThreads - 1) / kGatherThreads);
+}
+
+cudaError_t launch_element_forces(const LocalArgs& a, void* elembuf, double* energy_partials,
+                                  int* flags, cudaStream_t s) {
+  ElemParams p = make_params(a);
+  p.out = elembuf;
+  p.energy = energy_partials;
+  p.flags = flags;
+  const int nb = element_blocks(a.m);
+  if (a.precision == PD_PREC_MIXED)
+    element_kernel<float, MODE_FORCE><<<nb, kElemThreads, 0, s>>>(p);
+  else
+    element_kernel<double, MODE_FORCE><<<nb, kElemThreads, 0, s>>>(p);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_element_hvp(const LocalArgs& a, void* elembuf, int* flags, cudaStream_t s) {
+  ElemParams p = make_params(a);
+  p.out = elembuf;
+  p.flags = flags;
+  const int nb = element_blocks(a.m);
+  if (a.precision == PD_PREC_MIXED)
+    element_kernel<float, MODE_HVP><<<nb, kElemThreads, 0, s>>>(p);
+  else
+    element_kernel<double, MODE_HVP><<<nb, kElemThreads, 0, s>>>(p);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_element_param_grads(const LocalArgs& a, double* g_wc, double* g_wv,
+                                       double* g_wm, double* g_act, cudaStream_t s) {
+  ElemParams p = make_params(a);
+  p.g_wc = g_wc;
+  p.g_wv = g_wv;
+  p.g_wm = g_wm;
+  p.g_act = g_act;
+  p.flags = a.m->ws.flags;
+  const int nb = element_blocks(a.m);
+  // parameter gradients are accumulated over steps: always FP64
+  element_kernel<double, MODE_PGRAD><<<nb, kElemThreads, 0, s>>>(p);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gather_grad(const MeshImpl* m, const IterState* gate, const void* elembuf,
+                               int precision, const double* x, const double* y, const double* dir,
+                               double* grad, double* partials, cudaStream_t s) {
+  GatherParams p = make_gather(m);
+  p.gate = gate;
+  p.elembuf = elembuf;
+  p.x = x;
+  p.y = y;
+  p.v = dir;
+  p.out = grad;
+  p.partials = partials;
+  const int nb = gather_blocks(m);
+  if (precision == PD_PREC_MIXED)
+    gather_grad_kernel<float><<<nb, kGatherThreads, 0, s>>>(p);
+  else
+    gather_grad_kernel<double><<<nb, kGatherThreads, 0, s>>>(p);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gather_hvp(const MeshImpl* m, const IterState* gate, const void* elembuf,
+                              int precision, const double* x, const double* v, const double* aux,
+                              double* Hv, double* partials, cudaStream_t s) {
+  GatherParams p = make_gather(m);
+  p.gate = gate;
+  p.elembuf = elembuf;
+  p.x = x;
+  p.v = v;
+  p.aux = aux;
+  p.out = Hv;
+  p.partials = partials;
+  const int nb = gather_blocks(m);
+  if (precision == PD_PREC_MIXED)
+    gather_hvp_kernel<float><<<nb, kGatherThreads, 0, s>>>(p);
+  else
+    gather_hvp_kernel<double><<<nb, kGatherThreads, 0, s>>>(p);
+  return cudaGetLastError();
+}
+
+}  // namespace pd

@@ -1,0 +1,356 @@
+// Host-side mesh analysis (C++).  The definitions below are the canonical ones
+// of this implementation; they are reproduced bit for bit by an independent
+// re-derivation in the test suite.
+//
+//  incidence   kept node -> entries e*8+a (cell e, corner a), ascending.
+//  ordering    nested dissection over grid boxes of free nodes: a box with more
+//              than leaf_max free nodes splits along its longest axis (ties x, y,
+//              z) at node plane mid = floor((lo+hi)/2); left part [lo, mid-1]
+//              first, then right part [mid+1, hi], then the plane's free nodes in
+//              grid-id order.  Boxes with 1..leaf_max free nodes are leaves in
+//              grid-id order.
+//  supernodes  every leaf and every non-empty separator plane.
+//  structure   rows(s) = cols(s) + {r >= first(s) adjacent to a column of s} +
+//              below(t) of every child t; parent(s) = owner of min below(s).
+//  levels      0 for supernodes without children, else 1 + max over children.
+#include <algorithm>
+#include <cstring>
+#include <numeric>
+#include <stdexcept>
+
+#include "pd_host.h"
+
+namespace pd {
+namespace {
+
+struct NDBuilder {
+  const HostMesh& m;
+  const std::vector<int64_t>& fi, &fj, &fk;   // grid coordinates of free nodes
+  std::vector<int64_t>& perm;
+  std::vector<int64_t>& firsts;
+  int leaf_max;
+
+  // `ids`: free-node indices inside the box, ascending grid id (== ascending index)
+  void rec(const int64_t lo[3], const int64_t hi[3], std::vector<int64_t>& ids) {
+    if (ids.empty()) return;
+    if ((int64_t)ids.size() <= leaf_max) {
+      firsts.push_back((int64_t)perm.size());
+      perm.insert(perm.end(), ids.begin(), ids.end());
+      return;
+    }
+    int64_t ext[3] = {hi[0] - lo[0] + 1, hi[1] - lo[1] + 1, hi[2] - lo[2] + 1};
+    int d = 0;
+    if (ext[1] > ext[d]) d = 1;
+    if (ext[2] > ext[d]) d = 2;
+    const int64_t mid = (lo[d] + hi[d]) / 2;   // lo, hi >= 0
+    std::vector<int64_t> left, right, sep;
+    for (int64_t f : ids) {
+      const int64_t c = d == 0 ? fi[f] : (d == 1 ? fj[f] : fk[f]);
+      if (c < mid) left.push_back(f);
+      else if (c > mid) right.push_back(f);
+      else sep.push_back(f);
+    }
+    ids.clear();
+    ids.shrink_to_fit();
+    int64_t lhi[3] = {hi[0], hi[1], hi[2]};
+    lhi[d] = mid - 1;
+    int64_t rlo[3] = {lo[0], lo[1], lo[2]};
+    rlo[d] = mid + 1;
+    rec(lo, lhi, left);
+    rec(rlo, hi, right);
+    if (!sep.empty()) {
+      firsts.push_back((int64_t)perm.size());
+      perm.insert(perm.end(), sep.begin(), sep.end());
+    }
+  }
+};
+
+}  // namespace
+
+std::string analyse(const pd_mesh_desc& d, HostMesh& m) {
+  if (d.nx <= 0 || d.ny <= 0 || d.nz <= 0) return "mesh: nx, ny, nz must be positive";
+  if (!(d.dx > 0)) return "mesh: dx must be positive";
+  if (!(d.density > 0)) return "mesh: density must be positive";
+  m.nx = d.nx; m.ny = d.ny; m.nz = d.nz; m.dx = d.dx; m.density = d.density;
+  for (int c = 0; c < 3; ++c) m.origin[c] = d.origin[c];
+  m.leaf_max = d.leaf_max > 0 ? d.leaf_max : 64;
+  const int64_t nx = d.nx, ny = d.ny, nz = d.nz;
+  const int64_t ncell = nx * ny * nz;
+  const int64_t ngrid = (nx + 1) * (ny + 1) * (nz + 1);
+  if (ngrid >= (int64_t)1 << 31) return "mesh: grid too large for 32-bit node ids";
+
+  // ---- kept cells and nodes
+  std::vector<int64_t> cell_corner;   // grid ids
+  cell_corner.reserve(8 * ncell);
+  for (int64_t ci = 0; ci < nx; ++ci)
+    for (int64_t cj = 0; cj < ny; ++cj)
+      for (int64_t ck = 0; ck < nz; ++ck) {
+        const int64_t cid = (ci * ny + cj) * nz + ck;
+        if (d.cell_mask && !d.cell_mask[cid]) continue;
+        for (int a = 0; a < 8; ++a) {
+          const int64_t di = (a >> 2) & 1, dj = (a >> 1) & 1, dk = a & 1;
+          cell_corner.push_back(((ci + di) * (ny + 1) + (cj + dj)) * (nz + 1) + (ck + dk));
+        }
+      }
+  m.e = (int64_t)cell_corner.size() / 8;
+  if (m.e == 0) return "mesh: no kept cells";
+  std::vector<int32_t> kept_of_grid(ngrid, -1);
+  for (int64_t g : cell_corner) kept_of_grid[g] = 0;
+  m.grid.clear();
+  for (int64_t g = 0; g < ngrid; ++g)
+    if (kept_of_grid[g] == 0) {
+      kept_of_grid[g] = (int32_t)m.grid.size();
+      m.grid.push_back(g);
+    }
+  m.n = (int64_t)m.grid.size();
+  m.elems_kept.resize(8 * m.e);
+  for (int64_t i = 0; i < 8 * m.e; ++i) m.elems_kept[i] = kept_of_grid[cell_corner[i]];
+  m.dirichlet_kept.assign(m.n, 0);
+  m.contact_kept.assign(m.n, 0);
+  if (d.dirichlet) for (int64_t i = 0; i < m.n; ++i) m.dirichlet_kept[i] = d.dirichlet[i] ? 1 : 0;
+  if (d.contact) for (int64_t i = 0; i < m.n; ++i) m.contact_kept[i] = d.contact[i] ? 1 : 0;
+
+  // ---- incidence (kept order)
+  m.inc_ptr_kept.assign(m.n + 1, 0);
+  for (int64_t i = 0; i < 8 * m.e; ++i) m.inc_ptr_kept[m.elems_kept[i] + 1]++;
+  for (int64_t i = 0; i < m.n; ++i) m.inc_ptr_kept[i + 1] += m.inc_ptr_kept[i];
+  m.inc_kept.assign(8 * m.e, 0);
+  {
+    std::vector<int64_t> fill(m.inc_ptr_kept.begin(), m.inc_ptr_kept.end() - 1);
+    for (int64_t i = 0; i < 8 * m.e; ++i) m.inc_kept[fill[m.elems_kept[i]]++] = i;  // i = e*8+a ascending
+  }
+
+  // ---- free nodes and nested dissection
+  std::vector<int64_t> free_kept;   // free index -> kept index
+  for (int64_t i = 0; i < m.n; ++i)
+    if (!m.dirichlet_kept[i]) free_kept.push_back(i);
+  m.nf = (int64_t)free_kept.size();
+  if (m.nf == 0) return "mesh: every node is fixed";
+  std::vector<int64_t> fi(m.nf), fj(m.nf), fk(m.nf);
+  for (int64_t f = 0; f < m.nf; ++f) {
+    const int64_t g = m.grid[free_kept[f]];
+    fk[f] = g % (nz + 1);
+    fj[f] = (g / (nz + 1)) % (ny + 1);
+    fi[f] = g / ((nz + 1) * (ny + 1));
+  }
+  m.perm.clear();
+  m.snode_first.clear();
+  {
+    std::vector<int64_t> ids(m.nf);
+    std::iota(ids.begin(), ids.end(), 0);
+    NDBuilder b{m, fi, fj, fk, m.perm, m.snode_first, m.leaf_max};
+    const int64_t lo[3] = {0, 0, 0}, hi[3] = {nx, ny, nz};
+    b.rec(lo, hi, ids);
+  }
+  m.snode_first.push_back(m.nf);
+  m.ns = (int64_t)m.snode_first.size() - 1;
+
+  // ---- internal numbering
+  m.internal_of_kept.assign(m.n, -1);
+  m.kept_of_internal.assign(m.n, -1);
+  for (int64_t c = 0; c < m.nf; ++c) {
+    const int64_t k = free_kept[m.perm[c]];
+    m.internal_of_kept[k] = (int32_t)c;
+    m.kept_of_internal[c] = (int32_t)k;
+  }
+  {
+    int64_t next = m.nf;
+    for (int64_t k = 0; k < m.n; ++k)
+      if (m.dirichlet_kept[k]) {
+        m.internal_of_kept[k] = (int32_t)next;
+        m.kept_of_internal[next] = (int32_t)k;
+        ++next;
+      }
+  }
+  m.elems.resize(8 * m.e);
+  for (int64_t i = 0; i < 8 * m.e; ++i) m.elems[i] = m.internal_of_kept[m.elems_kept[i]];
+  m.X.resize(3 * m.n);
+  m.contact.assign(m.n, 0);
+  for (int64_t in = 0; in < m.n; ++in) {
+    const int64_t g = m.grid[m.kept_of_internal[in]];
+    const int64_t k = g % (nz + 1), j = (g / (nz + 1)) % (ny + 1), i = g / ((nz + 1) * (ny + 1));
+    m.X[3 * in + 0] = d.origin[0] + d.dx * (double)i;
+    m.X[3 * in + 1] = d.origin[1] + d.dx * (double)j;
+    m.X[3 * in + 2] = d.origin[2] + d.dx * (double)k;
+    m.contact[in] = m.contact_kept[m.kept_of_internal[in]];
+  }
+  m.mass.assign(m.n, 0.0);
+  const double mcorner = d.density * d.dx * d.dx * d.dx / 8.0;
+  for (int64_t i = 0; i < 8 * m.e; ++i) m.mass[m.elems[i]] += mcorner;
+  m.inc_ptr.assign(m.n + 1, 0);
+  for (int64_t i = 0; i < 8 * m.e; ++i) m.inc_ptr[m.elems[i] + 1]++;
+  for (int64_t i = 0; i < m.n; ++i) m.inc_ptr[i + 1] += m.inc_ptr[i];
+  m.inc.assign(8 * m.e, 0);
+  {
+    std::vector<int32_t> fill(m.inc_ptr.begin(), m.inc_ptr.end() - 1);
+    for (int64_t i = 0; i < 8 * m.e; ++i) m.inc[fill[m.elems[i]]++] = (int32_t)i;
+  }
+
+  // ---- adjacency of L_A over columns (free nodes share a kept cell), sorted
+  std::vector<int64_t> adj_ptr(m.nf + 1, 0);
+  std::vector<int32_t> adj;
+  {
+    std::vector<int64_t> mark(m.nf, -1);
+    std::vector<int32_t> tmp;
+    for (int64_t c = 0; c < m.nf; ++c) {
+      tmp.clear();
+      for (int32_t p = m.inc_ptr[c]; p < m.inc_ptr[c + 1]; ++p) {
+        const int32_t e = m.inc[p] / 8;
+        for (int b = 0; b < 8; ++b) {
+          const int32_t o = m.elems[8 * e + b];
+          if (o < m.nf && mark[o] != c) {
+            mark[o] = c;
+            tmp.push_back(o);
+          }
+        }
+      }
+      std::sort(tmp.begin(), tmp.end());
+      adj.insert(adj.end(), tmp.begin(), tmp.end());
+      adj_ptr[c + 1] = (int64_t)adj.size();
+    }
+  }
+
+  // ---- supernodal structure
+  std::vector<int64_t> owner(m.nf);
+  for (int64_t s = 0; s < m.ns; ++s)
+    for (int64_t c = m.snode_first[s]; c < m.snode_first[s + 1]; ++c) owner[c] = s;
+  m.parent.assign(m.ns, -1);
+  std::vector<std::vector<int64_t>> children(m.ns);
+  m.row_ptr.assign(m.ns + 1, 0);
+  m.rows.clear();
+  {
+    std::vector<int64_t> mark(m.nf, -1);
+    std::vector<int32_t> tmp;
+    for (int64_t s = 0; s < m.ns; ++s) {
+      const int64_t f = m.snode_first[s], l = m.snode_first[s + 1];
+      tmp.clear();
+      auto add = [&](int64_t r) {
+        if (r >= f && mark[r] != s) {
+          mark[r] = s;
+          tmp.push_back((int32_t)r);
+        }
+      };
+      for (int64_t c = f; c < l; ++c) {
+        add(c);
+        for (int64_t p = adj_ptr[c]; p < adj_ptr[c + 1]; ++p) add(adj[p]);
+      }
+      for (int64_t t : children[s])
+        for (int64_t p = m.row_ptr[t]; p < m.row_ptr[t + 1]; ++p)
+          if (m.rows[p] >= m.snode_first[t + 1]) add(m.rows[p]);
+      std::sort(tmp.begin(), tmp.end());
+      m.rows.insert(m.rows.end(), tmp.begin(), tmp.end());
+      m.row_ptr[s + 1] = (int64_t)m.rows.size();
+      const int64_t nrs = (int64_t)tmp.size(), ncs = l - f;
+      if (nrs > ncs) {
+        const int64_t p = owner[tmp[ncs]];
+        m.parent[s] = p;
+        children[p].push_back(s);
+      }
+    }
+  }
+  m.level.assign(m.ns, 0);
+  for (int64_t s = 0; s < m.ns; ++s)
+    for (int64_t t : children[s]) m.level[s] = std::max(m.level[s], m.level[t] + 1);
+  m.nlev = 0;
+  for (int64_t s = 0; s < m.ns; ++s) m.nlev = std::max(m.nlev, m.level[s] + 1);
+  m.level_ptr.assign(m.nlev + 1, 0);
+  for (int64_t s = 0; s < m.ns; ++s) m.level_ptr[m.level[s] + 1]++;
+  for (int64_t L = 0; L < m.nlev; ++L) m.level_ptr[L + 1] += m.level_ptr[L];
+  m.level_list.assign(m.ns, 0);
+  {
+    std::vector<int64_t> fill(m.level_ptr.begin(), m.level_ptr.end() - 1);
+    for (int64_t s = 0; s < m.ns; ++s) m.level_list[fill[m.level[s]]++] = s;
+  }
+  m.child_ptr.assign(m.ns + 1, 0);
+  m.child_list.clear();
+  for (int64_t s = 0; s < m.ns; ++s) {
+    m.child_list.insert(m.child_list.end(), children[s].begin(), children[s].end());
+    m.child_ptr[s + 1] = (int64_t)m.child_list.size();
+  }
+  // relative indices of below rows in the parent
+  m.rel_ptr.assign(m.ns + 1, 0);
+  m.rel.clear();
+  for (int64_t s = 0; s < m.ns; ++s) {
+    const int64_t p = m.parent[s];
+    const int64_t ncs = m.nc(s);
+    if (p >= 0) {
+      const int32_t* pr = m.rows.data() + m.row_ptr[p];
+      const int64_t pn = m.nr(p);
+      for (int64_t q = m.row_ptr[s] + ncs; q < m.row_ptr[s + 1]; ++q) {
+        const int32_t* it = std::lower_bound(pr, pr + pn, m.rows[q]);
+        if (it == pr + pn || *it != m.rows[q]) return "internal: below row missing in parent";
+        m.rel.push_back((int32_t)(it - pr));
+      }
+    }
+    m.rel_ptr[s + 1] = (int64_t)m.rel.size();
+  }
+  // panel / front offsets
+  m.panel_off.assign(m.ns + 1, 0);
+  m.front_off.assign(m.ns + 1, 0);
+  for (int64_t s = 0; s < m.ns; ++s) {
+    m.panel_off[s + 1] = m.panel_off[s] + m.nr(s) * m.nc(s);
+    m.front_off[s + 1] = m.front_off[s] + m.nr(s) * m.nr(s);
+  }
+  // forward-solve gather lists per supernode position
+  m.pos_off = m.row_ptr;
+  const int64_t npos = m.row_ptr[m.ns];
+  m.gath_ptr.assign(npos + 1, 0);
+  for (int64_t s = 0; s < m.ns; ++s) {
+    const int64_t p = m.parent[s];
+    if (p < 0) continue;
+    for (int64_t i = 0; i < m.rel_ptr[s + 1] - m.rel_ptr[s]; ++i)
+      m.gath_ptr[m.pos_off[p] + m.rel[m.rel_ptr[s] + i] + 1]++;
+  }
+  for (int64_t k = 0; k < npos; ++k) m.gath_ptr[k + 1] += m.gath_ptr[k];
+  m.gath.assign(m.gath_ptr[npos], 0);
+  {
+    std::vector<int64_t> fill(m.gath_ptr.begin(), m.gath_ptr.end() - 1);
+    for (int64_t p = 0; p < m.ns; ++p)            // parents ascending
+      for (int64_t ci = m.child_ptr[p]; ci < m.child_ptr[p + 1]; ++ci) {   // children ascending
+        const int64_t s = m.child_list[ci];
+        for (int64_t i = 0; i < m.rel_ptr[s + 1] - m.rel_ptr[s]; ++i) {
+          const int64_t k = m.pos_off[p] + m.rel[m.rel_ptr[s] + i];
+          m.gath[fill[k]++] = (int32_t)(m.rel_ptr[s] + i);
+        }
+      }
+  }
+
+  // ---- L_A assembly map (lower triangle, per column in supernode order)
+  m.la_target.clear();
+  m.la_diag_node.clear();
+  m.la_cptr.assign(1, 0);
+  m.la_contrib.clear();
+  {
+    std::vector<std::vector<int32_t>> contrib_of_row;   // scratch per column
+    for (int64_t s = 0; s < m.ns; ++s) {
+      const int32_t* sr = m.rows.data() + m.row_ptr[s];
+      const int64_t nrs = m.nr(s);
+      for (int64_t c = m.snode_first[s]; c < m.snode_first[s + 1]; ++c) {
+        // rows r >= c adjacent to c, with their element contributions
+        std::vector<std::pair<int32_t, int32_t>> items;   // (row, e*64+a*8+b)
+        for (int32_t p = m.inc_ptr[c]; p < m.inc_ptr[c + 1]; ++p) {
+          const int32_t e = m.inc[p] / 8, b = m.inc[p] % 8;
+          for (int a = 0; a < 8; ++a) {
+            const int32_t r = m.elems[8 * e + a];
+            if (r < m.nf && r >= c) items.push_back({r, e * 64 + a * 8 + b});
+          }
+        }
+        std::sort(items.begin(), items.end());
+        const int64_t pc = c - m.snode_first[s];
+        size_t i = 0;
+        while (i < items.size()) {
+          const int32_t r = items[i].first;
+          const int32_t* it = std::lower_bound(sr, sr + nrs, r);
+          if (it == sr + nrs || *it != r) return "internal: L_A row outside supernode structure";
+          m.la_target.push_back(m.front_off[s] + (int64_t)(it - sr) + pc * nrs);
+          m.la_diag_node.push_back(r == c ? (int32_t)c : -1);
+          while (i < items.size() && items[i].first == r) m.la_contrib.push_back(items[i++].second);
+          m.la_cptr.push_back((int64_t)m.la_contrib.size());
+        }
+      }
+    }
+  }
+  return "";
+}
+
+}  // namespace pd

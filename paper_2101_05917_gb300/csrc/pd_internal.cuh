@@ -1,0 +1,145 @@
+// Internal declarations shared by the CUDA translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "diffpd.h"
+#include "pd_host.h"
+#include "pd_iter.cuh"
+
+namespace pd {
+
+// ------------------------------------------------------------------ errors
+void set_error(const std::string& msg);
+#define PD_CUDA_TRY(expr)                                                        \
+  do {                                                                           \
+    cudaError_t _e = (expr);                                                     \
+    if (_e != cudaSuccess) {                                                     \
+      ::pd::set_error(std::string(#expr) + ": " + cudaGetErrorString(_e));       \
+      return PD_ERR_CUDA;                                                        \
+    }                                                                            \
+  } while (0)
+
+// Device status bits raised by kernels (integer atomicOr; never on data).
+enum : int {
+  DEV_ERR_NOT_SPD = 1,
+  DEV_ERR_INVERTED = 2,
+  DEV_ERR_NAN = 4,
+};
+
+// ---------------------------------------------------------------- buffers
+template <typename T>
+struct DArr {
+  T* p = nullptr;
+  size_t n = 0;
+};
+
+// Solve schedule for one level of the supernodal tree.
+struct SolveLevel {
+  int64_t fwd_off = 0, fwd_cnt = 0;   // tasks (s, first row) in fwd_tasks
+  int64_t bwd_off = 0, bwd_cnt = 0;   // tasks (s, first column) in bwd_tasks
+};
+
+// Factorisation schedule for one level.
+struct FactorLevel {
+  int64_t list_off = 0, count = 0;    // supernode ids in level_list (device copy)
+  int64_t max_nc = 0, max_nr = 0, max_child_nb2 = 0, max_children = 0;
+};
+
+
+struct Workspace {
+  // per-node / per-DoF vectors (FP64, internal order)
+  double *x = nullptr, *xt = nullptr, *y = nullptr, *xprev = nullptr, *vprev = nullptr;
+  double *grad = nullptr, *gradt = nullptr, *dir = nullptr, *q = nullptr, *r = nullptr;
+  double *S = nullptr, *Y = nullptr;          // L-BFGS history (m x 3nf each)
+  double *z = nullptr, *gs = nullptr, *Hd = nullptr;   // backward
+  double *ax = nullptr, *av = nullptr, *gbar = nullptr, *fext = nullptr, *ffric = nullptr;
+  double *iox = nullptr, *iov = nullptr;      // kept-order staging
+  void* elembuf = nullptr;                    // (8e x 3) T
+  double* partials = nullptr;                 // block partial sums
+  unsigned int* counters = nullptr;           // last-block counters
+  IterState* st = nullptr;                    // device iteration state
+  IterState* st_host = nullptr;               // pinned mirror
+  int* flags = nullptr;                       // device status bits
+  void* solve_u = nullptr;                    // (3 nf) T
+  void* solve_W = nullptr;                    // (3 * below rows) T
+  double* act_cur = nullptr;                  // unused placeholder for per-step actuation
+  int lbfgs_m = 0;
+  size_t bytes = 0;
+};
+
+struct MeshImpl {
+  HostMesh h;
+  int device = -1;
+  // geometry / topology (device)
+  int32_t *elems = nullptr, *inc_ptr = nullptr, *inc = nullptr, *kept_of_internal = nullptr;
+  double *X = nullptr, *mass = nullptr;
+  uint8_t* contact = nullptr;
+  // solve structure (device)
+  int64_t *snode_first = nullptr, *row_ptr = nullptr, *panel_off = nullptr, *rel_ptr = nullptr;
+  int64_t *gath_ptr = nullptr, *front_off = nullptr, *level_list = nullptr, *child_ptr = nullptr,
+          *child_list = nullptr;
+  int32_t *rows = nullptr, *gath = nullptr, *rel = nullptr;
+  int2 *fwd_tasks = nullptr, *bwd_tasks = nullptr;
+  std::vector<SolveLevel> slevels;
+  std::vector<FactorLevel> flevels;
+  // assembly map (device)
+  int64_t *la_target = nullptr, *la_cptr = nullptr;
+  int32_t *la_diag_node = nullptr, *la_contrib = nullptr;
+  // material state
+  bool factorized = false;
+  int precision = PD_PREC_FP64;
+  double h_step = 0, grav[3] = {0, 0, 0}, k_contact = 0;
+  double *wc = nullptr, *wv = nullptr, *wm = nullptr, *fiber = nullptr;   // null = energy absent
+  double *wc_buf = nullptr, *wv_buf = nullptr, *wm_buf = nullptr, *fiber_buf = nullptr;
+  // factor panels Q_s = [L11^-1 ; L21 L11^-1] (column-major nr x nc)
+  double* Q64 = nullptr;
+  float* Q32 = nullptr;
+  Workspace ws;
+  std::vector<void*> allocations;
+};
+
+// ------------------------------------------------------------------ launchers
+// Local steps (kernels_local.cu).  Vectors are internal-order node-major.
+struct LocalArgs {
+  const MeshImpl* m;
+  const IterState* gate;   // skip the launch's work once gate->converged is set (may be null)
+  const double* x;       // (n,3) positions
+  const double* v;       // (n,3) direction for HVP / adjoint for param grads
+  const double* act;     // (e) contraction or null
+  int precision;         // PD_PREC_FP64 / PD_PREC_MIXED (float local step)
+};
+// forces into ws.elembuf; energy block partials into partials[0..nblk)
+cudaError_t launch_element_forces(const LocalArgs& a, void* elembuf, double* energy_partials,
+                                  int* flags, cudaStream_t s);
+cudaError_t launch_element_hvp(const LocalArgs& a, void* elembuf, int* flags, cudaStream_t s);
+cudaError_t launch_element_param_grads(const LocalArgs& a, double* g_wc, double* g_wv,
+                                       double* g_wm, double* g_act, cudaStream_t s);
+int element_blocks(const MeshImpl* m);
+
+// Gathers (K2): out[c] = sum over incidence of elembuf + node terms, for c < nf
+// (gradient mode: + m (x - y)/h^2 + contact force; hvp mode: + m v/h^2 + contact).
+cudaError_t launch_gather_grad(const MeshImpl* m, const IterState* gate, const void* elembuf,
+                               int precision, const double* x, const double* y, const double* dir,
+                               double* grad, double* partials, cudaStream_t s);
+cudaError_t launch_gather_hvp(const MeshImpl* m, const IterState* gate, const void* elembuf,
+                              int precision, const double* x, const double* v, const double* gs,
+                              double* Hv, double* partials, cudaStream_t s);
+int gather_blocks(const MeshImpl* m);
+
+// Factorisation (kernels_factor.cu)
+pd_status factorize_device(MeshImpl* m, cudaStream_t s);
+
+// Triangular solves (kernels_solve.cu): out = A^-1 b on the free DoFs
+// (internal order, 3 nf entries each).
+// gate: skipped when gate->converged or !gate->accepted (may be null).
+cudaError_t solve_A(const MeshImpl* m, const IterState* gate, const double* b, double* out,
+                    int precision, cudaStream_t s);
+void build_solve_schedule(const HostMesh& h, std::vector<int2>& fwd, std::vector<int2>& bwd,
+                          std::vector<SolveLevel>& levels);
+
+}  // namespace pd

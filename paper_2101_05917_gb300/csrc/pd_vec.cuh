@@ -1,0 +1,599 @@
+// Iteration control of PD forward (Alg. 1 + L-BFGS, Sec. 4 "Further acceleration
+// with quasi-Newton methods") and of the adjoint solve (Alg. 2 + L-BFGS), with
+// every decision taken on the device so that the host only polls one flag.
+//
+// Vectors are FP64, internal node order, the free DoFs first (3 nf entries).
+// Reductions: each block writes one partial; the last block to finish (integer
+// ticket) sums the partials in index order, so results do not depend on block
+// scheduling.
+#pragma once
+
+#include "pd_internal.cuh"
+#include "pd_iter.cuh"
+
+namespace pd {
+
+struct StateCfg {
+  double tol, noise;
+  int m, ls_max, max_iter, accepted;
+};
+
+struct VecCtx {
+  int64_t n3;
+  IterState* st;
+  double* partials;
+  unsigned* counter;
+};
+
+struct PredParams {
+  int64_t n, nf;
+  const double *xi, *vi, *fext, *mass, *X;
+  const uint8_t* contact;
+  double k, mu, h, grav[3];
+  double *y, *xt, *x;
+  double* partials;
+  unsigned* counter;
+  IterState* st;
+};
+
+struct BwdStateParams {
+  int64_t n, nf;
+  const double *z, *mass, *xi, *vi;
+  const uint8_t* contact;
+  double k, mu, h, inv_h, inv_h2;
+  double *ax, *av, *gfext;
+  const double *gx_t, *gv_t;     // kept order, may be null
+  const int32_t* kept_of_internal;
+  double* gmu;
+  double* partials;
+  unsigned* counter;
+};
+
+namespace {
+
+constexpr int kT = 256;
+
+__device__ __forceinline__ double block_sum(double v) {
+  __shared__ double sh[kT / 32];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+  for (int off = 16; off >= 1; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+  __syncthreads();
+  if (lane == 0) sh[w] = v;
+  __syncthreads();
+  double t = 0;
+  if (threadIdx.x == 0)
+    for (int i = 0; i < kT / 32; ++i) t += sh[i];
+  return t;   // valid in thread 0
+}
+
+// Returns true in thread 0 of the last block, with *total = sum of all block partials.
+__device__ __forceinline__ bool grid_sum(double part, double* partials, unsigned* counter, double* total) {
+  const double b = block_sum(part);
+  __shared__ int is_last;
+  if (threadIdx.x == 0) {
+    partials[blockIdx.x] = b;
+    __threadfence();
+    const unsigned t = atomicAdd(counter, 1u);
+    is_last = (t == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (!is_last) return false;
+  __threadfence();
+  double acc = 0;
+  for (int i = threadIdx.x; i < (int)gridDim.x; i += kT) acc += __ldcg(partials + i);
+  const double tot = block_sum(acc);
+  if (threadIdx.x == 0) {
+    *counter = 0u;
+    *total = tot;
+  }
+  return threadIdx.x == 0;
+}
+
+__device__ __forceinline__ int idx_newest(const IterState* st, int k) {
+  return (st->head + st->count - 1 - k + 2 * st->m) % st->m;
+}
+__device__ __forceinline__ int idx_oldest(const IterState* st, int k) { return (st->head + k) % st->m; }
+
+// reduce up to `n` values at stride `stride` (fixed order), single block
+__device__ __forceinline__ double block_reduce_strided(const double* a, int64_t n, int stride, int off) {
+  double acc = 0;
+  for (int64_t i = threadIdx.x; i < n; i += kT) acc += a[i * stride + off];
+  return block_sum(acc);
+}
+
+}  // namespace
+
+inline int vec_blocks(int64_t n3) {
+  int64_t b = (n3 + kT * 4 - 1) / (kT * 4);
+  if (b < 1) b = 1;
+  if (b > 1184) b = 1184;   // 8 x 148; partial buffers hold at least this many
+  return (int)b;
+}
+
+__global__ void state_reset_kernel(IterState* st, StateCfg cfg) {
+  st->alpha = 1.0;
+  st->slope = 0.0;
+  st->g_acc = 0.0;
+  st->gn2_acc = 0.0;
+  st->ref2 = 0.0;
+  st->refM2 = 0.0;
+  st->tol2 = cfg.tol * cfg.tol;
+  st->c1 = 1e-4;
+  st->noise = cfg.noise;
+  st->m = cfg.m;
+  st->head = 0;
+  st->count = 0;
+  st->pslot = 0;
+  st->push = 0;
+  st->iters = 0;
+  st->evals = 0;
+  st->ls_tries = 0;
+  st->ls_total = 0;
+  st->ls_max = cfg.ls_max;
+  st->max_iter = cfg.max_iter;
+  st->accepted = cfg.accepted;
+  st->converged = 0;
+  st->hit_max = 0;
+  st->force_accept = 0;
+  st->status = 0;
+}
+
+// ---------------------------------------------------------------- forward
+// y = x + h v + h^2 (g + (f_ext + f_fric)/m); trial xt = y on free nodes, rest
+// position on Dirichlet nodes; friction from the state at the start of the step
+// (Sec. 5.1: penalty friction is added to f_ext).
+__global__ void predictor_kernel(PredParams p) {
+  double part = 0;
+  for (int64_t c = (int64_t)blockIdx.x * kT + threadIdx.x; c < p.n; c += (int64_t)gridDim.x * kT) {
+    const double m = p.mass[c];
+    double f[3] = {0, 0, 0};
+    if (p.fext) { f[0] = p.fext[3 * c]; f[1] = p.fext[3 * c + 1]; f[2] = p.fext[3 * c + 2]; }
+    if (p.contact && p.contact[c]) {
+      const double z = p.xi[3 * c + 2];
+      const double vx = p.vi[3 * c], vy = p.vi[3 * c + 1];
+      const double nv = sqrt(vx * vx + vy * vy);
+      if (z < 0.0 && nv > 0.0) {
+        const double fn = p.k * (-z);
+        const double mag = fmin(p.mu * fn, m * nv / p.h);
+        f[0] -= mag * vx / nv;
+        f[1] -= mag * vy / nv;
+      }
+    }
+    if (c < p.nf) {
+#pragma unroll
+      for (int i = 0; i < 3; ++i) {
+        const double yv = p.xi[3 * c + i] + p.h * p.vi[3 * c + i] + p.h * p.h * (p.grav[i] + f[i] / m);
+        p.y[3 * c + i] = yv;
+        p.xt[3 * c + i] = yv;
+        const double my = m * yv / (p.h * p.h);
+        part += my * my;
+      }
+    } else {
+#pragma unroll
+      for (int i = 0; i < 3; ++i) {
+        p.y[3 * c + i] = p.X[3 * c + i];
+        p.xt[3 * c + i] = p.X[3 * c + i];
+        p.x[3 * c + i] = p.X[3 * c + i];
+      }
+    }
+  }
+  double tot;
+  if (grid_sum(part, p.partials, p.counter, &tot)) p.st->refM2 = tot;
+}
+
+__global__ void decide_fwd_kernel(IterState* st, const double* energy_partials, int64_t nbe,
+                                  const double* gather_partials, int64_t nbg) {
+  const double e = block_reduce_strided(energy_partials, nbe, 1, 0);
+  const double kin = block_reduce_strided(gather_partials, nbg, 4, 0);
+  const double gn2 = block_reduce_strided(gather_partials, nbg, 4, 1);
+  const double gd = block_reduce_strided(gather_partials, nbg, 4, 2);
+  if (threadIdx.x != 0) return;
+  if (st->converged) return;
+  const double g = e + kin;
+  st->g_t = g;
+  st->gn2_t = gn2;
+  st->gd_t = gd;
+  if (!isfinite(g) || !isfinite(gn2)) {
+    st->status |= DEV_ERR_NAN;
+    st->converged = 1;
+    st->accepted = 0;
+    return;
+  }
+  const bool first = st->evals == 0 || st->force_accept;
+  if (st->evals == 0) st->ref2 = fmax(gn2, st->refM2);
+  st->evals += 1;
+  bool acc = first;
+  if (!first) {
+    acc = g <= st->g_acc + st->c1 * st->alpha * st->slope + st->noise * fabs(st->g_acc);
+    if (!acc && st->ls_tries >= st->ls_max) acc = true;
+  }
+  if (acc) {
+    st->push = 0;
+    if (!first && st->m > 0) {
+      const double sy = st->alpha * (gd - st->slope);   // s = alpha d, y = grad_t - grad
+      if (sy > 0.0) {
+        int slot;
+        if (st->count < st->m) {
+          slot = (st->head + st->count) % st->m;
+          st->count += 1;
+        } else {
+          slot = st->head;
+          st->head = (st->head + 1) % st->m;
+        }
+        st->rho[slot] = 1.0 / sy;
+        st->pslot = slot;
+        st->push = 1;
+      }
+    }
+    st->g_acc = g;
+    st->gn2_acc = gn2;
+    st->accepted = 1;
+    st->ls_tries = 0;
+    st->force_accept = 0;
+    if (!first) st->iters += 1;
+    st->alpha = 1.0;
+    if (gn2 <= st->tol2 * st->ref2) {
+      st->converged = 1;
+    } else if (st->iters >= st->max_iter) {
+      st->converged = 1;
+      st->hit_max = 1;
+    }
+  } else {
+    st->accepted = 0;
+    st->alpha *= 0.5;
+    st->ls_tries += 1;
+    st->ls_total += 1;
+  }
+}
+
+// accepted trial: history pair, x <- xt, grad <- gradt, q <- gradt
+__global__ void accept_fwd_kernel(IterState* st, int64_t n3, double* x, const double* xt, double* grad,
+                                  const double* gradt, double* q, double* S, double* Y) {
+  if (!st->accepted) return;
+  const int push = st->push;
+  const int slot = st->pslot;
+  for (int64_t i = (int64_t)blockIdx.x * kT + threadIdx.x; i < n3; i += (int64_t)gridDim.x * kT) {
+    const double xn = xt[i], gn = gradt[i];
+    if (push) {
+      S[(int64_t)slot * n3 + i] = xn - x[i];
+      Y[(int64_t)slot * n3 + i] = gn - grad[i];
+    }
+    x[i] = xn;
+    grad[i] = gn;
+    q[i] = gn;
+  }
+}
+
+// two-loop recursion, first loop (newest -> oldest): q -= al_k y_k, al_k = rho_k s_k.q
+__global__ void lbfgs_loop1_kernel(VecCtx c, int k, const double* S, const double* Y, double* q) {
+  IterState* st = c.st;
+  if (st->converged || !st->accepted) return;
+  const int cnt = st->count;
+  if (k > cnt) return;
+  const int ip = k > 0 ? idx_newest(st, k - 1) : -1;
+  const int ic = k < cnt ? idx_newest(st, k) : -1;
+  const double alp = ip >= 0 ? st->al[ip] : 0.0;
+  double part = 0;
+  for (int64_t i = (int64_t)blockIdx.x * kT + threadIdx.x; i < c.n3; i += (int64_t)gridDim.x * kT) {
+    double qi = q[i];
+    if (ip >= 0) {
+      qi -= alp * Y[(int64_t)ip * c.n3 + i];
+      q[i] = qi;
+    }
+    if (ic >= 0) part += S[(int64_t)ic * c.n3 + i] * qi;
+  }
+  if (ic < 0) return;
+  double tot;
+  if (grid_sum(part, c.partials, c.counter, &tot)) st->al[ic] = st->rho[ic] * tot;
+}
+
+// second loop (oldest -> newest): be_k = rho_k y_k.r, r += s_k (al_k - be_k)
+__global__ void lbfgs_loop2_kernel(VecCtx c, int k, const double* S, const double* Y, double* r) {
+  IterState* st = c.st;
+  if (st->converged || !st->accepted) return;
+  const int cnt = st->count;
+  if (k > cnt) return;
+  const int ip = k > 0 ? idx_oldest(st, k - 1) : -1;
+  const int ic = k < cnt ? idx_oldest(st, k) : -1;
+  const double coef = ip >= 0 ? st->al[ip] - st->be[ip] : 0.0;
+  double part = 0;
+  for (int64_t i = (int64_t)blockIdx.x * kT + threadIdx.x; i < c.n3; i += (int64_t)gridDim.x * kT) {
+    double ri = r[i];
+    if (ip >= 0) {
+      ri += coef * S[(int64_t)ip * c.n3 + i];
+      r[i] = ri;
+    }
+    if (ic >= 0) part += Y[(int64_t)ic * c.n3 + i] * ri;
+  }
+  if (ic < 0) return;
+  double tot;
+  if (grid_sum(part, c.partials, c.counter, &tot)) st->be[ic] = st->rho[ic] * tot;
+}
+
+// finishes the two-loop (pending update of the newest pair when the history is
+// full), d = -r, slope = d.grad; forward also sets the trial xt = x + alpha d.
+// After a rejected forward trial only xt = x + alpha d is recomputed.
+__global__ void lbfgs_final_kernel(VecCtx c, const double* S, double* r, double* d, const double* grad,
+                                   const double* x, double* xt, int forward) {
+  IterState* st = c.st;
+  if (st->converged) return;
+  if (!st->accepted) {
+    if (!forward) return;
+    const double a = st->alpha;
+    for (int64_t i = (int64_t)blockIdx.x * kT + threadIdx.x; i < c.n3; i += (int64_t)gridDim.x * kT)
+      xt[i] = x[i] + a * d[i];
+    return;
+  }
+  const int cnt = st->count;
+  const int ip = (cnt == st->m && cnt > 0) ? idx_oldest(st, cnt - 1) : -1;
+  const double coef = ip >= 0 ? st->al[ip] - st->be[ip] : 0.0;
+  double part = 0;
+  for (int64_t i = (int64_t)blockIdx.x * kT + threadIdx.x; i < c.n3; i += (int64_t)gridDim.x * kT) {
+    double ri = r[i];
+    if (ip >= 0) ri += coef * S[(int64_t)ip * c.n3 + i];
+    const double di = -ri;
+    d[i] = di;
+    if (forward) xt[i] = x[i] + di;
+    part += di * grad[i];
+  }
+  double tot;
+  if (grid_sum(part, c.partials, c.counter, &tot)) st->slope = tot;
+}
+
+// v_{t+1} = (x - x_t)/h, state advance, trajectory write in kept order
+__global__ void finalize_fwd_kernel(int64_t n, const double* x, double* xi, double* vi, double inv_h,
+                                    const int32_t* kept_of_internal, double* traj_x, double* traj_v) {
+  for (int64_t c = (int64_t)blockIdx.x * kT + threadIdx.x; c < n; c += (int64_t)gridDim.x * kT) {
+    const int64_t k = kept_of_internal[c];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      const double xn = x[3 * c + i];
+      const double vn = (xn - xi[3 * c + i]) * inv_h;
+      xi[3 * c + i] = xn;
+      vi[3 * c + i] = vn;
+      if (traj_x) traj_x[3 * k + i] = xn;
+      if (traj_v) traj_v[3 * k + i] = vn;
+    }
+  }
+}
+
+// ---------------------------------------------------------------- backward
+// gbar = ax + av/h, z = 0, gs = grad s(0) = -gbar, q = gs; ref2 = |gbar|^2
+__global__ void bwd_step_init_kernel(VecCtx c, const double* ax, const double* av, double inv_h,
+                                     double* z, double* gs, double* q) {
+  double part = 0;
+  for (int64_t i = (int64_t)blockIdx.x * kT + threadIdx.x; i < c.n3; i += (int64_t)gridDim.x * kT) {
+    const double gb = ax[i] + av[i] * inv_h;
+    z[i] = 0.0;
+    gs[i] = -gb;
+    q[i] = -gb;
+    part += gb * gb;
+  }
+  double tot;
+  if (grid_sum(part, c.partials, c.counter, &tot)) {
+    c.st->ref2 = tot;
+    c.st->gn2_acc = tot;
+    c.st->converged = (tot == 0.0);
+  }
+}
+
+// line search on the quadratic s along d with the curvature d.Hd (exact values,
+// no extra Hessian products), then the history pair (s, y) = alpha (d, Hd)
+__global__ void decide_bwd_kernel(IterState* st, const double* gather_partials, int64_t nbg) {
+  const double dHd = block_reduce_strided(gather_partials, nbg, 4, 0);
+  if (threadIdx.x != 0) return;
+  if (st->converged) return;
+  st->dHd = dHd;
+  if (!isfinite(dHd)) {
+    st->status |= DEV_ERR_NAN;
+    st->converged = 1;
+    st->alpha = 0.0;
+    st->push = 0;
+    return;
+  }
+  const double slope = st->slope;
+  if (!(slope < 0.0)) {   // not a descent direction: drop the history, no step
+    st->count = 0;
+    st->head = 0;
+    st->alpha = 0.0;
+    st->push = 0;
+    return;
+  }
+  double a = 1.0;
+  for (int t = 0; t < st->ls_max; ++t) {
+    if (a * slope + 0.5 * a * a * dHd <= st->c1 * a * slope) break;
+    a *= 0.5;
+    st->ls_total += 1;
+  }
+  st->alpha = a;
+  st->push = 0;
+  const double sy = a * a * dHd;
+  if (st->m > 0 && sy > 0.0) {
+    int slot;
+    if (st->count < st->m) {
+      slot = (st->head + st->count) % st->m;
+      st->count += 1;
+    } else {
+      slot = st->head;
+      st->head = (st->head + 1) % st->m;
+    }
+    st->rho[slot] = 1.0 / sy;
+    st->pslot = slot;
+    st->push = 1;
+  }
+}
+
+__global__ void update_bwd_kernel(VecCtx c, const double* d, const double* Hd, double* z, double* gs,
+                                  double* q, double* S, double* Y) {
+  IterState* st = c.st;
+  if (st->converged) return;
+  const double a = st->alpha;
+  const int push = st->push, slot = st->pslot;
+  double part = 0;
+  for (int64_t i = (int64_t)blockIdx.x * kT + threadIdx.x; i < c.n3; i += (int64_t)gridDim.x * kT) {
+    const double ad = a * d[i], ah = a * Hd[i];
+    z[i] += ad;
+    const double g = gs[i] + ah;
+    gs[i] = g;
+    q[i] = g;
+    if (push) {
+      S[(int64_t)slot * c.n3 + i] = ad;
+      Y[(int64_t)slot * c.n3 + i] = ah;
+    }
+    part += g * g;
+  }
+  double tot;
+  if (grid_sum(part, c.partials, c.counter, &tot)) {
+    st->gn2_acc = tot;
+    st->iters += 1;
+    if (tot <= st->tol2 * st->ref2) {
+      st->converged = 1;
+    } else if (st->iters >= st->max_iter) {
+      st->converged = 1;
+      st->hit_max = 1;
+    }
+  }
+}
+
+// gs = Hz - gbar from an exact product Hz (true-residual replacement)
+__global__ void residual_replace_kernel(VecCtx c, const double* Hz, const double* ax, const double* av,
+                                        double inv_h, double* gs, double* q) {
+  double part = 0;
+  for (int64_t i = (int64_t)blockIdx.x * kT + threadIdx.x; i < c.n3; i += (int64_t)gridDim.x * kT) {
+    const double g = Hz[i] - (ax[i] + av[i] * inv_h);
+    gs[i] = g;
+    q[i] = g;
+    part += g * g;
+  }
+  double tot;
+  if (grid_sum(part, c.partials, c.counter, &tot)) {
+    c.st->gn2_acc = tot;
+    c.st->converged = tot <= c.st->tol2 * c.st->ref2 ? 1 : 0;
+    c.st->accepted = 1;
+  }
+}
+
+// Adjoint of one step (Eqns 10-12) -> upstream gradients of the previous state:
+//   dL/dy = M z/h^2, ax <- dL/dy - av/h (+ friction), av <- h dL/dy (+ friction),
+//   g_fext += z, then the direct loss terms of step t are added.
+__global__ void bwd_state_kernel(BwdStateParams p) {
+  double part = 0;
+  for (int64_t c = (int64_t)blockIdx.x * kT + threadIdx.x; c < p.n; c += (int64_t)gridDim.x * kT) {
+    double nax[3] = {0, 0, 0}, nav[3] = {0, 0, 0};
+    if (c < p.nf) {
+      const double m = p.mass[c];
+#pragma unroll
+      for (int i = 0; i < 3; ++i) {
+        const double zi = p.z[3 * c + i];
+        const double dldy = m * zi * p.inv_h2;
+        nax[i] = dldy - p.av[3 * c + i] * p.inv_h;
+        nav[i] = p.h * dldy;
+        if (p.gfext) p.gfext[3 * c + i] += zi;
+      }
+      if (p.contact && p.contact[c]) {
+        // friction f_t(x_t, v_t, mu) entered f_ext of this step: dL/df = z
+        const double zc = p.xi[3 * c + 2];
+        const double vx = p.vi[3 * c], vy = p.vi[3 * c + 1];
+        const double nv = sqrt(vx * vx + vy * vy);
+        if (zc < 0.0 && nv > 0.0) {
+          const double m = p.mass[c];
+          const double tx = vx / nv, ty = vy / nv;
+          const double gx = p.z[3 * c], gy = p.z[3 * c + 1];
+          if (p.mu * p.k * (-zc) < m * nv / p.h) {
+            const double gt = gx * tx + gy * ty;
+            nax[2] += p.mu * p.k * gt;
+            part += p.k * zc * gt;
+            const double s = p.mu * p.k * zc / nv;
+            nav[0] += s * (gx - tx * gt);
+            nav[1] += s * (gy - ty * gt);
+          } else {
+            nav[0] += -m / p.h * gx;
+            nav[1] += -m / p.h * gy;
+          }
+        }
+      }
+    }
+    const int64_t k = p.kept_of_internal[c];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      if (p.gx_t) nax[i] += p.gx_t[3 * k + i];
+      if (p.gv_t) nav[i] += p.gv_t[3 * k + i];
+      p.ax[3 * c + i] = nax[i];
+      p.av[3 * c + i] = nav[i];
+    }
+  }
+  double tot;
+  if (grid_sum(part, p.partials, p.counter, &tot) && p.gmu) *p.gmu += tot;
+}
+
+// ---------------------------------------------------------------- misc
+__global__ void kept_to_internal_kernel(int64_t n, const int32_t* kept_of_internal, const double* in,
+                                        double* out) {
+  for (int64_t c = (int64_t)blockIdx.x * kT + threadIdx.x; c < n; c += (int64_t)gridDim.x * kT) {
+    const int64_t k = kept_of_internal[c];
+    out[3 * c] = in[3 * k];
+    out[3 * c + 1] = in[3 * k + 1];
+    out[3 * c + 2] = in[3 * k + 2];
+  }
+}
+
+__global__ void internal_to_kept_kernel(int64_t n, int64_t nvalid, const int32_t* kept_of_internal,
+                                        const double* in, double* out) {
+  for (int64_t c = (int64_t)blockIdx.x * kT + threadIdx.x; c < n; c += (int64_t)gridDim.x * kT) {
+    const int64_t k = kept_of_internal[c];
+    const bool v = c < nvalid;
+    out[3 * k] = v ? in[3 * c] : 0.0;
+    out[3 * k + 1] = v ? in[3 * c + 1] : 0.0;
+    out[3 * k + 2] = v ? in[3 * c + 2] : 0.0;
+  }
+}
+
+// grad E over all nodes from the element buffer (local-step entry point) and
+// the contact energy partials.
+template <typename T>
+__global__ void gather_all_kernel(int64_t n, const int32_t* inc_ptr, const int32_t* inc, const void* eb,
+                                  const double* x, const uint8_t* contact, double k, double* out,
+                                  double* partials, unsigned* counter, double* energy_total) {
+  const T* e = reinterpret_cast<const T*>(eb);
+  double part = 0;
+  for (int64_t c = (int64_t)blockIdx.x * kT + threadIdx.x; c < n; c += (int64_t)gridDim.x * kT) {
+    double g[3] = {0, 0, 0};
+    for (int32_t q = inc_ptr[c]; q < inc_ptr[c + 1]; ++q) {
+      const int64_t slot = (int64_t)inc[q] * 3;
+      g[0] += (double)e[slot];
+      g[1] += (double)e[slot + 1];
+      g[2] += (double)e[slot + 2];
+    }
+    if (contact && contact[c] && x[3 * c + 2] < 0.0) {
+      const double z = x[3 * c + 2];
+      g[2] += k * z;
+      part += 0.5 * k * z * z;
+    }
+    if (out) {
+      out[3 * c] = g[0];
+      out[3 * c + 1] = g[1];
+      out[3 * c + 2] = g[2];
+    }
+  }
+  double tot;
+  if (grid_sum(part, partials, counter, &tot) && energy_total) *energy_total += tot;
+}
+
+__global__ void sum_partials_kernel(const double* partials, int64_t n, double* out) {
+  const double t = block_reduce_strided(partials, n, 1, 0);
+  if (threadIdx.x == 0) *out = t;
+}
+
+__global__ void copy_kernel(int64_t n, const double* in, double* out) {
+  for (int64_t i = (int64_t)blockIdx.x * kT + threadIdx.x; i < n; i += (int64_t)gridDim.x * kT) out[i] = in[i];
+}
+
+__global__ void force_accept_kernel(IterState* st) {
+  st->force_accept = 1;
+  st->converged = 0;
+  st->hit_max = 0;
+  st->accepted = 0;
+}
+
+}  // namespace pd

@@ -1,0 +1,87 @@
+"""Kernel-level parity through the C ABI: local step (Eqn 20), Hessian-vector
+product (Eqns 21-22) and the prefactorised global solve (Eqn 19) against the
+FP64 CPU oracle, in FP64 and in the FP32 (mixed) path."""
+import numpy as np
+import pytest
+import scipy.sparse.linalg as spla
+import torch
+
+from _gpu_helpers import DEV, T, deformed, make_mesh, rel
+from oracle.model import Model
+from paper_2101_05917_gb300 import _native as N
+from test_oracle_dynamics import tiny_everything_scene
+from workloads import cantilever_c1, quadruped, small_beam
+
+pytestmark = pytest.mark.gpu
+
+TOL = {N.PD_PREC_FP64: 1e-10, N.PD_PREC_MIXED: 2e-5}
+
+
+def _scenes():
+    return {
+        "c1": cantilever_c1(T=1),
+        "beam_vol": small_beam(5, 3, 4, T=1),
+        "quad9": quadruped(9, T=2),
+        "tiny_all": tiny_everything_scene(),
+    }
+
+
+@pytest.mark.parametrize("name", ["c1", "beam_vol", "quad9", "tiny_all"])
+@pytest.mark.parametrize("prec", [N.PD_PREC_FP64, N.PD_PREC_MIXED])
+def test_local_step_matches_oracle(name, prec):
+    sc = _scenes()[name]
+    model = Model(sc)
+    mesh = make_mesh(sc, precision=prec)
+    act = None if sc.act is None else sc.act[0]
+    for seed in range(3):
+        x = deformed(sc, scale=0.05, seed=seed)
+        if sc.k_contact > 0:
+            x[:, 2] -= 0.3 * sc.dx   # put some contact candidates below the ground
+        g_ref = model.grad_E(x, act)
+        e_ref = model.energy(x, act)
+        g, e = mesh.local_step(T(x), None if act is None else T(act), precision=prec)
+        torch.cuda.synchronize()
+        assert rel(g.cpu().numpy(), g_ref) < TOL[prec]
+        assert abs(e.item() - e_ref) <= TOL[prec] * abs(e_ref)
+    mesh.close()
+
+
+@pytest.mark.parametrize("name", ["c1", "beam_vol", "quad9", "tiny_all"])
+@pytest.mark.parametrize("prec", [N.PD_PREC_FP64, N.PD_PREC_MIXED])
+def test_hessian_vector_matches_oracle(name, prec):
+    sc = _scenes()[name]
+    model = Model(sc)
+    mesh = make_mesh(sc, precision=prec)
+    act = None if sc.act is None else sc.act[0]
+    rng = np.random.default_rng(7)
+    x = deformed(sc, scale=0.05, seed=3)
+    if sc.k_contact > 0:
+        x[:, 2] -= 0.3 * sc.dx
+    H = model.hessian(x, act)[model.free_dofs][:, model.free_dofs]
+    for _ in range(2):
+        v = rng.standard_normal(x.shape)
+        v[model.dirichlet] = 0
+        ref = np.zeros_like(v)
+        ref[model.free_nodes] = (H @ v[model.free_nodes].ravel()).reshape(-1, 3)
+        out = mesh.hessian_vector(T(x), T(v), None if act is None else T(act), precision=prec)
+        torch.cuda.synchronize()
+        assert rel(out.cpu().numpy(), ref) < TOL[prec]
+    mesh.close()
+
+
+@pytest.mark.parametrize("name", ["c1", "beam_vol", "quad9", "tiny_all"])
+@pytest.mark.parametrize("leaf", [64, 8])
+@pytest.mark.parametrize("prec", [N.PD_PREC_FP64, N.PD_PREC_MIXED])
+def test_global_solve_matches_direct_solve(name, leaf, prec):
+    sc = _scenes()[name]
+    model = Model(sc)
+    mesh = make_mesh(sc, precision=prec, leaf_max=leaf)
+    A = model.A_matrix()[model.free_dofs][:, model.free_dofs].tocsc()
+    rng = np.random.default_rng(1)
+    b = rng.standard_normal(sc.x0.shape)
+    ref = np.zeros_like(b)
+    ref[model.free_nodes] = spla.spsolve(A, b[model.free_nodes].ravel()).reshape(-1, 3)
+    out = mesh.solve(T(b), precision=prec)
+    torch.cuda.synchronize()
+    assert rel(out.cpu().numpy(), ref) < TOL[prec]
+    mesh.close()
