@@ -103,7 +103,11 @@ def test_static_contact_force_balances_weight():
 
 
 def tiny_everything_scene(T=3):
-    """2x1x2 cells with volume + muscle energies, ground contact and friction."""
+    """2x1x2 cells with volume + muscle energies, ground contact and friction.
+
+    Heavy (rho = 1e4) soft material so that the PD splitting converges in a
+    few hundred iterations: near-rigid rotations contract by about
+    1 - (m/h^2)/(E dx) per plain PD iteration."""
     nx, ny, nz = 2, 1, 2
     n = (nx + 1) * (ny + 1) * (nz + 1)
     e = nx * ny * nz
@@ -118,12 +122,12 @@ def tiny_everything_scene(T=3):
     fib = rng.standard_normal((e, 3))
     fib /= np.linalg.norm(fib, axis=1, keepdims=True)
     return Scene(name="tiny", nx=nx, ny=ny, nz=nz, dx=0.01, origin=np.zeros(3), cell_mask=None,
-                 density=1e3, youngs=1e5 * np.exp(0.2 * rng.standard_normal(e)), poisson=0.4,
+                 density=1e4, youngs=1e5 * np.exp(0.2 * rng.standard_normal(e)), poisson=0.4,
                  corotated=True, volume=True, muscle=np.ones(e, dtype=np.uint8), fiber=fib,
                  dirichlet=np.zeros(n, dtype=np.uint8), contact=(k == 0).astype(np.uint8),
                  gravity=np.array([0.0, 0.0, -9.81]), h=0.01, T=T, x0=x0, v0=v0,
                  f_ext=0.01 * rng.standard_normal((n, 3)),
-                 act=rng.uniform(0, 0.3, size=(T, e)), k_contact=1e4, mu=0.5,
+                 act=rng.uniform(0, 0.3, size=(T, e)), k_contact=1e3, mu=0.5,
                  loss_w=rng.standard_normal((n, 3)), tol_fwd=1e-12, tol_bwd=1e-12)
 
 
@@ -152,7 +156,8 @@ def test_gradients_match_central_fd_everything():
     d = rng.standard_normal(sc.x0.shape)
     checks.append((fd(lambda s: _loss(sc, x0=sc.x0 + s * d), 1e-7), np.sum(g["g_x0"] * d)))
     checks.append((fd(lambda s: _loss(sc, v0=sc.v0 + s * d), 1e-6), np.sum(g["g_v0"] * d)))
-    checks.append((fd(lambda s: _loss(sc, f_ext=sc.f_ext + s * d), 1e-5), np.sum(g["g_fext"] * d)))
+    # small step: a node sits ~1.7e-5 from the static/dynamic friction switch
+    checks.append((fd(lambda s: _loss(sc, f_ext=sc.f_ext + s * d), 1e-6), np.sum(g["g_fext"] * d)))
     dE = rng.standard_normal(m.mesh.e) * sc.youngs
     checks.append((fd(lambda s: _loss(sc, youngs=sc.youngs + s * dE), 1e-6), np.sum(gE * dE)))
     checks.append((fd(lambda s: _loss(sc, poisson=sc.poisson + s), 1e-6), gnu))
