@@ -246,11 +246,16 @@ pd_status forward_step(Ctx& c, const double* act_t, const double* fext_int, doub
   pp.st = w.st;
   predictor_kernel<<<grid_for(c.n), 256, 0, c.s>>>(pp);
   PD_CUDA_TRY(cudaGetLastError());
-  int prec = m->precision == PD_PREC_MIXED ? PD_PREC_MIXED : PD_PREC_FP64;
-  bool fp64_phase = prec == PD_PREC_FP64;
-  int launched = 0, fp64_launched = 0;
+  // MIXED: iterate with FP32 local steps; when the FP32 residual meets the
+  // tolerance, re-evaluate the gradient at the accepted point with an FP64 local
+  // step (the convergence check).  If it fails the FP32 iteration continues from
+  // the FP64 gradient; after kMaxChecks failed checks the FP64 local step is used
+  // for the remaining iterations.
+  const bool mixed = m->precision == PD_PREC_MIXED;
+  int prec = mixed ? PD_PREC_MIXED : PD_PREC_FP64;
+  int launched = 0, fp64_launched = 0, checks = 0;
+  constexpr int kMaxChecks = 3;
   int chunk = std::max(guess, 1);
-  double last_rel = 1e300;
   const int hard_cap = 3 * c.o.max_iter_fwd + 64;
   info = StepInfo{};
   while (true) {
@@ -259,35 +264,32 @@ pd_status forward_step(Ctx& c, const double* act_t, const double* fext_int, doub
       if (e != PD_OK) return e;
     }
     launched += chunk;
-    if (fp64_phase && prec == PD_PREC_FP64 && m->precision == PD_PREC_MIXED) fp64_launched += chunk;
+    if (mixed && prec == PD_PREC_FP64) fp64_launched += chunk;
+    if (chunk > 0) clear_checked_kernel<<<1, 1, 0, c.s>>>(w.st);
     pd_status e = poll(c);
     if (e != PD_OK) return e;
     const IterState& sh = *w.st_host;
-    const double rel = sh.ref2 > 0 ? std::sqrt(sh.gn2_acc / sh.ref2) : 0.0;
     if (sh.status & DEV_ERR_NAN) {
       info.converged = false;
       break;
     }
     if (sh.converged) {
-      if (!fp64_phase && !sh.hit_max) {
-        // mixed precision: confirm / polish the FP32 solution with FP64 local steps
-        fp64_phase = true;
-        prec = PD_PREC_FP64;
+      if (mixed && prec == PD_PREC_MIXED && !sh.hit_max && !sh.fp64_checked) {
+        // FP64 convergence check at the accepted point
+        ++checks;
+        if (checks > kMaxChecks) prec = PD_PREC_FP64;
         force_accept_kernel<<<1, 1, 0, c.s>>>(w.st);
         copy_kernel<<<c.vb, 256, 0, c.s>>>(c.n3f, w.x, w.xt);
-        chunk = 1;
+        pd_status e2 = launch_fwd_iteration(c, PD_PREC_FP64, act_t);
+        if (e2 != PD_OK) return e2;
+        fp64_launched += 1;
+        mark_checked_kernel<<<1, 1, 0, c.s>>>(w.st);
+        chunk = 0;
         continue;
       }
       info.converged = !sh.hit_max;
       break;
     }
-    if (!fp64_phase && (rel <= c.o.mixed_switch || rel > 0.9 * last_rel)) {
-      fp64_phase = true;
-      prec = PD_PREC_FP64;
-      force_accept_kernel<<<1, 1, 0, c.s>>>(w.st);
-      copy_kernel<<<c.vb, 256, 0, c.s>>>(c.n3f, w.x, w.xt);
-    }
-    last_rel = rel;
     if (launched >= hard_cap) {
       info.converged = false;
       break;
@@ -342,12 +344,14 @@ pd_status backward_step(Ctx& c, const double* xnext, const double* xt_, const do
   StateCfg cfg{c.o.tol_bwd, 0.0, c.o.lbfgs_m, c.o.ls_max, c.o.max_iter_bwd, 1};
   state_reset_kernel<<<1, 1, 0, c.s>>>(w.st, cfg);
   bwd_step_init_kernel<<<c.vb, 256, 0, c.s>>>(c.vc, w.ax, w.av, inv_h, w.z, w.gs, w.q);
-  int prec = m->precision == PD_PREC_MIXED ? PD_PREC_MIXED : PD_PREC_FP64;
-  bool fp64_phase = prec == PD_PREC_FP64;
+  // Hessian products in the factor's precision; at convergence of the recursively
+  // updated residual, the true residual H z - gbar is evaluated with an FP64
+  // product and replaces it (iterative refinement); the iteration continues
+  // until the true residual meets the tolerance.
+  const int prec = m->precision == PD_PREC_MIXED ? PD_PREC_MIXED : PD_PREC_FP64;
   int launched = 0, fp64_launched = 0, checks = 0;
   int chunk = std::max(guess, 1);
   const int hard_cap = 3 * c.o.max_iter_bwd + 64;
-  double last_rel = 1e300;
   info = StepInfo{};
   while (true) {
     for (int k = 0; k < chunk; ++k) {
@@ -355,7 +359,6 @@ pd_status backward_step(Ctx& c, const double* xnext, const double* xt_, const do
       if (e != PD_OK) return e;
     }
     launched += chunk;
-    if (fp64_phase && m->precision == PD_PREC_MIXED) fp64_launched += chunk;
     pd_status e = poll(c);
     if (e != PD_OK) return e;
     const IterState* sh = w.st_host;
@@ -363,17 +366,16 @@ pd_status backward_step(Ctx& c, const double* xnext, const double* xt_, const do
       info.converged = false;
       break;
     }
-    double rel = sh->ref2 > 0 ? std::sqrt(sh->gn2_acc / sh->ref2) : 0.0;
     if (sh->converged) {
       if (sh->hit_max) {
         info.converged = false;
         break;
       }
-      // true residual gs = H z - gbar with an FP64 Hessian product
       LocalArgs la{m, nullptr, xnext, w.z, act_t, PD_PREC_FP64};
       PD_CUDA_TRY(launch_element_hvp(la, w.elembuf, w.flags, c.s));
       PD_CUDA_TRY(launch_gather_hvp(m, nullptr, w.elembuf, PD_PREC_FP64, xnext, w.z, nullptr, w.Hd, c.pg, c.s));
       residual_replace_kernel<<<c.vb, 256, 0, c.s>>>(c.vc, w.Hd, w.ax, w.av, inv_h, w.gs, w.q);
+      fp64_launched += 1;
       e = poll(c);
       if (e != PD_OK) return e;
       ++checks;
@@ -381,18 +383,9 @@ pd_status backward_step(Ctx& c, const double* xnext, const double* xt_, const do
         info.converged = w.st_host->converged != 0;
         break;
       }
-      if (m->precision == PD_PREC_MIXED) {
-        fp64_phase = true;
-        prec = PD_PREC_FP64;
-      }
       chunk = c.o.check_every;
       continue;
     }
-    if (!fp64_phase && (rel <= c.o.mixed_switch || rel > 0.9 * last_rel)) {
-      fp64_phase = true;
-      prec = PD_PREC_FP64;
-    }
-    last_rel = rel;
     if (launched >= hard_cap) {
       info.converged = false;
       break;
@@ -524,12 +517,22 @@ pd_status pd_create_mesh(const pd_mesh_desc* desc, pd_mesh* out) {
   UP(la_diag_node, la_diag_node);
   UP(la_contrib, la_contrib);
 #undef UP
-  std::vector<int2> fwd, bwd;
-  build_solve_schedule(h, fwd, bwd, I.slevels);
-  if ((e = dalloc(&I, &I.fwd_tasks, fwd.size())) != cudaSuccess) return fail(e);
-  if ((e = dalloc(&I, &I.bwd_tasks, bwd.size())) != cudaSuccess) return fail(e);
-  if (!fwd.empty() && (e = cudaMemcpy(I.fwd_tasks, fwd.data(), sizeof(int2) * fwd.size(), cudaMemcpyHostToDevice)) != cudaSuccess) return fail(e);
-  if (!bwd.empty() && (e = cudaMemcpy(I.bwd_tasks, bwd.data(), sizeof(int2) * bwd.size(), cudaMemcpyHostToDevice)) != cudaSuccess) return fail(e);
+  build_solve_schedule(h, I.sched);
+  {
+    const SolveSchedule& S = I.sched;
+    if ((e = upload(&I, &I.fwd_ntiles, S.fwd_ntiles)) != cudaSuccess) return fail(e);
+    if ((e = upload(&I, &I.bwd_ntiles, S.bwd_ntiles)) != cudaSuccess) return fail(e);
+    if ((e = upload(&I, &I.fwd_first, S.fwd_first)) != cudaSuccess) return fail(e);
+    if ((e = upload(&I, &I.bwd_first, S.bwd_first)) != cudaSuccess) return fail(e);
+    if ((e = dalloc(&I, &I.fwd_tiles, S.fwd.size())) != cudaSuccess) return fail(e);
+    if ((e = dalloc(&I, &I.bwd_tiles, S.bwd.size())) != cudaSuccess) return fail(e);
+    if (!S.fwd.empty() && (e = cudaMemcpy(I.fwd_tiles, S.fwd.data(), sizeof(SolveTile) * S.fwd.size(), cudaMemcpyHostToDevice)) != cudaSuccess) return fail(e);
+    if (!S.bwd.empty() && (e = cudaMemcpy(I.bwd_tiles, S.bwd.data(), sizeof(SolveTile) * S.bwd.size(), cudaMemcpyHostToDevice)) != cudaSuccess) return fail(e);
+    const size_t nt = S.fwd_ntiles.size() + S.bwd_ntiles.size();
+    if ((e = dalloc(&I, &I.ws.solve_tickets, nt)) != cudaSuccess) return fail(e);
+    if ((e = cudaMemset(I.ws.solve_tickets, 0, sizeof(unsigned) * nt)) != cudaSuccess) return fail(e);
+    if ((e = dalloc(&I, (char**)&I.ws.solve_partial, solve_partial_bytes(S))) != cudaSuccess) return fail(e);
+  }
   I.flevels.assign(h.nlev, FactorLevel{});
   for (int64_t L = 0; L < h.nlev; ++L) {
     FactorLevel& f = I.flevels[L];

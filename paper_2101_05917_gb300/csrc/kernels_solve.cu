@@ -9,10 +9,13 @@
 //                               [u_s; w_s] = Q_s rhs,  W_s = w_s + (children
 //                               updates on the below rows)
 //   backward (root -> leaves):  x_s = Q_s^T [u_s; -x(below rows)]
-// One launch per level and direction; each CTA owns a block of panel rows
-// (forward) or columns (backward), reads its panel block once with coalesced
-// column-major loads and writes disjoint outputs, so no atomics are needed and
-// every sum runs in a fixed order.
+// One launch per tree level and direction.  Each level is cut into 2D tiles of
+// the panels (forward: 64 rows x 128 columns, backward: 256 rows x 32 columns,
+// all-zero tiles of the triangular L11^-1 block skipped), so that even the
+// single root supernode spreads over many SMs; every thread keeps many
+// independent panel loads in flight.  Tiles sharing an output block write
+// partial sums; the last tile to finish (integer ticket) adds them in tile
+// order, so the result does not depend on scheduling and no float atomics run.
 #include <algorithm>
 
 #include "pd_internal.cuh"
@@ -22,15 +25,20 @@ namespace pd {
 namespace {
 
 constexpr int kThreads = 256;
-constexpr int kRowsPerTask = 64;    // forward: rows per CTA (4 column groups)
-constexpr int kColsPerTask = 32;    // backward: columns per CTA (8 warps x 4)
-constexpr int kChunk = 512;         // staged vector chunk
+constexpr int kFR = 64;     // forward tile rows
+constexpr int kFC = 128;    // forward tile columns (8 warps x 16)
+constexpr int kBR = 256;    // backward tile rows (32 lanes x 8)
+constexpr int kBC = 32;     // backward tile columns (8 warps x 4)
 
 struct SolveParams {
   const IterState* gate;
   const int64_t *snode_first, *row_ptr, *panel_off, *rel_ptr, *gath_ptr;
   const int32_t *rows, *gath;
-  const int2* tasks;
+  const SolveTile* tiles;
+  const int32_t* out_ntiles;    // tiles per output block
+  const int64_t* out_first;     // first tile of each output block
+  unsigned* tickets;            // per output block
+  void* partial;                // per tile partial sums (T)
   const void* Q;
   const double* b;
   void* u;       // (3 nf) T
@@ -39,31 +47,26 @@ struct SolveParams {
 };
 
 template <typename T>
-__global__ void __launch_bounds__(kThreads) fwd_level_kernel(SolveParams p, int64_t task_off) {
+__global__ void __launch_bounds__(kThreads) fwd_tile_kernel(SolveParams p, int64_t tile_off) {
   if (p.gate && (p.gate->converged || !p.gate->accepted)) return;
-  const int2 task = p.tasks[task_off + blockIdx.x];
-  const int64_t s = task.x, row0 = task.y;
+  const int64_t tid_g = tile_off + blockIdx.x;
+  const SolveTile tl = p.tiles[tid_g];
+  const int64_t s = tl.s, row0 = tl.a, col0 = tl.b;
   const int64_t first = p.snode_first[s];
   const int64_t nc = p.snode_first[s + 1] - first;
   const int64_t nr = p.row_ptr[s + 1] - p.row_ptr[s];
   const int64_t pos = p.row_ptr[s];
   const T* Q = reinterpret_cast<const T*>(p.Q) + p.panel_off[s];
   const T* W = reinterpret_cast<const T*>(p.W);
-  const int rl = threadIdx.x % kRowsPerTask;
-  const int grp = threadIdx.x / kRowsPerTask;     // 0..3
-  const int64_t r = row0 + rl;
-  const bool valid = r < nr;
-  // columns that can be nonzero for the task's rows (L11^-1 is lower triangular)
-  const int64_t jmax = (row0 + kRowsPerTask <= nc) ? row0 + kRowsPerTask : nc;
-  __shared__ T rhs[kChunk][3];
-  __shared__ T red[kThreads / kRowsPerTask][kRowsPerTask][3];
-  T acc0 = T(0), acc1 = T(0), acc2 = T(0);
-  for (int64_t j0 = 0; j0 < jmax; j0 += kChunk) {
-    const int64_t jn = min((int64_t)kChunk, jmax - j0);
-    __syncthreads();
-    for (int64_t jj = threadIdx.x; jj < jn; jj += kThreads) {
-      const int64_t j = j0 + jj;
-      const int64_t c = first + j;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  __shared__ T rhs[kFC][3];
+  __shared__ T red[kThreads / 32][kFR][3];
+  __shared__ int is_last;
+  const int64_t cn = min((int64_t)kFC, nc - col0);
+  for (int jj = threadIdx.x; jj < kFC; jj += kThreads) {
+    T r0 = T(0), r1 = T(0), r2 = T(0);
+    if (jj < cn) {
+      const int64_t j = col0 + jj, c = first + j;
       double v0 = p.b[3 * c], v1 = p.b[3 * c + 1], v2 = p.b[3 * c + 2];
       for (int64_t g = p.gath_ptr[pos + j]; g < p.gath_ptr[pos + j + 1]; ++g) {
         const int64_t wr = (int64_t)p.gath[g] * 3;
@@ -71,60 +74,96 @@ __global__ void __launch_bounds__(kThreads) fwd_level_kernel(SolveParams p, int6
         v1 -= (double)W[wr + 1];
         v2 -= (double)W[wr + 2];
       }
-      rhs[jj][0] = (T)v0;
-      rhs[jj][1] = (T)v1;
-      rhs[jj][2] = (T)v2;
+      r0 = (T)v0; r1 = (T)v1; r2 = (T)v2;
     }
-    __syncthreads();
-    if (valid) {
-      const int64_t jend = (r < nc) ? min(jn, r - j0 + 1) : jn;
-      for (int64_t jj = grp; jj < jend; jj += kThreads / kRowsPerTask) {
-        const T q = Q[r + (j0 + jj) * nr];
-        acc0 += q * rhs[jj][0];
-        acc1 += q * rhs[jj][1];
-        acc2 += q * rhs[jj][2];
-      }
-    }
+    rhs[jj][0] = r0; rhs[jj][1] = r1; rhs[jj][2] = r2;
   }
-  red[grp][rl][0] = acc0;
-  red[grp][rl][1] = acc1;
-  red[grp][rl][2] = acc2;
   __syncthreads();
-  if (grp == 0 && valid) {
-    T o[3];
+  // warp w: columns col0 + 16w .. +16, lanes: rows row0 + lane, row0 + 32 + lane
+  const int64_t ra = row0 + lane, rb = row0 + 32 + lane;
+  T a0[3] = {T(0), T(0), T(0)}, a1[3] = {T(0), T(0), T(0)};
+  T qa[16], qb[16];
+#pragma unroll
+  for (int k = 0; k < 16; ++k) {
+    const int64_t j = col0 + warp * 16 + k;
+    const bool jv = (warp * 16 + k) < cn;
+    // L11^-1 is lower triangular: rows < nc only use columns <= row
+    qa[k] = (jv && ra < nr && (ra >= nc || j <= ra)) ? Q[ra + j * nr] : T(0);
+    qb[k] = (jv && rb < nr && (rb >= nc || j <= rb)) ? Q[rb + j * nr] : T(0);
+  }
+#pragma unroll
+  for (int k = 0; k < 16; ++k) {
+    const int jj = warp * 16 + k;
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
-      T t = red[0][rl][i];
-#pragma unroll
-      for (int g = 1; g < kThreads / kRowsPerTask; ++g) t += red[g][rl][i];
-      o[i] = t;
+      a0[i] += qa[k] * rhs[jj][i];
+      a1[i] += qb[k] * rhs[jj][i];
     }
-    if (r < nc) {
-      T* u = reinterpret_cast<T*>(p.u) + 3 * (first + r);
-      u[0] = o[0];
-      u[1] = o[1];
-      u[2] = o[2];
+  }
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    red[warp][lane][i] = a0[i];
+    red[warp][lane + 32][i] = a1[i];
+  }
+  __syncthreads();
+  // tile partial: sum of the 8 warps
+  T* part = reinterpret_cast<T*>(p.partial) + tid_g * (kFR * 3);
+  const int ntile = p.out_ntiles[tl.out];
+  for (int idx = threadIdx.x; idx < kFR * 3; idx += kThreads) {
+    const int r = idx / 3, i = idx % 3;
+    T t = T(0);
+#pragma unroll
+    for (int w = 0; w < kThreads / 32; ++w) t += red[w][r][i];
+    if (ntile == 1) red[0][r][i] = t;
+    else part[idx] = t;
+  }
+  if (ntile > 1) {
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      __threadfence();
+      const unsigned t = atomicAdd(p.tickets + tl.out, 1u);
+      is_last = (t == (unsigned)ntile - 1);
+    }
+    __syncthreads();
+    if (!is_last) return;
+    __threadfence();
+    const T* parts = reinterpret_cast<const T*>(p.partial) + p.out_first[tl.out] * (kFR * 3);
+    for (int idx = threadIdx.x; idx < kFR * 3; idx += kThreads) {
+      T t = T(0);
+      for (int k = 0; k < ntile; ++k) t += __ldcg(parts + (int64_t)k * (kFR * 3) + idx);
+      red[0][idx / 3][idx % 3] = t;
+    }
+    if (threadIdx.x == 0) p.tickets[tl.out] = 0u;
+  }
+  __syncthreads();
+  // outputs: u on the supernode's columns, W on its below rows
+  for (int r = threadIdx.x; r < kFR; r += kThreads) {
+    const int64_t row = row0 + r;
+    if (row >= nr) continue;
+    if (row < nc) {
+      T* uo = reinterpret_cast<T*>(p.u) + 3 * (first + row);
+      uo[0] = red[0][r][0]; uo[1] = red[0][r][1]; uo[2] = red[0][r][2];
     } else {
-      double v0 = (double)o[0], v1 = (double)o[1], v2 = (double)o[2];
-      for (int64_t g = p.gath_ptr[pos + r]; g < p.gath_ptr[pos + r + 1]; ++g) {
+      double v0 = (double)red[0][r][0], v1 = (double)red[0][r][1], v2 = (double)red[0][r][2];
+      for (int64_t g = p.gath_ptr[pos + row]; g < p.gath_ptr[pos + row + 1]; ++g) {
         const int64_t wr = (int64_t)p.gath[g] * 3;
         v0 += (double)W[wr];
         v1 += (double)W[wr + 1];
         v2 += (double)W[wr + 2];
       }
-      T* Wo = reinterpret_cast<T*>(p.W) + 3 * (p.rel_ptr[s] + (r - nc));
-      Wo[0] = (T)v0;
-      Wo[1] = (T)v1;
-      Wo[2] = (T)v2;
+      T* Wo = reinterpret_cast<T*>(p.W) + 3 * (p.rel_ptr[s] + (row - nc));
+      Wo[0] = (T)v0; Wo[1] = (T)v1; Wo[2] = (T)v2;
     }
   }
 }
 
 template <typename T>
-__global__ void __launch_bounds__(kThreads) bwd_level_kernel(SolveParams p, int64_t task_off) {
+__global__ void __launch_bounds__(kThreads) bwd_tile_kernel(SolveParams p, int64_t tile_off) {
   if (p.gate && (p.gate->converged || !p.gate->accepted)) return;
-  const int2 task = p.tasks[task_off + blockIdx.x];
-  const int64_t s = task.x, col0 = task.y;
+  const int64_t tid_g = tile_off + blockIdx.x;
+  const SolveTile tl = p.tiles[tid_g];
+  const int64_t s = tl.s, col0 = tl.a, row0 = tl.b;
   const int64_t first = p.snode_first[s];
   const int64_t nc = p.snode_first[s + 1] - first;
   const int64_t nr = p.row_ptr[s + 1] - p.row_ptr[s];
@@ -132,82 +171,132 @@ __global__ void __launch_bounds__(kThreads) bwd_level_kernel(SolveParams p, int6
   const T* Q = reinterpret_cast<const T*>(p.Q) + p.panel_off[s];
   const T* u = reinterpret_cast<const T*>(p.u);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  constexpr int kPerWarp = kColsPerTask / (kThreads / 32);   // 4
-  __shared__ T v[kChunk][3];
-  T acc[kPerWarp][3];
-#pragma unroll
-  for (int c = 0; c < kPerWarp; ++c) acc[c][0] = acc[c][1] = acc[c][2] = T(0);
-  // column j of L11^-1 is zero above row j
-  for (int64_t r0 = col0; r0 < nr; r0 += kChunk) {
-    const int64_t rn = min((int64_t)kChunk, nr - r0);
-    __syncthreads();
-    for (int64_t rr = threadIdx.x; rr < rn; rr += kThreads) {
-      const int64_t r = r0 + rr;
+  __shared__ T v[kBR][3];
+  __shared__ T res[kBC][3];
+  __shared__ int is_last;
+  for (int rr = threadIdx.x; rr < kBR; rr += kThreads) {
+    const int64_t r = row0 + rr;
+    T v0 = T(0), v1 = T(0), v2 = T(0);
+    if (r < nr) {
       if (r < nc) {
         const T* ur = u + 3 * (first + r);
-        v[rr][0] = ur[0];
-        v[rr][1] = ur[1];
-        v[rr][2] = ur[2];
+        v0 = ur[0]; v1 = ur[1]; v2 = ur[2];
       } else {
         const int64_t g = srows[r];
-        v[rr][0] = (T)(-p.x[3 * g]);
-        v[rr][1] = (T)(-p.x[3 * g + 1]);
-        v[rr][2] = (T)(-p.x[3 * g + 2]);
+        v0 = (T)(-p.x[3 * g]); v1 = (T)(-p.x[3 * g + 1]); v2 = (T)(-p.x[3 * g + 2]);
       }
     }
-    __syncthreads();
-#pragma unroll
-    for (int c = 0; c < kPerWarp; ++c) {
-      const int64_t j = col0 + warp * kPerWarp + c;
-      if (j >= nc) continue;
-      const T* Qj = Q + j * nr;
-      const int64_t rstart = max((int64_t)0, j - r0);
-      for (int64_t rr = rstart + lane; rr < rn; rr += 32) {
-        const T q = Qj[r0 + rr];
-        acc[c][0] += q * v[rr][0];
-        acc[c][1] += q * v[rr][1];
-        acc[c][2] += q * v[rr][2];
-      }
-    }
+    v[rr][0] = v0; v[rr][1] = v1; v[rr][2] = v2;
   }
+  __syncthreads();
+  // warp w: columns col0 + 4w .. +4; lane: rows row0 + lane + 32k, k < 8
 #pragma unroll
-  for (int c = 0; c < kPerWarp; ++c) {
+  for (int c = 0; c < kBC / (kThreads / 32); ++c) {
+    const int jl = warp * (kBC / (kThreads / 32)) + c;
+    const int64_t j = col0 + jl;
+    T q[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      const int64_t r = row0 + lane + 32 * k;
+      // column j of L11^-1 is zero above row j
+      q[k] = (j < nc && r < nr && (r >= nc || r >= j)) ? Q[r + j * nr] : T(0);
+    }
+    T acc[3] = {T(0), T(0), T(0)};
+#pragma unroll
+    for (int k = 0; k < 8; ++k)
+#pragma unroll
+      for (int i = 0; i < 3; ++i) acc[i] += q[k] * v[lane + 32 * k][i];
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
-      T t = acc[c][i];
+      T t = acc[i];
 #pragma unroll
       for (int off = 16; off >= 1; off >>= 1) t += __shfl_xor_sync(0xffffffffu, t, off);
-      acc[c][i] = t;
+      if (lane == 0) res[jl][i] = t;
     }
-    const int64_t j = col0 + warp * kPerWarp + c;
-    if (lane == 0 && j < nc) {
-      p.x[3 * (first + j)] = (double)acc[c][0];
-      p.x[3 * (first + j) + 1] = (double)acc[c][1];
-      p.x[3 * (first + j) + 2] = (double)acc[c][2];
+  }
+  __syncthreads();
+  const int ntile = p.out_ntiles[tl.out];
+  if (ntile > 1) {
+    T* part = reinterpret_cast<T*>(p.partial) + tid_g * (kBC * 3);
+    for (int idx = threadIdx.x; idx < kBC * 3; idx += kThreads) part[idx] = res[idx / 3][idx % 3];
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      __threadfence();
+      const unsigned t = atomicAdd(p.tickets + tl.out, 1u);
+      is_last = (t == (unsigned)ntile - 1);
     }
+    __syncthreads();
+    if (!is_last) return;
+    __threadfence();
+    const T* parts = reinterpret_cast<const T*>(p.partial) + p.out_first[tl.out] * (kBC * 3);
+    for (int idx = threadIdx.x; idx < kBC * 3; idx += kThreads) {
+      T t = T(0);
+      for (int k = 0; k < ntile; ++k) t += __ldcg(parts + (int64_t)k * (kBC * 3) + idx);
+      res[idx / 3][idx % 3] = t;
+    }
+    if (threadIdx.x == 0) p.tickets[tl.out] = 0u;
+    __syncthreads();
+  }
+  for (int jl = threadIdx.x; jl < kBC; jl += kThreads) {
+    const int64_t j = col0 + jl;
+    if (j >= nc) continue;
+    p.x[3 * (first + j)] = (double)res[jl][0];
+    p.x[3 * (first + j) + 1] = (double)res[jl][1];
+    p.x[3 * (first + j) + 2] = (double)res[jl][2];
   }
 }
 
 }  // namespace
 
-// Builds the per-level task lists (host) -- called once per mesh.
-void build_solve_schedule(const HostMesh& h, std::vector<int2>& fwd, std::vector<int2>& bwd,
-                          std::vector<SolveLevel>& levels) {
-  fwd.clear();
-  bwd.clear();
-  levels.assign(h.nlev, SolveLevel{});
+// Builds the per-level tile lists (host) -- called once per mesh.  Tiles of one
+// output block are contiguous, so out_first indexes their partial sums.
+void build_solve_schedule(const HostMesh& h, SolveSchedule& S) {
+  S.fwd.clear();
+  S.bwd.clear();
+  S.fwd_ntiles.clear();
+  S.bwd_ntiles.clear();
+  S.fwd_first.clear();
+  S.bwd_first.clear();
+  S.levels.assign(h.nlev, SolveLevel{});
   for (int64_t L = 0; L < h.nlev; ++L) {
-    SolveLevel& sl = levels[L];
-    sl.fwd_off = (int64_t)fwd.size();
-    sl.bwd_off = (int64_t)bwd.size();
+    SolveLevel& sl = S.levels[L];
+    sl.fwd_off = (int64_t)S.fwd.size();
+    sl.bwd_off = (int64_t)S.bwd.size();
     for (int64_t i = h.level_ptr[L]; i < h.level_ptr[L + 1]; ++i) {
       const int64_t s = h.level_list[i];
-      for (int64_t r = 0; r < h.nr(s); r += kRowsPerTask) fwd.push_back(make_int2((int)s, (int)r));
-      for (int64_t c = 0; c < h.nc(s); c += kColsPerTask) bwd.push_back(make_int2((int)s, (int)c));
+      const int64_t nr = h.nr(s), nc = h.nc(s);
+      for (int64_t r0 = 0; r0 < nr; r0 += kFR) {
+        const int32_t out = (int32_t)S.fwd_ntiles.size();
+        S.fwd_first.push_back((int64_t)S.fwd.size());
+        int32_t cnt = 0;
+        // rows < nc of the L11^-1 block need columns <= row only
+        const int64_t cmax = (r0 + kFR <= nc) ? r0 + kFR : nc;
+        for (int64_t c0 = 0; c0 < cmax; c0 += kFC) {
+          S.fwd.push_back(SolveTile{(int32_t)s, (int32_t)r0, (int32_t)c0, out});
+          ++cnt;
+        }
+        S.fwd_ntiles.push_back(cnt);
+      }
+      for (int64_t c0 = 0; c0 < nc; c0 += kBC) {
+        const int32_t out = (int32_t)S.bwd_ntiles.size();
+        S.bwd_first.push_back((int64_t)S.bwd.size());
+        int32_t cnt = 0;
+        // column c of L11^-1 is zero above row c
+        for (int64_t r0 = (c0 / kBR) * kBR; r0 < nr; r0 += kBR) {
+          S.bwd.push_back(SolveTile{(int32_t)s, (int32_t)c0, (int32_t)r0, out});
+          ++cnt;
+        }
+        S.bwd_ntiles.push_back(cnt);
+      }
     }
-    sl.fwd_cnt = (int64_t)fwd.size() - sl.fwd_off;
-    sl.bwd_cnt = (int64_t)bwd.size() - sl.bwd_off;
+    sl.fwd_cnt = (int64_t)S.fwd.size() - sl.fwd_off;
+    sl.bwd_cnt = (int64_t)S.bwd.size() - sl.bwd_off;
   }
+}
+
+size_t solve_partial_bytes(const SolveSchedule& S) {
+  return std::max(S.fwd.size() * kFR * 3, S.bwd.size() * kBC * 3) * sizeof(double);
 }
 
 cudaError_t solve_A(const MeshImpl* m, const IterState* gate, const double* b, double* out,
@@ -224,23 +313,30 @@ cudaError_t solve_A(const MeshImpl* m, const IterState* gate, const double* b, d
   p.b = b;
   p.u = m->ws.solve_u;
   p.W = m->ws.solve_W;
+  p.partial = m->ws.solve_partial;
   p.x = out;
   const bool f32 = precision == PD_PREC_MIXED;
   p.Q = f32 ? (const void*)m->Q32 : (const void*)m->Q64;
-  const int64_t nlev = (int64_t)m->slevels.size();
-  p.tasks = m->fwd_tasks;
+  const int64_t nlev = (int64_t)m->sched.levels.size();
+  p.tiles = m->fwd_tiles;
+  p.out_ntiles = m->fwd_ntiles;
+  p.out_first = m->fwd_first;
+  p.tickets = m->ws.solve_tickets;
   for (int64_t L = 0; L < nlev; ++L) {
-    const SolveLevel& sl = m->slevels[L];
+    const SolveLevel& sl = m->sched.levels[L];
     if (sl.fwd_cnt == 0) continue;
-    if (f32) fwd_level_kernel<float><<<(unsigned)sl.fwd_cnt, kThreads, 0, st>>>(p, sl.fwd_off);
-    else fwd_level_kernel<double><<<(unsigned)sl.fwd_cnt, kThreads, 0, st>>>(p, sl.fwd_off);
+    if (f32) fwd_tile_kernel<float><<<(unsigned)sl.fwd_cnt, kThreads, 0, st>>>(p, sl.fwd_off);
+    else fwd_tile_kernel<double><<<(unsigned)sl.fwd_cnt, kThreads, 0, st>>>(p, sl.fwd_off);
   }
-  p.tasks = m->bwd_tasks;
+  p.tiles = m->bwd_tiles;
+  p.out_ntiles = m->bwd_ntiles;
+  p.out_first = m->bwd_first;
+  p.tickets = m->ws.solve_tickets + m->sched.fwd_ntiles.size();
   for (int64_t L = nlev - 1; L >= 0; --L) {
-    const SolveLevel& sl = m->slevels[L];
+    const SolveLevel& sl = m->sched.levels[L];
     if (sl.bwd_cnt == 0) continue;
-    if (f32) bwd_level_kernel<float><<<(unsigned)sl.bwd_cnt, kThreads, 0, st>>>(p, sl.bwd_off);
-    else bwd_level_kernel<double><<<(unsigned)sl.bwd_cnt, kThreads, 0, st>>>(p, sl.bwd_off);
+    if (f32) bwd_tile_kernel<float><<<(unsigned)sl.bwd_cnt, kThreads, 0, st>>>(p, sl.bwd_off);
+    else bwd_tile_kernel<double><<<(unsigned)sl.bwd_cnt, kThreads, 0, st>>>(p, sl.bwd_off);
   }
   return cudaGetLastError();
 }

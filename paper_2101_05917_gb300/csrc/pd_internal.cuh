@@ -38,10 +38,22 @@ struct DArr {
   size_t n = 0;
 };
 
-// Solve schedule for one level of the supernodal tree.
+// Solve schedule: per level, ranges of 2D panel tiles.
 struct SolveLevel {
-  int64_t fwd_off = 0, fwd_cnt = 0;   // tasks (s, first row) in fwd_tasks
-  int64_t bwd_off = 0, bwd_cnt = 0;   // tasks (s, first column) in bwd_tasks
+  int64_t fwd_off = 0, fwd_cnt = 0;
+  int64_t bwd_off = 0, bwd_cnt = 0;
+};
+struct SolveTile {
+  int32_t s;     // supernode
+  int32_t a;     // forward: first row; backward: first column
+  int32_t b;     // forward: first column; backward: first row
+  int32_t out;   // output block (tiles of one block are contiguous)
+};
+struct SolveSchedule {
+  std::vector<SolveTile> fwd, bwd;
+  std::vector<int32_t> fwd_ntiles, bwd_ntiles;
+  std::vector<int64_t> fwd_first, bwd_first;
+  std::vector<SolveLevel> levels;
 };
 
 // Factorisation schedule for one level.
@@ -67,6 +79,8 @@ struct Workspace {
   int* flags = nullptr;                       // device status bits
   void* solve_u = nullptr;                    // (3 nf) T
   void* solve_W = nullptr;                    // (3 * below rows) T
+  void* solve_partial = nullptr;              // per-tile partial sums
+  unsigned* solve_tickets = nullptr;          // per output block
   double* act_cur = nullptr;                  // unused placeholder for per-step actuation
   int lbfgs_m = 0;
   size_t bytes = 0;
@@ -84,8 +98,10 @@ struct MeshImpl {
   int64_t *gath_ptr = nullptr, *front_off = nullptr, *level_list = nullptr, *child_ptr = nullptr,
           *child_list = nullptr;
   int32_t *rows = nullptr, *gath = nullptr, *rel = nullptr;
-  int2 *fwd_tasks = nullptr, *bwd_tasks = nullptr;
-  std::vector<SolveLevel> slevels;
+  SolveTile *fwd_tiles = nullptr, *bwd_tiles = nullptr;
+  int32_t *fwd_ntiles = nullptr, *bwd_ntiles = nullptr;
+  int64_t *fwd_first = nullptr, *bwd_first = nullptr;
+  SolveSchedule sched;
   std::vector<FactorLevel> flevels;
   // assembly map (device)
   int64_t *la_target = nullptr, *la_cptr = nullptr;
@@ -139,7 +155,7 @@ pd_status factorize_device(MeshImpl* m, cudaStream_t s);
 // gate: skipped when gate->converged or !gate->accepted (may be null).
 cudaError_t solve_A(const MeshImpl* m, const IterState* gate, const double* b, double* out,
                     int precision, cudaStream_t s);
-void build_solve_schedule(const HostMesh& h, std::vector<int2>& fwd, std::vector<int2>& bwd,
-                          std::vector<SolveLevel>& levels);
+void build_solve_schedule(const HostMesh& h, SolveSchedule& S);
+size_t solve_partial_bytes(const SolveSchedule& S);
 
 }  // namespace pd

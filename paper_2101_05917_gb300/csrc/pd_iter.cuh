@@ -25,7 +25,7 @@ struct IterState {
   int head, count;
   int pslot, push;
   int iters, evals, ls_tries, ls_total, ls_max, max_iter;
-  int accepted, converged, hit_max, force_accept;
+  int accepted, converged, hit_max, force_accept, fp64_checked;
   int status;            // DEV_ERR_* bits
 };
 

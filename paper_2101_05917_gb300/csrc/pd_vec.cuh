@@ -136,6 +136,7 @@ __global__ void state_reset_kernel(IterState* st, StateCfg cfg) {
   st->converged = 0;
   st->hit_max = 0;
   st->force_accept = 0;
+  st->fp64_checked = 0;
   st->status = 0;
 }
 
@@ -400,11 +401,19 @@ __global__ void decide_bwd_kernel(IterState* st, const double* gather_partials, 
     st->push = 0;
     return;
   }
+  // s is quadratic along d: its exact minimiser is alpha* = -slope / d.Hd when the
+  // curvature is positive (with a fixed preconditioner this makes the L-BFGS
+  // iteration generate the preconditioned conjugate-gradient iterates); otherwise
+  // Armijo backtracking from alpha = 1 on the closed-form decrease.
   double a = 1.0;
-  for (int t = 0; t < st->ls_max; ++t) {
-    if (a * slope + 0.5 * a * a * dHd <= st->c1 * a * slope) break;
-    a *= 0.5;
-    st->ls_total += 1;
+  if (dHd > 0.0) {
+    a = -slope / dHd;
+  } else {
+    for (int t = 0; t < st->ls_max; ++t) {
+      if (a * slope + 0.5 * a * a * dHd <= st->c1 * a * slope) break;
+      a *= 0.5;
+      st->ls_total += 1;
+    }
   }
   st->alpha = a;
   st->push = 0;
@@ -588,6 +597,9 @@ __global__ void sum_partials_kernel(const double* partials, int64_t n, double* o
 __global__ void copy_kernel(int64_t n, const double* in, double* out) {
   for (int64_t i = (int64_t)blockIdx.x * kT + threadIdx.x; i < n; i += (int64_t)gridDim.x * kT) out[i] = in[i];
 }
+
+__global__ void mark_checked_kernel(IterState* st) { st->fp64_checked = 1; }
+__global__ void clear_checked_kernel(IterState* st) { st->fp64_checked = 0; }
 
 __global__ void force_accept_kernel(IterState* st) {
   st->force_accept = 1;

@@ -68,7 +68,8 @@ def test_rollout_matches_oracle(name, prec):
     xs_ref, vs_ref, _ = newton.rollout(model, sc.x0, sc.v0, sc.f_ext, sc.act)
     _, gx = adjoint.final_position_loss(model, xs_ref, sc.loss_w)
     ref = adjoint.backward(model, xs_ref, vs_ref, gx, act=sc.act)
-    opts = api.solver_opts(tol_fwd=1e-10, tol_bwd=1e-10)
+    # free-floating bodies on the ground converge slowly (near-rigid rotations)
+    opts = api.solver_opts(tol_fwd=1e-10, tol_bwd=1e-10, max_iter_fwd=3000, max_iter_bwd=3000)
     mesh, roll, g = _run(sc, prec, opts)
     xs = roll.x.cpu().numpy()
     assert _pos_err(xs, xs_ref) < POS_TOL
