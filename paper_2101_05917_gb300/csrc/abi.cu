@@ -83,7 +83,7 @@ pd_status ensure_workspace(MeshImpl* m, int lbfgs_m) {
       PD_CUDA_TRY(cudaMemset(*v, 0, sizeof(double) * n3));
     }
     PD_CUDA_TRY(dalloc(m, (double**)&w.elembuf, (size_t)(24 * m->h.e)));
-    const int64_t np = (int64_t)element_blocks(m) + 4 * (int64_t)gather_blocks(m) + 4 * 4096 + 64;
+    const int64_t np = (int64_t)element_energy_partials(m) + 4 * (int64_t)gather_blocks(m) + 4 * 4096 + 64;
     PD_CUDA_TRY(dalloc(m, &w.partials, (size_t)np));
     PD_CUDA_TRY(dalloc(m, &w.counters, 16));
     PD_CUDA_TRY(cudaMemset(w.counters, 0, 16 * sizeof(unsigned)));
@@ -139,6 +139,7 @@ struct Ctx {
   pd_solver_opts o;
   int64_t n, nf, n3f;
   int vb;          // vector kernel blocks
+  int coop;        // cooperative kernel blocks (co-resident)
   VecCtx vc;
   double* pe;      // energy partials
   double* pg;      // gather partials
@@ -154,11 +155,12 @@ Ctx make_ctx(MeshImpl* m, cudaStream_t s, const pd_solver_opts& o) {
   c.nf = m->h.nf;
   c.n3f = 3 * m->h.nf;
   c.vb = vec_blocks(c.n3f);
+  c.coop = m->coop_blocks;
   c.vc.n3 = c.n3f;
   c.vc.st = m->ws.st;
   c.vc.partials = m->ws.partials;
   c.vc.counter = m->ws.counters;
-  c.nbe = element_blocks(m);
+  c.nbe = element_energy_partials(m);
   c.nbg = gather_blocks(m);
   c.pe = m->ws.partials;
   c.pg = m->ws.partials + c.nbe;
@@ -171,7 +173,14 @@ pd_status poll(Ctx& c) {
   return PD_OK;
 }
 
-// one forward iteration: evaluate the trial point, decide, next direction
+template <typename... Args>
+cudaError_t coop_launch(void (*kern)(Args...), int grid, cudaStream_t s, Args... args) {
+  void* ptrs[] = {(void*)&args...};
+  return cudaLaunchCooperativeKernel((const void*)kern, dim3(grid), dim3(256), ptrs, 0, s);
+}
+
+// one forward iteration: evaluate the trial point, decide, commit and the
+// next direction (two-loop recursion around the global solve)
 pd_status launch_fwd_iteration(Ctx& c, int prec, const double* act_t) {
   MeshImpl* m = c.m;
   Workspace& w = m->ws;
@@ -180,32 +189,29 @@ pd_status launch_fwd_iteration(Ctx& c, int prec, const double* act_t) {
   PD_CUDA_TRY(launch_element_forces(la, w.elembuf, c.pe, w.flags, c.s));
   PD_CUDA_TRY(launch_gather_grad(m, st, w.elembuf, prec, w.xt, w.y, w.dir, w.gradt, c.pg, c.s));
   decide_fwd_kernel<<<1, 256, 0, c.s>>>(st, c.pe, c.nbe, c.pg, c.nbg);
-  accept_fwd_kernel<<<c.vb, 256, 0, c.s>>>(st, c.n3f, w.x, w.xt, w.grad, w.gradt, w.q, w.S, w.Y);
-  const int M = c.o.lbfgs_m;
-  for (int k = 0; k <= M; ++k) lbfgs_loop1_kernel<<<c.vb, 256, 0, c.s>>>(c.vc, k, w.S, w.Y, w.q);
+  PD_CUDA_TRY(coop_launch(lbfgs_pre_fwd_kernel, c.coop, c.s, c.vc, w.x, (const double*)w.xt, w.grad,
+                          (const double*)w.gradt, w.q, w.S, w.Y));
   PD_CUDA_TRY(solve_A(m, st, w.q, w.r, m->precision, c.s));
-  for (int k = 0; k < M; ++k) lbfgs_loop2_kernel<<<c.vb, 256, 0, c.s>>>(c.vc, k, w.S, w.Y, w.r);
-  lbfgs_final_kernel<<<c.vb, 256, 0, c.s>>>(c.vc, w.S, w.r, w.dir, w.grad, w.x, w.xt, 1);
-  PD_CUDA_TRY(cudaGetLastError());
+  PD_CUDA_TRY(coop_launch(lbfgs_post_fwd_kernel, c.coop, c.s, c.vc, (const double*)w.S, (const double*)w.Y,
+                          w.r, w.dir, (const double*)w.grad, (const double*)w.x, w.xt));
   return PD_OK;
 }
 
-// one backward iteration: direction from the two-loop around A^-1, Hessian
-// product, exact quadratic line search, update of z and of grad s
+// one backward iteration: apply the previous step and the two-loop recursion
+// around the global solve, then the Hessian product and the line search
 pd_status launch_bwd_iteration(Ctx& c, int prec, const double* xnext, const double* act_t) {
   MeshImpl* m = c.m;
   Workspace& w = m->ws;
   IterState* st = w.st;
-  const int M = c.o.lbfgs_m;
-  for (int k = 0; k <= M; ++k) lbfgs_loop1_kernel<<<c.vb, 256, 0, c.s>>>(c.vc, k, w.S, w.Y, w.q);
+  PD_CUDA_TRY(coop_launch(lbfgs_pre_bwd_kernel, c.coop, c.s, c.vc, (const double*)w.dir, (const double*)w.Hd,
+                          w.z, w.gs, w.q, w.S, w.Y));
   PD_CUDA_TRY(solve_A(m, st, w.q, w.r, m->precision, c.s));
-  for (int k = 0; k < M; ++k) lbfgs_loop2_kernel<<<c.vb, 256, 0, c.s>>>(c.vc, k, w.S, w.Y, w.r);
-  lbfgs_final_kernel<<<c.vb, 256, 0, c.s>>>(c.vc, w.S, w.r, w.dir, w.gs, nullptr, nullptr, 0);
+  PD_CUDA_TRY(coop_launch(lbfgs_post_bwd_kernel, c.coop, c.s, c.vc, (const double*)w.S, (const double*)w.Y,
+                          w.r, w.dir, (const double*)w.gs));
   LocalArgs la{m, st, xnext, w.dir, act_t, prec};
   PD_CUDA_TRY(launch_element_hvp(la, w.elembuf, w.flags, c.s));
   PD_CUDA_TRY(launch_gather_hvp(m, st, w.elembuf, prec, xnext, w.dir, w.gs, w.Hd, c.pg, c.s));
   decide_bwd_kernel<<<1, 256, 0, c.s>>>(st, c.pg, c.nbg);
-  update_bwd_kernel<<<c.vb, 256, 0, c.s>>>(c.vc, w.dir, w.Hd, w.z, w.gs, w.q, w.S, w.Y);
   PD_CUDA_TRY(cudaGetLastError());
   return PD_OK;
 }
@@ -253,7 +259,8 @@ pd_status forward_step(Ctx& c, const double* act_t, const double* fext_int, doub
   // for the remaining iterations.
   const bool mixed = m->precision == PD_PREC_MIXED;
   int prec = mixed ? PD_PREC_MIXED : PD_PREC_FP64;
-  int launched = 0, fp64_launched = 0, checks = 0;
+  int launched = 0, fp64_launched = 0, checks = 0, stall = 0;
+  double best_rel = 1e300;
   constexpr int kMaxChecks = 3;
   int chunk = std::max(guess, 1);
   const int hard_cap = 3 * c.o.max_iter_fwd + 64;
@@ -289,6 +296,16 @@ pd_status forward_step(Ctx& c, const double* act_t, const double* fext_int, doub
       }
       info.converged = !sh.hit_max;
       break;
+    }
+    // FP32 floor above the tolerance: no halving of the residual over three polls
+    if (mixed && prec == PD_PREC_MIXED && sh.ref2 > 0) {
+      const double rel = std::sqrt(sh.gn2_acc / sh.ref2);
+      if (rel < 0.5 * best_rel) {
+        best_rel = rel;
+        stall = 0;
+      } else if (++stall >= 3) {
+        prec = PD_PREC_FP64;
+      }
     }
     if (launched >= hard_cap) {
       info.converged = false;
@@ -520,15 +537,19 @@ pd_status pd_create_mesh(const pd_mesh_desc* desc, pd_mesh* out) {
   build_solve_schedule(h, I.sched);
   {
     const SolveSchedule& S = I.sched;
-    if ((e = upload(&I, &I.fwd_ntiles, S.fwd_ntiles)) != cudaSuccess) return fail(e);
-    if ((e = upload(&I, &I.bwd_ntiles, S.bwd_ntiles)) != cudaSuccess) return fail(e);
-    if ((e = upload(&I, &I.fwd_first, S.fwd_first)) != cudaSuccess) return fail(e);
-    if ((e = upload(&I, &I.bwd_first, S.bwd_first)) != cudaSuccess) return fail(e);
+    // fixed-width gather slots (max fan-in of the forward-solve assembly)
+    int64_t w = 1;
+    for (size_t k = 0; k + 1 < h.gath_ptr.size(); ++k) w = std::max<int64_t>(w, h.gath_ptr[k + 1] - h.gath_ptr[k]);
+    I.slot_w = (int)w;
+    std::vector<int32_t> slots((h.gath_ptr.size() - 1) * w, -1);
+    for (size_t k = 0; k + 1 < h.gath_ptr.size(); ++k)
+      for (int64_t g = h.gath_ptr[k]; g < h.gath_ptr[k + 1]; ++g) slots[k * w + (g - h.gath_ptr[k])] = h.gath[g];
+    if ((e = upload(&I, &I.gath_slots, slots)) != cudaSuccess) return fail(e);
     if ((e = dalloc(&I, &I.fwd_tiles, S.fwd.size())) != cudaSuccess) return fail(e);
     if ((e = dalloc(&I, &I.bwd_tiles, S.bwd.size())) != cudaSuccess) return fail(e);
     if (!S.fwd.empty() && (e = cudaMemcpy(I.fwd_tiles, S.fwd.data(), sizeof(SolveTile) * S.fwd.size(), cudaMemcpyHostToDevice)) != cudaSuccess) return fail(e);
     if (!S.bwd.empty() && (e = cudaMemcpy(I.bwd_tiles, S.bwd.data(), sizeof(SolveTile) * S.bwd.size(), cudaMemcpyHostToDevice)) != cudaSuccess) return fail(e);
-    const size_t nt = S.fwd_ntiles.size() + S.bwd_ntiles.size();
+    const size_t nt = (size_t)(S.n_fwd_out + S.n_bwd_out);
     if ((e = dalloc(&I, &I.ws.solve_tickets, nt)) != cudaSuccess) return fail(e);
     if ((e = cudaMemset(I.ws.solve_tickets, 0, sizeof(unsigned) * nt)) != cudaSuccess) return fail(e);
     if ((e = dalloc(&I, (char**)&I.ws.solve_partial, solve_partial_bytes(S))) != cudaSuccess) return fail(e);
@@ -549,6 +570,18 @@ pd_status pd_create_mesh(const pd_mesh_desc* desc, pd_mesh* out) {
         f.max_child_nb2 = std::max(f.max_child_nb2, nb * nb);
       }
     }
+  }
+  {
+    int dev = 0, sms = 0, occ = 1 << 20, o = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const void* ks[] = {(const void*)lbfgs_pre_fwd_kernel, (const void*)lbfgs_post_fwd_kernel,
+                        (const void*)lbfgs_pre_bwd_kernel, (const void*)lbfgs_post_bwd_kernel};
+    for (const void* k : ks) {
+      if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k, 256, 0)) != cudaSuccess) return fail(e);
+      occ = std::min(occ, o);
+    }
+    I.coop_blocks = std::max(1, sms * std::min(occ, 2));
   }
   pd_status ws = ensure_workspace(&I, 5);
   if (ws != PD_OK) {
@@ -887,7 +920,7 @@ pd_status pd_local_step(pd_mesh mesh, const double* x, const double* act, int32_
   LocalArgs la{m, nullptr, w.iox, nullptr, act, precision};
   double* pe = w.partials;
   PD_CUDA_TRY(launch_element_forces(la, w.elembuf, pe, w.flags, s));
-  const int nbe = element_blocks(m);
+  const int nbe = element_energy_partials(m);
   double* etot = w.partials + nbe + 8;
   sum_partials_kernel<<<1, 256, 0, s>>>(pe, nbe, etot);
   double* gi = w.iov;
@@ -924,7 +957,7 @@ pd_status pd_hessian_vector(pd_mesh mesh, const double* x, const double* act, co
   LocalArgs la{m, nullptr, w.iox, w.iov, act, precision};
   PD_CUDA_TRY(launch_element_hvp(la, w.elembuf, w.flags, s));
   PD_CUDA_TRY(launch_gather_hvp(m, nullptr, w.elembuf, precision, w.iox, w.iov, nullptr, w.Hd,
-                                w.partials + element_blocks(m), s));
+                                w.partials + element_energy_partials(m), s));
   internal_to_kept_kernel<<<grid_for(n), 256, 0, s>>>(n, m->h.nf, m->kept_of_internal, w.Hd, Hv);
   PD_CUDA_TRY(cudaGetLastError());
   return PD_OK;

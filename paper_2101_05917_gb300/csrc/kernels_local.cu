@@ -134,9 +134,9 @@ __global__ void __launch_bounds__(kElemThreads) element_kernel(ElemParams p) {
       gwc = -Vq * (M[0][0] * sv.sm1[0] + M[1][1] * sv.sm1[1] + M[2][2] * sv.sm1[2]);
     }
   }
-  if (wv != T(0)) {
+  if (__any_sync(0xffffffffu, wv != T(0))) {
     VolProj<T> vp;
-    if (volume_project<T>(sv, vp)) {
+    if (volume_project<T>(sv, vp, wv != T(0))) {
       if (MODE == MODE_FORCE) {
         add_UdVt<T>(S, sv.U, vp.gap, sv.V, wv * Vq);
         energy += T(0.5) * wv * Vq * (vp.gap[0] * vp.gap[0] + vp.gap[1] * vp.gap[1] + vp.gap[2] * vp.gap[2]);
@@ -232,17 +232,11 @@ __global__ void __launch_bounds__(kElemThreads) element_kernel(ElemParams p) {
     out[2] = fa[2];
   }
   if (MODE == MODE_FORCE) {
+    // per-warp energy partial (fixed butterfly; no block barrier)
     double en = valid ? (double)energy : 0.0;
 #pragma unroll
     for (int off = 16; off >= 1; off >>= 1) en += __shfl_xor_sync(0xffffffffu, en, off);
-    __shared__ double wsum[kElemThreads / 32];
-    if (lane == 0) wsum[threadIdx.x >> 5] = en;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      double t = 0;
-      for (int w = 0; w < kElemThreads / 32; ++w) t += wsum[w];
-      p.energy[blockIdx.x] = t;
-    }
+    if (lane == 0) p.energy[((int64_t)blockIdx.x * kElemThreads + threadIdx.x) >> 5] = en;
   }
 }
 
@@ -390,6 +384,7 @@ GatherParams make_gather(const MeshImpl* m) {
 int element_blocks(const MeshImpl* m) {
   return (int)((m->h.e * 8 + kElemThreads - 1) / kElemThreads);
 }
+int element_energy_partials(const MeshImpl* m) { return element_blocks(m) * (kElemThreads / 32); }
 int gather_blocks(const MeshImpl* m) {
   return (int)((m->h.nf + kGatherThreads - 1) / kGatherThreads);
 }

@@ -43,16 +43,23 @@ struct SolveLevel {
   int64_t fwd_off = 0, fwd_cnt = 0;
   int64_t bwd_off = 0, bwd_cnt = 0;
 };
-struct SolveTile {
-  int32_t s;     // supernode
-  int32_t a;     // forward: first row; backward: first column
-  int32_t b;     // forward: first column; backward: first row
-  int32_t out;   // output block (tiles of one block are contiguous)
+// Everything one tile needs, loaded with four 16-byte loads.
+struct alignas(16) SolveTile {
+  int64_t panel_off;   // offset of the supernode's panel
+  int64_t part_base;   // first tile of the output block (partial-sum slots)
+  int32_t s;           // supernode
+  int32_t a;           // forward: first row; backward: first column
+  int32_t b;           // forward: first column; backward: first row
+  int32_t out;         // output block (tiles of one block are contiguous)
+  int32_t first, nc, nr;   // first column, columns, rows of the supernode
+  int32_t pos;         // row_ptr[s]: start of its row structure / positions
+  int32_t relp;        // rel_ptr[s]: start of its update-vector rows
+  int32_t ntile;       // tiles in the output block
+  int32_t pad0, pad1;
 };
 struct SolveSchedule {
   std::vector<SolveTile> fwd, bwd;
-  std::vector<int32_t> fwd_ntiles, bwd_ntiles;
-  std::vector<int64_t> fwd_first, bwd_first;
+  int64_t n_fwd_out = 0, n_bwd_out = 0;
   std::vector<SolveLevel> levels;
 };
 
@@ -99,8 +106,8 @@ struct MeshImpl {
           *child_list = nullptr;
   int32_t *rows = nullptr, *gath = nullptr, *rel = nullptr;
   SolveTile *fwd_tiles = nullptr, *bwd_tiles = nullptr;
-  int32_t *fwd_ntiles = nullptr, *bwd_ntiles = nullptr;
-  int64_t *fwd_first = nullptr, *bwd_first = nullptr;
+  int32_t* gath_slots = nullptr;   // (sum nr) x slot_w update-row sources, -1 = none
+  int slot_w = 1;
   SolveSchedule sched;
   std::vector<FactorLevel> flevels;
   // assembly map (device)
@@ -116,6 +123,7 @@ struct MeshImpl {
   double* Q64 = nullptr;
   float* Q32 = nullptr;
   Workspace ws;
+  int coop_blocks = 0;        // co-resident blocks for the cooperative kernels
   std::vector<void*> allocations;
 };
 
@@ -136,6 +144,7 @@ cudaError_t launch_element_hvp(const LocalArgs& a, void* elembuf, int* flags, cu
 cudaError_t launch_element_param_grads(const LocalArgs& a, double* g_wc, double* g_wv,
                                        double* g_wm, double* g_act, cudaStream_t s);
 int element_blocks(const MeshImpl* m);
+int element_energy_partials(const MeshImpl* m);   // one per warp
 
 // Gathers (K2): out[c] = sum over incidence of elembuf + node terms, for c < nf
 // (gradient mode: + m (x - y)/h^2 + contact force; hvp mode: + m v/h^2 + contact).

@@ -26,6 +26,7 @@ struct IterState {
   int pslot, push;
   int iters, evals, ls_tries, ls_total, ls_max, max_iter;
   int accepted, converged, hit_max, force_accept, fp64_checked;
+  int pending;           // backward: a step (alpha, d, Hd) waits to be applied
   int status;            // DEV_ERR_* bits
 };
 

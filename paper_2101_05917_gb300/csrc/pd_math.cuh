@@ -27,16 +27,16 @@ template <typename T> struct Eps;
 template <> struct Eps<float> { static constexpr float v = 1.1920929e-7f; };
 template <> struct Eps<double> { static constexpr double v = 2.220446049250313e-16; };
 
-// One Jacobi rotation annihilating S[p][q]; r is the remaining index.
+// One Jacobi rotation annihilating S[p][q]; r is the remaining index.  Written
+// without branches: with d = (S_qq - S_pp)/2 the tangent of the rotation angle is
+// t = sign(d) S_pq / (|d| + sqrt(d^2 + S_pq^2)) (sign(0) = +1), which is 0 when
+// S_pq = 0 and 1 (45 degrees) when d = 0 (Golub & Van Loan, symmetric Schur).
 template <typename T, int p, int q, int r>
 __device__ __forceinline__ void jacobi_rot(T (&S)[3][3], T (&V)[3][3]) {
   const T apq = S[p][q];
-  if (apq == T(0)) return;
-  const T tau = (S[q][q] - S[p][p]) / (T(2) * apq);
-  const T at = fabs(tau);
-  T t;
-  if (at > T(1e12)) t = T(0.5) / tau;
-  else t = (tau >= T(0) ? T(1) : T(-1)) / (at + tsqrt<T>(T(1) + tau * tau));
+  const T d = T(0.5) * (S[q][q] - S[p][p]);
+  const T den = fabs(d) + tsqrt<T>(d * d + apq * apq);
+  const T t = den > T(0) ? (d >= T(0) ? apq : -apq) / den : T(0);
   const T c = T(1) / tsqrt<T>(T(1) + t * t);
   const T s = t * c;
   const T arp = S[r][p], arq = S[r][q];
@@ -59,8 +59,9 @@ template <typename T, int i, int k, int j>
 __device__ __forceinline__ void givens_qr(T (&B)[3][3], T (&U)[3][3]) {
   const T a = B[i][j], b = B[k][j];
   const T rr = tsqrt<T>(a * a + b * b);
-  T c = T(1), s = T(0);
-  if (rr > T(0)) { c = a / rr; s = b / rr; }
+  const T inv = rr > T(0) ? T(1) / rr : T(0);
+  const T c = rr > T(0) ? a * inv : T(1);
+  const T s = b * inv;
 #pragma unroll
   for (int col = 0; col < 3; ++col) {
     const T bi = B[i][col], bk = B[k][col];
@@ -99,9 +100,11 @@ __device__ __forceinline__ void svd3_from_H(const T (&H)[3][3], SVD3<T>& o) {
   const T nrm2 = E[0][0] * E[0][0] + E[1][1] * E[1][1] + E[2][2] * E[2][2] +
                  T(2) * (E[0][1] * E[0][1] + E[0][2] * E[0][2] + E[1][2] * E[1][2]);
   const T thr = nrm2 * Eps<T>::v * Eps<T>::v;
+  // all lanes of a warp run the same number of sweeps (no divergence); a sweep
+  // on an already diagonal matrix leaves it unchanged
   for (int sweep = 0; sweep < 12; ++sweep) {
     const T off = E[0][1] * E[0][1] + E[0][2] * E[0][2] + E[1][2] * E[1][2];
-    if (off <= thr) break;
+    if (!__any_sync(0xffffffffu, off > thr)) break;
     jacobi_rot<T, 0, 1, 2>(E, V);
     jacobi_rot<T, 0, 2, 1>(E, V);
     jacobi_rot<T, 1, 2, 0>(E, V);
@@ -206,44 +209,47 @@ struct VolProj {
   T a[3];     // 1 / (2 s_i - sigma_i)
 };
 
+// Must be called by all 32 lanes of the warp together (full-warp votes).  Lanes
+// with active == false (or an inverted element) get a dummy result and false.
 template <typename T>
-__device__ __forceinline__ bool volume_project(const SVD3<T>& d, VolProj<T>& o) {
-  if (!(d.sig[0] > T(0) && d.sig[1] > T(0) && d.sig[2] > T(0))) return false;
+__device__ __forceinline__ bool volume_project(const SVD3<T>& d, VolProj<T>& o, bool active) {
+  const bool ok = active && d.sig[0] > T(0) && d.sig[1] > T(0) && d.sig[2] > T(0);
+  const T sg[3] = {ok ? d.sig[0] : T(1), ok ? d.sig[1] : T(1), ok ? d.sig[2] : T(1)};
+  const T sm[3] = {ok ? d.sm1[0] : T(0), ok ? d.sm1[1] : T(0), ok ? d.sm1[2] : T(0)};
   T lam = T(0);
   // the branch s_i(lam) exists for lam <= sigma_min^2 / 4: Newton steps that
   // overshoot it are pulled back halfway to the bound
-  const T smin = fmin(d.sig[0], fmin(d.sig[1], d.sig[2]));
+  const T smin = fmin(sg[0], fmin(sg[1], sg[2]));
   const T lmax = T(0.25) * smin * smin;
   for (int it = 0; it < 40; ++it) {
     T phi = T(0), dphi = T(0);
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
-      const T sg = d.sig[i];
-      const T q = T(1) - T(4) * lam / (sg * sg);
+      const T q = T(1) - T(4) * lam / (sg[i] * sg[i]);
       const T rq = tsqrt<T>(q > T(0) ? q : T(0));
-      const T gap = T(2) * lam / (sg * (T(1) + rq));
-      const T sm1 = d.sm1[i] - gap;
+      const T gap = T(2) * lam / (sg[i] * (T(1) + rq));
+      const T sm1 = sm[i] - gap;
       const T s = T(1) + sm1;
       phi += tlog1p<T>(sm1);
-      dphi += -T(1) / ((T(2) * s - sg) * s);
+      dphi += -T(1) / ((T(2) * s - sg[i]) * s);
     }
     const T step = phi / dphi;
     const T lold = lam;
     lam -= step;
     if (lam >= lmax) lam = T(0.5) * (lold + lmax);
-    if (fabs(step) <= T(4) * Eps<T>::v * fabs(lam) + T(1e-30)) break;
+    // warp-uniform exit: converged lanes keep taking (vanishing) Newton steps
+    if (!__any_sync(0xffffffffu, fabs(step) > T(4) * Eps<T>::v * fabs(lam) + T(1e-30))) break;
   }
   o.lam = lam;
 #pragma unroll
   for (int i = 0; i < 3; ++i) {
-    const T sg = d.sig[i];
-    const T q = T(1) - T(4) * lam / (sg * sg);
+    const T q = T(1) - T(4) * lam / (sg[i] * sg[i]);
     const T rq = tsqrt<T>(q > T(0) ? q : T(0));
-    o.gap[i] = T(2) * lam / (sg * (T(1) + rq));
-    o.s[i] = sg - o.gap[i];
-    o.a[i] = T(1) / (T(2) * o.s[i] - sg);
+    o.gap[i] = T(2) * lam / (sg[i] * (T(1) + rq));
+    o.s[i] = sg[i] - o.gap[i];
+    o.a[i] = T(1) / (T(2) * o.s[i] - sg[i]);
   }
-  return true;
+  return ok;
 }
 
 // dF - dR(F)[dF] for the corotated energy, as a matrix in the rotated frame:

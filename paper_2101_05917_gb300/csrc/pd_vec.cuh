@@ -8,6 +8,8 @@
 // scheduling.
 #pragma once
 
+#include <cooperative_groups.h>
+
 #include "pd_internal.cuh"
 #include "pd_iter.cuh"
 
@@ -137,6 +139,7 @@ __global__ void state_reset_kernel(IterState* st, StateCfg cfg) {
   st->hit_max = 0;
   st->force_accept = 0;
   st->fp64_checked = 0;
+  st->pending = 0;
   st->status = 0;
 }
 
@@ -248,99 +251,190 @@ __global__ void decide_fwd_kernel(IterState* st, const double* energy_partials, 
   }
 }
 
-// accepted trial: history pair, x <- xt, grad <- gradt, q <- gradt
-__global__ void accept_fwd_kernel(IterState* st, int64_t n3, double* x, const double* xt, double* grad,
-                                  const double* gradt, double* q, double* S, double* Y) {
+// ---------------------------------------------------------------- L-BFGS
+// The two-loop recursion around A^-1 (Sec. 4, quasi-Newton acceleration) as two
+// cooperative kernels: the pre-solve kernel also commits the accepted forward
+// trial / applies the backward update, the post-solve kernel also forms the
+// direction.  One grid-wide barrier per reduction; every block sums the
+// per-block partials in the same fixed order (double-buffered partials).
+namespace cg = cooperative_groups;
+
+__device__ __forceinline__ double block_sum_bcast(double v) {
+  __shared__ double sh[kT / 32];
+  __shared__ double tot;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+  for (int off = 16; off >= 1; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+  __syncthreads();
+  if (lane == 0) sh[w] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0;
+    for (int i = 0; i < kT / 32; ++i) t += sh[i];
+    tot = t;
+  }
+  __syncthreads();
+  return tot;
+}
+
+__device__ __forceinline__ double grid_total(cg::grid_group& g, double part, double* bufs, int& which) {
+  const double b = block_sum_bcast(part);
+  double* buf = bufs + (size_t)which * gridDim.x;
+  if (threadIdx.x == 0) buf[blockIdx.x] = b;
+  g.sync();
+  double acc = 0;
+  for (int i = threadIdx.x; i < (int)gridDim.x; i += kT) acc += __ldcg(buf + i);
+  which ^= 1;
+  return block_sum_bcast(acc);
+}
+
+#define PD_FOR_MINE(i) \
+  for (int64_t i = (int64_t)blockIdx.x * kT + threadIdx.x; i < n3; i += (int64_t)gridDim.x * kT)
+
+// first loop: q -= al_k y_k, al_k = rho_k s_k . q, newest -> oldest
+__device__ __forceinline__ void two_loop_first(cg::grid_group& g, IterState* st, int64_t n3, const double* S,
+                                               const double* Y, double* q, double* bufs, int& which) {
+  const int cnt = st->count;
+  for (int k = 0; k < cnt; ++k) {
+    const int i = idx_newest(st, k);
+    double part = 0;
+    PD_FOR_MINE(e) part += S[(int64_t)i * n3 + e] * q[e];
+    const double al = st->rho[i] * grid_total(g, part, bufs, which);
+    if (blockIdx.x == 0 && threadIdx.x == 0) st->al[i] = al;
+    PD_FOR_MINE(e) q[e] -= al * Y[(int64_t)i * n3 + e];
+  }
+}
+
+// second loop: be_k = rho_k y_k . r, r += s_k (al_k - be_k), oldest -> newest.
+// al_k was written by block 0 in the pre-solve kernel (an earlier launch).
+__device__ __forceinline__ void two_loop_second(cg::grid_group& g, IterState* st, int64_t n3, const double* S,
+                                                const double* Y, double* r, double* bufs, int& which) {
+  const int cnt = st->count;
+  for (int k = 0; k < cnt; ++k) {
+    const int j = idx_oldest(st, k);
+    double part = 0;
+    PD_FOR_MINE(e) part += Y[(int64_t)j * n3 + e] * r[e];
+    const double be = st->rho[j] * grid_total(g, part, bufs, which);
+    const double coef = st->al[j] - be;
+    PD_FOR_MINE(e) r[e] += coef * S[(int64_t)j * n3 + e];
+  }
+}
+
+// forward, before the solve: commit an accepted trial (history pair, x, grad),
+// then q = grad and the first loop
+__global__ void lbfgs_pre_fwd_kernel(VecCtx c, double* x, const double* xt, double* grad, const double* gradt,
+                                     double* q, double* S, double* Y) {
+  cg::grid_group g = cg::this_grid();
+  IterState* st = c.st;
   if (!st->accepted) return;
-  const int push = st->push;
-  const int slot = st->pslot;
-  for (int64_t i = (int64_t)blockIdx.x * kT + threadIdx.x; i < n3; i += (int64_t)gridDim.x * kT) {
-    const double xn = xt[i], gn = gradt[i];
+  const int64_t n3 = c.n3;
+  const int push = st->push, slot = st->pslot;
+  PD_FOR_MINE(e) {
+    const double xn = xt[e], gn = gradt[e];
     if (push) {
-      S[(int64_t)slot * n3 + i] = xn - x[i];
-      Y[(int64_t)slot * n3 + i] = gn - grad[i];
+      S[(int64_t)slot * n3 + e] = xn - x[e];
+      Y[(int64_t)slot * n3 + e] = gn - grad[e];
     }
-    x[i] = xn;
-    grad[i] = gn;
-    q[i] = gn;
+    x[e] = xn;
+    grad[e] = gn;
+    q[e] = gn;
   }
+  if (st->converged) return;
+  int which = 0;
+  two_loop_first(g, st, n3, S, Y, q, c.partials, which);
 }
 
-// two-loop recursion, first loop (newest -> oldest): q -= al_k y_k, al_k = rho_k s_k.q
-__global__ void lbfgs_loop1_kernel(VecCtx c, int k, const double* S, const double* Y, double* q) {
-  IterState* st = c.st;
-  if (st->converged || !st->accepted) return;
-  const int cnt = st->count;
-  if (k > cnt) return;
-  const int ip = k > 0 ? idx_newest(st, k - 1) : -1;
-  const int ic = k < cnt ? idx_newest(st, k) : -1;
-  const double alp = ip >= 0 ? st->al[ip] : 0.0;
-  double part = 0;
-  for (int64_t i = (int64_t)blockIdx.x * kT + threadIdx.x; i < c.n3; i += (int64_t)gridDim.x * kT) {
-    double qi = q[i];
-    if (ip >= 0) {
-      qi -= alp * Y[(int64_t)ip * c.n3 + i];
-      q[i] = qi;
-    }
-    if (ic >= 0) part += S[(int64_t)ic * c.n3 + i] * qi;
-  }
-  if (ic < 0) return;
-  double tot;
-  if (grid_sum(part, c.partials, c.counter, &tot)) st->al[ic] = st->rho[ic] * tot;
-}
-
-// second loop (oldest -> newest): be_k = rho_k y_k.r, r += s_k (al_k - be_k)
-__global__ void lbfgs_loop2_kernel(VecCtx c, int k, const double* S, const double* Y, double* r) {
-  IterState* st = c.st;
-  if (st->converged || !st->accepted) return;
-  const int cnt = st->count;
-  if (k > cnt) return;
-  const int ip = k > 0 ? idx_oldest(st, k - 1) : -1;
-  const int ic = k < cnt ? idx_oldest(st, k) : -1;
-  const double coef = ip >= 0 ? st->al[ip] - st->be[ip] : 0.0;
-  double part = 0;
-  for (int64_t i = (int64_t)blockIdx.x * kT + threadIdx.x; i < c.n3; i += (int64_t)gridDim.x * kT) {
-    double ri = r[i];
-    if (ip >= 0) {
-      ri += coef * S[(int64_t)ip * c.n3 + i];
-      r[i] = ri;
-    }
-    if (ic >= 0) part += Y[(int64_t)ic * c.n3 + i] * ri;
-  }
-  if (ic < 0) return;
-  double tot;
-  if (grid_sum(part, c.partials, c.counter, &tot)) st->be[ic] = st->rho[ic] * tot;
-}
-
-// finishes the two-loop (pending update of the newest pair when the history is
-// full), d = -r, slope = d.grad; forward also sets the trial xt = x + alpha d.
-// After a rejected forward trial only xt = x + alpha d is recomputed.
-__global__ void lbfgs_final_kernel(VecCtx c, const double* S, double* r, double* d, const double* grad,
-                                   const double* x, double* xt, int forward) {
+// forward, after the solve: second loop, d = -r, trial xt = x + d, slope = d.grad;
+// after a rejected trial only xt = x + alpha d
+__global__ void lbfgs_post_fwd_kernel(VecCtx c, const double* S, const double* Y, double* r, double* d,
+                                      const double* grad, const double* x, double* xt) {
+  cg::grid_group g = cg::this_grid();
   IterState* st = c.st;
   if (st->converged) return;
+  const int64_t n3 = c.n3;
   if (!st->accepted) {
-    if (!forward) return;
     const double a = st->alpha;
-    for (int64_t i = (int64_t)blockIdx.x * kT + threadIdx.x; i < c.n3; i += (int64_t)gridDim.x * kT)
-      xt[i] = x[i] + a * d[i];
+    PD_FOR_MINE(e) xt[e] = x[e] + a * d[e];
     return;
   }
-  const int cnt = st->count;
-  const int ip = (cnt == st->m && cnt > 0) ? idx_oldest(st, cnt - 1) : -1;
-  const double coef = ip >= 0 ? st->al[ip] - st->be[ip] : 0.0;
+  int which = 0;
+  two_loop_second(g, st, n3, S, Y, r, c.partials, which);
   double part = 0;
-  for (int64_t i = (int64_t)blockIdx.x * kT + threadIdx.x; i < c.n3; i += (int64_t)gridDim.x * kT) {
-    double ri = r[i];
-    if (ip >= 0) ri += coef * S[(int64_t)ip * c.n3 + i];
-    const double di = -ri;
-    d[i] = di;
-    if (forward) xt[i] = x[i] + di;
-    part += di * grad[i];
+  PD_FOR_MINE(e) {
+    const double de = -r[e];
+    d[e] = de;
+    xt[e] = x[e] + de;
+    part += de * grad[e];
   }
-  double tot;
-  if (grid_sum(part, c.partials, c.counter, &tot)) st->slope = tot;
+  const double slope = grid_total(g, part, c.partials, which);
+  if (blockIdx.x == 0 && threadIdx.x == 0) st->slope = slope;
 }
+
+// backward, before the solve: apply the previous step z += alpha d,
+// gs += alpha Hd (history pair alpha (d, Hd)), convergence test on |gs|, q = gs,
+// first loop.  The first iteration of a step has no previous direction.
+__global__ void lbfgs_pre_bwd_kernel(VecCtx c, const double* d, const double* Hd, double* z, double* gs,
+                                     double* q, double* S, double* Y) {
+  cg::grid_group g = cg::this_grid();
+  IterState* st = c.st;
+  if (st->converged) return;
+  const int64_t n3 = c.n3;
+  int which = 0;
+  if (st->pending) {
+    const double a = st->alpha;
+    const int push = st->push, slot = st->pslot;
+    const double tol2 = st->tol2, ref2 = st->ref2;
+    const int iters = st->iters + 1, max_iter = st->max_iter;
+    double part = 0;
+    PD_FOR_MINE(e) {
+      const double ad = a * d[e], ah = a * Hd[e];
+      z[e] += ad;
+      const double gn = gs[e] + ah;
+      gs[e] = gn;
+      if (push) {
+        S[(int64_t)slot * n3 + e] = ad;
+        Y[(int64_t)slot * n3 + e] = ah;
+      }
+      part += gn * gn;
+    }
+    const double gn2 = grid_total(g, part, c.partials, which);
+    const bool conv = gn2 <= tol2 * ref2;
+    const bool cap = !conv && iters >= max_iter;
+    g.sync();   // every block has read st before block 0 updates it
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+      st->gn2_acc = gn2;
+      st->iters = iters;
+      st->pending = 0;
+      if (conv || cap) {
+        st->converged = 1;
+        st->hit_max = cap ? 1 : 0;
+      }
+    }
+    if (conv || cap) return;
+  }
+  PD_FOR_MINE(e) q[e] = gs[e];
+  two_loop_first(g, st, n3, S, Y, q, c.partials, which);
+}
+
+// backward, after the solve: second loop, d = -r, slope = d.gs
+__global__ void lbfgs_post_bwd_kernel(VecCtx c, const double* S, const double* Y, double* r, double* d,
+                                      const double* gs) {
+  cg::grid_group g = cg::this_grid();
+  IterState* st = c.st;
+  if (st->converged) return;
+  const int64_t n3 = c.n3;
+  int which = 0;
+  two_loop_second(g, st, n3, S, Y, r, c.partials, which);
+  double part = 0;
+  PD_FOR_MINE(e) {
+    const double de = -r[e];
+    d[e] = de;
+    part += de * gs[e];
+  }
+  const double slope = grid_total(g, part, c.partials, which);
+  if (blockIdx.x == 0 && threadIdx.x == 0) st->slope = slope;
+}
+#undef PD_FOR_MINE
 
 // v_{t+1} = (x - x_t)/h, state advance, trajectory write in kept order
 __global__ void finalize_fwd_kernel(int64_t n, const double* x, double* xi, double* vi, double inv_h,
@@ -386,6 +480,8 @@ __global__ void decide_bwd_kernel(IterState* st, const double* gather_partials, 
   if (threadIdx.x != 0) return;
   if (st->converged) return;
   st->dHd = dHd;
+  st->evals += 1;
+  st->pending = 1;
   if (!isfinite(dHd)) {
     st->status |= DEV_ERR_NAN;
     st->converged = 1;
@@ -430,38 +526,6 @@ __global__ void decide_bwd_kernel(IterState* st, const double* gather_partials, 
     st->rho[slot] = 1.0 / sy;
     st->pslot = slot;
     st->push = 1;
-  }
-}
-
-__global__ void update_bwd_kernel(VecCtx c, const double* d, const double* Hd, double* z, double* gs,
-                                  double* q, double* S, double* Y) {
-  IterState* st = c.st;
-  if (st->converged) return;
-  const double a = st->alpha;
-  const int push = st->push, slot = st->pslot;
-  double part = 0;
-  for (int64_t i = (int64_t)blockIdx.x * kT + threadIdx.x; i < c.n3; i += (int64_t)gridDim.x * kT) {
-    const double ad = a * d[i], ah = a * Hd[i];
-    z[i] += ad;
-    const double g = gs[i] + ah;
-    gs[i] = g;
-    q[i] = g;
-    if (push) {
-      S[(int64_t)slot * c.n3 + i] = ad;
-      Y[(int64_t)slot * c.n3 + i] = ah;
-    }
-    part += g * g;
-  }
-  double tot;
-  if (grid_sum(part, c.partials, c.counter, &tot)) {
-    st->gn2_acc = tot;
-    st->iters += 1;
-    if (tot <= st->tol2 * st->ref2) {
-      st->converged = 1;
-    } else if (st->iters >= st->max_iter) {
-      st->converged = 1;
-      st->hit_max = 1;
-    }
   }
 }
 
