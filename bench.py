@@ -1,0 +1,342 @@
+#!/usr/bin/env python3
+"""Benchmark of the differentiable Projective Dynamics hot path.
+
+Workload: 32x32x64-cell hex beam (70,785 nodes, 212,355 DoFs), corotated +
+volume-preserving energies, per-element Young's modulus ~ lognormal(1e6, 0.2),
+x=0 face fixed, gravity, h = 0.01 s, 100 implicit-Euler steps; one bench step is
+the whole rollout forward (PD + L-BFGS) and backward (adjoint splitting iteration
++ L-BFGS) with gradients w.r.t. the per-element stiffness and the initial velocity.
+Mixed precision: FP32 local steps and triangular solves, FP64 factor, vectors
+and convergence checks.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line (rank 0).  value = forward+backward simulation steps per
+second over all ranks (each rank runs an independent replica: the solve does not
+shard).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "fwd+bwd sim steps/s at 1e-5 rel error vs FP64 oracle; % HBM roofline; p50/p99"
+WORKLOAD = "c2_beam_32x32x64_mixed_T100"
+TOL_FWD = 1e-7
+TOL_BWD = 1e-7
+# oracle local-step evaluations per simulation step used to scale the bounded
+# CPU sample (forward + backward iterations per step of this workload, measured
+# on the GPU path at the tolerances above)
+EVALS_PER_STEP_DEFAULT = 150
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--T", type=int, default=100, help="simulation steps per rollout")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.path = tempfile.mktemp(prefix="pd_clocks_", suffix=".csv")
+        self.proc = None
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "200",
+                 "-i", str(gpu_index)], stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    smax.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for nm, v in zip(names, parts[5:9]):
+                    if v.lower().startswith("active"):
+                        reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def solve_bytes(mesh, itemsize):
+    """Algorithmic bytes of one solve pair (forward + backward sweep): every
+    structural nonzero of the solve panels Q_s = [L11^-1; L21 L11^-1] read once per
+    sweep, plus the right-hand side read, the intermediate u written and read and
+    the solution written (3 columns per node)."""
+    import numpy as np
+    first = mesh.export("snode_first")
+    rp = mesh.export("row_ptr")
+    nc = np.diff(first).astype(np.int64)
+    nr = np.diff(rp).astype(np.int64)
+    nnz = int(np.sum(nr * nc - nc * (nc - 1) // 2))
+    nf3 = 3 * int(first[-1])
+    return 2 * nnz * itemsize + nf3 * (8 + 8 + 2 * itemsize), nnz
+
+
+def oracle_sample(evals_per_step, budget_s=12.0):
+    """Bounded CPU sample of the FP64 oracle on the same workload: repeated
+    evaluations of the local step and of grad g (oracle.model) on the 32x32x64
+    beam, timed for about budget_s seconds.  Projected to fwd+bwd sim steps/s as
+    1 / (t_eval * evals_per_step).  The oracle's sparse factorisation and
+    triangular solves are not included, so the projection over-estimates the
+    oracle's speed."""
+    import numpy as np
+    from oracle.model import Model
+    from workloads import beam_c2
+    sc = beam_c2(T=1)
+    model = Model(sc)
+    rng = np.random.default_rng(0)
+    x = sc.x0 + 1e-4 * rng.standard_normal(sc.x0.shape)
+    t0 = time.perf_counter()
+    n = 0
+    while True:
+        loc = model.local(x)
+        model.grad_g(x, x, None, loc)
+        n += 1
+        if time.perf_counter() - t0 >= budget_s:
+            break
+    t_eval = (time.perf_counter() - t0) / n
+    cores = os.cpu_count()
+    return {
+        "value": 1.0 / (t_eval * evals_per_step),
+        "unit": "steps/s",
+        "cores": cores,
+        "kind": "oracle",
+        "sample": (f"{n} oracle FP64 local-step + grad g evaluations on the 32x32x64 beam "
+                   f"({t_eval:.2f} s each, numpy/LAPACK on {cores} host cores), projected with "
+                   f"{evals_per_step} evaluations per fwd+bwd sim step; oracle factorisation "
+                   f"and solves excluded"),
+    }
+
+
+def run_reference(args):
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return
+    res = None
+    for _ in range(args.warmup):
+        oracle_sample(EVALS_PER_STEP_DEFAULT, budget_s=3.0)
+    vals = []
+    for _ in range(args.steps):
+        res = oracle_sample(EVALS_PER_STEP_DEFAULT, budget_s=8.0)
+        vals.append(res["value"])
+    value = statistics.median(vals)
+    res["value"] = value
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "parallelism": "replicas"},
+            "cpu_baseline": res,
+            "e2e": {"value": value, "unit": "steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+    world, rank, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    from paper_2101_05917_gb300 import build as _build
+    _build.build()
+    from paper_2101_05917_gb300 import api
+    from paper_2101_05917_gb300 import _native as N
+    from workloads import beam_c2
+
+    torch.cuda.set_device(local)
+    dev = torch.device(f"cuda:{local}")
+    T = args.T
+    sc = beam_c2(T=T)
+    mesh = api.PDMesh.from_scene(sc, device=local)
+    wc, wv, _, _ = api.scene_weights(sc, dev)
+    tt = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device=dev)
+    x0, v0, lw = tt(sc.x0), tt(sc.v0), tt(sc.loss_w)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    mesh.factorize(wc, wv, None, None, h=sc.h, gravity=tuple(sc.gravity), precision=N.PD_PREC_MIXED)
+    torch.cuda.synchronize()
+    t_factor = time.perf_counter() - t0
+    stream = torch.cuda.current_stream()
+    want = ("w_corot", "w_vol", "v0")
+
+    def rollout(profile):
+        opts = api.solver_opts(tol_fwd=TOL_FWD, tol_bwd=TOL_BWD, profile=profile)
+        roll = mesh.forward(x0, v0, T, opts=opts)
+        g = mesh.backward(roll, T, lw, opts=opts, want=want)
+        return roll, g
+
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)   # 256 MB > L2
+    for _ in range(args.warmup):
+        rollout(False)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    clocks = ClockSampler(local)
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    flush.fill_(1.0)
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    fstats, bstats, per_rollout = [], [], []
+    for k in range(args.steps):
+        h0 = time.perf_counter()
+        roll, g = rollout(True)
+        per_rollout.append(time.perf_counter() - h0)
+        fstats.append(roll.stats)
+        bstats.append(g["stats"])
+        flush.fill_(float(k))   # evict the factor panels between timed rollouts
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    clk = clocks.stop()
+    elapsed = ev0.elapsed_time(ev1) / 1e3
+    if world > 1:
+        t = torch.tensor([elapsed], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        elapsed = float(t.item())
+    sim_steps = world * args.steps * T
+    value = sim_steps / elapsed
+
+    # roofline of the dominant kernel pair (triangular solves), from the live events
+    solves = sum(s["solves"] for s in fstats + bstats)
+    solve_ms = sum(s["solve_ms"] for s in fstats + bstats)
+    local_ms = sum(s["local_ms"] for s in fstats)
+    locals_ = sum(s["local_steps"] for s in fstats)
+    bytes_solve, nnzq = solve_bytes(mesh, 4)
+    t_solve = solve_ms / 1e3 / max(solves, 1)
+    peak, peak_kind = peaks()
+    achieved = bytes_solve / t_solve / 1e9
+    traffic_path = os.path.join(ROOT, "profiles", "solve_traffic.json")
+    traffic = None
+    if os.path.exists(traffic_path):
+        with open(traffic_path) as f:
+            traffic = json.load(f).get("bytes_per_solve")
+    launches = sum(s["kernel_launches"] for s in fstats + bstats)
+    fwd_it = sum(s["fwd_iters"] for s in fstats) / (args.steps * T)
+    bwd_it = sum(s["bwd_iters"] for s in bstats) / (args.steps * T)
+
+    # end to end through the public API with host buffers: H2D of the inputs,
+    # factorisation (the weights are inputs), forward, backward, D2H of the gradients
+    host = {k: torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64).pin_memory()
+            for k, a in (("x0", sc.x0), ("v0", sc.v0), ("lw", sc.loss_w),
+                         ("wc", wc.cpu().numpy()), ("wv", wv.cpu().numpy()))}
+    h2d = sum(t.numel() * 8 for t in host.values())
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    d = {k: t.to(dev, non_blocking=True) for k, t in host.items()}
+    mesh.factorize(d["wc"], d["wv"], None, None, h=sc.h, gravity=tuple(sc.gravity), precision=N.PD_PREC_MIXED)
+    opts = api.solver_opts(tol_fwd=TOL_FWD, tol_bwd=TOL_BWD)
+    roll = mesh.forward(d["x0"], d["v0"], T, opts=opts)
+    g = mesh.backward(roll, T, d["lw"], opts=opts, want=want)
+    loss = (roll.x[-1] * d["lw"]).sum()
+    out_host = [g["w_corot"].cpu(), g["w_vol"].cpu(), g["v0"].cpu(), loss.cpu()]
+    e1.record(stream)
+    torch.cuda.synchronize()
+    d2h = sum(t.numel() * 8 for t in out_host)
+    e2e_value = world * T / (e0.elapsed_time(e1) / 1e3)
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        cpu = oracle_sample(int(round(fwd_it + bwd_it)))
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * elapsed / (args.steps * T),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "mixed-f32-f64",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "cells": int(mesh.e), "nodes": int(mesh.n),
+                       "dofs": 3 * int(mesh.n), "T": T, "tol_fwd": TOL_FWD, "tol_bwd": TOL_BWD,
+                       "lbfgs_m": 5, "fwd_iters_per_step": fwd_it, "bwd_iters_per_step": bwd_it,
+                       "factorize_s": t_factor, "factor_nnz": int(mesh.info["factor_nnz"]),
+                       "rollout_s": per_rollout,
+                       "l2": "256 MB buffer written between timed rollouts; FP32 solve panels "
+                             f"{nnzq * 4 / 1e6:.0f} MB stream through each solve",
+                       "parallelism": "replicas"},
+            "roofline": {"bound": "hbm", "kernel": "triangular solve pair (fwd_tile + bwd_tile launches)",
+                         "achieved": achieved, "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": traffic,
+                         "bytes_per_launch": bytes_solve, "avg_solve_us": 1e6 * t_solve, "solves": solves},
+            "local_step": {"avg_us": 1e3 * local_ms / max(locals_, 1), "launches": locals_},
+            "cpu_baseline": cpu,
+            "e2e": {"value": e2e_value, "unit": "steps/s", "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h, "includes": "H2D inputs, factorisation, forward, backward, D2H"},
+            "gpu_launches": launches,
+            "clocks": clk,
+        }
+        print(json.dumps(line))
+    mesh.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

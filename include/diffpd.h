@@ -132,8 +132,11 @@ typedef struct {
   int32_t lbfgs_m;              /* history length (0 = plain PD / plain splitting iteration) */
   int32_t ls_max;               /* Armijo backtracking tries (Sec. 6 uses 10) */
   int32_t checkpoint_every;     /* 0 = every state stored; K > 0 = store states t % K == 0 */
-  int32_t check_every;          /* iterations between host convergence polls (0 = 4) */
-  double mixed_switch;          /* MIXED: relative residual below which FP64 local steps run */
+  int32_t check_every;          /* iterations between host convergence polls (0 = 4); with
+                                   PD_PREC_MIXED the local steps run in FP32 and the convergence
+                                   test is confirmed by an FP64 residual */
+  int32_t profile;              /* nonzero: time the solve and local-step launches with CUDA
+                                   events on the launching stream (pd_stats.*_ms) */
 } pd_solver_opts;
 
 typedef struct {
@@ -145,6 +148,11 @@ typedef struct {
   int32_t inverted;                     /* det F <= 0 seen */
   int32_t not_converged_steps;
   double fwd_ms, bwd_ms;                /* host wall time of the call */
+  int64_t kernel_launches;              /* kernels this call launched */
+  int64_t solves;                       /* global-step solves (forward + backward sweep pairs) */
+  double solve_ms;                      /* profile: summed device time of the solves */
+  int64_t local_steps;                  /* forward local steps (FP32 or FP64) */
+  double local_ms;                      /* profile: summed device time of the forward local steps */
 } pd_stats;
 
 /* Forward rollout of T implicit-Euler steps (Sec. 3 Eqns 1-4, Alg. 1).

@@ -61,7 +61,7 @@ class SolverOpts(ctypes.Structure):
                 ("max_iter_fwd", ctypes.c_int32), ("max_iter_bwd", ctypes.c_int32),
                 ("lbfgs_m", ctypes.c_int32), ("ls_max", ctypes.c_int32),
                 ("checkpoint_every", ctypes.c_int32), ("check_every", ctypes.c_int32),
-                ("mixed_switch", ctypes.c_double)]
+                ("profile", ctypes.c_int32)]
 
 
 class Stats(ctypes.Structure):
@@ -71,7 +71,9 @@ class Stats(ctypes.Structure):
                 ("max_fwd_iters_step", ctypes.c_int32), ("max_bwd_iters_step", ctypes.c_int32),
                 ("max_fwd_rel_residual", ctypes.c_double), ("max_bwd_rel_residual", ctypes.c_double),
                 ("inverted", ctypes.c_int32), ("not_converged_steps", ctypes.c_int32),
-                ("fwd_ms", ctypes.c_double), ("bwd_ms", ctypes.c_double)]
+                ("fwd_ms", ctypes.c_double), ("bwd_ms", ctypes.c_double),
+                ("kernel_launches", ctypes.c_int64), ("solves", ctypes.c_int64), ("solve_ms", ctypes.c_double),
+                ("local_steps", ctypes.c_int64), ("local_ms", ctypes.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

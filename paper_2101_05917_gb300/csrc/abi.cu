@@ -114,7 +114,6 @@ pd_solver_opts default_opts() {
   o.ls_max = 10;
   o.checkpoint_every = 0;
   o.check_every = 4;
-  o.mixed_switch = 1e-5;
   return o;
 }
 
@@ -129,12 +128,40 @@ pd_solver_opts fill_opts(const pd_solver_opts* o) {
   if (r.lbfgs_m > kMaxHistory) r.lbfgs_m = kMaxHistory;
   if (r.ls_max < 0) r.ls_max = 0;
   if (r.check_every <= 0) r.check_every = d.check_every;
-  if (!(r.mixed_switch > 0)) r.mixed_switch = d.mixed_switch;
   return r;
 }
 
+// CUDA events bracketing selected launches (profile mode); elapsed times are
+// summed after the call's final synchronisation.
+struct EventTimer {
+  std::vector<cudaEvent_t> pool;
+  size_t used = 0;
+  void record(cudaStream_t s) {
+    if (used == pool.size()) {
+      cudaEvent_t e;
+      cudaEventCreate(&e);
+      pool.push_back(e);
+    }
+    cudaEventRecord(pool[used++], s);
+  }
+  double total_ms() {   // pairs (start, end)
+    double t = 0;
+    for (size_t i = 0; i + 1 < used; i += 2) {
+      float ms = 0;
+      if (cudaEventElapsedTime(&ms, pool[i], pool[i + 1]) == cudaSuccess) t += ms;
+    }
+    return t;
+  }
+  ~EventTimer() {
+    for (cudaEvent_t e : pool) cudaEventDestroy(e);
+  }
+};
+
 struct Ctx {
   MeshImpl* m;
+  int64_t launches = 0, solves = 0, locals = 0;
+  EventTimer* solve_t = nullptr;
+  EventTimer* local_t = nullptr;
   cudaStream_t s;
   pd_solver_opts o;
   int64_t n, nf, n3f;
@@ -145,6 +172,12 @@ struct Ctx {
   double* pg;      // gather partials
   int nbe, nbg;
 };
+
+int64_t solve_launches(const MeshImpl* m) {
+  int64_t k = 0;
+  for (const SolveLevel& sl : m->sched.levels) k += (sl.fwd_cnt > 0) + (sl.bwd_cnt > 0);
+  return k;
+}
 
 Ctx make_ctx(MeshImpl* m, cudaStream_t s, const pd_solver_opts& o) {
   Ctx c;
@@ -186,12 +219,19 @@ pd_status launch_fwd_iteration(Ctx& c, int prec, const double* act_t) {
   Workspace& w = m->ws;
   IterState* st = w.st;
   LocalArgs la{m, st, w.xt, nullptr, act_t, prec};
+  if (c.local_t) c.local_t->record(c.s);
   PD_CUDA_TRY(launch_element_forces(la, w.elembuf, c.pe, w.flags, c.s));
+  if (c.local_t) c.local_t->record(c.s);
   PD_CUDA_TRY(launch_gather_grad(m, st, w.elembuf, prec, w.xt, w.y, w.dir, w.gradt, c.pg, c.s));
   decide_fwd_kernel<<<1, 256, 0, c.s>>>(st, c.pe, c.nbe, c.pg, c.nbg);
   PD_CUDA_TRY(coop_launch(lbfgs_pre_fwd_kernel, c.coop, c.s, c.vc, w.x, (const double*)w.xt, w.grad,
                           (const double*)w.gradt, w.q, w.S, w.Y));
+  if (c.solve_t) c.solve_t->record(c.s);
   PD_CUDA_TRY(solve_A(m, st, w.q, w.r, m->precision, c.s));
+  if (c.solve_t) c.solve_t->record(c.s);
+  c.launches += 5 + solve_launches(m);
+  c.solves += 1;
+  c.locals += 1;
   PD_CUDA_TRY(coop_launch(lbfgs_post_fwd_kernel, c.coop, c.s, c.vc, (const double*)w.S, (const double*)w.Y,
                           w.r, w.dir, (const double*)w.grad, (const double*)w.x, w.xt));
   return PD_OK;
@@ -205,7 +245,11 @@ pd_status launch_bwd_iteration(Ctx& c, int prec, const double* xnext, const doub
   IterState* st = w.st;
   PD_CUDA_TRY(coop_launch(lbfgs_pre_bwd_kernel, c.coop, c.s, c.vc, (const double*)w.dir, (const double*)w.Hd,
                           w.z, w.gs, w.q, w.S, w.Y));
+  if (c.solve_t) c.solve_t->record(c.s);
   PD_CUDA_TRY(solve_A(m, st, w.q, w.r, m->precision, c.s));
+  if (c.solve_t) c.solve_t->record(c.s);
+  c.launches += 6 + solve_launches(m);
+  c.solves += 1;
   PD_CUDA_TRY(coop_launch(lbfgs_post_bwd_kernel, c.coop, c.s, c.vc, (const double*)w.S, (const double*)w.Y,
                           w.r, w.dir, (const double*)w.gs));
   LocalArgs la{m, st, xnext, w.dir, act_t, prec};
@@ -252,6 +296,7 @@ pd_status forward_step(Ctx& c, const double* act_t, const double* fext_int, doub
   pp.st = w.st;
   predictor_kernel<<<grid_for(c.n), 256, 0, c.s>>>(pp);
   PD_CUDA_TRY(cudaGetLastError());
+  c.launches += 2;
   // MIXED: iterate with FP32 local steps; when the FP32 residual meets the
   // tolerance, re-evaluate the gradient at the accepted point with an FP64 local
   // step (the convergence check).  If it fails the FP32 iteration continues from
@@ -272,7 +317,10 @@ pd_status forward_step(Ctx& c, const double* act_t, const double* fext_int, doub
     }
     launched += chunk;
     if (mixed && prec == PD_PREC_FP64) fp64_launched += chunk;
-    if (chunk > 0) clear_checked_kernel<<<1, 1, 0, c.s>>>(w.st);
+    if (chunk > 0) {
+      clear_checked_kernel<<<1, 1, 0, c.s>>>(w.st);
+      c.launches += 1;
+    }
     pd_status e = poll(c);
     if (e != PD_OK) return e;
     const IterState& sh = *w.st_host;
@@ -291,6 +339,7 @@ pd_status forward_step(Ctx& c, const double* act_t, const double* fext_int, doub
         if (e2 != PD_OK) return e2;
         fp64_launched += 1;
         mark_checked_kernel<<<1, 1, 0, c.s>>>(w.st);
+        c.launches += 3;
         chunk = 0;
         continue;
       }
@@ -321,6 +370,7 @@ pd_status forward_step(Ctx& c, const double* act_t, const double* fext_int, doub
   guess = std::max(1, sh.iters - 1);
   finalize_fwd_kernel<<<grid_for(c.n), 256, 0, c.s>>>(c.n, w.x, w.xprev, w.vprev, 1.0 / m->h_step,
                                                       m->kept_of_internal, traj_x, traj_v);
+  c.launches += 1;
   PD_CUDA_TRY(cudaGetLastError());
   return PD_OK;
 }
@@ -342,6 +392,15 @@ void accumulate(pd_stats* st, const StepInfo& i, bool fwd) {
   if (!i.converged) st->not_converged_steps += 1;
 }
 
+void finish_stats(Ctx& c, pd_stats* st) {
+  if (!st) return;
+  st->kernel_launches = c.launches;
+  st->solves = c.solves;
+  st->local_steps = c.locals;
+  st->solve_ms = c.solve_t ? c.solve_t->total_ms() : 0.0;
+  st->local_ms = c.local_t ? c.local_t->total_ms() : 0.0;
+}
+
 pd_status check_flags(Ctx& c, pd_stats* stats) {
   int flags = 0;
   PD_CUDA_TRY(cudaMemcpyAsync(&flags, c.m->ws.flags, sizeof(int), cudaMemcpyDeviceToHost, c.s));
@@ -361,6 +420,7 @@ pd_status backward_step(Ctx& c, const double* xnext, const double* xt_, const do
   StateCfg cfg{c.o.tol_bwd, 0.0, c.o.lbfgs_m, c.o.ls_max, c.o.max_iter_bwd, 1};
   state_reset_kernel<<<1, 1, 0, c.s>>>(w.st, cfg);
   bwd_step_init_kernel<<<c.vb, 256, 0, c.s>>>(c.vc, w.ax, w.av, inv_h, w.z, w.gs, w.q);
+  c.launches += 2;
   // Hessian products in the factor's precision; at convergence of the recursively
   // updated residual, the true residual H z - gbar is evaluated with an FP64
   // product and replaces it (iterative refinement); the iteration continues
@@ -393,6 +453,7 @@ pd_status backward_step(Ctx& c, const double* xnext, const double* xt_, const do
       PD_CUDA_TRY(launch_gather_hvp(m, nullptr, w.elembuf, PD_PREC_FP64, xnext, w.z, nullptr, w.Hd, c.pg, c.s));
       residual_replace_kernel<<<c.vb, 256, 0, c.s>>>(c.vc, w.Hd, w.ax, w.av, inv_h, w.gs, w.q);
       fp64_launched += 1;
+      c.launches += 3;
       e = poll(c);
       if (e != PD_OK) return e;
       ++checks;
@@ -442,6 +503,7 @@ pd_status backward_step(Ctx& c, const double* xnext, const double* xt_, const do
   bp.counter = w.counters;
   bwd_state_kernel<<<grid_for(c.n), 256, 0, c.s>>>(bp);
   PD_CUDA_TRY(cudaGetLastError());
+  c.launches += 2;
   return PD_OK;
 }
 
@@ -734,6 +796,11 @@ pd_status pd_forward(pd_mesh mesh, const double* x0, const double* v0, const dou
   if (ws != PD_OK) return ws;
   cudaStream_t s = (cudaStream_t)stream;
   Ctx c = make_ctx(m, s, o);
+  EventTimer tsolve, tlocal;
+  if (o.profile) {
+    c.solve_t = &tsolve;
+    c.local_t = &tlocal;
+  }
   Workspace& w = m->ws;
   const int64_t n = m->h.n;
   if (stats) std::memset(stats, 0, sizeof(*stats));
@@ -769,6 +836,7 @@ pd_status pd_forward(pd_mesh mesh, const double* x0, const double* v0, const dou
   }
   PD_CUDA_TRY(cudaStreamSynchronize(s));
   check_flags(c, stats);
+  finish_stats(c, stats);
   if (stats) stats->fwd_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
   const int nan = w.st_host->status & DEV_ERR_NAN;
   if (nan) {
@@ -806,6 +874,11 @@ pd_status pd_backward(pd_mesh mesh, const double* x_traj, const double* v_traj, 
   if (ws != PD_OK) return ws;
   cudaStream_t s = (cudaStream_t)stream;
   Ctx c = make_ctx(m, s, o);
+  EventTimer tsolve, tlocal;
+  if (o.profile) {
+    c.solve_t = &tsolve;
+    c.local_t = &tlocal;
+  }
   Workspace& w = m->ws;
   const int64_t n = m->h.n, e = m->h.e;
   if (stats) std::memset(stats, 0, sizeof(*stats));
@@ -891,6 +964,7 @@ pd_status pd_backward(pd_mesh mesh, const double* x_traj, const double* v_traj, 
   if (seg) PD_CUDA_TRY(cudaFreeAsync(seg, s));
   PD_CUDA_TRY(cudaStreamSynchronize(s));
   check_flags(c, stats);
+  finish_stats(c, stats);
   if (stats) stats->bwd_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
   if (w.st_host->status & DEV_ERR_NAN) {
     set_error("pd_backward: non-finite residual");

@@ -149,7 +149,9 @@ __global__ void __launch_bounds__(kElemThreads) element_kernel(ElemParams p) {
       }
     }
   }
-  if (wm != T(0)) {
+  // dL/dw_muscle exists for every element with a fibre, also where w_muscle = 0
+  const bool musc = (MODE == MODE_PGRAD) ? (valid && p.wm != nullptr) : (wm != T(0));
+  if (musc) {
     const T m0 = (T)p.fiber[3 * e + 0], m1 = (T)p.fiber[3 * e + 1], m2 = (T)p.fiber[3 * e + 2];
     const T mv[3] = {m0, m1, m2};
     T f[3], Hm[3];
