@@ -104,6 +104,13 @@ pd_status ensure_workspace(MeshImpl* m, int lbfgs_m) {
   return PD_OK;
 }
 
+// The persistent solve counts tickets and finished blocks monotonically; a fresh
+// start at every public call also recovers from an aborted solve.
+cudaError_t reset_solve_counters(MeshImpl* m, cudaStream_t s) {
+  const size_t n = 1 + (size_t)(m->sched.n_fwd_out + m->sched.n_bwd_out) + 2 * (size_t)m->h.ns;
+  return cudaMemsetAsync(m->solve_counters, 0, sizeof(unsigned long long) * n, s);
+}
+
 pd_solver_opts default_opts() {
   pd_solver_opts o{};
   o.tol_fwd = 1e-9;
@@ -161,6 +168,7 @@ struct Ctx {
   MeshImpl* m;
   int64_t launches = 0, solves = 0, locals = 0;
   EventTimer* solve_t = nullptr;
+  int dev_flags = 0;
   EventTimer* local_t = nullptr;
   cudaStream_t s;
   pd_solver_opts o;
@@ -172,12 +180,6 @@ struct Ctx {
   double* pg;      // gather partials
   int nbe, nbg;
 };
-
-int64_t solve_launches(const MeshImpl* m) {
-  int64_t k = 0;
-  for (const SolveLevel& sl : m->sched.levels) k += (sl.fwd_cnt > 0) + (sl.bwd_cnt > 0);
-  return k;
-}
 
 Ctx make_ctx(MeshImpl* m, cudaStream_t s, const pd_solver_opts& o) {
   Ctx c;
@@ -229,7 +231,7 @@ pd_status launch_fwd_iteration(Ctx& c, int prec, const double* act_t) {
   if (c.solve_t) c.solve_t->record(c.s);
   PD_CUDA_TRY(solve_A(m, st, w.q, w.r, m->precision, c.s));
   if (c.solve_t) c.solve_t->record(c.s);
-  c.launches += 5 + solve_launches(m);
+  c.launches += 6;
   c.solves += 1;
   c.locals += 1;
   PD_CUDA_TRY(coop_launch(lbfgs_post_fwd_kernel, c.coop, c.s, c.vc, (const double*)w.S, (const double*)w.Y,
@@ -248,7 +250,7 @@ pd_status launch_bwd_iteration(Ctx& c, int prec, const double* xnext, const doub
   if (c.solve_t) c.solve_t->record(c.s);
   PD_CUDA_TRY(solve_A(m, st, w.q, w.r, m->precision, c.s));
   if (c.solve_t) c.solve_t->record(c.s);
-  c.launches += 6 + solve_launches(m);
+  c.launches += 7;
   c.solves += 1;
   PD_CUDA_TRY(coop_launch(lbfgs_post_bwd_kernel, c.coop, c.s, c.vc, (const double*)w.S, (const double*)w.Y,
                           w.r, w.dir, (const double*)w.gs));
@@ -406,6 +408,7 @@ pd_status check_flags(Ctx& c, pd_stats* stats) {
   PD_CUDA_TRY(cudaMemcpyAsync(&flags, c.m->ws.flags, sizeof(int), cudaMemcpyDeviceToHost, c.s));
   PD_CUDA_TRY(cudaStreamSynchronize(c.s));
   if (stats && (flags & DEV_ERR_INVERTED)) stats->inverted = 1;
+  c.dev_flags = flags;
   return PD_OK;
 }
 
@@ -607,13 +610,20 @@ pd_status pd_create_mesh(const pd_mesh_desc* desc, pd_mesh* out) {
     for (size_t k = 0; k + 1 < h.gath_ptr.size(); ++k)
       for (int64_t g = h.gath_ptr[k]; g < h.gath_ptr[k + 1]; ++g) slots[k * w + (g - h.gath_ptr[k])] = h.gath[g];
     if ((e = upload(&I, &I.gath_slots, slots)) != cudaSuccess) return fail(e);
-    if ((e = dalloc(&I, &I.fwd_tiles, S.fwd.size())) != cudaSuccess) return fail(e);
-    if ((e = dalloc(&I, &I.bwd_tiles, S.bwd.size())) != cudaSuccess) return fail(e);
-    if (!S.fwd.empty() && (e = cudaMemcpy(I.fwd_tiles, S.fwd.data(), sizeof(SolveTile) * S.fwd.size(), cudaMemcpyHostToDevice)) != cudaSuccess) return fail(e);
-    if (!S.bwd.empty() && (e = cudaMemcpy(I.bwd_tiles, S.bwd.data(), sizeof(SolveTile) * S.bwd.size(), cudaMemcpyHostToDevice)) != cudaSuccess) return fail(e);
-    const size_t nt = (size_t)(S.n_fwd_out + S.n_bwd_out);
-    if ((e = dalloc(&I, &I.ws.solve_tickets, nt)) != cudaSuccess) return fail(e);
-    if ((e = cudaMemset(I.ws.solve_tickets, 0, sizeof(unsigned) * nt)) != cudaSuccess) return fail(e);
+    if ((e = upload(&I, &I.nfb, S.nfb)) != cudaSuccess) return fail(e);
+    if ((e = upload(&I, &I.nbb, S.nbb)) != cudaSuccess) return fail(e);
+    if ((e = upload(&I, &I.parent, h.parent)) != cudaSuccess) return fail(e);
+    if ((e = dalloc(&I, &I.all_tiles, S.all.size())) != cudaSuccess) return fail(e);
+    if (!S.all.empty() && (e = cudaMemcpy(I.all_tiles, S.all.data(), sizeof(SolveTile) * S.all.size(), cudaMemcpyHostToDevice)) != cudaSuccess) return fail(e);
+    const size_t ncount = 1 + (size_t)(S.n_fwd_out + S.n_bwd_out) + 2 * (size_t)h.ns;
+    if ((e = dalloc(&I, &I.solve_counters, ncount)) != cudaSuccess) return fail(e);
+    if ((e = cudaMemset(I.solve_counters, 0, sizeof(unsigned long long) * ncount)) != cudaSuccess) return fail(e);
+    {
+      int dev = 0, sms = 0;
+      cudaGetDevice(&dev);
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+      I.solve_grid = sms * solve_persistent_occupancy();
+    }
     if ((e = dalloc(&I, (char**)&I.ws.solve_partial, solve_partial_bytes(S))) != cudaSuccess) return fail(e);
   }
   I.flevels.assign(h.nlev, FactorLevel{});
@@ -805,6 +815,7 @@ pd_status pd_forward(pd_mesh mesh, const double* x0, const double* v0, const dou
   const int64_t n = m->h.n;
   if (stats) std::memset(stats, 0, sizeof(*stats));
   PD_CUDA_TRY(cudaMemsetAsync(w.flags, 0, sizeof(int), s));
+  PD_CUDA_TRY(reset_solve_counters(m, s));
   kept_to_internal_kernel<<<grid_for(n), 256, 0, s>>>(n, m->kept_of_internal, x0, w.xprev);
   kept_to_internal_kernel<<<grid_for(n), 256, 0, s>>>(n, m->kept_of_internal, v0, w.vprev);
   const double* fext_int = nullptr;
@@ -838,6 +849,10 @@ pd_status pd_forward(pd_mesh mesh, const double* x0, const double* v0, const dou
   check_flags(c, stats);
   finish_stats(c, stats);
   if (stats) stats->fwd_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  if (c.dev_flags & DEV_ERR_TIMEOUT) {
+    set_error("pd_forward: a device-side wait in the solve timed out");
+    return PD_ERR_TIMEOUT;
+  }
   const int nan = w.st_host->status & DEV_ERR_NAN;
   if (nan) {
     set_error("pd_forward: non-finite residual");
@@ -883,6 +898,7 @@ pd_status pd_backward(pd_mesh mesh, const double* x_traj, const double* v_traj, 
   const int64_t n = m->h.n, e = m->h.e;
   if (stats) std::memset(stats, 0, sizeof(*stats));
   PD_CUDA_TRY(cudaMemsetAsync(w.flags, 0, sizeof(int), s));
+  PD_CUDA_TRY(reset_solve_counters(m, s));
   // segment storage for recomputed states (internal order): K+1 states of x and v
   double* seg = nullptr;
   if (K > 0) PD_CUDA_TRY(cudaMallocAsync((void**)&seg, sizeof(double) * 6 * n * (size_t)(K + 1), s));
@@ -966,6 +982,10 @@ pd_status pd_backward(pd_mesh mesh, const double* x_traj, const double* v_traj, 
   check_flags(c, stats);
   finish_stats(c, stats);
   if (stats) stats->bwd_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  if (c.dev_flags & DEV_ERR_TIMEOUT) {
+    set_error("pd_backward: a device-side wait in the solve timed out");
+    return PD_ERR_TIMEOUT;
+  }
   if (w.st_host->status & DEV_ERR_NAN) {
     set_error("pd_backward: non-finite residual");
     return PD_ERR_NAN;
@@ -1054,6 +1074,7 @@ pd_status pd_solve_A(pd_mesh mesh, const double* b, double* x, int32_t precision
   Workspace& w = m->ws;
   const int64_t n = m->h.n;
   kept_to_internal_kernel<<<grid_for(n), 256, 0, s>>>(n, m->kept_of_internal, b, w.iov);
+  PD_CUDA_TRY(reset_solve_counters(m, s));
   PD_CUDA_TRY(solve_A(m, nullptr, w.iov, w.iox, precision, s));
   internal_to_kept_kernel<<<grid_for(n), 256, 0, s>>>(n, m->h.nf, m->kept_of_internal, w.iox, x);
   PD_CUDA_TRY(cudaGetLastError());

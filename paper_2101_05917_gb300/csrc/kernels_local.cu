@@ -56,6 +56,12 @@ struct ElemParams {
 template <typename T, int MODE>
 __global__ void __launch_bounds__(kElemThreads) element_kernel(ElemParams p) {
   if (p.gate && p.gate->converged) return;
+  __shared__ double wsum[kElemThreads / 32];
+  __shared__ unsigned arrived;
+  if (MODE == MODE_FORCE) {
+    if (threadIdx.x == 0) arrived = 0u;
+    __syncthreads();   // at entry all warps are together: no wait
+  }
   const int lane = threadIdx.x & 31;
   const int base = lane & ~7;
   const int k = lane & 7;
@@ -234,11 +240,22 @@ __global__ void __launch_bounds__(kElemThreads) element_kernel(ElemParams p) {
     out[2] = fa[2];
   }
   if (MODE == MODE_FORCE) {
-    // per-warp energy partial (fixed butterfly; no block barrier)
+    // block energy partial without a block barrier: each warp deposits its sum,
+    // the last warp to arrive adds the 8 deposits in warp order
     double en = valid ? (double)energy : 0.0;
 #pragma unroll
     for (int off = 16; off >= 1; off >>= 1) en += __shfl_xor_sync(0xffffffffu, en, off);
-    if (lane == 0) p.energy[((int64_t)blockIdx.x * kElemThreads + threadIdx.x) >> 5] = en;
+    if (lane == 0) {
+      wsum[threadIdx.x >> 5] = en;
+      __threadfence_block();
+      const unsigned t = atomicAdd(&arrived, 1u);
+      if (t == kElemThreads / 32 - 1) {
+        __threadfence_block();
+        double tot = 0;
+        for (int w = 0; w < kElemThreads / 32; ++w) tot += ((volatile double*)wsum)[w];
+        p.energy[blockIdx.x] = tot;
+      }
+    }
   }
 }
 
@@ -386,7 +403,7 @@ GatherParams make_gather(const MeshImpl* m) {
 int element_blocks(const MeshImpl* m) {
   return (int)((m->h.e * 8 + kElemThreads - 1) / kElemThreads);
 }
-int element_energy_partials(const MeshImpl* m) { return element_blocks(m) * (kElemThreads / 32); }
+int element_energy_partials(const MeshImpl* m) { return element_blocks(m); }
 int gather_blocks(const MeshImpl* m) {
   return (int)((m->h.nf + kGatherThreads - 1) / kGatherThreads);
 }

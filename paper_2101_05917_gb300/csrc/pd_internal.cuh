@@ -29,6 +29,7 @@ enum : int {
   DEV_ERR_NOT_SPD = 1,
   DEV_ERR_INVERTED = 2,
   DEV_ERR_NAN = 4,
+  DEV_ERR_TIMEOUT = 8,   // a bounded device-side wait gave up
 };
 
 // ---------------------------------------------------------------- buffers
@@ -59,7 +60,9 @@ struct alignas(16) SolveTile {
 };
 struct SolveSchedule {
   std::vector<SolveTile> fwd, bwd;
+  std::vector<SolveTile> all;      // persistent order: forward tiles, then backward tiles by descending level
   int64_t n_fwd_out = 0, n_bwd_out = 0;
+  std::vector<int32_t> nfb, nbb;   // per supernode: forward / backward output blocks
   std::vector<SolveLevel> levels;
 };
 
@@ -87,7 +90,6 @@ struct Workspace {
   void* solve_u = nullptr;                    // (3 nf) T
   void* solve_W = nullptr;                    // (3 * below rows) T
   void* solve_partial = nullptr;              // per-tile partial sums
-  unsigned* solve_tickets = nullptr;          // per output block
   double* act_cur = nullptr;                  // unused placeholder for per-step actuation
   int lbfgs_m = 0;
   size_t bytes = 0;
@@ -105,7 +107,11 @@ struct MeshImpl {
   int64_t *gath_ptr = nullptr, *front_off = nullptr, *level_list = nullptr, *child_ptr = nullptr,
           *child_list = nullptr;
   int32_t *rows = nullptr, *gath = nullptr, *rel = nullptr;
-  SolveTile *fwd_tiles = nullptr, *bwd_tiles = nullptr;
+  SolveTile* all_tiles = nullptr;
+  int32_t *nfb = nullptr, *nbb = nullptr;
+  int64_t* parent = nullptr;
+  unsigned long long* solve_counters = nullptr;   // gticket | otick[...] | fdone[ns] | bdone[ns]
+  int solve_grid = 0;
   int32_t* gath_slots = nullptr;   // (sum nr) x slot_w update-row sources, -1 = none
   int slot_w = 1;
   SolveSchedule sched;
@@ -166,5 +172,6 @@ cudaError_t solve_A(const MeshImpl* m, const IterState* gate, const double* b, d
                     int precision, cudaStream_t s);
 void build_solve_schedule(const HostMesh& h, SolveSchedule& S);
 size_t solve_partial_bytes(const SolveSchedule& S);
+int solve_persistent_occupancy();
 
 }  // namespace pd

@@ -221,6 +221,9 @@ __device__ __forceinline__ bool volume_project(const SVD3<T>& d, VolProj<T>& o, 
   // overshoot it are pulled back halfway to the bound
   const T smin = fmin(sg[0], fmin(sg[1], sg[2]));
   const T lmax = T(0.25) * smin * smin;
+  // lam is of the order of the principal strains: converge relative to that
+  // scale (a test relative to |lam| alone never triggers when det F = 1)
+  const T scale = fabs(sm[0]) + fabs(sm[1]) + fabs(sm[2]) + T(1e-30);
   for (int it = 0; it < 40; ++it) {
     T phi = T(0), dphi = T(0);
 #pragma unroll
@@ -238,7 +241,7 @@ __device__ __forceinline__ bool volume_project(const SVD3<T>& d, VolProj<T>& o, 
     lam -= step;
     if (lam >= lmax) lam = T(0.5) * (lold + lmax);
     // warp-uniform exit: converged lanes keep taking (vanishing) Newton steps
-    if (!__any_sync(0xffffffffu, fabs(step) > T(4) * Eps<T>::v * fabs(lam) + T(1e-30))) break;
+    if (!__any_sync(0xffffffffu, fabs(step) > T(4) * Eps<T>::v * (fabs(lam) + scale))) break;
   }
   o.lam = lam;
 #pragma unroll
