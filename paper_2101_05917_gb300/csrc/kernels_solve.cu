@@ -71,7 +71,7 @@ __device__ __forceinline__ SolveTile load_tile(const SolveTile* t, int64_t i) {
 // flag DEV_ERR_TIMEOUT).  Counters only grow: a solve consumes ntiles + grid
 // tickets (every CTA draws one ticket past the end), so ticket t belongs to
 // solve t / (ntiles + grid).
-constexpr long long kSpinLimit = 1ll << 22;
+constexpr long long kSpinLimit = 1ll << 20;   // about a second of polling
 
 __device__ __forceinline__ unsigned long long vload(const unsigned long long* p) {
   return *reinterpret_cast<const volatile unsigned long long*>(p);
