@@ -54,7 +54,8 @@ struct ElemParams {
 };
 
 template <typename T, int MODE>
-__global__ void __launch_bounds__(kElemThreads) element_kernel(ElemParams p) {
+__global__ void __launch_bounds__(kElemThreads, sizeof(T) == 8 ? 1 : (MODE == MODE_FORCE ? 3 : 2))
+element_kernel(ElemParams p) {
   if (p.gate && p.gate->converged) return;
   __shared__ double wsum[kElemThreads / 32];
   __shared__ unsigned arrived;
