@@ -38,7 +38,7 @@ struct SolveParams {
   const SolveTile* tiles;
   // persistent kernel
   int64_t ntiles;               // forward tiles then backward tiles
-  unsigned long long* gticket;  // arrival tickets (grid per solve)
+  unsigned long long* gticket;  // tile tickets (grid + ntiles consumed per solve)
   unsigned long long* otick;    // per output block (64-bit, monotone)
   unsigned long long* fdone;    // per supernode: finished forward output blocks
   unsigned long long* bdone;    // per supernode: finished backward output blocks
@@ -63,33 +63,30 @@ __device__ __forceinline__ SolveTile load_tile(const SolveTile* t, int64_t i) {
 }
 
 // ------------------------------------------------------------ persistent
-// Whole solve (forward and backward sweeps) in one cooperative launch of G
-// co-resident CTAs.  Tile i is processed by CTA i mod G, each CTA in increasing
-// tile order.  Forward tiles come first (by ascending level), then backward tiles
-// (by descending level).  A forward tile waits until every child of its supernode
-// has finished its forward output blocks; a backward tile waits until its
-// parent (the root: its own forward) has finished its backward output blocks.
-// All awaited tiles have smaller indices; the smallest unfinished tile has no
-// unfinished dependency and its CTA is resident and working on it, so the waits
-// end.  They are also bounded (error flag DEV_ERR_TIMEOUT).  Counters only grow:
-// each CTA takes one arrival ticket per solve, so solve number = ticket / G, and
-// block targets are (solve + 1) * blocks.  While a tile reduces and writes its
-// outputs, the panel values of the CTA's next tile are already loading.
+// Whole solve (forward and backward sweeps) in one launch.  CTAs take tiles in
+// ticket order; a forward tile waits for its supernode's children to finish
+// their forward outputs, a backward tile for its parent's backward outputs (the
+// root for its own forward outputs).  Every awaited tile has an earlier ticket
+// and is held by a running CTA, so the waits end; they are also bounded (error
+// flag DEV_ERR_TIMEOUT).  Counters only grow: a solve consumes ntiles + grid
+// tickets (every CTA draws one ticket past the end), so ticket t belongs to
+// solve t / (ntiles + grid).
 constexpr long long kSpinLimit = 1ll << 20;   // about a second of polling
 
 __device__ __forceinline__ unsigned long long vload(const unsigned long long* p) {
   return *reinterpret_cast<const volatile unsigned long long*>(p);
 }
 
-__device__ __forceinline__ void wait_count(const unsigned long long* c, unsigned long long target, int* err) {
+__device__ __forceinline__ bool wait_count(const unsigned long long* c, unsigned long long target, int* err) {
   long long it = 0;
   while (vload(c) < target) {
     if (++it > kSpinLimit) {
       atomicOr(err, DEV_ERR_TIMEOUT);
-      return;
+      return false;
     }
-    __nanosleep(32);
+    __nanosleep(64);
   }
+  return true;
 }
 
 template <typename T>
@@ -113,79 +110,31 @@ struct __align__(16) PersistSmem {
   int flag;
 };
 
-constexpr int kQ = 32;   // panel values per thread and tile (both tile kinds)
-
-// panel values of a tile into registers (independent of every dependency)
 template <typename T>
-__device__ __forceinline__ void load_panel(const SolveParams& p, const SolveTile& tl, T (&q)[kQ]) {
-  const T* Q = reinterpret_cast<const T*>(p.Q) + tl.panel_off;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int64_t nc = tl.nc, nr = tl.nr;
-  if (tl.pad0 == 0) {
-    // forward: warp w -> columns b + 16w .. +16; lanes -> rows a + lane, a + 32 + lane
-    const int64_t col0 = tl.b, cn = min((int64_t)kFC, nc - col0);
-    const int64_t ra = tl.a + lane, rb = tl.a + 32 + lane;
-#pragma unroll
-    for (int k = 0; k < 16; ++k) {
-      const int64_t j = col0 + warp * 16 + k;
-      const bool jv = (warp * 16 + k) < cn;
-      // L11^-1 is lower triangular: rows < nc only use columns <= row
-      q[k] = (jv && ra < nr && (ra >= nc || j <= ra)) ? __ldg(Q + ra + j * nr) : T(0);
-      q[16 + k] = (jv && rb < nr && (rb >= nc || j <= rb)) ? __ldg(Q + rb + j * nr) : T(0);
-    }
-  } else {
-    // backward: warp w -> columns a + 4w .. +4; lanes -> rows b + lane + 32k
-    constexpr int kPerWarp = kBC / (kThreads / 32);
-#pragma unroll
-    for (int c = 0; c < kPerWarp; ++c) {
-      const int64_t j = tl.a + warp * kPerWarp + c;
-#pragma unroll
-      for (int k = 0; k < 8; ++k) {
-        const int64_t r = tl.b + lane + 32 * k;
-        // column j of L11^-1 is zero above row j
-        q[c * 8 + k] = (j < nc && r < nr && (r >= nc || r >= j)) ? __ldg(Q + r + j * nr) : T(0);
-      }
-    }
-  }
-}
-
-// last of the tiles of an output block?  (their partial sums are complete then)
-__device__ __forceinline__ bool last_of_block(const SolveParams& p, const SolveTile& tl, PersistSmem& sm) {
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    __threadfence();
-    const unsigned long long v = atomicAdd(p.otick + tl.out, 1ull);
-    const bool last = ((v + 1) % (unsigned long long)tl.ntile) == 0;
-    if (last) __threadfence();
-    sm.flag = last;
-  }
-  __syncthreads();
-  return sm.flag != 0;
-}
-
-__device__ __forceinline__ void signal_done(unsigned long long* c) {
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    __threadfence();
-    atomicAdd(c, 1ull);
-  }
-}
-
-template <typename T>
-__device__ void fwd_tile(const SolveParams& p, const SolveTile& tl, int64_t tid_g, unsigned long long epoch,
-                         PersistSmem& sm, T (&q)[kQ], const SolveTile* next) {
+__device__ void fwd_tile_body(const SolveParams& p, const SolveTile& tl, int64_t tid_g,
+                              unsigned long long epoch, PersistSmem& sm) {
   T (*rhs)[3] = reinterpret_cast<T (*)[3]>(sm.rhs_d);
   T (*red)[kFR][3] = reinterpret_cast<T (*)[kFR][3]>(sm.red_d);
   const int64_t row0 = tl.a, col0 = tl.b;
   const int64_t first = tl.first, nc = tl.nc, nr = tl.nr, pos = tl.pos;
+  const T* Q = reinterpret_cast<const T*>(p.Q) + tl.panel_off;
   const T* W = reinterpret_cast<const T*>(p.W);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int64_t cn = min((int64_t)kFC, nc - col0);
+  const int64_t ra = row0 + lane, rb = row0 + 32 + lane;
+  T qa[16], qb[16];
+#pragma unroll
+  for (int k = 0; k < 16; ++k) {
+    const int64_t j = col0 + warp * 16 + k;
+    const bool jv = (warp * 16 + k) < cn;
+    qa[k] = (jv && ra < nr && (ra >= nc || j <= ra)) ? __ldg(Q + ra + j * nr) : T(0);
+    qb[k] = (jv && rb < nr && (rb >= nc || j <= rb)) ? __ldg(Q + rb + j * nr) : T(0);
+  }
   // the children's update rows must be final
   if (threadIdx.x == 0) {
-    for (int64_t ci = __ldg(p.child_ptr + tl.s); ci < __ldg(p.child_ptr + tl.s + 1); ++ci) {
-      const int64_t c = __ldg(p.child_list + ci);
-      wait_count(p.fdone + c, (epoch + 1) * (unsigned long long)__ldg(p.nfb + c), p.err);
+    for (int64_t ci = p.child_ptr[tl.s]; ci < p.child_ptr[tl.s + 1]; ++ci) {
+      const int64_t c = p.child_list[ci];
+      wait_count(p.fdone + c, (epoch + 1) * (unsigned long long)p.nfb[c], p.err);
     }
     __threadfence();
   }
@@ -209,11 +158,10 @@ __device__ void fwd_tile(const SolveParams& p, const SolveTile& tl, int64_t tid_
     const int jj = warp * 16 + k;
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
-      a0[i] += q[k] * rhs[jj][i];
-      a1[i] += q[16 + k] * rhs[jj][i];
+      a0[i] += qa[k] * rhs[jj][i];
+      a1[i] += qb[k] * rhs[jj][i];
     }
   }
-  if (next) load_panel<T>(p, *next, q);   // in flight during the reduction below
 #pragma unroll
   for (int i = 0; i < 3; ++i) {
     red[warp][lane][i] = a0[i];
@@ -231,7 +179,16 @@ __device__ void fwd_tile(const SolveParams& p, const SolveTile& tl, int64_t tid_
     else part[idx] = t;
   }
   if (ntile > 1) {
-    if (!last_of_block(p, tl, sm)) return;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      __threadfence();
+      const unsigned long long v = atomicAdd(p.otick + tl.out, 1ull);
+      sm.flag = ((v + 1) % (unsigned long long)ntile) == 0;
+    }
+    __syncthreads();
+    if (!sm.flag) return;
+    __threadfence();
     const T* parts = reinterpret_cast<const T*>(p.partial) + tl.part_base * (kFR * 3);
     for (int idx = threadIdx.x; idx < kFR * 3; idx += kThreads) {
       T t = T(0);
@@ -253,25 +210,38 @@ __device__ void fwd_tile(const SolveParams& p, const SolveTile& tl, int64_t tid_
       Wo[0] = (T)v0; Wo[1] = (T)v1; Wo[2] = (T)v2;
     }
   }
-  signal_done(p.fdone + tl.s);
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) atomicAdd(p.fdone + tl.s, 1ull);
 }
 
 template <typename T>
-__device__ void bwd_tile(const SolveParams& p, const SolveTile& tl, int64_t tid_g, unsigned long long epoch,
-                         PersistSmem& sm, T (&q)[kQ], const SolveTile* next) {
+__device__ void bwd_tile_body(const SolveParams& p, const SolveTile& tl, int64_t tid_g,
+                              unsigned long long epoch, PersistSmem& sm) {
   T (*v)[3] = reinterpret_cast<T (*)[3]>(sm.v_d);
   T (*res)[3] = reinterpret_cast<T (*)[3]>(sm.res_d);
   const int64_t col0 = tl.a, row0 = tl.b;
   const int64_t first = tl.first, nc = tl.nc, nr = tl.nr;
   const int32_t* srows = p.rows + tl.pos;
+  const T* Q = reinterpret_cast<const T*>(p.Q) + tl.panel_off;
   const T* u = reinterpret_cast<const T*>(p.u);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   constexpr int kPerWarp = kBC / (kThreads / 32);
+  T q[kPerWarp][8];
+#pragma unroll
+  for (int c = 0; c < kPerWarp; ++c) {
+    const int64_t j = col0 + warp * kPerWarp + c;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      const int64_t r = row0 + lane + 32 * k;
+      q[c][k] = (j < nc && r < nr && (r >= nc || r >= j)) ? __ldg(Q + r + j * nr) : T(0);
+    }
+  }
   // the parent's solution (the root: its own forward outputs) must be final
   if (threadIdx.x == 0) {
-    const int64_t par = __ldg(p.parent + tl.s);
-    if (par >= 0) wait_count(p.bdone + par, (epoch + 1) * (unsigned long long)__ldg(p.nbb + par), p.err);
-    else wait_count(p.fdone + tl.s, (epoch + 1) * (unsigned long long)__ldg(p.nfb + tl.s), p.err);
+    const int64_t par = p.parent[tl.s];
+    if (par >= 0) wait_count(p.bdone + par, (epoch + 1) * (unsigned long long)p.nbb[par], p.err);
+    else wait_count(p.fdone + tl.s, (epoch + 1) * (unsigned long long)p.nfb[tl.s], p.err);
     __threadfence();
   }
   __syncthreads();
@@ -290,22 +260,17 @@ __device__ void bwd_tile(const SolveParams& p, const SolveTile& tl, int64_t tid_
     v[rr][0] = v0; v[rr][1] = v1; v[rr][2] = v2;
   }
   __syncthreads();
-  T acc[kPerWarp][3];
-#pragma unroll
-  for (int c = 0; c < kPerWarp; ++c) {
-    acc[c][0] = acc[c][1] = acc[c][2] = T(0);
-#pragma unroll
-    for (int k = 0; k < 8; ++k)
-#pragma unroll
-      for (int i = 0; i < 3; ++i) acc[c][i] += q[c * 8 + k] * v[lane + 32 * k][i];
-  }
-  if (next) load_panel<T>(p, *next, q);   // in flight during the reductions below
 #pragma unroll
   for (int c = 0; c < kPerWarp; ++c) {
     const int jl = warp * kPerWarp + c;
+    T acc[3] = {T(0), T(0), T(0)};
+#pragma unroll
+    for (int k = 0; k < 8; ++k)
+#pragma unroll
+      for (int i = 0; i < 3; ++i) acc[i] += q[c][k] * v[lane + 32 * k][i];
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
-      T t = acc[c][i];
+      T t = acc[i];
 #pragma unroll
       for (int off = 16; off >= 1; off >>= 1) t += __shfl_xor_sync(0xffffffffu, t, off);
       if (lane == 0) res[jl][i] = t;
@@ -316,7 +281,16 @@ __device__ void bwd_tile(const SolveParams& p, const SolveTile& tl, int64_t tid_
   if (ntile > 1) {
     T* part = reinterpret_cast<T*>(p.partial) + tid_g * (kFR * 3);
     for (int idx = threadIdx.x; idx < kBC * 3; idx += kThreads) part[idx] = res[idx / 3][idx % 3];
-    if (!last_of_block(p, tl, sm)) return;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      __threadfence();
+      const unsigned long long vv = atomicAdd(p.otick + tl.out, 1ull);
+      sm.flag = ((vv + 1) % (unsigned long long)ntile) == 0;
+    }
+    __syncthreads();
+    if (!sm.flag) return;
+    __threadfence();
     const T* parts = reinterpret_cast<const T*>(p.partial) + tl.part_base * (kFR * 3);
     for (int idx = threadIdx.x; idx < kBC * 3; idx += kThreads) {
       T t = T(0);
@@ -332,35 +306,28 @@ __device__ void bwd_tile(const SolveParams& p, const SolveTile& tl, int64_t tid_
     p.x[3 * (first + j) + 1] = (double)res[jl][1];
     p.x[3 * (first + j) + 2] = (double)res[jl][2];
   }
-  signal_done(p.bdone + tl.s);
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) atomicAdd(p.bdone + tl.s, 1ull);
 }
 
 template <typename T>
 __global__ void __launch_bounds__(kThreads) solve_persistent_kernel(SolveParams p) {
   if (p.gate && (p.gate->converged || !p.gate->accepted)) return;
   __shared__ PersistSmem sm;
-  __shared__ unsigned long long arrival;
-  if (threadIdx.x == 0) arrival = atomicAdd(p.gticket, 1ull);
-  __syncthreads();
-  const unsigned long long epoch = arrival / gridDim.x;
-  int64_t i = blockIdx.x;
-  if (i >= p.ntiles) return;
-  SolveTile tl = load_tile(p.tiles, i);
-  T q[kQ];
-  load_panel<T>(p, tl, q);
+  __shared__ unsigned long long tk;
+  const unsigned long long per = (unsigned long long)p.ntiles + gridDim.x;
   while (true) {
-    const int64_t nx = i + gridDim.x;
-    const bool has_next = nx < p.ntiles;
-    SolveTile tn;
-    if (has_next) tn = load_tile(p.tiles, nx);
-    if (tl.pad0 == 0) fwd_tile<T>(p, tl, i, epoch, sm, q, has_next ? &tn : nullptr);
-    else bwd_tile<T>(p, tl, i, epoch, sm, q, has_next ? &tn : nullptr);
-    if (!has_next) return;
-    // (a CTA that was not last of its output block returned early: it still
-    // loaded the next panel values before its reduction)
-    __syncthreads();   // shared memory of this tile is no longer in use
-    i = nx;
-    tl = tn;
+    __syncthreads();   // shared memory of the previous tile is no longer in use
+    if (threadIdx.x == 0) tk = atomicAdd(p.gticket, 1ull);
+    __syncthreads();
+    const unsigned long long t = tk;
+    const unsigned long long epoch = t / per;
+    const int64_t tile = (int64_t)(t % per);
+    if (tile >= p.ntiles) return;
+    const SolveTile tl = load_tile(p.tiles, tile);
+    if (tl.pad0 == 0) fwd_tile_body<T>(p, tl, tile, epoch, sm);
+    else bwd_tile_body<T>(p, tl, tile, epoch, sm);
   }
 }
 
@@ -494,12 +461,8 @@ cudaError_t solve_A(const MeshImpl* m, const IterState* gate, const double* b, d
   p.parent = m->parent;
   p.err = m->ws.flags;
   const unsigned grid = (unsigned)std::min<int64_t>(m->solve_grid, ntiles);
-  void* args[] = {(void*)&p};
-  // cooperative launch: all CTAs co-resident (required by the in-order waits)
-  if (f32) return cudaLaunchCooperativeKernel((const void*)solve_persistent_kernel<float>, dim3(grid),
-                                              dim3(kThreads), args, 0, st);
-  return cudaLaunchCooperativeKernel((const void*)solve_persistent_kernel<double>, dim3(grid), dim3(kThreads),
-                                     args, 0, st);
+  if (f32) solve_persistent_kernel<float><<<grid, kThreads, 0, st>>>(p);
+  else solve_persistent_kernel<double><<<grid, kThreads, 0, st>>>(p);
   return cudaGetLastError();
 }
 
