@@ -198,6 +198,34 @@ pd_status pd_hessian_vector(pd_mesh m, const double* x, const double* act, const
  * rows of x are set to zero) with the prefactorised supernodal factor. */
 pd_status pd_solve_A(pd_mesh m, const double* b, double* x, int32_t precision, void* stream);
 
+/* Local step that allocates no device memory (the paper has no counterpart).
+ * For callers that cannot call cudaMalloc -- e.g. while a CUDA graph is being
+ * captured, under a device-memory budget fixed in advance, or behind an allocator
+ * the library cannot reach -- this variant of pd_local_step takes every array
+ * from the caller and keeps its scratch (corner forces, partial sums, a status
+ * word) in one fixed-size device array owned by the library; every GPU that
+ * loads the library holds that array (6.3 MB) until the process exits.
+ * Computes grad_E (n_nodes, 3) and energy (1 scalar, may be NULL) exactly as
+ * pd_local_step, on the current device and `stream`, for at most
+ * PD_NOALLOC_MAX_CELLS cells and 8 x PD_NOALLOC_MAX_CELLS nodes (larger meshes
+ * return PD_ERR_INVALID_ARG).  Inputs (device): elems (n_elems, 8) node ids with
+ * corner a = 4 di + 2 dj + dk of a cube of edge dx; inc_ptr (n_nodes + 1) and inc
+ * (8 n_elems, entries e*8+a) the node -> corner incidence (pd_mesh_export gives
+ * it for a pd_mesh); x (n_nodes, 3); act (n_elems) or NULL; w_* (n_elems) per
+ * unit volume as in pd_factorize; fiber (n_elems, 3) with w_muscle; contact
+ * (n_nodes) uint8 or NULL with penalty k_contact.  The first call on a device
+ * looks up the scratch address there: make it before any stream capture.
+ * Calls share the scratch: calls that overlap on the GPU race (keep them on one
+ * stream).  The scratch keeps the last call's contents; each call clears what
+ * must start at zero. */
+#define PD_NOALLOC_MAX_CELLS 32768
+pd_status pd_local_step_noalloc(int64_t n_nodes, int64_t n_elems, const int32_t* elems,
+                                const int32_t* inc_ptr, const int32_t* inc, double dx,
+                                const double* x, const double* act, const double* w_corot,
+                                const double* w_vol, const double* w_muscle, const double* fiber,
+                                const uint8_t* contact, double k_contact, int32_t precision,
+                                double* grad_E, double* energy, void* stream);
+
 /* Continuous-batching server (rollout-plus-gradient requests). */
 typedef struct pd_server_s* pd_server;
 

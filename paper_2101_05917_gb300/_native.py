@@ -99,8 +99,8 @@ class Result(ctypes.Structure):
 
 SYMBOLS = ["pd_create_mesh", "pd_mesh_destroy", "pd_mesh_query", "pd_mesh_export", "pd_factorize",
            "pd_forward", "pd_backward", "pd_local_step", "pd_hessian_vector", "pd_solve_A",
-           "pd_serve_create", "pd_serve_submit", "pd_serve_poll", "pd_serve_drain", "pd_serve_destroy",
-           "pd_last_error"]
+           "pd_local_step_noalloc", "pd_serve_create", "pd_serve_submit", "pd_serve_poll", "pd_serve_drain",
+           "pd_serve_destroy", "pd_last_error"]
 
 _lib = None
 
@@ -138,6 +138,9 @@ def lib() -> ctypes.CDLL:
     L.pd_hessian_vector.restype = st
     L.pd_solve_A.argtypes = [vp, vp, vp, ctypes.c_int32, vp]
     L.pd_solve_A.restype = st
+    L.pd_local_step_noalloc.argtypes = [ctypes.c_int64, ctypes.c_int64, vp, vp, vp, ctypes.c_double, vp, vp, vp,
+                                        vp, vp, vp, vp, ctypes.c_double, ctypes.c_int32, vp, vp, vp]
+    L.pd_local_step_noalloc.restype = st
     L.pd_serve_create.argtypes = [ctypes.c_int32, ctypes.c_size_t, ctypes.c_int32, ctypes.POINTER(vp)]
     L.pd_serve_create.restype = st
     L.pd_serve_submit.argtypes = [vp, ctypes.POINTER(Request), ctypes.POINTER(ctypes.c_uint64)]

@@ -488,3 +488,34 @@ cudaError_t launch_gather_hvp(const MeshImpl* m, const IterState* gate, const vo
 }
 
 }  // namespace pd
+
+namespace pd {
+
+// Force-mode local step on caller-provided topology and weights (no mesh object).
+cudaError_t launch_element_forces_raw(int64_t ne, const int32_t* elems, const double* x, const double* act,
+                                      const double* wc, const double* wv, const double* wm, const double* fiber,
+                                      double dx, int precision, void* elembuf, double* energy_partials,
+                                      int* flags, cudaStream_t s) {
+  ElemParams p{};
+  p.ne = ne;
+  p.elems = elems;
+  p.x = x;
+  p.act = act;
+  p.wc = wc;
+  p.wv = wv;
+  p.wm = wm;
+  p.fiber = fiber;
+  p.dx = dx;
+  p.Vq = dx * dx * dx / 8.0;
+  p.out = elembuf;
+  p.energy = energy_partials;
+  p.flags = flags;
+  const int nb = (int)((ne * 8 + kElemThreads - 1) / kElemThreads);
+  if (precision == PD_PREC_MIXED)
+    element_kernel<float, MODE_FORCE><<<nb, kElemThreads, 0, s>>>(p);
+  else
+    element_kernel<double, MODE_FORCE><<<nb, kElemThreads, 0, s>>>(p);
+  return cudaGetLastError();
+}
+
+}  // namespace pd

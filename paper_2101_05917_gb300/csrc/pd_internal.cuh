@@ -161,6 +161,10 @@ cudaError_t launch_gather_hvp(const MeshImpl* m, const IterState* gate, const vo
                               int precision, const double* x, const double* v, const double* gs,
                               double* Hv, double* partials, cudaStream_t s);
 int gather_blocks(const MeshImpl* m);
+cudaError_t launch_element_forces_raw(int64_t ne, const int32_t* elems, const double* x, const double* act,
+                                      const double* wc, const double* wv, const double* wm, const double* fiber,
+                                      double dx, int precision, void* elembuf, double* energy_partials,
+                                      int* flags, cudaStream_t s);
 
 // Factorisation (kernels_factor.cu)
 pd_status factorize_device(MeshImpl* m, cudaStream_t s);
