@@ -137,6 +137,9 @@ typedef struct {
                                    test is confirmed by an FP64 residual */
   int32_t profile;              /* nonzero: time the solve and local-step launches with CUDA
                                    events on the launching stream (pd_stats.*_ms) */
+  int32_t warm_start;           /* nonzero: keep the L-BFGS pairs from one time step to the
+                                   next and start each adjoint solve from the previous
+                                   step's z (fixed points unchanged) */
 } pd_solver_opts;
 
 typedef struct {

@@ -61,7 +61,7 @@ class SolverOpts(ctypes.Structure):
                 ("max_iter_fwd", ctypes.c_int32), ("max_iter_bwd", ctypes.c_int32),
                 ("lbfgs_m", ctypes.c_int32), ("ls_max", ctypes.c_int32),
                 ("checkpoint_every", ctypes.c_int32), ("check_every", ctypes.c_int32),
-                ("profile", ctypes.c_int32)]
+                ("profile", ctypes.c_int32), ("warm_start", ctypes.c_int32)]
 
 
 class Stats(ctypes.Structure):

@@ -43,9 +43,9 @@ def _u8(a, n, name):
 
 
 def solver_opts(tol_fwd=1e-9, tol_bwd=1e-9, max_iter_fwd=500, max_iter_bwd=500, lbfgs_m=5, ls_max=10,
-                checkpoint_every=0, check_every=4, profile=False) -> N.SolverOpts:
+                checkpoint_every=0, check_every=4, profile=False, warm_start=False) -> N.SolverOpts:
     return N.SolverOpts(tol_fwd, tol_bwd, max_iter_fwd, max_iter_bwd, lbfgs_m, ls_max, checkpoint_every,
-                        check_every, 1 if profile else 0)
+                        check_every, 1 if profile else 0, 1 if warm_start else 0)
 
 
 @dataclass

@@ -167,6 +167,8 @@ struct EventTimer {
 struct Ctx {
   MeshImpl* m;
   int64_t launches = 0, solves = 0, locals = 0;
+  int64_t bwd_steps = 0;
+  int last_kind = -1;   // 0 forward, 1 backward: L-BFGS pairs carry over within a kind
   EventTimer* solve_t = nullptr;
   int dev_flags = 0;
   EventTimer* local_t = nullptr;
@@ -275,7 +277,8 @@ pd_status forward_step(Ctx& c, const double* act_t, const double* fext_int, doub
   MeshImpl* m = c.m;
   Workspace& w = m->ws;
   StateCfg cfg{c.o.tol_fwd, m->precision == PD_PREC_MIXED ? 1e-6 : 1e-12, c.o.lbfgs_m, c.o.ls_max,
-               c.o.max_iter_fwd, 0};
+               c.o.max_iter_fwd, 0, (c.o.warm_start && c.last_kind == 0) ? 1 : 0};
+  c.last_kind = 0;
   state_reset_kernel<<<1, 1, 0, c.s>>>(w.st, cfg);
   PredParams pp{};
   pp.n = c.n;
@@ -420,10 +423,23 @@ pd_status backward_step(Ctx& c, const double* xnext, const double* xt_, const do
   MeshImpl* m = c.m;
   Workspace& w = m->ws;
   const double inv_h = 1.0 / m->h_step;
-  StateCfg cfg{c.o.tol_bwd, 0.0, c.o.lbfgs_m, c.o.ls_max, c.o.max_iter_bwd, 1};
+  const bool warm = c.o.warm_start && c.bwd_steps > 0;   // w.z holds the previous adjoint
+  StateCfg cfg{c.o.tol_bwd, 0.0, c.o.lbfgs_m, c.o.ls_max, c.o.max_iter_bwd, 1,
+               (c.o.warm_start && c.last_kind == 1) ? 1 : 0};
+  c.bwd_steps += 1;
+  c.last_kind = 1;
   state_reset_kernel<<<1, 1, 0, c.s>>>(w.st, cfg);
-  bwd_step_init_kernel<<<c.vb, 256, 0, c.s>>>(c.vc, w.ax, w.av, inv_h, w.z, w.gs, w.q);
+  bwd_step_init_kernel<<<c.vb, 256, 0, c.s>>>(c.vc, w.ax, w.av, inv_h, w.z, w.gs, w.q, warm ? 1 : 0);
   c.launches += 2;
+  if (warm) {
+    // start from the previous step's adjoint: gs = H z - gbar at that z
+    const int p0 = m->precision == PD_PREC_MIXED ? PD_PREC_MIXED : PD_PREC_FP64;
+    LocalArgs la0{m, nullptr, xnext, w.z, act_t, p0};
+    PD_CUDA_TRY(launch_element_hvp(la0, w.elembuf, w.flags, c.s));
+    PD_CUDA_TRY(launch_gather_hvp(m, nullptr, w.elembuf, p0, xnext, w.z, nullptr, w.Hd, c.pg, c.s));
+    residual_replace_kernel<<<c.vb, 256, 0, c.s>>>(c.vc, w.Hd, w.ax, w.av, inv_h, w.gs, w.q);
+    c.launches += 3;
+  }
   // Hessian products in the factor's precision; at convergence of the recursively
   // updated residual, the true residual H z - gbar is evaluated with an FP64
   // product and replaces it (iterative refinement); the iteration continues

@@ -18,6 +18,7 @@ namespace pd {
 struct StateCfg {
   double tol, noise;
   int m, ls_max, max_iter, accepted;
+  int keep_history;   // keep the L-BFGS pairs of the previous solve
 };
 
 struct VecCtx {
@@ -123,9 +124,11 @@ __global__ void state_reset_kernel(IterState* st, StateCfg cfg) {
   st->tol2 = cfg.tol * cfg.tol;
   st->c1 = 1e-4;
   st->noise = cfg.noise;
+  if (!cfg.keep_history || st->m != cfg.m) {
+    st->head = 0;
+    st->count = 0;
+  }
   st->m = cfg.m;
-  st->head = 0;
-  st->count = 0;
   st->pslot = 0;
   st->push = 0;
   st->iters = 0;
@@ -456,11 +459,11 @@ __global__ void finalize_fwd_kernel(int64_t n, const double* x, double* xi, doub
 // ---------------------------------------------------------------- backward
 // gbar = ax + av/h, z = 0, gs = grad s(0) = -gbar, q = gs; ref2 = |gbar|^2
 __global__ void bwd_step_init_kernel(VecCtx c, const double* ax, const double* av, double inv_h,
-                                     double* z, double* gs, double* q) {
+                                     double* z, double* gs, double* q, int keep_z) {
   double part = 0;
   for (int64_t i = (int64_t)blockIdx.x * kT + threadIdx.x; i < c.n3; i += (int64_t)gridDim.x * kT) {
     const double gb = ax[i] + av[i] * inv_h;
-    z[i] = 0.0;
+    if (!keep_z) z[i] = 0.0;
     gs[i] = -gb;
     q[i] = -gb;
     part += gb * gb;
