@@ -26,10 +26,11 @@ namespace pd {
 namespace {
 
 constexpr int kThreads = 256;
-constexpr int kFR = 64;     // forward tile rows
-constexpr int kFC = 128;    // forward tile columns (8 warps x 16)
-constexpr int kBR = 256;    // backward tile rows (32 lanes x 8)
+constexpr int kFR = 256;    // forward tile rows (one thread per row)
+constexpr int kFC = 256;    // forward tile columns
+constexpr int kBR = 1024;   // backward tile rows (32 lanes x 32)
 constexpr int kBC = 32;     // backward tile columns (8 warps x 4)
+constexpr int kPart = kFR * 3;   // partial-sum slots per tile
 
 struct SolveParams {
   const IterState* gate;
@@ -103,38 +104,60 @@ __device__ __forceinline__ void gather_W_cg(const SolveParams& p, const T* W, in
 }
 
 struct __align__(16) PersistSmem {
-  double rhs_d[kFC][3];
-  double red_d[kThreads / 32][kFR][3];
-  double v_d[kBR][3];
+  double rhs_d[kFC][3];   // forward: right-hand side of the tile's columns
+  double v_d[kBR][3];     // backward: [u_s; -x(below rows)] of the tile's rows
   double res_d[kBC][3];
   int flag;
 };
 
+// last of the tiles of an output block?  (then the partial sums are complete)
+__device__ __forceinline__ bool last_of_block(const SolveParams& p, const SolveTile& tl, PersistSmem& sm) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    const unsigned long long v = atomicAdd(p.otick + tl.out, 1ull);
+    const bool last = ((v + 1) % (unsigned long long)tl.ntile) == 0;
+    if (last) __threadfence();
+    sm.flag = last;
+  }
+  __syncthreads();
+  return sm.flag != 0;
+}
+
+__device__ __forceinline__ void signal_done(unsigned long long* c) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    atomicAdd(c, 1ull);
+  }
+}
+
+// Forward tile: rows [a, a + kFR) x columns [b, b + kFC) of panel s; thread t
+// owns row a + t and accumulates its whole dot product over the tile's columns
+// (coalesced: consecutive threads read consecutive rows of one column).
 template <typename T>
-__device__ void fwd_tile_body(const SolveParams& p, const SolveTile& tl, int64_t tid_g,
-                              unsigned long long epoch, PersistSmem& sm) {
+__device__ void fwd_tile_body(const SolveParams& p, const SolveTile& tl, int64_t tid_g, unsigned long long epoch,
+                              PersistSmem& sm) {
   T (*rhs)[3] = reinterpret_cast<T (*)[3]>(sm.rhs_d);
-  T (*red)[kFR][3] = reinterpret_cast<T (*)[kFR][3]>(sm.red_d);
   const int64_t row0 = tl.a, col0 = tl.b;
   const int64_t first = tl.first, nc = tl.nc, nr = tl.nr, pos = tl.pos;
   const T* Q = reinterpret_cast<const T*>(p.Q) + tl.panel_off;
   const T* W = reinterpret_cast<const T*>(p.W);
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int64_t cn = min((int64_t)kFC, nc - col0);
-  const int64_t ra = row0 + lane, rb = row0 + 32 + lane;
-  T qa[16], qb[16];
+  const int64_t r = row0 + threadIdx.x;
+  const bool valid = r < nr;
+  // L11^-1 is lower triangular: rows < nc use columns <= row only
+  const int64_t jend = !valid ? 0 : (r < nc ? min(cn, r - col0 + 1) : cn);
+  const T* Qr = Q + r + col0 * nr;
+  // the first panel values load while the dependencies are awaited
+  constexpr int kPre = 16;
+  T pre[kPre];
 #pragma unroll
-  for (int k = 0; k < 16; ++k) {
-    const int64_t j = col0 + warp * 16 + k;
-    const bool jv = (warp * 16 + k) < cn;
-    qa[k] = (jv && ra < nr && (ra >= nc || j <= ra)) ? __ldg(Q + ra + j * nr) : T(0);
-    qb[k] = (jv && rb < nr && (rb >= nc || j <= rb)) ? __ldg(Q + rb + j * nr) : T(0);
-  }
-  // the children's update rows must be final
+  for (int k = 0; k < kPre; ++k) pre[k] = (k < jend) ? __ldg(Qr + (int64_t)k * nr) : T(0);
   if (threadIdx.x == 0) {
-    for (int64_t ci = p.child_ptr[tl.s]; ci < p.child_ptr[tl.s + 1]; ++ci) {
-      const int64_t c = p.child_list[ci];
-      wait_count(p.fdone + c, (epoch + 1) * (unsigned long long)p.nfb[c], p.err);
+    for (int64_t ci = __ldg(p.child_ptr + tl.s); ci < __ldg(p.child_ptr + tl.s + 1); ++ci) {
+      const int64_t c = __ldg(p.child_list + ci);
+      wait_count(p.fdone + c, (epoch + 1) * (unsigned long long)__ldg(p.nfb + c), p.err);
     }
     __threadfence();
   }
@@ -152,72 +175,59 @@ __device__ void fwd_tile_body(const SolveParams& p, const SolveTile& tl, int64_t
     rhs[jj][0] = r0; rhs[jj][1] = r1; rhs[jj][2] = r2;
   }
   __syncthreads();
-  T a0[3] = {T(0), T(0), T(0)}, a1[3] = {T(0), T(0), T(0)};
+  T a0 = T(0), a1 = T(0), a2 = T(0);
 #pragma unroll
-  for (int k = 0; k < 16; ++k) {
-    const int jj = warp * 16 + k;
+  for (int k = 0; k < kPre; ++k) {
+    a0 += pre[k] * rhs[k][0];
+    a1 += pre[k] * rhs[k][1];
+    a2 += pre[k] * rhs[k][2];
+  }
+  for (int64_t j = kPre; j < jend; j += 16) {
+    T q[16];
 #pragma unroll
-    for (int i = 0; i < 3; ++i) {
-      a0[i] += qa[k] * rhs[jj][i];
-      a1[i] += qb[k] * rhs[jj][i];
+    for (int k = 0; k < 16; ++k) q[k] = (j + k < jend) ? __ldg(Qr + (j + k) * nr) : T(0);
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {
+      const int64_t jj = min(j + k, (int64_t)kFC - 1);
+      a0 += q[k] * rhs[jj][0];
+      a1 += q[k] * rhs[jj][1];
+      a2 += q[k] * rhs[jj][2];
     }
   }
-#pragma unroll
-  for (int i = 0; i < 3; ++i) {
-    red[warp][lane][i] = a0[i];
-    red[warp][lane + 32][i] = a1[i];
-  }
-  __syncthreads();
   const int ntile = tl.ntile;
-  T* part = reinterpret_cast<T*>(p.partial) + tid_g * (kFR * 3);
-  for (int idx = threadIdx.x; idx < kFR * 3; idx += kThreads) {
-    const int r = idx / 3, i = idx % 3;
-    T t = T(0);
-#pragma unroll
-    for (int w = 0; w < kThreads / 32; ++w) t += red[w][r][i];
-    if (ntile == 1) red[0][r][i] = t;
-    else part[idx] = t;
-  }
   if (ntile > 1) {
-    __threadfence();
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      __threadfence();
-      const unsigned long long v = atomicAdd(p.otick + tl.out, 1ull);
-      sm.flag = ((v + 1) % (unsigned long long)ntile) == 0;
-    }
-    __syncthreads();
-    if (!sm.flag) return;
-    __threadfence();
-    const T* parts = reinterpret_cast<const T*>(p.partial) + tl.part_base * (kFR * 3);
-    for (int idx = threadIdx.x; idx < kFR * 3; idx += kThreads) {
-      T t = T(0);
-      for (int k = 0; k < ntile; ++k) t += __ldcg(parts + (int64_t)k * (kFR * 3) + idx);
-      red[0][idx / 3][idx % 3] = t;
+    T* part = reinterpret_cast<T*>(p.partial) + tid_g * kPart;
+    part[3 * threadIdx.x] = a0;
+    part[3 * threadIdx.x + 1] = a1;
+    part[3 * threadIdx.x + 2] = a2;
+    if (!last_of_block(p, tl, sm)) return;
+    const T* parts = reinterpret_cast<const T*>(p.partial) + tl.part_base * kPart;
+    a0 = a1 = a2 = T(0);
+    for (int k = 0; k < ntile; ++k) {
+      a0 += __ldcg(parts + (int64_t)k * kPart + 3 * threadIdx.x);
+      a1 += __ldcg(parts + (int64_t)k * kPart + 3 * threadIdx.x + 1);
+      a2 += __ldcg(parts + (int64_t)k * kPart + 3 * threadIdx.x + 2);
     }
   }
-  __syncthreads();
-  for (int r = threadIdx.x; r < kFR; r += kThreads) {
-    const int64_t row = row0 + r;
-    if (row >= nr) continue;
-    if (row < nc) {
-      T* uo = reinterpret_cast<T*>(p.u) + 3 * (first + row);
-      uo[0] = red[0][r][0]; uo[1] = red[0][r][1]; uo[2] = red[0][r][2];
+  if (valid) {
+    if (r < nc) {
+      T* uo = reinterpret_cast<T*>(p.u) + 3 * (first + r);
+      uo[0] = a0; uo[1] = a1; uo[2] = a2;
     } else {
-      double v0 = (double)red[0][r][0], v1 = (double)red[0][r][1], v2 = (double)red[0][r][2];
-      gather_W_cg<T>(p, W, pos + row, v0, v1, v2);
-      T* Wo = reinterpret_cast<T*>(p.W) + 3 * (tl.relp + (row - nc));
+      double v0 = (double)a0, v1 = (double)a1, v2 = (double)a2;
+      gather_W_cg<T>(p, W, pos + r, v0, v1, v2);
+      T* Wo = reinterpret_cast<T*>(p.W) + 3 * (tl.relp + (r - nc));
       Wo[0] = (T)v0; Wo[1] = (T)v1; Wo[2] = (T)v2;
     }
   }
-  __threadfence();
-  __syncthreads();
-  if (threadIdx.x == 0) atomicAdd(p.fdone + tl.s, 1ull);
+  signal_done(p.fdone + tl.s);
 }
 
+// Backward tile: columns [a, a + kBC) x rows [b, b + kBR) of panel s; warp w owns
+// 4 columns, lanes stride the rows of a column (contiguous, coalesced).
 template <typename T>
-__device__ void bwd_tile_body(const SolveParams& p, const SolveTile& tl, int64_t tid_g,
-                              unsigned long long epoch, PersistSmem& sm) {
+__device__ void bwd_tile_body(const SolveParams& p, const SolveTile& tl, int64_t tid_g, unsigned long long epoch,
+                              PersistSmem& sm) {
   T (*v)[3] = reinterpret_cast<T (*)[3]>(sm.v_d);
   T (*res)[3] = reinterpret_cast<T (*)[3]>(sm.res_d);
   const int64_t col0 = tl.a, row0 = tl.b;
@@ -227,35 +237,31 @@ __device__ void bwd_tile_body(const SolveParams& p, const SolveTile& tl, int64_t
   const T* u = reinterpret_cast<const T*>(p.u);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   constexpr int kPerWarp = kBC / (kThreads / 32);
-  T q[kPerWarp][8];
+  const int64_t rn = min((int64_t)kBR, nr - row0);
+  // first rows of each column load while the dependencies are awaited
+  T pre[kPerWarp];
 #pragma unroll
   for (int c = 0; c < kPerWarp; ++c) {
     const int64_t j = col0 + warp * kPerWarp + c;
-#pragma unroll
-    for (int k = 0; k < 8; ++k) {
-      const int64_t r = row0 + lane + 32 * k;
-      q[c][k] = (j < nc && r < nr && (r >= nc || r >= j)) ? __ldg(Q + r + j * nr) : T(0);
-    }
+    const int64_t rr = row0 + lane;
+    pre[c] = (j < nc && lane < rn && (rr >= nc || rr >= j)) ? __ldg(Q + rr + j * nr) : T(0);
   }
-  // the parent's solution (the root: its own forward outputs) must be final
   if (threadIdx.x == 0) {
-    const int64_t par = p.parent[tl.s];
-    if (par >= 0) wait_count(p.bdone + par, (epoch + 1) * (unsigned long long)p.nbb[par], p.err);
-    else wait_count(p.fdone + tl.s, (epoch + 1) * (unsigned long long)p.nfb[tl.s], p.err);
+    const int64_t par = __ldg(p.parent + tl.s);
+    if (par >= 0) wait_count(p.bdone + par, (epoch + 1) * (unsigned long long)__ldg(p.nbb + par), p.err);
+    else wait_count(p.fdone + tl.s, (epoch + 1) * (unsigned long long)__ldg(p.nfb + tl.s), p.err);
     __threadfence();
   }
   __syncthreads();
-  for (int rr = threadIdx.x; rr < kBR; rr += kThreads) {
+  for (int64_t rr = threadIdx.x; rr < rn; rr += kThreads) {
     const int64_t r = row0 + rr;
-    T v0 = T(0), v1 = T(0), v2 = T(0);
-    if (r < nr) {
-      if (r < nc) {
-        const T* ur = u + 3 * (first + r);
-        v0 = __ldcg(ur); v1 = __ldcg(ur + 1); v2 = __ldcg(ur + 2);
-      } else {
-        const int64_t g = __ldg(srows + r);
-        v0 = (T)(-__ldcg(p.x + 3 * g)); v1 = (T)(-__ldcg(p.x + 3 * g + 1)); v2 = (T)(-__ldcg(p.x + 3 * g + 2));
-      }
+    T v0, v1, v2;
+    if (r < nc) {
+      const T* ur = u + 3 * (first + r);
+      v0 = __ldcg(ur); v1 = __ldcg(ur + 1); v2 = __ldcg(ur + 2);
+    } else {
+      const int64_t g = __ldg(srows + r);
+      v0 = (T)(-__ldcg(p.x + 3 * g)); v1 = (T)(-__ldcg(p.x + 3 * g + 1)); v2 = (T)(-__ldcg(p.x + 3 * g + 2));
     }
     v[rr][0] = v0; v[rr][1] = v1; v[rr][2] = v2;
   }
@@ -263,38 +269,49 @@ __device__ void bwd_tile_body(const SolveParams& p, const SolveTile& tl, int64_t
 #pragma unroll
   for (int c = 0; c < kPerWarp; ++c) {
     const int jl = warp * kPerWarp + c;
-    T acc[3] = {T(0), T(0), T(0)};
+    const int64_t j = col0 + jl;
+    const int64_t l0 = min((int64_t)lane, rn - 1);
+    T a0 = pre[c] * v[l0][0], a1 = pre[c] * v[l0][1], a2 = pre[c] * v[l0][2];
+    if (j < nc) {
+      // column j of L11^-1 is zero above row j
+      const int64_t rs = max((int64_t)32, (j - row0) & ~(int64_t)31);
+      const T* Qj = Q + j * nr + row0;
+      for (int64_t base = rs; base < rn; base += 32 * 8) {
+        T q[8];
 #pragma unroll
-    for (int k = 0; k < 8; ++k)
+        for (int k = 0; k < 8; ++k) {
+          const int64_t rr = base + lane + 32 * k;
+          q[k] = (rr < rn && (row0 + rr >= nc || row0 + rr >= j)) ? __ldg(Qj + rr) : T(0);
+        }
 #pragma unroll
-      for (int i = 0; i < 3; ++i) acc[i] += q[c][k] * v[lane + 32 * k][i];
-#pragma unroll
-    for (int i = 0; i < 3; ++i) {
-      T t = acc[i];
-#pragma unroll
-      for (int off = 16; off >= 1; off >>= 1) t += __shfl_xor_sync(0xffffffffu, t, off);
-      if (lane == 0) res[jl][i] = t;
+        for (int k = 0; k < 8; ++k) {
+          // rows past the tile carry q = 0; read a filled row so no stale value enters
+          const int64_t rr = min(base + lane + 32 * k, rn - 1);
+          a0 += q[k] * v[rr][0];
+          a1 += q[k] * v[rr][1];
+          a2 += q[k] * v[rr][2];
+        }
+      }
     }
+    T t0 = a0, t1 = a1, t2 = a2;
+#pragma unroll
+    for (int off = 16; off >= 1; off >>= 1) {
+      t0 += __shfl_xor_sync(0xffffffffu, t0, off);
+      t1 += __shfl_xor_sync(0xffffffffu, t1, off);
+      t2 += __shfl_xor_sync(0xffffffffu, t2, off);
+    }
+    if (lane == 0) { res[jl][0] = t0; res[jl][1] = t1; res[jl][2] = t2; }
   }
   __syncthreads();
   const int ntile = tl.ntile;
   if (ntile > 1) {
-    T* part = reinterpret_cast<T*>(p.partial) + tid_g * (kFR * 3);
+    T* part = reinterpret_cast<T*>(p.partial) + tid_g * kPart;
     for (int idx = threadIdx.x; idx < kBC * 3; idx += kThreads) part[idx] = res[idx / 3][idx % 3];
-    __threadfence();
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      __threadfence();
-      const unsigned long long vv = atomicAdd(p.otick + tl.out, 1ull);
-      sm.flag = ((vv + 1) % (unsigned long long)ntile) == 0;
-    }
-    __syncthreads();
-    if (!sm.flag) return;
-    __threadfence();
-    const T* parts = reinterpret_cast<const T*>(p.partial) + tl.part_base * (kFR * 3);
+    if (!last_of_block(p, tl, sm)) return;
+    const T* parts = reinterpret_cast<const T*>(p.partial) + tl.part_base * kPart;
     for (int idx = threadIdx.x; idx < kBC * 3; idx += kThreads) {
       T t = T(0);
-      for (int k = 0; k < ntile; ++k) t += __ldcg(parts + (int64_t)k * (kFR * 3) + idx);
+      for (int k = 0; k < ntile; ++k) t += __ldcg(parts + (int64_t)k * kPart + idx);
       res[idx / 3][idx % 3] = t;
     }
     __syncthreads();
@@ -306,28 +323,36 @@ __device__ void bwd_tile_body(const SolveParams& p, const SolveTile& tl, int64_t
     p.x[3 * (first + j) + 1] = (double)res[jl][1];
     p.x[3 * (first + j) + 2] = (double)res[jl][2];
   }
-  __threadfence();
-  __syncthreads();
-  if (threadIdx.x == 0) atomicAdd(p.bdone + tl.s, 1ull);
+  signal_done(p.bdone + tl.s);
 }
 
 template <typename T>
 __global__ void __launch_bounds__(kThreads) solve_persistent_kernel(SolveParams p) {
   if (p.gate && (p.gate->converged || !p.gate->accepted)) return;
   __shared__ PersistSmem sm;
-  __shared__ unsigned long long tk;
+  __shared__ unsigned long long tk[2];
   const unsigned long long per = (unsigned long long)p.ntiles + gridDim.x;
+  if (threadIdx.x == 0) tk[0] = atomicAdd(p.gticket, 1ull);
+  __syncthreads();
+  int slot = 0;
+  unsigned long long t = tk[0];
   while (true) {
-    __syncthreads();   // shared memory of the previous tile is no longer in use
-    if (threadIdx.x == 0) tk = atomicAdd(p.gticket, 1ull);
-    __syncthreads();
-    const unsigned long long t = tk;
-    const unsigned long long epoch = t / per;
     const int64_t tile = (int64_t)(t % per);
     if (tile >= p.ntiles) return;
+    const unsigned long long epoch = t / per;
+    // The next ticket is drawn now, so its latency overlaps this tile.  A CTA
+    // holds at most one drawn-but-unstarted ticket, always above the one it is
+    // working on, so the lowest unfinished ticket is always being worked on and
+    // its dependencies (lower tickets) are done: the schedule cannot deadlock.
+    // The two slots alternate: the slot written here was last read before the
+    // barrier that ended the previous tile.
+    if (threadIdx.x == 0) tk[slot ^ 1] = atomicAdd(p.gticket, 1ull);
     const SolveTile tl = load_tile(p.tiles, tile);
     if (tl.pad0 == 0) fwd_tile_body<T>(p, tl, tile, epoch, sm);
     else bwd_tile_body<T>(p, tl, tile, epoch, sm);
+    __syncthreads();   // shared memory of this tile is free; the drawn ticket is visible
+    slot ^= 1;
+    t = tk[slot];
   }
 }
 
@@ -376,7 +401,7 @@ void build_solve_schedule(const HostMesh& h, SolveSchedule& S) {
       for (int64_t c0 = 0; c0 < nc; c0 += kBC) {
         const int32_t out = (int32_t)S.n_bwd_out++;
         const size_t b0 = S.bwd.size();
-        // column c of L11^-1 is zero above row c
+        // column c of L11^-1 is zero above row c: start at the row block holding c0
         for (int64_t r0 = (c0 / kBR) * kBR; r0 < nr; r0 += kBR) {
           SolveTile t = base(s);
           t.a = (int32_t)c0;
@@ -420,7 +445,7 @@ void build_solve_schedule(const HostMesh& h, SolveSchedule& S) {
 }
 
 size_t solve_partial_bytes(const SolveSchedule& S) {
-  return std::max(S.fwd.size() * kFR * 3, (S.fwd.size() + S.bwd.size()) * kFR * 3) * sizeof(double);
+  return (S.fwd.size() + S.bwd.size()) * (size_t)kPart * sizeof(double);
 }
 
 int solve_persistent_occupancy() {
