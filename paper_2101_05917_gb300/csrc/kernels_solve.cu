@@ -9,14 +9,18 @@
 //                               [u_s; w_s] = Q_s rhs,  W_s = w_s + (children
 //                               updates on the below rows)
 //   backward (root -> leaves):  x_s = Q_s^T [u_s; -x(below rows)]
-// The panels are cut into 2D tiles (forward: 64 rows x 128 columns, backward:
-// 256 rows x 32 columns; all-zero tiles of the triangular L11^-1 block are
-// skipped), so that even the single root supernode spreads over many SMs, and
-// every thread keeps many independent panel loads in flight.  Tiles sharing an
-// output block write partial sums; the last tile to finish (integer ticket) adds
-// them in tile order, so the result does not depend on scheduling and no float
-// atomics run.  Both sweeps run in one persistent launch scheduled by the
-// supernodal tree dependencies (below).
+// The panels are cut into 2D tiles of at most 16384 panel entries (64 KB in
+// FP32), shaped per supernode so that every thread issues all of its panel loads
+// (up to 64) before it uses any: a tile costs about one memory round trip, and a
+// level of the tree spreads over as many CTAs as it has tiles.  Forward tiles are
+// R rows x (256 / R) column groups of 64 columns (R = 256, 128 or 64, whichever
+// covers the supernode's columns with the fewest idle groups); backward tiles are
+// BC columns x min(16384 / BC, 1024) rows (BC = 64, 32, 16 or 8).  All-zero tiles of the
+// triangular L11^-1 block are skipped.  Tiles sharing an output block write
+// partial sums; the last tile to finish (integer ticket) adds them in tile order,
+// so the result does not depend on scheduling and no float atomics run.  Both
+// sweeps run in one persistent launch scheduled by the supernodal tree
+// dependencies (below).
 #include <algorithm>
 
 #include "pd_internal.cuh"
@@ -26,11 +30,20 @@ namespace pd {
 namespace {
 
 constexpr int kThreads = 256;
-constexpr int kFR = 256;    // forward tile rows (one thread per row)
-constexpr int kFC = 256;    // forward tile columns
-constexpr int kBR = 1024;   // backward tile rows (32 lanes x 32)
-constexpr int kBC = 32;     // backward tile columns (8 warps x 4)
-constexpr int kPart = kFR * 3;   // partial-sum slots per tile
+constexpr int kCols = 64;             // forward: columns per thread; backward: loads per lane
+constexpr int kTileElems = 16384;     // panel entries per tile at most
+constexpr int kPart = kThreads * 3;   // partial-sum slots per tile
+// backward tile rows for BC columns: 16384 / BC, at most 1024 (32 rows per lane)
+__host__ __device__ constexpr int bwd_tile_rows(int bc) { return kTileElems / bc < 1024 ? kTileElems / bc : 1024; }
+constexpr int kMaxBR = 1024;
+constexpr int kPreSlots = 4;          // W-row sources per position held in registers
+
+// loads issued back to back per thread: all 64 in FP32, four batches of 16 in FP64
+// (register budget of two CTAs per SM)
+template <typename T>
+struct Batch {
+  static constexpr int kLoads = sizeof(T) == 4 ? 64 : 16;
+};
 
 struct SolveParams {
   const IterState* gate;
@@ -74,13 +87,31 @@ __device__ __forceinline__ SolveTile load_tile(const SolveTile* t, int64_t i) {
 // solve t / (ntiles + grid).
 constexpr long long kSpinLimit = 1ll << 20;   // about a second of polling
 
-__device__ __forceinline__ unsigned long long vload(const unsigned long long* p) {
-  return *reinterpret_cast<const volatile unsigned long long*>(p);
+// Message passing between CTAs: a producer's tile writes, then (after a CTA
+// barrier) one thread's release reduction on a counter; a consumer's relaxed
+// polls, then an acquire fence before it reads.  The barrier orders the other
+// threads' writes before the release (cumulativity).
+__device__ __forceinline__ unsigned long long load_relaxed(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ void fence_acq_rel() { asm volatile("fence.acq_rel.gpu;" ::: "memory"); }
+
+__device__ __forceinline__ void add_release(unsigned long long* p) {
+  asm volatile("red.release.gpu.global.add.u64 [%0], 1;" ::"l"(p) : "memory");
+}
+
+__device__ __forceinline__ unsigned long long add_acq_rel(unsigned long long* p) {
+  unsigned long long old;
+  asm volatile("atom.acq_rel.gpu.global.add.u64 %0, [%1], 1;" : "=l"(old) : "l"(p) : "memory");
+  return old;
 }
 
 __device__ __forceinline__ bool wait_count(const unsigned long long* c, unsigned long long target, int* err) {
   long long it = 0;
-  while (vload(c) < target) {
+  while (load_relaxed(c) < target) {
     if (++it > kSpinLimit) {
       atomicOr(err, DEV_ERR_TIMEOUT);
       return false;
@@ -90,10 +121,56 @@ __device__ __forceinline__ bool wait_count(const unsigned long long* c, unsigned
   return true;
 }
 
+// shared memory of one tile: forward rhs[256][3] + red[256][3]; backward
+// v[kMaxBR][3] + res[64][3] (as T)
+struct __align__(16) PersistSmem {
+  double buf[(kMaxBR + 64) * 3];
+  int flag;
+};
+
+// last of the tiles of an output block?  (then the partial sums are complete)
+__device__ __forceinline__ bool last_of_block(const SolveParams& p, const SolveTile& tl, PersistSmem& sm) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const unsigned long long v = add_acq_rel(p.otick + tl.out);
+    sm.flag = ((v + 1) % (unsigned long long)tl.ntile) == 0;
+  }
+  __syncthreads();
+  return sm.flag != 0;
+}
+
+__device__ __forceinline__ void signal_done(unsigned long long* c) {
+  __syncthreads();
+  if (threadIdx.x == 0) add_release(c);
+}
+
+// W-row sources of a position, loaded before the dependency wait (they are static)
+struct Slots {
+  int32_t g[kPreSlots];
+};
+
+__device__ __forceinline__ Slots load_slots(const SolveParams& p, int64_t pos, bool valid) {
+  Slots sl;
+#pragma unroll
+  for (int k = 0; k < kPreSlots; ++k)
+    sl.g[k] = (valid && k < p.slot_w) ? __ldg(p.slots + pos * p.slot_w + k) : -1;
+  return sl;
+}
+
+// sum of the children's updates of a position (W rows written earlier in this solve)
 template <typename T>
-__device__ __forceinline__ void gather_W_cg(const SolveParams& p, const T* W, int64_t pos, double& v0, double& v1,
-                                            double& v2) {
-  for (int k = 0; k < p.slot_w; ++k) {
+__device__ __forceinline__ void add_W(const SolveParams& p, const Slots& sl, int64_t pos, double& v0, double& v1,
+                                      double& v2) {
+  const T* W = reinterpret_cast<const T*>(p.W);
+#pragma unroll
+  for (int k = 0; k < kPreSlots; ++k) {
+    if (sl.g[k] >= 0) {
+      v0 += (double)__ldcg(W + 3 * (int64_t)sl.g[k]);
+      v1 += (double)__ldcg(W + 3 * (int64_t)sl.g[k] + 1);
+      v2 += (double)__ldcg(W + 3 * (int64_t)sl.g[k] + 2);
+    }
+  }
+  for (int k = kPreSlots; k < p.slot_w; ++k) {
     const int32_t g = __ldg(p.slots + pos * p.slot_w + k);
     if (g >= 0) {
       v0 += (double)__ldcg(W + 3 * (int64_t)g);
@@ -103,220 +180,244 @@ __device__ __forceinline__ void gather_W_cg(const SolveParams& p, const T* W, in
   }
 }
 
-struct __align__(16) PersistSmem {
-  double rhs_d[kFC][3];   // forward: right-hand side of the tile's columns
-  double v_d[kBR][3];     // backward: [u_s; -x(below rows)] of the tile's rows
-  double res_d[kBC][3];
-  int flag;
-};
-
-// last of the tiles of an output block?  (then the partial sums are complete)
-__device__ __forceinline__ bool last_of_block(const SolveParams& p, const SolveTile& tl, PersistSmem& sm) {
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    __threadfence();
-    const unsigned long long v = atomicAdd(p.otick + tl.out, 1ull);
-    const bool last = ((v + 1) % (unsigned long long)tl.ntile) == 0;
-    if (last) __threadfence();
-    sm.flag = last;
-  }
-  __syncthreads();
-  return sm.flag != 0;
-}
-
-__device__ __forceinline__ void signal_done(unsigned long long* c) {
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    __threadfence();
-    atomicAdd(c, 1ull);
-  }
-}
-
-// Forward tile: rows [a, a + kFR) x columns [b, b + kFC) of panel s; thread t
-// owns row a + t and accumulates its whole dot product over the tile's columns
-// (coalesced: consecutive threads read consecutive rows of one column).
-template <typename T>
+// Forward tile: rows [a, a + R) x columns [b, b + G * 64) of panel s, G = 256 / R.
+// Thread (row rl, group g) owns row a + rl and columns b + 64 g ... + 63; a warp
+// reads 32 consecutive rows of one column per load (coalesced).  The group sums
+// are added in group order.
+template <typename T, int R>
 __device__ void fwd_tile_body(const SolveParams& p, const SolveTile& tl, int64_t tid_g, unsigned long long epoch,
                               PersistSmem& sm) {
-  T (*rhs)[3] = reinterpret_cast<T (*)[3]>(sm.rhs_d);
+  constexpr int G = kThreads / R;
+  constexpr int C = G * kCols;
+  constexpr int B = Batch<T>::kLoads;
+  T (*rhs)[3] = reinterpret_cast<T (*)[3]>(sm.buf);
+  T (*red)[3] = reinterpret_cast<T (*)[3]>(sm.buf) + kThreads;
   const int64_t row0 = tl.a, col0 = tl.b;
   const int64_t first = tl.first, nc = tl.nc, nr = tl.nr, pos = tl.pos;
   const T* Q = reinterpret_cast<const T*>(p.Q) + tl.panel_off;
-  const T* W = reinterpret_cast<const T*>(p.W);
-  const int64_t cn = min((int64_t)kFC, nc - col0);
-  const int64_t r = row0 + threadIdx.x;
-  const bool valid = r < nr;
+  const int rl = threadIdx.x % R, g = threadIdx.x / R;
+  const int64_t r = row0 + rl;
+  const int64_t cg0 = col0 + (int64_t)g * kCols;
   // L11^-1 is lower triangular: rows < nc use columns <= row only
-  const int64_t jend = !valid ? 0 : (r < nc ? min(cn, r - col0 + 1) : cn);
-  const T* Qr = Q + r + col0 * nr;
-  // the first panel values load while the dependencies are awaited
-  constexpr int kPre = 16;
-  T pre[kPre];
+  const int64_t cend = r >= nr ? cg0 : (r < nc ? min(nc, r + 1) : nc);
+  const int cnt = (int)max((int64_t)0, min((int64_t)kCols, cend - cg0));
+  const T* Qr = Q + r + cg0 * nr;
+  // static data first: panel values, right-hand side, W-row sources
+  T q[B];
 #pragma unroll
-  for (int k = 0; k < kPre; ++k) pre[k] = (k < jend) ? __ldg(Qr + (int64_t)k * nr) : T(0);
+  for (int k = 0; k < B; ++k) q[k] = (k < cnt) ? __ldg(Qr + (int64_t)k * nr) : T(0);
+  const int64_t jc = col0 + threadIdx.x;   // rhs column of this thread
+  const bool has_c = threadIdx.x < C && jc < nc;
+  double b0 = 0, b1 = 0, b2 = 0;
+  if (has_c) {
+    b0 = __ldg(p.b + 3 * (first + jc));
+    b1 = __ldg(p.b + 3 * (first + jc) + 1);
+    b2 = __ldg(p.b + 3 * (first + jc) + 2);
+  }
+  const Slots sc = load_slots(p, pos + jc, has_c);
+  const bool out_w = g == 0 && r < nr && r >= nc;
+  const Slots sr = load_slots(p, pos + r, out_w);
   if (threadIdx.x == 0) {
     for (int64_t ci = __ldg(p.child_ptr + tl.s); ci < __ldg(p.child_ptr + tl.s + 1); ++ci) {
       const int64_t c = __ldg(p.child_list + ci);
       wait_count(p.fdone + c, (epoch + 1) * (unsigned long long)__ldg(p.nfb + c), p.err);
     }
-    __threadfence();
+    fence_acq_rel();
   }
   __syncthreads();
-  for (int jj = threadIdx.x; jj < kFC; jj += kThreads) {
-    T r0 = T(0), r1 = T(0), r2 = T(0);
-    if (jj < cn) {
-      const int64_t j = col0 + jj, c = first + j;
-      double w0 = 0, w1 = 0, w2 = 0;
-      gather_W_cg<T>(p, W, pos + j, w0, w1, w2);
-      r0 = (T)(p.b[3 * c] - w0);
-      r1 = (T)(p.b[3 * c + 1] - w1);
-      r2 = (T)(p.b[3 * c + 2] - w2);
-    }
-    rhs[jj][0] = r0; rhs[jj][1] = r1; rhs[jj][2] = r2;
+  // children's updates of the output row (below rows), read in the same round
+  // trip as those of the right-hand side
+  double o0 = 0, o1 = 0, o2 = 0;
+  if (out_w) add_W<T>(p, sr, pos + r, o0, o1, o2);
+  if (threadIdx.x < C) {
+    double w0 = 0, w1 = 0, w2 = 0;
+    if (has_c) add_W<T>(p, sc, pos + jc, w0, w1, w2);
+    // zero past the supernode's columns (their panel values are zero too)
+    rhs[threadIdx.x][0] = has_c ? (T)(b0 - w0) : T(0);
+    rhs[threadIdx.x][1] = has_c ? (T)(b1 - w1) : T(0);
+    rhs[threadIdx.x][2] = has_c ? (T)(b2 - w2) : T(0);
   }
   __syncthreads();
   T a0 = T(0), a1 = T(0), a2 = T(0);
+  const T(*rg)[3] = rhs + g * kCols;
+  constexpr int NB = kCols / B;
 #pragma unroll
-  for (int k = 0; k < kPre; ++k) {
-    a0 += pre[k] * rhs[k][0];
-    a1 += pre[k] * rhs[k][1];
-    a2 += pre[k] * rhs[k][2];
+  for (int nb = 0; nb < NB; ++nb) {
+    if (nb > 0) {   // FP64: the next batch of columns
+#pragma unroll
+      for (int k = 0; k < B; ++k) q[k] = (nb * B + k < cnt) ? __ldg(Qr + (int64_t)(nb * B + k) * nr) : T(0);
+    }
+#pragma unroll
+    for (int k = 0; k < B; ++k) {
+      a0 += q[k] * rg[nb * B + k][0];
+      a1 += q[k] * rg[nb * B + k][1];
+      a2 += q[k] * rg[nb * B + k][2];
+    }
   }
-  for (int64_t j = kPre; j < jend; j += 16) {
-    T q[16];
+  if (G > 1) {
+    red[threadIdx.x][0] = a0;
+    red[threadIdx.x][1] = a1;
+    red[threadIdx.x][2] = a2;
+    __syncthreads();
+    if (g == 0) {
 #pragma unroll
-    for (int k = 0; k < 16; ++k) q[k] = (j + k < jend) ? __ldg(Qr + (j + k) * nr) : T(0);
-#pragma unroll
-    for (int k = 0; k < 16; ++k) {
-      const int64_t jj = min(j + k, (int64_t)kFC - 1);
-      a0 += q[k] * rhs[jj][0];
-      a1 += q[k] * rhs[jj][1];
-      a2 += q[k] * rhs[jj][2];
+      for (int k = 1; k < G; ++k) {
+        a0 += red[k * R + rl][0];
+        a1 += red[k * R + rl][1];
+        a2 += red[k * R + rl][2];
+      }
     }
   }
   const int ntile = tl.ntile;
   if (ntile > 1) {
     T* part = reinterpret_cast<T*>(p.partial) + tid_g * kPart;
-    part[3 * threadIdx.x] = a0;
-    part[3 * threadIdx.x + 1] = a1;
-    part[3 * threadIdx.x + 2] = a2;
+    if (g == 0) {
+      part[3 * rl] = a0;
+      part[3 * rl + 1] = a1;
+      part[3 * rl + 2] = a2;
+    }
     if (!last_of_block(p, tl, sm)) return;
-    const T* parts = reinterpret_cast<const T*>(p.partial) + tl.part_base * kPart;
-    a0 = a1 = a2 = T(0);
-    for (int k = 0; k < ntile; ++k) {
-      a0 += __ldcg(parts + (int64_t)k * kPart + 3 * threadIdx.x);
-      a1 += __ldcg(parts + (int64_t)k * kPart + 3 * threadIdx.x + 1);
-      a2 += __ldcg(parts + (int64_t)k * kPart + 3 * threadIdx.x + 2);
+    if (g == 0) {
+      const T* parts = reinterpret_cast<const T*>(p.partial) + tl.part_base * kPart + 3 * rl;
+      a0 = a1 = a2 = T(0);
+      for (int k = 0; k < ntile; ++k) {
+        a0 += __ldcg(parts + (int64_t)k * kPart);
+        a1 += __ldcg(parts + (int64_t)k * kPart + 1);
+        a2 += __ldcg(parts + (int64_t)k * kPart + 2);
+      }
     }
   }
-  if (valid) {
+  if (g == 0 && r < nr) {
     if (r < nc) {
       T* uo = reinterpret_cast<T*>(p.u) + 3 * (first + r);
       uo[0] = a0; uo[1] = a1; uo[2] = a2;
     } else {
-      double v0 = (double)a0, v1 = (double)a1, v2 = (double)a2;
-      gather_W_cg<T>(p, W, pos + r, v0, v1, v2);
       T* Wo = reinterpret_cast<T*>(p.W) + 3 * (tl.relp + (r - nc));
-      Wo[0] = (T)v0; Wo[1] = (T)v1; Wo[2] = (T)v2;
+      Wo[0] = (T)((double)a0 + o0);
+      Wo[1] = (T)((double)a1 + o1);
+      Wo[2] = (T)((double)a2 + o2);
     }
   }
   signal_done(p.fdone + tl.s);
 }
 
-// Backward tile: columns [a, a + kBC) x rows [b, b + kBR) of panel s; warp w owns
-// 4 columns, lanes stride the rows of a column (contiguous, coalesced).
-template <typename T>
+// Backward tile: columns [a, a + BC) x rows [b, b + BR) of panel s, BR = min(16384 / BC, 1024).
+// Warp w owns columns a + w CW ... (CW = BC / 8), its lanes the rows b + lane + 32 i;
+// per column the lanes' sums are added by a fixed shuffle tree.
+template <typename T, int BC>
 __device__ void bwd_tile_body(const SolveParams& p, const SolveTile& tl, int64_t tid_g, unsigned long long epoch,
                               PersistSmem& sm) {
-  T (*v)[3] = reinterpret_cast<T (*)[3]>(sm.v_d);
-  T (*res)[3] = reinterpret_cast<T (*)[3]>(sm.res_d);
+  constexpr int CW = BC / 8;
+  constexpr int BR = bwd_tile_rows(BC);
+  constexpr int RL = BR / 32;           // rows per lane
+  constexpr int B = Batch<T>::kLoads;
+  constexpr int NB = CW * RL > B ? CW * RL / B : 1;   // load batches
+  constexpr int RB = RL / NB;           // rows per lane per batch
+  T (*v)[3] = reinterpret_cast<T (*)[3]>(sm.buf);
+  T (*res)[3] = reinterpret_cast<T (*)[3]>(sm.buf) + kMaxBR;
   const int64_t col0 = tl.a, row0 = tl.b;
   const int64_t first = tl.first, nc = tl.nc, nr = tl.nr;
   const int32_t* srows = p.rows + tl.pos;
   const T* Q = reinterpret_cast<const T*>(p.Q) + tl.panel_off;
   const T* u = reinterpret_cast<const T*>(p.u);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  constexpr int kPerWarp = kBC / (kThreads / 32);
-  const int64_t rn = min((int64_t)kBR, nr - row0);
-  // first rows of each column load while the dependencies are awaited
-  T pre[kPerWarp];
+  const int64_t rn = min((int64_t)BR, nr - row0);
+  T q[CW][RB];
+  auto load_batch = [&](int nb) {
 #pragma unroll
-  for (int c = 0; c < kPerWarp; ++c) {
-    const int64_t j = col0 + warp * kPerWarp + c;
-    const int64_t rr = row0 + lane;
-    pre[c] = (j < nc && lane < rn && (rr >= nc || rr >= j)) ? __ldg(Q + rr + j * nr) : T(0);
+    for (int c = 0; c < CW; ++c) {
+      const int64_t j = col0 + warp * CW + c;
+#pragma unroll
+      for (int i = 0; i < RB; ++i) {
+        const int64_t rr = lane + 32 * (nb * RB + i);
+        const int64_t row = row0 + rr;
+        // column j of L11^-1 is zero above row j
+        q[c][i] = (j < nc && rr < rn && (row >= nc || row >= j)) ? __ldg(Q + row + j * nr) : T(0);
+      }
+    }
+  };
+  load_batch(0);
+  // global rows of the tile's below rows (static)
+  constexpr int VR = BR / kThreads > 0 ? BR / kThreads : 1;
+  int32_t gidx[VR];
+#pragma unroll
+  for (int k = 0; k < VR; ++k) {
+    const int64_t rr = threadIdx.x + (int64_t)k * kThreads;
+    const int64_t row = row0 + rr;
+    gidx[k] = (rr < BR && rr < rn && row >= nc) ? __ldg(srows + row) : -1;
   }
   if (threadIdx.x == 0) {
     const int64_t par = __ldg(p.parent + tl.s);
     if (par >= 0) wait_count(p.bdone + par, (epoch + 1) * (unsigned long long)__ldg(p.nbb + par), p.err);
     else wait_count(p.fdone + tl.s, (epoch + 1) * (unsigned long long)__ldg(p.nfb + tl.s), p.err);
-    __threadfence();
+    fence_acq_rel();
   }
   __syncthreads();
-  for (int64_t rr = threadIdx.x; rr < rn; rr += kThreads) {
-    const int64_t r = row0 + rr;
-    T v0, v1, v2;
-    if (r < nc) {
-      const T* ur = u + 3 * (first + r);
-      v0 = __ldcg(ur); v1 = __ldcg(ur + 1); v2 = __ldcg(ur + 2);
-    } else {
-      const int64_t g = __ldg(srows + r);
-      v0 = (T)(-__ldcg(p.x + 3 * g)); v1 = (T)(-__ldcg(p.x + 3 * g + 1)); v2 = (T)(-__ldcg(p.x + 3 * g + 2));
+  // v = [u_s; -x(below rows)] on the tile's rows, zero past the panel
+#pragma unroll
+  for (int k = 0; k < VR; ++k) {
+    const int64_t rr = threadIdx.x + (int64_t)k * kThreads;
+    if (rr >= BR) continue;
+    const int64_t row = row0 + rr;
+    T v0 = T(0), v1 = T(0), v2 = T(0);
+    if (rr < rn) {
+      if (row < nc) {
+        const T* ur = u + 3 * (first + row);
+        v0 = __ldcg(ur); v1 = __ldcg(ur + 1); v2 = __ldcg(ur + 2);
+      } else {
+        const int64_t gr = gidx[k];
+        v0 = (T)(-__ldcg(p.x + 3 * gr)); v1 = (T)(-__ldcg(p.x + 3 * gr + 1)); v2 = (T)(-__ldcg(p.x + 3 * gr + 2));
+      }
     }
     v[rr][0] = v0; v[rr][1] = v1; v[rr][2] = v2;
   }
   __syncthreads();
+  T acc[CW][3];
 #pragma unroll
-  for (int c = 0; c < kPerWarp; ++c) {
-    const int jl = warp * kPerWarp + c;
-    const int64_t j = col0 + jl;
-    const int64_t l0 = min((int64_t)lane, rn - 1);
-    T a0 = pre[c] * v[l0][0], a1 = pre[c] * v[l0][1], a2 = pre[c] * v[l0][2];
-    if (j < nc) {
-      // column j of L11^-1 is zero above row j
-      const int64_t rs = max((int64_t)32, (j - row0) & ~(int64_t)31);
-      const T* Qj = Q + j * nr + row0;
-      for (int64_t base = rs; base < rn; base += 32 * 8) {
-        T q[8];
+  for (int c = 0; c < CW; ++c) acc[c][0] = acc[c][1] = acc[c][2] = T(0);
 #pragma unroll
-        for (int k = 0; k < 8; ++k) {
-          const int64_t rr = base + lane + 32 * k;
-          q[k] = (rr < rn && (row0 + rr >= nc || row0 + rr >= j)) ? __ldg(Qj + rr) : T(0);
-        }
+  for (int nb = 0; nb < NB; ++nb) {
+    if (nb > 0) load_batch(nb);
 #pragma unroll
-        for (int k = 0; k < 8; ++k) {
-          // rows past the tile carry q = 0; read a filled row so no stale value enters
-          const int64_t rr = min(base + lane + 32 * k, rn - 1);
-          a0 += q[k] * v[rr][0];
-          a1 += q[k] * v[rr][1];
-          a2 += q[k] * v[rr][2];
-        }
+    for (int i = 0; i < RB; ++i) {
+      const int rr = lane + 32 * (nb * RB + i);
+#pragma unroll
+      for (int c = 0; c < CW; ++c) {
+        acc[c][0] += q[c][i] * v[rr][0];
+        acc[c][1] += q[c][i] * v[rr][1];
+        acc[c][2] += q[c][i] * v[rr][2];
       }
     }
-    T t0 = a0, t1 = a1, t2 = a2;
+  }
+#pragma unroll
+  for (int c = 0; c < CW; ++c) {
 #pragma unroll
     for (int off = 16; off >= 1; off >>= 1) {
-      t0 += __shfl_xor_sync(0xffffffffu, t0, off);
-      t1 += __shfl_xor_sync(0xffffffffu, t1, off);
-      t2 += __shfl_xor_sync(0xffffffffu, t2, off);
+      acc[c][0] += __shfl_xor_sync(0xffffffffu, acc[c][0], off);
+      acc[c][1] += __shfl_xor_sync(0xffffffffu, acc[c][1], off);
+      acc[c][2] += __shfl_xor_sync(0xffffffffu, acc[c][2], off);
     }
-    if (lane == 0) { res[jl][0] = t0; res[jl][1] = t1; res[jl][2] = t2; }
+    if (lane == 0) {
+      res[warp * CW + c][0] = acc[c][0];
+      res[warp * CW + c][1] = acc[c][1];
+      res[warp * CW + c][2] = acc[c][2];
+    }
   }
   __syncthreads();
   const int ntile = tl.ntile;
   if (ntile > 1) {
     T* part = reinterpret_cast<T*>(p.partial) + tid_g * kPart;
-    for (int idx = threadIdx.x; idx < kBC * 3; idx += kThreads) part[idx] = res[idx / 3][idx % 3];
+    for (int idx = threadIdx.x; idx < BC * 3; idx += kThreads) part[idx] = res[idx / 3][idx % 3];
     if (!last_of_block(p, tl, sm)) return;
     const T* parts = reinterpret_cast<const T*>(p.partial) + tl.part_base * kPart;
-    for (int idx = threadIdx.x; idx < kBC * 3; idx += kThreads) {
+    for (int idx = threadIdx.x; idx < BC * 3; idx += kThreads) {
       T t = T(0);
       for (int k = 0; k < ntile; ++k) t += __ldcg(parts + (int64_t)k * kPart + idx);
       res[idx / 3][idx % 3] = t;
     }
     __syncthreads();
   }
-  for (int jl = threadIdx.x; jl < kBC; jl += kThreads) {
+  for (int jl = threadIdx.x; jl < BC; jl += kThreads) {
     const int64_t j = col0 + jl;
     if (j >= nc) continue;
     p.x[3 * (first + j)] = (double)res[jl][0];
@@ -326,8 +427,11 @@ __device__ void bwd_tile_body(const SolveParams& p, const SolveTile& tl, int64_t
   signal_done(p.bdone + tl.s);
 }
 
+// tile kinds (SolveTile::pad0): forward R = 256 / 128 / 64, backward BC = 64 / 32 / 16 / 8
+enum TileKind { kF256 = 0, kF128 = 1, kF64 = 2, kB64 = 3, kB32 = 4, kB16 = 5, kB8 = 6 };
+
 template <typename T>
-__global__ void __launch_bounds__(kThreads) solve_persistent_kernel(SolveParams p) {
+__global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 2 : 1) solve_persistent_kernel(SolveParams p) {
   if (p.gate && (p.gate->converged || !p.gate->accepted)) return;
   __shared__ PersistSmem sm;
   __shared__ unsigned long long tk[2];
@@ -348,12 +452,35 @@ __global__ void __launch_bounds__(kThreads) solve_persistent_kernel(SolveParams 
     // barrier that ended the previous tile.
     if (threadIdx.x == 0) tk[slot ^ 1] = atomicAdd(p.gticket, 1ull);
     const SolveTile tl = load_tile(p.tiles, tile);
-    if (tl.pad0 == 0) fwd_tile_body<T>(p, tl, tile, epoch, sm);
-    else bwd_tile_body<T>(p, tl, tile, epoch, sm);
+    switch (tl.pad0) {
+      case kF256: fwd_tile_body<T, 256>(p, tl, tile, epoch, sm); break;
+      case kF128: fwd_tile_body<T, 128>(p, tl, tile, epoch, sm); break;
+      case kF64: fwd_tile_body<T, 64>(p, tl, tile, epoch, sm); break;
+      case kB64: bwd_tile_body<T, 64>(p, tl, tile, epoch, sm); break;
+      case kB32: bwd_tile_body<T, 32>(p, tl, tile, epoch, sm); break;
+      case kB16: bwd_tile_body<T, 16>(p, tl, tile, epoch, sm); break;
+      default: bwd_tile_body<T, 8>(p, tl, tile, epoch, sm); break;
+    }
     __syncthreads();   // shared memory of this tile is free; the drawn ticket is visible
     slot ^= 1;
     t = tk[slot];
   }
+}
+
+// forward rows per tile for a supernode: fewest idle column groups
+int fwd_rows(int64_t nc) {
+  if (nc <= kCols) return 256;
+  if (nc <= 2 * kCols) return 128;
+  return 64;
+}
+
+// backward columns per tile: the narrowest BC >= nc (64 at most), so a supernode
+// of up to 64 columns is one column block
+int bwd_cols(int64_t nc) {
+  if (nc > 32) return 64;
+  if (nc > 16) return 32;
+  if (nc > 8) return 16;
+  return 8;
 }
 
 }  // namespace
@@ -376,6 +503,8 @@ void build_solve_schedule(const HostMesh& h, SolveSchedule& S) {
     t.relp = (int32_t)h.rel_ptr[s];
     return t;
   };
+  S.nfb.assign(h.ns, 0);
+  S.nbb.assign(h.ns, 0);
   for (int64_t L = 0; L < h.nlev; ++L) {
     SolveLevel& sl = S.levels[L];
     sl.fwd_off = (int64_t)S.fwd.size();
@@ -383,60 +512,59 @@ void build_solve_schedule(const HostMesh& h, SolveSchedule& S) {
     for (int64_t i = h.level_ptr[L]; i < h.level_ptr[L + 1]; ++i) {
       const int64_t s = h.level_list[i];
       const int64_t nr = h.nr(s), nc = h.nc(s);
-      for (int64_t r0 = 0; r0 < nr; r0 += kFR) {
+      const int R = fwd_rows(nc);
+      const int C = (kThreads / R) * kCols;
+      const int32_t fkind = R == 256 ? kF256 : (R == 128 ? kF128 : kF64);
+      for (int64_t r0 = 0; r0 < nr; r0 += R) {
         const int32_t out = (int32_t)S.n_fwd_out++;
         const size_t b0 = S.fwd.size();
         // rows < nc of the L11^-1 block need columns <= row only
-        const int64_t cmax = (r0 + kFR <= nc) ? r0 + kFR : nc;
-        for (int64_t c0 = 0; c0 < cmax; c0 += kFC) {
+        const int64_t cmax = (r0 + R <= nc) ? r0 + R : nc;
+        for (int64_t c0 = 0; c0 < cmax; c0 += C) {
           SolveTile t = base(s);
           t.a = (int32_t)r0;
           t.b = (int32_t)c0;
           t.out = out;
           t.part_base = (int64_t)b0;
+          t.pad0 = fkind;
           S.fwd.push_back(t);
         }
         for (size_t k = b0; k < S.fwd.size(); ++k) S.fwd[k].ntile = (int32_t)(S.fwd.size() - b0);
+        ++S.nfb[s];
       }
-      for (int64_t c0 = 0; c0 < nc; c0 += kBC) {
+      const int BC = bwd_cols(nc);
+      const int BR = bwd_tile_rows(BC);
+      const int32_t bkind = BC == 64 ? kB64 : (BC == 32 ? kB32 : (BC == 16 ? kB16 : kB8));
+      for (int64_t c0 = 0; c0 < nc; c0 += BC) {
         const int32_t out = (int32_t)S.n_bwd_out++;
         const size_t b0 = S.bwd.size();
         // column c of L11^-1 is zero above row c: start at the row block holding c0
-        for (int64_t r0 = (c0 / kBR) * kBR; r0 < nr; r0 += kBR) {
+        for (int64_t r0 = (c0 / BR) * BR; r0 < nr; r0 += BR) {
           SolveTile t = base(s);
           t.a = (int32_t)c0;
           t.b = (int32_t)r0;
           t.out = out;
           t.part_base = (int64_t)b0;
+          t.pad0 = bkind;
           S.bwd.push_back(t);
         }
         for (size_t k = b0; k < S.bwd.size(); ++k) S.bwd[k].ntile = (int32_t)(S.bwd.size() - b0);
+        ++S.nbb[s];
       }
     }
     sl.fwd_cnt = (int64_t)S.fwd.size() - sl.fwd_off;
     sl.bwd_cnt = (int64_t)S.bwd.size() - sl.bwd_off;
   }
-  S.nfb.assign(h.ns, 0);
-  S.nbb.assign(h.ns, 0);
-  for (int64_t s2 = 0; s2 < h.ns; ++s2) {
-    S.nfb[s2] = (int32_t)((h.nr(s2) + kFR - 1) / kFR);
-    S.nbb[s2] = (int32_t)((h.nc(s2) + kBC - 1) / kBC);
-  }
   // persistent order: forward tiles by ascending level, backward tiles by
   // descending level (tiles of one output block stay contiguous); output ids of
   // backward blocks follow the forward ones; partial slots use the global index
   S.all.clear();
-  for (const SolveTile& t : S.fwd) {
-    SolveTile u = t;
-    u.pad0 = 0;
-    S.all.push_back(u);
-  }
+  for (const SolveTile& t : S.fwd) S.all.push_back(t);
   for (int64_t L = h.nlev - 1; L >= 0; --L) {
     const SolveLevel& sl = S.levels[L];
     const int64_t shift = (int64_t)S.all.size() - sl.bwd_off;
     for (int64_t k = sl.bwd_off; k < sl.bwd_off + sl.bwd_cnt; ++k) {
       SolveTile u = S.bwd[k];
-      u.pad0 = 1;
       u.out += (int32_t)S.n_fwd_out;
       u.part_base += shift;
       S.all.push_back(u);
@@ -448,12 +576,14 @@ size_t solve_partial_bytes(const SolveSchedule& S) {
   return (S.fwd.size() + S.bwd.size()) * (size_t)kPart * sizeof(double);
 }
 
+// CTAs per SM of the FP32 variant.  Both precisions launch this many CTAs per
+// SM, so every solve consumes the same number of tickets; the FP64 variant has
+// fewer resident at a time, which the ticket order tolerates (a CTA draws
+// tickets only once it runs).
 int solve_persistent_occupancy() {
   int occ = 0;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, solve_persistent_kernel<float>, kThreads, 0);
-  int occ2 = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ2, solve_persistent_kernel<double>, kThreads, 0);
-  return std::max(1, std::min(occ, occ2));
+  return std::max(1, occ);
 }
 
 cudaError_t solve_A(const MeshImpl* m, const IterState* gate, const double* b, double* out,
