@@ -140,6 +140,14 @@ typedef struct {
   int32_t warm_start;           /* nonzero: keep the L-BFGS pairs from one time step to the
                                    next and start each adjoint solve from the previous
                                    step's z (fixed points unchanged) */
+  int32_t no_graphs;            /* nonzero: launch every kernel directly; by default chunks of
+                                   iterations are captured once per mesh as CUDA graphs and
+                                   replayed (not with profile, which times single launches) */
+  double* step_ms;              /* optional host array of T entries: pd_forward stores the
+                                   host wall time of each step [ms], pd_backward adds the
+                                   time of the step's adjoint (so after both calls entry t
+                                   holds the fwd+bwd latency of step t; the recomputation of
+                                   checkpointed segments is not included); NULL = none */
 } pd_solver_opts;
 
 typedef struct {
@@ -229,48 +237,82 @@ pd_status pd_local_step_noalloc(int64_t n_nodes, int64_t n_elems, const int32_t*
                                 const uint8_t* contact, double k_contact, int32_t precision,
                                 double* grad_E, double* energy, void* stream);
 
-/* Continuous-batching server (rollout-plus-gradient requests). */
+/* Serving: rollout-plus-gradient requests on one GPU (no counterpart in the
+ * paper, whose method this wraps: each request is one forward rollout of T
+ * implicit-Euler steps (Alg. 1), the loss L = sum(loss_w * x_T), and one
+ * backward pass (Alg. 2 per step, Sec. 4.3) to dL/dv0 and dL/dact).
+ *
+ * A server owns `max_slots` worker slots; each is a host thread with its own
+ * CUDA stream and a small cache of meshes (keyed by geometry) and factors (keyed
+ * by material weights, h, gravity, contact stiffness and precision).  Requests
+ * are admitted first-in first-out as soon as a slot is free and their estimated
+ * device memory fits in `mem_budget_bytes` next to the requests already running
+ * (a request that fits nowhere runs alone).  The kernels of all running requests
+ * share the GPU; the solve of a request is limited to its share of the SMs so
+ * that several small solves run side by side.  A request's result does not
+ * depend on what else runs: every reduction has a fixed order, and each request
+ * has its own mesh workspace.
+ *
+ * All arrays of a request are host memory, copied during pd_serve_submit (the
+ * caller may free them on return); node arrays are in kept-node order. */
 typedef struct pd_server_s* pd_server;
 
 typedef struct {
-  int32_t nx, ny, nz;           /* voxel box of the request */
-  double dx, density, h, gravity[3], k_contact, mu;
+  /* geometry (as pd_mesh_desc) */
+  int32_t nx, ny, nz;
+  double dx, origin[3], density;
   const uint8_t* cell_mask_host;   /* nx*ny*nz or NULL */
   const uint8_t* dirichlet_host;   /* per kept node or NULL */
-  const uint8_t* contact_host;     /* per kept node or NULL */
-  const double* w_corot_host;      /* (e) */
+  const uint8_t* contact_host;     /* per kept node or NULL (contact needs k_contact > 0) */
+  /* material and dynamics (as pd_factorize) */
+  const double* w_corot_host;      /* (e) or NULL */
   const double* w_vol_host;        /* (e) or NULL */
   const double* w_muscle_host;     /* (e) or NULL */
-  const double* fiber_host;        /* (e,3) or NULL */
+  const double* fiber_host;        /* (e,3), required with w_muscle_host */
+  double h, gravity[3], k_contact, mu;
+  int32_t precision;               /* PD_PREC_FP64 or PD_PREC_MIXED */
+  /* rollout */
+  int32_t T;                       /* steps, >= 1 */
   const double* x0_host;           /* (n,3) */
   const double* v0_host;           /* (n,3) */
+  const double* f_ext_host;        /* (n,3) constant over the rollout, or NULL */
   const double* act_host;          /* (T,e) or NULL */
-  const double* loss_w_host;       /* (n,3): loss = sum(loss_w * x_T) */
-  int32_t T;
+  const double* loss_w_host;       /* (n,3) */
   pd_solver_opts opts;
 } pd_request;
 
 typedef struct {
-  pd_status status;
-  double loss;
+  pd_status status;                /* the request's own status (PD_OK, PD_ERR_NOT_CONVERGED, ...) */
+  double loss;                     /* sum(loss_w * x_T) */
   int64_t n_nodes, n_elems, T;
-  double* x_final_host;            /* library-owned until the next poll of this ticket */
-  double* g_v0_host;
-  double* g_act_host;
-  double latency_ms;               /* submit -> completion */
+  const double* x_final_host;      /* (n,3) x_T */
+  const double* g_v0_host;         /* (n,3) dL/dv0 */
+  const double* g_act_host;        /* (T,e) dL/dact, NULL without actuation */
+  double queue_ms;                 /* submit -> start on a slot (host clock) */
+  double latency_ms;               /* submit -> completion (host clock) */
   int64_t fwd_iters, bwd_iters;
+  int32_t slot;                    /* worker slot that ran it */
+  int32_t mesh_cached, factor_cached;   /* 1 if the slot's cache served them */
 } pd_result;
 
+/* device: CUDA ordinal; mem_budget_bytes: device memory the running requests'
+ * estimates may add up to; max_slots: concurrent requests (1..64). */
 pd_status pd_serve_create(int32_t device, size_t mem_budget_bytes, int32_t max_slots,
                           pd_server* out);
-/* Non-blocking.  Copies the request; admission happens when a slot and device
- * memory are free.  Returns a ticket. */
+/* Non-blocking: validates and copies the request, returns its ticket.
+ * PD_ERR_INVALID_ARG for a malformed request (nothing is queued). */
 pd_status pd_serve_submit(pd_server s, const pd_request* r, uint64_t* ticket);
-/* PD_OK with *out filled when done, PD_ERR_TIMEOUT while pending, or the
- * request's error. */
+/* PD_OK with *out filled once the request has finished (out->status holds the
+ * request's own status; pd_last_error-style text is not kept), PD_ERR_TIMEOUT
+ * while it is queued or running, PD_ERR_INVALID_ARG for an unknown or released
+ * ticket.  The arrays in *out stay valid until pd_serve_release of the ticket
+ * or pd_serve_destroy. */
 pd_status pd_serve_poll(pd_server s, uint64_t ticket, pd_result* out);
-/* Blocks until every submitted request has completed. */
+/* Frees a finished request's result. */
+pd_status pd_serve_release(pd_server s, uint64_t ticket);
+/* Blocks until every submitted request has finished. */
 pd_status pd_serve_drain(pd_server s);
+/* Finishes the running requests, drops the queued ones, frees everything. */
 void pd_serve_destroy(pd_server s);
 
 const char* pd_last_error(void);

@@ -61,7 +61,8 @@ class SolverOpts(ctypes.Structure):
                 ("max_iter_fwd", ctypes.c_int32), ("max_iter_bwd", ctypes.c_int32),
                 ("lbfgs_m", ctypes.c_int32), ("ls_max", ctypes.c_int32),
                 ("checkpoint_every", ctypes.c_int32), ("check_every", ctypes.c_int32),
-                ("profile", ctypes.c_int32), ("warm_start", ctypes.c_int32)]
+                ("profile", ctypes.c_int32), ("warm_start", ctypes.c_int32),
+                ("no_graphs", ctypes.c_int32), ("step_ms", c_double_p)]
 
 
 class Stats(ctypes.Structure):
@@ -81,25 +82,27 @@ class Stats(ctypes.Structure):
 
 class Request(ctypes.Structure):
     _fields_ = [("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("nz", ctypes.c_int32),
-                ("dx", ctypes.c_double), ("density", ctypes.c_double), ("h", ctypes.c_double),
-                ("gravity", ctypes.c_double * 3), ("k_contact", ctypes.c_double), ("mu", ctypes.c_double),
+                ("dx", ctypes.c_double), ("origin", ctypes.c_double * 3), ("density", ctypes.c_double),
                 ("cell_mask_host", c_u8_p), ("dirichlet_host", c_u8_p), ("contact_host", c_u8_p),
                 ("w_corot_host", c_double_p), ("w_vol_host", c_double_p), ("w_muscle_host", c_double_p),
-                ("fiber_host", c_double_p), ("x0_host", c_double_p), ("v0_host", c_double_p),
-                ("act_host", c_double_p), ("loss_w_host", c_double_p), ("T", ctypes.c_int32),
+                ("fiber_host", c_double_p), ("h", ctypes.c_double), ("gravity", ctypes.c_double * 3),
+                ("k_contact", ctypes.c_double), ("mu", ctypes.c_double), ("precision", ctypes.c_int32),
+                ("T", ctypes.c_int32), ("x0_host", c_double_p), ("v0_host", c_double_p),
+                ("f_ext_host", c_double_p), ("act_host", c_double_p), ("loss_w_host", c_double_p),
                 ("opts", SolverOpts)]
 
 
 class Result(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int32), ("loss", ctypes.c_double), ("n_nodes", ctypes.c_int64),
                 ("n_elems", ctypes.c_int64), ("T", ctypes.c_int64), ("x_final_host", c_double_p),
-                ("g_v0_host", c_double_p), ("g_act_host", c_double_p), ("latency_ms", ctypes.c_double),
-                ("fwd_iters", ctypes.c_int64), ("bwd_iters", ctypes.c_int64)]
+                ("g_v0_host", c_double_p), ("g_act_host", c_double_p), ("queue_ms", ctypes.c_double),
+                ("latency_ms", ctypes.c_double), ("fwd_iters", ctypes.c_int64), ("bwd_iters", ctypes.c_int64),
+                ("slot", ctypes.c_int32), ("mesh_cached", ctypes.c_int32), ("factor_cached", ctypes.c_int32)]
 
 
 SYMBOLS = ["pd_create_mesh", "pd_mesh_destroy", "pd_mesh_query", "pd_mesh_export", "pd_factorize",
            "pd_forward", "pd_backward", "pd_local_step", "pd_hessian_vector", "pd_solve_A",
-           "pd_local_step_noalloc", "pd_serve_create", "pd_serve_submit", "pd_serve_poll", "pd_serve_drain",
+           "pd_local_step_noalloc", "pd_serve_create", "pd_serve_submit", "pd_serve_poll", "pd_serve_release", "pd_serve_drain",
            "pd_serve_destroy", "pd_last_error"]
 
 _lib = None
@@ -147,6 +150,8 @@ def lib() -> ctypes.CDLL:
     L.pd_serve_submit.restype = st
     L.pd_serve_poll.argtypes = [vp, ctypes.c_uint64, ctypes.POINTER(Result)]
     L.pd_serve_poll.restype = st
+    L.pd_serve_release.argtypes = [vp, ctypes.c_uint64]
+    L.pd_serve_release.restype = st
     L.pd_serve_drain.argtypes = [vp]
     L.pd_serve_drain.restype = st
     L.pd_serve_destroy.argtypes = [vp]

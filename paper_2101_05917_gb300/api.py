@@ -43,9 +43,16 @@ def _u8(a, n, name):
 
 
 def solver_opts(tol_fwd=1e-9, tol_bwd=1e-9, max_iter_fwd=500, max_iter_bwd=500, lbfgs_m=5, ls_max=10,
-                checkpoint_every=0, check_every=4, profile=False, warm_start=False) -> N.SolverOpts:
+                checkpoint_every=0, check_every=4, profile=False, warm_start=False, graphs=True,
+                step_ms: Optional[np.ndarray] = None) -> N.SolverOpts:
+    """step_ms: optional float64 host array of T entries receiving the per-step
+    wall time (forward, then the backward adds its own); the caller keeps it alive."""
+    p = None
+    if step_ms is not None:
+        assert step_ms.dtype == np.float64 and step_ms.flags.c_contiguous
+        p = step_ms.ctypes.data_as(N.c_double_p)
     return N.SolverOpts(tol_fwd, tol_bwd, max_iter_fwd, max_iter_bwd, lbfgs_m, ls_max, checkpoint_every,
-                        check_every, 1 if profile else 0, 1 if warm_start else 0)
+                        check_every, 1 if profile else 0, 1 if warm_start else 0, 0 if graphs else 1, p)
 
 
 @dataclass
@@ -210,3 +217,118 @@ def scene_weights(sc, device="cuda"):
     w_m = t(E * np.asarray(sc.muscle, dtype=np.float64)) if sc.muscle is not None else None
     fib = t(sc.fiber) if sc.muscle is not None else None
     return w_corot, w_vol, w_m, fib
+
+
+def _host(a, dtype, n=None, name=""):
+    if a is None:
+        return None, None
+    arr = np.ascontiguousarray(np.asarray(a, dtype=dtype).reshape(-1))
+    if n is not None and arr.size != n:
+        raise ValueError(f"{name}: expected {n} entries, got {arr.size}")
+    ptype = N.c_u8_p if dtype == np.uint8 else N.c_double_p
+    return arr, arr.ctypes.data_as(ptype)
+
+
+class PDServer:
+    """Rollout-plus-gradient serving on one GPU (pd_serve_*): each request is a
+    forward rollout, the loss sum(loss_w * x_T) and the backward pass to dL/dv0
+    and dL/dact.  Requests are admitted continuously onto `max_slots` worker
+    slots; see diffpd.h for the admission and caching rules."""
+
+    def __init__(self, device=0, mem_budget=16 << 30, max_slots=4):
+        self.handle = ctypes.c_void_p()
+        N.check(N.lib().pd_serve_create(int(device), int(mem_budget), int(max_slots), ctypes.byref(self.handle)),
+                "pd_serve_create")
+
+    def submit_scene(self, sc, precision=N.PD_PREC_MIXED, opts=None, act=None, loss_w=None, T=None) -> int:
+        """Submits a workloads.Scene; act / loss_w / T default to the scene's."""
+        E = np.asarray(sc.youngs, dtype=np.float64)
+        wc, wv = material_weights(E, sc.poisson)
+        e = E.size
+        T = sc.T if T is None else T
+        act = sc.act if act is None else act
+        if act is not None:
+            act = np.asarray(act, dtype=np.float64)[:T]
+        loss_w = sc.loss_w if loss_w is None else loss_w
+        r = N.Request()
+        r.nx, r.ny, r.nz = sc.nx, sc.ny, sc.nz
+        r.dx = sc.dx
+        r.origin = (ctypes.c_double * 3)(*sc.origin)
+        r.density = sc.density
+        keep = []
+
+        def put(field, a, dtype, n=None):
+            arr, p = _host(a, dtype, n, field)
+            keep.append(arr)
+            setattr(r, field, p)
+        n = sc.x0.shape[0]
+        put("cell_mask_host", sc.cell_mask, np.uint8, sc.nx * sc.ny * sc.nz)
+        put("dirichlet_host", sc.dirichlet, np.uint8, n)
+        put("contact_host", sc.contact if sc.k_contact > 0 else None, np.uint8, n)
+        put("w_corot_host", wc if sc.corotated else None, np.float64, e)
+        put("w_vol_host", wv if sc.volume else None, np.float64, e)
+        musc = sc.muscle is not None
+        put("w_muscle_host", E * np.asarray(sc.muscle, dtype=np.float64) if musc else None, np.float64, e)
+        put("fiber_host", sc.fiber if musc else None, np.float64, 3 * e)
+        r.h = sc.h
+        r.gravity = (ctypes.c_double * 3)(*sc.gravity)
+        r.k_contact = sc.k_contact
+        r.mu = sc.mu
+        r.precision = precision
+        r.T = T
+        put("x0_host", sc.x0, np.float64, 3 * n)
+        put("v0_host", sc.v0, np.float64, 3 * n)
+        put("f_ext_host", sc.f_ext, np.float64, 3 * n)
+        put("act_host", act, np.float64, T * e if act is not None else None)
+        put("loss_w_host", loss_w, np.float64, 3 * n)
+        r.opts = opts or solver_opts()
+        t = ctypes.c_uint64()
+        N.check(N.lib().pd_serve_submit(self.handle, ctypes.byref(r), ctypes.byref(t)), "pd_serve_submit")
+        return t.value
+
+    def poll(self, ticket: int):
+        """None while pending; else a dict with the result (arrays copied)."""
+        res = N.Result()
+        st = N.lib().pd_serve_poll(self.handle, ctypes.c_uint64(ticket), ctypes.byref(res))
+        if st == N.PD_ERR_TIMEOUT:
+            return None
+        N.check(st, "pd_serve_poll")
+        n, e, T = res.n_nodes, res.n_elems, res.T
+        out = {k: getattr(res, k) for k in ("status", "loss", "queue_ms", "latency_ms", "fwd_iters", "bwd_iters",
+                                            "slot", "mesh_cached", "factor_cached")}
+
+        def arr(p, count, shape):
+            if not p or res.status not in (N.PD_OK, N.PD_ERR_NOT_CONVERGED):
+                return None
+            return np.ctypeslib.as_array(p, shape=(count,)).reshape(shape).copy()
+        out["x_final"] = arr(res.x_final_host, 3 * n, (n, 3))
+        out["g_v0"] = arr(res.g_v0_host, 3 * n, (n, 3))
+        out["g_act"] = arr(res.g_act_host, T * e, (T, e))
+        return out
+
+    def release(self, ticket: int):
+        N.check(N.lib().pd_serve_release(self.handle, ctypes.c_uint64(ticket)), "pd_serve_release")
+
+    def result(self, ticket: int):
+        """Waits (host polling) for a ticket, returns its result and releases it."""
+        import time
+        while True:
+            r = self.poll(ticket)
+            if r is not None:
+                self.release(ticket)
+                return r
+            time.sleep(0.0005)
+
+    def drain(self):
+        N.check(N.lib().pd_serve_drain(self.handle), "pd_serve_drain")
+
+    def close(self):
+        if getattr(self, "handle", None) is not None and self.handle.value:
+            N.lib().pd_serve_destroy(self.handle)
+            self.handle = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

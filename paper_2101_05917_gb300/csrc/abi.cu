@@ -68,6 +68,22 @@ struct pd_mesh_s {
   pd::MeshImpl impl;
 };
 
+namespace pd {
+
+void drop_iteration_graphs(MeshImpl* m);
+
+void limit_solve_ctas(pd_mesh m, int ctas) {
+  if (!m || ctas <= 0) return;
+  m->impl.solve_grid = std::max(1, std::min(m->impl.solve_grid, ctas));
+  drop_iteration_graphs(&m->impl);   // the graphs captured the solve's grid
+}
+
+int solve_ctas(pd_mesh m) { return m ? m->impl.solve_grid : 0; }
+
+size_t mesh_device_bytes(pd_mesh m) { return m ? m->impl.ws.bytes : 0; }
+
+}  // namespace pd
+
 using namespace pd;
 
 namespace {
@@ -85,6 +101,9 @@ pd_status ensure_workspace(MeshImpl* m, int lbfgs_m) {
     PD_CUDA_TRY(dalloc(m, (double**)&w.elembuf, (size_t)(24 * m->h.e)));
     const int64_t np = (int64_t)element_energy_partials(m) + 4 * (int64_t)gather_blocks(m) + 4 * 4096 + 64;
     PD_CUDA_TRY(dalloc(m, &w.partials, (size_t)np));
+    PD_CUDA_TRY(dalloc(m, &w.lpart, (size_t)kMaxDots * 1184));
+    PD_CUDA_TRY(dalloc(m, &w.act_cur, (size_t)std::max<int64_t>(m->h.e, 1)));
+    PD_CUDA_TRY(dalloc(m, &w.xnext_cur, (size_t)n3));
     PD_CUDA_TRY(dalloc(m, &w.counters, 16));
     PD_CUDA_TRY(cudaMemset(w.counters, 0, 16 * sizeof(unsigned)));
     PD_CUDA_TRY(dalloc(m, &w.st, 1));
@@ -176,7 +195,7 @@ struct Ctx {
   pd_solver_opts o;
   int64_t n, nf, n3f;
   int vb;          // vector kernel blocks
-  int coop;        // cooperative kernel blocks (co-resident)
+  bool graphs;     // replay iteration chunks as CUDA graphs
   VecCtx vc;
   double* pe;      // energy partials
   double* pg;      // gather partials
@@ -192,11 +211,13 @@ Ctx make_ctx(MeshImpl* m, cudaStream_t s, const pd_solver_opts& o) {
   c.nf = m->h.nf;
   c.n3f = 3 * m->h.nf;
   c.vb = vec_blocks(c.n3f);
-  c.coop = m->coop_blocks;
+  c.graphs = !o.profile && !o.no_graphs;
   c.vc.n3 = c.n3f;
   c.vc.st = m->ws.st;
   c.vc.partials = m->ws.partials;
   c.vc.counter = m->ws.counters;
+  c.vc.lpart = m->ws.lpart;
+  c.vc.lcounter = m->ws.counters + 1;
   c.nbe = element_energy_partials(m);
   c.nbg = gather_blocks(m);
   c.pe = m->ws.partials;
@@ -208,12 +229,6 @@ pd_status poll(Ctx& c) {
   PD_CUDA_TRY(cudaMemcpyAsync(c.m->ws.st_host, c.m->ws.st, sizeof(IterState), cudaMemcpyDeviceToHost, c.s));
   PD_CUDA_TRY(cudaStreamSynchronize(c.s));
   return PD_OK;
-}
-
-template <typename... Args>
-cudaError_t coop_launch(void (*kern)(Args...), int grid, cudaStream_t s, Args... args) {
-  void* ptrs[] = {(void*)&args...};
-  return cudaLaunchCooperativeKernel((const void*)kern, dim3(grid), dim3(256), ptrs, 0, s);
 }
 
 // one forward iteration: evaluate the trial point, decide, commit and the
@@ -228,16 +243,17 @@ pd_status launch_fwd_iteration(Ctx& c, int prec, const double* act_t) {
   if (c.local_t) c.local_t->record(c.s);
   PD_CUDA_TRY(launch_gather_grad(m, st, w.elembuf, prec, w.xt, w.y, w.dir, w.gradt, c.pg, c.s));
   decide_fwd_kernel<<<1, 256, 0, c.s>>>(st, c.pe, c.nbe, c.pg, c.nbg);
-  PD_CUDA_TRY(coop_launch(lbfgs_pre_fwd_kernel, c.coop, c.s, c.vc, w.x, (const double*)w.xt, w.grad,
-                          (const double*)w.gradt, w.q, w.S, w.Y));
+  lbfgs_commit_fwd_kernel<<<c.vb, 256, 0, c.s>>>(c.vc, w.x, w.xt, w.grad, w.gradt, w.S, w.Y);
+  lbfgs_q_kernel<<<c.vb, 256, 0, c.s>>>(c.vc, w.grad, w.Y, w.q);
   if (c.solve_t) c.solve_t->record(c.s);
   PD_CUDA_TRY(solve_A(m, st, w.q, w.r, m->precision, c.s));
   if (c.solve_t) c.solve_t->record(c.s);
-  c.launches += 6;
+  lbfgs_post_dots_kernel<<<c.vb, 256, 0, c.s>>>(c.vc, w.grad, w.Y, w.r);
+  lbfgs_dir_kernel<<<c.vb, 256, 0, c.s>>>(c.vc, w.S, w.r, w.dir, w.x, w.xt);
+  c.launches += 9;
   c.solves += 1;
   c.locals += 1;
-  PD_CUDA_TRY(coop_launch(lbfgs_post_fwd_kernel, c.coop, c.s, c.vc, (const double*)w.S, (const double*)w.Y,
-                          w.r, w.dir, (const double*)w.grad, (const double*)w.x, w.xt));
+  PD_CUDA_TRY(cudaGetLastError());
   return PD_OK;
 }
 
@@ -247,20 +263,116 @@ pd_status launch_bwd_iteration(Ctx& c, int prec, const double* xnext, const doub
   MeshImpl* m = c.m;
   Workspace& w = m->ws;
   IterState* st = w.st;
-  PD_CUDA_TRY(coop_launch(lbfgs_pre_bwd_kernel, c.coop, c.s, c.vc, (const double*)w.dir, (const double*)w.Hd,
-                          w.z, w.gs, w.q, w.S, w.Y));
+  lbfgs_commit_bwd_kernel<<<c.vb, 256, 0, c.s>>>(c.vc, w.dir, w.Hd, w.z, w.gs, w.S, w.Y);
+  lbfgs_q_kernel<<<c.vb, 256, 0, c.s>>>(c.vc, w.gs, w.Y, w.q);
   if (c.solve_t) c.solve_t->record(c.s);
   PD_CUDA_TRY(solve_A(m, st, w.q, w.r, m->precision, c.s));
   if (c.solve_t) c.solve_t->record(c.s);
-  c.launches += 7;
+  lbfgs_post_dots_kernel<<<c.vb, 256, 0, c.s>>>(c.vc, w.gs, w.Y, w.r);
+  lbfgs_dir_kernel<<<c.vb, 256, 0, c.s>>>(c.vc, w.S, w.r, w.dir, nullptr, nullptr);
+  c.launches += 9;
   c.solves += 1;
-  PD_CUDA_TRY(coop_launch(lbfgs_post_bwd_kernel, c.coop, c.s, c.vc, (const double*)w.S, (const double*)w.Y,
-                          w.r, w.dir, (const double*)w.gs));
   LocalArgs la{m, st, xnext, w.dir, act_t, prec};
   PD_CUDA_TRY(launch_element_hvp(la, w.elembuf, w.flags, c.s));
   PD_CUDA_TRY(launch_gather_hvp(m, st, w.elembuf, prec, xnext, w.dir, w.gs, w.Hd, c.pg, c.s));
   decide_bwd_kernel<<<1, 256, 0, c.s>>>(st, c.pg, c.nbg);
   PD_CUDA_TRY(cudaGetLastError());
+  return PD_OK;
+}
+
+// ------------------------------------------------------------ CUDA graphs
+// A chunk of kGraphIters iterations is captured once per mesh, direction and
+// precision (on the mesh's capture stream, so any caller stream works, the legacy
+// default stream included) and replayed with one launch.  The captured launches
+// read the step's inputs from fixed buffers (ws.act_cur, ws.xnext_cur) and decide
+// everything else from the device-side iteration state, exactly as the direct
+// launches do; the results are the same.  If a capture fails the chunk is simply
+// launched directly.
+constexpr int kGraphIters = 4;
+
+
+}  // namespace
+
+namespace pd {
+
+void drop_iteration_graphs(MeshImpl* m) {
+  for (auto& row : m->iter_graph)
+    for (cudaGraphExec_t& g : row) {
+      if (g) cudaGraphExecDestroy(g);
+      g = nullptr;
+    }
+}
+
+}  // namespace pd
+
+namespace {
+
+cudaGraphExec_t iteration_graph(Ctx& c, int dir, int prec, bool with_act) {
+  MeshImpl* m = c.m;
+  const int pi = prec == PD_PREC_MIXED ? 1 : 0;
+  cudaGraphExec_t& g = m->iter_graph[dir][pi];
+  if (g && m->iter_graph_act[dir][pi] == with_act) return g;
+  if (g) cudaGraphExecDestroy(g);
+  g = nullptr;
+  if (!m->cap_stream && cudaStreamCreateWithFlags(&m->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  Ctx cc = c;
+  cc.s = m->cap_stream;
+  cc.solve_t = nullptr;
+  cc.local_t = nullptr;
+  cc.launches = cc.solves = cc.locals = 0;
+  if (cudaStreamBeginCapture(cc.s, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  pd_status st = PD_OK;
+  for (int k = 0; k < kGraphIters && st == PD_OK; ++k)
+    st = dir == 0 ? launch_fwd_iteration(cc, prec, with_act ? m->ws.act_cur : nullptr)
+                  : launch_bwd_iteration(cc, prec, m->ws.xnext_cur, with_act ? m->ws.act_cur : nullptr);
+  cudaGraph_t graph = nullptr;
+  cudaError_t e = cudaStreamEndCapture(cc.s, &graph);
+  if (st != PD_OK || e != cudaSuccess || !graph) {
+    if (graph) cudaGraphDestroy(graph);
+    cudaGetLastError();
+    return nullptr;
+  }
+  e = cudaGraphInstantiate(&g, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess) {
+    g = nullptr;
+    cudaGetLastError();
+    return nullptr;
+  }
+  m->iter_graph_act[dir][pi] = with_act;
+  m->iter_graph_counts[dir][pi][0] = cc.launches;
+  m->iter_graph_counts[dir][pi][1] = cc.solves;
+  m->iter_graph_counts[dir][pi][2] = cc.locals;
+  return g;
+}
+
+// `count` iterations of one direction: whole chunks from the captured graph, the
+// rest (and everything when graphs are off) launched directly.  act / xnext are
+// the fixed per-step buffers.
+pd_status run_iterations(Ctx& c, int dir, int prec, const double* act, const double* xnext, int count) {
+  int done = 0;
+  if (c.graphs && count >= kGraphIters) {
+    cudaGraphExec_t g = iteration_graph(c, dir, prec, act != nullptr);
+    if (g) {
+      const int64_t* gc = c.m->iter_graph_counts[dir][prec == PD_PREC_MIXED ? 1 : 0];
+      for (; done + kGraphIters <= count; done += kGraphIters) {
+        PD_CUDA_TRY(cudaGraphLaunch(g, c.s));
+        c.launches += gc[0];
+        c.solves += gc[1];
+        c.locals += gc[2];
+      }
+    }
+  }
+  for (; done < count; ++done) {
+    pd_status e = dir == 0 ? launch_fwd_iteration(c, prec, act) : launch_bwd_iteration(c, prec, xnext, act);
+    if (e != PD_OK) return e;
+  }
   return PD_OK;
 }
 
@@ -315,11 +427,14 @@ pd_status forward_step(Ctx& c, const double* act_t, const double* fext_int, doub
   int chunk = std::max(guess, 1);
   const int hard_cap = 3 * c.o.max_iter_fwd + 64;
   info = StepInfo{};
+  const double* act_c = nullptr;   // the step's actuation in the fixed buffer the graphs read
+  if (act_t) {
+    PD_CUDA_TRY(cudaMemcpyAsync(w.act_cur, act_t, sizeof(double) * m->h.e, cudaMemcpyDeviceToDevice, c.s));
+    act_c = w.act_cur;
+  }
   while (true) {
-    for (int k = 0; k < chunk; ++k) {
-      pd_status e = launch_fwd_iteration(c, prec, act_t);
-      if (e != PD_OK) return e;
-    }
+    pd_status er = run_iterations(c, 0, prec, act_c, nullptr, chunk);
+    if (er != PD_OK) return er;
     launched += chunk;
     if (mixed && prec == PD_PREC_FP64) fp64_launched += chunk;
     if (chunk > 0) {
@@ -340,7 +455,7 @@ pd_status forward_step(Ctx& c, const double* act_t, const double* fext_int, doub
         if (checks > kMaxChecks) prec = PD_PREC_FP64;
         force_accept_kernel<<<1, 1, 0, c.s>>>(w.st);
         copy_kernel<<<c.vb, 256, 0, c.s>>>(c.n3f, w.x, w.xt);
-        pd_status e2 = launch_fwd_iteration(c, PD_PREC_FP64, act_t);
+        pd_status e2 = launch_fwd_iteration(c, PD_PREC_FP64, act_c);
         if (e2 != PD_OK) return e2;
         fp64_launched += 1;
         mark_checked_kernel<<<1, 1, 0, c.s>>>(w.st);
@@ -449,11 +564,16 @@ pd_status backward_step(Ctx& c, const double* xnext, const double* xt_, const do
   int chunk = std::max(guess, 1);
   const int hard_cap = 3 * c.o.max_iter_bwd + 64;
   info = StepInfo{};
+  // the step's inputs in the fixed buffers the graphs read
+  PD_CUDA_TRY(cudaMemcpyAsync(w.xnext_cur, xnext, sizeof(double) * 3 * c.n, cudaMemcpyDeviceToDevice, c.s));
+  const double* act_c = nullptr;
+  if (act_t) {
+    PD_CUDA_TRY(cudaMemcpyAsync(w.act_cur, act_t, sizeof(double) * m->h.e, cudaMemcpyDeviceToDevice, c.s));
+    act_c = w.act_cur;
+  }
   while (true) {
-    for (int k = 0; k < chunk; ++k) {
-      pd_status e = launch_bwd_iteration(c, prec, xnext, act_t);
-      if (e != PD_OK) return e;
-    }
+    pd_status er = run_iterations(c, 1, prec, act_c, w.xnext_cur, chunk);
+    if (er != PD_OK) return er;
     launched += chunk;
     pd_status e = poll(c);
     if (e != PD_OK) return e;
@@ -659,18 +779,6 @@ pd_status pd_create_mesh(const pd_mesh_desc* desc, pd_mesh* out) {
       }
     }
   }
-  {
-    int dev = 0, sms = 0, occ = 1 << 20, o = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const void* ks[] = {(const void*)lbfgs_pre_fwd_kernel, (const void*)lbfgs_post_fwd_kernel,
-                        (const void*)lbfgs_pre_bwd_kernel, (const void*)lbfgs_post_bwd_kernel};
-    for (const void* k : ks) {
-      if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k, 256, 0)) != cudaSuccess) return fail(e);
-      occ = std::min(occ, o);
-    }
-    I.coop_blocks = std::max(1, sms * std::min(occ, 2));
-  }
   pd_status ws = ensure_workspace(&I, 5);
   if (ws != PD_OK) {
     pd_mesh_destroy(m);
@@ -686,6 +794,8 @@ void pd_mesh_destroy(pd_mesh m) {
   if (I.device >= 0) {
     DeviceGuard g(I.device);
     cudaDeviceSynchronize();
+    drop_iteration_graphs(&I);
+    if (I.cap_stream) cudaStreamDestroy(I.cap_stream);
     for (void* p : I.allocations) cudaFree(p);
     if (I.ws.st_host) cudaFreeHost(I.ws.st_host);
   }
@@ -795,6 +905,7 @@ pd_status pd_factorize(pd_mesh mesh, const double* w_corot, const double* w_vol,
   const int64_t nnz = I.h.factor_nnz();
   if (!I.Q64) PD_CUDA_TRY(dalloc(&I, &I.Q64, (size_t)nnz));
   if (I.precision == PD_PREC_MIXED && !I.Q32) PD_CUDA_TRY(dalloc(&I, &I.Q32, (size_t)nnz));
+  drop_iteration_graphs(&I);   // they captured the weights, panels and precision
   I.factorized = false;
   pd_status r = factorize_device(&I, s);
   if (r == PD_OK) I.factorized = true;
@@ -856,7 +967,9 @@ pd_status pd_forward(pd_mesh mesh, const double* x0, const double* v0, const dou
       tv = v_traj ? v_traj + (int64_t)((t + 1) / K) * 3 * n : nullptr;
     }
     StepInfo info;
+    const auto ts = std::chrono::steady_clock::now();
     pd_status e = forward_step(c, act_t, fext_int, mu, tx, tv, info, guess);
+    if (o.step_ms) o.step_ms[t] = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - ts).count();
     if (e != PD_OK) return e;
     accumulate(stats, info, true);
     if (!info.converged) all_ok = false;
@@ -982,9 +1095,12 @@ pd_status pd_backward(pd_mesh mesh, const double* x_traj, const double* v_traj, 
         kept_to_internal_kernel<<<grid_for(n), 256, 0, s>>>(n, m->kept_of_internal, v_traj + (int64_t)t * 3 * n, vt_int);
       }
       StepInfo info;
+      const auto ts = std::chrono::steady_clock::now();
       pd_status er = backward_step(c, xn_int, xt_int, vt_int, act_t, mu, loss_x(t), loss_v(t), gfext_int,
                                    g_w_corot, g_w_vol, g_w_muscle, g_act ? g_act + (int64_t)t * e : nullptr,
                                    g_mu, info, guess_b);
+      if (o.step_ms)
+        o.step_ms[t] += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - ts).count();
       if (er != PD_OK) return er;
       accumulate(stats, info, false);
       if (!info.converged) all_ok = false;

@@ -15,6 +15,13 @@ namespace pd {
 
 // ------------------------------------------------------------------ errors
 void set_error(const std::string& msg);
+
+// Mesh handles (abi.cu) as seen by the server: cap the persistent solve's CTAs
+// (takes effect from the next pd_forward / pd_backward / pd_solve_A call) and the
+// device bytes the mesh holds.
+void limit_solve_ctas(pd_mesh m, int ctas);
+int solve_ctas(pd_mesh m);
+size_t mesh_device_bytes(pd_mesh m);
 #define PD_CUDA_TRY(expr)                                                        \
   do {                                                                           \
     cudaError_t _e = (expr);                                                     \
@@ -56,7 +63,8 @@ struct alignas(16) SolveTile {
   int32_t pos;         // row_ptr[s]: start of its row structure / positions
   int32_t relp;        // rel_ptr[s]: start of its update-vector rows
   int32_t ntile;       // tiles in the output block
-  int32_t pad0, pad1;
+  int32_t pad0;        // tile kind: forward rows per tile / backward columns per tile
+  int32_t pad1;
 };
 struct SolveSchedule {
   std::vector<SolveTile> fwd, bwd;
@@ -83,6 +91,7 @@ struct Workspace {
   double *iox = nullptr, *iov = nullptr;      // kept-order staging
   void* elembuf = nullptr;                    // (8e x 3) T
   double* partials = nullptr;                 // block partial sums
+  double* lpart = nullptr;                    // L-BFGS inner products, per block
   unsigned int* counters = nullptr;           // last-block counters
   IterState* st = nullptr;                    // device iteration state
   IterState* st_host = nullptr;               // pinned mirror
@@ -90,7 +99,8 @@ struct Workspace {
   void* solve_u = nullptr;                    // (3 nf) T
   void* solve_W = nullptr;                    // (3 * below rows) T
   void* solve_partial = nullptr;              // per-tile partial sums
-  double* act_cur = nullptr;                  // unused placeholder for per-step actuation
+  double* act_cur = nullptr;                  // (e) actuation of the current step
+  double* xnext_cur = nullptr;                // (3n) x_{t+1} of the current adjoint step
   int lbfgs_m = 0;
   size_t bytes = 0;
 };
@@ -119,6 +129,13 @@ struct MeshImpl {
   // assembly map (device)
   int64_t *la_target = nullptr, *la_cptr = nullptr;
   int32_t *la_diag_node = nullptr, *la_contrib = nullptr;
+  // iteration chunks replayed as CUDA graphs: [forward/backward][precision index],
+  // captured on cap_stream with the per-step inputs read from ws.act_cur /
+  // ws.xnext_cur; dropped whenever a captured argument could change
+  cudaStream_t cap_stream = nullptr;
+  cudaGraphExec_t iter_graph[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
+  bool iter_graph_act[2][2] = {{false, false}, {false, false}};
+  int64_t iter_graph_counts[2][2][3] = {};   // kernels, solves, local steps per replay
   // material state
   bool factorized = false;
   int precision = PD_PREC_FP64;
@@ -129,7 +146,6 @@ struct MeshImpl {
   double* Q64 = nullptr;
   float* Q32 = nullptr;
   Workspace ws;
-  int coop_blocks = 0;        // co-resident blocks for the cooperative kernels
   std::vector<void*> allocations;
 };
 

@@ -19,7 +19,9 @@ struct IterState {
   double tol2;
   double c1;
   double noise;          // relative objective noise accepted by the Armijo test
-  double rho[kMaxHistory], al[kMaxHistory], be[kMaxHistory];
+  double rho[kMaxHistory], al[kMaxHistory], cf[kMaxHistory];
+  double sg[kMaxHistory];                // s_i . g at the current gradient
+  double SY[kMaxHistory][kMaxHistory];   // s_i . y_j of the stored pairs (ring slots)
   double aux;            // scalar accumulator (friction coefficient gradient)
   int m;                 // history capacity
   int head, count;

@@ -8,8 +8,6 @@
 // scheduling.
 #pragma once
 
-#include <cooperative_groups.h>
-
 #include "pd_internal.cuh"
 #include "pd_iter.cuh"
 
@@ -26,6 +24,8 @@ struct VecCtx {
   IterState* st;
   double* partials;
   unsigned* counter;
+  double* lpart;       // L-BFGS products: kMaxDots per block
+  unsigned* lcounter;
 };
 
 struct PredParams {
@@ -255,79 +255,127 @@ __global__ void decide_fwd_kernel(IterState* st, const double* energy_partials, 
 }
 
 // ---------------------------------------------------------------- L-BFGS
-// The two-loop recursion around A^-1 (Sec. 4, quasi-Newton acceleration) as two
-// cooperative kernels: the pre-solve kernel also commits the accepted forward
-// trial / applies the backward update, the post-solve kernel also forms the
-// direction.  One grid-wide barrier per reduction; every block sums the
-// per-block partials in the same fixed order (double-buffered partials).
-namespace cg = cooperative_groups;
-
-__device__ __forceinline__ double block_sum_bcast(double v) {
-  __shared__ double sh[kT / 32];
-  __shared__ double tot;
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-#pragma unroll
-  for (int off = 16; off >= 1; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
-  __syncthreads();
-  if (lane == 0) sh[w] = v;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double t = 0;
-    for (int i = 0; i < kT / 32; ++i) t += sh[i];
-    tot = t;
-  }
-  __syncthreads();
-  return tot;
-}
-
-__device__ __forceinline__ double grid_total(cg::grid_group& g, double part, double* bufs, int& which) {
-  const double b = block_sum_bcast(part);
-  double* buf = bufs + (size_t)which * gridDim.x;
-  if (threadIdx.x == 0) buf[blockIdx.x] = b;
-  g.sync();
-  double acc = 0;
-  for (int i = threadIdx.x; i < (int)gridDim.x; i += kT) acc += __ldcg(buf + i);
-  which ^= 1;
-  return block_sum_bcast(acc);
-}
+// The two-loop recursion around A^-1 (Sec. 4, quasi-Newton acceleration) in
+// compact form: every inner product of a loop is expressed through products
+// that do not depend on the loop's own updates,
+//   s_i . q_i = s_i . g - sum_{j newer than i} al_j (s_i . y_j)
+//   y_i . r_i = y_i . r0 + sum_{j older than i} (al_j - be_j) (s_j . y_i)
+// with the matrix SY_ij = s_i . y_j of the stored pairs kept on the device (one
+// new row and column per stored pair).  So each loop is one pass that forms the
+// products (a fixed-order reduction, below), a scalar recursion of m steps in
+// the last block, and one pass that combines the vectors:
+//   commit (+ products s_i . g, new SY entries) -> q = g - sum al_i y_i -> solve
+//   -> products y_i . r0, r0 . g -> d = -(r0 + sum (al_i - be_i) s_i)
+// The recursion visits the pairs in the order of the two-loop recursion, so the
+// result equals it up to rounding.
+constexpr int kMaxDots = 3 * kMaxHistory + 2;
 
 #define PD_FOR_MINE(i) \
   for (int64_t i = (int64_t)blockIdx.x * kT + threadIdx.x; i < n3; i += (int64_t)gridDim.x * kT)
 
-// first loop: q -= al_k y_k, al_k = rho_k s_k . q, newest -> oldest
-__device__ __forceinline__ void two_loop_first(cg::grid_group& g, IterState* st, int64_t n3, const double* S,
-                                               const double* Y, double* q, double* bufs, int& which) {
+// warp sum of one product into sh[k][warp]
+__device__ __forceinline__ void dot_to_shared(double v, double (*sh)[kT / 32], int k) {
+#pragma unroll
+  for (int off = 16; off >= 1; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+  if ((threadIdx.x & 31) == 0) sh[k][threadIdx.x >> 5] = v;
+}
+
+// Block sums of products 0..K-1 to partials; true (all threads) in the last
+// block to finish, with the grid totals in tot[0..K) summed in block order.
+__device__ bool finish_dots(int K, double (*sh)[kT / 32], double* partials, unsigned* counter, double* tot) {
+  __shared__ int is_last;
+  __syncthreads();
+  for (int k = threadIdx.x; k < K; k += kT) {
+    double t = 0;
+#pragma unroll
+    for (int w = 0; w < kT / 32; ++w) t += sh[k][w];
+    partials[(int64_t)blockIdx.x * kMaxDots + k] = t;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    is_last = atomicAdd(counter, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (!is_last) return false;
+  __threadfence();
+  // warp w sums products k = w, w + 8, ...; lane l the blocks l, l + 32, ...
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int k = warp; k < K; k += kT / 32) {
+    double t = 0;
+    for (int b = lane; b < (int)gridDim.x; b += 32) t += __ldcg(partials + (int64_t)b * kMaxDots + k);
+#pragma unroll
+    for (int off = 16; off >= 1; off >>= 1) t += __shfl_xor_sync(0xffffffffu, t, off);
+    if (lane == 0) tot[k] = t;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) *counter = 0u;
+  return true;
+}
+
+// products of the first loop: s_i . g over the stored pairs (newest first) and,
+// after a push into `slot`, s_i . y_slot and s_slot . y_i
+__device__ __forceinline__ int first_loop_dots(const IterState* st, int64_t n3, const double* S, const double* Y,
+                                               const double* g, bool push, int slot, double (*sh)[kT / 32],
+                                               int k0) {
   const int cnt = st->count;
+  int K = k0;
   for (int k = 0; k < cnt; ++k) {
-    const int i = idx_newest(st, k);
-    double part = 0;
-    PD_FOR_MINE(e) part += S[(int64_t)i * n3 + e] * q[e];
-    const double al = st->rho[i] * grid_total(g, part, bufs, which);
-    if (blockIdx.x == 0 && threadIdx.x == 0) st->al[i] = al;
-    PD_FOR_MINE(e) q[e] -= al * Y[(int64_t)i * n3 + e];
+    const double* Si = S + (int64_t)idx_newest(st, k) * n3;
+    double v = 0;
+    PD_FOR_MINE(e) v += Si[e] * g[e];
+    dot_to_shared(v, sh, K++);
+  }
+  if (push) {
+    const double* Ss = S + (int64_t)slot * n3;
+    const double* Ys = Y + (int64_t)slot * n3;
+    for (int k = 0; k < cnt; ++k) {
+      const int i = idx_newest(st, k);
+      const double* Si = S + (int64_t)i * n3;
+      const double* Yi = Y + (int64_t)i * n3;
+      double a = 0, b = 0;
+      PD_FOR_MINE(e) {
+        a += Si[e] * Ys[e];
+        b += Ss[e] * Yi[e];
+      }
+      dot_to_shared(a, sh, K++);
+      dot_to_shared(b, sh, K++);
+    }
+  }
+  return K;
+}
+
+// last block, one thread: store the products (s_i . g and the new SY entries)
+__device__ __forceinline__ void store_products(IterState* st, const double* tot, bool push, int slot) {
+  const int cnt = st->count;
+  for (int k = 0; k < cnt; ++k) st->sg[idx_newest(st, k)] = tot[k];
+  if (push) {
+    for (int k = 0; k < cnt; ++k) {
+      const int i = idx_newest(st, k);
+      st->SY[i][slot] = tot[cnt + 2 * k];
+      st->SY[slot][i] = tot[cnt + 2 * k + 1];
+    }
   }
 }
 
-// second loop: be_k = rho_k y_k . r, r += s_k (al_k - be_k), oldest -> newest.
-// al_k was written by block 0 in the pre-solve kernel (an earlier launch).
-__device__ __forceinline__ void two_loop_second(cg::grid_group& g, IterState* st, int64_t n3, const double* S,
-                                                const double* Y, double* r, double* bufs, int& which) {
+// last block, one thread: al_i newest -> oldest
+__device__ __forceinline__ void first_loop_coefficients(IterState* st) {
   const int cnt = st->count;
   for (int k = 0; k < cnt; ++k) {
-    const int j = idx_oldest(st, k);
-    double part = 0;
-    PD_FOR_MINE(e) part += Y[(int64_t)j * n3 + e] * r[e];
-    const double be = st->rho[j] * grid_total(g, part, bufs, which);
-    const double coef = st->al[j] - be;
-    PD_FOR_MINE(e) r[e] += coef * S[(int64_t)j * n3 + e];
+    const int i = idx_newest(st, k);
+    double acc = st->sg[i];
+    for (int kk = 0; kk < k; ++kk) {
+      const int j = idx_newest(st, kk);
+      acc -= st->al[j] * st->SY[i][j];
+    }
+    st->al[i] = st->rho[i] * acc;
   }
 }
 
 // forward, before the solve: commit an accepted trial (history pair, x, grad),
-// then q = grad and the first loop
-__global__ void lbfgs_pre_fwd_kernel(VecCtx c, double* x, const double* xt, double* grad, const double* gradt,
-                                     double* q, double* S, double* Y) {
-  cg::grid_group g = cg::this_grid();
+// then the first-loop products and coefficients
+__global__ void __launch_bounds__(kT) lbfgs_commit_fwd_kernel(VecCtx c, double* x, const double* xt, double* grad,
+                                                             const double* gradt, double* S, double* Y) {
   IterState* st = c.st;
   if (!st->accepted) return;
   const int64_t n3 = c.n3;
@@ -340,54 +388,35 @@ __global__ void lbfgs_pre_fwd_kernel(VecCtx c, double* x, const double* xt, doub
     }
     x[e] = xn;
     grad[e] = gn;
-    q[e] = gn;
   }
-  if (st->converged) return;
-  int which = 0;
-  two_loop_first(g, st, n3, S, Y, q, c.partials, which);
-}
-
-// forward, after the solve: second loop, d = -r, trial xt = x + d, slope = d.grad;
-// after a rejected trial only xt = x + alpha d
-__global__ void lbfgs_post_fwd_kernel(VecCtx c, const double* S, const double* Y, double* r, double* d,
-                                      const double* grad, const double* x, double* xt) {
-  cg::grid_group g = cg::this_grid();
-  IterState* st = c.st;
-  if (st->converged) return;
-  const int64_t n3 = c.n3;
-  if (!st->accepted) {
-    const double a = st->alpha;
-    PD_FOR_MINE(e) xt[e] = x[e] + a * d[e];
-    return;
-  }
-  int which = 0;
-  two_loop_second(g, st, n3, S, Y, r, c.partials, which);
-  double part = 0;
-  PD_FOR_MINE(e) {
-    const double de = -r[e];
-    d[e] = de;
-    xt[e] = x[e] + de;
-    part += de * grad[e];
-  }
-  const double slope = grid_total(g, part, c.partials, which);
-  if (blockIdx.x == 0 && threadIdx.x == 0) st->slope = slope;
+  // a converged solve still records the new pair's products (history kept for the next step)
+  const bool conv = st->converged;
+  if (conv && !push) return;
+  __shared__ double sh[kMaxDots][kT / 32];
+  __shared__ double tot[kMaxDots];
+  const int K = first_loop_dots(st, n3, S, Y, grad, push != 0, slot, sh, 0);
+  if (!finish_dots(K, sh, c.lpart, c.lcounter, tot)) return;
+  if (threadIdx.x != 0) return;
+  store_products(st, tot, push != 0, slot);
+  if (!conv) first_loop_coefficients(st);
 }
 
 // backward, before the solve: apply the previous step z += alpha d,
-// gs += alpha Hd (history pair alpha (d, Hd)), convergence test on |gs|, q = gs,
-// first loop.  The first iteration of a step has no previous direction.
-__global__ void lbfgs_pre_bwd_kernel(VecCtx c, const double* d, const double* Hd, double* z, double* gs,
-                                     double* q, double* S, double* Y) {
-  cg::grid_group g = cg::this_grid();
+// gs += alpha Hd (history pair alpha (d, Hd)) and test |gs| for convergence;
+// then the first-loop products and coefficients.  The first iteration of a step
+// (or the one after a residual replacement) has no step to apply.
+__global__ void __launch_bounds__(kT) lbfgs_commit_bwd_kernel(VecCtx c, const double* d, const double* Hd, double* z,
+                                                             double* gs, double* S, double* Y) {
   IterState* st = c.st;
   if (st->converged) return;
   const int64_t n3 = c.n3;
-  int which = 0;
-  if (st->pending) {
+  const int pending = st->pending;
+  const int push = pending ? st->push : 0, slot = st->pslot;
+  __shared__ double sh[kMaxDots][kT / 32];
+  __shared__ double tot[kMaxDots];
+  int K0 = 0;
+  if (pending) {
     const double a = st->alpha;
-    const int push = st->push, slot = st->pslot;
-    const double tol2 = st->tol2, ref2 = st->ref2;
-    const int iters = st->iters + 1, max_iter = st->max_iter;
     double part = 0;
     PD_FOR_MINE(e) {
       const double ad = a * d[e], ah = a * Hd[e];
@@ -400,42 +429,103 @@ __global__ void lbfgs_pre_bwd_kernel(VecCtx c, const double* d, const double* Hd
       }
       part += gn * gn;
     }
-    const double gn2 = grid_total(g, part, c.partials, which);
-    const bool conv = gn2 <= tol2 * ref2;
-    const bool cap = !conv && iters >= max_iter;
-    g.sync();   // every block has read st before block 0 updates it
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
-      st->gn2_acc = gn2;
-      st->iters = iters;
-      st->pending = 0;
-      if (conv || cap) {
-        st->converged = 1;
-        st->hit_max = cap ? 1 : 0;
-      }
-    }
-    if (conv || cap) return;
+    dot_to_shared(part, sh, 0);
+    K0 = 1;
   }
-  PD_FOR_MINE(e) q[e] = gs[e];
-  two_loop_first(g, st, n3, S, Y, q, c.partials, which);
+  const int K = first_loop_dots(st, n3, S, Y, gs, push != 0, slot, sh, K0);
+  if (!finish_dots(K, sh, c.lpart, c.lcounter, tot)) return;
+  if (threadIdx.x != 0) return;
+  store_products(st, tot + K0, push != 0, slot);
+  if (pending) {
+    const double gn2 = tot[0];
+    const bool conv = gn2 <= st->tol2 * st->ref2;
+    st->iters += 1;
+    const bool cap = !conv && st->iters >= st->max_iter;
+    st->gn2_acc = gn2;
+    st->pending = 0;
+    if (conv || cap) {
+      st->converged = 1;
+      st->hit_max = cap ? 1 : 0;
+      return;
+    }
+  }
+  first_loop_coefficients(st);
 }
 
-// backward, after the solve: second loop, d = -r, slope = d.gs
-__global__ void lbfgs_post_bwd_kernel(VecCtx c, const double* S, const double* Y, double* r, double* d,
-                                      const double* gs) {
-  cg::grid_group g = cg::this_grid();
+// q = g - sum al_i y_i (newest first, as the first loop subtracts them)
+__global__ void __launch_bounds__(kT) lbfgs_q_kernel(VecCtx c, const double* g, const double* Y, double* q) {
+  const IterState* st = c.st;
+  if (st->converged || !st->accepted) return;
+  const int64_t n3 = c.n3;
+  const int cnt = st->count;
+  PD_FOR_MINE(e) {
+    double v = g[e];
+    for (int k = 0; k < cnt; ++k) {
+      const int i = idx_newest(st, k);
+      v -= st->al[i] * Y[(int64_t)i * n3 + e];
+    }
+    q[e] = v;
+  }
+}
+
+// after the solve r0 = A^-1 q: products y_i . r0 and r0 . g, then be_i oldest ->
+// newest, the coefficients cf_i = al_i - be_i and the slope d . g of
+// d = -(r0 + sum cf_i s_i)
+__global__ void __launch_bounds__(kT) lbfgs_post_dots_kernel(VecCtx c, const double* g, const double* Y,
+                                                            const double* r) {
   IterState* st = c.st;
+  if (st->converged || !st->accepted) return;
+  const int64_t n3 = c.n3;
+  const int cnt = st->count;
+  __shared__ double sh[kMaxDots][kT / 32];
+  __shared__ double tot[kMaxDots];
+  for (int k = 0; k < cnt; ++k) {
+    const double* Yi = Y + (int64_t)idx_oldest(st, k) * n3;
+    double v = 0;
+    PD_FOR_MINE(e) v += Yi[e] * r[e];
+    dot_to_shared(v, sh, k);
+  }
+  double v = 0;
+  PD_FOR_MINE(e) v += r[e] * g[e];
+  dot_to_shared(v, sh, cnt);
+  if (!finish_dots(cnt + 1, sh, c.lpart, c.lcounter, tot)) return;
+  if (threadIdx.x != 0) return;
+  double slope = tot[cnt];
+  for (int k = 0; k < cnt; ++k) {
+    const int i = idx_oldest(st, k);
+    double acc = tot[k];
+    for (int kk = 0; kk < k; ++kk) {
+      const int j = idx_oldest(st, kk);
+      acc += st->cf[j] * st->SY[j][i];
+    }
+    st->cf[i] = st->al[i] - st->rho[i] * acc;
+    slope += st->cf[i] * st->sg[i];
+  }
+  st->slope = -slope;
+}
+
+// d = -(r0 + sum cf_i s_i) (oldest first, as the second loop adds them); forward:
+// trial xt = x + d, or xt = x + alpha d after a rejected trial
+__global__ void __launch_bounds__(kT) lbfgs_dir_kernel(VecCtx c, const double* S, const double* r, double* d,
+                                                      const double* x, double* xt) {
+  const IterState* st = c.st;
   if (st->converged) return;
   const int64_t n3 = c.n3;
-  int which = 0;
-  two_loop_second(g, st, n3, S, Y, r, c.partials, which);
-  double part = 0;
-  PD_FOR_MINE(e) {
-    const double de = -r[e];
-    d[e] = de;
-    part += de * gs[e];
+  if (!st->accepted) {
+    const double a = st->alpha;
+    if (xt) PD_FOR_MINE(e) xt[e] = x[e] + a * d[e];
+    return;
   }
-  const double slope = grid_total(g, part, c.partials, which);
-  if (blockIdx.x == 0 && threadIdx.x == 0) st->slope = slope;
+  const int cnt = st->count;
+  PD_FOR_MINE(e) {
+    double v = r[e];
+    for (int k = 0; k < cnt; ++k) {
+      const int j = idx_oldest(st, k);
+      v += st->cf[j] * S[(int64_t)j * n3 + e];
+    }
+    d[e] = -v;
+    if (xt) xt[e] = x[e] - v;
+  }
 }
 #undef PD_FOR_MINE
 

@@ -61,3 +61,19 @@ def test_invalid_arguments_are_rejected(native):
     st = native.lib().pd_factorize(m.handle, None, None, None, None, None, None)
     assert st == N.PD_ERR_NO_DEVICE
     m.close()
+
+
+def test_serve_create_rejects_bad_arguments(native):
+    import ctypes
+    import torch
+    from paper_2101_05917_gb300 import _native as N
+    L = native.lib()
+    h = ctypes.c_void_p()
+    assert L.pd_serve_create(0, 1 << 30, 0, ctypes.byref(h)) == N.PD_ERR_INVALID_ARG
+    assert L.pd_serve_create(0, 1 << 30, 65, ctypes.byref(h)) == N.PD_ERR_INVALID_ARG
+    assert not h.value
+    if not torch.cuda.is_available():
+        assert L.pd_serve_create(0, 1 << 30, 2, ctypes.byref(h)) == N.PD_ERR_NO_DEVICE
+        assert not h.value
+    assert L.pd_serve_submit(None, None, None) == N.PD_ERR_INVALID_ARG
+    assert L.pd_serve_drain(None) == N.PD_ERR_INVALID_ARG
