@@ -48,6 +48,10 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--T", type=int, default=100, help="simulation steps per rollout")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--serve", action="store_true",
+                    help="serving workload instead: quadruped requests under Poisson arrivals")
+    ap.add_argument("--serve-requests", type=int, default=24)
+    ap.add_argument("--serve-slots", type=int, default=8)
     return ap.parse_args()
 
 
@@ -216,8 +220,8 @@ def run_ours(args):
     stream = torch.cuda.current_stream()
     want = ("w_corot", "w_vol", "v0")
 
-    def rollout(profile):
-        opts = api.solver_opts(tol_fwd=TOL_FWD, tol_bwd=TOL_BWD, profile=profile)
+    def rollout(profile, step_ms=None):
+        opts = api.solver_opts(tol_fwd=TOL_FWD, tol_bwd=TOL_BWD, profile=profile, step_ms=step_ms)
         roll = mesh.forward(x0, v0, T, opts=opts)
         g = mesh.backward(roll, T, lw, opts=opts, want=want)
         return roll, g
@@ -234,11 +238,13 @@ def run_ours(args):
     flush.fill_(1.0)
     torch.cuda.synchronize()
     ev0.record(stream)
-    fstats, bstats, per_rollout = [], [], []
+    fstats, bstats, per_rollout, step_lat = [], [], [], []
     for k in range(args.steps):
         h0 = time.perf_counter()
-        roll, g = rollout(True)
+        sm = np.zeros(T)
+        roll, g = rollout(True, sm)
         per_rollout.append(time.perf_counter() - h0)
+        step_lat.append(sm)
         fstats.append(roll.stats)
         bstats.append(g["stats"])
         flush.fill_(float(k))   # evict the factor panels between timed rollouts
@@ -270,6 +276,7 @@ def run_ours(args):
         with open(traffic_path) as f:
             traffic = json.load(f).get("bytes_per_solve")
     launches = sum(s["kernel_launches"] for s in fstats + bstats)
+    lat = np.concatenate(step_lat)   # host wall time of each step, forward + adjoint
     fwd_it = sum(s["fwd_iters"] for s in fstats) / (args.steps * T)
     bwd_it = sum(s["bwd_iters"] for s in bstats) / (args.steps * T)
 
@@ -318,6 +325,9 @@ def run_ours(args):
                          "frac": achieved / peak, "traffic": traffic,
                          "bytes_per_launch": bytes_solve, "avg_solve_us": 1e6 * t_solve, "solves": solves},
             "local_step": {"avg_us": 1e3 * local_ms / max(locals_, 1), "launches": locals_},
+            "step_latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
+                                "max": float(lat.max()), "steps": int(lat.size),
+                                "what": "host wall time of one simulation step, forward + adjoint"},
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": "steps/s", "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h, "includes": "H2D inputs, factorisation, forward, backward, D2H"},
@@ -330,10 +340,70 @@ def run_ours(args):
         torch.distributed.destroy_process_group()
 
 
+def run_serve(args):
+    """Rollout-plus-gradient serving: quadruped requests (N^3 box, N ~ U{8..24},
+    T steps, muscle actuation, ground contact with friction) arriving as a Poisson
+    stream at twice the serial service rate of a calibration pass; requests/s and
+    request latency percentiles."""
+    import numpy as np
+    from paper_2101_05917_gb300 import build as _build
+    _build.build()
+    from paper_2101_05917_gb300 import api
+    from paper_2101_05917_gb300 import _native as N
+    from workloads import quadruped, serving_stream_c4
+
+    T = args.T
+    n_req = args.serve_requests
+    _, sizes = serving_stream_c4(n_requests=n_req, rate_hz=1.0, T=T)
+    scenes = [quadruped(int(Nn), T=T, request=i) for i, Nn in enumerate(sizes)]
+    opts = api.solver_opts(tol_fwd=scenes[0].tol_fwd, tol_bwd=scenes[0].tol_bwd, max_iter_fwd=3000,
+                           max_iter_bwd=3000)
+    srv = api.PDServer(max_slots=args.serve_slots)
+    # calibration: the first three requests one at a time (meshes and factors enter the caches)
+    serial = []
+    for sc in scenes[:3]:
+        r = srv.result(srv.submit_scene(sc, opts=opts))
+        serial.append(r["latency_ms"] / 1e3)
+    rate = 2.0 / statistics.mean(serial)
+    gaps, _ = serving_stream_c4(n_requests=n_req, rate_hz=rate, T=T)
+    arrivals = gaps
+    t0 = time.perf_counter()
+    tickets, done = [], {}
+    for i, sc in enumerate(scenes):
+        while time.perf_counter() - t0 < arrivals[i]:
+            time.sleep(0.0005)
+        tickets.append(srv.submit_scene(sc, opts=opts))
+    for t in tickets:
+        done[t] = srv.result(t)
+    wall = time.perf_counter() - t0
+    srv.close()
+    lat = np.array([done[t]["latency_ms"] for t in tickets])
+    q = np.array([done[t]["queue_ms"] for t in tickets])
+    ok = sum(1 for t in tickets if done[t]["status"] in (N.PD_OK, N.PD_ERR_NOT_CONVERGED))
+    line = {
+        "metric": "rollout+gradient requests/s under Poisson arrivals; p50/p99 request latency",
+        "value": n_req / wall, "unit": "requests/s", "n_gpus": 1, "higher_is_better": True,
+        "dtype": "mixed-f32-f64", "data": "synthetic",
+        "config": {"workload": f"c4_quadruped_stream_T{T}", "requests": n_req, "sizes": [int(x) for x in sizes],
+                   "arrival_rate_hz": rate, "serial_service_s": serial, "slots": args.serve_slots,
+                   "tol_fwd": scenes[0].tol_fwd, "tol_bwd": scenes[0].tol_bwd},
+        "sim_steps_per_s": n_req * T / wall,
+        "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
+                       "max": float(lat.max())},
+        "queue_ms": {"p50": float(np.percentile(q, 50)), "p99": float(np.percentile(q, 99))},
+        "fwd_iters_per_step": float(np.mean([done[t]["fwd_iters"] for t in tickets]) / T),
+        "bwd_iters_per_step": float(np.mean([done[t]["bwd_iters"] for t in tickets]) / T),
+        "completed": ok,
+    }
+    print(json.dumps(line))
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.serve:
+        run_serve(args)
     else:
         run_ours(args)
 

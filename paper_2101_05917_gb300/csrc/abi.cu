@@ -195,6 +195,7 @@ struct Ctx {
   pd_solver_opts o;
   int64_t n, nf, n3f;
   int vb;          // vector kernel blocks
+  int mx;          // compile-time bound of the L-BFGS history (2, 4, 8, 16)
   bool graphs;     // replay iteration chunks as CUDA graphs
   VecCtx vc;
   double* pe;      // energy partials
@@ -211,6 +212,7 @@ Ctx make_ctx(MeshImpl* m, cudaStream_t s, const pd_solver_opts& o) {
   c.nf = m->h.nf;
   c.n3f = 3 * m->h.nf;
   c.vb = vec_blocks(c.n3f);
+  c.mx = lbfgs_bound(o.lbfgs_m);
   c.graphs = !o.profile && !o.no_graphs;
   c.vc.n3 = c.n3f;
   c.vc.st = m->ws.st;
@@ -231,6 +233,27 @@ pd_status poll(Ctx& c) {
   return PD_OK;
 }
 
+// runs the statement with the constant MX bound to the context's history bound
+#define PD_WITH_MX(mx, ...)          \
+  switch (mx) {                      \
+    case 2: {                        \
+      constexpr int MX = 2;          \
+      __VA_ARGS__;                   \
+    } break;                         \
+    case 4: {                        \
+      constexpr int MX = 4;          \
+      __VA_ARGS__;                   \
+    } break;                         \
+    case 8: {                        \
+      constexpr int MX = 8;          \
+      __VA_ARGS__;                   \
+    } break;                         \
+    default: {                       \
+      constexpr int MX = 16;         \
+      __VA_ARGS__;                   \
+    } break;                         \
+  }
+
 // one forward iteration: evaluate the trial point, decide, commit and the
 // next direction (two-loop recursion around the global solve)
 pd_status launch_fwd_iteration(Ctx& c, int prec, const double* act_t) {
@@ -243,13 +266,13 @@ pd_status launch_fwd_iteration(Ctx& c, int prec, const double* act_t) {
   if (c.local_t) c.local_t->record(c.s);
   PD_CUDA_TRY(launch_gather_grad(m, st, w.elembuf, prec, w.xt, w.y, w.dir, w.gradt, c.pg, c.s));
   decide_fwd_kernel<<<1, 256, 0, c.s>>>(st, c.pe, c.nbe, c.pg, c.nbg);
-  lbfgs_commit_fwd_kernel<<<c.vb, 256, 0, c.s>>>(c.vc, w.x, w.xt, w.grad, w.gradt, w.S, w.Y);
-  lbfgs_q_kernel<<<c.vb, 256, 0, c.s>>>(c.vc, w.grad, w.Y, w.q);
+  PD_WITH_MX(c.mx, lbfgs_commit_fwd_kernel<MX><<<c.vb, 256, 0, c.s>>>(c.vc, w.x, w.xt, w.grad, w.gradt, w.S, w.Y));
+  PD_WITH_MX(c.mx, lbfgs_q_kernel<MX><<<c.vb, 256, 0, c.s>>>(c.vc, w.grad, w.Y, w.q));
   if (c.solve_t) c.solve_t->record(c.s);
   PD_CUDA_TRY(solve_A(m, st, w.q, w.r, m->precision, c.s));
   if (c.solve_t) c.solve_t->record(c.s);
-  lbfgs_post_dots_kernel<<<c.vb, 256, 0, c.s>>>(c.vc, w.grad, w.Y, w.r);
-  lbfgs_dir_kernel<<<c.vb, 256, 0, c.s>>>(c.vc, w.S, w.r, w.dir, w.x, w.xt);
+  PD_WITH_MX(c.mx, lbfgs_post_dots_kernel<MX><<<c.vb, 256, 0, c.s>>>(c.vc, w.grad, w.Y, w.r));
+  PD_WITH_MX(c.mx, lbfgs_dir_kernel<MX><<<c.vb, 256, 0, c.s>>>(c.vc, w.S, w.r, w.dir, w.x, w.xt));
   c.launches += 9;
   c.solves += 1;
   c.locals += 1;
@@ -263,13 +286,13 @@ pd_status launch_bwd_iteration(Ctx& c, int prec, const double* xnext, const doub
   MeshImpl* m = c.m;
   Workspace& w = m->ws;
   IterState* st = w.st;
-  lbfgs_commit_bwd_kernel<<<c.vb, 256, 0, c.s>>>(c.vc, w.dir, w.Hd, w.z, w.gs, w.S, w.Y);
-  lbfgs_q_kernel<<<c.vb, 256, 0, c.s>>>(c.vc, w.gs, w.Y, w.q);
+  PD_WITH_MX(c.mx, lbfgs_commit_bwd_kernel<MX><<<c.vb, 256, 0, c.s>>>(c.vc, w.dir, w.Hd, w.z, w.gs, w.S, w.Y));
+  PD_WITH_MX(c.mx, lbfgs_q_kernel<MX><<<c.vb, 256, 0, c.s>>>(c.vc, w.gs, w.Y, w.q));
   if (c.solve_t) c.solve_t->record(c.s);
   PD_CUDA_TRY(solve_A(m, st, w.q, w.r, m->precision, c.s));
   if (c.solve_t) c.solve_t->record(c.s);
-  lbfgs_post_dots_kernel<<<c.vb, 256, 0, c.s>>>(c.vc, w.gs, w.Y, w.r);
-  lbfgs_dir_kernel<<<c.vb, 256, 0, c.s>>>(c.vc, w.S, w.r, w.dir, nullptr, nullptr);
+  PD_WITH_MX(c.mx, lbfgs_post_dots_kernel<MX><<<c.vb, 256, 0, c.s>>>(c.vc, w.gs, w.Y, w.r));
+  PD_WITH_MX(c.mx, lbfgs_dir_kernel<MX><<<c.vb, 256, 0, c.s>>>(c.vc, w.S, w.r, w.dir, nullptr, nullptr));
   c.launches += 9;
   c.solves += 1;
   LocalArgs la{m, st, xnext, w.dir, act_t, prec};

@@ -261,13 +261,15 @@ __global__ void decide_fwd_kernel(IterState* st, const double* energy_partials, 
 //   s_i . q_i = s_i . g - sum_{j newer than i} al_j (s_i . y_j)
 //   y_i . r_i = y_i . r0 + sum_{j older than i} (al_j - be_j) (s_j . y_i)
 // with the matrix SY_ij = s_i . y_j of the stored pairs kept on the device (one
-// new row and column per stored pair).  So each loop is one pass that forms the
-// products (a fixed-order reduction, below), a scalar recursion of m steps in
-// the last block, and one pass that combines the vectors:
+// new row and column per stored pair).  So each loop is one pass that forms all
+// its products at once (every thread loads an entry of every history vector
+// together, then a fixed-order reduction), a scalar recursion of m steps in the
+// last block, and one pass that combines the vectors:
 //   commit (+ products s_i . g, new SY entries) -> q = g - sum al_i y_i -> solve
 //   -> products y_i . r0, r0 . g -> d = -(r0 + sum (al_i - be_i) s_i)
 // The recursion visits the pairs in the order of the two-loop recursion, so the
-// result equals it up to rounding.
+// result equals it up to rounding.  MX is a compile-time bound on the history
+// length (2, 4, 8 or 16) so that the per-pair accumulators live in registers.
 constexpr int kMaxDots = 3 * kMaxHistory + 2;
 
 #define PD_FOR_MINE(i) \
@@ -313,33 +315,59 @@ __device__ bool finish_dots(int K, double (*sh)[kT / 32], double* partials, unsi
   return true;
 }
 
-// products of the first loop: s_i . g over the stored pairs (newest first) and,
-// after a push into `slot`, s_i . y_slot and s_slot . y_i
+// ring slots newest first / oldest first (uniform over the grid)
+template <int MX>
+__device__ __forceinline__ void ring_newest(const IterState* st, int* idx) {
+#pragma unroll
+  for (int k = 0; k < MX; ++k) idx[k] = k < st->count ? idx_newest(st, k) : 0;
+}
+template <int MX>
+__device__ __forceinline__ void ring_oldest(const IterState* st, int* idx) {
+#pragma unroll
+  for (int k = 0; k < MX; ++k) idx[k] = k < st->count ? idx_oldest(st, k) : 0;
+}
+
+// Products of the first loop at gradient g: s_i . g over the stored pairs (newest
+// first) and, after a push into `slot`, s_i . y_slot and s_slot . y_i; written to
+// sh[k0 ...] in that order.  Returns the number of products.
+template <int MX>
 __device__ __forceinline__ int first_loop_dots(const IterState* st, int64_t n3, const double* S, const double* Y,
                                                const double* g, bool push, int slot, double (*sh)[kT / 32],
                                                int k0) {
   const int cnt = st->count;
-  int K = k0;
-  for (int k = 0; k < cnt; ++k) {
-    const double* Si = S + (int64_t)idx_newest(st, k) * n3;
-    double v = 0;
-    PD_FOR_MINE(e) v += Si[e] * g[e];
-    dot_to_shared(v, sh, K++);
-  }
-  if (push) {
-    const double* Ss = S + (int64_t)slot * n3;
-    const double* Ys = Y + (int64_t)slot * n3;
-    for (int k = 0; k < cnt; ++k) {
-      const int i = idx_newest(st, k);
-      const double* Si = S + (int64_t)i * n3;
-      const double* Yi = Y + (int64_t)i * n3;
-      double a = 0, b = 0;
-      PD_FOR_MINE(e) {
-        a += Si[e] * Ys[e];
-        b += Ss[e] * Yi[e];
+  int idx[MX];
+  ring_newest<MX>(st, idx);
+  double sg[MX], a[MX], b[MX];
+#pragma unroll
+  for (int k = 0; k < MX; ++k) sg[k] = a[k] = b[k] = 0.0;
+  const double* Ss = S + (int64_t)slot * n3;
+  const double* Ys = Y + (int64_t)slot * n3;
+  PD_FOR_MINE(e) {
+    const double ge = g[e];
+    const double ss = push ? Ss[e] : 0.0, ys = push ? Ys[e] : 0.0;
+#pragma unroll
+    for (int k = 0; k < MX; ++k) {
+      if (k < cnt) {
+        const double si = S[(int64_t)idx[k] * n3 + e];
+        sg[k] += si * ge;
+        if (push) {
+          a[k] += si * ys;
+          b[k] += ss * Y[(int64_t)idx[k] * n3 + e];
+        }
       }
-      dot_to_shared(a, sh, K++);
-      dot_to_shared(b, sh, K++);
+    }
+  }
+  int K = k0;
+#pragma unroll
+  for (int k = 0; k < MX; ++k)
+    if (k < cnt) dot_to_shared(sg[k], sh, K++);
+  if (push) {
+#pragma unroll
+    for (int k = 0; k < MX; ++k) {
+      if (k < cnt) {
+        dot_to_shared(a[k], sh, K++);
+        dot_to_shared(b[k], sh, K++);
+      }
     }
   }
   return K;
@@ -374,6 +402,7 @@ __device__ __forceinline__ void first_loop_coefficients(IterState* st) {
 
 // forward, before the solve: commit an accepted trial (history pair, x, grad),
 // then the first-loop products and coefficients
+template <int MX>
 __global__ void __launch_bounds__(kT) lbfgs_commit_fwd_kernel(VecCtx c, double* x, const double* xt, double* grad,
                                                              const double* gradt, double* S, double* Y) {
   IterState* st = c.st;
@@ -394,7 +423,7 @@ __global__ void __launch_bounds__(kT) lbfgs_commit_fwd_kernel(VecCtx c, double* 
   if (conv && !push) return;
   __shared__ double sh[kMaxDots][kT / 32];
   __shared__ double tot[kMaxDots];
-  const int K = first_loop_dots(st, n3, S, Y, grad, push != 0, slot, sh, 0);
+  const int K = first_loop_dots<MX>(st, n3, S, Y, grad, push != 0, slot, sh, 0);
   if (!finish_dots(K, sh, c.lpart, c.lcounter, tot)) return;
   if (threadIdx.x != 0) return;
   store_products(st, tot, push != 0, slot);
@@ -405,6 +434,7 @@ __global__ void __launch_bounds__(kT) lbfgs_commit_fwd_kernel(VecCtx c, double* 
 // gs += alpha Hd (history pair alpha (d, Hd)) and test |gs| for convergence;
 // then the first-loop products and coefficients.  The first iteration of a step
 // (or the one after a residual replacement) has no step to apply.
+template <int MX>
 __global__ void __launch_bounds__(kT) lbfgs_commit_bwd_kernel(VecCtx c, const double* d, const double* Hd, double* z,
                                                              double* gs, double* S, double* Y) {
   IterState* st = c.st;
@@ -432,7 +462,7 @@ __global__ void __launch_bounds__(kT) lbfgs_commit_bwd_kernel(VecCtx c, const do
     dot_to_shared(part, sh, 0);
     K0 = 1;
   }
-  const int K = first_loop_dots(st, n3, S, Y, gs, push != 0, slot, sh, K0);
+  const int K = first_loop_dots<MX>(st, n3, S, Y, gs, push != 0, slot, sh, K0);
   if (!finish_dots(K, sh, c.lpart, c.lcounter, tot)) return;
   if (threadIdx.x != 0) return;
   store_products(st, tot + K0, push != 0, slot);
@@ -453,17 +483,25 @@ __global__ void __launch_bounds__(kT) lbfgs_commit_bwd_kernel(VecCtx c, const do
 }
 
 // q = g - sum al_i y_i (newest first, as the first loop subtracts them)
+template <int MX>
 __global__ void __launch_bounds__(kT) lbfgs_q_kernel(VecCtx c, const double* g, const double* Y, double* q) {
   const IterState* st = c.st;
   if (st->converged || !st->accepted) return;
   const int64_t n3 = c.n3;
   const int cnt = st->count;
+  int idx[MX];
+  double al[MX];
+  ring_newest<MX>(st, idx);
+#pragma unroll
+  for (int k = 0; k < MX; ++k) al[k] = k < cnt ? st->al[idx[k]] : 0.0;
   PD_FOR_MINE(e) {
+    double yv[MX];
+#pragma unroll
+    for (int k = 0; k < MX; ++k) yv[k] = k < cnt ? Y[(int64_t)idx[k] * n3 + e] : 0.0;
     double v = g[e];
-    for (int k = 0; k < cnt; ++k) {
-      const int i = idx_newest(st, k);
-      v -= st->al[i] * Y[(int64_t)i * n3 + e];
-    }
+#pragma unroll
+    for (int k = 0; k < MX; ++k)
+      if (k < cnt) v -= al[k] * yv[k];
     q[e] = v;
   }
 }
@@ -471,6 +509,7 @@ __global__ void __launch_bounds__(kT) lbfgs_q_kernel(VecCtx c, const double* g, 
 // after the solve r0 = A^-1 q: products y_i . r0 and r0 . g, then be_i oldest ->
 // newest, the coefficients cf_i = al_i - be_i and the slope d . g of
 // d = -(r0 + sum cf_i s_i)
+template <int MX>
 __global__ void __launch_bounds__(kT) lbfgs_post_dots_kernel(VecCtx c, const double* g, const double* Y,
                                                             const double* r) {
   IterState* st = c.st;
@@ -479,15 +518,23 @@ __global__ void __launch_bounds__(kT) lbfgs_post_dots_kernel(VecCtx c, const dou
   const int cnt = st->count;
   __shared__ double sh[kMaxDots][kT / 32];
   __shared__ double tot[kMaxDots];
-  for (int k = 0; k < cnt; ++k) {
-    const double* Yi = Y + (int64_t)idx_oldest(st, k) * n3;
-    double v = 0;
-    PD_FOR_MINE(e) v += Yi[e] * r[e];
-    dot_to_shared(v, sh, k);
+  int idx[MX];
+  ring_oldest<MX>(st, idx);
+  double yr[MX];
+#pragma unroll
+  for (int k = 0; k < MX; ++k) yr[k] = 0.0;
+  double rg = 0.0;
+  PD_FOR_MINE(e) {
+    const double re = r[e];
+    rg += re * g[e];
+#pragma unroll
+    for (int k = 0; k < MX; ++k)
+      if (k < cnt) yr[k] += Y[(int64_t)idx[k] * n3 + e] * re;
   }
-  double v = 0;
-  PD_FOR_MINE(e) v += r[e] * g[e];
-  dot_to_shared(v, sh, cnt);
+#pragma unroll
+  for (int k = 0; k < MX; ++k)
+    if (k < cnt) dot_to_shared(yr[k], sh, k);
+  dot_to_shared(rg, sh, cnt);
   if (!finish_dots(cnt + 1, sh, c.lpart, c.lcounter, tot)) return;
   if (threadIdx.x != 0) return;
   double slope = tot[cnt];
@@ -506,6 +553,7 @@ __global__ void __launch_bounds__(kT) lbfgs_post_dots_kernel(VecCtx c, const dou
 
 // d = -(r0 + sum cf_i s_i) (oldest first, as the second loop adds them); forward:
 // trial xt = x + d, or xt = x + alpha d after a rejected trial
+template <int MX>
 __global__ void __launch_bounds__(kT) lbfgs_dir_kernel(VecCtx c, const double* S, const double* r, double* d,
                                                       const double* x, double* xt) {
   const IterState* st = c.st;
@@ -517,17 +565,27 @@ __global__ void __launch_bounds__(kT) lbfgs_dir_kernel(VecCtx c, const double* S
     return;
   }
   const int cnt = st->count;
+  int idx[MX];
+  double cf[MX];
+  ring_oldest<MX>(st, idx);
+#pragma unroll
+  for (int k = 0; k < MX; ++k) cf[k] = k < cnt ? st->cf[idx[k]] : 0.0;
   PD_FOR_MINE(e) {
+    double sv[MX];
+#pragma unroll
+    for (int k = 0; k < MX; ++k) sv[k] = k < cnt ? S[(int64_t)idx[k] * n3 + e] : 0.0;
     double v = r[e];
-    for (int k = 0; k < cnt; ++k) {
-      const int j = idx_oldest(st, k);
-      v += st->cf[j] * S[(int64_t)j * n3 + e];
-    }
+#pragma unroll
+    for (int k = 0; k < MX; ++k)
+      if (k < cnt) v += cf[k] * sv[k];
     d[e] = -v;
     if (xt) xt[e] = x[e] - v;
   }
 }
 #undef PD_FOR_MINE
+
+// compile-time history bound for a history length m (<= kMaxHistory)
+inline int lbfgs_bound(int m) { return m <= 2 ? 2 : (m <= 4 ? 4 : (m <= 8 ? 8 : 16)); }
 
 // v_{t+1} = (x - x_t)/h, state advance, trajectory write in kept order
 __global__ void finalize_fwd_kernel(int64_t n, const double* x, double* xi, double* vi, double inv_h,
