@@ -52,6 +52,12 @@ def parse():
                     help="serving workload instead: quadruped requests under Poisson arrivals")
     ap.add_argument("--serve-requests", type=int, default=24)
     ap.add_argument("--serve-slots", type=int, default=8)
+    ap.add_argument("--probe", choices=["solve", "local", "hvp", "rollout", "quadruped"],
+                    help="profiling driver (no timing, no JSON): factorise the benchmark beam in mixed "
+                         "precision, then run --repeat solves / local steps / Hessian products, or one "
+                         "rollout of --T steps forward and backward; 'quadruped' = one 16^3 quadruped "
+                         "rollout of --T steps")
+    ap.add_argument("--repeat", type=int, default=4)
     return ap.parse_args()
 
 
@@ -290,15 +296,21 @@ def run_ours(args):
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record(stream)
+    hp = [time.perf_counter()]
     d = {k: t.to(dev, non_blocking=True) for k, t in host.items()}
     mesh.factorize(d["wc"], d["wv"], None, None, h=sc.h, gravity=tuple(sc.gravity), precision=N.PD_PREC_MIXED)
+    hp.append(time.perf_counter())
     opts = api.solver_opts(tol_fwd=TOL_FWD, tol_bwd=TOL_BWD)
     roll = mesh.forward(d["x0"], d["v0"], T, opts=opts)
+    hp.append(time.perf_counter())
     g = mesh.backward(roll, T, d["lw"], opts=opts, want=want)
+    hp.append(time.perf_counter())
     loss = (roll.x[-1] * d["lw"]).sum()
     out_host = [g["w_corot"].cpu(), g["w_vol"].cpu(), g["v0"].cpu(), loss.cpu()]
     e1.record(stream)
     torch.cuda.synchronize()
+    hp.append(time.perf_counter())
+    phases = {k: 1e3 * (hp[i + 1] - hp[i]) for i, k in enumerate(("h2d_factorize", "forward", "backward", "d2h"))}
     d2h = sum(t.numel() * 8 for t in out_host)
     e2e_value = world * T / (e0.elapsed_time(e1) / 1e3)
 
@@ -330,7 +342,8 @@ def run_ours(args):
                                 "what": "host wall time of one simulation step, forward + adjoint"},
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": "steps/s", "h2d_bytes_per_step": h2d,
-                    "d2h_bytes_per_step": d2h, "includes": "H2D inputs, factorisation, forward, backward, D2H"},
+                    "d2h_bytes_per_step": d2h, "includes": "H2D inputs, factorisation, forward, backward, D2H",
+                    "host_phases_ms": phases},
             "gpu_launches": launches,
             "clocks": clk,
         }
@@ -398,9 +411,51 @@ def run_serve(args):
     print(json.dumps(line))
 
 
+def run_probe(args):
+    """Fixed launch sequences for ncu captures (see profiles/)."""
+    import numpy as np
+    import torch
+    from paper_2101_05917_gb300 import build as _build
+    _build.build()
+    from paper_2101_05917_gb300 import api
+    from paper_2101_05917_gb300 import _native as N
+    from workloads import beam_c2, quadruped
+    dev = torch.device("cuda:0")
+    tt = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device=dev)
+    sc = quadruped(16, T=args.T) if args.probe == "quadruped" else beam_c2(T=args.T)
+    mesh = api.PDMesh.from_scene(sc)
+    wc, wv, wm, fib = api.scene_weights(sc, dev)
+    mesh.factorize(wc, wv, wm, fib, h=sc.h, gravity=tuple(sc.gravity), k_contact=sc.k_contact,
+                   precision=N.PD_PREC_MIXED)
+    x = tt(sc.x0)
+    v = tt(np.random.default_rng(1).standard_normal(sc.x0.shape))
+    if args.probe == "solve":
+        for _ in range(args.repeat):
+            mesh.solve(v, precision=N.PD_PREC_MIXED)
+    elif args.probe == "local":
+        for _ in range(args.repeat):
+            mesh.local_step(x, precision=N.PD_PREC_MIXED)
+    elif args.probe == "hvp":
+        for _ in range(args.repeat):
+            mesh.hessian_vector(x, v, precision=N.PD_PREC_MIXED)
+    else:
+        opts = api.solver_opts(tol_fwd=TOL_FWD if args.probe == "rollout" else sc.tol_fwd,
+                               tol_bwd=TOL_BWD if args.probe == "rollout" else sc.tol_bwd, max_iter_fwd=3000,
+                               max_iter_bwd=3000)
+        act = tt(sc.act[:args.T]) if sc.act is not None else None
+        roll = mesh.forward(x, tt(sc.v0), args.T, f_ext=tt(sc.f_ext), act=act, mu=sc.mu, opts=opts)
+        g = mesh.backward(roll, args.T, tt(sc.loss_w), f_ext=tt(sc.f_ext), act=act, mu=sc.mu, opts=opts)
+        print("forward", roll.stats)
+        print("backward", g["stats"])
+    torch.cuda.synchronize()
+    mesh.close()
+
+
 def main():
     args = parse()
-    if args.impl == "reference":
+    if args.probe:
+        run_probe(args)
+    elif args.impl == "reference":
         run_reference(args)
     elif args.serve:
         run_serve(args)

@@ -79,10 +79,37 @@ def c2(T=2, n_sample=2000):
                         loss=float(np.sum(sc.loss_w * xs[-1])))
 
 
+def c3(T=2, n_sample=2000):
+    """24^3 contact cube (penalty ground contact and friction, Sec. 5.1), first T
+    steps: Newton forward and the full-linearisation adjoint (direct solves);
+    stores sampled nodes with full-vector norms, the friction-coefficient gradient
+    and the loss sum(w x_T)."""
+    from workloads import contact_cube_c3
+    sc = contact_cube_c3(T=T)
+    model = Model(sc)
+    xs, vs, infos = newton.rollout(model, sc.x0, sc.v0, sc.f_ext, mu=sc.mu, T=T)
+    for t, i in enumerate(infos):
+        print("step", t, i, flush=True)
+    loss, gx = adjoint.final_position_loss(model, xs, sc.loss_w)
+    g = adjoint.backward(model, xs, vs, gx, mu=sc.mu)
+    n = xs.shape[1]
+    rng = np.random.default_rng(2026)
+    nodes = np.sort(rng.choice(n, size=min(n_sample, n), replace=False))
+    np.savez_compressed(os.path.join(HERE, "c3_cube_T%d_oracle_sampled.npz" % T), T=T, nodes=nodes,
+                        xs=xs[:, nodes], x_norm=np.linalg.norm(xs.reshape(T + 1, -1), axis=1),
+                        g_v0=g["g_v0"][nodes], g_v0_norm=np.linalg.norm(g["g_v0"]),
+                        g_x0=g["g_x0"][nodes], g_x0_norm=np.linalg.norm(g["g_x0"]),
+                        g_mu=np.asarray(g["g_mu"]), loss=loss,
+                        contact_nodes=np.array([int(np.sum((xs[t][:, 2] < 0) & (sc.contact > 0)))
+                                                for t in range(T + 1)]))
+
+
 if __name__ == "__main__":
     which = sys.argv[1:] or ["c1"]
     if "c1" in which:
         c1()
     if "c2" in which:
         c2()
+    if "c3" in which:
+        c3()
     print("written")
