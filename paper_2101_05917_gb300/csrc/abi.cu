@@ -195,7 +195,8 @@ struct Ctx {
   pd_solver_opts o;
   int64_t n, nf, n3f;
   int vb;          // vector kernel blocks
-  int mx;          // compile-time bound of the L-BFGS history (2, 4, 8, 16)
+  int mx;          // compile-time bound of the L-BFGS history (2, 4, 5, 8, 10, 16)
+  int lb;          // blocks of the L-BFGS kernels: one wave, two per SM
   bool graphs;     // replay iteration chunks as CUDA graphs
   VecCtx vc;
   double* pe;      // energy partials
@@ -213,6 +214,7 @@ Ctx make_ctx(MeshImpl* m, cudaStream_t s, const pd_solver_opts& o) {
   c.n3f = 3 * m->h.nf;
   c.vb = vec_blocks(c.n3f);
   c.mx = lbfgs_bound(o.lbfgs_m);
+  c.lb = std::max(1, std::min(c.vb, 2 * m->sms));
   c.graphs = !o.profile && !o.no_graphs;
   c.vc.n3 = c.n3f;
   c.vc.st = m->ws.st;
@@ -244,8 +246,16 @@ pd_status poll(Ctx& c) {
       constexpr int MX = 4;          \
       __VA_ARGS__;                   \
     } break;                         \
+    case 5: {                        \
+      constexpr int MX = 5;          \
+      __VA_ARGS__;                   \
+    } break;                         \
     case 8: {                        \
       constexpr int MX = 8;          \
+      __VA_ARGS__;                   \
+    } break;                         \
+    case 10: {                       \
+      constexpr int MX = 10;         \
       __VA_ARGS__;                   \
     } break;                         \
     default: {                       \
@@ -266,13 +276,13 @@ pd_status launch_fwd_iteration(Ctx& c, int prec, const double* act_t) {
   if (c.local_t) c.local_t->record(c.s);
   PD_CUDA_TRY(launch_gather_grad(m, st, w.elembuf, prec, w.xt, w.y, w.dir, w.gradt, c.pg, c.s));
   decide_fwd_kernel<<<1, 256, 0, c.s>>>(st, c.pe, c.nbe, c.pg, c.nbg);
-  PD_WITH_MX(c.mx, lbfgs_commit_fwd_kernel<MX><<<c.vb, 256, 0, c.s>>>(c.vc, w.x, w.xt, w.grad, w.gradt, w.S, w.Y));
-  PD_WITH_MX(c.mx, lbfgs_q_kernel<MX><<<c.vb, 256, 0, c.s>>>(c.vc, w.grad, w.Y, w.q));
+  PD_WITH_MX(c.mx, lbfgs_commit_fwd_kernel<MX><<<c.lb, 256, 0, c.s>>>(c.vc, w.x, w.xt, w.grad, w.gradt, w.S, w.Y));
+  PD_WITH_MX(c.mx, lbfgs_q_kernel<MX><<<c.lb, 256, 0, c.s>>>(c.vc, w.grad, w.Y, w.q));
   if (c.solve_t) c.solve_t->record(c.s);
   PD_CUDA_TRY(solve_A(m, st, w.q, w.r, m->precision, c.s));
   if (c.solve_t) c.solve_t->record(c.s);
-  PD_WITH_MX(c.mx, lbfgs_post_dots_kernel<MX><<<c.vb, 256, 0, c.s>>>(c.vc, w.grad, w.Y, w.r));
-  PD_WITH_MX(c.mx, lbfgs_dir_kernel<MX><<<c.vb, 256, 0, c.s>>>(c.vc, w.S, w.r, w.dir, w.x, w.xt));
+  PD_WITH_MX(c.mx, lbfgs_post_dots_kernel<MX><<<c.lb, 256, 0, c.s>>>(c.vc, w.grad, w.Y, w.r));
+  PD_WITH_MX(c.mx, lbfgs_dir_kernel<MX><<<c.lb, 256, 0, c.s>>>(c.vc, w.S, w.r, w.dir, w.x, w.xt));
   c.launches += 9;
   c.solves += 1;
   c.locals += 1;
@@ -286,13 +296,13 @@ pd_status launch_bwd_iteration(Ctx& c, int prec, const double* xnext, const doub
   MeshImpl* m = c.m;
   Workspace& w = m->ws;
   IterState* st = w.st;
-  PD_WITH_MX(c.mx, lbfgs_commit_bwd_kernel<MX><<<c.vb, 256, 0, c.s>>>(c.vc, w.dir, w.Hd, w.z, w.gs, w.S, w.Y));
-  PD_WITH_MX(c.mx, lbfgs_q_kernel<MX><<<c.vb, 256, 0, c.s>>>(c.vc, w.gs, w.Y, w.q));
+  PD_WITH_MX(c.mx, lbfgs_commit_bwd_kernel<MX><<<c.lb, 256, 0, c.s>>>(c.vc, w.dir, w.Hd, w.z, w.gs, w.S, w.Y));
+  PD_WITH_MX(c.mx, lbfgs_q_kernel<MX><<<c.lb, 256, 0, c.s>>>(c.vc, w.gs, w.Y, w.q));
   if (c.solve_t) c.solve_t->record(c.s);
   PD_CUDA_TRY(solve_A(m, st, w.q, w.r, m->precision, c.s));
   if (c.solve_t) c.solve_t->record(c.s);
-  PD_WITH_MX(c.mx, lbfgs_post_dots_kernel<MX><<<c.vb, 256, 0, c.s>>>(c.vc, w.gs, w.Y, w.r));
-  PD_WITH_MX(c.mx, lbfgs_dir_kernel<MX><<<c.vb, 256, 0, c.s>>>(c.vc, w.S, w.r, w.dir, nullptr, nullptr));
+  PD_WITH_MX(c.mx, lbfgs_post_dots_kernel<MX><<<c.lb, 256, 0, c.s>>>(c.vc, w.gs, w.Y, w.r));
+  PD_WITH_MX(c.mx, lbfgs_dir_kernel<MX><<<c.lb, 256, 0, c.s>>>(c.vc, w.S, w.r, w.dir, nullptr, nullptr));
   c.launches += 9;
   c.solves += 1;
   LocalArgs la{m, st, xnext, w.dir, act_t, prec};
@@ -782,6 +792,7 @@ pd_status pd_create_mesh(const pd_mesh_desc* desc, pd_mesh* out) {
       cudaGetDevice(&dev);
       cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
       I.solve_grid = sms * solve_persistent_occupancy();
+      I.sms = std::max(1, sms);
     }
     if ((e = dalloc(&I, (char**)&I.ws.solve_partial, solve_partial_bytes(S))) != cudaSuccess) return fail(e);
   }

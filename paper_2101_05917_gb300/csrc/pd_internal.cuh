@@ -122,6 +122,7 @@ struct MeshImpl {
   int64_t* parent = nullptr;
   unsigned long long* solve_counters = nullptr;   // gticket | otick[...] | fdone[ns] | bdone[ns]
   int solve_grid = 0;
+  int sms = 1;                     // SMs of the device
   int32_t* gath_slots = nullptr;   // (sum nr) x slot_w update-row sources, -1 = none
   int slot_w = 1;
   SolveSchedule sched;

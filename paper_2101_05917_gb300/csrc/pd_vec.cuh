@@ -269,7 +269,7 @@ __global__ void decide_fwd_kernel(IterState* st, const double* energy_partials, 
 //   -> products y_i . r0, r0 . g -> d = -(r0 + sum (al_i - be_i) s_i)
 // The recursion visits the pairs in the order of the two-loop recursion, so the
 // result equals it up to rounding.  MX is a compile-time bound on the history
-// length (2, 4, 8 or 16) so that the per-pair accumulators live in registers.
+// length (2, 4, 5, 8, 10 or 16) so that the per-pair accumulators live in registers.
 constexpr int kMaxDots = 3 * kMaxHistory + 2;
 
 #define PD_FOR_MINE(i) \
@@ -337,24 +337,33 @@ __device__ __forceinline__ int first_loop_dots(const IterState* st, int64_t n3, 
   const int cnt = st->count;
   int idx[MX];
   ring_newest<MX>(st, idx);
+  // pairs past the count read g instead (a valid address), so that every load is
+  // unconditional and all of them are in flight together
+  const double* sp[MX];
+  const double* yp[MX];
+#pragma unroll
+  for (int k = 0; k < MX; ++k) {
+    sp[k] = k < cnt ? S + (int64_t)idx[k] * n3 : g;
+    yp[k] = (k < cnt && push) ? Y + (int64_t)idx[k] * n3 : g;
+  }
+  const double* Ss = push ? S + (int64_t)slot * n3 : g;
+  const double* Ys = push ? Y + (int64_t)slot * n3 : g;
   double sg[MX], a[MX], b[MX];
 #pragma unroll
   for (int k = 0; k < MX; ++k) sg[k] = a[k] = b[k] = 0.0;
-  const double* Ss = S + (int64_t)slot * n3;
-  const double* Ys = Y + (int64_t)slot * n3;
   PD_FOR_MINE(e) {
-    const double ge = g[e];
-    const double ss = push ? Ss[e] : 0.0, ys = push ? Ys[e] : 0.0;
+    const double ge = g[e], ss = Ss[e], ys = Ys[e];
+    double si[MX], yi[MX];
 #pragma unroll
     for (int k = 0; k < MX; ++k) {
-      if (k < cnt) {
-        const double si = S[(int64_t)idx[k] * n3 + e];
-        sg[k] += si * ge;
-        if (push) {
-          a[k] += si * ys;
-          b[k] += ss * Y[(int64_t)idx[k] * n3 + e];
-        }
-      }
+      si[k] = sp[k][e];
+      yi[k] = yp[k][e];
+    }
+#pragma unroll
+    for (int k = 0; k < MX; ++k) {
+      sg[k] += si[k] * ge;
+      a[k] += si[k] * ys;
+      b[k] += ss * yi[k];
     }
   }
   int K = k0;
@@ -494,14 +503,16 @@ __global__ void __launch_bounds__(kT) lbfgs_q_kernel(VecCtx c, const double* g, 
   ring_newest<MX>(st, idx);
 #pragma unroll
   for (int k = 0; k < MX; ++k) al[k] = k < cnt ? st->al[idx[k]] : 0.0;
+  const double* yp[MX];
+#pragma unroll
+  for (int k = 0; k < MX; ++k) yp[k] = k < cnt ? Y + (int64_t)idx[k] * n3 : g;   // al = 0 past the count
   PD_FOR_MINE(e) {
     double yv[MX];
 #pragma unroll
-    for (int k = 0; k < MX; ++k) yv[k] = k < cnt ? Y[(int64_t)idx[k] * n3 + e] : 0.0;
+    for (int k = 0; k < MX; ++k) yv[k] = yp[k][e];
     double v = g[e];
 #pragma unroll
-    for (int k = 0; k < MX; ++k)
-      if (k < cnt) v -= al[k] * yv[k];
+    for (int k = 0; k < MX; ++k) v -= al[k] * yv[k];
     q[e] = v;
   }
 }
@@ -524,12 +535,17 @@ __global__ void __launch_bounds__(kT) lbfgs_post_dots_kernel(VecCtx c, const dou
 #pragma unroll
   for (int k = 0; k < MX; ++k) yr[k] = 0.0;
   double rg = 0.0;
+  const double* yp[MX];
+#pragma unroll
+  for (int k = 0; k < MX; ++k) yp[k] = k < cnt ? Y + (int64_t)idx[k] * n3 : g;
   PD_FOR_MINE(e) {
     const double re = r[e];
+    double yv[MX];
+#pragma unroll
+    for (int k = 0; k < MX; ++k) yv[k] = yp[k][e];
     rg += re * g[e];
 #pragma unroll
-    for (int k = 0; k < MX; ++k)
-      if (k < cnt) yr[k] += Y[(int64_t)idx[k] * n3 + e] * re;
+    for (int k = 0; k < MX; ++k) yr[k] += yv[k] * re;
   }
 #pragma unroll
   for (int k = 0; k < MX; ++k)
@@ -570,14 +586,16 @@ __global__ void __launch_bounds__(kT) lbfgs_dir_kernel(VecCtx c, const double* S
   ring_oldest<MX>(st, idx);
 #pragma unroll
   for (int k = 0; k < MX; ++k) cf[k] = k < cnt ? st->cf[idx[k]] : 0.0;
+  const double* sp[MX];
+#pragma unroll
+  for (int k = 0; k < MX; ++k) sp[k] = k < cnt ? S + (int64_t)idx[k] * n3 : r;   // cf = 0 past the count
   PD_FOR_MINE(e) {
     double sv[MX];
 #pragma unroll
-    for (int k = 0; k < MX; ++k) sv[k] = k < cnt ? S[(int64_t)idx[k] * n3 + e] : 0.0;
+    for (int k = 0; k < MX; ++k) sv[k] = sp[k][e];
     double v = r[e];
 #pragma unroll
-    for (int k = 0; k < MX; ++k)
-      if (k < cnt) v += cf[k] * sv[k];
+    for (int k = 0; k < MX; ++k) v += cf[k] * sv[k];
     d[e] = -v;
     if (xt) xt[e] = x[e] - v;
   }
@@ -585,7 +603,9 @@ __global__ void __launch_bounds__(kT) lbfgs_dir_kernel(VecCtx c, const double* S
 #undef PD_FOR_MINE
 
 // compile-time history bound for a history length m (<= kMaxHistory)
-inline int lbfgs_bound(int m) { return m <= 2 ? 2 : (m <= 4 ? 4 : (m <= 8 ? 8 : 16)); }
+inline int lbfgs_bound(int m) {
+  return m <= 2 ? 2 : (m <= 4 ? 4 : (m <= 5 ? 5 : (m <= 8 ? 8 : (m <= 10 ? 10 : 16))));
+}
 
 // v_{t+1} = (x - x_t)/h, state advance, trajectory write in kept order
 __global__ void finalize_fwd_kernel(int64_t n, const double* x, double* xi, double* vi, double inv_h,

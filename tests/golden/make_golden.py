@@ -112,4 +112,6 @@ if __name__ == "__main__":
         c2()
     if "c3" in which:
         c3()
+    if "c3_24" in which:
+        c3(T=24)   # the cube reaches the ground near step 20: contact and friction engage
     print("written")
