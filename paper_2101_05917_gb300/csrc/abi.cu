@@ -101,7 +101,7 @@ pd_status ensure_workspace(MeshImpl* m, int lbfgs_m) {
     PD_CUDA_TRY(dalloc(m, (double**)&w.elembuf, (size_t)(24 * m->h.e)));
     const int64_t np = (int64_t)element_energy_partials(m) + 4 * (int64_t)gather_blocks(m) + 4 * 4096 + 64;
     PD_CUDA_TRY(dalloc(m, &w.partials, (size_t)np));
-    PD_CUDA_TRY(dalloc(m, &w.lpart, (size_t)kMaxDots * 1184));
+    PD_CUDA_TRY(dalloc(m, &w.lpart, (size_t)kMaxDots * kLbfgsMaxBlocks));
     PD_CUDA_TRY(dalloc(m, &w.act_cur, (size_t)std::max<int64_t>(m->h.e, 1)));
     PD_CUDA_TRY(dalloc(m, &w.xnext_cur, (size_t)n3));
     PD_CUDA_TRY(dalloc(m, &w.counters, 16));
@@ -196,7 +196,7 @@ struct Ctx {
   int64_t n, nf, n3f;
   int vb;          // vector kernel blocks
   int mx;          // compile-time bound of the L-BFGS history (2, 4, 5, 8, 10, 16)
-  int lb;          // blocks of the L-BFGS kernels: one wave, two per SM
+  int lb;          // blocks of the L-BFGS kernels: at most two per SM (one completion counter)
   bool graphs;     // replay iteration chunks as CUDA graphs
   VecCtx vc;
   double* pe;      // energy partials

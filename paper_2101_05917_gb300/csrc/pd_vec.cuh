@@ -101,7 +101,17 @@ __device__ __forceinline__ int idx_oldest(const IterState* st, int k) { return (
 // reduce up to `n` values at stride `stride` (fixed order), single block
 __device__ __forceinline__ double block_reduce_strided(const double* a, int64_t n, int stride, int off) {
   double acc = 0;
-  for (int64_t i = threadIdx.x; i < n; i += kT) acc += a[i * stride + off];
+  // eight loads in flight per thread, added in index order
+  for (int64_t i0 = threadIdx.x; i0 < n; i0 += 8 * kT) {
+    double v[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int64_t i = i0 + (int64_t)u * kT;
+      v[u] = i < n ? a[i * stride + off] : 0.0;
+    }
+#pragma unroll
+    for (int u = 0; u < 8; ++u) acc += v[u];
+  }
   return block_sum(acc);
 }
 
@@ -301,11 +311,22 @@ __device__ bool finish_dots(int K, double (*sh)[kT / 32], double* partials, unsi
   __syncthreads();
   if (!is_last) return false;
   __threadfence();
-  // warp w sums products k = w, w + 8, ...; lane l the blocks l, l + 32, ...
+  // warp w sums products k = w, w + 8, ...; lane l the blocks l, l + 32, ... (eight
+  // loads in flight per lane, added in block order)
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int nb = (int)gridDim.x;
   for (int k = warp; k < K; k += kT / 32) {
     double t = 0;
-    for (int b = lane; b < (int)gridDim.x; b += 32) t += __ldcg(partials + (int64_t)b * kMaxDots + k);
+    for (int b0 = 0; b0 < nb; b0 += 32 * 8) {
+      double v[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int b = b0 + lane + 32 * u;
+        v[u] = b < nb ? __ldcg(partials + (int64_t)b * kMaxDots + k) : 0.0;
+      }
+#pragma unroll
+      for (int u = 0; u < 8; ++u) t += v[u];
+    }
 #pragma unroll
     for (int off = 16; off >= 1; off >>= 1) t += __shfl_xor_sync(0xffffffffu, t, off);
     if (lane == 0) tot[k] = t;
@@ -327,45 +348,97 @@ __device__ __forceinline__ void ring_oldest(const IterState* st, int* idx) {
   for (int k = 0; k < MX; ++k) idx[k] = k < st->count ? idx_oldest(st, k) : 0;
 }
 
-// Products of the first loop at gradient g: s_i . g over the stored pairs (newest
-// first) and, after a push into `slot`, s_i . y_slot and s_slot . y_i; written to
-// sh[k0 ...] in that order.  Returns the number of products.
+// The scalar state of the recursions (the Gram matrix, rho, al, cf, s_i . g),
+// staged in shared memory by the last block: one cooperative load, the m-step
+// recursion on one thread from shared memory, one cooperative store.
+struct LbfgsScalars {
+  double SY[kMaxHistory][kMaxHistory];
+  double rho[kMaxHistory], al[kMaxHistory], cf[kMaxHistory], sg[kMaxHistory];
+  int head, count, m;
+};
+
+__device__ __forceinline__ void scalars_load(const IterState* st, LbfgsScalars& L) {
+  for (int i = threadIdx.x; i < kMaxHistory * kMaxHistory; i += kT)
+    L.SY[i / kMaxHistory][i % kMaxHistory] = st->SY[i / kMaxHistory][i % kMaxHistory];
+  for (int i = threadIdx.x; i < kMaxHistory; i += kT) {
+    L.rho[i] = st->rho[i];
+    L.al[i] = st->al[i];
+    L.cf[i] = st->cf[i];
+    L.sg[i] = st->sg[i];
+  }
+  if (threadIdx.x == 0) {
+    L.head = st->head;
+    L.count = st->count;
+    L.m = st->m;
+  }
+  __syncthreads();
+}
+
+__device__ __forceinline__ void scalars_store(IterState* st, const LbfgsScalars& L) {
+  __syncthreads();
+  for (int i = threadIdx.x; i < kMaxHistory * kMaxHistory; i += kT)
+    st->SY[i / kMaxHistory][i % kMaxHistory] = L.SY[i / kMaxHistory][i % kMaxHistory];
+  for (int i = threadIdx.x; i < kMaxHistory; i += kT) {
+    st->al[i] = L.al[i];
+    st->cf[i] = L.cf[i];
+    st->sg[i] = L.sg[i];
+  }
+}
+
+__device__ __forceinline__ int ring_newest_s(const LbfgsScalars& L, int k) {
+  return (L.head + L.count - 1 - k + 2 * L.m) % L.m;
+}
+__device__ __forceinline__ int ring_oldest_s(const LbfgsScalars& L, int k) { return (L.head + k) % L.m; }
+
+// one thread: store the products (s_i . g and the new SY entries)
+__device__ __forceinline__ void store_products(LbfgsScalars& L, const double* tot, bool push, int slot) {
+  const int cnt = L.count;
+  for (int k = 0; k < cnt; ++k) L.sg[ring_newest_s(L, k)] = tot[k];
+  if (push) {
+    for (int k = 0; k < cnt; ++k) {
+      const int i = ring_newest_s(L, k);
+      L.SY[i][slot] = tot[cnt + 2 * k];
+      L.SY[slot][i] = tot[cnt + 2 * k + 1];
+    }
+  }
+}
+
+// one thread: al_i newest -> oldest
+__device__ __forceinline__ void first_loop_coefficients(LbfgsScalars& L) {
+  const int cnt = L.count;
+  for (int k = 0; k < cnt; ++k) {
+    const int i = ring_newest_s(L, k);
+    double acc = L.sg[i];
+    for (int kk = 0; kk < k; ++kk) {
+      const int j = ring_newest_s(L, kk);
+      acc -= L.al[j] * L.SY[i][j];
+    }
+    L.al[i] = L.rho[i] * acc;
+  }
+}
+
+// Products of the first loop at the new gradient gn, accumulated per entry:
+// s_i . gn over the stored pairs (newest first) and, after a push into `slot`,
+// s_i . y_slot and s_slot . y_i.  The pushed pair's own entries (ss, ys) come from
+// registers; every other history entry was loaded before the entry's stores.
 template <int MX>
-__device__ __forceinline__ int first_loop_dots(const IterState* st, int64_t n3, const double* S, const double* Y,
-                                               const double* g, bool push, int slot, double (*sh)[kT / 32],
-                                               int k0) {
-  const int cnt = st->count;
-  int idx[MX];
-  ring_newest<MX>(st, idx);
-  // pairs past the count read g instead (a valid address), so that every load is
-  // unconditional and all of them are in flight together
-  const double* sp[MX];
-  const double* yp[MX];
+__device__ __forceinline__ void accumulate_first_loop(const int* idx, int cnt, bool push, int slot,
+                                                      const double* si, const double* yi, double gn, double ss,
+                                                      double ys, double* sg, double* a, double* b) {
 #pragma unroll
   for (int k = 0; k < MX; ++k) {
-    sp[k] = k < cnt ? S + (int64_t)idx[k] * n3 : g;
-    yp[k] = (k < cnt && push) ? Y + (int64_t)idx[k] * n3 : g;
+    const bool fresh = push && k < cnt && idx[k] == slot;
+    const double sk = fresh ? ss : si[k];
+    const double yk = fresh ? ys : yi[k];
+    sg[k] += sk * gn;
+    a[k] += sk * ys;
+    b[k] += ss * yk;
   }
-  const double* Ss = push ? S + (int64_t)slot * n3 : g;
-  const double* Ys = push ? Y + (int64_t)slot * n3 : g;
-  double sg[MX], a[MX], b[MX];
-#pragma unroll
-  for (int k = 0; k < MX; ++k) sg[k] = a[k] = b[k] = 0.0;
-  PD_FOR_MINE(e) {
-    const double ge = g[e], ss = Ss[e], ys = Ys[e];
-    double si[MX], yi[MX];
-#pragma unroll
-    for (int k = 0; k < MX; ++k) {
-      si[k] = sp[k][e];
-      yi[k] = yp[k][e];
-    }
-#pragma unroll
-    for (int k = 0; k < MX; ++k) {
-      sg[k] += si[k] * ge;
-      a[k] += si[k] * ys;
-      b[k] += ss * yi[k];
-    }
-  }
+}
+
+template <int MX>
+__device__ __forceinline__ int first_loop_to_shared(int cnt, bool push, const double* sg, const double* a,
+                                                    const double* b, double (*sh)[kT / 32], int k0) {
   int K = k0;
 #pragma unroll
   for (int k = 0; k < MX; ++k)
@@ -382,67 +455,81 @@ __device__ __forceinline__ int first_loop_dots(const IterState* st, int64_t n3, 
   return K;
 }
 
-// last block, one thread: store the products (s_i . g and the new SY entries)
-__device__ __forceinline__ void store_products(IterState* st, const double* tot, bool push, int slot) {
-  const int cnt = st->count;
-  for (int k = 0; k < cnt; ++k) st->sg[idx_newest(st, k)] = tot[k];
-  if (push) {
-    for (int k = 0; k < cnt; ++k) {
-      const int i = idx_newest(st, k);
-      st->SY[i][slot] = tot[cnt + 2 * k];
-      st->SY[slot][i] = tot[cnt + 2 * k + 1];
-    }
-  }
-}
-
-// last block, one thread: al_i newest -> oldest
-__device__ __forceinline__ void first_loop_coefficients(IterState* st) {
-  const int cnt = st->count;
-  for (int k = 0; k < cnt; ++k) {
-    const int i = idx_newest(st, k);
-    double acc = st->sg[i];
-    for (int kk = 0; kk < k; ++kk) {
-      const int j = idx_newest(st, kk);
-      acc -= st->al[j] * st->SY[i][j];
-    }
-    st->al[i] = st->rho[i] * acc;
-  }
-}
-
-// forward, before the solve: commit an accepted trial (history pair, x, grad),
-// then the first-loop products and coefficients
+// forward, before the solve: commit an accepted trial (history pair, x, grad) and
+// form the first-loop products in the same pass; then the coefficients
 template <int MX>
 __global__ void __launch_bounds__(kT) lbfgs_commit_fwd_kernel(VecCtx c, double* x, const double* xt, double* grad,
                                                              const double* gradt, double* S, double* Y) {
   IterState* st = c.st;
   if (!st->accepted) return;
   const int64_t n3 = c.n3;
-  const int push = st->push, slot = st->pslot;
-  PD_FOR_MINE(e) {
-    const double xn = xt[e], gn = gradt[e];
-    if (push) {
-      S[(int64_t)slot * n3 + e] = xn - x[e];
-      Y[(int64_t)slot * n3 + e] = gn - grad[e];
+  const int push = st->push, slot = st->pslot, cnt = st->count;
+  const bool conv = st->converged;
+  int idx[MX];
+  ring_newest<MX>(st, idx);
+  const double* sp[MX];
+  const double* yp[MX];
+#pragma unroll
+  for (int k = 0; k < MX; ++k) {   // unused entries read xt (a valid address)
+    sp[k] = k < cnt ? S + (int64_t)idx[k] * n3 : xt;
+    yp[k] = (k < cnt && push) ? Y + (int64_t)idx[k] * n3 : xt;
+  }
+  double sg[MX], a[MX], b[MX];
+#pragma unroll
+  for (int k = 0; k < MX; ++k) sg[k] = a[k] = b[k] = 0.0;
+  // two entries per iteration, every load of both issued before any store
+  const int64_t stride = (int64_t)gridDim.x * kT;
+  for (int64_t e0 = (int64_t)blockIdx.x * kT + threadIdx.x; e0 < n3; e0 += 2 * stride) {
+    const int64_t e1 = e0 + stride;
+    const bool v1 = e1 < n3;
+    const int64_t f1 = v1 ? e1 : e0;
+    double xn[2], gn[2], xo[2], go[2], si[2][MX], yi[2][MX];
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      const int64_t e = u ? f1 : e0;
+      xn[u] = xt[e];
+      gn[u] = gradt[e];
+      xo[u] = x[e];
+      go[u] = grad[e];
+#pragma unroll
+      for (int k = 0; k < MX; ++k) {
+        si[u][k] = sp[k][e];
+        yi[u][k] = yp[k][e];
+      }
     }
-    x[e] = xn;
-    grad[e] = gn;
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      if (u == 1 && !v1) break;
+      const int64_t e = u ? e1 : e0;
+      const double ss = xn[u] - xo[u], ys = gn[u] - go[u];
+      if (push) {
+        S[(int64_t)slot * n3 + e] = ss;
+        Y[(int64_t)slot * n3 + e] = ys;
+      }
+      x[e] = xn[u];
+      grad[e] = gn[u];
+      accumulate_first_loop<MX>(idx, cnt, push != 0, slot, si[u], yi[u], gn[u], ss, ys, sg, a, b);
+    }
   }
   // a converged solve still records the new pair's products (history kept for the next step)
-  const bool conv = st->converged;
   if (conv && !push) return;
   __shared__ double sh[kMaxDots][kT / 32];
   __shared__ double tot[kMaxDots];
-  const int K = first_loop_dots<MX>(st, n3, S, Y, grad, push != 0, slot, sh, 0);
+  const int K = first_loop_to_shared<MX>(cnt, push != 0, sg, a, b, sh, 0);
   if (!finish_dots(K, sh, c.lpart, c.lcounter, tot)) return;
-  if (threadIdx.x != 0) return;
-  store_products(st, tot, push != 0, slot);
-  if (!conv) first_loop_coefficients(st);
+  __shared__ LbfgsScalars L;
+  scalars_load(st, L);
+  if (threadIdx.x == 0) {
+    store_products(L, tot, push != 0, slot);
+    if (!conv) first_loop_coefficients(L);
+  }
+  scalars_store(st, L);
 }
 
 // backward, before the solve: apply the previous step z += alpha d,
-// gs += alpha Hd (history pair alpha (d, Hd)) and test |gs| for convergence;
-// then the first-loop products and coefficients.  The first iteration of a step
-// (or the one after a residual replacement) has no step to apply.
+// gs += alpha Hd (history pair alpha (d, Hd)) and test |gs| for convergence, with
+// the first-loop products in the same pass; then the coefficients.  The first
+// iteration of a step (or the one after a residual replacement) has no step to apply.
 template <int MX>
 __global__ void __launch_bounds__(kT) lbfgs_commit_bwd_kernel(VecCtx c, const double* d, const double* Hd, double* z,
                                                              double* gs, double* S, double* Y) {
@@ -450,45 +537,90 @@ __global__ void __launch_bounds__(kT) lbfgs_commit_bwd_kernel(VecCtx c, const do
   if (st->converged) return;
   const int64_t n3 = c.n3;
   const int pending = st->pending;
-  const int push = pending ? st->push : 0, slot = st->pslot;
+  const int push = pending ? st->push : 0, slot = st->pslot, cnt = st->count;
+  const double al = pending ? st->alpha : 0.0;
+  int idx[MX];
+  ring_newest<MX>(st, idx);
+  const double* sp[MX];
+  const double* yp[MX];
+#pragma unroll
+  for (int k = 0; k < MX; ++k) {
+    sp[k] = k < cnt ? S + (int64_t)idx[k] * n3 : gs;
+    yp[k] = (k < cnt && push) ? Y + (int64_t)idx[k] * n3 : gs;
+  }
+  double sg[MX], a[MX], b[MX];
+#pragma unroll
+  for (int k = 0; k < MX; ++k) sg[k] = a[k] = b[k] = 0.0;
+  double part = 0;
+  const int64_t stride = (int64_t)gridDim.x * kT;
+  for (int64_t e0 = (int64_t)blockIdx.x * kT + threadIdx.x; e0 < n3; e0 += 2 * stride) {
+    const int64_t e1 = e0 + stride;
+    const bool v1 = e1 < n3;
+    const int64_t f1 = v1 ? e1 : e0;
+    double go[2], dd[2], hh[2], zz[2], si[2][MX], yi[2][MX];
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      const int64_t e = u ? f1 : e0;
+      go[u] = gs[e];
+      dd[u] = pending ? d[e] : 0.0;
+      hh[u] = pending ? Hd[e] : 0.0;
+      zz[u] = pending ? z[e] : 0.0;
+#pragma unroll
+      for (int k = 0; k < MX; ++k) {
+        si[u][k] = sp[k][e];
+        yi[u][k] = yp[k][e];
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      if (u == 1 && !v1) break;
+      const int64_t e = u ? e1 : e0;
+      double gn = go[u], ad = 0.0, ah = 0.0;
+      if (pending) {
+        ad = al * dd[u];
+        ah = al * hh[u];
+        z[e] = zz[u] + ad;
+        gn = go[u] + ah;
+        gs[e] = gn;
+        if (push) {
+          S[(int64_t)slot * n3 + e] = ad;
+          Y[(int64_t)slot * n3 + e] = ah;
+        }
+        part += gn * gn;
+      }
+      accumulate_first_loop<MX>(idx, cnt, push != 0, slot, si[u], yi[u], gn, ad, ah, sg, a, b);
+    }
+  }
   __shared__ double sh[kMaxDots][kT / 32];
   __shared__ double tot[kMaxDots];
   int K0 = 0;
   if (pending) {
-    const double a = st->alpha;
-    double part = 0;
-    PD_FOR_MINE(e) {
-      const double ad = a * d[e], ah = a * Hd[e];
-      z[e] += ad;
-      const double gn = gs[e] + ah;
-      gs[e] = gn;
-      if (push) {
-        S[(int64_t)slot * n3 + e] = ad;
-        Y[(int64_t)slot * n3 + e] = ah;
-      }
-      part += gn * gn;
-    }
     dot_to_shared(part, sh, 0);
     K0 = 1;
   }
-  const int K = first_loop_dots<MX>(st, n3, S, Y, gs, push != 0, slot, sh, K0);
+  const int K = first_loop_to_shared<MX>(cnt, push != 0, sg, a, b, sh, K0);
   if (!finish_dots(K, sh, c.lpart, c.lcounter, tot)) return;
-  if (threadIdx.x != 0) return;
-  store_products(st, tot + K0, push != 0, slot);
-  if (pending) {
-    const double gn2 = tot[0];
-    const bool conv = gn2 <= st->tol2 * st->ref2;
-    st->iters += 1;
-    const bool cap = !conv && st->iters >= st->max_iter;
-    st->gn2_acc = gn2;
-    st->pending = 0;
-    if (conv || cap) {
-      st->converged = 1;
-      st->hit_max = cap ? 1 : 0;
-      return;
+  __shared__ LbfgsScalars L;
+  scalars_load(st, L);
+  if (threadIdx.x == 0) {
+    store_products(L, tot + K0, push != 0, slot);
+    bool stop = false;
+    if (pending) {
+      const double gn2 = tot[0];
+      const bool conv = gn2 <= st->tol2 * st->ref2;
+      st->iters += 1;
+      const bool cap = !conv && st->iters >= st->max_iter;
+      st->gn2_acc = gn2;
+      st->pending = 0;
+      if (conv || cap) {
+        st->converged = 1;
+        st->hit_max = cap ? 1 : 0;
+        stop = true;
+      }
     }
+    if (!stop) first_loop_coefficients(L);
   }
-  first_loop_coefficients(st);
+  scalars_store(st, L);
 }
 
 // q = g - sum al_i y_i (newest first, as the first loop subtracts them)
@@ -538,33 +670,50 @@ __global__ void __launch_bounds__(kT) lbfgs_post_dots_kernel(VecCtx c, const dou
   const double* yp[MX];
 #pragma unroll
   for (int k = 0; k < MX; ++k) yp[k] = k < cnt ? Y + (int64_t)idx[k] * n3 : g;
-  PD_FOR_MINE(e) {
-    const double re = r[e];
-    double yv[MX];
+  const int64_t stride = (int64_t)gridDim.x * kT;
+  for (int64_t e0 = (int64_t)blockIdx.x * kT + threadIdx.x; e0 < n3; e0 += 2 * stride) {
+    const int64_t e1 = e0 + stride;
+    const bool v1 = e1 < n3;
+    const int64_t f1 = v1 ? e1 : e0;
+    double re[2], ge[2], yv[2][MX];
 #pragma unroll
-    for (int k = 0; k < MX; ++k) yv[k] = yp[k][e];
-    rg += re * g[e];
+    for (int u = 0; u < 2; ++u) {
+      const int64_t e = u ? f1 : e0;
+      re[u] = r[e];
+      ge[u] = g[e];
 #pragma unroll
-    for (int k = 0; k < MX; ++k) yr[k] += yv[k] * re;
+      for (int k = 0; k < MX; ++k) yv[u][k] = yp[k][e];
+    }
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      if (u == 1 && !v1) break;
+      rg += re[u] * ge[u];
+#pragma unroll
+      for (int k = 0; k < MX; ++k) yr[k] += yv[u][k] * re[u];
+    }
   }
 #pragma unroll
   for (int k = 0; k < MX; ++k)
     if (k < cnt) dot_to_shared(yr[k], sh, k);
   dot_to_shared(rg, sh, cnt);
   if (!finish_dots(cnt + 1, sh, c.lpart, c.lcounter, tot)) return;
-  if (threadIdx.x != 0) return;
-  double slope = tot[cnt];
-  for (int k = 0; k < cnt; ++k) {
-    const int i = idx_oldest(st, k);
-    double acc = tot[k];
-    for (int kk = 0; kk < k; ++kk) {
-      const int j = idx_oldest(st, kk);
-      acc += st->cf[j] * st->SY[j][i];
+  __shared__ LbfgsScalars L;
+  scalars_load(st, L);
+  if (threadIdx.x == 0) {
+    double slope = tot[cnt];
+    for (int k = 0; k < cnt; ++k) {
+      const int i = ring_oldest_s(L, k);
+      double acc = tot[k];
+      for (int kk = 0; kk < k; ++kk) {
+        const int j = ring_oldest_s(L, kk);
+        acc += L.cf[j] * L.SY[j][i];
+      }
+      L.cf[i] = L.al[i] - L.rho[i] * acc;
+      slope += L.cf[i] * L.sg[i];
     }
-    st->cf[i] = st->al[i] - st->rho[i] * acc;
-    slope += st->cf[i] * st->sg[i];
+    st->slope = -slope;
   }
-  st->slope = -slope;
+  scalars_store(st, L);
 }
 
 // d = -(r0 + sum cf_i s_i) (oldest first, as the second loop adds them); forward:
@@ -603,6 +752,13 @@ __global__ void __launch_bounds__(kT) lbfgs_dir_kernel(VecCtx c, const double* S
 #undef PD_FOR_MINE
 
 // compile-time history bound for a history length m (<= kMaxHistory)
+// blocks of the L-BFGS kernels: one entry per thread up to the partial-sum capacity
+constexpr int kLbfgsMaxBlocks = 2048;
+inline int lbfgs_blocks(int64_t n3) {
+  const int64_t b = (n3 + kT - 1) / kT;
+  return (int)(b < 1 ? 1 : (b > kLbfgsMaxBlocks ? kLbfgsMaxBlocks : b));
+}
+
 inline int lbfgs_bound(int m) {
   return m <= 2 ? 2 : (m <= 4 ? 4 : (m <= 5 ? 5 : (m <= 8 ? 8 : (m <= 10 ? 10 : 16))));
 }
