@@ -135,14 +135,16 @@ typedef struct {
   int32_t check_every;          /* iterations between host convergence polls (0 = 4); with
                                    PD_PREC_MIXED the local steps run in FP32 and the convergence
                                    test is confirmed by an FP64 residual */
-  int32_t profile;              /* nonzero: time the solve and local-step launches with CUDA
-                                   events on the launching stream (pd_stats.*_ms) */
+  int32_t profile;              /* nonzero: time solve and local-step launches with CUDA events
+                                   on the launching stream (pd_stats.*_ms, *_timed); with
+                                   graphs on, the last iteration of every chunk of 4 is
+                                   launched directly and timed, the others replayed */
   int32_t warm_start;           /* nonzero: keep the L-BFGS pairs from one time step to the
                                    next and start each adjoint solve from the previous
                                    step's z (fixed points unchanged) */
   int32_t no_graphs;            /* nonzero: launch every kernel directly; by default chunks of
                                    iterations are captured once per mesh as CUDA graphs and
-                                   replayed (not with profile, which times single launches) */
+                                   replayed */
   double* step_ms;              /* optional host array of T entries: pd_forward stores the
                                    host wall time of each step [ms], pd_backward adds the
                                    time of the step's adjoint (so after both calls entry t
@@ -164,6 +166,8 @@ typedef struct {
   double solve_ms;                      /* profile: summed device time of the solves */
   int64_t local_steps;                  /* forward local steps (FP32 or FP64) */
   double local_ms;                      /* profile: summed device time of the forward local steps */
+  int64_t solves_timed;                 /* profile: solves timed by events (solve_ms covers these) */
+  int64_t local_steps_timed;            /* profile: forward local steps timed by events */
 } pd_stats;
 
 /* Forward rollout of T implicit-Euler steps (Sec. 3 Eqns 1-4, Alg. 1).

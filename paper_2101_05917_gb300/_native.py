@@ -74,7 +74,8 @@ class Stats(ctypes.Structure):
                 ("inverted", ctypes.c_int32), ("not_converged_steps", ctypes.c_int32),
                 ("fwd_ms", ctypes.c_double), ("bwd_ms", ctypes.c_double),
                 ("kernel_launches", ctypes.c_int64), ("solves", ctypes.c_int64), ("solve_ms", ctypes.c_double),
-                ("local_steps", ctypes.c_int64), ("local_ms", ctypes.c_double)]
+                ("local_steps", ctypes.c_int64), ("local_ms", ctypes.c_double),
+                ("solves_timed", ctypes.c_int64), ("local_steps_timed", ctypes.c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

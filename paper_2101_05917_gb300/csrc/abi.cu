@@ -170,6 +170,7 @@ struct EventTimer {
     }
     cudaEventRecord(pool[used++], s);
   }
+  int64_t pairs() const { return (int64_t)(used / 2); }
   double total_ms() {   // pairs (start, end)
     double t = 0;
     for (size_t i = 0; i + 1 < used; i += 2) {
@@ -215,7 +216,7 @@ Ctx make_ctx(MeshImpl* m, cudaStream_t s, const pd_solver_opts& o) {
   c.vb = vec_blocks(c.n3f);
   c.mx = lbfgs_bound(o.lbfgs_m);
   c.lb = std::max(1, std::min(c.vb, 2 * m->sms));
-  c.graphs = !o.profile && !o.no_graphs;
+  c.graphs = !o.no_graphs;
   c.vc.n3 = c.n3f;
   c.vc.st = m->ws.st;
   c.vc.partials = m->ws.partials;
@@ -329,22 +330,24 @@ constexpr int kGraphIters = 4;
 namespace pd {
 
 void drop_iteration_graphs(MeshImpl* m) {
-  for (auto& row : m->iter_graph)
-    for (cudaGraphExec_t& g : row) {
-      if (g) cudaGraphExecDestroy(g);
-      g = nullptr;
-    }
+  for (auto& dir : m->iter_graph)
+    for (auto& prec : dir)
+      for (cudaGraphExec_t& g : prec) {
+        if (g) cudaGraphExecDestroy(g);
+        g = nullptr;
+      }
 }
 
 }  // namespace pd
 
 namespace {
 
-cudaGraphExec_t iteration_graph(Ctx& c, int dir, int prec, bool with_act) {
+cudaGraphExec_t iteration_graph(Ctx& c, int dir, int prec, bool with_act, int variant) {
   MeshImpl* m = c.m;
   const int pi = prec == PD_PREC_MIXED ? 1 : 0;
-  cudaGraphExec_t& g = m->iter_graph[dir][pi];
-  if (g && m->iter_graph_act[dir][pi] == with_act) return g;
+  const int iters = kGraphIters - variant;
+  cudaGraphExec_t& g = m->iter_graph[dir][pi][variant];
+  if (g && m->iter_graph_act[dir][pi][variant] == with_act) return g;
   if (g) cudaGraphExecDestroy(g);
   g = nullptr;
   if (!m->cap_stream && cudaStreamCreateWithFlags(&m->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
@@ -361,7 +364,7 @@ cudaGraphExec_t iteration_graph(Ctx& c, int dir, int prec, bool with_act) {
     return nullptr;
   }
   pd_status st = PD_OK;
-  for (int k = 0; k < kGraphIters && st == PD_OK; ++k)
+  for (int k = 0; k < iters && st == PD_OK; ++k)
     st = dir == 0 ? launch_fwd_iteration(cc, prec, with_act ? m->ws.act_cur : nullptr)
                   : launch_bwd_iteration(cc, prec, m->ws.xnext_cur, with_act ? m->ws.act_cur : nullptr);
   cudaGraph_t graph = nullptr;
@@ -378,10 +381,10 @@ cudaGraphExec_t iteration_graph(Ctx& c, int dir, int prec, bool with_act) {
     cudaGetLastError();
     return nullptr;
   }
-  m->iter_graph_act[dir][pi] = with_act;
-  m->iter_graph_counts[dir][pi][0] = cc.launches;
-  m->iter_graph_counts[dir][pi][1] = cc.solves;
-  m->iter_graph_counts[dir][pi][2] = cc.locals;
+  m->iter_graph_act[dir][pi][variant] = with_act;
+  m->iter_graph_counts[dir][pi][variant][0] = cc.launches;
+  m->iter_graph_counts[dir][pi][variant][1] = cc.solves;
+  m->iter_graph_counts[dir][pi][variant][2] = cc.locals;
   return g;
 }
 
@@ -389,21 +392,32 @@ cudaGraphExec_t iteration_graph(Ctx& c, int dir, int prec, bool with_act) {
 // rest (and everything when graphs are off) launched directly.  act / xnext are
 // the fixed per-step buffers.
 pd_status run_iterations(Ctx& c, int dir, int prec, const double* act, const double* xnext, int count) {
+  auto direct = [&]() {
+    return dir == 0 ? launch_fwd_iteration(c, prec, act) : launch_bwd_iteration(c, prec, xnext, act);
+  };
   int done = 0;
   if (c.graphs && count >= kGraphIters) {
-    cudaGraphExec_t g = iteration_graph(c, dir, prec, act != nullptr);
+    // profiled: a graph of all but one iteration, then the last one launched directly
+    // with its timing events (the GPU is still busy with the graph when they are
+    // recorded, so they time the kernels, not the host launch latency)
+    const int variant = (c.solve_t || c.local_t) ? 1 : 0;
+    cudaGraphExec_t g = iteration_graph(c, dir, prec, act != nullptr, variant);
     if (g) {
-      const int64_t* gc = c.m->iter_graph_counts[dir][prec == PD_PREC_MIXED ? 1 : 0];
+      const int64_t* gc = c.m->iter_graph_counts[dir][prec == PD_PREC_MIXED ? 1 : 0][variant];
       for (; done + kGraphIters <= count; done += kGraphIters) {
         PD_CUDA_TRY(cudaGraphLaunch(g, c.s));
         c.launches += gc[0];
         c.solves += gc[1];
         c.locals += gc[2];
+        if (variant) {
+          pd_status e = direct();
+          if (e != PD_OK) return e;
+        }
       }
     }
   }
   for (; done < count; ++done) {
-    pd_status e = dir == 0 ? launch_fwd_iteration(c, prec, act) : launch_bwd_iteration(c, prec, xnext, act);
+    pd_status e = direct();
     if (e != PD_OK) return e;
   }
   return PD_OK;
@@ -552,6 +566,8 @@ void finish_stats(Ctx& c, pd_stats* st) {
   st->local_steps = c.locals;
   st->solve_ms = c.solve_t ? c.solve_t->total_ms() : 0.0;
   st->local_ms = c.local_t ? c.local_t->total_ms() : 0.0;
+  st->solves_timed = c.solve_t ? c.solve_t->pairs() : 0;
+  st->local_steps_timed = c.local_t ? c.local_t->pairs() : 0;
 }
 
 pd_status check_flags(Ctx& c, pd_stats* stats) {
@@ -648,8 +664,9 @@ pd_status backward_step(Ctx& c, const double* xnext, const double* xt_, const do
   info.fp64_iters = fp64_launched;
   info.rel = sh->ref2 > 0 ? std::sqrt(sh->gn2_acc / sh->ref2) : 0.0;
   guess = std::max(1, sh->iters - 1);
-  // parameter gradients at x_{t+1} (FP64), then the state adjoint of step t
-  LocalArgs la{m, nullptr, xnext, w.z, act_t, PD_PREC_FP64};
+  // parameter gradients at x_{t+1} (per-element products in the factor's precision,
+  // FP64 accumulation over steps), then the state adjoint of step t
+  LocalArgs la{m, nullptr, xnext, w.z, act_t, prec};
   PD_CUDA_TRY(launch_element_param_grads(la, g_wc, g_wv, g_wm, g_act_t, c.s));
   BwdStateParams bp{};
   bp.n = c.n;

@@ -444,8 +444,11 @@ cudaError_t launch_element_param_grads(const LocalArgs& a, double* g_wc, double*
   p.g_act = g_act;
   p.flags = a.m->ws.flags;
   const int nb = element_blocks(a.m);
-  // parameter gradients are accumulated over steps: always FP64
-  element_kernel<double, MODE_PGRAD><<<nb, kElemThreads, 0, s>>>(p);
+  // per-element products in the requested precision, accumulated over the steps in FP64
+  if (a.precision == PD_PREC_MIXED)
+    element_kernel<float, MODE_PGRAD><<<nb, kElemThreads, 0, s>>>(p);
+  else
+    element_kernel<double, MODE_PGRAD><<<nb, kElemThreads, 0, s>>>(p);
   return cudaGetLastError();
 }
 

@@ -134,9 +134,11 @@ struct MeshImpl {
   // captured on cap_stream with the per-step inputs read from ws.act_cur /
   // ws.xnext_cur; dropped whenever a captured argument could change
   cudaStream_t cap_stream = nullptr;
-  cudaGraphExec_t iter_graph[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
-  bool iter_graph_act[2][2] = {{false, false}, {false, false}};
-  int64_t iter_graph_counts[2][2][3] = {};   // kernels, solves, local steps per replay
+  // [direction][precision][variant]: variant 1 holds one iteration fewer (profiled
+  // chunks launch their first iteration directly, with timing events)
+  cudaGraphExec_t iter_graph[2][2][2] = {};
+  bool iter_graph_act[2][2][2] = {};
+  int64_t iter_graph_counts[2][2][2][3] = {};   // kernels, solves, local steps per replay
   // material state
   bool factorized = false;
   int precision = PD_PREC_FP64;
