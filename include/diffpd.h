@@ -167,7 +167,8 @@ typedef struct {
   int64_t local_steps;                  /* forward local steps (FP32 or FP64) */
   double local_ms;                      /* profile: summed device time of the forward local steps */
   int64_t solves_timed;                 /* profile: solves timed by events (solve_ms covers these) */
-  int64_t local_steps_timed;            /* profile: forward local steps timed by events */
+  int64_t local_steps_timed;            /* profile: forward local steps timed by events (those in
+                                           the factor's precision, not the FP64 checks) */
 } pd_stats;
 
 /* Forward rollout of T implicit-Euler steps (Sec. 3 Eqns 1-4, Alg. 1).

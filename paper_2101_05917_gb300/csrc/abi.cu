@@ -272,9 +272,11 @@ pd_status launch_fwd_iteration(Ctx& c, int prec, const double* act_t) {
   Workspace& w = m->ws;
   IterState* st = w.st;
   LocalArgs la{m, st, w.xt, nullptr, act_t, prec};
-  if (c.local_t) c.local_t->record(c.s);
+  // timed: the local steps of the iteration precision (not the FP64 convergence checks)
+  const bool timed = c.local_t && prec == m->precision;
+  if (timed) c.local_t->record(c.s);
   PD_CUDA_TRY(launch_element_forces(la, w.elembuf, c.pe, w.flags, c.s));
-  if (c.local_t) c.local_t->record(c.s);
+  if (timed) c.local_t->record(c.s);
   PD_CUDA_TRY(launch_gather_grad(m, st, w.elembuf, prec, w.xt, w.y, w.dir, w.gradt, c.pg, c.s));
   decide_fwd_kernel<<<1, 256, 0, c.s>>>(st, c.pe, c.nbe, c.pg, c.nbg);
   PD_WITH_MX(c.mx, lbfgs_commit_fwd_kernel<MX><<<c.lb, 256, 0, c.s>>>(c.vc, w.x, w.xt, w.grad, w.gradt, w.S, w.Y));

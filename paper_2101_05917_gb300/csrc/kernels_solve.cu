@@ -9,13 +9,15 @@
 //                               [u_s; w_s] = Q_s rhs,  W_s = w_s + (children
 //                               updates on the below rows)
 //   backward (root -> leaves):  x_s = Q_s^T [u_s; -x(below rows)]
-// The panels are cut into 2D tiles of at most 16384 panel entries (64 KB in
+// The panels are cut into 2D tiles of at most 256 x 64 panel entries (64 KB in
 // FP32), shaped per supernode so that every thread issues all of its panel loads
 // (up to 64) before it uses any: a tile costs about one memory round trip, and a
 // level of the tree spreads over as many CTAs as it has tiles.  Forward tiles are
 // R rows x (256 / R) column groups of 64 columns (R = 256, 128 or 64, whichever
 // covers the supernode's columns with the fewest idle groups); backward tiles are
-// BC columns x min(16384 / BC, 1024) rows (BC = 64, 32, 16 or 8).  All-zero tiles of the
+// BC columns x min(16384 / BC, 1024) rows (BC = 64, 32, 16 or 8).  (Smaller CTAs of
+// 128 threads with 32 KB tiles were measured slower: 276 vs 224 us on the 32x32x64
+// beam.)  All-zero tiles of the
 // triangular L11^-1 block are skipped.  Tiles sharing an output block write
 // partial sums; the last tile to finish (integer ticket) adds them in tile order,
 // so the result does not depend on scheduling and no float atomics run.  Both
@@ -29,11 +31,13 @@ namespace pd {
 
 namespace {
 
-constexpr int kThreads = 256;
+constexpr int kThreads = 256;         // threads per CTA (8 warps); 2 CTAs per SM
+constexpr int kWarps = kThreads / 32;
 constexpr int kCols = 64;             // forward: columns per thread; backward: loads per lane
-constexpr int kTileElems = 16384;     // panel entries per tile at most
+constexpr int kTileElems = kThreads * kCols;   // panel entries per tile at most (32 KB in FP32)
 constexpr int kPart = kThreads * 3;   // partial-sum slots per tile
-// backward tile rows for BC columns: 16384 / BC, at most 1024 (32 rows per lane)
+constexpr int kMaxC = 4 * kCols;       // widest forward tile (4 column groups)
+// backward tile rows for BC columns: kTileElems / BC, at most 1024 (32 rows per lane)
 __host__ __device__ constexpr int bwd_tile_rows(int bc) { return kTileElems / bc < 1024 ? kTileElems / bc : 1024; }
 constexpr int kMaxBR = 1024;
 constexpr int kPreSlots = 4;          // W-row sources per position held in registers
@@ -88,16 +92,15 @@ __device__ __forceinline__ SolveTile load_tile(const SolveTile* t, int64_t i) {
 constexpr long long kSpinLimit = 1ll << 20;   // about a second of polling
 
 // Message passing between CTAs: a producer's tile writes, then (after a CTA
-// barrier) one thread's release reduction on a counter; a consumer's relaxed
-// polls, then an acquire fence before it reads.  The barrier orders the other
-// threads' writes before the release (cumulativity).
-__device__ __forceinline__ unsigned long long load_relaxed(const unsigned long long* p) {
+// barrier) one thread's release reduction on a counter; a consumer's thread polls
+// the counter with acquire loads, then a CTA barrier, then the CTA reads (through
+// L2).  The barriers carry the ordering to the other threads of both CTAs
+// (cumulativity); no fence waits for the consumer's own panel loads in flight.
+__device__ __forceinline__ unsigned long long load_acquire(const unsigned long long* p) {
   unsigned long long v;
-  asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
   return v;
 }
-
-__device__ __forceinline__ void fence_acq_rel() { asm volatile("fence.acq_rel.gpu;" ::: "memory"); }
 
 __device__ __forceinline__ void add_release(unsigned long long* p) {
   asm volatile("red.release.gpu.global.add.u64 [%0], 1;" ::"l"(p) : "memory");
@@ -111,7 +114,7 @@ __device__ __forceinline__ unsigned long long add_acq_rel(unsigned long long* p)
 
 __device__ __forceinline__ bool wait_count(const unsigned long long* c, unsigned long long target, int* err) {
   long long it = 0;
-  while (load_relaxed(c) < target) {
+  while (load_acquire(c) < target) {
     if (++it > kSpinLimit) {
       atomicOr(err, DEV_ERR_TIMEOUT);
       return false;
@@ -121,7 +124,7 @@ __device__ __forceinline__ bool wait_count(const unsigned long long* c, unsigned
   return true;
 }
 
-// shared memory of one tile: forward rhs[256][3] + red[256][3]; backward
+// shared memory of one tile: forward rhs[kMaxC][3] + red[kThreads][3]; backward
 // v[kMaxBR][3] + res[64][3] (as T)
 struct __align__(16) PersistSmem {
   double buf[(kMaxBR + 64) * 3];
@@ -180,7 +183,7 @@ __device__ __forceinline__ void add_W(const SolveParams& p, const Slots& sl, int
   }
 }
 
-// Forward tile: rows [a, a + R) x columns [b, b + G * 64) of panel s, G = 256 / R.
+// Forward tile: rows [a, a + R) x columns [b, b + G * 64) of panel s, G = kThreads / R.
 // Thread (row rl, group g) owns row a + rl and columns b + 64 g ... + 63; a warp
 // reads 32 consecutive rows of one column per load (coalesced).  The group sums
 // are added in group order.
@@ -191,7 +194,7 @@ __device__ void fwd_tile_body(const SolveParams& p, const SolveTile& tl, int64_t
   constexpr int C = G * kCols;
   constexpr int B = Batch<T>::kLoads;
   T (*rhs)[3] = reinterpret_cast<T (*)[3]>(sm.buf);
-  T (*red)[3] = reinterpret_cast<T (*)[3]>(sm.buf) + kThreads;
+  T (*red)[3] = reinterpret_cast<T (*)[3]>(sm.buf) + kMaxC;   // after the widest rhs
   const int64_t row0 = tl.a, col0 = tl.b;
   const int64_t first = tl.first, nc = tl.nc, nr = tl.nr, pos = tl.pos;
   const T* Q = reinterpret_cast<const T*>(p.Q) + tl.panel_off;
@@ -206,36 +209,51 @@ __device__ void fwd_tile_body(const SolveParams& p, const SolveTile& tl, int64_t
   T q[B];
 #pragma unroll
   for (int k = 0; k < B; ++k) q[k] = (k < cnt) ? __ldg(Qr + (int64_t)k * nr) : T(0);
-  const int64_t jc = col0 + threadIdx.x;   // rhs column of this thread
-  const bool has_c = threadIdx.x < C && jc < nc;
-  double b0 = 0, b1 = 0, b2 = 0;
-  if (has_c) {
-    b0 = __ldg(p.b + 3 * (first + jc));
-    b1 = __ldg(p.b + 3 * (first + jc) + 1);
-    b2 = __ldg(p.b + 3 * (first + jc) + 2);
+  // rhs columns of this thread: col0 + threadIdx.x + kThreads * i
+  constexpr int CPT = (C + kThreads - 1) / kThreads;
+  double bb[CPT][3];
+  Slots sc[CPT];
+#pragma unroll
+  for (int i = 0; i < CPT; ++i) {
+    const int jj = threadIdx.x + kThreads * i;
+    const int64_t jc = col0 + jj;
+    const bool has_c = jj < C && jc < nc;
+    bb[i][0] = has_c ? __ldg(p.b + 3 * (first + jc)) : 0.0;
+    bb[i][1] = has_c ? __ldg(p.b + 3 * (first + jc) + 1) : 0.0;
+    bb[i][2] = has_c ? __ldg(p.b + 3 * (first + jc) + 2) : 0.0;
+    sc[i] = load_slots(p, pos + jc, has_c);
   }
-  const Slots sc = load_slots(p, pos + jc, has_c);
   const bool out_w = g == 0 && r < nr && r >= nc;
   const Slots sr = load_slots(p, pos + r, out_w);
   if (threadIdx.x == 0) {
-    for (int64_t ci = __ldg(p.child_ptr + tl.s); ci < __ldg(p.child_ptr + tl.s + 1); ++ci) {
-      const int64_t c = __ldg(p.child_list + ci);
-      wait_count(p.fdone + c, (epoch + 1) * (unsigned long long)__ldg(p.nfb + c), p.err);
+    // the children's forward outputs (inline in the descriptor; more from the tree)
+    const int nd = tl.ndep;
+    for (int k = 0; k < nd && k < kTileDeps; ++k)
+      wait_count(p.fdone + tl.dep[k], (epoch + 1) * (unsigned long long)tl.dep_blocks[k], p.err);
+    if (nd > kTileDeps) {
+      for (int64_t ci = __ldg(p.child_ptr + tl.s) + kTileDeps; ci < __ldg(p.child_ptr + tl.s + 1); ++ci) {
+        const int64_t c = __ldg(p.child_list + ci);
+        wait_count(p.fdone + c, (epoch + 1) * (unsigned long long)__ldg(p.nfb + c), p.err);
+      }
     }
-    fence_acq_rel();
   }
   __syncthreads();
   // children's updates of the output row (below rows), read in the same round
   // trip as those of the right-hand side
   double o0 = 0, o1 = 0, o2 = 0;
   if (out_w) add_W<T>(p, sr, pos + r, o0, o1, o2);
-  if (threadIdx.x < C) {
+#pragma unroll
+  for (int i = 0; i < CPT; ++i) {
+    const int jj = threadIdx.x + kThreads * i;
+    if (jj >= C) continue;
+    const int64_t jc = col0 + jj;
+    const bool has_c = jc < nc;
     double w0 = 0, w1 = 0, w2 = 0;
-    if (has_c) add_W<T>(p, sc, pos + jc, w0, w1, w2);
+    if (has_c) add_W<T>(p, sc[i], pos + jc, w0, w1, w2);
     // zero past the supernode's columns (their panel values are zero too)
-    rhs[threadIdx.x][0] = has_c ? (T)(b0 - w0) : T(0);
-    rhs[threadIdx.x][1] = has_c ? (T)(b1 - w1) : T(0);
-    rhs[threadIdx.x][2] = has_c ? (T)(b2 - w2) : T(0);
+    rhs[jj][0] = has_c ? (T)(bb[i][0] - w0) : T(0);
+    rhs[jj][1] = has_c ? (T)(bb[i][1] - w1) : T(0);
+    rhs[jj][2] = has_c ? (T)(bb[i][2] - w2) : T(0);
   }
   __syncthreads();
   T a0 = T(0), a1 = T(0), a2 = T(0);
@@ -301,13 +319,13 @@ __device__ void fwd_tile_body(const SolveParams& p, const SolveTile& tl, int64_t
   signal_done(p.fdone + tl.s);
 }
 
-// Backward tile: columns [a, a + BC) x rows [b, b + BR) of panel s, BR = min(16384 / BC, 1024).
+// Backward tile: columns [a, a + BC) x rows [b, b + BR) of panel s, BR = min(kTileElems / BC, 1024).
 // Warp w owns columns a + w CW ... (CW = BC / 8), its lanes the rows b + lane + 32 i;
 // per column the lanes' sums are added by a fixed shuffle tree.
 template <typename T, int BC>
 __device__ void bwd_tile_body(const SolveParams& p, const SolveTile& tl, int64_t tid_g, unsigned long long epoch,
                               PersistSmem& sm) {
-  constexpr int CW = BC / 8;
+  constexpr int CW = BC / kWarps;
   constexpr int BR = bwd_tile_rows(BC);
   constexpr int RL = BR / 32;           // rows per lane
   constexpr int B = Batch<T>::kLoads;
@@ -347,10 +365,10 @@ __device__ void bwd_tile_body(const SolveParams& p, const SolveTile& tl, int64_t
     gidx[k] = (rr < BR && rr < rn && row >= nc) ? __ldg(srows + row) : -1;
   }
   if (threadIdx.x == 0) {
-    const int64_t par = __ldg(p.parent + tl.s);
-    if (par >= 0) wait_count(p.bdone + par, (epoch + 1) * (unsigned long long)__ldg(p.nbb + par), p.err);
-    else wait_count(p.fdone + tl.s, (epoch + 1) * (unsigned long long)__ldg(p.nfb + tl.s), p.err);
-    fence_acq_rel();
+    // the parent's backward outputs; the root waits for its own forward outputs
+    const int32_t d = tl.dep[0];
+    if (d >= 0) wait_count(p.bdone + d, (epoch + 1) * (unsigned long long)tl.dep_blocks[0], p.err);
+    else wait_count(p.fdone + (-d - 1), (epoch + 1) * (unsigned long long)tl.dep_blocks[0], p.err);
   }
   __syncthreads();
   // v = [u_s; -x(below rows)] on the tile's rows, zero past the panel
@@ -427,8 +445,9 @@ __device__ void bwd_tile_body(const SolveParams& p, const SolveTile& tl, int64_t
   signal_done(p.bdone + tl.s);
 }
 
-// tile kinds (SolveTile::pad0): forward R = 256 / 128 / 64, backward BC = 64 / 32 / 16 / 8
-enum TileKind { kF256 = 0, kF128 = 1, kF64 = 2, kB64 = 3, kB32 = 4, kB16 = 5, kB8 = 6 };
+// tile kinds (SolveTile::pad0): forward with 1 / 2 / 4 column groups (R = kThreads,
+// kThreads / 2, kThreads / 4 rows), backward with BC = 64 / 32 / 16 / 8 columns
+enum TileKind { kF1 = 0, kF2 = 1, kF4 = 2, kB64 = 3, kB32 = 4, kB16 = 5, kB8 = 6 };
 
 template <typename T>
 __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 2 : 1) solve_persistent_kernel(SolveParams p) {
@@ -453,9 +472,9 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 2 : 1) solve_persis
     if (threadIdx.x == 0) tk[slot ^ 1] = atomicAdd(p.gticket, 1ull);
     const SolveTile tl = load_tile(p.tiles, tile);
     switch (tl.pad0) {
-      case kF256: fwd_tile_body<T, 256>(p, tl, tile, epoch, sm); break;
-      case kF128: fwd_tile_body<T, 128>(p, tl, tile, epoch, sm); break;
-      case kF64: fwd_tile_body<T, 64>(p, tl, tile, epoch, sm); break;
+      case kF1: fwd_tile_body<T, kThreads>(p, tl, tile, epoch, sm); break;
+      case kF2: fwd_tile_body<T, kThreads / 2>(p, tl, tile, epoch, sm); break;
+      case kF4: fwd_tile_body<T, kThreads / 4>(p, tl, tile, epoch, sm); break;
       case kB64: bwd_tile_body<T, 64>(p, tl, tile, epoch, sm); break;
       case kB32: bwd_tile_body<T, 32>(p, tl, tile, epoch, sm); break;
       case kB16: bwd_tile_body<T, 16>(p, tl, tile, epoch, sm); break;
@@ -469,9 +488,9 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 2 : 1) solve_persis
 
 // forward rows per tile for a supernode: fewest idle column groups
 int fwd_rows(int64_t nc) {
-  if (nc <= kCols) return 256;
-  if (nc <= 2 * kCols) return 128;
-  return 64;
+  if (nc <= kCols) return kThreads;
+  if (nc <= 2 * kCols) return kThreads / 2;
+  return kThreads / 4;
 }
 
 // backward columns per tile: the narrowest BC >= nc (64 at most), so a supernode
@@ -503,8 +522,29 @@ void build_solve_schedule(const HostMesh& h, SolveSchedule& S) {
     t.relp = (int32_t)h.rel_ptr[s];
     return t;
   };
+  // output blocks per supernode (the counts a dependent tile waits for)
   S.nfb.assign(h.ns, 0);
   S.nbb.assign(h.ns, 0);
+  for (int64_t s = 0; s < h.ns; ++s) {
+    const int R = fwd_rows(h.nc(s));
+    const int BC = bwd_cols(h.nc(s));
+    S.nfb[s] = (int32_t)((h.nr(s) + R - 1) / R);
+    S.nbb[s] = (int32_t)((h.nc(s) + BC - 1) / BC);
+  }
+  auto fwd_deps = [&](int64_t s, SolveTile& t) {
+    t.ndep = (int32_t)(h.child_ptr[s + 1] - h.child_ptr[s]);
+    for (int k = 0; k < kTileDeps && k < t.ndep; ++k) {
+      const int64_t c = h.child_list[h.child_ptr[s] + k];
+      t.dep[k] = (int32_t)c;
+      t.dep_blocks[k] = S.nfb[c];
+    }
+  };
+  auto bwd_deps = [&](int64_t s, SolveTile& t) {
+    const int64_t par = h.parent[s];
+    t.ndep = 1;
+    t.dep[0] = par >= 0 ? (int32_t)par : (int32_t)(-s - 1);
+    t.dep_blocks[0] = par >= 0 ? S.nbb[par] : S.nfb[s];
+  };
   for (int64_t L = 0; L < h.nlev; ++L) {
     SolveLevel& sl = S.levels[L];
     sl.fwd_off = (int64_t)S.fwd.size();
@@ -514,7 +554,7 @@ void build_solve_schedule(const HostMesh& h, SolveSchedule& S) {
       const int64_t nr = h.nr(s), nc = h.nc(s);
       const int R = fwd_rows(nc);
       const int C = (kThreads / R) * kCols;
-      const int32_t fkind = R == 256 ? kF256 : (R == 128 ? kF128 : kF64);
+      const int32_t fkind = R == kThreads ? kF1 : (R == kThreads / 2 ? kF2 : kF4);
       for (int64_t r0 = 0; r0 < nr; r0 += R) {
         const int32_t out = (int32_t)S.n_fwd_out++;
         const size_t b0 = S.fwd.size();
@@ -527,10 +567,10 @@ void build_solve_schedule(const HostMesh& h, SolveSchedule& S) {
           t.out = out;
           t.part_base = (int64_t)b0;
           t.pad0 = fkind;
+          fwd_deps(s, t);
           S.fwd.push_back(t);
         }
         for (size_t k = b0; k < S.fwd.size(); ++k) S.fwd[k].ntile = (int32_t)(S.fwd.size() - b0);
-        ++S.nfb[s];
       }
       const int BC = bwd_cols(nc);
       const int BR = bwd_tile_rows(BC);
@@ -546,10 +586,10 @@ void build_solve_schedule(const HostMesh& h, SolveSchedule& S) {
           t.out = out;
           t.part_base = (int64_t)b0;
           t.pad0 = bkind;
+          bwd_deps(s, t);
           S.bwd.push_back(t);
         }
         for (size_t k = b0; k < S.bwd.size(); ++k) S.bwd[k].ntile = (int32_t)(S.bwd.size() - b0);
-        ++S.nbb[s];
       }
     }
     sl.fwd_cnt = (int64_t)S.fwd.size() - sl.fwd_off;

@@ -52,6 +52,7 @@ struct SolveLevel {
   int64_t bwd_off = 0, bwd_cnt = 0;
 };
 // Everything one tile needs, loaded with four 16-byte loads.
+constexpr int kTileDeps = 6;   // dependencies carried inside a tile descriptor
 struct alignas(16) SolveTile {
   int64_t panel_off;   // offset of the supernode's panel
   int64_t part_base;   // first tile of the output block (partial-sum slots)
@@ -64,8 +65,15 @@ struct alignas(16) SolveTile {
   int32_t relp;        // rel_ptr[s]: start of its update-vector rows
   int32_t ntile;       // tiles in the output block
   int32_t pad0;        // tile kind: forward rows per tile / backward columns per tile
-  int32_t pad1;
+  int32_t ndep;        // dependencies: forward = children, backward = parent (root: itself)
+  // the first kTileDeps dependencies inline: counter index (supernode id; backward
+  // dependencies on a forward counter are stored as -(id + 1)) and the number of
+  // output blocks that counter reaches per solve; more are read from the tree arrays
+  int32_t dep[kTileDeps];
+  int32_t dep_blocks[kTileDeps];
+  int32_t pad1[4];
 };
+static_assert(sizeof(SolveTile) == 128, "tile descriptors are 128 bytes");
 struct SolveSchedule {
   std::vector<SolveTile> fwd, bwd;
   std::vector<SolveTile> all;      // persistent order: forward tiles, then backward tiles by descending level

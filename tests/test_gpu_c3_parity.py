@@ -69,4 +69,6 @@ def test_c3_through_first_contact(precision, tol):
     assert contact == int(g["contact_nodes"][-1])
     assert pos <= 1e-5
     assert max(gv0, gx0) <= 1e-4
-    assert abs(gmu - float(g["g_mu"])) <= 1e-4 * abs(float(g["g_mu"]))
+    # every contact node is in the static friction regime here (m |v_t| / h < mu f_n),
+    # where the friction force does not depend on mu: both sides give 0
+    assert abs(gmu - float(g["g_mu"])) <= 1e-4 * abs(float(g["g_mu"])) + 1e-12
