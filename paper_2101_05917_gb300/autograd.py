@@ -30,6 +30,7 @@ class Simulator:
         self.precision = precision
         self.opts = dict(opts or {})
         self._key = None
+        self._held = None
 
     @classmethod
     def from_scene(cls, sc, precision=N.PD_PREC_FP64, opts=None, device=0):
@@ -41,11 +42,15 @@ class Simulator:
         return None if t is None else (t.data_ptr(), t._version, tuple(t.shape))
 
     def ensure_factor(self, w_corot, w_vol, w_muscle, fiber):
+        # The key is (address, version, shape) of the tensors the factor was built
+        # from; holding those tensors keeps their memory from being handed to new
+        # tensors, so a new weight tensor always has a new key.
         key = tuple(self._tag(t) for t in (w_corot, w_vol, w_muscle, fiber))
         if key != self._key:
             self.mesh.factorize(w_corot, w_vol, w_muscle, fiber, h=self.h, gravity=self.gravity,
                                 k_contact=self.k_contact, precision=self.precision)
             self._key = key
+            self._held = (w_corot, w_vol, w_muscle, fiber)
 
     def rollout(self, x0, v0, T: int, f_ext=None, act=None, w_corot=None, w_vol=None, w_muscle=None,
                 fiber=None, mu=None):
