@@ -214,6 +214,29 @@ pd_status pd_hessian_vector(pd_mesh m, const double* x, const double* act, const
  * rows of x are set to zero) with the prefactorised supernodal factor. */
 pd_status pd_solve_A(pd_mesh m, const double* b, double* x, int32_t precision, void* stream);
 
+/* Complementarity contact (Sec. 5.2): the global step with the contact set C held
+ * fixed -- the solve inside Alg. 3, which Alg. 4 evaluates with a low-rank update
+ * of the prefactorised A.  Every node j in C is held at its target x*_j; the other
+ * free nodes C' solve A_{C'C'} x_{C'} = b_{C'}.
+ *
+ * pd_contact_prepare: after pd_factorize, computes the columns L_A^-1 e_j of every
+ * candidate node (candidates_host: per kept node, nonzero = candidate; fixed nodes
+ * are never candidates) in FP64, three per solve; memory nf x (candidates) doubles.
+ * A later pd_factorize makes them stale (PD_ERR_INVALID_ARG until prepared again). */
+pd_status pd_contact_prepare(pd_mesh m, const uint8_t* candidates_host, void* stream);
+
+/* Fixes the contact set: c distinct kept node ids (host), each a candidate; forms
+ * S = (L_A^-1)_{CC} and its inverse (FP64 Cholesky on the host; PD_ERR_NOT_SPD if it
+ * fails).  c = 0 clears the set.  Synchronises the stream. */
+pd_status pd_contact_set(pd_mesh m, const int32_t* nodes_host, int64_t c, void* stream);
+
+/* x (n,3) with x_C = x* and A_{C'C'} x_{C'} = b_{C'}: one solve of A (precision as
+ * pd_solve_A) then x = a1 - B_{.,C} S^-1 (a1)_C in FP64.  b, x: (n,3) device, kept
+ * order (Dirichlet rows of x are zero); x_star: (c,3) device, in the order given to
+ * pd_contact_set (NULL when c = 0). */
+pd_status pd_solve_A_contact(pd_mesh m, const double* b, const double* x_star, double* x, int32_t precision,
+                             void* stream);
+
 /* Local step that allocates no device memory (the paper has no counterpart).
  * For callers that cannot call cudaMalloc -- e.g. while a CUDA graph is being
  * captured, under a device-memory budget fixed in advance, or behind an allocator

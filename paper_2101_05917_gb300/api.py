@@ -200,6 +200,26 @@ class PDMesh:
                                           _stream(stream)), "pd_hessian_vector")
         return out
 
+    # ---------------------------------------------------- complementarity contact
+    def contact_prepare(self, candidates, stream=None):
+        """L_A^-1 columns of the contact candidates (per kept node mask), after factorize."""
+        arr, p = _u8(candidates, self.n, "candidates")
+        N.check(N.lib().pd_contact_prepare(self.handle, p, _stream(stream)), "pd_contact_prepare")
+
+    def contact_set(self, nodes, stream=None):
+        """Fixes the contact set (kept node ids, each a candidate)."""
+        arr = np.ascontiguousarray(np.asarray(nodes, dtype=np.int32).reshape(-1))
+        N.check(N.lib().pd_contact_set(self.handle, arr.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), arr.size,
+                                       _stream(stream)), "pd_contact_set")
+        self.contact_count = int(arr.size)
+
+    def solve_contact(self, b, x_star=None, precision=N.PD_PREC_FP64, stream=None):
+        """x with x_C = x_star ((c,3), set order) and A_{C'C'} x_{C'} = b_{C'}."""
+        out = torch.empty((self.n, 3), dtype=torch.float64, device=b.device)
+        N.check(N.lib().pd_solve_A_contact(self.handle, _ptr(b), _ptr(x_star), _ptr(out), precision,
+                                           _stream(stream)), "pd_solve_A_contact")
+        return out
+
     def solve(self, b, precision=N.PD_PREC_FP64, stream=None):
         out = torch.empty((self.n, 3), dtype=torch.float64, device=b.device)
         N.check(N.lib().pd_solve_A(self.handle, _ptr(b), _ptr(out), precision, _stream(stream)), "pd_solve_A")

@@ -20,7 +20,8 @@ OUT_DIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(OUT_DIR, "libdiffpd.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES_CU = ["abi.cu", "kernels_local.cu", "kernels_factor.cu", "kernels_solve.cu", "serve.cu", "noalloc.cu"]
+SOURCES_CU = ["abi.cu", "kernels_local.cu", "kernels_factor.cu", "kernels_solve.cu", "kernels_contact.cu", "serve.cu",
+              "noalloc.cu"]
 SOURCES_CPP = ["mesh_host.cpp"]
 
 

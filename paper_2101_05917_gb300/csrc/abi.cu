@@ -959,6 +959,7 @@ pd_status pd_factorize(pd_mesh mesh, const double* w_corot, const double* w_vol,
   if (!I.Q64) PD_CUDA_TRY(dalloc(&I, &I.Q64, (size_t)nnz));
   if (I.precision == PD_PREC_MIXED && !I.Q32) PD_CUDA_TRY(dalloc(&I, &I.Q32, (size_t)nnz));
   drop_iteration_graphs(&I);   // they captured the weights, panels and precision
+  I.factor_gen += 1;           // contact candidate columns of the old factor are stale
   I.factorized = false;
   pd_status r = factorize_device(&I, s);
   if (r == PD_OK) I.factorized = true;
@@ -1262,6 +1263,178 @@ pd_status pd_solve_A(pd_mesh mesh, const double* b, double* x, int32_t precision
   PD_CUDA_TRY(reset_solve_counters(m, s));
   PD_CUDA_TRY(solve_A(m, nullptr, w.iov, w.iox, precision, s));
   internal_to_kept_kernel<<<grid_for(n), 256, 0, s>>>(n, m->h.nf, m->kept_of_internal, w.iox, x);
+  PD_CUDA_TRY(cudaGetLastError());
+  return PD_OK;
+}
+
+}  // extern "C"
+
+// ------------------------------------------------------------ complementarity contact
+namespace {
+
+// In-place inverse of a symmetric positive definite c x c matrix (row-major) by
+// Cholesky S = L L^T, then S^-1 = L^-T L^-1 column by column.  False if a pivot is
+// not positive.
+bool spd_inverse(std::vector<double>& S, int64_t c) {
+  std::vector<double> L(S.size(), 0.0);
+  for (int64_t j = 0; j < c; ++j) {
+    double d = S[j * c + j];
+    for (int64_t k = 0; k < j; ++k) d -= L[j * c + k] * L[j * c + k];
+    if (!(d > 0.0)) return false;
+    const double ljj = std::sqrt(d);
+    L[j * c + j] = ljj;
+    for (int64_t i = j + 1; i < c; ++i) {
+      double v = S[i * c + j];
+      for (int64_t k = 0; k < j; ++k) v -= L[i * c + k] * L[j * c + k];
+      L[i * c + j] = v / ljj;
+    }
+  }
+  std::vector<double> y(c), x(c);
+  for (int64_t col = 0; col < c; ++col) {
+    for (int64_t i = 0; i < c; ++i) {   // L y = e_col
+      double v = i == col ? 1.0 : 0.0;
+      for (int64_t k = 0; k < i; ++k) v -= L[i * c + k] * y[k];
+      y[i] = v / L[i * c + i];
+    }
+    for (int64_t i = c - 1; i >= 0; --i) {   // L^T x = y
+      double v = y[i];
+      for (int64_t k = i + 1; k < c; ++k) v -= L[k * c + i] * x[k];
+      x[i] = v / L[i * c + i];
+    }
+    for (int64_t i = 0; i < c; ++i) S[i * c + col] = x[i];
+  }
+  return true;
+}
+
+}  // namespace
+
+extern "C" {
+
+pd_status pd_contact_prepare(pd_mesh mesh, const uint8_t* candidates_host, void* stream) {
+  pd_status ck = check_mesh(mesh, true);
+  if (ck != PD_OK) return ck;
+  if (!candidates_host) {
+    set_error("pd_contact_prepare: candidates are required");
+    return PD_ERR_INVALID_ARG;
+  }
+  MeshImpl* m = &mesh->impl;
+  DeviceGuard g(m->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  const HostMesh& h = m->h;
+  std::vector<int32_t> cand;
+  m->cand_of_internal.assign(h.n, -1);
+  for (int64_t k = 0; k < h.n; ++k) {
+    if (!candidates_host[k]) continue;
+    const int32_t in = h.internal_of_kept[k];
+    if (in >= h.nf) continue;   // fixed nodes are never in contact
+    m->cand_of_internal[in] = (int32_t)cand.size();
+    cand.push_back(in);
+  }
+  m->ncand = (int64_t)cand.size();
+  PD_CUDA_TRY(upload(m, &m->cand, cand));
+  PD_CUDA_TRY(dalloc(m, &m->Bc, (size_t)std::max<int64_t>(h.nf * m->ncand, 1)));
+  Workspace& w = m->ws;
+  for (int64_t k0 = 0; k0 < m->ncand; k0 += 3) {
+    const int count = (int)std::min<int64_t>(3, m->ncand - k0);
+    PD_CUDA_TRY(contact_unit_rhs(h.nf, m->cand, k0, count, w.iov, s));
+    PD_CUDA_TRY(reset_solve_counters(m, s));
+    PD_CUDA_TRY(solve_A(m, nullptr, w.iov, w.iox, PD_PREC_FP64, s));
+    PD_CUDA_TRY(contact_extract_columns(h.nf, w.iox, k0, count, m->Bc, s));
+  }
+  PD_CUDA_TRY(cudaStreamSynchronize(s));
+  m->contact_gen = m->factor_gen;
+  m->cset = 0;
+  return PD_OK;
+}
+
+pd_status pd_contact_set(pd_mesh mesh, const int32_t* nodes_host, int64_t c, void* stream) {
+  pd_status ck = check_mesh(mesh, true);
+  if (ck != PD_OK) return ck;
+  MeshImpl* m = &mesh->impl;
+  if (m->contact_gen != m->factor_gen) {
+    set_error("pd_contact_set: call pd_contact_prepare after the last pd_factorize");
+    return PD_ERR_INVALID_ARG;
+  }
+  if (c < 0 || (c > 0 && !nodes_host) || c > m->ncand) {
+    set_error("pd_contact_set: invalid contact set size");
+    return PD_ERR_INVALID_ARG;
+  }
+  DeviceGuard g(m->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  const HostMesh& h = m->h;
+  std::vector<int32_t> node(c), cidx(c);
+  std::vector<uint8_t> seen(m->ncand, 0);
+  for (int64_t k = 0; k < c; ++k) {
+    const int32_t kept = nodes_host[k];
+    if (kept < 0 || kept >= h.n) {
+      set_error("pd_contact_set: node id out of range");
+      return PD_ERR_INVALID_ARG;
+    }
+    const int32_t in = h.internal_of_kept[kept];
+    const int32_t ci = m->cand_of_internal[in];
+    if (ci < 0 || seen[ci]) {
+      set_error("pd_contact_set: every node must be a distinct contact candidate");
+      return PD_ERR_INVALID_ARG;
+    }
+    seen[ci] = 1;
+    node[k] = in;
+    cidx[k] = ci;
+  }
+  if (c > m->cset_cap) {
+    PD_CUDA_TRY(dalloc(m, &m->cset_node, (size_t)c));
+    PD_CUDA_TRY(dalloc(m, &m->cset_cand, (size_t)c));
+    PD_CUDA_TRY(dalloc(m, &m->cset_Sinv, (size_t)(c * c)));
+    PD_CUDA_TRY(dalloc(m, &m->cset_lam, (size_t)(3 * c)));
+    m->cset_cap = c;
+  }
+  m->cset = 0;
+  if (c == 0) return PD_OK;
+  PD_CUDA_TRY(cudaMemcpyAsync(m->cset_node, node.data(), sizeof(int32_t) * c, cudaMemcpyHostToDevice, s));
+  PD_CUDA_TRY(cudaMemcpyAsync(m->cset_cand, cidx.data(), sizeof(int32_t) * c, cudaMemcpyHostToDevice, s));
+  PD_CUDA_TRY(contact_gather_S(h.nf, m->Bc, m->cset_node, m->cset_cand, c, m->cset_Sinv, s));
+  std::vector<double> S((size_t)(c * c));
+  PD_CUDA_TRY(cudaMemcpyAsync(S.data(), m->cset_Sinv, sizeof(double) * c * c, cudaMemcpyDeviceToHost, s));
+  PD_CUDA_TRY(cudaStreamSynchronize(s));
+  // symmetrise (the two halves come from different solves) before the factorisation
+  for (int64_t i = 0; i < c; ++i)
+    for (int64_t j = i + 1; j < c; ++j) S[i * c + j] = S[j * c + i] = 0.5 * (S[i * c + j] + S[j * c + i]);
+  if (!spd_inverse(S, c)) {
+    set_error("pd_contact_set: (A^-1)_CC is not positive definite");
+    return PD_ERR_NOT_SPD;
+  }
+  PD_CUDA_TRY(cudaMemcpyAsync(m->cset_Sinv, S.data(), sizeof(double) * c * c, cudaMemcpyHostToDevice, s));
+  PD_CUDA_TRY(cudaStreamSynchronize(s));
+  m->cset = c;
+  return PD_OK;
+}
+
+pd_status pd_solve_A_contact(pd_mesh mesh, const double* b, const double* x_star, double* x, int32_t precision,
+                             void* stream) {
+  pd_status ck = check_mesh(mesh, true);
+  if (ck != PD_OK) return ck;
+  MeshImpl* m = &mesh->impl;
+  if (!b || !x || (m->cset > 0 && !x_star)) {
+    set_error("pd_solve_A_contact: b, x and (with a contact set) x_star are required");
+    return PD_ERR_INVALID_ARG;
+  }
+  if (m->contact_gen != m->factor_gen) {
+    set_error("pd_solve_A_contact: call pd_contact_prepare after the last pd_factorize");
+    return PD_ERR_INVALID_ARG;
+  }
+  if (precision == PD_PREC_MIXED && !m->Q32) {
+    set_error("pd_solve_A_contact: FP32 panels exist only after a PD_PREC_MIXED factorisation");
+    return PD_ERR_INVALID_ARG;
+  }
+  DeviceGuard g(m->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  Workspace& w = m->ws;
+  const int64_t n = m->h.n;
+  kept_to_internal_kernel<<<grid_for(n), 256, 0, s>>>(n, m->kept_of_internal, b, w.iov);
+  PD_CUDA_TRY(reset_solve_counters(m, s));
+  PD_CUDA_TRY(solve_A(m, nullptr, w.iov, w.iox, precision, s));
+  PD_CUDA_TRY(contact_correct(m->h.nf, m->Bc, m->cset_node, m->cset_cand, m->cset, m->cset_Sinv, m->cset_lam,
+                              w.iox, x_star, w.iov, s));
+  internal_to_kept_kernel<<<grid_for(n), 256, 0, s>>>(n, m->h.nf, m->kept_of_internal, w.iov, x);
   PD_CUDA_TRY(cudaGetLastError());
   return PD_OK;
 }

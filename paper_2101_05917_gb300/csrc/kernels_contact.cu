@@ -1,0 +1,141 @@
+// Complementarity contact (Sec. 5.2): the global step with the contact set C held
+// fixed (Alg. 3's inner solve, computed by Alg. 4 with a low-rank update of the
+// prefactorised A).
+//
+// A = I_3 (x) L_A, so everything is scalar per coordinate.  With the columns
+// B_j = L_A^-1 e_j of every contact candidate j precomputed once per
+// factorisation, the solution with x_C = x* and L_{C'C'} x_{C'} = b_{C'} is
+//   a1 = L_A^-1 b,  lambda = S^-1 (a1)_C  with S = (L_A^-1)_{CC} = B_{C,C},
+//   x  = a1 - B_{.,C} lambda,  then x_C = x*.
+// (Multipliers lambda on the rows of C make (a1 - B lambda)_C = 0, and the rows
+// C' of L_A x + E_C lambda = b are the reduced system.)  This is the same rank-|C|
+// update of A as the paper's Woodbury identity, written with the |C| x |C| matrix
+// S instead of its 2|C| x 2|C| one; the result is identical in exact arithmetic.
+// Per solve it costs one solve of A plus O(nf |C|) work.
+#include "pd_internal.cuh"
+
+namespace pd {
+
+namespace {
+
+constexpr int kT = 256;
+
+// b = 0 except b[3 cand[k0 + i] + i] = 1, i < count (<= 3): three unit right-hand
+// sides, one per coordinate column
+__global__ void unit_rhs_kernel(const int32_t* cand, int64_t k0, int count, double* b) {
+  const int i = threadIdx.x;
+  if (i < count) b[3 * (int64_t)cand[k0 + i] + i] = 1.0;
+}
+
+// Bc[:, k0 + j] = x[:, j] (coordinate column j of the solve), j < count
+__global__ void extract_columns_kernel(int64_t nf, const double* x, int64_t k0, int count, double* Bc) {
+  const int64_t i = (int64_t)blockIdx.x * kT + threadIdx.x;
+  if (i >= nf) return;
+  for (int j = 0; j < count; ++j) Bc[(k0 + j) * nf + i] = x[3 * i + j];
+}
+
+// S[r][k] = Bc[cidx[k]][node[r]]  (c x c, row-major)
+__global__ void gather_S_kernel(int64_t nf, const double* Bc, const int32_t* node, const int32_t* cidx, int64_t c,
+                                double* S) {
+  const int64_t t = (int64_t)blockIdx.x * kT + threadIdx.x;
+  if (t >= c * c) return;
+  const int64_t r = t / c, k = t % c;
+  S[t] = Bc[(int64_t)cidx[k] * nf + node[r]];
+}
+
+// lambda[r] = sum_k Sinv[k][r] a1[node[k]] (Sinv symmetric: column reads coalesce)
+__global__ void lambda_kernel(const double* Sinv, const int32_t* node, int64_t c, const double* a1, double* lam) {
+  const int64_t r = (int64_t)blockIdx.x * kT + threadIdx.x;
+  if (r >= c) return;
+  double l0 = 0, l1 = 0, l2 = 0;
+  for (int64_t k = 0; k < c; ++k) {
+    const double s = Sinv[k * c + r];
+    const int64_t g = 3 * (int64_t)node[k];
+    l0 += s * a1[g];
+    l1 += s * a1[g + 1];
+    l2 += s * a1[g + 2];
+  }
+  lam[3 * r] = l0;
+  lam[3 * r + 1] = l1;
+  lam[3 * r + 2] = l2;
+}
+
+// x[i] = a1[i] - sum_k Bc[cidx[k]][i] lambda[k] for the free nodes i; the
+// multipliers pass through shared memory in chunks
+constexpr int kChunk = 512;
+__global__ void correct_kernel(int64_t nf, const double* Bc, const int32_t* cidx, int64_t c, const double* lam,
+                               const double* a1, double* x) {
+  __shared__ double sl[kChunk][3];
+  __shared__ int32_t sc[kChunk];
+  const int64_t i = (int64_t)blockIdx.x * kT + threadIdx.x;
+  double x0 = 0, x1 = 0, x2 = 0;
+  for (int64_t k0 = 0; k0 < c; k0 += kChunk) {
+    const int64_t kn = c - k0 < kChunk ? c - k0 : kChunk;
+    __syncthreads();
+    for (int64_t k = threadIdx.x; k < kn; k += kT) {
+      sl[k][0] = lam[3 * (k0 + k)];
+      sl[k][1] = lam[3 * (k0 + k) + 1];
+      sl[k][2] = lam[3 * (k0 + k) + 2];
+      sc[k] = cidx[k0 + k];
+    }
+    __syncthreads();
+    if (i < nf) {
+      for (int64_t k = 0; k < kn; ++k) {
+        const double bv = Bc[(int64_t)sc[k] * nf + i];
+        x0 += bv * sl[k][0];
+        x1 += bv * sl[k][1];
+        x2 += bv * sl[k][2];
+      }
+    }
+  }
+  if (i < nf) {
+    x[3 * i] = a1[3 * i] - x0;
+    x[3 * i + 1] = a1[3 * i + 1] - x1;
+    x[3 * i + 2] = a1[3 * i + 2] - x2;
+  }
+}
+
+// x[node[k]] = xstar[k]
+__global__ void set_targets_kernel(const int32_t* node, int64_t c, const double* xstar, double* x) {
+  const int64_t k = (int64_t)blockIdx.x * kT + threadIdx.x;
+  if (k >= c) return;
+  const int64_t g = 3 * (int64_t)node[k];
+  x[g] = xstar[3 * k];
+  x[g + 1] = xstar[3 * k + 1];
+  x[g + 2] = xstar[3 * k + 2];
+}
+
+unsigned blocks(int64_t n) { return (unsigned)((n + kT - 1) / kT); }
+
+}  // namespace
+
+cudaError_t contact_unit_rhs(int64_t nf, const int32_t* cand, int64_t k0, int count, double* b, cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(b, 0, sizeof(double) * 3 * nf, s);
+  if (e != cudaSuccess) return e;
+  unit_rhs_kernel<<<1, 32, 0, s>>>(cand, k0, count, b);
+  return cudaGetLastError();
+}
+
+cudaError_t contact_extract_columns(int64_t nf, const double* x, int64_t k0, int count, double* Bc,
+                                    cudaStream_t s) {
+  extract_columns_kernel<<<blocks(nf), kT, 0, s>>>(nf, x, k0, count, Bc);
+  return cudaGetLastError();
+}
+
+cudaError_t contact_gather_S(int64_t nf, const double* Bc, const int32_t* node, const int32_t* cidx, int64_t c,
+                             double* S, cudaStream_t s) {
+  if (c == 0) return cudaSuccess;
+  gather_S_kernel<<<blocks(c * c), kT, 0, s>>>(nf, Bc, node, cidx, c, S);
+  return cudaGetLastError();
+}
+
+cudaError_t contact_correct(int64_t nf, const double* Bc, const int32_t* node, const int32_t* cidx, int64_t c,
+                            const double* Sinv, double* lam, const double* a1, const double* xstar, double* x,
+                            cudaStream_t s) {
+  if (c > 0) lambda_kernel<<<blocks(c), kT, 0, s>>>(Sinv, node, c, a1, lam);
+  correct_kernel<<<blocks(nf), kT, 0, s>>>(nf, Bc, cidx, c, lam, a1, x);
+  if (c > 0) set_targets_kernel<<<blocks(c), kT, 0, s>>>(node, c, xstar, x);
+  return cudaGetLastError();
+}
+
+}  // namespace pd

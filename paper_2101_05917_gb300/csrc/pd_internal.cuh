@@ -147,6 +147,18 @@ struct MeshImpl {
   cudaGraphExec_t iter_graph[2][2][2] = {};
   bool iter_graph_act[2][2][2] = {};
   int64_t iter_graph_counts[2][2][2][3] = {};   // kernels, solves, local steps per replay
+  // complementarity contact (contact.cu): A^-1 columns of the candidate nodes and
+  // the current contact set
+  int64_t factor_gen = 0;              // bumped by every factorisation
+  int64_t contact_gen = -1;            // factor_gen the candidate columns belong to
+  int64_t ncand = 0;
+  int32_t* cand = nullptr;             // (ncand) internal free-node ids
+  std::vector<int32_t> cand_of_internal;   // host: internal id -> candidate index, -1
+  double* Bc = nullptr;                // (nf x ncand) column-major: L_A^-1 e_j
+  int64_t cset = 0, cset_cap = 0;      // contact set size / buffer capacity
+  int32_t *cset_node = nullptr, *cset_cand = nullptr;   // (cset) internal id, candidate index
+  double* cset_Sinv = nullptr;         // (cset x cset) inverse of (L_A^-1)_{CC}
+  double* cset_lam = nullptr;          // (cset x 3) multipliers of the current solve
   // material state
   bool factorized = false;
   int precision = PD_PREC_FP64;
@@ -199,6 +211,16 @@ pd_status factorize_device(MeshImpl* m, cudaStream_t s);
 // Triangular solves (kernels_solve.cu): out = A^-1 b on the free DoFs
 // (internal order, 3 nf entries each).
 // gate: skipped when gate->converged or !gate->accepted (may be null).
+// Complementarity contact (kernels_contact.cu); vectors in internal node order.
+cudaError_t contact_unit_rhs(int64_t nf, const int32_t* cand, int64_t k0, int count, double* b, cudaStream_t s);
+cudaError_t contact_extract_columns(int64_t nf, const double* x, int64_t k0, int count, double* Bc,
+                                    cudaStream_t s);
+cudaError_t contact_gather_S(int64_t nf, const double* Bc, const int32_t* node, const int32_t* cidx, int64_t c,
+                             double* S, cudaStream_t s);
+cudaError_t contact_correct(int64_t nf, const double* Bc, const int32_t* node, const int32_t* cidx, int64_t c,
+                            const double* Sinv, double* lam, const double* a1, const double* xstar, double* x,
+                            cudaStream_t s);
+
 cudaError_t solve_A(const MeshImpl* m, const IterState* gate, const double* b, double* out,
                     int precision, cudaStream_t s);
 void build_solve_schedule(const HostMesh& h, SolveSchedule& S);
