@@ -145,6 +145,10 @@ typedef struct {
   int32_t no_graphs;            /* nonzero: launch every kernel directly; by default chunks of
                                    iterations are captured once per mesh as CUDA graphs and
                                    replayed */
+  int32_t complementarity;      /* nonzero: complementarity contact on the ground z = 0 (Sec. 5.2,
+                                   Alg. 3 forward / Alg. 5 backward) for the candidates given to
+                                   pd_contact_prepare; needs k_contact = 0.  pd_backward uses the
+                                   contact sets of the last pd_forward (same T). */
   double* step_ms;              /* optional host array of T entries: pd_forward stores the
                                    host wall time of each step [ms], pd_backward adds the
                                    time of the step's adjoint (so after both calls entry t

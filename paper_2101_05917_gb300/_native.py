@@ -62,7 +62,7 @@ class SolverOpts(ctypes.Structure):
                 ("lbfgs_m", ctypes.c_int32), ("ls_max", ctypes.c_int32),
                 ("checkpoint_every", ctypes.c_int32), ("check_every", ctypes.c_int32),
                 ("profile", ctypes.c_int32), ("warm_start", ctypes.c_int32),
-                ("no_graphs", ctypes.c_int32), ("step_ms", c_double_p)]
+                ("no_graphs", ctypes.c_int32), ("complementarity", ctypes.c_int32), ("step_ms", c_double_p)]
 
 
 class Stats(ctypes.Structure):

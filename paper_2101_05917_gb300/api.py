@@ -44,7 +44,7 @@ def _u8(a, n, name):
 
 def solver_opts(tol_fwd=1e-9, tol_bwd=1e-9, max_iter_fwd=500, max_iter_bwd=500, lbfgs_m=5, ls_max=10,
                 checkpoint_every=0, check_every=4, profile=False, warm_start=False, graphs=True,
-                step_ms: Optional[np.ndarray] = None) -> N.SolverOpts:
+                complementarity=False, step_ms: Optional[np.ndarray] = None) -> N.SolverOpts:
     """step_ms: optional float64 host array of T entries receiving the per-step
     wall time (forward, then the backward adds its own); the caller keeps it alive."""
     p = None
@@ -52,7 +52,8 @@ def solver_opts(tol_fwd=1e-9, tol_bwd=1e-9, max_iter_fwd=500, max_iter_bwd=500, 
         assert step_ms.dtype == np.float64 and step_ms.flags.c_contiguous
         p = step_ms.ctypes.data_as(N.c_double_p)
     return N.SolverOpts(tol_fwd, tol_bwd, max_iter_fwd, max_iter_bwd, lbfgs_m, ls_max, checkpoint_every,
-                        check_every, 1 if profile else 0, 1 if warm_start else 0, 0 if graphs else 1, p)
+                        check_every, 1 if profile else 0, 1 if warm_start else 0, 0 if graphs else 1,
+                        1 if complementarity else 0, p)
 
 
 @dataclass

@@ -199,6 +199,7 @@ struct Ctx {
   int mx;          // compile-time bound of the L-BFGS history (2, 4, 5, 8, 10, 16)
   int lb;          // blocks of the L-BFGS kernels: at most two per SM (one completion counter)
   bool graphs;     // replay iteration chunks as CUDA graphs
+  bool complementarity = false;   // contact by the active set on the prepared candidates
   VecCtx vc;
   double* pe;      // energy partials
   double* pg;      // gather partials
@@ -217,6 +218,8 @@ Ctx make_ctx(MeshImpl* m, cudaStream_t s, const pd_solver_opts& o) {
   c.mx = lbfgs_bound(o.lbfgs_m);
   c.lb = std::max(1, std::min(c.vb, 2 * m->sms));
   c.graphs = !o.no_graphs;
+  c.complementarity = o.complementarity != 0;
+  if (c.complementarity) c.graphs = false;   // the captured launches would fix the set size
   c.vc.n3 = c.n3f;
   c.vc.st = m->ws.st;
   c.vc.partials = m->ws.partials;
@@ -265,6 +268,16 @@ pd_status poll(Ctx& c) {
     } break;                         \
   }
 
+// Complementarity contact: the global step of an iteration restricted to the free
+// nodes outside the held set (Alg. 3 / Alg. 5 global step, computed as in
+// kernels_contact.cu with zero targets: held rows of the direction stay zero).
+// Idempotent, so it is harmless when the gated solve was skipped.
+cudaError_t held_correction(MeshImpl* m, double* r, cudaStream_t s) {
+  if (!m->held_active || m->cset == 0) return cudaSuccess;
+  return contact_correct(m->h.nf, m->Bc, m->cset_node, m->cset_cand, m->cset, m->cset_Sinv, m->cset_lam, r,
+                         m->cset_zero, r, s);
+}
+
 // one forward iteration: evaluate the trial point, decide, commit and the
 // next direction (two-loop recursion around the global solve)
 pd_status launch_fwd_iteration(Ctx& c, int prec, const double* act_t) {
@@ -284,6 +297,7 @@ pd_status launch_fwd_iteration(Ctx& c, int prec, const double* act_t) {
   if (c.solve_t) c.solve_t->record(c.s);
   PD_CUDA_TRY(solve_A(m, st, w.q, w.r, m->precision, c.s));
   if (c.solve_t) c.solve_t->record(c.s);
+  PD_CUDA_TRY(held_correction(m, w.r, c.s));
   PD_WITH_MX(c.mx, lbfgs_post_dots_kernel<MX><<<c.lb, 256, 0, c.s>>>(c.vc, w.grad, w.Y, w.r));
   PD_WITH_MX(c.mx, lbfgs_dir_kernel<MX><<<c.lb, 256, 0, c.s>>>(c.vc, w.S, w.r, w.dir, w.x, w.xt));
   c.launches += 9;
@@ -304,6 +318,7 @@ pd_status launch_bwd_iteration(Ctx& c, int prec, const double* xnext, const doub
   if (c.solve_t) c.solve_t->record(c.s);
   PD_CUDA_TRY(solve_A(m, st, w.q, w.r, m->precision, c.s));
   if (c.solve_t) c.solve_t->record(c.s);
+  PD_CUDA_TRY(held_correction(m, w.r, c.s));
   PD_WITH_MX(c.mx, lbfgs_post_dots_kernel<MX><<<c.lb, 256, 0, c.s>>>(c.vc, w.gs, w.Y, w.r));
   PD_WITH_MX(c.mx, lbfgs_dir_kernel<MX><<<c.lb, 256, 0, c.s>>>(c.vc, w.S, w.r, w.dir, nullptr, nullptr));
   c.launches += 9;
@@ -433,8 +448,127 @@ struct StepInfo {
 
 // One implicit-Euler step from the internal state (w.xprev, w.vprev): on return
 // w.x holds x_{t+1}; finalize writes the trajectory and advances the state.
+pd_status contact_apply(MeshImpl* m, const std::vector<int32_t>& node, cudaStream_t s);
+
+// Complementarity contact (Alg. 3): the contact set of a step and its targets on
+// the ground z = 0, updated until stable (same rules as the oracle): a candidate
+// whose ray x_t + s v_t reaches z = 0 within the step is held at the intersection,
+// one already touching or joining later at (x_t, y_t, 0); nodes whose contact force
+// r_z = [M (x - y)/h^2 + grad E]_z is below -tau_r leave (at most once per step),
+// candidates below -tau_z join.  `iterate` runs the inner PD + L-BFGS solve.
+template <typename It>
+pd_status contact_rounds(Ctx& c, const StateCfg& cfg, const PredParams& pp, const double* act_c, int step,
+                         It& iterate, int& total_iters) {
+  MeshImpl* m = c.m;
+  Workspace& w = m->ws;
+  const HostMesh& h = m->h;
+  const int64_t nc = m->ncand;
+  const double hs = m->h_step;
+  auto rows = [&](const double* a, std::vector<double>& out) -> cudaError_t {
+    out.resize((size_t)(3 * nc));
+    cudaError_t e = contact_pack_rows(m->cand, nc, a, m->cand_buf, c.s);
+    if (e != cudaSuccess) return e;
+    if (nc) e = cudaMemcpyAsync(out.data(), m->cand_buf, sizeof(double) * 3 * nc, cudaMemcpyDeviceToHost, c.s);
+    if (e != cudaSuccess) return e;
+    return cudaStreamSynchronize(c.s);
+  };
+  std::vector<double> xc, vc, xn, rn;
+  PD_CUDA_TRY(rows(w.xprev, xc));
+  PD_CUDA_TRY(rows(w.vprev, vc));
+  std::vector<int32_t> C;       // candidate indices
+  std::vector<uint8_t> ray;     // 1 = ray target, 0 = drop target
+  for (int64_t k = 0; k < nc; ++k) {
+    const double z = xc[3 * k + 2], vz = vc[3 * k + 2];
+    if (z <= 0.0) {
+      C.push_back((int32_t)k), ray.push_back(0);
+    } else if (z + hs * vz <= 0.0) {
+      C.push_back((int32_t)k), ray.push_back(1);
+    }
+  }
+  double mmax = 0;
+  for (double mm : h.mass) mmax = std::max(mmax, mm);
+  const double tau_r = 1e-8 * mmax * std::sqrt(m->grav[0] * m->grav[0] + m->grav[1] * m->grav[1] +
+                                                m->grav[2] * m->grav[2]);
+  const double tau_z = 1e-9 * h.dx;
+  std::vector<uint8_t> left((size_t)nc, 0), locked((size_t)nc, 0), inC((size_t)nc, 0);
+  constexpr int kMaxRounds = 64;
+  for (int round = 1;; ++round) {
+    const int64_t cs = (int64_t)C.size();
+    std::vector<int32_t> node((size_t)cs);
+    std::vector<double> xs((size_t)(3 * cs));
+    for (int64_t i = 0; i < cs; ++i) {
+      const int64_t k = C[i];
+      node[i] = m->cand_host[k];
+      const double* xt = &xc[3 * k];
+      const double* vt = &vc[3 * k];
+      if (ray[i]) {
+        const double sr = xt[2] / (-vt[2]);
+        for (int d = 0; d < 3; ++d) xs[3 * i + d] = xt[d] + sr * vt[d];
+      } else {
+        xs[3 * i] = xt[0], xs[3 * i + 1] = xt[1], xs[3 * i + 2] = 0.0;
+      }
+    }
+    pd_status e = contact_apply(m, node, c.s);
+    if (e != PD_OK) return e;
+    if (cs) {
+      PD_CUDA_TRY(cudaMemcpyAsync(m->cset_xstar, xs.data(), sizeof(double) * 3 * cs, cudaMemcpyHostToDevice, c.s));
+    }
+    if (round > 1) {   // restart from the last solution with the new set
+      state_reset_kernel<<<1, 1, 0, c.s>>>(w.st, cfg);
+      predictor_kernel<<<grid_for(c.n), 256, 0, c.s>>>(pp);
+      copy_kernel<<<c.vb, 256, 0, c.s>>>(c.n3f, w.x, w.xt);
+      c.launches += 3;
+    }
+    PD_CUDA_TRY(contact_set_targets(m->cset_node, cs, m->cset_xstar, w.xt, c.s));
+    m->held_active = true;
+    e = iterate();
+    m->held_active = false;
+    if (e != PD_OK) return e;
+    total_iters += w.st_host->iters;
+    // contact forces and positions at the candidates: unmasked FP64 gradient at x
+    LocalArgs la{m, nullptr, w.x, nullptr, act_c, PD_PREC_FP64};
+    PD_CUDA_TRY(launch_element_forces(la, w.elembuf, c.pe, w.flags, c.s));
+    PD_CUDA_TRY(launch_gather_grad(m, nullptr, w.elembuf, PD_PREC_FP64, w.x, w.y, nullptr, w.gbar, c.pg, c.s));
+    c.launches += 2;
+    PD_CUDA_TRY(rows(w.gbar, rn));
+    PD_CUDA_TRY(rows(w.x, xn));
+    std::fill(inC.begin(), inC.end(), 0);
+    for (int32_t k : C) inC[k] = 1;
+    std::vector<int32_t> keepC;
+    std::vector<uint8_t> keepR;
+    bool leave = false;
+    for (int64_t i = 0; i < cs; ++i) {
+      const int32_t k = C[i];
+      if (rn[3 * k + 2] < -tau_r && !locked[k]) {
+        leave = true;
+        left[k] = 1;
+      } else {
+        keepC.push_back(k), keepR.push_back(ray[i]);
+      }
+    }
+    bool join = false;
+    for (int64_t k = 0; k < nc; ++k) {
+      if (inC[k] || !(xn[3 * k + 2] < -tau_z)) continue;
+      join = true;
+      if (left[k]) locked[k] = 1;
+      keepC.push_back((int32_t)k), keepR.push_back(0);
+    }
+    if ((!leave && !join) || round == kMaxRounds) break;
+    // left marks are only final for nodes that actually left in this round
+    C.swap(keepC);
+    ray.swap(keepR);
+  }
+  if (step >= 0 && step < (int)m->contact_log_node.size()) {
+    std::vector<int32_t> node(C.size());
+    for (size_t i = 0; i < C.size(); ++i) node[i] = m->cand_host[C[i]];
+    m->contact_log_node[step] = node;
+    m->contact_log_rule[step] = ray;
+  }
+  return PD_OK;
+}
+
 pd_status forward_step(Ctx& c, const double* act_t, const double* fext_int, double mu,
-                       double* traj_x, double* traj_v, StepInfo& info, int& guess) {
+                       double* traj_x, double* traj_v, StepInfo& info, int& guess, int step) {
   MeshImpl* m = c.m;
   Workspace& w = m->ws;
   StateCfg cfg{c.o.tol_fwd, m->precision == PD_PREC_MIXED ? 1e-6 : 1e-12, c.o.lbfgs_m, c.o.ls_max,
@@ -469,11 +603,8 @@ pd_status forward_step(Ctx& c, const double* act_t, const double* fext_int, doub
   // the FP64 gradient; after kMaxChecks failed checks the FP64 local step is used
   // for the remaining iterations.
   const bool mixed = m->precision == PD_PREC_MIXED;
-  int prec = mixed ? PD_PREC_MIXED : PD_PREC_FP64;
-  int launched = 0, fp64_launched = 0, checks = 0, stall = 0;
-  double best_rel = 1e300;
+  int fp64_launched = 0;
   constexpr int kMaxChecks = 3;
-  int chunk = std::max(guess, 1);
   const int hard_cap = 3 * c.o.max_iter_fwd + 64;
   info = StepInfo{};
   const double* act_c = nullptr;   // the step's actuation in the fixed buffer the graphs read
@@ -481,58 +612,75 @@ pd_status forward_step(Ctx& c, const double* act_t, const double* fext_int, doub
     PD_CUDA_TRY(cudaMemcpyAsync(w.act_cur, act_t, sizeof(double) * m->h.e, cudaMemcpyDeviceToDevice, c.s));
     act_c = w.act_cur;
   }
-  while (true) {
-    pd_status er = run_iterations(c, 0, prec, act_c, nullptr, chunk);
-    if (er != PD_OK) return er;
-    launched += chunk;
-    if (mixed && prec == PD_PREC_FP64) fp64_launched += chunk;
-    if (chunk > 0) {
-      clear_checked_kernel<<<1, 1, 0, c.s>>>(w.st);
-      c.launches += 1;
+  // the PD + L-BFGS iteration from the trial in w.xt (iteration state reset)
+  auto iterate = [&]() -> pd_status {
+    int prec = mixed ? PD_PREC_MIXED : PD_PREC_FP64;
+    int launched = 0, checks = 0, stall = 0;
+    double best_rel = 1e300;
+    int chunk = std::max(guess, 1);
+    while (true) {
+      pd_status er = run_iterations(c, 0, prec, act_c, nullptr, chunk);
+      if (er != PD_OK) return er;
+      launched += chunk;
+      if (mixed && prec == PD_PREC_FP64) fp64_launched += chunk;
+      if (chunk > 0) {
+        clear_checked_kernel<<<1, 1, 0, c.s>>>(w.st);
+        c.launches += 1;
+      }
+      pd_status e = poll(c);
+      if (e != PD_OK) return e;
+      const IterState& sh = *w.st_host;
+      if (sh.status & DEV_ERR_NAN) {
+        info.converged = false;
+        break;
+      }
+      if (sh.converged) {
+        if (mixed && prec == PD_PREC_MIXED && !sh.hit_max && !sh.fp64_checked) {
+          // FP64 convergence check at the accepted point
+          ++checks;
+          if (checks > kMaxChecks) prec = PD_PREC_FP64;
+          force_accept_kernel<<<1, 1, 0, c.s>>>(w.st);
+          copy_kernel<<<c.vb, 256, 0, c.s>>>(c.n3f, w.x, w.xt);
+          pd_status e2 = launch_fwd_iteration(c, PD_PREC_FP64, act_c);
+          if (e2 != PD_OK) return e2;
+          fp64_launched += 1;
+          mark_checked_kernel<<<1, 1, 0, c.s>>>(w.st);
+          c.launches += 3;
+          chunk = 0;
+          continue;
+        }
+        info.converged = !sh.hit_max;
+        break;
+      }
+      // FP32 floor above the tolerance: no halving of the residual over three polls
+      if (mixed && prec == PD_PREC_MIXED && sh.ref2 > 0) {
+        const double rel = std::sqrt(sh.gn2_acc / sh.ref2);
+        if (rel < 0.5 * best_rel) {
+          best_rel = rel;
+          stall = 0;
+        } else if (++stall >= 3) {
+          prec = PD_PREC_FP64;
+        }
+      }
+      if (launched >= hard_cap) {
+        info.converged = false;
+        break;
+      }
+      chunk = c.o.check_every;
     }
-    pd_status e = poll(c);
+    return PD_OK;
+  };
+  int total_iters = 0;
+  if (!c.complementarity) {
+    pd_status e = iterate();
     if (e != PD_OK) return e;
-    const IterState& sh = *w.st_host;
-    if (sh.status & DEV_ERR_NAN) {
-      info.converged = false;
-      break;
-    }
-    if (sh.converged) {
-      if (mixed && prec == PD_PREC_MIXED && !sh.hit_max && !sh.fp64_checked) {
-        // FP64 convergence check at the accepted point
-        ++checks;
-        if (checks > kMaxChecks) prec = PD_PREC_FP64;
-        force_accept_kernel<<<1, 1, 0, c.s>>>(w.st);
-        copy_kernel<<<c.vb, 256, 0, c.s>>>(c.n3f, w.x, w.xt);
-        pd_status e2 = launch_fwd_iteration(c, PD_PREC_FP64, act_c);
-        if (e2 != PD_OK) return e2;
-        fp64_launched += 1;
-        mark_checked_kernel<<<1, 1, 0, c.s>>>(w.st);
-        c.launches += 3;
-        chunk = 0;
-        continue;
-      }
-      info.converged = !sh.hit_max;
-      break;
-    }
-    // FP32 floor above the tolerance: no halving of the residual over three polls
-    if (mixed && prec == PD_PREC_MIXED && sh.ref2 > 0) {
-      const double rel = std::sqrt(sh.gn2_acc / sh.ref2);
-      if (rel < 0.5 * best_rel) {
-        best_rel = rel;
-        stall = 0;
-      } else if (++stall >= 3) {
-        prec = PD_PREC_FP64;
-      }
-    }
-    if (launched >= hard_cap) {
-      info.converged = false;
-      break;
-    }
-    chunk = c.o.check_every;
+    total_iters = w.st_host->iters;
+  } else {
+    pd_status e = contact_rounds(c, cfg, pp, act_c, step, iterate, total_iters);
+    if (e != PD_OK) return e;
   }
   const IterState& sh = *w.st_host;
-  info.iters = sh.iters;
+  info.iters = total_iters;
   info.ls = sh.ls_total;
   info.fp64_iters = fp64_launched;
   info.rel = sh.ref2 > 0 ? std::sqrt(sh.gn2_acc / sh.ref2) : 0.0;
@@ -986,6 +1134,15 @@ pd_status pd_forward(pd_mesh mesh, const double* x0, const double* v0, const dou
   pd_status ws = ensure_workspace(m, o.lbfgs_m);
   if (ws != PD_OK) return ws;
   cudaStream_t s = (cudaStream_t)stream;
+  if (o.complementarity) {
+    if (m->contact_gen != m->factor_gen || m->k_contact > 0) {
+      set_error("pd_forward: complementarity contact needs pd_contact_prepare after the last pd_factorize "
+                "and no penalty contact (k_contact = 0)");
+      return PD_ERR_INVALID_ARG;
+    }
+    m->contact_log_node.assign((size_t)T, {});
+    m->contact_log_rule.assign((size_t)T, {});
+  }
   Ctx c = make_ctx(m, s, o);
   EventTimer tsolve, tlocal;
   if (o.profile) {
@@ -1022,7 +1179,7 @@ pd_status pd_forward(pd_mesh mesh, const double* x0, const double* v0, const dou
     }
     StepInfo info;
     const auto ts = std::chrono::steady_clock::now();
-    pd_status e = forward_step(c, act_t, fext_int, mu, tx, tv, info, guess);
+    pd_status e = forward_step(c, act_t, fext_int, mu, tx, tv, info, guess, t);
     if (o.step_ms) o.step_ms[t] = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - ts).count();
     if (e != PD_OK) return e;
     accumulate(stats, info, true);
@@ -1071,6 +1228,10 @@ pd_status pd_backward(pd_mesh mesh, const double* x_traj, const double* v_traj, 
   pd_status ws = ensure_workspace(m, o.lbfgs_m);
   if (ws != PD_OK) return ws;
   cudaStream_t s = (cudaStream_t)stream;
+  if (o.complementarity && (m->contact_gen != m->factor_gen || (int64_t)m->contact_log_node.size() != T)) {
+    set_error("pd_backward: complementarity contact needs the contact sets of a pd_forward of the same T");
+    return PD_ERR_INVALID_ARG;
+  }
   Ctx c = make_ctx(m, s, o);
   EventTimer tsolve, tlocal;
   if (o.profile) {
@@ -1128,7 +1289,7 @@ pd_status pd_backward(pd_mesh mesh, const double* x_traj, const double* v_traj, 
       for (int t = ta; t < tb - 1; ++t) {
         StepInfo info;
         const double* act_t = act ? act + (int64_t)t * e : nullptr;
-        pd_status er = forward_step(c, act_t, fext_int, mu, nullptr, nullptr, info, guess_f);
+        pd_status er = forward_step(c, act_t, fext_int, mu, nullptr, nullptr, info, guess_f, t);
         if (er != PD_OK) return er;
         copy_kernel<<<grid_for(3 * n), 256, 0, s>>>(3 * n, w.xprev, seg + (int64_t)(t + 1 - ta) * 6 * n);
         copy_kernel<<<grid_for(3 * n), 256, 0, s>>>(3 * n, w.vprev, seg + (int64_t)(t + 1 - ta) * 6 * n + 3 * n);
@@ -1306,6 +1467,56 @@ bool spd_inverse(std::vector<double>& S, int64_t c) {
   return true;
 }
 
+// Makes `node` (internal ids, distinct candidates) the contact set: index lists,
+// S = (L_A^-1)_{CC} inverted on the host, the held mask.  Synchronises.
+pd_status contact_apply(MeshImpl* m, const std::vector<int32_t>& node, cudaStream_t s) {
+  const HostMesh& h = m->h;
+  const int64_t c = (int64_t)node.size();
+  std::vector<int32_t> cidx(c);
+  std::vector<uint8_t> seen(m->ncand, 0);
+  for (int64_t k = 0; k < c; ++k) {
+    const int32_t ci = (node[k] >= 0 && node[k] < h.n) ? m->cand_of_internal[node[k]] : -1;
+    if (ci < 0 || seen[ci]) {
+      set_error("contact set: every node must be a distinct contact candidate");
+      return PD_ERR_INVALID_ARG;
+    }
+    seen[ci] = 1;
+    cidx[k] = ci;
+  }
+  if (c > m->cset_cap) {
+    PD_CUDA_TRY(dalloc(m, &m->cset_node, (size_t)c));
+    PD_CUDA_TRY(dalloc(m, &m->cset_cand, (size_t)c));
+    PD_CUDA_TRY(dalloc(m, &m->cset_Sinv, (size_t)(c * c)));
+    PD_CUDA_TRY(dalloc(m, &m->cset_lam, (size_t)(3 * c)));
+    PD_CUDA_TRY(dalloc(m, &m->cset_zero, (size_t)(3 * c)));
+    PD_CUDA_TRY(cudaMemsetAsync(m->cset_zero, 0, sizeof(double) * 3 * c, s));
+    PD_CUDA_TRY(dalloc(m, &m->cset_xstar, (size_t)(3 * c)));
+    m->cset_cap = c;
+  }
+  std::vector<uint8_t> held((size_t)h.nf, 0);
+  for (int32_t in : node) held[in] = 1;
+  PD_CUDA_TRY(cudaMemcpyAsync(m->held, held.data(), (size_t)h.nf, cudaMemcpyHostToDevice, s));
+  m->cset = 0;
+  if (c == 0) return cudaStreamSynchronize(s) == cudaSuccess ? PD_OK : PD_ERR_CUDA;
+  PD_CUDA_TRY(cudaMemcpyAsync(m->cset_node, node.data(), sizeof(int32_t) * c, cudaMemcpyHostToDevice, s));
+  PD_CUDA_TRY(cudaMemcpyAsync(m->cset_cand, cidx.data(), sizeof(int32_t) * c, cudaMemcpyHostToDevice, s));
+  PD_CUDA_TRY(contact_gather_S(h.nf, m->Bc, m->cset_node, m->cset_cand, c, m->cset_Sinv, s));
+  std::vector<double> S((size_t)(c * c));
+  PD_CUDA_TRY(cudaMemcpyAsync(S.data(), m->cset_Sinv, sizeof(double) * c * c, cudaMemcpyDeviceToHost, s));
+  PD_CUDA_TRY(cudaStreamSynchronize(s));
+  // symmetrise (the two halves come from different solves) before the factorisation
+  for (int64_t i = 0; i < c; ++i)
+    for (int64_t j = i + 1; j < c; ++j) S[i * c + j] = S[j * c + i] = 0.5 * (S[i * c + j] + S[j * c + i]);
+  if (!spd_inverse(S, c)) {
+    set_error("contact set: (A^-1)_CC is not positive definite");
+    return PD_ERR_NOT_SPD;
+  }
+  PD_CUDA_TRY(cudaMemcpyAsync(m->cset_Sinv, S.data(), sizeof(double) * c * c, cudaMemcpyHostToDevice, s));
+  PD_CUDA_TRY(cudaStreamSynchronize(s));
+  m->cset = c;
+  return PD_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -1331,8 +1542,11 @@ pd_status pd_contact_prepare(pd_mesh mesh, const uint8_t* candidates_host, void*
     cand.push_back(in);
   }
   m->ncand = (int64_t)cand.size();
+  m->cand_host = cand;
   PD_CUDA_TRY(upload(m, &m->cand, cand));
   PD_CUDA_TRY(dalloc(m, &m->Bc, (size_t)std::max<int64_t>(h.nf * m->ncand, 1)));
+  PD_CUDA_TRY(dalloc(m, &m->cand_buf, (size_t)std::max<int64_t>(3 * m->ncand, 3)));
+  if (!m->held) PD_CUDA_TRY(dalloc(m, &m->held, (size_t)std::max<int64_t>(h.nf, 1)));
   Workspace& w = m->ws;
   for (int64_t k0 = 0; k0 < m->ncand; k0 += 3) {
     const int count = (int)std::min<int64_t>(3, m->ncand - k0);
@@ -1360,52 +1574,17 @@ pd_status pd_contact_set(pd_mesh mesh, const int32_t* nodes_host, int64_t c, voi
     return PD_ERR_INVALID_ARG;
   }
   DeviceGuard g(m->device);
-  cudaStream_t s = (cudaStream_t)stream;
   const HostMesh& h = m->h;
-  std::vector<int32_t> node(c), cidx(c);
-  std::vector<uint8_t> seen(m->ncand, 0);
+  std::vector<int32_t> node(c);
   for (int64_t k = 0; k < c; ++k) {
     const int32_t kept = nodes_host[k];
     if (kept < 0 || kept >= h.n) {
       set_error("pd_contact_set: node id out of range");
       return PD_ERR_INVALID_ARG;
     }
-    const int32_t in = h.internal_of_kept[kept];
-    const int32_t ci = m->cand_of_internal[in];
-    if (ci < 0 || seen[ci]) {
-      set_error("pd_contact_set: every node must be a distinct contact candidate");
-      return PD_ERR_INVALID_ARG;
-    }
-    seen[ci] = 1;
-    node[k] = in;
-    cidx[k] = ci;
+    node[k] = h.internal_of_kept[kept];
   }
-  if (c > m->cset_cap) {
-    PD_CUDA_TRY(dalloc(m, &m->cset_node, (size_t)c));
-    PD_CUDA_TRY(dalloc(m, &m->cset_cand, (size_t)c));
-    PD_CUDA_TRY(dalloc(m, &m->cset_Sinv, (size_t)(c * c)));
-    PD_CUDA_TRY(dalloc(m, &m->cset_lam, (size_t)(3 * c)));
-    m->cset_cap = c;
-  }
-  m->cset = 0;
-  if (c == 0) return PD_OK;
-  PD_CUDA_TRY(cudaMemcpyAsync(m->cset_node, node.data(), sizeof(int32_t) * c, cudaMemcpyHostToDevice, s));
-  PD_CUDA_TRY(cudaMemcpyAsync(m->cset_cand, cidx.data(), sizeof(int32_t) * c, cudaMemcpyHostToDevice, s));
-  PD_CUDA_TRY(contact_gather_S(h.nf, m->Bc, m->cset_node, m->cset_cand, c, m->cset_Sinv, s));
-  std::vector<double> S((size_t)(c * c));
-  PD_CUDA_TRY(cudaMemcpyAsync(S.data(), m->cset_Sinv, sizeof(double) * c * c, cudaMemcpyDeviceToHost, s));
-  PD_CUDA_TRY(cudaStreamSynchronize(s));
-  // symmetrise (the two halves come from different solves) before the factorisation
-  for (int64_t i = 0; i < c; ++i)
-    for (int64_t j = i + 1; j < c; ++j) S[i * c + j] = S[j * c + i] = 0.5 * (S[i * c + j] + S[j * c + i]);
-  if (!spd_inverse(S, c)) {
-    set_error("pd_contact_set: (A^-1)_CC is not positive definite");
-    return PD_ERR_NOT_SPD;
-  }
-  PD_CUDA_TRY(cudaMemcpyAsync(m->cset_Sinv, S.data(), sizeof(double) * c * c, cudaMemcpyHostToDevice, s));
-  PD_CUDA_TRY(cudaStreamSynchronize(s));
-  m->cset = c;
-  return PD_OK;
+  return contact_apply(m, node, (cudaStream_t)stream);
 }
 
 pd_status pd_solve_A_contact(pd_mesh mesh, const double* b, const double* x_star, double* x, int32_t precision,

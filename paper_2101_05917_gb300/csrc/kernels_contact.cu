@@ -105,6 +105,16 @@ __global__ void set_targets_kernel(const int32_t* node, int64_t c, const double*
   x[g + 2] = xstar[3 * k + 2];
 }
 
+// out[k] = a[rows[k]] (3 values per row)
+__global__ void pack_rows_kernel(const int32_t* rows, int64_t c, const double* a, double* out) {
+  const int64_t k = (int64_t)blockIdx.x * kT + threadIdx.x;
+  if (k >= c) return;
+  const int64_t g = 3 * (int64_t)rows[k];
+  out[3 * k] = a[g];
+  out[3 * k + 1] = a[g + 1];
+  out[3 * k + 2] = a[g + 2];
+}
+
 unsigned blocks(int64_t n) { return (unsigned)((n + kT - 1) / kT); }
 
 }  // namespace
@@ -135,6 +145,18 @@ cudaError_t contact_correct(int64_t nf, const double* Bc, const int32_t* node, c
   if (c > 0) lambda_kernel<<<blocks(c), kT, 0, s>>>(Sinv, node, c, a1, lam);
   correct_kernel<<<blocks(nf), kT, 0, s>>>(nf, Bc, cidx, c, lam, a1, x);
   if (c > 0) set_targets_kernel<<<blocks(c), kT, 0, s>>>(node, c, xstar, x);
+  return cudaGetLastError();
+}
+
+cudaError_t contact_pack_rows(const int32_t* rows, int64_t c, const double* a, double* out, cudaStream_t s) {
+  if (c == 0) return cudaSuccess;
+  pack_rows_kernel<<<blocks(c), kT, 0, s>>>(rows, c, a, out);
+  return cudaGetLastError();
+}
+
+cudaError_t contact_set_targets(const int32_t* node, int64_t c, const double* xstar, double* x, cudaStream_t s) {
+  if (c == 0) return cudaSuccess;
+  set_targets_kernel<<<blocks(c), kT, 0, s>>>(node, c, xstar, x);
   return cudaGetLastError();
 }
 

@@ -294,6 +294,7 @@ struct GatherParams {
   const double* aux;    // hvp mode: second vector for a dot product (may be null)
   double* out;
   double* partials;
+  const uint8_t* held;  // nodes held at contact targets: gradient / product rows are zero
 };
 
 // grad g at x: partials = [kinetic + contact energy, |g|^2, g.dir, 0]
@@ -326,6 +327,7 @@ __global__ void __launch_bounds__(kGatherThreads) gather_grad_kernel(GatherParam
         kin += 0.5 * p.k_contact * z * z;
       }
     }
+    if (p.held && p.held[c]) g[0] = g[1] = g[2] = 0.0;
     double gd = 0, gg = 0;
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
@@ -359,6 +361,7 @@ __global__ void __launch_bounds__(kGatherThreads) gather_hvp_kernel(GatherParams
 #pragma unroll
     for (int i = 0; i < 3; ++i) g[i] += m * p.v[3 * c + i] * p.inv_h2;
     if (p.contact && p.contact[c] && p.x[3 * c + 2] < 0.0) g[2] += p.k_contact * p.v[3 * c + 2];
+    if (p.held && p.held[c]) g[0] = g[1] = g[2] = 0.0;
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
       p.out[3 * c + i] = g[i];
@@ -396,6 +399,7 @@ GatherParams make_gather(const MeshImpl* m) {
   p.contact = m->k_contact > 0 ? m->contact : nullptr;
   p.inv_h2 = 1.0 / (m->h_step * m->h_step);
   p.k_contact = m->k_contact;
+  p.held = m->held_active ? m->held : nullptr;
   return p;
 }
 

@@ -153,12 +153,22 @@ struct MeshImpl {
   int64_t contact_gen = -1;            // factor_gen the candidate columns belong to
   int64_t ncand = 0;
   int32_t* cand = nullptr;             // (ncand) internal free-node ids
+  std::vector<int32_t> cand_host;      // the same on the host
   std::vector<int32_t> cand_of_internal;   // host: internal id -> candidate index, -1
   double* Bc = nullptr;                // (nf x ncand) column-major: L_A^-1 e_j
   int64_t cset = 0, cset_cap = 0;      // contact set size / buffer capacity
   int32_t *cset_node = nullptr, *cset_cand = nullptr;   // (cset) internal id, candidate index
   double* cset_Sinv = nullptr;         // (cset x cset) inverse of (L_A^-1)_{CC}
   double* cset_lam = nullptr;          // (cset x 3) multipliers of the current solve
+  double* cset_zero = nullptr;         // (cset x 3) zeros: targets of the iteration's directions
+  double* cset_xstar = nullptr;        // (cset x 3) targets of the current set
+  double* cand_buf = nullptr;          // (ncand x 3) scratch for candidate rows
+  uint8_t* held = nullptr;             // (nf) 1 = node held at its contact target
+  bool held_active = false;            // gathers mask held rows (complementarity steps)
+  // per time step of the last complementarity rollout: contact set (internal ids),
+  // target rule (1 = ray, 0 = drop) -- read by the backward pass
+  std::vector<std::vector<int32_t>> contact_log_node;
+  std::vector<std::vector<uint8_t>> contact_log_rule;
   // material state
   bool factorized = false;
   int precision = PD_PREC_FP64;
@@ -220,6 +230,9 @@ cudaError_t contact_gather_S(int64_t nf, const double* Bc, const int32_t* node, 
 cudaError_t contact_correct(int64_t nf, const double* Bc, const int32_t* node, const int32_t* cidx, int64_t c,
                             const double* Sinv, double* lam, const double* a1, const double* xstar, double* x,
                             cudaStream_t s);
+
+cudaError_t contact_pack_rows(const int32_t* rows, int64_t c, const double* a, double* out, cudaStream_t s);
+cudaError_t contact_set_targets(const int32_t* node, int64_t c, const double* xstar, double* x, cudaStream_t s);
 
 cudaError_t solve_A(const MeshImpl* m, const IterState* gate, const double* b, double* out,
                     int precision, cudaStream_t s);
