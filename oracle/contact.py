@@ -63,7 +63,9 @@ def woodbury_solve(Ld, C, xstar, b):
 # ------------------------------------------------------------------ time step
 # Alg. 3 on the ground z = 0 (phi(x) = z), with static friction (sticky contact).
 # Readings (the paper leaves them open): a candidate whose ray x_t + s v_t,
-# 0 < s <= h, reaches z = 0 is held at that intersection ("ray"); a candidate
+# 0 < s <= h, reaches z = 0 is held at that intersection ("ray"; its height is 0
+# by the choice of s and is stored as exactly 0, so that the next step sees the
+# node touching instead of a rounding residue of either sign); a candidate
 # already touching (z_t <= 0) or added later because it penetrates is held at
 # (x_t, y_t, 0) ("drop").  Both targets depend on the start of the step only.
 # The contact set is updated until stable: nodes whose contact force
@@ -74,7 +76,7 @@ def contact_target(xt, vt, h, rule):
     """x* of one node; rule 'ray' or 'drop'."""
     if rule == "ray":
         s = xt[2] / (-vt[2])
-        return xt + s * vt
+        return np.array([xt[0] + s * vt[0], xt[1] + s * vt[1], 0.0])
     return np.array([xt[0], xt[1], 0.0])
 
 
