@@ -147,8 +147,17 @@ typedef struct {
                                    replayed */
   int32_t complementarity;      /* nonzero: complementarity contact on the ground z = 0 (Sec. 5.2,
                                    Alg. 3 forward / Alg. 5 backward) for the candidates given to
-                                   pd_contact_prepare; needs k_contact = 0.  pd_backward uses the
-                                   contact sets of the last pd_forward (same T). */
+                                   pd_contact_prepare; needs k_contact = 0; CUDA graphs are not
+                                   used.  Per step the contact set starts with the candidates
+                                   touching the ground (target (x_t, y_t, 0), "drop") or whose
+                                   ray x_t + s v_t reaches it within h (target: the
+                                   intersection, "ray"); after each solve nodes whose normal
+                                   contact force [M (x - y)/h^2 + grad E]_z is below
+                                   -1e-8 max(m) |g| leave (once per step: a node that leaves
+                                   and then sinks again stays), candidates below -1e-9 dx join
+                                   (drop), until the set is stable (at most 64 solves).
+                                   pd_backward uses the sets of the last pd_forward (same T);
+                                   a checkpointed backward recomputes them identically. */
   double* step_ms;              /* optional host array of T entries: pd_forward stores the
                                    host wall time of each step [ms], pd_backward adds the
                                    time of the step's adjoint (so after both calls entry t
@@ -240,6 +249,14 @@ pd_status pd_contact_set(pd_mesh m, const int32_t* nodes_host, int64_t c, void* 
  * pd_contact_set (NULL when c = 0). */
 pd_status pd_solve_A_contact(pd_mesh m, const double* b, const double* x_star, double* x, int32_t precision,
                              void* stream);
+
+/* The final contact set of step t (0 <= t < T) of the last pd_forward with
+ * complementarity contact: *count nodes (kept ids, in the order they joined) into
+ * nodes_host and their targets into rules_host (1 = ray, 0 = drop; may be NULL),
+ * both host arrays of capacity cap.  PD_ERR_INVALID_ARG if there is no such step
+ * or cap < *count (*count is still set). */
+pd_status pd_contact_step_set(pd_mesh m, int32_t t, int32_t* nodes_host, uint8_t* rules_host, int64_t cap,
+                              int64_t* count);
 
 /* Local step that allocates no device memory (the paper has no counterpart).
  * For callers that cannot call cudaMalloc -- e.g. while a CUDA graph is being

@@ -103,7 +103,7 @@ class Result(ctypes.Structure):
 
 SYMBOLS = ["pd_create_mesh", "pd_mesh_destroy", "pd_mesh_query", "pd_mesh_export", "pd_factorize",
            "pd_forward", "pd_backward", "pd_local_step", "pd_hessian_vector", "pd_solve_A",
-           "pd_local_step_noalloc", "pd_contact_prepare", "pd_contact_set", "pd_solve_A_contact", "pd_serve_create", "pd_serve_submit", "pd_serve_poll", "pd_serve_release", "pd_serve_drain",
+           "pd_local_step_noalloc", "pd_contact_prepare", "pd_contact_set", "pd_solve_A_contact", "pd_contact_step_set", "pd_serve_create", "pd_serve_submit", "pd_serve_poll", "pd_serve_release", "pd_serve_drain",
            "pd_serve_destroy", "pd_last_error"]
 
 _lib = None
@@ -157,6 +157,9 @@ def lib() -> ctypes.CDLL:
     L.pd_contact_set.restype = st
     L.pd_solve_A_contact.argtypes = [vp, vp, vp, vp, ctypes.c_int32, vp]
     L.pd_solve_A_contact.restype = st
+    L.pd_contact_step_set.argtypes = [vp, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32), c_u8_p, ctypes.c_int64,
+                                      ctypes.POINTER(ctypes.c_int64)]
+    L.pd_contact_step_set.restype = st
     L.pd_serve_release.argtypes = [vp, ctypes.c_uint64]
     L.pd_serve_release.restype = st
     L.pd_serve_drain.argtypes = [vp]

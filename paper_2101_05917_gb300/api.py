@@ -214,6 +214,21 @@ class PDMesh:
                                        _stream(stream)), "pd_contact_set")
         self.contact_count = int(arr.size)
 
+    def contact_step_set(self, t):
+        """(nodes, ray) of step t of the last forward pass with complementarity
+        contact: kept node ids in the order they joined and their target rule
+        (True = ray intersection, False = dropped onto the ground)."""
+        cnt = ctypes.c_int64(0)
+        st = N.lib().pd_contact_step_set(self.handle, int(t), None, None, 0, ctypes.byref(cnt))
+        if st != N.PD_OK and cnt.value == 0:
+            N.check(st, "pd_contact_step_set")
+        nodes = np.zeros(cnt.value, dtype=np.int32)
+        rules = np.zeros(cnt.value, dtype=np.uint8)
+        N.check(N.lib().pd_contact_step_set(self.handle, int(t), nodes.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                                            rules.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)), nodes.size,
+                                            ctypes.byref(cnt)), "pd_contact_step_set")
+        return nodes, rules.astype(bool)
+
     def solve_contact(self, b, x_star=None, precision=N.PD_PREC_FP64, stream=None):
         """x with x_C = x_star ((c,3), set order) and A_{C'C'} x_{C'} = b_{C'}."""
         out = torch.empty((self.n, 3), dtype=torch.float64, device=b.device)

@@ -24,10 +24,24 @@ cudaError_t dalloc(MeshImpl* m, T** p, size_t count) {
   if (count == 0) count = 1;
   cudaError_t e = cudaMalloc((void**)p, sizeof(T) * count);
   if (e == cudaSuccess) {
-    m->allocations.push_back((void*)*p);
+    m->allocations.emplace_back((void*)*p, sizeof(T) * count);
     m->ws.bytes += sizeof(T) * count;
   }
   return e;
+}
+
+// frees a buffer made by dalloc (null is a no-op)
+template <typename T>
+void dfree(MeshImpl* m, T** p) {
+  if (!*p) return;
+  for (size_t i = 0; i < m->allocations.size(); ++i) {
+    if (m->allocations[i].first != (void*)*p) continue;
+    m->ws.bytes -= m->allocations[i].second;
+    m->allocations.erase(m->allocations.begin() + (std::ptrdiff_t)i);
+    cudaFree((void*)*p);
+    break;
+  }
+  *p = nullptr;
 }
 
 template <typename T, typename S>
@@ -451,8 +465,8 @@ struct StepInfo {
 pd_status contact_apply(MeshImpl* m, const std::vector<int32_t>& node, cudaStream_t s);
 
 // Complementarity contact (Alg. 3): the contact set of a step and its targets on
-// the ground z = 0, updated until stable (same rules as the oracle): a candidate
-// whose ray x_t + s v_t reaches z = 0 within the step is held at the intersection,
+// the ground z = 0, updated until stable: a candidate whose ray x_t + s v_t
+// reaches z = 0 within the step is held at the intersection (height exactly 0),
 // one already touching or joining later at (x_t, y_t, 0); nodes whose contact force
 // r_z = [M (x - y)/h^2 + grad E]_z is below -tau_r leave (at most once per step),
 // candidates below -tau_z join.  `iterate` runs the inner PD + L-BFGS solve.
@@ -501,9 +515,9 @@ pd_status contact_rounds(Ctx& c, const StateCfg& cfg, const PredParams& pp, cons
       node[i] = m->cand_host[k];
       const double* xt = &xc[3 * k];
       const double* vt = &vc[3 * k];
-      if (ray[i]) {
+      if (ray[i]) {   // on the ground by the choice of s: height exactly 0
         const double sr = xt[2] / (-vt[2]);
-        for (int d = 0; d < 3; ++d) xs[3 * i + d] = xt[d] + sr * vt[d];
+        xs[3 * i] = xt[0] + sr * vt[0], xs[3 * i + 1] = xt[1] + sr * vt[1], xs[3 * i + 2] = 0.0;
       } else {
         xs[3 * i] = xt[0], xs[3 * i + 1] = xt[1], xs[3 * i + 2] = 0.0;
       }
@@ -528,9 +542,9 @@ pd_status contact_rounds(Ctx& c, const StateCfg& cfg, const PredParams& pp, cons
     // contact forces and positions at the candidates: unmasked FP64 gradient at x
     LocalArgs la{m, nullptr, w.x, nullptr, act_c, PD_PREC_FP64};
     PD_CUDA_TRY(launch_element_forces(la, w.elembuf, c.pe, w.flags, c.s));
-    PD_CUDA_TRY(launch_gather_grad(m, nullptr, w.elembuf, PD_PREC_FP64, w.x, w.y, nullptr, w.gbar, c.pg, c.s));
+    PD_CUDA_TRY(launch_gather_grad(m, nullptr, w.elembuf, PD_PREC_FP64, w.x, w.y, nullptr, w.Hd, c.pg, c.s));
     c.launches += 2;
-    PD_CUDA_TRY(rows(w.gbar, rn));
+    PD_CUDA_TRY(rows(w.Hd, rn));
     PD_CUDA_TRY(rows(w.x, xn));
     std::fill(inC.begin(), inC.end(), 0);
     for (int32_t k : C) inC[k] = 1;
@@ -730,20 +744,42 @@ pd_status check_flags(Ctx& c, pd_stats* stats) {
 }
 
 // Adjoint of one step at x_{t+1} (w.x holds x_{t+1} internal; w.xprev/w.vprev hold x_t, v_t).
+// Complementarity contact: the held set takes part in the gathers only while a
+// scope is open
+struct HeldScope {
+  MeshImpl* m;
+  HeldScope(MeshImpl* mm, bool on) : m(mm) { m->held_active = on; }
+  ~HeldScope() { m->held_active = false; }
+};
+
 pd_status backward_step(Ctx& c, const double* xnext, const double* xt_, const double* vt_,
                         const double* act_t, double mu, const double* gx_t, const double* gv_t,
                         double* gfext_int, double* g_wc, double* g_wv, double* g_wm, double* g_act_t,
-                        double* g_mu, StepInfo& info, int& guess) {
+                        double* g_mu, StepInfo& info, int& guess, int step) {
   MeshImpl* m = c.m;
   Workspace& w = m->ws;
   const double inv_h = 1.0 / m->h_step;
+  // complementarity contact (Alg. 5): the step's final contact set from the
+  // forward pass; its rows of the adjoint are zero (H_{C'C'} z_{C'} = gbar_{C'})
+  const uint8_t* held = nullptr;
+  if (c.complementarity) {
+    const std::vector<int32_t>& node = m->contact_log_node[step];
+    const std::vector<uint8_t>& rule = m->contact_log_rule[step];
+    pd_status e = contact_apply(m, node, c.s);
+    if (e != PD_OK) return e;
+    if (m->cset > 0) {
+      PD_CUDA_TRY(cudaMemcpyAsync(m->cset_rule, rule.data(), rule.size(), cudaMemcpyHostToDevice, c.s));
+    }
+    held = m->held;
+  }
+  HeldScope scope(m, c.complementarity);
   const bool warm = c.o.warm_start && c.bwd_steps > 0;   // w.z holds the previous adjoint
   StateCfg cfg{c.o.tol_bwd, 0.0, c.o.lbfgs_m, c.o.ls_max, c.o.max_iter_bwd, 1,
                (c.o.warm_start && c.last_kind == 1) ? 1 : 0};
   c.bwd_steps += 1;
   c.last_kind = 1;
   state_reset_kernel<<<1, 1, 0, c.s>>>(w.st, cfg);
-  bwd_step_init_kernel<<<c.vb, 256, 0, c.s>>>(c.vc, w.ax, w.av, inv_h, w.z, w.gs, w.q, warm ? 1 : 0);
+  bwd_step_init_kernel<<<c.vb, 256, 0, c.s>>>(c.vc, w.ax, w.av, inv_h, w.z, w.gs, w.q, warm ? 1 : 0, held);
   c.launches += 2;
   if (warm) {
     // start from the previous step's adjoint: gs = H z - gbar at that z
@@ -751,7 +787,7 @@ pd_status backward_step(Ctx& c, const double* xnext, const double* xt_, const do
     LocalArgs la0{m, nullptr, xnext, w.z, act_t, p0};
     PD_CUDA_TRY(launch_element_hvp(la0, w.elembuf, w.flags, c.s));
     PD_CUDA_TRY(launch_gather_hvp(m, nullptr, w.elembuf, p0, xnext, w.z, nullptr, w.Hd, c.pg, c.s));
-    residual_replace_kernel<<<c.vb, 256, 0, c.s>>>(c.vc, w.Hd, w.ax, w.av, inv_h, w.gs, w.q);
+    residual_replace_kernel<<<c.vb, 256, 0, c.s>>>(c.vc, w.Hd, w.ax, w.av, inv_h, w.gs, w.q, held);
     c.launches += 3;
   }
   // Hessian products in the factor's precision; at convergence of the recursively
@@ -789,7 +825,7 @@ pd_status backward_step(Ctx& c, const double* xnext, const double* xt_, const do
       LocalArgs la{m, nullptr, xnext, w.z, act_t, PD_PREC_FP64};
       PD_CUDA_TRY(launch_element_hvp(la, w.elembuf, w.flags, c.s));
       PD_CUDA_TRY(launch_gather_hvp(m, nullptr, w.elembuf, PD_PREC_FP64, xnext, w.z, nullptr, w.Hd, c.pg, c.s));
-      residual_replace_kernel<<<c.vb, 256, 0, c.s>>>(c.vc, w.Hd, w.ax, w.av, inv_h, w.gs, w.q);
+      residual_replace_kernel<<<c.vb, 256, 0, c.s>>>(c.vc, w.Hd, w.ax, w.av, inv_h, w.gs, w.q, held);
       fp64_launched += 1;
       c.launches += 3;
       e = poll(c);
@@ -814,6 +850,17 @@ pd_status backward_step(Ctx& c, const double* xnext, const double* xt_, const do
   info.fp64_iters = fp64_launched;
   info.rel = sh->ref2 > 0 ? std::sqrt(sh->gn2_acc / sh->ref2) : 0.0;
   guess = std::max(1, sh->iters - 1);
+  const int64_t cs = c.complementarity ? m->cset : 0;
+  m->held_active = false;
+  if (cs > 0) {
+    // dL/dx* = gbar_C - (H z)_C with the unmasked FP64 product, through the targets
+    LocalArgs lh{m, nullptr, xnext, w.z, act_t, PD_PREC_FP64};
+    PD_CUDA_TRY(launch_element_hvp(lh, w.elembuf, w.flags, c.s));
+    PD_CUDA_TRY(launch_gather_hvp(m, nullptr, w.elembuf, PD_PREC_FP64, xnext, w.z, nullptr, w.Hd, c.pg, c.s));
+    PD_CUDA_TRY(contact_target_vjp(m->cset_node, m->cset_rule, cs, xt_, vt_, w.ax, w.av, w.Hd, inv_h,
+                                   m->cset_gx, m->cset_gv, c.s));
+    c.launches += 3;
+  }
   // parameter gradients at x_{t+1} (per-element products in the factor's precision,
   // FP64 accumulation over steps), then the state adjoint of step t
   LocalArgs la{m, nullptr, xnext, w.z, act_t, prec};
@@ -843,6 +890,10 @@ pd_status backward_step(Ctx& c, const double* xnext, const double* xt_, const do
   bwd_state_kernel<<<grid_for(c.n), 256, 0, c.s>>>(bp);
   PD_CUDA_TRY(cudaGetLastError());
   c.launches += 2;
+  if (cs > 0) {
+    PD_CUDA_TRY(contact_add_rows(m->cset_node, cs, m->cset_gx, m->cset_gv, w.ax, w.av, c.s));
+    c.launches += 1;
+  }
   return PD_OK;
 }
 
@@ -997,7 +1048,7 @@ void pd_mesh_destroy(pd_mesh m) {
     cudaDeviceSynchronize();
     drop_iteration_graphs(&I);
     if (I.cap_stream) cudaStreamDestroy(I.cap_stream);
-    for (void* p : I.allocations) cudaFree(p);
+    for (auto& a : I.allocations) cudaFree(a.first);
     if (I.ws.st_host) cudaFreeHost(I.ws.st_host);
   }
   delete m;
@@ -1313,7 +1364,7 @@ pd_status pd_backward(pd_mesh mesh, const double* x_traj, const double* v_traj, 
       const auto ts = std::chrono::steady_clock::now();
       pd_status er = backward_step(c, xn_int, xt_int, vt_int, act_t, mu, loss_x(t), loss_v(t), gfext_int,
                                    g_w_corot, g_w_vol, g_w_muscle, g_act ? g_act + (int64_t)t * e : nullptr,
-                                   g_mu, info, guess_b);
+                                   g_mu, info, guess_b, t);
       if (o.step_ms)
         o.step_ms[t] += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - ts).count();
       if (er != PD_OK) return er;
@@ -1484,14 +1535,30 @@ pd_status contact_apply(MeshImpl* m, const std::vector<int32_t>& node, cudaStrea
     cidx[k] = ci;
   }
   if (c > m->cset_cap) {
-    PD_CUDA_TRY(dalloc(m, &m->cset_node, (size_t)c));
-    PD_CUDA_TRY(dalloc(m, &m->cset_cand, (size_t)c));
-    PD_CUDA_TRY(dalloc(m, &m->cset_Sinv, (size_t)(c * c)));
-    PD_CUDA_TRY(dalloc(m, &m->cset_lam, (size_t)(3 * c)));
-    PD_CUDA_TRY(dalloc(m, &m->cset_zero, (size_t)(3 * c)));
-    PD_CUDA_TRY(cudaMemsetAsync(m->cset_zero, 0, sizeof(double) * 3 * c, s));
-    PD_CUDA_TRY(dalloc(m, &m->cset_xstar, (size_t)(3 * c)));
-    m->cset_cap = c;
+    // grow geometrically (at most the candidate count): few reallocations when a
+    // set grows node by node
+    const int64_t cap = std::min<int64_t>(m->ncand, std::max<int64_t>(c, 2 * m->cset_cap));
+    PD_CUDA_TRY(cudaStreamSynchronize(s));   // the last set's solves may still read them
+    dfree(m, &m->cset_node);
+    dfree(m, &m->cset_cand);
+    dfree(m, &m->cset_Sinv);
+    dfree(m, &m->cset_lam);
+    dfree(m, &m->cset_zero);
+    dfree(m, &m->cset_xstar);
+    dfree(m, &m->cset_rule);
+    dfree(m, &m->cset_gx);
+    dfree(m, &m->cset_gv);
+    PD_CUDA_TRY(dalloc(m, &m->cset_node, (size_t)cap));
+    PD_CUDA_TRY(dalloc(m, &m->cset_cand, (size_t)cap));
+    PD_CUDA_TRY(dalloc(m, &m->cset_Sinv, (size_t)(cap * cap)));
+    PD_CUDA_TRY(dalloc(m, &m->cset_lam, (size_t)(3 * cap)));
+    PD_CUDA_TRY(dalloc(m, &m->cset_zero, (size_t)(3 * cap)));
+    PD_CUDA_TRY(cudaMemsetAsync(m->cset_zero, 0, sizeof(double) * 3 * cap, s));
+    PD_CUDA_TRY(dalloc(m, &m->cset_xstar, (size_t)(3 * cap)));
+    PD_CUDA_TRY(dalloc(m, &m->cset_rule, (size_t)cap));
+    PD_CUDA_TRY(dalloc(m, &m->cset_gx, (size_t)(3 * cap)));
+    PD_CUDA_TRY(dalloc(m, &m->cset_gv, (size_t)(3 * cap)));
+    m->cset_cap = cap;
   }
   std::vector<uint8_t> held((size_t)h.nf, 0);
   for (int32_t in : node) held[in] = 1;
@@ -1543,6 +1610,10 @@ pd_status pd_contact_prepare(pd_mesh mesh, const uint8_t* candidates_host, void*
   }
   m->ncand = (int64_t)cand.size();
   m->cand_host = cand;
+  PD_CUDA_TRY(cudaStreamSynchronize(s));   // earlier work may still read the old buffers
+  dfree(m, &m->cand);
+  dfree(m, &m->Bc);
+  dfree(m, &m->cand_buf);
   PD_CUDA_TRY(upload(m, &m->cand, cand));
   PD_CUDA_TRY(dalloc(m, &m->Bc, (size_t)std::max<int64_t>(h.nf * m->ncand, 1)));
   PD_CUDA_TRY(dalloc(m, &m->cand_buf, (size_t)std::max<int64_t>(3 * m->ncand, 3)));
@@ -1585,6 +1656,32 @@ pd_status pd_contact_set(pd_mesh mesh, const int32_t* nodes_host, int64_t c, voi
     node[k] = h.internal_of_kept[kept];
   }
   return contact_apply(m, node, (cudaStream_t)stream);
+}
+
+pd_status pd_contact_step_set(pd_mesh mesh, int32_t t, int32_t* nodes_host, uint8_t* rules_host, int64_t cap,
+                              int64_t* count) {
+  if (!mesh || !count) {
+    set_error("pd_contact_step_set: null argument");
+    return PD_ERR_INVALID_ARG;
+  }
+  MeshImpl* m = &mesh->impl;
+  *count = 0;
+  if (t < 0 || t >= (int32_t)m->contact_log_node.size()) {
+    set_error("pd_contact_step_set: no such step in the last complementarity forward pass");
+    return PD_ERR_INVALID_ARG;
+  }
+  const std::vector<int32_t>& node = m->contact_log_node[t];
+  const std::vector<uint8_t>& rule = m->contact_log_rule[t];
+  *count = (int64_t)node.size();
+  if (cap < *count || (*count > 0 && !nodes_host)) {
+    set_error("pd_contact_step_set: output capacity too small");
+    return PD_ERR_INVALID_ARG;
+  }
+  for (size_t k = 0; k < node.size(); ++k) {
+    nodes_host[k] = m->h.kept_of_internal[node[k]];
+    if (rules_host) rules_host[k] = rule[k];
+  }
+  return PD_OK;
 }
 
 pd_status pd_solve_A_contact(pd_mesh mesh, const double* b, const double* x_star, double* x, int32_t precision,

@@ -115,6 +115,46 @@ __global__ void pack_rows_kernel(const int32_t* rows, int64_t c, const double* a
   out[3 * k + 2] = a[g + 2];
 }
 
+// Adjoint of the targets (Alg. 5): with z_C = 0, dL/dx*_j = gbar_j - (H z)_j for
+// every held node j, gbar = ax + av/h, chained into (x_t, v_t) of that node.
+//   ray  x* = x_t + s v_t, s = z_t / (-v_z):  the height of x* is identically 0;
+//        ds/dz_t = -1/v_z, ds/dv_z = -s/v_z, so with w = -(g_x v_x + g_y v_y)/v_z
+//        dL/dx_t = (g_x, g_y, w), dL/dv_t = s (g_x, g_y, w)
+//   drop x* = (x_t, y_t, 0):  dL/dx_t = (g_x, g_y, 0), dL/dv_t = 0
+__global__ void target_vjp_kernel(const int32_t* node, const uint8_t* ray, int64_t c, const double* xt,
+                                  const double* vt, const double* ax, const double* av, const double* Hz,
+                                  double inv_h, double* gx, double* gv) {
+  const int64_t k = (int64_t)blockIdx.x * kT + threadIdx.x;
+  if (k >= c) return;
+  const int64_t j = 3 * (int64_t)node[k];
+  const double g0 = ax[j] + av[j] * inv_h - Hz[j];
+  const double g1 = ax[j + 1] + av[j + 1] * inv_h - Hz[j + 1];
+  double dx2 = 0, s = 0;
+  if (ray[k]) {
+    const double vz = vt[j + 2];
+    s = xt[j + 2] / (-vz);
+    dx2 = -(g0 * vt[j] + g1 * vt[j + 1]) / vz;
+  }
+  gx[3 * k] = g0;
+  gx[3 * k + 1] = g1;
+  gx[3 * k + 2] = dx2;
+  gv[3 * k] = s * g0;
+  gv[3 * k + 1] = s * g1;
+  gv[3 * k + 2] = s * dx2;
+}
+
+// ax[node[k]] += gx[k], av[node[k]] += gv[k]
+__global__ void add_rows_kernel(const int32_t* node, int64_t c, const double* gx, const double* gv, double* ax,
+                                double* av) {
+  const int64_t k = (int64_t)blockIdx.x * kT + threadIdx.x;
+  if (k >= c) return;
+  const int64_t j = 3 * (int64_t)node[k];
+  for (int d = 0; d < 3; ++d) {
+    ax[j + d] += gx[3 * k + d];
+    av[j + d] += gv[3 * k + d];
+  }
+}
+
 unsigned blocks(int64_t n) { return (unsigned)((n + kT - 1) / kT); }
 
 }  // namespace
@@ -157,6 +197,21 @@ cudaError_t contact_pack_rows(const int32_t* rows, int64_t c, const double* a, d
 cudaError_t contact_set_targets(const int32_t* node, int64_t c, const double* xstar, double* x, cudaStream_t s) {
   if (c == 0) return cudaSuccess;
   set_targets_kernel<<<blocks(c), kT, 0, s>>>(node, c, xstar, x);
+  return cudaGetLastError();
+}
+
+cudaError_t contact_target_vjp(const int32_t* node, const uint8_t* ray, int64_t c, const double* xt,
+                               const double* vt, const double* ax, const double* av, const double* Hz, double inv_h,
+                               double* gx, double* gv, cudaStream_t s) {
+  if (c == 0) return cudaSuccess;
+  target_vjp_kernel<<<blocks(c), kT, 0, s>>>(node, ray, c, xt, vt, ax, av, Hz, inv_h, gx, gv);
+  return cudaGetLastError();
+}
+
+cudaError_t contact_add_rows(const int32_t* node, int64_t c, const double* gx, const double* gv, double* ax,
+                             double* av, cudaStream_t s) {
+  if (c == 0) return cudaSuccess;
+  add_rows_kernel<<<blocks(c), kT, 0, s>>>(node, c, gx, gv, ax, av);
   return cudaGetLastError();
 }
 

@@ -162,6 +162,9 @@ struct MeshImpl {
   double* cset_lam = nullptr;          // (cset x 3) multipliers of the current solve
   double* cset_zero = nullptr;         // (cset x 3) zeros: targets of the iteration's directions
   double* cset_xstar = nullptr;        // (cset x 3) targets of the current set
+  uint8_t* cset_rule = nullptr;        // (cset) 1 = ray target, 0 = drop target (backward)
+  double* cset_gx = nullptr;           // (cset x 3) adjoint of the targets into x_t (backward)
+  double* cset_gv = nullptr;           // (cset x 3) adjoint of the targets into v_t (backward)
   double* cand_buf = nullptr;          // (ncand x 3) scratch for candidate rows
   uint8_t* held = nullptr;             // (nf) 1 = node held at its contact target
   bool held_active = false;            // gathers mask held rows (complementarity steps)
@@ -179,7 +182,7 @@ struct MeshImpl {
   double* Q64 = nullptr;
   float* Q32 = nullptr;
   Workspace ws;
-  std::vector<void*> allocations;
+  std::vector<std::pair<void*, size_t>> allocations;   // device buffers and their bytes
 };
 
 // ------------------------------------------------------------------ launchers
@@ -233,6 +236,11 @@ cudaError_t contact_correct(int64_t nf, const double* Bc, const int32_t* node, c
 
 cudaError_t contact_pack_rows(const int32_t* rows, int64_t c, const double* a, double* out, cudaStream_t s);
 cudaError_t contact_set_targets(const int32_t* node, int64_t c, const double* xstar, double* x, cudaStream_t s);
+cudaError_t contact_target_vjp(const int32_t* node, const uint8_t* ray, int64_t c, const double* xt,
+                               const double* vt, const double* ax, const double* av, const double* Hz, double inv_h,
+                               double* gx, double* gv, cudaStream_t s);
+cudaError_t contact_add_rows(const int32_t* node, int64_t c, const double* gx, const double* gv, double* ax,
+                             double* av, cudaStream_t s);
 
 cudaError_t solve_A(const MeshImpl* m, const IterState* gate, const double* b, double* out,
                     int precision, cudaStream_t s);

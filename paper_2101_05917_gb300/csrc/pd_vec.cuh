@@ -781,13 +781,16 @@ __global__ void finalize_fwd_kernel(int64_t n, const double* x, double* xi, doub
 }
 
 // ---------------------------------------------------------------- backward
-// gbar = ax + av/h, z = 0, gs = grad s(0) = -gbar, q = gs; ref2 = |gbar|^2
+// gbar = ax + av/h, z = 0, gs = grad s(0) = -gbar, q = gs; ref2 = |gbar|^2.
+// Rows of held nodes (complementarity contact, may be null) take no part: their
+// right-hand side and z are zero.
 __global__ void bwd_step_init_kernel(VecCtx c, const double* ax, const double* av, double inv_h,
-                                     double* z, double* gs, double* q, int keep_z) {
+                                     double* z, double* gs, double* q, int keep_z, const uint8_t* held) {
   double part = 0;
   for (int64_t i = (int64_t)blockIdx.x * kT + threadIdx.x; i < c.n3; i += (int64_t)gridDim.x * kT) {
-    const double gb = ax[i] + av[i] * inv_h;
-    if (!keep_z) z[i] = 0.0;
+    const bool h = held && held[i / 3];
+    const double gb = h ? 0.0 : ax[i] + av[i] * inv_h;
+    if (!keep_z || h) z[i] = 0.0;
     gs[i] = -gb;
     q[i] = -gb;
     part += gb * gb;
@@ -856,12 +859,13 @@ __global__ void decide_bwd_kernel(IterState* st, const double* gather_partials, 
   }
 }
 
-// gs = Hz - gbar from an exact product Hz (true-residual replacement)
+// gs = Hz - gbar from an exact product Hz (true-residual replacement); held rows
+// (may be null) are zero
 __global__ void residual_replace_kernel(VecCtx c, const double* Hz, const double* ax, const double* av,
-                                        double inv_h, double* gs, double* q) {
+                                        double inv_h, double* gs, double* q, const uint8_t* held) {
   double part = 0;
   for (int64_t i = (int64_t)blockIdx.x * kT + threadIdx.x; i < c.n3; i += (int64_t)gridDim.x * kT) {
-    const double g = Hz[i] - (ax[i] + av[i] * inv_h);
+    const double g = (held && held[i / 3]) ? 0.0 : Hz[i] - (ax[i] + av[i] * inv_h);
     gs[i] = g;
     q[i] = g;
     part += g * g;

@@ -1,6 +1,6 @@
 """Complementarity contact through time (Sec. 5.2, Alg. 3 forward, Alg. 5
 backward): a cube falling onto the ground, GPU against the oracle's active-set
-Newton rollout and its adjoint (positions, contact sets, gradients)."""
+Newton rollout and its adjoint (positions, contact sets and targets, gradients)."""
 import dataclasses
 
 import numpy as np
@@ -16,6 +16,8 @@ from workloads import contact_cube_c3
 pytestmark = pytest.mark.gpu
 
 DEV = torch.device("cuda:0")
+T = 4
+WANT = ("x0", "v0", "w_corot", "w_vol")
 
 
 def _t(a):
@@ -23,7 +25,8 @@ def _t(a):
 
 
 def falling_cube(N=4, gap=0.002, vz=-0.6):
-    sc = contact_cube_c3(N=N, T=4)
+    """Lands during the first step (ray targets), then partly rebounds (nodes leave)."""
+    sc = contact_cube_c3(N=N, T=T)
     x0 = sc.x0.copy()
     x0[:, 2] += gap - x0[:, 2].min()
     v0 = sc.v0 * 0.1
@@ -31,30 +34,83 @@ def falling_cube(N=4, gap=0.002, vz=-0.6):
     return dataclasses.replace(sc, x0=x0, v0=v0, k_contact=0.0, mu=0.0)
 
 
-def _gpu(sc, T, precision, tol, want=None):
+def loss_grads(sc, seed=7):
+    """dL/dx_t for every t of a seeded linear loss."""
+    return np.random.default_rng(seed).standard_normal((T + 1, sc.x0.shape[0], 3))
+
+
+@pytest.fixture(scope="module")
+def oracle_run():
+    sc = falling_cube()
+    model = Model(sc)
+    xs, vs, infos = oc.rollout_complementarity(model, sc.x0, sc.v0, sc.f_ext, sc.contact, T)
+    grads = oc.backward_complementarity(model, xs, vs, infos, loss_grads(sc))
+    return sc, xs, vs, infos, grads
+
+
+def _gpu(sc, precision, tol, checkpoint=0, backward=True):
     mesh = api.PDMesh.from_scene(sc)
     wc, wv, _, _ = api.scene_weights(sc, DEV)
     mesh.factorize(wc, wv, None, None, h=sc.h, gravity=tuple(sc.gravity), k_contact=0.0, precision=precision)
     mesh.contact_prepare(sc.contact.astype(np.uint8))
-    opts = api.solver_opts(tol_fwd=tol, tol_bwd=tol, max_iter_fwd=5000, max_iter_bwd=5000, complementarity=True)
+    opts = api.solver_opts(tol_fwd=tol, tol_bwd=tol, max_iter_fwd=5000, max_iter_bwd=5000, complementarity=True,
+                           checkpoint_every=checkpoint)
     roll = mesh.forward(_t(sc.x0), _t(sc.v0), T, f_ext=_t(sc.f_ext), opts=opts)
+    sets = [mesh.contact_step_set(t) for t in range(T)]
     out = None
-    if want:
-        out = mesh.backward(roll, T, _t(sc.loss_w), f_ext=_t(sc.f_ext), opts=opts, want=want)
-    return mesh, roll, out
+    if backward:
+        out = mesh.backward(roll, T, _t(loss_grads(sc)), loss_all_steps=True, f_ext=_t(sc.f_ext), opts=opts,
+                            want=WANT)
+    mesh.close()
+    return roll, sets, out
 
 
-@pytest.mark.parametrize("precision,tol,gate", [(N.PD_PREC_FP64, 1e-11, 1e-9), (N.PD_PREC_MIXED, 1e-9, 1e-6)])
-def test_forward_matches_oracle(precision, tol, gate):
-    sc = falling_cube()
-    T = 4
-    xs, vs, infos = oc.rollout_complementarity(Model(sc), sc.x0, sc.v0, sc.f_ext, sc.contact, T)
-    mesh, roll, _ = _gpu(sc, T, precision, tol)
+PRECS = [(N.PD_PREC_FP64, 1e-11, 1e-9, 1e-7), (N.PD_PREC_MIXED, 1e-9, 1e-6, 1e-5)]
+
+
+@pytest.mark.parametrize("precision,tol,pos_gate,grad_gate", PRECS)
+def test_rollout_and_adjoint_match_oracle(oracle_run, precision, tol, pos_gate, grad_gate):
+    sc, xs, vs, infos, grads = oracle_run
+    roll, sets, out = _gpu(sc, precision, tol)
     xg = roll.x.cpu().numpy()
     for t in range(1, T + 1):
         err = np.linalg.norm(xg[t] - xs[t]) / np.linalg.norm(xs[t] - sc.x0)
-        contact_gpu = int(np.sum(np.isclose(xg[t][:, 2], 0.0, atol=1e-12) & (sc.contact > 0)))
-        print(f"step {t}: displacement-relative position error {err:.2e}, contact set {infos[t - 1]['C'].size} "
-              f"(ground nodes gpu {contact_gpu})")
-        assert err <= gate
+        print(f"step {t}: displacement-relative position error {err:.2e}, |C| {infos[t - 1]['C'].size}")
+        assert err <= pos_gate
+        # the same set (the order of joining may differ) with the same target rules
+        nodes, ray = sets[t - 1]
+        rule_gpu = dict(zip(nodes.tolist(), ray.tolist()))
+        rule_ora = {int(j): r == "ray" for j, r in zip(infos[t - 1]["C"], infos[t - 1]["rules"])}
+        assert rule_gpu == rule_ora
+    assert any(r for _, ray in sets for r in ray) and any(not r for _, ray in sets for r in ray)
+    for name, key in (("x0", "g_x0"), ("v0", "g_v0"), ("w_corot", "g_wc"), ("w_vol", "g_wv")):
+        g = out[name].cpu().numpy().reshape(grads[key].shape)
+        rel = np.linalg.norm(g - grads[key]) / np.linalg.norm(grads[key])
+        print(f"dL/d{name}: relative error {rel:.2e}")
+        assert rel <= grad_gate
+
+
+def test_checkpointed_adjoint_is_identical(oracle_run):
+    """Recomputing the segments (and their contact sets) reproduces the gradients."""
+    sc = oracle_run[0]
+    _, sets0, out0 = _gpu(sc, N.PD_PREC_FP64, 1e-11)
+    _, sets1, out1 = _gpu(sc, N.PD_PREC_FP64, 1e-11, checkpoint=2)
+    for (n0, r0), (n1, r1) in zip(sets0, sets1):
+        assert np.array_equal(n0, n1) and np.array_equal(r0, r1)
+    for name in WANT:
+        assert torch.equal(out0[name], out1[name]), name
+
+
+def test_backward_needs_the_forward_sets():
+    sc = falling_cube()
+    mesh = api.PDMesh.from_scene(sc)
+    wc, wv, _, _ = api.scene_weights(sc, DEV)
+    mesh.factorize(wc, wv, None, None, h=sc.h, gravity=tuple(sc.gravity), k_contact=0.0)
+    mesh.contact_prepare(sc.contact.astype(np.uint8))
+    opts = api.solver_opts(complementarity=True)
+    roll = mesh.forward(_t(sc.x0), _t(sc.v0), 2, f_ext=_t(sc.f_ext), opts=opts)
+    with pytest.raises(RuntimeError):
+        mesh.backward(roll, 3, _t(np.zeros((4, sc.x0.shape[0], 3))), loss_all_steps=True, opts=opts)
+    with pytest.raises(RuntimeError):
+        mesh.contact_step_set(2)
     mesh.close()
