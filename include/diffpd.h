@@ -239,12 +239,14 @@ pd_status pd_solve_A(pd_mesh m, const double* b, double* x, int32_t precision, v
 pd_status pd_contact_prepare(pd_mesh m, const uint8_t* candidates_host, void* stream);
 
 /* Fixes the contact set: c distinct kept node ids (host), each a candidate; forms
- * S = (L_A^-1)_{CC} and its inverse (FP64 Cholesky on the host; PD_ERR_NOT_SPD if it
- * fails).  c = 0 clears the set.  Synchronises the stream. */
+ * S = (L_A^-1)_{CC} and factors it on the device, S = L L^T with Q = L^-1 (FP64,
+ * c^3/3 multiply-adds for each; PD_ERR_NOT_SPD if a pivot is not positive).  Device
+ * memory 2 c^2 doubles, kept for later sets.  c = 0 clears the set.  Synchronises
+ * the stream. */
 pd_status pd_contact_set(pd_mesh m, const int32_t* nodes_host, int64_t c, void* stream);
 
 /* x (n,3) with x_C = x* and A_{C'C'} x_{C'} = b_{C'}: one solve of A (precision as
- * pd_solve_A) then x = a1 - B_{.,C} S^-1 (a1)_C in FP64.  b, x: (n,3) device, kept
+ * pd_solve_A) then x = a1 - B_{.,C} Q^T Q (a1)_C in FP64.  b, x: (n,3) device, kept
  * order (Dirichlet rows of x are zero); x_star: (c,3) device, in the order given to
  * pd_contact_set (NULL when c = 0). */
 pd_status pd_solve_A_contact(pd_mesh m, const double* b, const double* x_star, double* x, int32_t precision,

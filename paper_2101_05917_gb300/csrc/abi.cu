@@ -288,8 +288,8 @@ pd_status poll(Ctx& c) {
 // Idempotent, so it is harmless when the gated solve was skipped.
 cudaError_t held_correction(MeshImpl* m, double* r, cudaStream_t s) {
   if (!m->held_active || m->cset == 0) return cudaSuccess;
-  return contact_correct(m->h.nf, m->Bc, m->cset_node, m->cset_cand, m->cset, m->cset_Sinv, m->cset_lam, r,
-                         m->cset_zero, r, s);
+  return contact_correct(m->h.nf, m->Bc, m->cset_node, m->cset_cand, m->cset, m->cset_Q, m->cset_S, m->cset_a,
+                         m->cset_u, m->cset_lam, r, m->cset_zero, r, s);
 }
 
 // one forward iteration: evaluate the trial point, decide, commit and the
@@ -1484,42 +1484,9 @@ pd_status pd_solve_A(pd_mesh mesh, const double* b, double* x, int32_t precision
 // ------------------------------------------------------------ complementarity contact
 namespace {
 
-// In-place inverse of a symmetric positive definite c x c matrix (row-major) by
-// Cholesky S = L L^T, then S^-1 = L^-T L^-1 column by column.  False if a pivot is
-// not positive.
-bool spd_inverse(std::vector<double>& S, int64_t c) {
-  std::vector<double> L(S.size(), 0.0);
-  for (int64_t j = 0; j < c; ++j) {
-    double d = S[j * c + j];
-    for (int64_t k = 0; k < j; ++k) d -= L[j * c + k] * L[j * c + k];
-    if (!(d > 0.0)) return false;
-    const double ljj = std::sqrt(d);
-    L[j * c + j] = ljj;
-    for (int64_t i = j + 1; i < c; ++i) {
-      double v = S[i * c + j];
-      for (int64_t k = 0; k < j; ++k) v -= L[i * c + k] * L[j * c + k];
-      L[i * c + j] = v / ljj;
-    }
-  }
-  std::vector<double> y(c), x(c);
-  for (int64_t col = 0; col < c; ++col) {
-    for (int64_t i = 0; i < c; ++i) {   // L y = e_col
-      double v = i == col ? 1.0 : 0.0;
-      for (int64_t k = 0; k < i; ++k) v -= L[i * c + k] * y[k];
-      y[i] = v / L[i * c + i];
-    }
-    for (int64_t i = c - 1; i >= 0; --i) {   // L^T x = y
-      double v = y[i];
-      for (int64_t k = i + 1; k < c; ++k) v -= L[k * c + i] * x[k];
-      x[i] = v / L[i * c + i];
-    }
-    for (int64_t i = 0; i < c; ++i) S[i * c + col] = x[i];
-  }
-  return true;
-}
-
 // Makes `node` (internal ids, distinct candidates) the contact set: index lists,
-// S = (L_A^-1)_{CC} inverted on the host, the held mask.  Synchronises.
+// the held mask, S = (L_A^-1)_{CC} and Q = L^-1 of S = L L^T on the device
+// (c^3/3 multiply-adds each for the factor and the inverse).  Synchronises.
 pd_status contact_apply(MeshImpl* m, const std::vector<int32_t>& node, cudaStream_t s) {
   const HostMesh& h = m->h;
   const int64_t c = (int64_t)node.size();
@@ -1541,7 +1508,10 @@ pd_status contact_apply(MeshImpl* m, const std::vector<int32_t>& node, cudaStrea
     PD_CUDA_TRY(cudaStreamSynchronize(s));   // the last set's solves may still read them
     dfree(m, &m->cset_node);
     dfree(m, &m->cset_cand);
-    dfree(m, &m->cset_Sinv);
+    dfree(m, &m->cset_S);
+    dfree(m, &m->cset_Q);
+    dfree(m, &m->cset_a);
+    dfree(m, &m->cset_u);
     dfree(m, &m->cset_lam);
     dfree(m, &m->cset_zero);
     dfree(m, &m->cset_xstar);
@@ -1550,7 +1520,10 @@ pd_status contact_apply(MeshImpl* m, const std::vector<int32_t>& node, cudaStrea
     dfree(m, &m->cset_gv);
     PD_CUDA_TRY(dalloc(m, &m->cset_node, (size_t)cap));
     PD_CUDA_TRY(dalloc(m, &m->cset_cand, (size_t)cap));
-    PD_CUDA_TRY(dalloc(m, &m->cset_Sinv, (size_t)(cap * cap)));
+    PD_CUDA_TRY(dalloc(m, &m->cset_S, (size_t)(cap * cap)));
+    PD_CUDA_TRY(dalloc(m, &m->cset_Q, (size_t)(cap * cap)));
+    PD_CUDA_TRY(dalloc(m, &m->cset_a, (size_t)(3 * cap)));
+    PD_CUDA_TRY(dalloc(m, &m->cset_u, (size_t)(3 * cap)));
     PD_CUDA_TRY(dalloc(m, &m->cset_lam, (size_t)(3 * cap)));
     PD_CUDA_TRY(dalloc(m, &m->cset_zero, (size_t)(3 * cap)));
     PD_CUDA_TRY(cudaMemsetAsync(m->cset_zero, 0, sizeof(double) * 3 * cap, s));
@@ -1567,19 +1540,22 @@ pd_status contact_apply(MeshImpl* m, const std::vector<int32_t>& node, cudaStrea
   if (c == 0) return cudaStreamSynchronize(s) == cudaSuccess ? PD_OK : PD_ERR_CUDA;
   PD_CUDA_TRY(cudaMemcpyAsync(m->cset_node, node.data(), sizeof(int32_t) * c, cudaMemcpyHostToDevice, s));
   PD_CUDA_TRY(cudaMemcpyAsync(m->cset_cand, cidx.data(), sizeof(int32_t) * c, cudaMemcpyHostToDevice, s));
-  PD_CUDA_TRY(contact_gather_S(h.nf, m->Bc, m->cset_node, m->cset_cand, c, m->cset_Sinv, s));
-  std::vector<double> S((size_t)(c * c));
-  PD_CUDA_TRY(cudaMemcpyAsync(S.data(), m->cset_Sinv, sizeof(double) * c * c, cudaMemcpyDeviceToHost, s));
+  PD_CUDA_TRY(contact_gather_S(h.nf, m->Bc, m->cset_node, m->cset_cand, c, m->cset_S, s));
+  if (!m->cset_meta) PD_CUDA_TRY(dalloc(m, &m->cset_meta, 4));
+  if (!m->cset_flags) PD_CUDA_TRY(dalloc(m, &m->cset_flags, 1));
+  pd_status e = dense_cholesky_inverse(m->cset_S, c, m->cset_Q, m->cset_S, m->cset_meta, m->cset_flags, s);
+  if (e != PD_OK) return e;
+  int flags = 0;
+  PD_CUDA_TRY(cudaMemcpyAsync(&flags, m->cset_flags, sizeof(int), cudaMemcpyDeviceToHost, s));
   PD_CUDA_TRY(cudaStreamSynchronize(s));
-  // symmetrise (the two halves come from different solves) before the factorisation
-  for (int64_t i = 0; i < c; ++i)
-    for (int64_t j = i + 1; j < c; ++j) S[i * c + j] = S[j * c + i] = 0.5 * (S[i * c + j] + S[j * c + i]);
-  if (!spd_inverse(S, c)) {
+  if (flags & DEV_ERR_NOT_SPD) {
     set_error("contact set: (A^-1)_CC is not positive definite");
     return PD_ERR_NOT_SPD;
   }
-  PD_CUDA_TRY(cudaMemcpyAsync(m->cset_Sinv, S.data(), sizeof(double) * c * c, cudaMemcpyHostToDevice, s));
-  PD_CUDA_TRY(cudaStreamSynchronize(s));
+  if (flags & DEV_ERR_NAN) {
+    set_error("contact set: non-finite entry in the inverse factor of (A^-1)_CC");
+    return PD_ERR_NAN;
+  }
   m->cset = c;
   return PD_OK;
 }
@@ -1708,8 +1684,8 @@ pd_status pd_solve_A_contact(pd_mesh mesh, const double* b, const double* x_star
   kept_to_internal_kernel<<<grid_for(n), 256, 0, s>>>(n, m->kept_of_internal, b, w.iov);
   PD_CUDA_TRY(reset_solve_counters(m, s));
   PD_CUDA_TRY(solve_A(m, nullptr, w.iov, w.iox, precision, s));
-  PD_CUDA_TRY(contact_correct(m->h.nf, m->Bc, m->cset_node, m->cset_cand, m->cset, m->cset_Sinv, m->cset_lam,
-                              w.iox, x_star, w.iov, s));
+  PD_CUDA_TRY(contact_correct(m->h.nf, m->Bc, m->cset_node, m->cset_cand, m->cset, m->cset_Q, m->cset_S,
+                              m->cset_a, m->cset_u, m->cset_lam, w.iox, x_star, w.iov, s));
   internal_to_kept_kernel<<<grid_for(n), 256, 0, s>>>(n, m->h.nf, m->kept_of_internal, w.iov, x);
   PD_CUDA_TRY(cudaGetLastError());
   return PD_OK;

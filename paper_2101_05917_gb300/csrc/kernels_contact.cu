@@ -11,7 +11,9 @@
 // C' of L_A x + E_C lambda = b are the reduced system.)  This is the same rank-|C|
 // update of A as the paper's Woodbury identity, written with the |C| x |C| matrix
 // S instead of its 2|C| x 2|C| one; the result is identical in exact arithmetic.
-// Per solve it costs one solve of A plus O(nf |C|) work.
+// S is factored once per contact set on the device (S = L L^T, Q = L^-1), so
+// lambda = Q^T (Q (a1)_C): two triangular matrix-vector products.  Per solve the
+// update costs one solve of A plus O(nf |C| + |C|^2) memory traffic.
 #include "pd_internal.cuh"
 
 namespace pd {
@@ -34,30 +36,44 @@ __global__ void extract_columns_kernel(int64_t nf, const double* x, int64_t k0, 
   for (int j = 0; j < count; ++j) Bc[(k0 + j) * nf + i] = x[3 * i + j];
 }
 
-// S[r][k] = Bc[cidx[k]][node[r]]  (c x c, row-major)
+// S[r][k] = (L_A^-1)[node[r], node[k]] from the candidate columns, averaged over
+// the two columns that hold it (they come from different solves): symmetric
 __global__ void gather_S_kernel(int64_t nf, const double* Bc, const int32_t* node, const int32_t* cidx, int64_t c,
                                 double* S) {
   const int64_t t = (int64_t)blockIdx.x * kT + threadIdx.x;
   if (t >= c * c) return;
   const int64_t r = t / c, k = t % c;
-  S[t] = Bc[(int64_t)cidx[k] * nf + node[r]];
+  S[t] = 0.5 * (Bc[(int64_t)cidx[k] * nf + node[r]] + Bc[(int64_t)cidx[r] * nf + node[k]]);
 }
 
-// lambda[r] = sum_k Sinv[k][r] a1[node[k]] (Sinv symmetric: column reads coalesce)
-__global__ void lambda_kernel(const double* Sinv, const int32_t* node, int64_t c, const double* a1, double* lam) {
-  const int64_t r = (int64_t)blockIdx.x * kT + threadIdx.x;
+// out[r] = sum_k M[k + r c] in[k] over k <= r (kPrefix) or k >= r, three columns:
+// one warp per output row, reading column r of M contiguously.  With M = Q^T
+// (prefix) this is Q in for lower-triangular Q; with M = Q (suffix), Q^T in.
+template <bool kPrefix>
+__global__ void tri_matvec_kernel(const double* M, int64_t c, const double* in, double* out) {
+  const int64_t r = ((int64_t)blockIdx.x * kT + threadIdx.x) / 32;
+  const int lane = threadIdx.x & 31;
   if (r >= c) return;
-  double l0 = 0, l1 = 0, l2 = 0;
-  for (int64_t k = 0; k < c; ++k) {
-    const double s = Sinv[k * c + r];
-    const int64_t g = 3 * (int64_t)node[k];
-    l0 += s * a1[g];
-    l1 += s * a1[g + 1];
-    l2 += s * a1[g + 2];
+  const int64_t k0 = kPrefix ? 0 : r, k1 = kPrefix ? r + 1 : c;
+  const double* col = M + r * c;
+  double a0 = 0, a1 = 0, a2 = 0;
+  for (int64_t k = k0 + lane; k < k1; k += 32) {
+    const double q = col[k];
+    a0 += q * in[3 * k];
+    a1 += q * in[3 * k + 1];
+    a2 += q * in[3 * k + 2];
   }
-  lam[3 * r] = l0;
-  lam[3 * r + 1] = l1;
-  lam[3 * r + 2] = l2;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    a0 += __shfl_down_sync(0xffffffffu, a0, o);
+    a1 += __shfl_down_sync(0xffffffffu, a1, o);
+    a2 += __shfl_down_sync(0xffffffffu, a2, o);
+  }
+  if (lane == 0) {
+    out[3 * r] = a0;
+    out[3 * r + 1] = a1;
+    out[3 * r + 2] = a2;
+  }
 }
 
 // x[i] = a1[i] - sum_k Bc[cidx[k]][i] lambda[k] for the free nodes i; the
@@ -180,9 +196,13 @@ cudaError_t contact_gather_S(int64_t nf, const double* Bc, const int32_t* node, 
 }
 
 cudaError_t contact_correct(int64_t nf, const double* Bc, const int32_t* node, const int32_t* cidx, int64_t c,
-                            const double* Sinv, double* lam, const double* a1, const double* xstar, double* x,
-                            cudaStream_t s) {
-  if (c > 0) lambda_kernel<<<blocks(c), kT, 0, s>>>(Sinv, node, c, a1, lam);
+                            const double* Q, const double* QT, double* abuf, double* ubuf, double* lam,
+                            const double* a1, const double* xstar, double* x, cudaStream_t s) {
+  if (c > 0) {
+    pack_rows_kernel<<<blocks(c), kT, 0, s>>>(node, c, a1, abuf);
+    tri_matvec_kernel<true><<<blocks(32 * c), kT, 0, s>>>(QT, c, abuf, ubuf);
+    tri_matvec_kernel<false><<<blocks(32 * c), kT, 0, s>>>(Q, c, ubuf, lam);
+  }
   correct_kernel<<<blocks(nf), kT, 0, s>>>(nf, Bc, cidx, c, lam, a1, x);
   if (c > 0) set_targets_kernel<<<blocks(c), kT, 0, s>>>(node, c, xstar, x);
   return cudaGetLastError();

@@ -329,7 +329,59 @@ __global__ void nan_scan_kernel(const double* a, int64_t n, int* flags) {
     if (!isfinite(a[i])) { atomicOr(flags, DEV_ERR_NAN); return; }
 }
 
+// QT = Q^T for a c x c column-major matrix (32 x 32 tiles through shared memory)
+__global__ void transpose_kernel(const double* Q, int64_t c, double* QT) {
+  __shared__ double t[32][33];
+  const int64_t i0 = (int64_t)blockIdx.x * 32, j0 = (int64_t)blockIdx.y * 32;
+  for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+    const int64_t i = i0 + threadIdx.x, j = j0 + r;
+    t[r][threadIdx.x] = (i < c && j < c) ? Q[i + j * c] : 0.0;
+  }
+  __syncthreads();
+  for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+    const int64_t j = j0 + threadIdx.x, i = i0 + r;
+    if (i < c && j < c) QT[j + i * c] = t[threadIdx.x][r];
+  }
+}
+
 }  // namespace
+
+// Dense SPD matrix as a tree of one supernode (nr = nc = c, no children): the
+// same blocked Cholesky and right solve as the fronts, giving Q = L^-1.
+pd_status dense_cholesky_inverse(double* S, int64_t c, double* Q, double* QT, int64_t* meta, int* flags,
+                                 cudaStream_t st) {
+  if (c <= 0) return PD_OK;
+  // level_list = front_off = panel_off = {0}; snode_first = row_ptr = {0, c}; child_ptr = {0, 0}
+  const int64_t host_meta[4] = {0, c, 0, 0};
+  PD_CUDA_TRY(cudaMemcpyAsync(meta, host_meta, sizeof(host_meta), cudaMemcpyHostToDevice, st));
+  PD_CUDA_TRY(cudaMemsetAsync(flags, 0, sizeof(int), st));
+  TreeView tv{meta, meta, meta, meta, meta + 2, nullptr, meta, meta, nullptr, S};
+  const int nkb = (int)((c + NB - 1) / NB);
+  for (int kb = 0; kb < nkb; ++kb) {
+    potrf_diag_kernel<<<1, 256, 0, st>>>(tv, 0, kb, flags);
+    const int64_t rows = std::max<int64_t>(c - (int64_t)kb * NB, 1);
+    trsm_panel_kernel<<<dim3((unsigned)((rows + 127) / 128), 1), 128, 0, st>>>(tv, 0, kb);
+    const int64_t ntr = (rows + TILE - 1) / TILE;
+    syrk_update_kernel<<<dim3((unsigned)std::max<int64_t>(ntr * (ntr + 1) / 2, 1), 1), 256, 0, st>>>(tv, 0, kb);
+    PD_CUDA_TRY(cudaGetLastError());
+  }
+  init_Q_kernel<<<dim3((unsigned)std::min<int64_t>((c * c + 255) / 256, 2048), 1), 256, 0, st>>>(tv, Q, 0);
+  const int64_t row_tiles = (c + TILE - 1) / TILE;
+  for (int rb = 0; rb < nkb; ++rb) {
+    trsm_right_diag_kernel<<<dim3((unsigned)((c + 127) / 128), 1), 128, 0, st>>>(tv, Q, 0, rb);
+    const int64_t j0max = (int64_t)(nkb - 1 - rb) * NB;
+    if (j0max > 0) {
+      gemm_right_update_kernel<<<dim3((unsigned)row_tiles, (unsigned)((j0max + TILE - 1) / TILE), 1), 256, 0, st>>>(
+          tv, Q, 0, rb);
+    }
+    PD_CUDA_TRY(cudaGetLastError());
+  }
+  const unsigned tb = (unsigned)((c + 31) / 32);
+  transpose_kernel<<<dim3(tb, tb), dim3(32, 8), 0, st>>>(Q, c, QT);
+  nan_scan_kernel<<<256, 256, 0, st>>>(Q, c * c, flags);
+  PD_CUDA_TRY(cudaGetLastError());
+  return PD_OK;
+}
 
 pd_status factorize_device(MeshImpl* m, cudaStream_t st) {
   const HostMesh& h = m->h;

@@ -158,7 +158,12 @@ struct MeshImpl {
   double* Bc = nullptr;                // (nf x ncand) column-major: L_A^-1 e_j
   int64_t cset = 0, cset_cap = 0;      // contact set size / buffer capacity
   int32_t *cset_node = nullptr, *cset_cand = nullptr;   // (cset) internal id, candidate index
-  double* cset_Sinv = nullptr;         // (cset x cset) inverse of (L_A^-1)_{CC}
+  double* cset_S = nullptr;            // (cset x cset) S = (L_A^-1)_{CC}, factored in place; then Q^T
+  double* cset_Q = nullptr;            // (cset x cset) Q = L^-1 of S = L L^T (column-major, lower)
+  double* cset_a = nullptr;            // (cset x 3) scratch: (a1)_C
+  double* cset_u = nullptr;            // (cset x 3) scratch: Q (a1)_C
+  int64_t* cset_meta = nullptr;        // (4) one-supernode tree of S for the dense factorisation
+  int* cset_flags = nullptr;           // SPD / finite flags of that factorisation
   double* cset_lam = nullptr;          // (cset x 3) multipliers of the current solve
   double* cset_zero = nullptr;         // (cset x 3) zeros: targets of the iteration's directions
   double* cset_xstar = nullptr;        // (cset x 3) targets of the current set
@@ -231,8 +236,12 @@ cudaError_t contact_extract_columns(int64_t nf, const double* x, int64_t k0, int
 cudaError_t contact_gather_S(int64_t nf, const double* Bc, const int32_t* node, const int32_t* cidx, int64_t c,
                              double* S, cudaStream_t s);
 cudaError_t contact_correct(int64_t nf, const double* Bc, const int32_t* node, const int32_t* cidx, int64_t c,
-                            const double* Sinv, double* lam, const double* a1, const double* xstar, double* x,
-                            cudaStream_t s);
+                            const double* Q, const double* QT, double* abuf, double* ubuf, double* lam,
+                            const double* a1, const double* xstar, double* x, cudaStream_t s);
+// Q = L^-1 and QT = Q^T for S = L L^T (c x c, factored in place; QT may alias S);
+// meta: 4 device int64; flags gets DEV_ERR_NOT_SPD / DEV_ERR_NAN
+pd_status dense_cholesky_inverse(double* S, int64_t c, double* Q, double* QT, int64_t* meta, int* flags,
+                                 cudaStream_t st);
 
 cudaError_t contact_pack_rows(const int32_t* rows, int64_t c, const double* a, double* out, cudaStream_t s);
 cudaError_t contact_set_targets(const int32_t* node, int64_t c, const double* xstar, double* x, cudaStream_t s);

@@ -1,6 +1,7 @@
 """Complementarity contact through time (Sec. 5.2, Alg. 3 forward, Alg. 5
-backward): a cube falling onto the ground, GPU against the oracle's active-set
-Newton rollout and its adjoint (positions, contact sets and targets, gradients)."""
+backward): a cube falling onto the ground and the rolling sphere, GPU against
+the oracle's active-set Newton rollout and its adjoint (positions, contact sets
+and targets, gradients)."""
 import dataclasses
 
 import numpy as np
@@ -11,7 +12,7 @@ from oracle import contact as oc
 from oracle.model import Model
 from paper_2101_05917_gb300 import _native as N
 from paper_2101_05917_gb300 import api
-from workloads import contact_cube_c3
+from workloads import contact_cube_c3, rolling_sphere
 
 pytestmark = pytest.mark.gpu
 
@@ -114,3 +115,24 @@ def test_backward_needs_the_forward_sets():
     with pytest.raises(RuntimeError):
         mesh.contact_step_set(2)
     mesh.close()
+
+
+def test_rolling_sphere_matches_oracle():
+    """Resting contact (drop targets) that releases nodes behind the rolling sphere."""
+    sc = rolling_sphere(T=T)
+    model = Model(sc)
+    xs, vs, infos = oc.rollout_complementarity(model, sc.x0, sc.v0, sc.f_ext, sc.contact, T)
+    grads = oc.backward_complementarity(model, xs, vs, infos, loss_grads(sc))
+    roll, sets, out = _gpu(sc, N.PD_PREC_FP64, 1e-11)
+    xg = roll.x.cpu().numpy()
+    for t in range(1, T + 1):
+        err = np.linalg.norm(xg[t] - xs[t]) / np.linalg.norm(xs[t] - sc.x0)
+        nodes, ray = sets[t - 1]
+        print(f"step {t}: displacement-relative position error {err:.2e}, |C| {nodes.size}")
+        assert err <= 1e-8
+        assert set(nodes.tolist()) == set(infos[t - 1]["C"].tolist())
+    for name, key in (("x0", "g_x0"), ("v0", "g_v0"), ("w_corot", "g_wc"), ("w_vol", "g_wv")):
+        g = out[name].cpu().numpy().reshape(grads[key].shape)
+        rel = np.linalg.norm(g - grads[key]) / np.linalg.norm(grads[key])
+        print(f"dL/d{name}: relative error {rel:.2e}")
+        assert rel <= 1e-6

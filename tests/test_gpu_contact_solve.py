@@ -12,7 +12,7 @@ from oracle.model import Model
 from oracle.pd_cpu import ScalarA
 from paper_2101_05917_gb300 import _native as N
 from paper_2101_05917_gb300 import api
-from workloads import contact_cube_c3, quadruped, small_beam
+from workloads import contact_cube_c3, napkin, quadruped, small_beam
 
 pytestmark = pytest.mark.gpu
 
@@ -26,8 +26,11 @@ def _cases():
     beam_cand = (np.isclose(z, z.min()) & (beam.dirichlet == 0)).astype(np.uint8)
     cube = contact_cube_c3(N=6, T=1)
     quad = quadruped(8, T=1)
+    # napkin: 169 bottom candidates; sets of 33, 97 and 169 nodes span several 32-column
+    # blocks and 64-row tiles of the dense factorisation of S, with ragged tails
+    nap = napkin(12, 0.5)
     return [("beam", beam, beam_cand), ("cube", cube, cube.contact.astype(np.uint8)),
-            ("quadruped", quad, quad.contact.astype(np.uint8))]
+            ("quadruped", quad, quad.contact.astype(np.uint8)), ("napkin", nap, nap.contact.astype(np.uint8))]
 
 
 def _mesh(sc, precision):
@@ -42,7 +45,7 @@ def _mesh(sc, precision):
 # mixed: the FP32 solve's ~1e-7 error is amplified by the correction when a large
 # contact set cancels most of a1 (4e-5 with every surface node of the quadruped fixed)
 @pytest.mark.parametrize("precision,tol", [(N.PD_PREC_FP64, 1e-10), (N.PD_PREC_MIXED, 1e-4)])
-@pytest.mark.parametrize("case", range(3))
+@pytest.mark.parametrize("case", range(4))
 def test_constrained_solve_matches_oracle(precision, tol, case):
     name, sc, cand = _cases()[case]
     sc0, mesh, L = _mesh(sc, precision)
@@ -52,7 +55,7 @@ def test_constrained_solve_matches_oracle(precision, tol, case):
     pos_in_free[free] = np.arange(free.size)
     cands = np.flatnonzero(cand)
     rng = np.random.default_rng(100 + case)
-    for c in sorted({0, 1, 7, cands.size}):
+    for c in sorted({0, 1, 7, 33, 97, cands.size} & set(range(cands.size + 1))):
         C = np.sort(rng.choice(cands, size=c, replace=False)) if c else np.zeros(0, dtype=np.int64)
         rng.shuffle(C)   # any order
         b = rng.standard_normal(sc0.x0.shape)

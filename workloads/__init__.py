@@ -27,5 +27,7 @@ from .scenes import (  # noqa: F401
     serving_stream_c4,
     beam_c5,
     small_beam,
+    rolling_sphere,
+    napkin,
     SCENES,
 )

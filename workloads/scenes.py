@@ -234,6 +234,75 @@ def serving_stream_c4(n_requests: int = 256, rate_hz: float = 50.0, T: int = 100
     return np.cumsum(gaps) - gaps[0], sizes
 
 
+def _sphere_mask(D: int, R: float) -> np.ndarray:
+    c = np.arange(D) + 0.5
+    X, Y, Z = np.meshgrid(c, c, c, indexing="ij")
+    return (((X - D / 2) ** 2 + (Y - D / 2) ** 2 + (Z - D / 2) ** 2) <= R * R).astype(np.uint8).ravel()
+
+
+def rolling_sphere(T: int = 100, v: float = 0.2, index: int = 6) -> Scene:
+    """Soft sphere rolling on the ground z = 0 with complementarity contact: the
+    cells of a 10^3 grid whose centres lie within 5 cells of its centre (552
+    elements, 823 nodes = 2469 DoFs, the paper's rolling-sphere size), dx = 1 cm,
+    resting on the ground and rolling along +x without slipping (v_x = v,
+    omega_y = v / radius).  Contact candidates: the 72 surface nodes of the lower
+    front quarter in a 5-node band around the rolling plane (|y - y_c| <= 2 dx,
+    z <= z_c, x >= x_c - dx), the region the rolling brings down to the ground."""
+    D, dx = 10, 0.01
+    mask = _sphere_mask(D, 5.0)
+    nodes = kept_nodes(D, D, D, mask)
+    n = nodes.size
+    e = int(np.count_nonzero(mask))
+    i, j, k = _grid_ijk(nodes, D, D)
+    x0 = _positions(D, D, D, dx, (0.0, 0.0, 0.0), nodes)
+    surf = _surface_nodes(D, D, D, mask, nodes).astype(bool)
+    contact = (surf & (np.abs(j - 5) <= 2) & (k <= 5) & (i >= 4)).astype(np.uint8)
+    centre = np.full(3, 5 * dx)
+    radius = 5 * dx
+    omega = np.array([0.0, v / radius, 0.0])
+    v0 = np.array([v, 0.0, 0.0])[None, :] + np.cross(omega[None, :], x0 - centre[None, :])
+    return Scene(name="rolling_sphere", nx=D, ny=D, nz=D, dx=dx, origin=np.zeros(3), cell_mask=mask,
+                 density=1e3, youngs=np.full(e, 1e5), poisson=0.45, corotated=True, volume=True,
+                 muscle=None, fiber=None, dirichlet=np.zeros(n, dtype=np.uint8), contact=contact,
+                 gravity=np.array([0.0, 0.0, -9.81]), h=0.005, T=T, x0=x0, v0=v0, f_ext=np.zeros((n, 3)),
+                 act=None, k_contact=0.0, mu=0.0, loss_w=_rng(index, 3).standard_normal((n, 3)),
+                 tol_fwd=1e-6, tol_bwd=1e-6)
+
+
+def napkin(N: int, frac: float, T: int = 3, gap: float = 5e-4, v_drop: float = 0.2, index: int = 7) -> Scene:
+    """One-layer N x N x 1-cell napkin (2 (N+1)^2 nodes; N = 25 ... 100 gives the
+    paper's 4056 ... 61206 DoFs), dx = 1 cm, gap above the ground z = 0.  The
+    nodes over a central disc move down at v_drop, so the disc's bottom nodes
+    reach the ground in the first step; the disc holds round(frac * n) bottom
+    nodes (frac <= 0.5: at most every bottom node), which sets the contact-set
+    size as the obstacle's solid angle does in the paper.  Candidates: every
+    bottom node."""
+    nx = ny = N
+    nz = 1
+    dx = 0.01
+    nodes = kept_nodes(nx, ny, nz, None)
+    n = nodes.size
+    i, j, k = _grid_ijk(nodes, ny, nz)
+    x0 = _positions(nx, ny, nz, dx, (0.0, 0.0, gap), nodes)
+    bottom = k == 0
+    # disc: the round(frac * n) bottom nodes nearest the centre (ties by node order)
+    r2 = (i - N / 2) ** 2 + (j - N / 2) ** 2
+    want = min(int(round(frac * n)), int(bottom.sum()))
+    order = np.lexsort((np.arange(n), r2))
+    order = order[bottom[order]][:want]
+    disc_ij = set(zip(i[order].tolist(), j[order].tolist()))
+    in_disc = np.array([(a, b) in disc_ij for a, b in zip(i.tolist(), j.tolist())])
+    v0 = np.zeros((n, 3))
+    v0[in_disc, 2] = -v_drop
+    return Scene(name=f"napkin_{N}x{N}x1_{int(round(100 * frac))}", nx=nx, ny=ny, nz=nz, dx=dx,
+                 origin=np.array([0.0, 0.0, gap]), cell_mask=None, density=1e3, youngs=np.full(N * N, 1e5),
+                 poisson=0.45, corotated=True, volume=True, muscle=None, fiber=None,
+                 dirichlet=np.zeros(n, dtype=np.uint8), contact=bottom.astype(np.uint8),
+                 gravity=np.array([0.0, 0.0, -9.81]), h=0.005, T=T, x0=x0, v0=v0, f_ext=np.zeros((n, 3)),
+                 act=None, k_contact=0.0, mu=0.0, loss_w=_rng(index, 3).standard_normal((n, 3)),
+                 tol_fwd=1e-6, tol_bwd=1e-6)
+
+
 SCENES = {
     "c1": cantilever_c1,
     "c2": beam_c2,
