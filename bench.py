@@ -277,7 +277,7 @@ def run_ours(args):
     t_solve = solve_ms / 1e3 / max(solves_timed, 1)
     peak, peak_kind = peaks()
     achieved = bytes_solve / t_solve / 1e9
-    traffic_path = os.path.join(ROOT, "profiles", "solve_traffic.json")
+    traffic_path = os.path.join(ROOT, "profiles", "solve_traffic.txt")
     traffic = None
     if os.path.exists(traffic_path):
         with open(traffic_path) as f:

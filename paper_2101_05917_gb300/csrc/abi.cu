@@ -1157,6 +1157,7 @@ pd_status pd_factorize(pd_mesh mesh, const double* w_corot, const double* w_vol,
   const int64_t nnz = I.h.factor_nnz();
   if (!I.Q64) PD_CUDA_TRY(dalloc(&I, &I.Q64, (size_t)nnz));
   if (I.precision == PD_PREC_MIXED && !I.Q32) PD_CUDA_TRY(dalloc(&I, &I.Q32, (size_t)nnz));
+  if (I.precision == PD_PREC_MIXED && !I.Qs) PD_CUDA_TRY(dalloc(&I, &I.Qs, (size_t)I.sched.stream_elems));
   drop_iteration_graphs(&I);   // they captured the weights, panels and precision
   I.factor_gen += 1;           // contact candidate columns of the old factor are stale
   I.factorized = false;

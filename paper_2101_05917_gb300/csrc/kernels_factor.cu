@@ -482,6 +482,7 @@ pd_status factorize_device(MeshImpl* m, cudaStream_t st) {
   if (m->Q32) {
     to_float_kernel<<<2048, 256, 0, st>>>(m->Q64, m->Q32, nnz);
     PD_CUDA_TRY(cudaGetLastError());
+    PD_CUDA_TRY(pack_solve_stream(m, st));   // the FP32 solve's tile-contiguous copy
   }
   PD_CUDA_TRY(cudaFreeAsync(front, st));
   int flags = 0;

@@ -18,7 +18,16 @@
 // BC columns x min(16384 / BC, 1024) rows (BC = 64, 32, 16 or 8).  (Smaller CTAs of
 // 128 threads with 32 KB tiles were measured slower: 276 vs 224 us on the 32x32x64
 // beam.)  All-zero tiles of the
-// triangular L11^-1 block are skipped.  Tiles sharing an output block write
+// triangular L11^-1 block are skipped.
+// In FP32 every tile's panel values are also stored contiguously, in the order the
+// tile body reads them (MeshImpl::Qs, packed once per factorisation), and reach
+// shared memory by one bulk copy (cp.async.bulk, completion on an mbarrier) issued
+// before the tile waits for its dependencies: the copy engine keeps a whole 64 KB
+// tile in flight per CTA, where per-thread register loads were limited by the
+// requests an SM can have outstanding (a traced solve showed ~2.5 us just to issue
+// a tile's loads).  The stored layout adds zeros for the upper triangle of L11^-1
+// and for ragged tile edges (about 13 % more bytes than the structural entries).
+// FP64 tiles keep the register loads.  Tiles sharing an output block write
 // partial sums; the last tile to finish (integer ticket) adds them in tile order,
 // so the result does not depend on scheduling and no float atomics run.  Both
 // sweeps run in one persistent launch scheduled by the supernodal tree
@@ -41,6 +50,7 @@ constexpr int kMaxC = 4 * kCols;       // widest forward tile (4 column groups)
 __host__ __device__ constexpr int bwd_tile_rows(int bc) { return kTileElems / bc < 1024 ? kTileElems / bc : 1024; }
 constexpr int kMaxBR = 1024;
 constexpr int kPreSlots = 4;          // W-row sources per position held in registers
+constexpr int kStreamBytes = kTileElems * 4;   // shared-memory tile buffer of the FP32 kernel
 
 // loads issued back to back per thread: all 64 in FP32, four batches of 16 in FP64
 // (register budget of two CTAs per SM)
@@ -65,6 +75,7 @@ struct SolveParams {
   int* err;
   void* partial;                // per tile partial sums (T)
   const void* Q;
+  const float* Qs;              // FP32: tiles stored contiguously (SolveTile::soff)
   const double* b;
   void* u;       // (3 nf) T
   void* W;       // (3 * below rows) T
@@ -147,6 +158,83 @@ __device__ __forceinline__ void signal_done(unsigned long long* c) {
   if (threadIdx.x == 0) add_release(c);
 }
 
+// ------------------------------------------------------------ bulk copies
+// One mbarrier per CTA tracks the tile copy: thread 0 arms it with the byte count
+// and issues the copy; every thread waits for the phase to complete (bounded), and
+// the parity flips once per streamed tile.
+struct StreamCtx {
+  float* tile;               // kStreamBytes of dynamic shared memory
+  unsigned long long* mbar;  // shared
+  int* state;                // shared: 0 = copy in flight, 1 = not issued (bad descriptor), 2 = wait gave up
+  unsigned phase;            // parity of the next completion
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(unsigned long long* bar) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar)) : "memory");
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, unsigned phase) {
+  uint32_t done;
+  asm volatile(
+      "{\n .reg .pred P;\n mbarrier.try_wait.parity.shared::cta.b64 P, [%1], %2;\n selp.u32 %0, 1, 0, P;\n}"
+      : "=r"(done)
+      : "r"(smem_u32(bar)), "r"(phase)
+      : "memory");
+  return done != 0;
+}
+
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// thread 0: bulk copy of the tile's streamed panel values into sc.tile
+__device__ __forceinline__ void stream_issue(const SolveParams& p, const SolveTile& tl, StreamCtx& sc) {
+  if (threadIdx.x != 0) return;
+  const float* src = p.Qs + tl.soff;
+  const uint32_t bytes = (uint32_t)tl.sbytes;
+  const uint32_t dst = smem_u32(sc.tile), bar = smem_u32(sc.mbar);
+  if (bytes == 0u || bytes > (uint32_t)kStreamBytes || (bytes & 15u) || (dst & 15u) ||
+      (reinterpret_cast<uintptr_t>(src) & 15u)) {
+    atomicOr(p.err, DEV_ERR_TIMEOUT);
+    *sc.state = 1;
+    return;
+  }
+  *sc.state = 0;
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+               ::"r"(dst), "l"(src), "r"(bytes), "r"(bar)
+               : "memory");
+}
+
+// every thread: wait (at most about a second) for the tile copy, then flip its
+// parity.  Called after a CTA barrier that follows stream_issue (so *sc.state is
+// visible) and before the barrier that ends the tile (so thread 0 rewrites the
+// state only after every thread has read it).  A wait that gives up sets state 2:
+// the persistent loop then leaves after the tile.
+__device__ __forceinline__ void stream_wait(const SolveParams& p, StreamCtx& sc) {
+  if (*sc.state != 0) return;
+  if (!mbar_try_wait(sc.mbar, sc.phase)) {
+    const unsigned long long t0 = global_ns();
+    while (!mbar_try_wait(sc.mbar, sc.phase)) {
+      if (global_ns() - t0 > 1000000000ull) {
+        atomicOr(p.err, DEV_ERR_TIMEOUT);
+        *sc.state = 2;
+        return;
+      }
+    }
+  }
+  sc.phase ^= 1u;
+}
+
 // W-row sources of a position, loaded before the dependency wait (they are static)
 struct Slots {
   int32_t g[kPreSlots];
@@ -189,7 +277,8 @@ __device__ __forceinline__ void add_W(const SolveParams& p, const Slots& sl, int
 // are added in group order.
 template <typename T, int R>
 __device__ void fwd_tile_body(const SolveParams& p, const SolveTile& tl, int64_t tid_g, unsigned long long epoch,
-                              PersistSmem& sm) {
+                              PersistSmem& sm, StreamCtx& stc) {
+  constexpr bool kStream = sizeof(T) == 4;   // FP32: panel values by bulk copy
   constexpr int G = kThreads / R;
   constexpr int C = G * kCols;
   constexpr int B = Batch<T>::kLoads;
@@ -206,9 +295,13 @@ __device__ void fwd_tile_body(const SolveParams& p, const SolveTile& tl, int64_t
   const int cnt = (int)max((int64_t)0, min((int64_t)kCols, cend - cg0));
   const T* Qr = Q + r + cg0 * nr;
   // static data first: panel values, right-hand side, W-row sources
-  T q[B];
+  T q[kStream ? 1 : B];
+  if constexpr (kStream) {
+    stream_issue(p, tl, stc);
+  } else {
 #pragma unroll
-  for (int k = 0; k < B; ++k) q[k] = (k < cnt) ? __ldg(Qr + (int64_t)k * nr) : T(0);
+    for (int k = 0; k < B; ++k) q[k] = (k < cnt) ? __ldg(Qr + (int64_t)k * nr) : T(0);
+  }
   // rhs columns of this thread: col0 + threadIdx.x + kThreads * i
   constexpr int CPT = (C + kThreads - 1) / kThreads;
   double bb[CPT][3];
@@ -258,18 +351,38 @@ __device__ void fwd_tile_body(const SolveParams& p, const SolveTile& tl, int64_t
   __syncthreads();
   T a0 = T(0), a1 = T(0), a2 = T(0);
   const T(*rg)[3] = rhs + g * kCols;
-  constexpr int NB = kCols / B;
-#pragma unroll
-  for (int nb = 0; nb < NB; ++nb) {
-    if (nb > 0) {   // FP64: the next batch of columns
-#pragma unroll
-      for (int k = 0; k < B; ++k) q[k] = (nb * B + k < cnt) ? __ldg(Qr + (int64_t)(nb * B + k) * nr) : T(0);
+  if constexpr (kStream) {
+    // stored layout [group][column k < kmax][row rl < rv], zeros past each row's
+    // columns: the same products in the same order as the masked register loads of
+    // the FP64 path.  (Staging the 64 values into registers first, as the backward
+    // tile does, was measured slower here.)
+    stream_wait(p, stc);
+    const int kmax = tl.sld;
+    const int rv = (int)min((int64_t)R, nr - row0);
+    if (rl < rv) {
+      const float* qs = stc.tile + g * kmax * rv + rl;
+#pragma unroll 8
+      for (int k = 0; k < kmax; ++k) {
+        const float qk = qs[k * rv];
+        a0 += qk * rg[k][0];
+        a1 += qk * rg[k][1];
+        a2 += qk * rg[k][2];
+      }
     }
+  } else {
+    constexpr int NB = kCols / B;
 #pragma unroll
-    for (int k = 0; k < B; ++k) {
-      a0 += q[k] * rg[nb * B + k][0];
-      a1 += q[k] * rg[nb * B + k][1];
-      a2 += q[k] * rg[nb * B + k][2];
+    for (int nb = 0; nb < NB; ++nb) {
+      if (nb > 0) {   // FP64: the next batch of columns
+#pragma unroll
+        for (int k = 0; k < B; ++k) q[k] = (nb * B + k < cnt) ? __ldg(Qr + (int64_t)(nb * B + k) * nr) : T(0);
+      }
+#pragma unroll
+      for (int k = 0; k < B; ++k) {
+        a0 += q[k] * rg[nb * B + k][0];
+        a1 += q[k] * rg[nb * B + k][1];
+        a2 += q[k] * rg[nb * B + k][2];
+      }
     }
   }
   if (G > 1) {
@@ -324,7 +437,8 @@ __device__ void fwd_tile_body(const SolveParams& p, const SolveTile& tl, int64_t
 // per column the lanes' sums are added by a fixed shuffle tree.
 template <typename T, int BC>
 __device__ void bwd_tile_body(const SolveParams& p, const SolveTile& tl, int64_t tid_g, unsigned long long epoch,
-                              PersistSmem& sm) {
+                              PersistSmem& sm, StreamCtx& stc) {
+  constexpr bool kStream = sizeof(T) == 4;   // FP32: panel values by bulk copy
   constexpr int CW = BC / kWarps;
   constexpr int BR = bwd_tile_rows(BC);
   constexpr int RL = BR / 32;           // rows per lane
@@ -354,7 +468,8 @@ __device__ void bwd_tile_body(const SolveParams& p, const SolveTile& tl, int64_t
       }
     }
   };
-  load_batch(0);
+  if constexpr (kStream) stream_issue(p, tl, stc);
+  else load_batch(0);
   // global rows of the tile's below rows (static)
   constexpr int VR = BR / kThreads > 0 ? BR / kThreads : 1;
   int32_t gidx[VR];
@@ -393,17 +508,46 @@ __device__ void bwd_tile_body(const SolveParams& p, const SolveTile& tl, int64_t
   T acc[CW][3];
 #pragma unroll
   for (int c = 0; c < CW; ++c) acc[c][0] = acc[c][1] = acc[c][2] = T(0);
+  if constexpr (kStream) {
+    // stored layout [column c < bcv][row rr < rn], zeros above the diagonal of
+    // L11^-1.  Staged into registers first (all shared loads in flight together;
+    // reading them inside the product loop was measured ~2.5 us slower per tile),
+    // then the same products in the same order as the masked register loads of the
+    // FP64 path.
+    stream_wait(p, stc);
+    const int rs = (int)rn;
+    const int bcv = (int)min((int64_t)BC, nc - col0);
+    T qq[CW][RL];
 #pragma unroll
-  for (int nb = 0; nb < NB; ++nb) {
-    if (nb > 0) load_batch(nb);
+    for (int c = 0; c < CW; ++c)
 #pragma unroll
-    for (int i = 0; i < RB; ++i) {
-      const int rr = lane + 32 * (nb * RB + i);
+      for (int i = 0; i < RL; ++i) {
+        const int rr = lane + 32 * i, cc = warp * CW + c;
+        qq[c][i] = (rr < rs && cc < bcv) ? stc.tile[cc * rs + rr] : T(0);
+      }
+#pragma unroll
+    for (int i = 0; i < RL; ++i) {
+      const int rr = lane + 32 * i;
 #pragma unroll
       for (int c = 0; c < CW; ++c) {
-        acc[c][0] += q[c][i] * v[rr][0];
-        acc[c][1] += q[c][i] * v[rr][1];
-        acc[c][2] += q[c][i] * v[rr][2];
+        acc[c][0] += qq[c][i] * v[rr][0];
+        acc[c][1] += qq[c][i] * v[rr][1];
+        acc[c][2] += qq[c][i] * v[rr][2];
+      }
+    }
+  } else {
+#pragma unroll
+    for (int nb = 0; nb < NB; ++nb) {
+      if (nb > 0) load_batch(nb);
+#pragma unroll
+      for (int i = 0; i < RB; ++i) {
+        const int rr = lane + 32 * (nb * RB + i);
+#pragma unroll
+        for (int c = 0; c < CW; ++c) {
+          acc[c][0] += q[c][i] * v[rr][0];
+          acc[c][1] += q[c][i] * v[rr][1];
+          acc[c][2] += q[c][i] * v[rr][2];
+        }
       }
     }
   }
@@ -449,13 +593,23 @@ __device__ void bwd_tile_body(const SolveParams& p, const SolveTile& tl, int64_t
 // kThreads / 2, kThreads / 4 rows), backward with BC = 64 / 32 / 16 / 8 columns
 enum TileKind { kF1 = 0, kF2 = 1, kF4 = 2, kB64 = 3, kB32 = 4, kB16 = 5, kB8 = 6 };
 
+// dynamic shared memory of the FP32 kernel: the streamed tile
+extern __shared__ __align__(128) unsigned char solve_dsm[];
+
 template <typename T>
 __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 2 : 1) solve_persistent_kernel(SolveParams p) {
   if (p.gate && (p.gate->converged || !p.gate->accepted)) return;
   __shared__ PersistSmem sm;
   __shared__ unsigned long long tk[2];
+  __shared__ __align__(8) unsigned long long mbar;
+  __shared__ int sstate;
+  StreamCtx stc{reinterpret_cast<float*>(solve_dsm), &mbar, &sstate, 0u};
   const unsigned long long per = (unsigned long long)p.ntiles + gridDim.x;
-  if (threadIdx.x == 0) tk[0] = atomicAdd(p.gticket, 1ull);
+  if (threadIdx.x == 0) {
+    tk[0] = atomicAdd(p.gticket, 1ull);
+    sstate = 0;
+    if (sizeof(T) == 4) mbar_init(&mbar);
+  }
   __syncthreads();
   int slot = 0;
   unsigned long long t = tk[0];
@@ -472,15 +626,23 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 2 : 1) solve_persis
     if (threadIdx.x == 0) tk[slot ^ 1] = atomicAdd(p.gticket, 1ull);
     const SolveTile tl = load_tile(p.tiles, tile);
     switch (tl.pad0) {
-      case kF1: fwd_tile_body<T, kThreads>(p, tl, tile, epoch, sm); break;
-      case kF2: fwd_tile_body<T, kThreads / 2>(p, tl, tile, epoch, sm); break;
-      case kF4: fwd_tile_body<T, kThreads / 4>(p, tl, tile, epoch, sm); break;
-      case kB64: bwd_tile_body<T, 64>(p, tl, tile, epoch, sm); break;
-      case kB32: bwd_tile_body<T, 32>(p, tl, tile, epoch, sm); break;
-      case kB16: bwd_tile_body<T, 16>(p, tl, tile, epoch, sm); break;
-      default: bwd_tile_body<T, 8>(p, tl, tile, epoch, sm); break;
+      case kF1: fwd_tile_body<T, kThreads>(p, tl, tile, epoch, sm, stc); break;
+      case kF2: fwd_tile_body<T, kThreads / 2>(p, tl, tile, epoch, sm, stc); break;
+      case kF4: fwd_tile_body<T, kThreads / 4>(p, tl, tile, epoch, sm, stc); break;
+      case kB64: bwd_tile_body<T, 64>(p, tl, tile, epoch, sm, stc); break;
+      case kB32: bwd_tile_body<T, 32>(p, tl, tile, epoch, sm, stc); break;
+      case kB16: bwd_tile_body<T, 16>(p, tl, tile, epoch, sm, stc); break;
+      default: bwd_tile_body<T, 8>(p, tl, tile, epoch, sm, stc); break;
     }
     __syncthreads();   // shared memory of this tile is free; the drawn ticket is visible
+    if (sizeof(T) == 4 && sstate == 2) {
+      // a copy wait gave up (the copy may still be in flight): wait once more,
+      // bounded, and leave; every other issued copy completed inside its tile
+      const unsigned long long t0 = global_ns();
+      while (!mbar_try_wait(&mbar, stc.phase) && global_ns() - t0 < 1000000000ull) {
+      }
+      return;
+    }
     slot ^= 1;
     t = tk[slot];
   }
@@ -610,6 +772,69 @@ void build_solve_schedule(const HostMesh& h, SolveSchedule& S) {
       S.all.push_back(u);
     }
   }
+  // streamed FP32 layout, tile after tile in persistent order, each start 16-byte
+  // aligned: forward [group][column k < kmax][row < rv], kmax = the columns of the
+  // tile's last row inside its first group (the most of any thread); backward
+  // [column < bcv][row < rn]
+  int64_t off = 0;
+  for (SolveTile& t : S.all) {
+    int64_t elems = 0;
+    if (t.pad0 <= kF4) {
+      const int R = t.pad0 == kF1 ? kThreads : (t.pad0 == kF2 ? kThreads / 2 : kThreads / 4);
+      const int64_t rv = std::min<int64_t>(R, (int64_t)t.nr - t.a);
+      const int64_t rmax = t.a + rv - 1;
+      const int64_t cend = rmax < t.nc ? std::min<int64_t>(t.nc, rmax + 1) : t.nc;
+      const int64_t kmax = std::max<int64_t>(0, std::min<int64_t>(kCols, cend - t.b));
+      t.sld = (int32_t)kmax;
+      elems = (kThreads / R) * kmax * rv;
+    } else {
+      const int BC = t.pad0 == kB64 ? 64 : (t.pad0 == kB32 ? 32 : (t.pad0 == kB16 ? 16 : 8));
+      const int64_t rn = std::min<int64_t>(bwd_tile_rows(BC), (int64_t)t.nr - t.b);
+      const int64_t bcv = std::min<int64_t>(BC, (int64_t)t.nc - t.a);
+      t.sld = (int32_t)rn;
+      elems = bcv * rn;
+    }
+    const int64_t padded = (elems + 3) / 4 * 4;
+    t.soff = off;
+    t.sbytes = (int32_t)(padded * 4);
+    off += padded;
+  }
+  S.stream_elems = off;
+}
+
+// Copies the FP32 panels into the streamed layout, one block per tile (the same
+// index rules as the tile bodies' masked loads: zeros above the diagonal of L11^-1
+// and past the panel).
+__global__ void pack_stream_kernel(const SolveTile* tiles, const float* Q, float* Qs) {
+  const SolveTile tl = load_tile(tiles, blockIdx.x);
+  const int64_t nr = tl.nr, nc = tl.nc;
+  const float* P = Q + tl.panel_off;
+  float* out = Qs + tl.soff;
+  int64_t total;
+  if (tl.pad0 <= kF4) {
+    const int R = tl.pad0 == kF1 ? kThreads : (tl.pad0 == kF2 ? kThreads / 2 : kThreads / 4);
+    const int64_t rv = min((int64_t)R, nr - tl.a);
+    const int64_t kmax = tl.sld;
+    total = (kThreads / R) * kmax * rv;
+    for (int64_t i = threadIdx.x; i < total; i += blockDim.x) {
+      const int64_t rl = i % rv, gk = i / rv;
+      const int64_t k = gk % kmax, g = gk / kmax;
+      const int64_t r = tl.a + rl, col = tl.b + g * kCols + k;
+      const int64_t cend = r < nc ? min(nc, r + 1) : nc;
+      out[i] = col < cend ? P[r + col * nr] : 0.0f;
+    }
+  } else {
+    const int BC = tl.pad0 == kB64 ? 64 : (tl.pad0 == kB32 ? 32 : (tl.pad0 == kB16 ? 16 : 8));
+    const int64_t rn = tl.sld;
+    const int64_t bcv = min((int64_t)BC, nc - tl.a);
+    total = bcv * rn;
+    for (int64_t i = threadIdx.x; i < total; i += blockDim.x) {
+      const int64_t rr = i % rn, c = i / rn;
+      const int64_t row = tl.b + rr, j = tl.a + c;
+      out[i] = (row >= nc || row >= j) ? P[row + j * nr] : 0.0f;
+    }
+  }
+  for (int64_t i = total + threadIdx.x; i < tl.sbytes / 4; i += blockDim.x) out[i] = 0.0f;
 }
 
 size_t solve_partial_bytes(const SolveSchedule& S) {
@@ -621,9 +846,19 @@ size_t solve_partial_bytes(const SolveSchedule& S) {
 // fewer resident at a time, which the ticket order tolerates (a CTA draws
 // tickets only once it runs).
 int solve_persistent_occupancy() {
+  // the FP32 kernel's streamed tile buffer; set on the current device (meshes and
+  // servers call this on their device before any solve)
+  cudaFuncSetAttribute(solve_persistent_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, kStreamBytes);
   int occ = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, solve_persistent_kernel<float>, kThreads, 0);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, solve_persistent_kernel<float>, kThreads, kStreamBytes);
   return std::max(1, occ);
+}
+
+cudaError_t pack_solve_stream(const MeshImpl* m, cudaStream_t st) {
+  const int64_t ntiles = (int64_t)m->sched.all.size();
+  if (!m->Qs || !m->Q32 || ntiles == 0) return cudaSuccess;
+  pack_stream_kernel<<<(unsigned)ntiles, 256, 0, st>>>(m->all_tiles, m->Q32, m->Qs);
+  return cudaGetLastError();
 }
 
 cudaError_t solve_A(const MeshImpl* m, const IterState* gate, const double* b, double* out,
@@ -640,6 +875,8 @@ cudaError_t solve_A(const MeshImpl* m, const IterState* gate, const double* b, d
   p.x = out;
   const bool f32 = precision == PD_PREC_MIXED;
   p.Q = f32 ? (const void*)m->Q32 : (const void*)m->Q64;
+  p.Qs = f32 ? m->Qs : nullptr;
+  if (f32 && !m->Qs) return cudaErrorInvalidValue;
   const int64_t ntiles = (int64_t)m->sched.all.size();
   if (ntiles == 0) return cudaSuccess;
   p.tiles = m->all_tiles;
@@ -656,7 +893,7 @@ cudaError_t solve_A(const MeshImpl* m, const IterState* gate, const double* b, d
   p.parent = m->parent;
   p.err = m->ws.flags;
   const unsigned grid = (unsigned)std::min<int64_t>(m->solve_grid, ntiles);
-  if (f32) solve_persistent_kernel<float><<<grid, kThreads, 0, st>>>(p);
+  if (f32) solve_persistent_kernel<float><<<grid, kThreads, kStreamBytes, st>>>(p);
   else solve_persistent_kernel<double><<<grid, kThreads, 0, st>>>(p);
   return cudaGetLastError();
 }

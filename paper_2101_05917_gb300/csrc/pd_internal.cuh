@@ -71,13 +71,19 @@ struct alignas(16) SolveTile {
   // output blocks that counter reaches per solve; more are read from the tree arrays
   int32_t dep[kTileDeps];
   int32_t dep_blocks[kTileDeps];
-  int32_t pad1[4];
+  // FP32 streamed copy of the tile's panel values (one bulk copy into shared memory):
+  // offset in floats (16-byte aligned), bytes (multiple of 16), and the leading
+  // dimension of the tile's layout (forward: columns per thread group; backward: rows)
+  int64_t soff;
+  int32_t sbytes;
+  int32_t sld;
 };
 static_assert(sizeof(SolveTile) == 128, "tile descriptors are 128 bytes");
 struct SolveSchedule {
   std::vector<SolveTile> fwd, bwd;
   std::vector<SolveTile> all;      // persistent order: forward tiles, then backward tiles by descending level
   int64_t n_fwd_out = 0, n_bwd_out = 0;
+  int64_t stream_elems = 0;        // floats of the streamed FP32 tiles (both sweeps)
   std::vector<int32_t> nfb, nbb;   // per supernode: forward / backward output blocks
   std::vector<SolveLevel> levels;
 };
@@ -186,6 +192,9 @@ struct MeshImpl {
   // factor panels Q_s = [L11^-1 ; L21 L11^-1] (column-major nr x nc)
   double* Q64 = nullptr;
   float* Q32 = nullptr;
+  // the FP32 panels again, cut into the solve's tiles and stored tile after tile in
+  // the order each tile body reads them (SolveTile::soff), for one bulk copy per tile
+  float* Qs = nullptr;
   Workspace ws;
   std::vector<std::pair<void*, size_t>> allocations;   // device buffers and their bytes
 };
@@ -256,5 +265,7 @@ cudaError_t solve_A(const MeshImpl* m, const IterState* gate, const double* b, d
 void build_solve_schedule(const HostMesh& h, SolveSchedule& S);
 size_t solve_partial_bytes(const SolveSchedule& S);
 int solve_persistent_occupancy();
+// fills m->Qs from m->Q32 (after every mixed-precision factorisation)
+cudaError_t pack_solve_stream(const MeshImpl* m, cudaStream_t s);
 
 }  // namespace pd

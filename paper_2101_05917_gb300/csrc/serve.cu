@@ -138,12 +138,13 @@ struct pd_server_s {
 namespace {
 
 // Device memory of one running request, estimated from its node and cell counts:
-// the factor panels (FP64 + FP32) of a 3D nested-dissection ordering grow like
-// n^(4/3); trajectories (T+1) x n x 3 positions and velocities; about 40 work
-// vectors of 3n.  Used for admission only.
+// the factor panels (FP64, FP32 and the FP32 solve tiles of both sweeps, about
+// 8 + 4 + 9 bytes per entry) of a 3D nested-dissection ordering grow like n^(4/3);
+// trajectories (T+1) x n x 3 positions and velocities; about 40 work vectors of
+// 3n.  Used for admission only.
 size_t estimate_bytes(const Job& j) {
   const double n = (double)j.n;
-  const double panels = 12.0 * 8.0 * n * std::cbrt(n) * 4.0;
+  const double panels = 21.0 * 8.0 * n * std::cbrt(n) * 4.0;
   const double traj = 2.0 * (j.T + 1.0) * 3.0 * n * 8.0;
   const double vecs = 40.0 * 3.0 * n * 8.0 + 8.0 * 24.0 * j.e + (double)j.T * j.e * 16.0;
   return (size_t)(panels + traj + vecs);
