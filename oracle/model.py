@@ -7,8 +7,8 @@
   Hess E    = sum_c w_c G_c^T (I - dp_c/dx) G_c                        (Eqn 21)
   A         = M/h^2 + sum_c w_c G_c^T G_c                              (Eqn 19)
 
-Energy set per Gauss point q of element e (weights per unit volume times
-V_q = dx^3/8): corotated w = E/(1+nu) (= 2 mu), volume-preserving
+Energy set per quadrature point q of element e (weights per unit volume times
+V_q = dx^3/8 for hexahedra, dx^3/6 per tetrahedron of the tet6 rule): corotated w = E/(1+nu) (= 2 mu), volume-preserving
 w = E nu/((1+nu)(1-2nu)) (= lambda), muscle w = E on fibre elements; penalty
 contact w = k per candidate node.  (Reading: the paper does not state the
 map from (E, nu) to w.)
@@ -35,7 +35,8 @@ class Model:
     def __init__(self, scene, youngs=None, poisson=None, mu=None):
         s = scene
         self.scene = s
-        self.mesh = VoxelMesh(s.nx, s.ny, s.nz, s.dx, s.origin, s.cell_mask)
+        self.mesh = VoxelMesh(s.nx, s.ny, s.nz, s.dx, s.origin, s.cell_mask,
+                              rule=getattr(s, "element_rule", "hex8"))
         mesh = self.mesh
         assert mesh.n == s.x0.shape[0]
         E = np.asarray(s.youngs if youngs is None else youngs, dtype=np.float64)
@@ -125,8 +126,9 @@ class Model:
         GtG = np.einsum("qki,qkj->qij", G, G)                  # (8, 24, 24)
         blocks = np.einsum("e,qij->eij", (self.w_corot + self.w_vol) * Vq, GtG)
         if np.any(self.w_musc):
-            Gm = np.zeros((mesh.e, 8, 3, 24))
-            for q in range(8):
+            Q = G.shape[0]
+            Gm = np.zeros((mesh.e, Q, 3, 24))
+            for q in range(Q):
                 Gq = G[q].reshape(3, 3, 24)                    # [i, j, dof]
                 Gm[:, q] = np.einsum("ijd,ej->eid", Gq, self.fiber)
             blocks = blocks + np.einsum("e,eqki,eqkj->eij", self.w_musc * Vq, Gm, Gm)
@@ -134,7 +136,7 @@ class Model:
             return blocks
         loc = self.local(x, act)
         F = loc["F"]
-        J = np.zeros((mesh.e, 8, 9, 9))
+        J = np.zeros((mesh.e, G.shape[0], 9, 9))
         if np.any(self.w_corot):
             J += self.w_corot[:, None, None, None] * pj.jacobian_corotated(F)
         if np.any(self.w_vol):

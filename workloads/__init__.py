@@ -29,5 +29,7 @@ from .scenes import (  # noqa: F401
     small_beam,
     rolling_sphere,
     napkin,
+    tet_beam,
+    tet_ball,
     SCENES,
 )

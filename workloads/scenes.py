@@ -42,6 +42,9 @@ class Scene:
     loss_w: np.ndarray                 # (n, 3): loss = sum(loss_w * x_T)
     tol_fwd: float
     tol_bwd: float
+    # element rule on the kept cells: "hex8" (trilinear hexahedra) or "tet6" (six
+    # linear tetrahedra per cell); per-element arrays stay per cell either way
+    element_rule: str = "hex8"
 
     @property
     def n_nodes(self) -> int:
@@ -309,3 +312,35 @@ SCENES = {
     "c3": contact_cube_c3,
     "c5": beam_c5,
 }
+
+
+def tet_beam(nx=4, ny=2, nz=2, *, T=5, **kw) -> Scene:
+    """small_beam meshed with six tetrahedra per cell (tet6 rule); materials,
+    boundary, loads and loss weights as the hexahedral beam."""
+    sc = small_beam(nx, ny, nz, T=T, **kw)
+    return dataclasses.replace(sc, name=f"tet_beam_{nx}x{ny}x{nz}", element_rule="tet6")
+
+
+def tet_ball(T: int = 20, index: int = 8) -> Scene:
+    """Ball of 336 linear tetrahedra: the cells of a 6^3 grid within 2.4 cells of
+    its centre, six tetrahedra each (117 nodes, 351 DoFs; the paper's tennis-ball
+    mesh has 320 tetrahedra, Sec. 7), dx = 1 cm, its lowest nodes 2 mm above the
+    ground z = 0, moving at (0.2, 0, -0.3) m/s plus N(0, 0.01^2) per DoF; penalty
+    contact k = 1e4 N/m on the surface nodes with Coulomb friction mu = 0.4."""
+    D, dx = 6, 0.01
+    mask = _sphere_mask(D, 2.4)
+    nodes = kept_nodes(D, D, D, mask)
+    n = nodes.size
+    e = int(np.count_nonzero(mask))
+    i, j, k = _grid_ijk(nodes, D, D)
+    origin = np.array([0.0, 0.0, 0.002 - dx * float(k.min())])
+    x0 = _positions(D, D, D, dx, origin, nodes)
+    contact = _surface_nodes(D, D, D, mask, nodes)
+    v0 = np.array([0.2, 0.0, -0.3])[None, :] + 0.01 * _rng(index, 2).standard_normal((n, 3))
+    return Scene(name="tet_ball_336", nx=D, ny=D, nz=D, dx=dx, origin=origin, cell_mask=mask,
+                 density=1e3, youngs=np.full(e, 1e5), poisson=0.45, corotated=True, volume=True,
+                 muscle=None, fiber=None, dirichlet=np.zeros(n, dtype=np.uint8), contact=contact,
+                 gravity=np.array([0.0, 0.0, -9.81]), h=0.005, T=T, x0=x0, v0=v0,
+                 f_ext=np.zeros((n, 3)), act=None, k_contact=1e4, mu=0.4,
+                 loss_w=_rng(index, 3).standard_normal((n, 3)), tol_fwd=1e-10, tol_bwd=1e-10,
+                 element_rule="tet6")
