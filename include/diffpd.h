@@ -55,6 +55,19 @@ enum { PD_PREC_FP64 = 0, PD_PREC_MIXED = 1 };
 
 typedef struct pd_mesh_s* pd_mesh;
 
+/* Element rules on the kept cells of the voxel grid. */
+enum {
+  PD_ELEM_HEX8 = 0,  /* trilinear hexahedron, 2x2x2 Gauss points of weight dx^3/8 each;
+                        lumped mass rho dx^3/8 per cell corner */
+  PD_ELEM_TET6 = 1   /* six linear tetrahedra per cell, one for each order of the axes
+                        along the path from corner (0,0,0) to corner (1,1,1) (conforming
+                        between cells), one point of weight dx^3/6 each; lumped mass
+                        rho V/4 per tetrahedron vertex.  Stands in for the tetrahedral
+                        meshes of Secs. 5.1 and 7; per-element inputs (weights, fibres,
+                        actuation, their gradients) stay per cell and are shared by its
+                        six tetrahedra */
+};
+
 /* Voxel mesh description.  All pointers are host memory, read during the call. */
 typedef struct {
   int32_t nx, ny, nz;           /* cells along x, y, z */
@@ -66,6 +79,7 @@ typedef struct {
   const uint8_t* contact;       /* per kept node: ground-penalty candidate, NULL = none */
   int32_t leaf_max;             /* nested-dissection leaf size, 0 = 64 */
   int32_t device;               /* CUDA device ordinal, -1 = host analysis only */
+  int32_t element_rule;         /* PD_ELEM_HEX8 (0) or PD_ELEM_TET6 */
 } pd_mesh_desc;
 
 typedef struct {
@@ -268,7 +282,7 @@ pd_status pd_contact_step_set(pd_mesh m, int32_t t, int32_t* nodes_host, uint8_t
  * word) in one fixed-size device array owned by the library; every GPU that
  * loads the library holds that array (6.3 MB) until the process exits.
  * Computes grad_E (n_nodes, 3) and energy (1 scalar, may be NULL) exactly as
- * pd_local_step, on the current device and `stream`, for at most
+ * pd_local_step on a PD_ELEM_HEX8 mesh, on the current device and `stream`, for at most
  * PD_NOALLOC_MAX_CELLS cells and 8 x PD_NOALLOC_MAX_CELLS nodes (larger meshes
  * return PD_ERR_INVALID_ARG).  Inputs (device): elems (n_elems, 8) node ids with
  * corner a = 4 di + 2 dj + dk of a cube of edge dx; inc_ptr (n_nodes + 1) and inc

@@ -27,6 +27,9 @@ STATUS_NAMES = {0: "PD_OK", 1: "PD_ERR_INVALID_ARG", 2: "PD_ERR_OOM", 3: "PD_ERR
 
 PD_PREC_FP64 = 0
 PD_PREC_MIXED = 1
+PD_ELEM_HEX8 = 0
+PD_ELEM_TET6 = 1
+ELEMENT_RULES = {"hex8": PD_ELEM_HEX8, "tet6": PD_ELEM_TET6}
 
 EXPORT = {"inc_ptr": 0, "inc": 1, "perm": 2, "snode_first": 3, "row_ptr": 4, "rows": 5, "parent": 6,
           "level": 7, "rel": 8, "level_ptr": 9, "level_list": 10}
@@ -40,7 +43,7 @@ class MeshDesc(ctypes.Structure):
     _fields_ = [("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("nz", ctypes.c_int32),
                 ("dx", ctypes.c_double), ("origin", ctypes.c_double * 3), ("density", ctypes.c_double),
                 ("cell_mask", c_u8_p), ("dirichlet", c_u8_p), ("contact", c_u8_p),
-                ("leaf_max", ctypes.c_int32), ("device", ctypes.c_int32)]
+                ("leaf_max", ctypes.c_int32), ("device", ctypes.c_int32), ("element_rule", ctypes.c_int32)]
 
 
 class MeshInfo(ctypes.Structure):

@@ -65,10 +65,11 @@ class Rollout:
 
 
 class PDMesh:
-    """A voxel hex mesh resident on one GPU (pd_create_mesh ... pd_mesh_destroy)."""
+    """A voxel mesh (hexahedra, or six tetrahedra per cell with element_rule
+    "tet6") resident on one GPU (pd_create_mesh ... pd_mesh_destroy)."""
 
     def __init__(self, nx, ny, nz, dx, density, origin=(0.0, 0.0, 0.0), cell_mask=None, dirichlet=None,
-                 contact=None, leaf_max=64, device: Optional[int] = 0):
+                 contact=None, leaf_max=64, device: Optional[int] = 0, element_rule: str = "hex8"):
         L = N.lib()
         self._keep = []
         mask_arr, mask_p = _u8(cell_mask, nx * ny * nz, "cell_mask")
@@ -78,6 +79,9 @@ class PDMesh:
         desc.origin = (ctypes.c_double * 3)(*origin)
         desc.density = density
         desc.cell_mask = mask_p
+        if element_rule not in N.ELEMENT_RULES:
+            raise N.PDError(N.PD_ERR_INVALID_ARG, f"unknown element rule {element_rule!r}")
+        desc.element_rule = N.ELEMENT_RULES[element_rule]
         # per-node masks need the node count: a host-only analysis gives it
         probe = N.MeshDesc.from_buffer_copy(desc)
         probe.device = -1
@@ -107,7 +111,8 @@ class PDMesh:
     @classmethod
     def from_scene(cls, sc, leaf_max=64, device=0):
         return cls(sc.nx, sc.ny, sc.nz, sc.dx, sc.density, tuple(sc.origin), sc.cell_mask, sc.dirichlet,
-                   sc.contact if sc.k_contact > 0 else None, leaf_max, device)
+                   sc.contact if sc.k_contact > 0 else None, leaf_max, device,
+                   getattr(sc, "element_rule", "hex8"))
 
     def close(self):
         if getattr(self, "handle", None) is not None and self.handle.value:

@@ -402,8 +402,27 @@ pd_status factorize_device(MeshImpl* m, cudaStream_t st) {
   ap.contact = m->contact;
   ap.inv_h2 = 1.0 / (m->h_step * m->h_step);
   ap.k = m->k_contact;
-  ap.Vq = h.dx * h.dx * h.dx / 8.0;
-  {
+  ap.Vq = h.dx * h.dx * h.dx / (h.rule == PD_ELEM_TET6 ? 6.0 : 8.0);
+  if (h.rule == PD_ELEM_TET6) {
+    // tetrahedron q < 6: the path from corner 0 along axes p1, p2, p3 to corner 7;
+    // barycentric gradients (-e_p1, e_p1 - e_p2, e_p2 - e_p3, e_p3) / dx at its four
+    // corners, zero elsewhere; points 6 and 7 unused (zero)
+    for (int q = 0; q < 8; ++q)
+      for (int a = 0; a < 8; ++a)
+        for (int d = 0; d < 3; ++d) ap.gN[q][a][d] = 0.0;
+    for (int q = 0; q < 6; ++q) {
+      const int p1 = q >> 1, lo = p1 == 0 ? 1 : 0, hi = p1 == 2 ? 1 : 2;
+      const int p2 = (q & 1) ? hi : lo, p3 = 3 - p1 - p2;
+      const int c1 = 4 >> p1, c2 = c1 + (4 >> p2);
+      const double s = 1.0 / h.dx;
+      ap.gN[q][0][p1] -= s;
+      ap.gN[q][c1][p1] += s;
+      ap.gN[q][c1][p2] -= s;
+      ap.gN[q][c2][p2] += s;
+      ap.gN[q][c2][p3] -= s;
+      ap.gN[q][7][p3] += s;
+    }
+  } else {
     const double g = 1.0 / std::sqrt(3.0);
     for (int q = 0; q < 8; ++q)
       for (int a = 0; a < 8; ++a)
@@ -416,6 +435,8 @@ pd_status factorize_device(MeshImpl* m, cudaStream_t st) {
           }
           ap.gN[q][a][d] = ((a >> (2 - d)) & 1) ? prod : -prod;
         }
+  }
+  {
     for (int a = 0; a < 8; ++a)
       for (int b = 0; b < 8; ++b) {
         double s = 0;

@@ -36,6 +36,31 @@ __device__ __forceinline__ T gradN(int a, int q, int d, T inv_dx) {
   return cbit(a, d) ? prod : -prod;
 }
 
+// Tetrahedral rule: tetrahedron q < 6 runs from corner 0 along axes p1, p2, p3 to
+// corner 7 (q = 2 p1 + [p2 is the larger of the other two]); the gradients of its
+// barycentric coordinates are (-e_p1, e_p1 - e_p2, e_p2 - e_p3, e_p3) / dx at corners
+// 0, c1 = {p1}, c2 = {p1, p2}, 7, zero at the other corners; q = 6, 7 are unused.
+template <typename T>
+__device__ __forceinline__ T gradN_tet(int a, int q, int d, T inv_dx) {
+  if (q >= 6) return T(0);
+  const int p1 = q >> 1, lo = p1 == 0 ? 1 : 0, hi = p1 == 2 ? 1 : 2;
+  const int p2 = (q & 1) ? hi : lo, p3 = 3 - p1 - p2;
+  const int c1 = 4 >> p1, c2 = c1 + (4 >> p2);
+  int g = 0;
+  if (a == 0) g = -(d == p1);
+  else if (a == c1) g = (d == p1) - (d == p2);
+  else if (a == c2) g = (d == p2) - (d == p3);
+  else if (a == 7) g = (d == p3);
+  return T(g) * inv_dx;
+}
+
+enum { RULE_HEX8 = 0, RULE_TET6 = 1 };
+
+template <typename T, int RULE>
+__device__ __forceinline__ T shape_grad(int a, int q, int d, T inv_dx) {
+  return RULE == RULE_TET6 ? gradN_tet<T>(a, q, d, inv_dx) : gradN<T>(a, q, d, inv_dx);
+}
+
 enum { MODE_FORCE = 0, MODE_HVP = 1, MODE_PGRAD = 2 };
 
 struct ElemParams {
@@ -53,7 +78,7 @@ struct ElemParams {
   int* flags;
 };
 
-template <typename T, int MODE>
+template <typename T, int MODE, int RULE = RULE_HEX8>
 __global__ void __launch_bounds__(kElemThreads, sizeof(T) == 8 ? 1 : (MODE == MODE_FORCE ? 3 : 2))
 element_kernel(ElemParams p) {
   if (p.gate && p.gate->converged) return;
@@ -69,7 +94,8 @@ element_kernel(ElemParams p) {
   const int64_t e = ((int64_t)blockIdx.x * kElemThreads + threadIdx.x) >> 3;
   const bool valid = e < p.ne;
   const T inv_dx = T(1.0 / p.dx);
-  const T Vq = T(p.Vq);
+  // volume weight of this lane's point (the tetrahedral rule leaves lanes 6, 7 idle)
+  const T Vq = (RULE == RULE_TET6 && k >= 6) ? T(0) : T(p.Vq);
 
   // ---- corner loads: relative displacement of corner k w.r.t. corner 0
   int node = valid ? p.elems[e * 8 + k] : 0;
@@ -105,7 +131,7 @@ element_kernel(ElemParams p) {
     }
 #pragma unroll
     for (int j = 0; j < 3; ++j) {
-      const T gN = gradN<T>(a, k, j, inv_dx);
+      const T gN = shape_grad<T, RULE>(a, k, j, inv_dx);
 #pragma unroll
       for (int i = 0; i < 3; ++i) {
         H[i][j] += da[i] * gN;
@@ -229,7 +255,7 @@ element_kernel(ElemParams p) {
       for (int j = 0; j < 3; ++j) Sq[i][j] = __shfl_sync(0xffffffffu, S[i][j], base + q);
 #pragma unroll
     for (int j = 0; j < 3; ++j) {
-      const T gN = gradN<T>(k, q, j, inv_dx);
+      const T gN = shape_grad<T, RULE>(k, q, j, inv_dx);
 #pragma unroll
       for (int i = 0; i < 3; ++i) fa[i] += Sq[i][j] * gN;
     }
@@ -386,8 +412,22 @@ ElemParams make_params(const LocalArgs& a) {
   p.wm = a.m->wm;
   p.fiber = a.m->fiber;
   p.dx = a.m->h.dx;
-  p.Vq = a.m->h.dx * a.m->h.dx * a.m->h.dx / 8.0;
+  p.Vq = a.m->h.dx * a.m->h.dx * a.m->h.dx / (a.m->h.rule == PD_ELEM_TET6 ? 6.0 : 8.0);
   return p;
+}
+
+// element_kernel<T, MODE, rule of the mesh>
+template <int MODE>
+void launch_elem(const MeshImpl* m, int precision, const ElemParams& p, cudaStream_t s) {
+  const int nb = (int)((m->h.e * 8 + kElemThreads - 1) / kElemThreads);
+  const bool tet = m->h.rule == PD_ELEM_TET6;
+  if (precision == PD_PREC_MIXED) {
+    if (tet) element_kernel<float, MODE, RULE_TET6><<<nb, kElemThreads, 0, s>>>(p);
+    else element_kernel<float, MODE, RULE_HEX8><<<nb, kElemThreads, 0, s>>>(p);
+  } else {
+    if (tet) element_kernel<double, MODE, RULE_TET6><<<nb, kElemThreads, 0, s>>>(p);
+    else element_kernel<double, MODE, RULE_HEX8><<<nb, kElemThreads, 0, s>>>(p);
+  }
 }
 
 GatherParams make_gather(const MeshImpl* m) {
@@ -419,11 +459,7 @@ cudaError_t launch_element_forces(const LocalArgs& a, void* elembuf, double* ene
   p.out = elembuf;
   p.energy = energy_partials;
   p.flags = flags;
-  const int nb = element_blocks(a.m);
-  if (a.precision == PD_PREC_MIXED)
-    element_kernel<float, MODE_FORCE><<<nb, kElemThreads, 0, s>>>(p);
-  else
-    element_kernel<double, MODE_FORCE><<<nb, kElemThreads, 0, s>>>(p);
+  launch_elem<MODE_FORCE>(a.m, a.precision, p, s);
   return cudaGetLastError();
 }
 
@@ -431,11 +467,7 @@ cudaError_t launch_element_hvp(const LocalArgs& a, void* elembuf, int* flags, cu
   ElemParams p = make_params(a);
   p.out = elembuf;
   p.flags = flags;
-  const int nb = element_blocks(a.m);
-  if (a.precision == PD_PREC_MIXED)
-    element_kernel<float, MODE_HVP><<<nb, kElemThreads, 0, s>>>(p);
-  else
-    element_kernel<double, MODE_HVP><<<nb, kElemThreads, 0, s>>>(p);
+  launch_elem<MODE_HVP>(a.m, a.precision, p, s);
   return cudaGetLastError();
 }
 
@@ -447,12 +479,8 @@ cudaError_t launch_element_param_grads(const LocalArgs& a, double* g_wc, double*
   p.g_wm = g_wm;
   p.g_act = g_act;
   p.flags = a.m->ws.flags;
-  const int nb = element_blocks(a.m);
   // per-element products in the requested precision, accumulated over the steps in FP64
-  if (a.precision == PD_PREC_MIXED)
-    element_kernel<float, MODE_PGRAD><<<nb, kElemThreads, 0, s>>>(p);
-  else
-    element_kernel<double, MODE_PGRAD><<<nb, kElemThreads, 0, s>>>(p);
+  launch_elem<MODE_PGRAD>(a.m, a.precision, p, s);
   return cudaGetLastError();
 }
 

@@ -74,6 +74,8 @@ std::string analyse(const pd_mesh_desc& d, HostMesh& m) {
   m.nx = d.nx; m.ny = d.ny; m.nz = d.nz; m.dx = d.dx; m.density = d.density;
   for (int c = 0; c < 3; ++c) m.origin[c] = d.origin[c];
   m.leaf_max = d.leaf_max > 0 ? d.leaf_max : 64;
+  if (d.element_rule != PD_ELEM_HEX8 && d.element_rule != PD_ELEM_TET6) return "mesh: unknown element rule";
+  m.rule = d.element_rule;
   const int64_t nx = d.nx, ny = d.ny, nz = d.nz;
   const int64_t ncell = nx * ny * nz;
   const int64_t ngrid = (nx + 1) * (ny + 1) * (nz + 1);
@@ -175,8 +177,16 @@ std::string analyse(const pd_mesh_desc& d, HostMesh& m) {
     m.contact[in] = m.contact_kept[m.kept_of_internal[in]];
   }
   m.mass.assign(m.n, 0.0);
-  const double mcorner = d.density * d.dx * d.dx * d.dx / 8.0;
-  for (int64_t i = 0; i < 8 * m.e; ++i) m.mass[m.elems[i]] += mcorner;
+  if (m.rule == PD_ELEM_HEX8) {
+    const double mcorner = d.density * d.dx * d.dx * d.dx / 8.0;
+    for (int64_t i = 0; i < 8 * m.e; ++i) m.mass[m.elems[i]] += mcorner;
+  } else {
+    // rho V / 4 to each vertex of each tetrahedron, V = dx^3 / 6: the two corners on
+    // the cell diagonal belong to all six tetrahedra, the other six corners to two
+    const double share = d.density * d.dx * d.dx * d.dx / 24.0;
+    for (int64_t c = 0; c < m.e; ++c)
+      for (int a = 0; a < 8; ++a) m.mass[m.elems[8 * c + a]] += (a == 0 || a == 7 ? 6.0 : 2.0) * share;
+  }
   m.inc_ptr.assign(m.n + 1, 0);
   for (int64_t i = 0; i < 8 * m.e; ++i) m.inc_ptr[m.elems[i] + 1]++;
   for (int64_t i = 0; i < m.n; ++i) m.inc_ptr[i + 1] += m.inc_ptr[i];

@@ -15,6 +15,7 @@ struct HostMesh {
   int nx = 0, ny = 0, nz = 0;
   double dx = 0, origin[3] = {0, 0, 0}, density = 0;
   int leaf_max = 64;
+  int rule = 0;                        // PD_ELEM_HEX8 / PD_ELEM_TET6
   int64_t n = 0, e = 0, nf = 0;       // kept nodes, kept cells, free nodes
 
   // kept order (increasing grid id / cell id)

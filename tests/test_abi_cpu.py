@@ -7,7 +7,7 @@ import numpy as np
 import pytest
 
 from oracle import structure
-from workloads import cantilever_c1, quadruped, small_beam, contact_cube_c3
+from workloads import cantilever_c1, quadruped, small_beam, contact_cube_c3, tet_ball
 
 
 @pytest.fixture(scope="module")
@@ -30,7 +30,7 @@ def test_exports_every_declared_symbol(native):
 
 
 CASES = [(cantilever_c1(), 64), (cantilever_c1(), 8), (quadruped(8, T=1), 16), (quadruped(9, T=1), 64),
-         (small_beam(5, 3, 4, T=1), 5), (contact_cube_c3(N=6, T=1), 32)]
+         (small_beam(5, 3, 4, T=1), 5), (contact_cube_c3(N=6, T=1), 32), (tet_ball(T=1), 16)]
 
 
 @pytest.mark.parametrize("case", range(len(CASES)))
@@ -56,6 +56,14 @@ def test_invalid_arguments_are_rejected(native):
     # every node fixed
     with pytest.raises(N.PDError):
         api.PDMesh(1, 1, 1, 0.01, 1e3, dirichlet=np.ones(8, np.uint8), device=None)
+    # unknown element rule (binding and host analysis)
+    with pytest.raises(N.PDError):
+        api.PDMesh(2, 1, 1, 0.01, 1e3, device=None, element_rule="hex27")
+    import ctypes
+    desc = N.MeshDesc()
+    desc.nx, desc.ny, desc.nz, desc.dx, desc.density, desc.device, desc.element_rule = 2, 1, 1, 0.01, 1e3, -1, 7
+    h = ctypes.c_void_p()
+    assert N.lib().pd_create_mesh(ctypes.byref(desc), ctypes.byref(h)) == N.PD_ERR_INVALID_ARG
     m = api.PDMesh(2, 1, 1, 0.01, 1e3, device=None)
     import ctypes
     st = native.lib().pd_factorize(m.handle, None, None, None, None, None, None)
