@@ -458,6 +458,7 @@ struct StepInfo {
   int iters = 0, fp64_iters = 0, ls = 0;
   double rel = 0;
   bool converged = true;
+  bool nan = false;   // a residual was non-finite (the call reports PD_ERR_NAN)
 };
 
 // One implicit-Euler step from the internal state (w.xprev, w.vprev): on return
@@ -646,6 +647,7 @@ pd_status forward_step(Ctx& c, const double* act_t, const double* fext_int, doub
       const IterState& sh = *w.st_host;
       if (sh.status & DEV_ERR_NAN) {
         info.converged = false;
+        info.nan = true;
         break;
       }
       if (sh.converged) {
@@ -815,6 +817,7 @@ pd_status backward_step(Ctx& c, const double* xnext, const double* xt_, const do
     const IterState* sh = w.st_host;
     if (sh->status & DEV_ERR_NAN) {
       info.converged = false;
+      info.nan = true;
       break;
     }
     if (sh->converged) {
@@ -1217,7 +1220,7 @@ pd_status pd_forward(pd_mesh mesh, const double* x0, const double* v0, const dou
   if (x_traj) PD_CUDA_TRY(cudaMemcpyAsync(x_traj, x0, sizeof(double) * 3 * n, cudaMemcpyDeviceToDevice, s));
   if (v_traj) PD_CUDA_TRY(cudaMemcpyAsync(v_traj, v0, sizeof(double) * 3 * n, cudaMemcpyDeviceToDevice, s));
   int guess = 4;
-  bool all_ok = true;
+  bool all_ok = true, any_nan = false;
   for (int t = 0; t < T; ++t) {
     const double* act_t = act ? act + (int64_t)t * m->h.e : nullptr;
     double* tx = nullptr;
@@ -1236,6 +1239,7 @@ pd_status pd_forward(pd_mesh mesh, const double* x0, const double* v0, const dou
     if (e != PD_OK) return e;
     accumulate(stats, info, true);
     if (!info.converged) all_ok = false;
+    if (info.nan) any_nan = true;
   }
   PD_CUDA_TRY(cudaStreamSynchronize(s));
   check_flags(c, stats);
@@ -1245,8 +1249,9 @@ pd_status pd_forward(pd_mesh mesh, const double* x0, const double* v0, const dou
     set_error("pd_forward: a device-side wait in the solve timed out");
     return PD_ERR_TIMEOUT;
   }
-  const int nan = w.st_host->status & DEV_ERR_NAN;
-  if (nan) {
+  // a step whose residual was non-finite stops there and the later steps restart
+  // from stale values: the call reports it even when the last step converged
+  if (any_nan || (w.st_host->status & DEV_ERR_NAN)) {
     set_error("pd_forward: non-finite residual");
     return PD_ERR_NAN;
   }
@@ -1323,7 +1328,7 @@ pd_status pd_backward(pd_mesh mesh, const double* x_traj, const double* v_traj, 
   if (loss_v(T)) kept_to_internal_kernel<<<grid_for(n), 256, 0, s>>>(n, m->kept_of_internal, loss_v(T), w.av);
   else PD_CUDA_TRY(cudaMemsetAsync(w.av, 0, sizeof(double) * 3 * n, s));
   int guess_f = 4, guess_b = 4;
-  bool all_ok = true;
+  bool all_ok = true, any_nan = false;
   // scratch for x_{t+1}, x_t, v_t in internal order
   double* xn_int = w.iox;     // x_{t+1}
   double* xt_int = w.xprev;   // x_t
@@ -1371,6 +1376,7 @@ pd_status pd_backward(pd_mesh mesh, const double* x_traj, const double* v_traj, 
       if (er != PD_OK) return er;
       accumulate(stats, info, false);
       if (!info.converged) all_ok = false;
+      if (info.nan) any_nan = true;
     }
   }
   if (g_x0) internal_to_kept_kernel<<<grid_for(n), 256, 0, s>>>(n, n, m->kept_of_internal, w.ax, g_x0);
@@ -1385,7 +1391,7 @@ pd_status pd_backward(pd_mesh mesh, const double* x_traj, const double* v_traj, 
     set_error("pd_backward: a device-side wait in the solve timed out");
     return PD_ERR_TIMEOUT;
   }
-  if (w.st_host->status & DEV_ERR_NAN) {
+  if (any_nan || (w.st_host->status & DEV_ERR_NAN)) {
     set_error("pd_backward: non-finite residual");
     return PD_ERR_NAN;
   }
