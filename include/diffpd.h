@@ -114,7 +114,15 @@ enum {
   PD_EXPORT_LEVEL = 7,     /* (n_snodes) */
   PD_EXPORT_REL = 8,       /* positions of each supernode's below rows in its parent */
   PD_EXPORT_LEVEL_PTR = 9, /* (n_levels+1) into PD_EXPORT_LEVEL_LIST */
-  PD_EXPORT_LEVEL_LIST = 10 /* (n_snodes) supernodes grouped by level, ascending ids */
+  PD_EXPORT_LEVEL_LIST = 10, /* (n_snodes) supernodes grouped by level, ascending ids */
+  PD_EXPORT_SOLVE_TILES = 11 /* 7 per triangular-solve tile, in the persistent solve's order
+                                (forward tiles by ascending level, then backward tiles by
+                                descending level): supernode, tile kind (0-2 forward tiles of
+                                256/128/64 rows, 3-6 backward tiles of 64/32/16/8 columns),
+                                first row (forward) or column (backward), first column or
+                                row, offset of its FP32 streamed copy in floats, its bytes,
+                                and the leading dimension of that copy (forward: columns
+                                per thread group; backward: rows) */
 };
 pd_status pd_mesh_export(pd_mesh m, int32_t what, int64_t* host_out, int64_t capacity,
                          int64_t* count);

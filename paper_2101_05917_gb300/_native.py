@@ -32,7 +32,7 @@ PD_ELEM_TET6 = 1
 ELEMENT_RULES = {"hex8": PD_ELEM_HEX8, "tet6": PD_ELEM_TET6}
 
 EXPORT = {"inc_ptr": 0, "inc": 1, "perm": 2, "snode_first": 3, "row_ptr": 4, "rows": 5, "parent": 6,
-          "level": 7, "rel": 8, "level_ptr": 9, "level_list": 10}
+          "level": 7, "rel": 8, "level_ptr": 9, "level_list": 10, "solve_tiles": 11}
 
 c_double_p = ctypes.POINTER(ctypes.c_double)
 c_u8_p = ctypes.POINTER(ctypes.c_uint8)

@@ -1100,6 +1100,20 @@ pd_status pd_mesh_export(pd_mesh m, int32_t what, int64_t* host_out, int64_t cap
     case PD_EXPORT_REL: v.assign(h.rel.begin(), h.rel.end()); break;
     case PD_EXPORT_LEVEL_PTR: v = h.level_ptr; break;
     case PD_EXPORT_LEVEL_LIST: v = h.level_list; break;
+    case PD_EXPORT_SOLVE_TILES: {
+      SolveSchedule S;   // host-only meshes have none built: derive it here
+      const SolveSchedule* sp = &m->impl.sched;
+      if (m->impl.device < 0) {
+        build_solve_schedule(h, S);
+        sp = &S;
+      }
+      v.reserve(7 * sp->all.size());
+      for (const SolveTile& t : sp->all) {
+        const int64_t row[7] = {t.s, t.pad0, t.a, t.b, t.soff, t.sbytes, t.sld};
+        v.insert(v.end(), row, row + 7);
+      }
+      break;
+    }
     default:
       set_error("pd_mesh_export: unknown structure");
       return PD_ERR_INVALID_ARG;
