@@ -10,6 +10,8 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "pd_internal.cuh"
 #include "pd_vec.cuh"
 
@@ -101,6 +103,28 @@ size_t mesh_device_bytes(pd_mesh m) { return m ? m->impl.ws.bytes : 0; }
 using namespace pd;
 
 namespace {
+
+// NVTX range around a call or a time step (step index as payload), for profilers
+// that attribute kernels to ranges (nsys, ncu --nvtx); a no-op without a tool
+struct Range {
+  explicit Range(const char* name, int64_t step = -1) {
+    if (step < 0) {
+      nvtxRangePushA(name);
+      return;
+    }
+    nvtxEventAttributes_t a{};
+    a.version = NVTX_VERSION;
+    a.size = NVTX_EVENT_ATTRIB_STRUCT_SIZE;
+    a.messageType = NVTX_MESSAGE_TYPE_ASCII;
+    a.message.ascii = name;
+    a.payloadType = NVTX_PAYLOAD_TYPE_INT64;
+    a.payload.llValue = step;
+    nvtxRangePushEx(&a);
+  }
+  ~Range() { nvtxRangePop(); }
+  Range(const Range&) = delete;
+  Range& operator=(const Range&) = delete;
+};
 
 pd_status ensure_workspace(MeshImpl* m, int lbfgs_m) {
   Workspace& w = m->ws;
@@ -1131,6 +1155,7 @@ pd_status pd_mesh_export(pd_mesh m, int32_t what, int64_t* host_out, int64_t cap
 
 pd_status pd_factorize(pd_mesh mesh, const double* w_corot, const double* w_vol, const double* w_muscle,
                        const double* fiber, const pd_factor_opts* opts, void* stream) {
+  const Range range("pd_factorize");
   pd_status ck = check_mesh(mesh, false);
   if (ck != PD_OK) return ck;
   if (!opts || !(opts->h > 0)) {
@@ -1186,6 +1211,7 @@ pd_status pd_factorize(pd_mesh mesh, const double* w_corot, const double* w_vol,
 pd_status pd_forward(pd_mesh mesh, const double* x0, const double* v0, const double* f_ext, const double* act,
                      double mu, int32_t T, const pd_solver_opts* opts, double* x_traj, double* v_traj,
                      pd_stats* stats, void* stream) {
+  const Range range("pd_forward");
   pd_status ck = check_mesh(mesh, true);
   if (ck != PD_OK) return ck;
   if (!x0 || !v0 || T < 0) {
@@ -1248,6 +1274,7 @@ pd_status pd_forward(pd_mesh mesh, const double* x0, const double* v0, const dou
     }
     StepInfo info;
     const auto ts = std::chrono::steady_clock::now();
+    const Range step_range("forward step", t);
     pd_status e = forward_step(c, act_t, fext_int, mu, tx, tv, info, guess, t);
     if (o.step_ms) o.step_ms[t] = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - ts).count();
     if (e != PD_OK) return e;
@@ -1281,6 +1308,7 @@ pd_status pd_backward(pd_mesh mesh, const double* x_traj, const double* v_traj, 
                       int32_t loss_all_steps, const pd_solver_opts* opts, double* g_x0, double* g_v0,
                       double* g_fext, double* g_w_corot, double* g_w_vol, double* g_w_muscle, double* g_act,
                       double* g_mu, pd_stats* stats, void* stream) {
+  const Range range("pd_backward");
   pd_status ck = check_mesh(mesh, true);
   if (ck != PD_OK) return ck;
   if (!x_traj || !v_traj || !dL_dx || T < 0) {
@@ -1360,6 +1388,7 @@ pd_status pd_backward(pd_mesh mesh, const double* x_traj, const double* v_traj, 
       for (int t = ta; t < tb - 1; ++t) {
         StepInfo info;
         const double* act_t = act ? act + (int64_t)t * e : nullptr;
+        const Range step_range("recompute step", t);
         pd_status er = forward_step(c, act_t, fext_int, mu, nullptr, nullptr, info, guess_f, t);
         if (er != PD_OK) return er;
         copy_kernel<<<grid_for(3 * n), 256, 0, s>>>(3 * n, w.xprev, seg + (int64_t)(t + 1 - ta) * 6 * n);
@@ -1382,6 +1411,7 @@ pd_status pd_backward(pd_mesh mesh, const double* x_traj, const double* v_traj, 
       }
       StepInfo info;
       const auto ts = std::chrono::steady_clock::now();
+      const Range step_range("adjoint step", t);
       pd_status er = backward_step(c, xn_int, xt_int, vt_int, act_t, mu, loss_x(t), loss_v(t), gfext_int,
                                    g_w_corot, g_w_vol, g_w_muscle, g_act ? g_act + (int64_t)t * e : nullptr,
                                    g_mu, info, guess_b, t);
