@@ -197,6 +197,18 @@ def run_reference(args):
     print(json.dumps(line))
 
 
+def whole_job_rate(elapsed_s, sim_steps_per_rank, world, device):
+    """(slowest rank's timed seconds, whole-job simulation steps/s): every rank runs
+    an independent replica, so the job's rate is all ranks' steps over the slowest
+    rank's time (a MAX all-reduce; called by every rank after the closing barrier)."""
+    if world > 1:
+        import torch
+        t = torch.tensor([float(elapsed_s)], dtype=torch.float64, device=device)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        elapsed_s = float(t.item())
+    return elapsed_s, world * sim_steps_per_rank / elapsed_s
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -259,13 +271,7 @@ def run_ours(args):
     if world > 1:
         torch.distributed.barrier()
     clk = clocks.stop()
-    elapsed = ev0.elapsed_time(ev1) / 1e3
-    if world > 1:
-        t = torch.tensor([elapsed], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        elapsed = float(t.item())
-    sim_steps = world * args.steps * T
-    value = sim_steps / elapsed
+    elapsed, value = whole_job_rate(ev0.elapsed_time(ev1) / 1e3, args.steps * T, world, dev)
 
     # roofline of the dominant kernel pair (triangular solves), from the live events
     solves = sum(s["solves"] for s in fstats + bstats)
