@@ -1,7 +1,8 @@
 /*
  * diffpd.h -- C ABI of a GB300-native differentiable Projective Dynamics solver.
  *
- * The library simulates hexahedral voxel meshes with implicit Euler solved by
+ * The library simulates voxel meshes (hexahedra, or six tetrahedra per cell)
+ * with implicit Euler solved by
  * Projective Dynamics (Sec. 3, Alg. 1 of "DiffPD: Differentiable Projective
  * Dynamics", arXiv 2101.05917) and back-propagates through the rollout with the
  * adjoint splitting iteration  A z_{k+1} = Delta A z_k + dL/dx  (Sec. 4, Eqn 23,
@@ -211,7 +212,13 @@ typedef struct {
  * NULL.  act: (T, e) muscle contraction per step, or NULL.  mu: friction
  * coefficient of the ground penalty contact (Sec. 5.1).
  * x_traj, v_traj: ((S, n, 3)) with S = T+1, or with checkpointing
- * S = T/K + 1 (T must be a multiple of K) holding states 0, K, 2K, ... */
+ * S = T/K + 1 (T must be a multiple of K) holding states 0, K, 2K, ...
+ * Status: PD_OK; PD_ERR_NOT_CONVERGED when a step reached the iteration cap
+ * (outputs and statistics are still written); PD_ERR_NAN when a residual of any
+ * step was non-finite (that step stops, later steps restart from the last finite
+ * iterate: the outputs are not a trajectory); PD_ERR_TIMEOUT when a bounded
+ * device-side wait gave up; PD_ERR_INVALID_ARG before pd_factorize succeeded.
+ * An element with det F <= 0 sets stats->inverted. */
 pd_status pd_forward(pd_mesh m, const double* x0, const double* v0, const double* f_ext,
                      const double* act, double mu, int32_t T, const pd_solver_opts* opts,
                      double* x_traj, double* v_traj, pd_stats* stats, void* stream);
@@ -223,7 +230,8 @@ pd_status pd_forward(pd_mesh m, const double* x0, const double* v0, const double
  * else (n, 3) for the final state only; dL_dv may be NULL.
  * Outputs (each may be NULL): g_x0, g_v0 (n,3); g_fext (n,3) summed over steps;
  * g_w_corot, g_w_vol, g_w_muscle (e) = dL/dw per unit volume; g_act (T, e);
- * g_mu (1). */
+ * g_mu (1).  Status as pd_forward (PD_ERR_NOT_CONVERGED for an adjoint solve that
+ * reached its cap, PD_ERR_NAN for a non-finite residual in any step). */
 pd_status pd_backward(pd_mesh m, const double* x_traj, const double* v_traj,
                       const double* f_ext, const double* act, double mu, int32_t T,
                       const double* dL_dx, const double* dL_dv, int32_t loss_all_steps,
