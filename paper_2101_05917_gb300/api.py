@@ -80,7 +80,7 @@ class PDMesh:
         desc.density = density
         desc.cell_mask = mask_p
         if element_rule not in N.ELEMENT_RULES:
-            raise N.PDError(N.PD_ERR_INVALID_ARG, f"unknown element rule {element_rule!r}")
+            raise ValueError(f"unknown element rule {element_rule!r} (expected one of {sorted(N.ELEMENT_RULES)})")
         desc.element_rule = N.ELEMENT_RULES[element_rule]
         # per-node masks need the node count: a host-only analysis gives it
         probe = N.MeshDesc.from_buffer_copy(desc)
@@ -282,7 +282,11 @@ class PDServer:
                 "pd_serve_create")
 
     def submit_scene(self, sc, precision=N.PD_PREC_MIXED, opts=None, act=None, loss_w=None, T=None) -> int:
-        """Submits a workloads.Scene; act / loss_w / T default to the scene's."""
+        """Submits a workloads.Scene; act / loss_w / T default to the scene's.
+        Requests are hexahedral meshes (the request carries no element rule)."""
+        if getattr(sc, "element_rule", "hex8") != "hex8":
+            raise ValueError("serving requests are hexahedral meshes; got element rule "
+                             f"{sc.element_rule!r}")
         E = np.asarray(sc.youngs, dtype=np.float64)
         wc, wv = material_weights(E, sc.poisson)
         e = E.size

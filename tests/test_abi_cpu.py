@@ -57,7 +57,7 @@ def test_invalid_arguments_are_rejected(native):
     with pytest.raises(N.PDError):
         api.PDMesh(1, 1, 1, 0.01, 1e3, dirichlet=np.ones(8, np.uint8), device=None)
     # unknown element rule (binding and host analysis)
-    with pytest.raises(N.PDError):
+    with pytest.raises(ValueError):
         api.PDMesh(2, 1, 1, 0.01, 1e3, device=None, element_rule="hex27")
     import ctypes
     desc = N.MeshDesc()
@@ -85,3 +85,12 @@ def test_serve_create_rejects_bad_arguments(native):
         assert not h.value
     assert L.pd_serve_submit(None, None, None) == N.PD_ERR_INVALID_ARG
     assert L.pd_serve_drain(None) == N.PD_ERR_INVALID_ARG
+
+
+def test_serving_refuses_tetrahedral_scenes(native):
+    from paper_2101_05917_gb300 import api
+    from workloads import tet_beam
+    srv = api.PDServer.__new__(api.PDServer)   # no device needed: the check comes first
+    srv.handle = None
+    with pytest.raises(ValueError):
+        srv.submit_scene(tet_beam(2, 1, 1, T=1))
