@@ -12,8 +12,9 @@ and convergence checks.
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
 Prints one JSON line (rank 0).  value = forward+backward simulation steps per
-second over all ranks (each rank runs an independent replica: the solve does not
-shard).
+second over all ranks (each rank runs an independent replica: every global step is
+one sweep over one factor's elimination tree, so a rollout does not shard across
+GPUs and no collective is on the data path).
 """
 from __future__ import annotations
 
