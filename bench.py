@@ -1,20 +1,27 @@
 #!/usr/bin/env python3
 """Benchmark of the differentiable Projective Dynamics hot path.
 
-Workload: 32x32x64-cell hex beam (70,785 nodes, 212,355 DoFs), corotated +
-volume-preserving energies, per-element Young's modulus ~ lognormal(1e6, 0.2),
-x=0 face fixed, gravity, h = 0.01 s, 100 implicit-Euler steps; one bench step is
-the whole rollout forward (PD + L-BFGS) and backward (adjoint splitting iteration
-+ L-BFGS) with gradients w.r.t. the per-element stiffness and the initial velocity.
-Mixed precision: FP32 local steps and triangular solves, FP64 factor, vectors
-and convergence checks.
+Default workload (the largest single-GPU configuration): 64x64x128-cell hex
+cantilever (545,025 nodes, 1,635,075 DoFs), corotated energy E = 1e6 Pa,
+nu = 0.45, x=0 face fixed, gravity plus seeded surface tractions, h = 0.01 s;
+forward rollout (PD + L-BFGS, Alg. 1) with a state checkpoint every 25 steps and
+the backward pass (adjoint splitting iteration + L-BFGS, Alg. 2, with the states
+of each 25-step segment recomputed from its checkpoint, Sec. 4) to the gradients
+w.r.t. the traction field and the initial velocity.  Mixed precision: FP32 local
+steps and triangular solves, FP64 factor, vectors and convergence checks.
+
+One bench step is one 25-step checkpoint segment: --steps K times a rollout of
+T = 25 K simulation steps forward and backward (K = 20 is the configuration's
+500-step horizon), after a warm-up rollout of 25 W steps.  `value` = simulated
+fwd+bwd steps per second over the timed rollout.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--workload c5|c2] [--serve] [--probe ...]
 
-Prints one JSON line (rank 0).  value = forward+backward simulation steps per
-second over all ranks (each rank runs an independent replica: every global step is
-one sweep over one factor's elimination tree, so a rollout does not shard across
-GPUs and no collective is on the data path).
+Prints one JSON line (rank 0).  Under torchrun every rank runs an independent
+replica (every global step is one sweep over one factor's elimination tree, so a
+rollout does not shard across GPUs and no collective is on the data path); value
+= all ranks' simulation steps over the slowest rank's time.
 """
 from __future__ import annotations
 
@@ -32,33 +39,46 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 METRIC = "fwd+bwd sim steps/s at 1e-5 rel error vs FP64 oracle; % HBM roofline; p50/p99"
-WORKLOAD = "c2_beam_32x32x64_mixed_T100"
-TOL_FWD = 1e-7
-TOL_BWD = 1e-7
-# oracle local-step evaluations per simulation step used to scale the bounded
-# CPU sample (forward + backward iterations per step of this workload, measured
-# on the GPU path at the tolerances above)
-EVALS_PER_STEP_DEFAULT = 150
+SEG = 25   # simulation steps per checkpoint segment = one bench step (C5)
+# FP32 peak of the CUDA cores: 152 SMs x 128 FP32 lanes x 2 flop per FMA x 2.07 GHz
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+# Algorithmic flops per Gauss point of the forward local step with the corotated
+# energy (FMA = 2 flops): F - I from the 8 corners (72 FMA), the Green strain
+# H + H^T + H^T H (42), cyclic Jacobi on it (4 sweeps x 3 rotations x 40), sigma - 1
+# (12), F V (27 FMA), its Givens QR (3 x 30), the stress U diag(sigma - 1) V^T
+# (63), the corner forces (72 FMA) and the energy (6).
+LOCAL_FLOPS_PER_GP = 144 + 42 + 4 * 3 * 40 + 12 + 54 + 90 + 63 + 144 + 6
+WORKLOADS = {
+    "c5": dict(name="c5_beam_64x64x128_mixed_ckpt25", K=SEG, tol=1e-8, want=("fext", "v0"), iters_per_step=100.0),
+    "c2": dict(name="c2_beam_32x32x64_mixed", K=0, tol=1e-8, want=("w_corot", "w_vol", "v0"),
+               iters_per_step=150.0),
+}
 
 
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--steps", type=int, default=3,
+                    help="bench steps timed: 25-step checkpoint segments (c5) or 100-step rollouts (c2)")
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--T", type=int, default=100, help="simulation steps per rollout")
+    ap.add_argument("--workload", default="c5", choices=sorted(WORKLOADS))
+    ap.add_argument("--tol", type=float, default=None, help="PD / adjoint tolerance (default per workload)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 (4x4x8 cantilever) line")
     ap.add_argument("--serve", action="store_true",
                     help="serving workload instead: quadruped requests under Poisson arrivals")
     ap.add_argument("--serve-requests", type=int, default=24)
     ap.add_argument("--serve-slots", type=int, default=8)
+    ap.add_argument("--T", type=int, default=100, help="simulation steps per rollout (c2, --serve, --probe)")
     ap.add_argument("--probe", choices=["solve", "local", "hvp", "rollout", "quadruped"],
-                    help="profiling driver (no timing, no JSON): factorise the benchmark beam in mixed "
+                    help="profiling driver (no timing, no JSON): factorise the workload's beam in mixed "
                          "precision, then run --repeat solves / local steps / Hessian products, or one "
                          "rollout of --T steps forward and backward; 'quadruped' = one 16^3 quadruped "
                          "rollout of --T steps")
     ap.add_argument("--repeat", type=int, default=4)
+    ap.add_argument("--profile-events", action="store_true",
+                    help="probe rollout: time solves and local steps with CUDA events and print the stats")
     return ap.parse_args()
 
 
@@ -140,39 +160,43 @@ def solve_bytes(mesh, itemsize):
     return 2 * nnz * itemsize + nf3 * (8 + 8 + 2 * itemsize), nnz
 
 
-def oracle_sample(evals_per_step, budget_s=12.0):
-    """Bounded CPU sample of the FP64 oracle on the same workload: repeated
-    evaluations of the local step and of grad g (oracle.model) on the 32x32x64
-    beam, timed for about budget_s seconds.  Projected to fwd+bwd sim steps/s as
-    1 / (t_eval * evals_per_step).  The oracle's sparse factorisation and
-    triangular solves are not included, so the projection over-estimates the
-    oracle's speed."""
+def oracle_sample(workload, iters_per_step, budget_s=20.0):
+    """Bounded CPU sample of the FP64 oracle on the same workload.  The oracle's
+    one-time setup (its model and the SuperLU factor of L_A, like the GPU's
+    factorisation excluded from steps/s) is timed and reported separately; then
+    the oracle's own PD + L-BFGS forward iteration of step 1 (local step, grad g,
+    the A^-1 solve, the Armijo line search: oracle/pd_cpu.py) runs for about
+    budget_s seconds.  Projected to fwd+bwd sim steps/s as 1 / (t_iter *
+    iters_per_step) with the GPU path's measured forward + backward iterations
+    per step (the oracle's MINRES adjoint iteration is cheaper than a forward
+    iteration, so the projection under-estimates the oracle's backward speed)."""
     import numpy as np
+    from oracle import pd_cpu
     from oracle.model import Model
-    from workloads import beam_c2
-    sc = beam_c2(T=1)
-    model = Model(sc)
-    rng = np.random.default_rng(0)
-    x = sc.x0 + 1e-4 * rng.standard_normal(sc.x0.shape)
+    sc = _scene(workload, 1)
     t0 = time.perf_counter()
-    n = 0
-    while True:
-        loc = model.local(x)
-        model.grad_g(x, x, None, loc)
-        n += 1
-        if time.perf_counter() - t0 >= budget_s:
-            break
-    t_eval = (time.perf_counter() - t0) / n
+    model = Model(sc)
+    Afac = pd_cpu.ScalarA(model)
+    t_setup = time.perf_counter() - t0
+    it = {"n": 0}
+    t0 = time.perf_counter()
+
+    def stop(n):
+        it["n"] = n
+        return time.perf_counter() - t0 >= budget_s
+    pd_cpu.pd_lbfgs_step(model, Afac, sc.x0, sc.v0, sc.f_ext, None, None, 1e-12, 5, 100000, stop=stop)
+    t_iter = (time.perf_counter() - t0) / max(it["n"], 1)
     cores = os.cpu_count()
     return {
-        "value": 1.0 / (t_eval * evals_per_step),
+        "value": 1.0 / (t_iter * iters_per_step),
         "unit": "steps/s",
         "cores": cores,
         "kind": "oracle",
-        "sample": (f"{n} oracle FP64 local-step + grad g evaluations on the 32x32x64 beam "
-                   f"({t_eval:.2f} s each, numpy/LAPACK on {cores} host cores), projected with "
-                   f"{evals_per_step} evaluations per fwd+bwd sim step; oracle factorisation "
-                   f"and solves excluded"),
+        "sample": (f"{it['n']} FP64 oracle PD + L-BFGS iterations of step 1 of {sc.name} ({t_iter:.2f} s each: "
+                   f"local step, grad g, SuperLU A^-1 solve, Armijo line search; numpy/LAPACK on {cores} "
+                   f"host cores), projected with the GPU path's {iters_per_step:.1f} fwd+bwd iterations per "
+                   f"step; oracle setup (model + SuperLU factor of L_A) {t_setup:.1f} s, excluded"),
+        "setup_s": t_setup,
     }
 
 
@@ -180,19 +204,23 @@ def run_reference(args):
     world, rank, _ = dist_env()
     if rank != 0:
         return
+    wl = WORKLOADS[args.workload]
+    # iterations per step of the GPU path at this workload (measured; used to
+    # project the oracle's timed iterations to simulation steps)
+    ips = wl["iters_per_step"]
     res = None
     for _ in range(args.warmup):
-        oracle_sample(EVALS_PER_STEP_DEFAULT, budget_s=3.0)
+        oracle_sample(args.workload, ips, budget_s=2.0)
     vals = []
     for _ in range(args.steps):
-        res = oracle_sample(EVALS_PER_STEP_DEFAULT, budget_s=8.0)
+        res = oracle_sample(args.workload, ips, budget_s=8.0)
         vals.append(res["value"])
     value = statistics.median(vals)
     res["value"] = value
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "parallelism": "replicas"},
+            "config": {"workload": wl["name"], "parallelism": "replicas"},
             "cpu_baseline": res,
             "e2e": {"value": value, "unit": "steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
@@ -210,6 +238,83 @@ def whole_job_rate(elapsed_s, sim_steps_per_rank, world, device):
     return elapsed_s, world * sim_steps_per_rank / elapsed_s
 
 
+def _scene(wl, T):
+    from workloads import beam_c2, beam_c5
+    return beam_c5(T=T) if wl == "c5" else beam_c2(T=T)
+
+
+def _profile_key(wl):
+    return "c5_beam_64x64x128" if wl == "c5" else "c2_beam_32x32x64"
+
+
+def _traffic(wl):
+    """ncu DRAM bytes of one solve pair at this workload, from the committed
+    profile summary (profiles/solve_traffic.txt); None when not captured."""
+    path = os.path.join(ROOT, "profiles", "solve_traffic.txt")
+    if not os.path.exists(path):
+        return None, None
+    with open(path) as f:
+        d = json.load(f)
+    e = d.get(_profile_key(wl))
+    if not e:
+        return None, None
+    return e.get("bytes_per_solve"), e.get("source")
+
+
+def fp64_line(dev, steps=5):
+    """Plain FP64 method on the 4x4x8 cantilever (675 DoFs, 50 steps, tol 1e-9):
+    fwd+bwd sim steps/s with gradients w.r.t. E (through w_corot), nu and v0."""
+    import numpy as np
+    import torch
+    from paper_2101_05917_gb300 import api
+    from paper_2101_05917_gb300 import _native as N
+    from workloads import cantilever_c1
+    sc = cantilever_c1()
+    mesh = api.PDMesh.from_scene(sc, device=dev.index or 0)
+    wc, wv, _, _ = api.scene_weights(sc, dev)
+    mesh.factorize(wc, None, None, None, h=sc.h, gravity=tuple(sc.gravity), precision=N.PD_PREC_FP64)
+    tt = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device=dev)
+    x0, v0, lw, f = tt(sc.x0), tt(sc.v0), tt(sc.loss_w), tt(sc.f_ext)
+    opts = api.solver_opts(tol_fwd=sc.tol_fwd, tol_bwd=sc.tol_bwd, max_iter_fwd=5000, max_iter_bwd=5000)
+    lat = []
+
+    def one():
+        sm = np.zeros(sc.T)
+        o = api.solver_opts(tol_fwd=sc.tol_fwd, tol_bwd=sc.tol_bwd, max_iter_fwd=5000, max_iter_bwd=5000,
+                            step_ms=sm)
+        roll = mesh.forward(x0, v0, sc.T, f_ext=f, opts=o)
+        g = mesh.backward(roll, sc.T, lw, f_ext=f, opts=o, want=("w_corot", "v0"))
+        return roll, g, sm
+    one()
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    it = [0, 0]
+    for _ in range(steps):
+        roll, g, sm = one()
+        lat.append(sm)
+        it[0] += roll.stats["fwd_iters"]
+        it[1] += g["stats"]["bwd_iters"]
+    e1.record(stream)
+    torch.cuda.synchronize()
+    el = e0.elapsed_time(e1) / 1e3
+    # dL/dE and dL/dnu through w = E / (1 + nu) (the only energy of this configuration)
+    gw = g["w_corot"].cpu().numpy()
+    E = np.asarray(sc.youngs)
+    gE = gw / (1 + sc.poisson)
+    gnu = float(np.sum(gw * (-E / (1 + sc.poisson) ** 2)))
+    lat = np.concatenate(lat)
+    mesh.close()
+    return {"workload": "c1_cantilever_4x4x8_fp64_T50", "value": steps * sc.T / el, "unit": "steps/s",
+            "dtype": "f64", "rollouts": steps, "ms_per_rollout": 1e3 * el / steps, "tol": sc.tol_fwd,
+            "fwd_iters_per_step": it[0] / (steps * sc.T), "bwd_iters_per_step": it[1] / (steps * sc.T),
+            "step_latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99))},
+            "grad_norms": {"E": float(np.linalg.norm(gE)), "nu": abs(gnu),
+                           "v0": float(g["v0"].norm())},
+            "bound": "latency (675 DoFs: every launch is a few CTAs)"}
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -221,142 +326,176 @@ def run_ours(args):
     _build.build()
     from paper_2101_05917_gb300 import api
     from paper_2101_05917_gb300 import _native as N
-    from workloads import beam_c2
 
     torch.cuda.set_device(local)
     dev = torch.device(f"cuda:{local}")
-    T = args.T
-    sc = beam_c2(T=T)
+    wl = WORKLOADS[args.workload]
+    K = wl["K"]
+    tol = args.tol if args.tol is not None else wl["tol"]
+    seg = K if K > 0 else args.T             # simulation steps per bench step
+    T = seg * args.steps if K > 0 else args.T
+    sc = _scene(args.workload, T)
+    t0 = time.perf_counter()
     mesh = api.PDMesh.from_scene(sc, device=local)
+    t_mesh = time.perf_counter() - t0
     wc, wv, _, _ = api.scene_weights(sc, dev)
     tt = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device=dev)
-    x0, v0, lw = tt(sc.x0), tt(sc.v0), tt(sc.loss_w)
+    d = {"x0": tt(sc.x0), "v0": tt(sc.v0), "f": tt(sc.f_ext), "lw": tt(sc.loss_w)}
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     mesh.factorize(wc, wv, None, None, h=sc.h, gravity=tuple(sc.gravity), precision=N.PD_PREC_MIXED)
     torch.cuda.synchronize()
     t_factor = time.perf_counter() - t0
     stream = torch.cuda.current_stream()
-    want = ("w_corot", "w_vol", "v0")
+    want = wl["want"]
 
-    def rollout(profile, step_ms=None):
-        opts = api.solver_opts(tol_fwd=TOL_FWD, tol_bwd=TOL_BWD, profile=profile, step_ms=step_ms)
-        roll = mesh.forward(x0, v0, T, opts=opts)
-        g = mesh.backward(roll, T, lw, opts=opts, want=want)
+    def opts_for(profile=False, step_ms=None):
+        return api.solver_opts(tol_fwd=tol, tol_bwd=tol, max_iter_fwd=5000, max_iter_bwd=5000, checkpoint_every=K,
+                               profile=profile, step_ms=step_ms)
+
+    def rollout(Tr, inputs, profile=False, step_ms=None):
+        o = opts_for(profile, step_ms)
+        roll = mesh.forward(inputs["x0"], inputs["v0"], Tr, f_ext=inputs["f"], opts=o)
+        g = mesh.backward(roll, Tr, inputs["lw"], f_ext=inputs["f"], opts=o, want=want)
         return roll, g
 
-    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)   # 256 MB > L2
-    for _ in range(args.warmup):
-        rollout(False)
+    # warm-up: W bench steps (one rollout of W segments, or W rollouts)
+    if K > 0:
+        rollout(seg * args.warmup, d)
+    else:
+        for _ in range(args.warmup):
+            rollout(T, d)
     torch.cuda.synchronize()
     if world > 1:
         torch.distributed.barrier()
     clocks = ClockSampler(local)
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
-    flush.fill_(1.0)
+    flush = None
+    if K == 0:
+        flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)   # 256 MB > L2
+        flush.fill_(1.0)
     torch.cuda.synchronize()
     ev0.record(stream)
-    fstats, bstats, per_rollout, step_lat = [], [], [], []
-    for k in range(args.steps):
-        h0 = time.perf_counter()
+    fstats, bstats, lat = [], [], []
+    h0 = time.perf_counter()
+    rollouts = 1 if K > 0 else args.steps
+    for k in range(rollouts):
         sm = np.zeros(T)
-        roll, g = rollout(True, sm)
-        per_rollout.append(time.perf_counter() - h0)
-        step_lat.append(sm)
+        roll, g = rollout(T, d, step_ms=sm)
+        lat.append(sm)
         fstats.append(roll.stats)
         bstats.append(g["stats"])
-        flush.fill_(float(k))   # evict the factor panels between timed rollouts
+        if flush is not None:
+            flush.fill_(float(k))   # evict the factor panels between timed rollouts
     ev1.record(stream)
     torch.cuda.synchronize()
+    host_s = time.perf_counter() - h0
     if world > 1:
         torch.distributed.barrier()
     clk = clocks.stop()
-    elapsed, value = whole_job_rate(ev0.elapsed_time(ev1) / 1e3, args.steps * T, world, dev)
+    sim_steps = rollouts * T
+    elapsed, value = whole_job_rate(ev0.elapsed_time(ev1) / 1e3, sim_steps, world, dev)
+    launches = sum(s["kernel_launches"] for s in fstats + bstats)
+    lat = np.concatenate(lat)
+    fwd_it = sum(s["fwd_iters"] for s in fstats) / sim_steps
+    bwd_it = sum(s["bwd_iters"] for s in bstats) / sim_steps
+    fp64_checks = (sum(s["fwd_fp64_iters"] for s in fstats) + sum(s["bwd_fp64_iters"] for s in bstats)) / sim_steps
+    g_final = {k: float(g[k].norm()) for k in want}
 
-    # roofline of the dominant kernel pair (triangular solves), from the live events
-    solves = sum(s["solves"] for s in fstats + bstats)
-    solves_timed = sum(s["solves_timed"] for s in fstats + bstats)
-    solve_ms = sum(s["solve_ms"] for s in fstats + bstats)
-    local_ms = sum(s["local_ms"] for s in fstats)
-    locals_timed = sum(s["local_steps_timed"] for s in fstats)
+    # profiled pass after the timed region (CUDA events around every directly
+    # launched solve and forward local step; graphs replay the rest of each chunk)
+    prof_T = seg if K > 0 else min(T, 10)
+    rp, gp = rollout(prof_T, d, profile=True)
+    ps = [rp.stats, gp["stats"]]
+    solves_timed = sum(s["solves_timed"] for s in ps)
+    t_solve = sum(s["solve_ms"] for s in ps) / 1e3 / max(solves_timed, 1)
+    locals_timed = rp.stats["local_steps_timed"]
+    t_local = rp.stats["local_ms"] / 1e3 / max(locals_timed, 1)
     bytes_solve, nnzq = solve_bytes(mesh, 4)
-    t_solve = solve_ms / 1e3 / max(solves_timed, 1)
     peak, peak_kind = peaks()
     achieved = bytes_solve / t_solve / 1e9
-    traffic_path = os.path.join(ROOT, "profiles", "solve_traffic.txt")
-    traffic = None
-    if os.path.exists(traffic_path):
-        with open(traffic_path) as f:
-            traffic = json.load(f).get("bytes_per_solve")
-    launches = sum(s["kernel_launches"] for s in fstats + bstats)
-    lat = np.concatenate(step_lat)   # host wall time of each step, forward + adjoint
-    fwd_it = sum(s["fwd_iters"] for s in fstats) / (args.steps * T)
-    bwd_it = sum(s["bwd_iters"] for s in bstats) / (args.steps * T)
+    traffic, traffic_src = _traffic(args.workload)
+    gps = 8 * int(mesh.e)
+    local_tflops = LOCAL_FLOPS_PER_GP * gps / t_local / 1e12 if locals_timed else None
 
     # end to end through the public API with host buffers: H2D of the inputs,
     # factorisation (the weights are inputs), forward, backward, D2H of the gradients
+    T_e = seg * max(1, args.steps // 4) if K > 0 else T
     host = {k: torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64).pin_memory()
-            for k, a in (("x0", sc.x0), ("v0", sc.v0), ("lw", sc.loss_w),
-                         ("wc", wc.cpu().numpy()), ("wv", wv.cpu().numpy()))}
+            for k, a in (("x0", sc.x0), ("v0", sc.v0), ("f", sc.f_ext), ("lw", sc.loss_w),
+                         ("wc", wc.cpu().numpy()))}
     h2d = sum(t.numel() * 8 for t in host.values())
-    # the loss and copies below use torch kernels that load lazily on first use: load
-    # them outside the timed region
-    float((roll.x[-1] * lw).sum().cpu())
+    float((roll.x[-1] * d["lw"]).sum().cpu())   # lazily loaded torch kernels, outside the timed region
     torch.cuda.synchronize()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     hp = [time.perf_counter()]
-    d = {k: t.to(dev, non_blocking=True) for k, t in host.items()}
-    mesh.factorize(d["wc"], d["wv"], None, None, h=sc.h, gravity=tuple(sc.gravity), precision=N.PD_PREC_MIXED)
+    dd = {k: t.to(dev, non_blocking=True) for k, t in host.items()}
+    mesh.factorize(dd["wc"], None, None, None, h=sc.h, gravity=tuple(sc.gravity), precision=N.PD_PREC_MIXED)
     hp.append(time.perf_counter())
-    opts = api.solver_opts(tol_fwd=TOL_FWD, tol_bwd=TOL_BWD)
-    roll = mesh.forward(d["x0"], d["v0"], T, opts=opts)
+    o = opts_for()
+    re_ = mesh.forward(dd["x0"], dd["v0"], T_e, f_ext=dd["f"], opts=o)
     hp.append(time.perf_counter())
-    g = mesh.backward(roll, T, d["lw"], opts=opts, want=want)
+    ge = mesh.backward(re_, T_e, dd["lw"], f_ext=dd["f"], opts=o, want=want)
     hp.append(time.perf_counter())
-    loss = (roll.x[-1] * d["lw"]).sum()
-    out_host = [g["w_corot"].cpu(), g["w_vol"].cpu(), g["v0"].cpu(), loss.cpu()]
+    loss = (re_.x[-1] * dd["lw"]).sum()
+    out_host = [ge[k].cpu() for k in want] + [loss.cpu()]
     e1.record(stream)
     torch.cuda.synchronize()
     hp.append(time.perf_counter())
     phases = {k: 1e3 * (hp[i + 1] - hp[i]) for i, k in enumerate(("h2d_factorize", "forward", "backward", "d2h"))}
     d2h = sum(t.numel() * 8 for t in out_host)
-    e2e_value = world * T / (e0.elapsed_time(e1) / 1e3)
+    e2e_value = world * T_e / (e0.elapsed_time(e1) / 1e3)
 
+    fp64 = None
+    if rank == 0 and not args.no_fp64:
+        fp64 = fp64_line(dev)
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
-        cpu = oracle_sample(int(round(fwd_it + bwd_it)))
+        cpu = oracle_sample(args.workload, fwd_it + bwd_it)
 
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": 1e3 * elapsed / (args.steps * T),
+            "warmup": args.warmup, "ms_per_step": 1e3 * elapsed / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "mixed-f32-f64",
             "data": "synthetic",
-            "config": {"workload": WORKLOAD, "cells": int(mesh.e), "nodes": int(mesh.n),
-                       "dofs": 3 * int(mesh.n), "T": T, "tol_fwd": TOL_FWD, "tol_bwd": TOL_BWD,
-                       "lbfgs_m": 5, "fwd_iters_per_step": fwd_it, "bwd_iters_per_step": bwd_it,
-                       "factorize_s": t_factor, "factor_nnz": int(mesh.info["factor_nnz"]),
-                       "rollout_s": per_rollout,
-                       "l2": "256 MB buffer written between timed rollouts; FP32 solve panels "
-                             f"{nnzq * 4 / 1e6:.0f} MB stream through each solve",
+            "config": {"workload": wl["name"], "cells": int(mesh.e), "nodes": int(mesh.n),
+                       "dofs": 3 * int(mesh.n), "T": T, "sim_steps_per_bench_step": seg,
+                       "checkpoint_every": K, "ms_per_sim_step": 1e3 * elapsed / sim_steps,
+                       "tol_fwd": tol, "tol_bwd": tol, "lbfgs_m": 5,
+                       "fwd_iters_per_step": fwd_it, "bwd_iters_per_step": bwd_it,
+                       "fp64_checks_per_step": fp64_checks,
+                       "mesh_s": t_mesh, "factorize_s": t_factor, "factor_nnz": int(mesh.info["factor_nnz"]),
+                       "timed_host_s": host_s, "grad_norms": g_final,
+                       "l2": ("inputs larger than L2: the FP32 solve panels (%.0f MB) stream through every "
+                              "solve" % (nnzq * 4 / 1e6)) if K > 0 else
+                             "256 MB buffer written between timed rollouts",
                        "parallelism": "replicas"},
-            "roofline": {"bound": "hbm", "kernel": "triangular solve pair (fwd_tile + bwd_tile launches)",
+            "roofline": {"bound": "hbm", "kernel": "triangular solve pair (solve_persistent_kernel)",
                          "achieved": achieved, "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": traffic,
-                         "bytes_per_launch": bytes_solve, "avg_solve_us": 1e6 * t_solve, "solves": solves,
+                         "frac": achieved / peak, "traffic": traffic, "traffic_source": traffic_src,
+                         "bytes_per_launch": bytes_solve, "avg_solve_us": 1e6 * t_solve,
                          "solves_timed": solves_timed,
-                         "timing": "CUDA events on the launching stream around the directly launched "
-                                   "solve that ends every chunk of 4 iterations (the other 3 replay as a CUDA graph)"},
-            "local_step": {"avg_us": 1e3 * local_ms / max(locals_timed, 1), "launches_timed": locals_timed},
+                         "timing": "CUDA events on the launching stream around every directly launched solve "
+                                   "of a profiled %d-step rollout run after the timed region (the timed rollout "
+                                   "runs without events)" % prof_T},
+            "local_step": {"bound": "alu", "kernel": "element_kernel (forward, FP32)",
+                           "avg_us": 1e6 * t_local, "launches_timed": locals_timed,
+                           "flops_per_gauss_point": LOCAL_FLOPS_PER_GP, "gauss_points": gps,
+                           "achieved": local_tflops, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                           "frac": (local_tflops / FP32_PEAK_TFLOPS) if local_tflops else None},
             "step_latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
                                 "max": float(lat.max()), "steps": int(lat.size),
-                                "what": "host wall time of one simulation step, forward + adjoint"},
+                                "what": "host wall time of one simulation step: forward + recomputation + "
+                                        "adjoint"},
+            "fp64": fp64,
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": "steps/s", "h2d_bytes_per_step": h2d,
-                    "d2h_bytes_per_step": d2h, "includes": "H2D inputs, factorisation, forward, backward, D2H",
+                    "d2h_bytes_per_step": d2h, "T": T_e,
+                    "includes": "H2D inputs, factorisation, forward, backward, D2H of the gradients and loss",
                     "host_phases_ms": phases},
             "gpu_launches": launches,
             "clocks": clk,
@@ -433,10 +572,10 @@ def run_probe(args):
     _build.build()
     from paper_2101_05917_gb300 import api
     from paper_2101_05917_gb300 import _native as N
-    from workloads import beam_c2, quadruped
+    from workloads import quadruped
     dev = torch.device("cuda:0")
     tt = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device=dev)
-    sc = quadruped(16, T=args.T) if args.probe == "quadruped" else beam_c2(T=args.T)
+    sc = quadruped(16, T=args.T) if args.probe == "quadruped" else _scene(args.workload, args.T)
     mesh = api.PDMesh.from_scene(sc)
     wc, wv, wm, fib = api.scene_weights(sc, dev)
     mesh.factorize(wc, wv, wm, fib, h=sc.h, gravity=tuple(sc.gravity), k_contact=sc.k_contact,
@@ -453,9 +592,10 @@ def run_probe(args):
         for _ in range(args.repeat):
             mesh.hessian_vector(x, v, precision=N.PD_PREC_MIXED)
     else:
-        opts = api.solver_opts(tol_fwd=TOL_FWD if args.probe == "rollout" else sc.tol_fwd,
-                               tol_bwd=TOL_BWD if args.probe == "rollout" else sc.tol_bwd, max_iter_fwd=3000,
-                               max_iter_bwd=3000)
+        tol = (args.tol if args.tol is not None else WORKLOADS[args.workload]["tol"]) \
+            if args.probe == "rollout" else sc.tol_fwd
+        opts = api.solver_opts(tol_fwd=tol, tol_bwd=tol, max_iter_fwd=3000, max_iter_bwd=3000,
+                               profile=args.profile_events)
         act = tt(sc.act[:args.T]) if sc.act is not None else None
         roll = mesh.forward(x, tt(sc.v0), args.T, f_ext=tt(sc.f_ext), act=act, mu=sc.mu, opts=opts)
         g = mesh.backward(roll, args.T, tt(sc.loss_w), f_ext=tt(sc.f_ext), act=act, mu=sc.mu, opts=opts)

@@ -47,9 +47,12 @@ typedef enum {
   PD_ERR_NOT_CONVERGED = 4, /* iteration cap reached before the tolerance */
   PD_ERR_INVERTED = 5,      /* an element with det F <= 0 was seen */
   PD_ERR_NAN = 6,           /* non-finite value in a residual */
-  PD_ERR_TIMEOUT = 7,       /* serving: result not ready yet */
+  PD_ERR_TIMEOUT = 7,       /* serving: result not ready yet; solves: a bounded
+                               device-side wait (about 1 s) gave up */
   PD_ERR_CUDA = 8,          /* CUDA runtime error */
-  PD_ERR_NO_DEVICE = 9      /* mesh created without a device */
+  PD_ERR_NO_DEVICE = 9,     /* mesh created without a device */
+  PD_ERR_INTERNAL = 10      /* an internal descriptor failed a device-side check
+                               (a library defect, not an input error) */
 } pd_status;
 
 enum { PD_PREC_FP64 = 0, PD_PREC_MIXED = 1 };
@@ -183,9 +186,9 @@ typedef struct {
                                    a checkpointed backward recomputes them identically. */
   double* step_ms;              /* optional host array of T entries: pd_forward stores the
                                    host wall time of each step [ms], pd_backward adds the
-                                   time of the step's adjoint (so after both calls entry t
-                                   holds the fwd+bwd latency of step t; the recomputation of
-                                   checkpointed segments is not included); NULL = none */
+                                   time of the step's adjoint and, with checkpointing, of its
+                                   recomputation (so after both calls entry t holds the
+                                   fwd+bwd latency of step t); NULL = none */
 } pd_solver_opts;
 
 typedef struct {
@@ -226,15 +229,18 @@ pd_status pd_forward(pd_mesh m, const double* x0, const double* v0, const double
 /* Backward rollout (Sec. 4, Alg. 2 with L-BFGS; Eqns 10-12 per step).
  * x_traj, v_traj, f_ext, act, mu, T: exactly as given to / produced by pd_forward
  * (with checkpointing the missing states are recomputed segment by segment).
- * dL_dx, dL_dv: direct loss gradients, (T+1, n, 3) when loss_all_steps != 0,
- * else (n, 3) for the final state only; dL_dv may be NULL.
+ * dL_dx, dL_dv: direct loss gradients of loss_states states: loss_states = 1
+ * (or 0) means (n, 3) for the final state x_T / v_T only; loss_states = T+1 means
+ * (T+1, n, 3), one block per state t = 0..T (with checkpointing as well: a loss
+ * on the checkpointed states only puts zeros in the other blocks).  Any other
+ * value returns PD_ERR_INVALID_ARG before anything is read.  dL_dv may be NULL.
  * Outputs (each may be NULL): g_x0, g_v0 (n,3); g_fext (n,3) summed over steps;
  * g_w_corot, g_w_vol, g_w_muscle (e) = dL/dw per unit volume; g_act (T, e);
  * g_mu (1).  Status as pd_forward (PD_ERR_NOT_CONVERGED for an adjoint solve that
  * reached its cap, PD_ERR_NAN for a non-finite residual in any step). */
 pd_status pd_backward(pd_mesh m, const double* x_traj, const double* v_traj,
                       const double* f_ext, const double* act, double mu, int32_t T,
-                      const double* dL_dx, const double* dL_dv, int32_t loss_all_steps,
+                      const double* dL_dx, const double* dL_dv, int32_t loss_states,
                       const pd_solver_opts* opts, double* g_x0, double* g_v0,
                       double* g_fext, double* g_w_corot, double* g_w_vol,
                       double* g_w_muscle, double* g_act, double* g_mu,
@@ -254,7 +260,15 @@ pd_status pd_hessian_vector(pd_mesh m, const double* x, const double* act, const
                             int32_t precision, double* Hv, void* stream);
 
 /* Global step (Eqn 19): x = A^-1 b on the free DoFs (b, x: (n,3); Dirichlet
- * rows of x are set to zero) with the prefactorised supernodal factor. */
+ * rows of x are set to zero) with the prefactorised supernodal factor.
+ * Synchronises the stream and reads the solve's device flags: PD_ERR_TIMEOUT
+ * when a bounded dependency or copy wait gave up (the results are then not
+ * valid; the mesh stays usable), PD_ERR_INTERNAL for a rejected tile
+ * descriptor.  The environment variable PD_SOLVE_SPIN_LIMIT (polls, read by
+ * pd_create_mesh) shortens the dependency waits' bound; PD_TEST_SOLVE_STALLS=k
+ * (test support, read by pd_create_mesh) makes the first k solves of the mesh
+ * wait for one block more than a forward dependency delivers, so that wait
+ * runs out. */
 pd_status pd_solve_A(pd_mesh m, const double* b, double* x, int32_t precision, void* stream);
 
 /* Complementarity contact (Sec. 5.2): the global step with the contact set C held
@@ -291,9 +305,9 @@ pd_status pd_contact_step_set(pd_mesh m, int32_t t, int32_t* nodes_host, uint8_t
                               int64_t* count);
 
 /* Local step that allocates no device memory (the paper has no counterpart).
- * For callers that cannot call cudaMalloc -- e.g. while a CUDA graph is being
- * captured, under a device-memory budget fixed in advance, or behind an allocator
- * the library cannot reach -- this variant of pd_local_step takes every array
+ * For callers that cannot call cudaMalloc -- e.g. code under a device-memory
+ * budget fixed in advance, or behind an allocator the library cannot reach --
+ * this variant of pd_local_step takes every array
  * from the caller and keeps its scratch (corner forces, partial sums, a status
  * word) in one fixed-size device array owned by the library; every GPU that
  * loads the library holds that array (6.3 MB) until the process exits.
@@ -309,14 +323,23 @@ pd_status pd_contact_step_set(pd_mesh m, int32_t t, int32_t* nodes_host, uint8_t
  * looks up the scratch address there: make it before any stream capture.
  * Calls share the scratch: calls that overlap on the GPU race (keep them on one
  * stream).  The scratch keeps the last call's contents; each call clears what
- * must start at zero. */
+ * must start at zero.
+ * status_flags (device, one int32, may be NULL): set in stream order, once the
+ * call's kernels have run, to the OR of PD_LOCAL_FLAG_INVERTED (an element with
+ * det F <= 0) and PD_LOCAL_FLAG_NAN (a non-finite gradient entry); 0 when
+ * neither happened.  The returned pd_status reports argument and launch errors
+ * only: it cannot wait for the kernels.  With status_flags NULL these two
+ * conditions are not reported. */
 #define PD_NOALLOC_MAX_CELLS 32768
+#define PD_LOCAL_FLAG_INVERTED 2
+#define PD_LOCAL_FLAG_NAN 4
 pd_status pd_local_step_noalloc(int64_t n_nodes, int64_t n_elems, const int32_t* elems,
                                 const int32_t* inc_ptr, const int32_t* inc, double dx,
                                 const double* x, const double* act, const double* w_corot,
                                 const double* w_vol, const double* w_muscle, const double* fiber,
                                 const uint8_t* contact, double k_contact, int32_t precision,
-                                double* grad_E, double* energy, void* stream);
+                                double* grad_E, double* energy, int32_t* status_flags,
+                                void* stream);
 
 /* Serving: rollout-plus-gradient requests on one GPU (no counterpart in the
  * paper, whose method this wraps: each request is one forward rollout of T

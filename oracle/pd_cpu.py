@@ -40,7 +40,10 @@ class ScalarA:
 
 
 def pd_lbfgs_step(model: Model, Afac: ScalarA, x, v, f_ext, act=None, mu=None, tol=1e-12,
-                  history=5, max_iter=2000):
+                  history=5, max_iter=2000, stop=None):
+    """One implicit-Euler step by PD + L-BFGS from the predictor; `stop(iters)`,
+    when given, is called after every iteration and ends the step early when it
+    returns True (used to time a bounded number of iterations)."""
     free = model.free_nodes
     y = model.predictor(x, v, f_ext, mu)
     xn = np.array(y, copy=True)
@@ -88,6 +91,8 @@ def pd_lbfgs_step(model: Model, Afac: ScalarA, x, v, f_ext, act=None, mu=None, t
                 Y.pop(0)
         xn, gr, gval = xt, grt, gt
         it += 1
+        if stop is not None and stop(it):
+            break
     vn = (xn - x) / model.h
     return xn, vn, {"iters": it, "residual": float(np.linalg.norm(gr)), "ref": float(ref)}
 

@@ -21,9 +21,11 @@ PD_ERR_NAN = 6
 PD_ERR_TIMEOUT = 7
 PD_ERR_CUDA = 8
 PD_ERR_NO_DEVICE = 9
+PD_ERR_INTERNAL = 10
 STATUS_NAMES = {0: "PD_OK", 1: "PD_ERR_INVALID_ARG", 2: "PD_ERR_OOM", 3: "PD_ERR_NOT_SPD",
                 4: "PD_ERR_NOT_CONVERGED", 5: "PD_ERR_INVERTED", 6: "PD_ERR_NAN",
-                7: "PD_ERR_TIMEOUT", 8: "PD_ERR_CUDA", 9: "PD_ERR_NO_DEVICE"}
+                7: "PD_ERR_TIMEOUT", 8: "PD_ERR_CUDA", 9: "PD_ERR_NO_DEVICE",
+                10: "PD_ERR_INTERNAL"}
 
 PD_PREC_FP64 = 0
 PD_PREC_MIXED = 1
@@ -146,7 +148,7 @@ def lib() -> ctypes.CDLL:
     L.pd_solve_A.argtypes = [vp, vp, vp, ctypes.c_int32, vp]
     L.pd_solve_A.restype = st
     L.pd_local_step_noalloc.argtypes = [ctypes.c_int64, ctypes.c_int64, vp, vp, vp, ctypes.c_double, vp, vp, vp,
-                                        vp, vp, vp, vp, ctypes.c_double, ctypes.c_int32, vp, vp, vp]
+                                        vp, vp, vp, vp, ctypes.c_double, ctypes.c_int32, vp, vp, vp, vp]
     L.pd_local_step_noalloc.restype = st
     L.pd_serve_create.argtypes = [ctypes.c_int32, ctypes.c_size_t, ctypes.c_int32, ctypes.POINTER(vp)]
     L.pd_serve_create.restype = st

@@ -170,6 +170,18 @@ class PDMesh:
         opts = opts or solver_opts()
         dev = roll.x.device
         out = {}
+        # the library reads loss_states blocks of (n, 3): check the caller's shapes here
+        states = T + 1 if loss_all_steps else 1
+        want_shape = (T + 1, self.n, 3) if loss_all_steps else (self.n, 3)
+        for name, g in (("dL_dx", dL_dx), ("dL_dv", dL_dv)):
+            if g is not None and tuple(g.shape) != want_shape:
+                raise ValueError(f"{name}: expected shape {want_shape} (loss_all_steps={bool(loss_all_steps)}), "
+                                 f"got {tuple(g.shape)}")
+        K = opts.checkpoint_every
+        S = T + 1 if K <= 0 else T // K + 1
+        if tuple(roll.x.shape) != (S, self.n, 3) or tuple(roll.v.shape) != (S, self.n, 3):
+            raise ValueError(f"rollout states: expected shape {(S, self.n, 3)} for checkpoint_every={K}, "
+                             f"got {tuple(roll.x.shape)}")
 
         def alloc(name, shape):
             if name in want:
@@ -186,7 +198,7 @@ class PDMesh:
         gmu = alloc("mu", (1,))
         st = N.Stats()
         status = N.lib().pd_backward(self.handle, _ptr(roll.x), _ptr(roll.v), _ptr(f_ext), _ptr(act), mu, T,
-                                     _ptr(dL_dx), _ptr(dL_dv), 1 if loss_all_steps else 0, ctypes.byref(opts),
+                                     _ptr(dL_dx), _ptr(dL_dv), states, ctypes.byref(opts),
                                      _ptr(gx0), _ptr(gv0), _ptr(gf), _ptr(gwc), _ptr(gwv), _ptr(gwm), _ptr(ga),
                                      _ptr(gmu), ctypes.byref(st), _stream(stream))
         N.check(status, "pd_backward", allow=(N.PD_ERR_NOT_CONVERGED,) if allow_not_converged else ())

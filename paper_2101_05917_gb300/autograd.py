@@ -1,7 +1,8 @@
 """PyTorch autograd over the differentiable PD rollout.
 
 `Simulator.rollout(x0, v0, T, ...)` returns the trajectories (x_t, v_t),
-t = 0..T, as tensors that carry gradients to x0, v0, f_ext, the actuation, the
+t = 0..T (with opts checkpoint_every = K > 0: the checkpointed states t = 0, K,
+2K, ..., T; the others are recomputed in the backward pass), as tensors that carry gradients to x0, v0, f_ext, the actuation, the
 material weights (w_corot, w_vol, w_muscle) and the friction coefficient mu.  The
 forward pass is pd_forward (Alg. 1 with L-BFGS); the backward pass is one
 pd_backward call with the loss gradients of every state (Sec. 4: the adjoint
@@ -54,7 +55,8 @@ class Simulator:
 
     def rollout(self, x0, v0, T: int, f_ext=None, act=None, w_corot=None, w_vol=None, w_muscle=None,
                 fiber=None, mu=None):
-        """(x, v): (T+1, n, 3) each.  mu: Python float or 0-dim tensor."""
+        """(x, v): (S, n, 3) each, S = T+1, or T/K+1 checkpointed states with opts
+        checkpoint_every = K > 0.  mu: Python float or 0-dim tensor."""
         if mu is None:
             mu = 0.0
         mu_t = mu if torch.is_tensor(mu) else torch.tensor(float(mu), dtype=torch.float64, device=x0.device)
@@ -63,6 +65,16 @@ class Simulator:
 
 def _c(t):
     return None if t is None else t.detach().contiguous()
+
+
+def _every_state(g, T, K):
+    """(T+1, n, 3) loss gradient from the gradient of the returned states, which
+    are every state (K <= 0) or the checkpoints 0, K, 2K, ... (K > 0)."""
+    if K <= 0:
+        return g.contiguous()
+    full = g.new_zeros((T + 1,) + tuple(g.shape[1:]))
+    full[::K] = g
+    return full
 
 
 class _Rollout(torch.autograd.Function):
@@ -91,8 +103,11 @@ class _Rollout(torch.autograd.Function):
         sim.ensure_factor(wc, wv, wm, fib)
         if gx is None:
             gx = torch.zeros_like(xs)
-        gx = gx.contiguous()
-        gv = None if gv is None else gv.contiguous()
+        # with checkpointing the forward output holds states 0, K, 2K, ... only: their
+        # gradients go to those steps of the (T+1)-state loss gradient, zeros elsewhere
+        K = int(sim.opts.get("checkpoint_every", 0) or 0)
+        gx = _every_state(gx, T, K)
+        gv = None if gv is None else _every_state(gv, T, K)
         need = ctx.needs_input_grad
         names = [(3, "x0"), (4, "v0"), (5, "fext"), (6, "act"), (7, "w_corot"), (8, "w_vol"), (9, "w_muscle"),
                  (10, "mu")]

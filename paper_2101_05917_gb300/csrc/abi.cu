@@ -5,6 +5,7 @@
 #include <algorithm>
 #include <chrono>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 #include <string>
@@ -924,6 +925,20 @@ pd_status backward_step(Ctx& c, const double* xnext, const double* xt_, const do
   return PD_OK;
 }
 
+// status of the solve's device flags: a rejected tile descriptor is an internal
+// inconsistency, a bounded wait that gave up a timeout
+pd_status solve_flags_status(const char* who, int flags) {
+  if (flags & DEV_ERR_LAYOUT) {
+    set_error(std::string(who) + ": a solve tile descriptor failed its size / alignment check");
+    return PD_ERR_INTERNAL;
+  }
+  if (flags & DEV_ERR_TIMEOUT) {
+    set_error(std::string(who) + ": a bounded device-side wait in the solve gave up");
+    return PD_ERR_TIMEOUT;
+  }
+  return PD_OK;
+}
+
 pd_status check_mesh(pd_mesh m, bool need_factor) {
   if (!m) {
     set_error("null mesh");
@@ -1039,6 +1054,17 @@ pd_status pd_create_mesh(const pd_mesh_desc* desc, pd_mesh* out) {
       I.solve_grid = sms * solve_persistent_occupancy();
       I.sms = std::max(1, sms);
     }
+    // bounded-wait settings and the test hook that makes one wait run out
+    if (const char* ev = std::getenv("PD_SOLVE_SPIN_LIMIT")) {
+      const long long v = std::atoll(ev);
+      if (v > 0) I.solve_spin_limit = v;
+    }
+    if (const char* ev = std::getenv("PD_TEST_SOLVE_STALLS")) I.test_stall_solves = std::max(0, std::atoi(ev));
+    for (int64_t k = (int64_t)S.fwd.size() - 1; k >= 0; --k)
+      if (S.all[k].ndep > 0) {   // the last forward tile that waits for children
+        I.stall_tile = k;
+        break;
+      }
     if ((e = dalloc(&I, (char**)&I.ws.solve_partial, solve_partial_bytes(S))) != cudaSuccess) return fail(e);
   }
   I.flevels.assign(h.nlev, FactorLevel{});
@@ -1286,10 +1312,7 @@ pd_status pd_forward(pd_mesh mesh, const double* x0, const double* v0, const dou
   check_flags(c, stats);
   finish_stats(c, stats);
   if (stats) stats->fwd_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
-  if (c.dev_flags & DEV_ERR_TIMEOUT) {
-    set_error("pd_forward: a device-side wait in the solve timed out");
-    return PD_ERR_TIMEOUT;
-  }
+  if (c.dev_flags & (DEV_ERR_TIMEOUT | DEV_ERR_LAYOUT)) return solve_flags_status("pd_forward", c.dev_flags);
   // a step whose residual was non-finite stops there and the later steps restart
   // from stale values: the call reports it even when the last step converged
   if (any_nan || (w.st_host->status & DEV_ERR_NAN)) {
@@ -1305,16 +1328,22 @@ pd_status pd_forward(pd_mesh mesh, const double* x0, const double* v0, const dou
 
 pd_status pd_backward(pd_mesh mesh, const double* x_traj, const double* v_traj, const double* f_ext,
                       const double* act, double mu, int32_t T, const double* dL_dx, const double* dL_dv,
-                      int32_t loss_all_steps, const pd_solver_opts* opts, double* g_x0, double* g_v0,
+                      int32_t loss_states, const pd_solver_opts* opts, double* g_x0, double* g_v0,
                       double* g_fext, double* g_w_corot, double* g_w_vol, double* g_w_muscle, double* g_act,
                       double* g_mu, pd_stats* stats, void* stream) {
   const Range range("pd_backward");
+  if (loss_states != 0 && loss_states != 1 && loss_states != T + 1) {
+    set_error("pd_backward: loss_states must be 1 (final state) or T+1 (every state), got " +
+              std::to_string(loss_states));
+    return PD_ERR_INVALID_ARG;
+  }
   pd_status ck = check_mesh(mesh, true);
   if (ck != PD_OK) return ck;
   if (!x_traj || !v_traj || !dL_dx || T < 0) {
     set_error("pd_backward: x_traj, v_traj and dL_dx are required");
     return PD_ERR_INVALID_ARG;
   }
+  const bool loss_all_steps = loss_states == T + 1 && T + 1 != 1;
   const pd_solver_opts o = fill_opts(opts);
   const int K = o.checkpoint_every;
   if (K > 0 && T % K != 0) {
@@ -1389,7 +1418,10 @@ pd_status pd_backward(pd_mesh mesh, const double* x_traj, const double* v_traj, 
         StepInfo info;
         const double* act_t = act ? act + (int64_t)t * e : nullptr;
         const Range step_range("recompute step", t);
+        const auto ts = std::chrono::steady_clock::now();
         pd_status er = forward_step(c, act_t, fext_int, mu, nullptr, nullptr, info, guess_f, t);
+        if (o.step_ms)
+          o.step_ms[t] += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - ts).count();
         if (er != PD_OK) return er;
         copy_kernel<<<grid_for(3 * n), 256, 0, s>>>(3 * n, w.xprev, seg + (int64_t)(t + 1 - ta) * 6 * n);
         copy_kernel<<<grid_for(3 * n), 256, 0, s>>>(3 * n, w.vprev, seg + (int64_t)(t + 1 - ta) * 6 * n + 3 * n);
@@ -1431,10 +1463,7 @@ pd_status pd_backward(pd_mesh mesh, const double* x_traj, const double* v_traj, 
   check_flags(c, stats);
   finish_stats(c, stats);
   if (stats) stats->bwd_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
-  if (c.dev_flags & DEV_ERR_TIMEOUT) {
-    set_error("pd_backward: a device-side wait in the solve timed out");
-    return PD_ERR_TIMEOUT;
-  }
+  if (c.dev_flags & (DEV_ERR_TIMEOUT | DEV_ERR_LAYOUT)) return solve_flags_status("pd_backward", c.dev_flags);
   if (any_nan || (w.st_host->status & DEV_ERR_NAN)) {
     set_error("pd_backward: non-finite residual");
     return PD_ERR_NAN;
@@ -1522,12 +1551,16 @@ pd_status pd_solve_A(pd_mesh mesh, const double* b, double* x, int32_t precision
   cudaStream_t s = (cudaStream_t)stream;
   Workspace& w = m->ws;
   const int64_t n = m->h.n;
+  PD_CUDA_TRY(cudaMemsetAsync(w.flags, 0, sizeof(int), s));
   kept_to_internal_kernel<<<grid_for(n), 256, 0, s>>>(n, m->kept_of_internal, b, w.iov);
   PD_CUDA_TRY(reset_solve_counters(m, s));
   PD_CUDA_TRY(solve_A(m, nullptr, w.iov, w.iox, precision, s));
   internal_to_kept_kernel<<<grid_for(n), 256, 0, s>>>(n, m->h.nf, m->kept_of_internal, w.iox, x);
   PD_CUDA_TRY(cudaGetLastError());
-  return PD_OK;
+  int flags = 0;
+  PD_CUDA_TRY(cudaMemcpyAsync(&flags, w.flags, sizeof(int), cudaMemcpyDeviceToHost, s));
+  PD_CUDA_TRY(cudaStreamSynchronize(s));
+  return solve_flags_status("pd_solve_A", flags);
 }
 
 }  // extern "C"

@@ -16,7 +16,7 @@ namespace pd {
 
 namespace {
 
-constexpr int kElemThreads = 256;   // 8 warps = 32 cells per block
+constexpr int kElemThreads = kElemBlockThreads;   // 8 warps = 32 cells per block
 constexpr int kGatherThreads = 256;
 
 __device__ __forceinline__ int cbit(int a, int d) { return (a >> (2 - d)) & 1; }
@@ -545,7 +545,7 @@ cudaError_t launch_element_forces_raw(int64_t ne, const int32_t* elems, const do
   p.out = elembuf;
   p.energy = energy_partials;
   p.flags = flags;
-  const int nb = (int)((ne * 8 + kElemThreads - 1) / kElemThreads);
+  const int nb = (int)raw_element_blocks(ne);
   if (precision == PD_PREC_MIXED)
     element_kernel<float, MODE_FORCE><<<nb, kElemThreads, 0, s>>>(p);
   else

@@ -74,6 +74,8 @@ struct SolveParams {
   const int32_t *nfb, *nbb;     // per supernode: forward / backward output blocks
   const int64_t *child_ptr, *child_list, *parent;
   int* err;
+  long long spin_limit;         // polls of a dependency wait before it gives up
+  int64_t stall_tile;           // test support: this tile's first wait target is raised by one (-1: none)
   void* partial;                // per tile partial sums (T)
   const void* Q;
   const float* Qs;              // FP32: tiles stored contiguously (SolveTile::soff)
@@ -98,10 +100,10 @@ __device__ __forceinline__ SolveTile load_tile(const SolveTile* t, int64_t i) {
 // their forward outputs, a backward tile for its parent's backward outputs (the
 // root for its own forward outputs).  Every awaited tile has an earlier ticket
 // and is held by a running CTA, so the waits end; they are also bounded (error
-// flag DEV_ERR_TIMEOUT).  Counters only grow: a solve consumes ntiles + grid
+// flag DEV_ERR_TIMEOUT after SolveParams::spin_limit polls, about a second by
+// default).  Counters only grow: a solve consumes ntiles + grid
 // tickets (every CTA draws one ticket past the end), so ticket t belongs to
 // solve t / (ntiles + grid).
-constexpr long long kSpinLimit = 1ll << 20;   // about a second of polling
 
 // Message passing between CTAs: a producer's tile writes, then (after a CTA
 // barrier) one thread's release reduction on a counter; a consumer's thread polls
@@ -124,10 +126,11 @@ __device__ __forceinline__ unsigned long long add_acq_rel(unsigned long long* p)
   return old;
 }
 
-__device__ __forceinline__ bool wait_count(const unsigned long long* c, unsigned long long target, int* err) {
+__device__ __forceinline__ bool wait_count(const unsigned long long* c, unsigned long long target, int* err,
+                                           long long limit) {
   long long it = 0;
   while (load_acquire(c) < target) {
-    if (++it > kSpinLimit) {
+    if (++it > limit) {
       atomicOr(err, DEV_ERR_TIMEOUT);
       return false;
     }
@@ -204,7 +207,7 @@ __device__ __forceinline__ void stream_issue(const SolveParams& p, const SolveTi
   const uint32_t dst = smem_u32(sc.tile), bar = smem_u32(sc.mbar);
   if (bytes == 0u || bytes > (uint32_t)kStreamBytes || (bytes & 15u) || (dst & 15u) ||
       (reinterpret_cast<uintptr_t>(src) & 15u)) {
-    atomicOr(p.err, DEV_ERR_TIMEOUT);
+    atomicOr(p.err, DEV_ERR_LAYOUT);   // nothing issued: the tile skips its products
     *sc.state = 1;
     return;
   }
@@ -323,11 +326,13 @@ __device__ void fwd_tile_body(const SolveParams& p, const SolveTile& tl, int64_t
     // the children's forward outputs (inline in the descriptor; more from the tree)
     const int nd = tl.ndep;
     for (int k = 0; k < nd && k < kTileDeps; ++k)
-      wait_count(p.fdone + tl.dep[k], (epoch + 1) * (unsigned long long)tl.dep_blocks[k], p.err);
+      wait_count(p.fdone + tl.dep[k],
+                 (epoch + 1) * (unsigned long long)tl.dep_blocks[k] + (k == 0 && tid_g == p.stall_tile ? 1 : 0),
+                 p.err, p.spin_limit);
     if (nd > kTileDeps) {
       for (int64_t ci = __ldg(p.child_ptr + tl.s) + kTileDeps; ci < __ldg(p.child_ptr + tl.s + 1); ++ci) {
         const int64_t c = __ldg(p.child_list + ci);
-        wait_count(p.fdone + c, (epoch + 1) * (unsigned long long)__ldg(p.nfb + c), p.err);
+        wait_count(p.fdone + c, (epoch + 1) * (unsigned long long)__ldg(p.nfb + c), p.err, p.spin_limit);
       }
     }
   }
@@ -360,7 +365,8 @@ __device__ void fwd_tile_body(const SolveParams& p, const SolveTile& tl, int64_t
     stream_wait(p, stc);
     const int kmax = tl.sld;
     const int rv = (int)min((int64_t)R, nr - row0);
-    if (rl < rv) {
+    // products only from a completed copy (a rejected or timed-out copy leaves zeros)
+    if (rl < rv && *stc.state == 0) {
       const float* qs = stc.tile + g * kmax * rv + rl;
 #pragma unroll 8
       for (int k = 0; k < kmax; ++k) {
@@ -483,8 +489,8 @@ __device__ void bwd_tile_body(const SolveParams& p, const SolveTile& tl, int64_t
   if (threadIdx.x == 0) {
     // the parent's backward outputs; the root waits for its own forward outputs
     const int32_t d = tl.dep[0];
-    if (d >= 0) wait_count(p.bdone + d, (epoch + 1) * (unsigned long long)tl.dep_blocks[0], p.err);
-    else wait_count(p.fdone + (-d - 1), (epoch + 1) * (unsigned long long)tl.dep_blocks[0], p.err);
+    if (d >= 0) wait_count(p.bdone + d, (epoch + 1) * (unsigned long long)tl.dep_blocks[0], p.err, p.spin_limit);
+    else wait_count(p.fdone + (-d - 1), (epoch + 1) * (unsigned long long)tl.dep_blocks[0], p.err, p.spin_limit);
   }
   __syncthreads();
   // v = [u_s; -x(below rows)] on the tile's rows, zero past the panel
@@ -517,7 +523,8 @@ __device__ void bwd_tile_body(const SolveParams& p, const SolveTile& tl, int64_t
     // FP64 path.
     stream_wait(p, stc);
     const int rs = (int)rn;
-    const int bcv = (int)min((int64_t)BC, nc - col0);
+    // products only from a completed copy (a rejected or timed-out copy leaves zeros)
+    const int bcv = *stc.state == 0 ? (int)min((int64_t)BC, nc - col0) : 0;
     T qq[CW][RL];
 #pragma unroll
     for (int c = 0; c < CW; ++c)
@@ -637,10 +644,13 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 2 : 1) solve_persis
     }
     __syncthreads();   // shared memory of this tile is free; the drawn ticket is visible
     if (sizeof(T) == 4 && sstate == 2) {
-      // a copy wait gave up (the copy may still be in flight): wait once more,
-      // bounded, and leave; every other issued copy completed inside its tile
+      // A copy wait gave up, so the copy may still be writing this CTA's shared
+      // memory.  Every issued copy reads a source range checked in stream_issue
+      // (16-byte aligned, inside the streamed panels), so it completes; wait for it
+      // once more, bounded like every other wait, before the CTA retires.  Every
+      // other issued copy completed inside its tile.
       const unsigned long long t0 = global_ns();
-      while (!mbar_try_wait(&mbar, stc.phase) && global_ns() - t0 < 1000000000ull) {
+      while (!mbar_try_wait(&mbar, stc.phase) && global_ns() - t0 < 2000000000ull) {
       }
       return;
     }
@@ -893,6 +903,12 @@ cudaError_t solve_A(const MeshImpl* m, const IterState* gate, const double* b, d
   p.child_list = m->child_list;
   p.parent = m->parent;
   p.err = m->ws.flags;
+  p.spin_limit = m->solve_spin_limit;
+  p.stall_tile = -1;
+  if (m->test_stall_solves > 0 && m->stall_tile >= 0) {
+    p.stall_tile = m->stall_tile;
+    --m->test_stall_solves;
+  }
   const unsigned grid = (unsigned)std::min<int64_t>(m->solve_grid, ntiles);
   if (f32) solve_persistent_kernel<float><<<grid, kThreads, kStreamBytes, st>>>(p);
   else solve_persistent_kernel<double><<<grid, kThreads, 0, st>>>(p);

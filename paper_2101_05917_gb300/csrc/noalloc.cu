@@ -1,14 +1,14 @@
 // Local step for callers that cannot allocate device memory.
 //
-// Some callers cannot call cudaMalloc: code running while a CUDA graph is being
-// captured (an allocation there is not captured and breaks the capture), code that
-// must run under a hard device-memory budget fixed up front, or hosts whose memory
-// is handed out by an allocator the library cannot reach.  pd_local_step_noalloc
-// serves them: the caller passes every input and output array, and the only
-// scratch the computation needs (the per-cell corner forces, the block partial
-// sums of the energy and a status word) lives in one file-scope device array of
-// fixed size.  That array exists on every GPU that loads this library, for the
-// life of the process.
+// Some callers cannot call cudaMalloc: code that must run under a hard
+// device-memory budget fixed up front, or hosts whose memory is handed out by an
+// allocator the library cannot reach.  pd_local_step_noalloc serves them: the
+// caller passes every input and output array, and the only scratch the
+// computation needs (the per-cell corner forces, the block partial sums of the
+// energy and a status word) lives in one file-scope device array of fixed size.
+// That array exists on every GPU that loads this library, for the life of the
+// process.  The status word (det F <= 0 seen, a non-finite gradient entry) is
+// copied to the caller's status_flags, when given, at the end of the call.
 //
 // Limits and rules of use:
 //   * at most kMaxCells cells (and at most 8 kMaxCells nodes) per call;
@@ -30,8 +30,13 @@ namespace {
 
 constexpr int64_t kMaxCells = PD_NOALLOC_MAX_CELLS;
 constexpr int kT = 256;
-constexpr int64_t kMaxElemBlocks = (kMaxCells * 8 + kT - 1) / kT;
+// one energy partial per block of the element kernel (its block size is shared
+// through pd_internal.cuh, so the layout follows it)
+constexpr int64_t kMaxElemBlocks = raw_element_blocks(kMaxCells);
 constexpr int64_t kMaxNodeBlocks = (kMaxCells * 8 + kT - 1) / kT;
+static_assert(kMaxElemBlocks * kElemBlockThreads >= 8 * kMaxCells, "element partials do not cover the cells");
+static_assert(PD_LOCAL_FLAG_INVERTED == DEV_ERR_INVERTED && PD_LOCAL_FLAG_NAN == DEV_ERR_NAN,
+              "status bits of the header and of the kernels differ");
 // layout (in doubles): corner forces (FP64 worst case) | element block partials |
 // node block partials | energy accumulator | status word
 constexpr int64_t kForcesOff = 0;
@@ -50,7 +55,7 @@ void* g_addr[256] = {};   // device address of the scratch array, per device ord
 template <typename T>
 __global__ void __launch_bounds__(kT) noalloc_gather_kernel(int64_t n, const int32_t* inc_ptr, const int32_t* inc,
                                                            const T* forces, const double* x, const uint8_t* contact,
-                                                           double k, double* grad, double* partials) {
+                                                           double k, double* grad, double* partials, int* status) {
   const int64_t c = (int64_t)blockIdx.x * kT + threadIdx.x;
   double en = 0;
   if (c < n) {
@@ -71,6 +76,7 @@ __global__ void __launch_bounds__(kT) noalloc_gather_kernel(int64_t n, const int
     grad[3 * c] = g0;
     grad[3 * c + 1] = g1;
     grad[3 * c + 2] = g2;
+    if (!isfinite(g0) || !isfinite(g1) || !isfinite(g2)) atomicOr(status, DEV_ERR_NAN);
   }
   __shared__ double sh[kT / 32];
 #pragma unroll
@@ -127,7 +133,8 @@ extern "C" pd_status pd_local_step_noalloc(int64_t n_nodes, int64_t n_elems, con
                                            const double* x, const double* act, const double* w_corot,
                                            const double* w_vol, const double* w_muscle, const double* fiber,
                                            const uint8_t* contact, double k_contact, int32_t precision,
-                                           double* grad_E, double* energy, void* stream) {
+                                           double* grad_E, double* energy, int32_t* status_flags,
+                                           void* stream) {
   using namespace pd;
   if (n_elems <= 0 || n_nodes <= 0) {
     set_error("pd_local_step_noalloc: empty mesh");
@@ -162,20 +169,23 @@ extern "C" pd_status pd_local_step_noalloc(int64_t n_nodes, int64_t n_elems, con
   PD_CUDA_TRY(cudaMemsetAsync(status, 0, sizeof(int), s));
   PD_CUDA_TRY(launch_element_forces_raw(n_elems, elems, x, act, w_corot, w_vol, w_muscle, fiber, dx, precision,
                                         scratch + kForcesOff, scratch + kElemPartOff, status, s));
-  const int64_t ne_blk = (n_elems * 8 + kT - 1) / kT;
+  const int64_t ne_blk = raw_element_blocks(n_elems);
   const int64_t nn_blk = (n_nodes + kT - 1) / kT;
   if (precision == PD_PREC_MIXED)
     noalloc_gather_kernel<float><<<(unsigned)nn_blk, kT, 0, s>>>(
         n_nodes, inc_ptr, inc, reinterpret_cast<const float*>(scratch + kForcesOff), x,
-        k_contact > 0 ? contact : nullptr, k_contact, grad_E, scratch + kNodePartOff);
+        k_contact > 0 ? contact : nullptr, k_contact, grad_E, scratch + kNodePartOff, status);
   else
     noalloc_gather_kernel<double><<<(unsigned)nn_blk, kT, 0, s>>>(
         n_nodes, inc_ptr, inc, scratch + kForcesOff, x, k_contact > 0 ? contact : nullptr, k_contact, grad_E,
-        scratch + kNodePartOff);
+        scratch + kNodePartOff, status);
   PD_CUDA_TRY(cudaGetLastError());
   if (energy) {
     noalloc_energy_kernel<<<1, kT, 0, s>>>(scratch + kElemPartOff, ne_blk, scratch + kNodePartOff, nn_blk, energy);
     PD_CUDA_TRY(cudaGetLastError());
   }
+  // the status word leaves the shared scratch in stream order (a device-to-device
+  // copy of 4 bytes allocates nothing)
+  if (status_flags) PD_CUDA_TRY(cudaMemcpyAsync(status_flags, status, sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
   return PD_OK;
 }

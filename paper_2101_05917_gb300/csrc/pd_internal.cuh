@@ -37,6 +37,7 @@ enum : int {
   DEV_ERR_INVERTED = 2,
   DEV_ERR_NAN = 4,
   DEV_ERR_TIMEOUT = 8,   // a bounded device-side wait gave up
+  DEV_ERR_LAYOUT = 16,   // an internal descriptor failed its size / alignment check
 };
 
 // ---------------------------------------------------------------- buffers
@@ -136,6 +137,14 @@ struct MeshImpl {
   int64_t* parent = nullptr;
   unsigned long long* solve_counters = nullptr;   // gticket | otick[...] | fdone[ns] | bdone[ns]
   int solve_grid = 0;
+  // polls of a solve dependency wait before it gives up (~1 s by default); the
+  // environment variable PD_SOLVE_SPIN_LIMIT, read at mesh creation, lowers it
+  long long solve_spin_limit = 1ll << 20;
+  // test support (PD_TEST_SOLVE_STALLS at mesh creation): the next solves raise one
+  // forward dependency target by one, so that wait runs out and reports
+  // DEV_ERR_TIMEOUT; each such solve decrements the count
+  mutable int test_stall_solves = 0;
+  int64_t stall_tile = -1;         // the forward tile whose wait is raised
   int sms = 1;                     // SMs of the device
   int32_t* gath_slots = nullptr;   // (sum nr) x slot_w update-row sources, -1 = none
   int slot_w = 1;
@@ -227,6 +236,10 @@ cudaError_t launch_gather_hvp(const MeshImpl* m, const IterState* gate, const vo
                               int precision, const double* x, const double* v, const double* gs,
                               double* Hv, double* partials, cudaStream_t s);
 int gather_blocks(const MeshImpl* m);
+// Threads per block of the element kernels (8 lanes per cell): the raw force
+// launch writes one energy partial per block, raw_element_blocks(ne) of them.
+constexpr int kElemBlockThreads = 256;
+constexpr int64_t raw_element_blocks(int64_t ne) { return (ne * 8 + kElemBlockThreads - 1) / kElemBlockThreads; }
 cudaError_t launch_element_forces_raw(int64_t ne, const int32_t* elems, const double* x, const double* act,
                                       const double* wc, const double* wv, const double* wm, const double* fiber,
                                       double dx, int precision, void* elembuf, double* energy_partials,

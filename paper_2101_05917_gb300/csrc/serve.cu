@@ -38,16 +38,21 @@ double ms_between(Clock::time_point a, Clock::time_point b) {
   return std::chrono::duration<double, std::milli>(b - a).count();
 }
 
-// FNV-1a over bytes: cache keys for geometry and factor inputs
+// Cache keys for geometry and factor inputs: the full byte string of the inputs
+// plus its FNV-1a hash; a lookup compares the hash first and then every byte, so
+// two different inputs never share a cache entry.
 struct Hasher {
   uint64_t h = 1469598103934665603ull;
+  std::vector<unsigned char> key;
   void bytes(const void* p, size_t n) {
     const unsigned char* c = static_cast<const unsigned char*>(p);
+    key.insert(key.end(), c, c + n);
     for (size_t i = 0; i < n; ++i) {
       h ^= c[i];
       h *= 1099511628211ull;
     }
   }
+  bool same(uint64_t hash, const std::vector<unsigned char>& k) const { return hash == h && k == key; }
   template <typename T>
   void pod(const T& v) {
     bytes(&v, sizeof(T));
@@ -103,7 +108,9 @@ struct DevBuf {
 
 struct CachedMesh {
   uint64_t geom = 0;
+  std::vector<unsigned char> geom_key;
   uint64_t factor = 0;   // 0 = not factorised
+  std::vector<unsigned char> factor_key;
   pd_mesh mesh = nullptr;
 };
 
@@ -194,7 +201,8 @@ pd_status prepare_mesh(pd_server s, Slot& sl, const Job& j, pd_mesh* out, int* m
   f.vec(j.wc), f.vec(j.wv), f.vec(j.wm), f.vec(j.fiber);
   f.pod(j.h), f.bytes(j.gravity, sizeof(j.gravity)), f.pod(j.k_contact), f.pod(j.precision);
   const uint64_t fkey = f.h | 1ull;   // never 0
-  auto it = std::find_if(sl.cache.begin(), sl.cache.end(), [&](const CachedMesh& c) { return c.geom == g.h; });
+  auto it = std::find_if(sl.cache.begin(), sl.cache.end(),
+                         [&](const CachedMesh& c) { return g.same(c.geom, c.geom_key); });
   *mesh_hit = it != sl.cache.end();
   if (it == sl.cache.end()) {
     pd_mesh_desc d{};
@@ -218,13 +226,14 @@ pd_status prepare_mesh(pd_server s, Slot& sl, const Job& j, pd_mesh* out, int* m
       pd_mesh_destroy(sl.cache.back().mesh);
       sl.cache.pop_back();
     }
-    sl.cache.push_front(CachedMesh{g.h, 0, m});
+    sl.cache.push_front(CachedMesh{g.h, g.key, 0, {}, m});
   } else if (it != sl.cache.begin()) {
     sl.cache.splice(sl.cache.begin(), sl.cache, it);
   }
   CachedMesh& c = sl.cache.front();
-  *factor_hit = c.factor == fkey;
-  if (c.factor != fkey) {
+  const bool fhit = c.factor == fkey && c.factor_key == f.key;
+  *factor_hit = fhit;
+  if (!fhit) {
     const size_t e = (size_t)j.e;
     auto up = [&](DevBuf& b, const std::vector<double>& v) -> const double* {
       if (v.empty()) return nullptr;
@@ -247,9 +256,11 @@ pd_status prepare_mesh(pd_server s, Slot& sl, const Job& j, pd_mesh* out, int* m
     fo.k_contact = j.k_contact;
     fo.precision = j.precision;
     c.factor = 0;
+    c.factor_key.clear();
     pd_status st = pd_factorize(c.mesh, wc, wv, wm, fb, &fo, sl.stream);
     if (st != PD_OK) return st;
     c.factor = fkey;
+    c.factor_key = std::move(f.key);
   }
   *out = c.mesh;
   return PD_OK;

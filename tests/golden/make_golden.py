@@ -110,6 +110,8 @@ if __name__ == "__main__":
         c1()
     if "c2" in which:
         c2()
+    if "c2_10" in which:
+        c2(T=10)   # a longer prefix of the 100-step benchmark horizon
     if "c3" in which:
         c3()
     if "c3_24" in which:

@@ -94,3 +94,34 @@ def test_serving_refuses_tetrahedral_scenes(native):
     srv.handle = None
     with pytest.raises(ValueError):
         srv.submit_scene(tet_beam(2, 1, 1, T=1))
+
+
+def test_backward_rejects_mismatched_loss_gradients(native):
+    """pd_backward reads loss_states blocks of (n, 3): the Python front end checks
+    the caller's shapes (states, loss gradients) and the C ABI refuses a
+    loss_states that is neither 1 nor T+1 before it touches any array."""
+    import ctypes
+    import torch
+    from paper_2101_05917_gb300 import api
+    sc = small_beam(3, 2, 2, T=1)
+    m = api.PDMesh.from_scene(sc, device=None)
+    n, T, K = m.n, 4, 2
+    opts = api.solver_opts(checkpoint_every=K)
+    roll = api.Rollout(torch.zeros((T // K + 1, n, 3), dtype=torch.float64),
+                       torch.zeros((T // K + 1, n, 3), dtype=torch.float64), {}, 0)
+    # the checkpointed states' gradient where every state's is expected
+    with pytest.raises(ValueError, match="dL_dx"):
+        m.backward(roll, T, torch.zeros((T // K + 1, n, 3), dtype=torch.float64), loss_all_steps=True, opts=opts)
+    with pytest.raises(ValueError, match="dL_dv"):
+        m.backward(roll, T, torch.zeros((n, 3), dtype=torch.float64),
+                   dL_dv=torch.zeros((T + 1, n, 3), dtype=torch.float64), opts=opts)
+    # states stored for another checkpoint interval
+    with pytest.raises(ValueError, match="rollout states"):
+        m.backward(roll, T, torch.zeros((n, 3), dtype=torch.float64), opts=api.solver_opts())
+    L = native.lib()
+    for bad in (2, T, T + 2, -1):
+        st = L.pd_backward(m.handle, None, None, None, None, 0.0, T, None, None, bad, None, None, None, None, None,
+                           None, None, None, None, None, None)
+        assert st == native.PD_ERR_INVALID_ARG
+        assert b"loss_states" in L.pd_last_error()
+    m.close()

@@ -110,8 +110,14 @@ def test_backward_needs_the_forward_sets():
     mesh.contact_prepare(sc.contact.astype(np.uint8))
     opts = api.solver_opts(complementarity=True)
     roll = mesh.forward(_t(sc.x0), _t(sc.v0), 2, f_ext=_t(sc.f_ext), opts=opts)
-    with pytest.raises(RuntimeError):
+    # states of a 2-step rollout given as a 3-step one: the front end refuses the
+    # shapes before the library is called
+    with pytest.raises(ValueError):
         mesh.backward(roll, 3, _t(np.zeros((4, sc.x0.shape[0], 3))), loss_all_steps=True, opts=opts)
+    # the right shapes with a T the forward pass did not run: the library refuses it
+    roll3 = api.Rollout(_t(np.zeros((4, sc.x0.shape[0], 3))), _t(np.zeros((4, sc.x0.shape[0], 3))), {}, 0)
+    with pytest.raises(RuntimeError):
+        mesh.backward(roll3, 3, _t(np.zeros((4, sc.x0.shape[0], 3))), loss_all_steps=True, opts=opts)
     with pytest.raises(RuntimeError):
         mesh.contact_step_set(2)
     mesh.close()

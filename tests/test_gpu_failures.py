@@ -84,3 +84,37 @@ def test_iteration_cap_reports_not_converged():
     assert roll.stats["not_converged_steps"] == sc.T
     assert np.all(np.isfinite(roll.x.cpu().numpy()))
     mesh.close()
+
+
+@pytest.mark.parametrize("prec", [N.PD_PREC_FP64, N.PD_PREC_MIXED])
+def test_solve_dependency_wait_runs_out(monkeypatch, prec):
+    """A bounded device wait that gives up reports PD_ERR_TIMEOUT instead of
+    hanging.  The test hook PD_TEST_SOLVE_STALLS=1 makes the first solve of the
+    mesh wait for one forward block more than its children deliver (nothing
+    else is changed), with the wait bound lowered to 20,000 polls by
+    PD_SOLVE_SPIN_LIMIT; the wait runs out, the call returns the status, and
+    the next solve on the same mesh is correct."""
+    from oracle.model import Model
+    sc = small_beam(6, 3, 3, T=1)
+    monkeypatch.setenv("PD_SOLVE_SPIN_LIMIT", "20000")
+    monkeypatch.setenv("PD_TEST_SOLVE_STALLS", "1")
+    mesh = make_mesh(sc, precision=prec, leaf_max=8)   # several levels: the root waits for children
+    monkeypatch.delenv("PD_TEST_SOLVE_STALLS")
+    model = Model(sc)
+    rng = np.random.default_rng(3)
+    b = rng.standard_normal(sc.x0.shape)
+    b[model.dirichlet] = 0
+    with pytest.raises(N.PDError) as err:
+        mesh.solve(T(b), precision=prec)
+    assert err.value.status == N.PD_ERR_TIMEOUT
+    x = mesh.solve(T(b), precision=prec).cpu().numpy()
+    A = model.A_matrix().toarray() if hasattr(model.A_matrix(), "toarray") else model.A_matrix()
+    fd = model.free_dofs
+    ref = np.zeros(b.size)
+    ref[fd] = np.linalg.solve(A[np.ix_(fd, fd)], b.ravel()[fd])
+    tol = 1e-10 if prec == N.PD_PREC_FP64 else 2e-5
+    assert np.linalg.norm(x.ravel() - ref) <= tol * np.linalg.norm(ref)
+    # the rollout path on the same mesh works too
+    roll = _forward(mesh, sc, sc.x0, opts=api.solver_opts(**OPTS))
+    assert roll.status == N.PD_OK
+    mesh.close()
