@@ -56,6 +56,75 @@ __device__ __forceinline__ T gradN_tet(int a, int q, int d, T inv_dx) {
 
 enum { RULE_HEX8 = 0, RULE_TET6 = 1 };
 
+// Hexahedron: the shape gradients factor over the three axes, so the sums over
+// the 8 corners (F at a Gauss point) and over the 8 Gauss points (corner forces)
+// are Kronecker products of 2 x 2 matrices applied across the cell's 8 lanes: one
+// butterfly stage per axis, exchanging with the lane whose index differs in that
+// axis' bit (d = 0, 1, 2 <-> lane bit 4, 2, 1).  Per axis, with w(equal bits) =
+// (1 + 1/sqrt3)/2 and w(different bits) = (1 - 1/sqrt3)/2:
+//   W (an axis other than the derivative's): v' = w+ v + w- v_partner
+//   D (the derivative axis, corners -> point): v' = v[bit 1] - v[bit 0]
+//   S (the derivative axis, points -> corner): v' = sign(own bit) (v + v_partner)
+// which reproduces sum_a v_a dN_a/dX_j(xi_q) (and its transpose) with the factor
+// 1/dx applied once at the end.
+template <typename T>
+struct HexW {
+  static constexpr double kWp = 0.78867513459481288225;   // (1 + 1/sqrt3) / 2
+  static constexpr double kWm = 0.21132486540518711775;   // (1 - 1/sqrt3) / 2
+};
+
+template <typename T, int MASK>
+__device__ __forceinline__ T bf_w(T v) {
+  const T p = __shfl_xor_sync(0xffffffffu, v, MASK);
+  return T(HexW<T>::kWp) * v + T(HexW<T>::kWm) * p;
+}
+template <typename T, int MASK>
+__device__ __forceinline__ T bf_d(T v, int k) {
+  const T p = __shfl_xor_sync(0xffffffffu, v, MASK);
+  return (k & MASK) ? v - p : p - v;
+}
+template <typename T, int MASK>
+__device__ __forceinline__ T bf_s(T v, int k) {
+  const T t = v + __shfl_xor_sync(0xffffffffu, v, MASK);
+  return (k & MASK) ? t : -t;
+}
+
+// G[i][j] += inv_dx * sum_a v_a[i] dN_a/dX_j at the lane's Gauss point k (v: the
+// lane's corner value, corner a = lane k)
+template <typename T>
+__device__ __forceinline__ void hex_grad(const T (&v)[3], int k, T inv_dx, T (&G)[3][3]) {
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    const T p0 = __shfl_xor_sync(0xffffffffu, v[i], 4);
+    const T w0 = T(HexW<T>::kWp) * v[i] + T(HexW<T>::kWm) * p0;
+    const T d0 = (k & 4) ? v[i] - p0 : p0 - v[i];
+    const T pw = __shfl_xor_sync(0xffffffffu, w0, 2);
+    const T pd = __shfl_xor_sync(0xffffffffu, d0, 2);
+    const T d0w1 = T(HexW<T>::kWp) * d0 + T(HexW<T>::kWm) * pd;
+    const T w0d1 = (k & 2) ? w0 - pw : pw - w0;
+    const T w0w1 = T(HexW<T>::kWp) * w0 + T(HexW<T>::kWm) * pw;
+    G[i][0] += inv_dx * bf_w<T, 1>(d0w1);
+    G[i][1] += inv_dx * bf_w<T, 1>(w0d1);
+    G[i][2] += inv_dx * bf_d<T, 1>(w0w1, k);
+  }
+}
+
+// f[i] = inv_dx * sum_q sum_j S_q[i][j] dN_k/dX_j(xi_q) for the lane's corner k
+// (S: the lane's Gauss-point stress)
+template <typename T>
+__device__ __forceinline__ void hex_forces(const T (&S)[3][3], int k, T inv_dx, T (&f)[3]) {
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    const T u0 = bf_s<T, 4>(S[i][0], k);
+    const T u1 = bf_w<T, 4>(S[i][1]);
+    const T u2 = bf_w<T, 4>(S[i][2]);
+    const T v0 = bf_w<T, 2>(u0);
+    const T v1 = bf_s<T, 2>(u1, k);
+    const T v2 = bf_w<T, 2>(u2);
+    f[i] = inv_dx * (bf_w<T, 1>(v0 + v1) + bf_s<T, 1>(v2, k));
+  }
+}
+
 template <typename T, int RULE>
 __device__ __forceinline__ T shape_grad(int a, int q, int d, T inv_dx) {
   return RULE == RULE_TET6 ? gradN_tet<T>(a, q, d, inv_dx) : gradN<T>(a, q, d, inv_dx);
@@ -121,21 +190,26 @@ element_kernel(ElemParams p) {
   // ---- per Gauss point (q = k): H = F - I and, when needed, dF = G_q v
   T H[3][3] = {{T(0), T(0), T(0)}, {T(0), T(0), T(0)}, {T(0), T(0), T(0)}};
   T dF[3][3] = {{T(0), T(0), T(0)}, {T(0), T(0), T(0)}, {T(0), T(0), T(0)}};
+  if constexpr (RULE == RULE_HEX8) {
+    hex_grad<T>(dk, k, inv_dx, H);
+    if (MODE != MODE_FORCE) hex_grad<T>(vk, k, inv_dx, dF);
+  } else {
 #pragma unroll
-  for (int a = 0; a < 8; ++a) {
-    T da[3], va[3];
-#pragma unroll
-    for (int i = 0; i < 3; ++i) {
-      da[i] = __shfl_sync(0xffffffffu, dk[i], base + a);
-      if (MODE != MODE_FORCE) va[i] = __shfl_sync(0xffffffffu, vk[i], base + a);
-    }
-#pragma unroll
-    for (int j = 0; j < 3; ++j) {
-      const T gN = shape_grad<T, RULE>(a, k, j, inv_dx);
+    for (int a = 0; a < 8; ++a) {
+      T da[3], va[3];
 #pragma unroll
       for (int i = 0; i < 3; ++i) {
-        H[i][j] += da[i] * gN;
-        if (MODE != MODE_FORCE) dF[i][j] += va[i] * gN;
+        da[i] = __shfl_sync(0xffffffffu, dk[i], base + a);
+        if (MODE != MODE_FORCE) va[i] = __shfl_sync(0xffffffffu, vk[i], base + a);
+      }
+#pragma unroll
+      for (int j = 0; j < 3; ++j) {
+        const T gN = shape_grad<T, RULE>(a, k, j, inv_dx);
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+          H[i][j] += da[i] * gN;
+          if (MODE != MODE_FORCE) dF[i][j] += va[i] * gN;
+        }
       }
     }
   }
@@ -246,18 +320,22 @@ element_kernel(ElemParams p) {
 
   // ---- corner forces f_a = sum_q S_q gradN_a(q), lane k acting as corner a = k
   T fa[3] = {T(0), T(0), T(0)};
+  if constexpr (RULE == RULE_HEX8) {
+    hex_forces<T>(S, k, inv_dx, fa);
+  } else {
 #pragma unroll
-  for (int q = 0; q < 8; ++q) {
-    T Sq[3][3];
+    for (int q = 0; q < 8; ++q) {
+      T Sq[3][3];
 #pragma unroll
-    for (int i = 0; i < 3; ++i)
+      for (int i = 0; i < 3; ++i)
 #pragma unroll
-      for (int j = 0; j < 3; ++j) Sq[i][j] = __shfl_sync(0xffffffffu, S[i][j], base + q);
+        for (int j = 0; j < 3; ++j) Sq[i][j] = __shfl_sync(0xffffffffu, S[i][j], base + q);
 #pragma unroll
-    for (int j = 0; j < 3; ++j) {
-      const T gN = shape_grad<T, RULE>(k, q, j, inv_dx);
+      for (int j = 0; j < 3; ++j) {
+        const T gN = shape_grad<T, RULE>(k, q, j, inv_dx);
 #pragma unroll
-      for (int i = 0; i < 3; ++i) fa[i] += Sq[i][j] * gN;
+        for (int i = 0; i < 3; ++i) fa[i] += Sq[i][j] * gN;
+      }
     }
   }
   if (valid) {
