@@ -49,7 +49,9 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 # (63), the corner forces (72 FMA) and the energy (6).
 LOCAL_FLOPS_PER_GP = 144 + 42 + 4 * 3 * 40 + 12 + 54 + 90 + 63 + 144 + 6
 WORKLOADS = {
-    "c5": dict(name="c5_beam_64x64x128_mixed_ckpt25", K=SEG, tol=1e-8, want=("fext", "v0"), iters_per_step=100.0),
+    # tol 1e-7: over 50 steps the mixed path at this tolerance stays within 2.5e-8
+    # (positions) and 7e-8 (gradients) of the FP64 path at tol 1e-10
+    "c5": dict(name="c5_beam_64x64x128_mixed_ckpt25", K=SEG, tol=1e-7, want=("fext", "v0"), iters_per_step=75.0),
     "c2": dict(name="c2_beam_32x32x64_mixed", K=0, tol=1e-8, want=("w_corot", "w_vol", "v0"),
                iters_per_step=150.0),
 }

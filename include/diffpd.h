@@ -55,7 +55,16 @@ typedef enum {
                                (a library defect, not an input error) */
 } pd_status;
 
-enum { PD_PREC_FP64 = 0, PD_PREC_MIXED = 1 };
+enum {
+  PD_PREC_FP64 = 0,
+  PD_PREC_MIXED = 1,
+  /* pd_local_step / pd_hessian_vector only: the FP32 local step with the
+     displacement gradient F - I and the Green strain F^T F - I formed in FP64, so
+     that the stresses stay accurate relative to the strain under large rotations
+     (hexahedra; the tetrahedral rule runs the plain FP32 step).  The mixed-precision
+     rollouts switch to it when the plain FP32 residual stops decreasing. */
+  PD_PREC_MIXED_STRAIN = 2
+};
 
 typedef struct pd_mesh_s* pd_mesh;
 
@@ -189,6 +198,9 @@ typedef struct {
                                    time of the step's adjoint and, with checkpointing, of its
                                    recomputation (so after both calls entry t holds the
                                    fwd+bwd latency of step t); NULL = none */
+  int32_t* step_iters;          /* optional host array of T entries: pd_forward stores the
+                                   iterations of each step, pd_backward those of each step's
+                                   adjoint solve (it overwrites the entries); NULL = none */
 } pd_solver_opts;
 
 typedef struct {

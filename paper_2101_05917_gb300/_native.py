@@ -29,6 +29,7 @@ STATUS_NAMES = {0: "PD_OK", 1: "PD_ERR_INVALID_ARG", 2: "PD_ERR_OOM", 3: "PD_ERR
 
 PD_PREC_FP64 = 0
 PD_PREC_MIXED = 1
+PD_PREC_MIXED_STRAIN = 2
 PD_ELEM_HEX8 = 0
 PD_ELEM_TET6 = 1
 ELEMENT_RULES = {"hex8": PD_ELEM_HEX8, "tet6": PD_ELEM_TET6}
@@ -67,7 +68,8 @@ class SolverOpts(ctypes.Structure):
                 ("lbfgs_m", ctypes.c_int32), ("ls_max", ctypes.c_int32),
                 ("checkpoint_every", ctypes.c_int32), ("check_every", ctypes.c_int32),
                 ("profile", ctypes.c_int32), ("warm_start", ctypes.c_int32),
-                ("no_graphs", ctypes.c_int32), ("complementarity", ctypes.c_int32), ("step_ms", c_double_p)]
+                ("no_graphs", ctypes.c_int32), ("complementarity", ctypes.c_int32), ("step_ms", c_double_p),
+                ("step_iters", ctypes.POINTER(ctypes.c_int32))]
 
 
 class Stats(ctypes.Structure):

@@ -44,16 +44,23 @@ def _u8(a, n, name):
 
 def solver_opts(tol_fwd=1e-9, tol_bwd=1e-9, max_iter_fwd=500, max_iter_bwd=500, lbfgs_m=5, ls_max=10,
                 checkpoint_every=0, check_every=4, profile=False, warm_start=False, graphs=True,
-                complementarity=False, step_ms: Optional[np.ndarray] = None) -> N.SolverOpts:
+                complementarity=False, step_ms: Optional[np.ndarray] = None,
+                step_iters: Optional[np.ndarray] = None) -> N.SolverOpts:
     """step_ms: optional float64 host array of T entries receiving the per-step
-    wall time (forward, then the backward adds its own); the caller keeps it alive."""
+    wall time (forward, then the backward adds its own); step_iters: optional
+    int32 host array of T entries receiving the per-step iterations (forward, then
+    the backward's adjoint iterations); the caller keeps both alive."""
     p = None
     if step_ms is not None:
         assert step_ms.dtype == np.float64 and step_ms.flags.c_contiguous
         p = step_ms.ctypes.data_as(N.c_double_p)
+    q = None
+    if step_iters is not None:
+        assert step_iters.dtype == np.int32 and step_iters.flags.c_contiguous
+        q = step_iters.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
     return N.SolverOpts(tol_fwd, tol_bwd, max_iter_fwd, max_iter_bwd, lbfgs_m, ls_max, checkpoint_every,
                         check_every, 1 if profile else 0, 1 if warm_start else 0, 0 if graphs else 1,
-                        1 if complementarity else 0, p)
+                        1 if complementarity else 0, p, q)
 
 
 @dataclass

@@ -228,6 +228,9 @@ struct Ctx {
   int64_t launches = 0, solves = 0, locals = 0;
   int64_t bwd_steps = 0;
   int last_kind = -1;   // 0 forward, 1 backward: L-BFGS pairs carry over within a kind
+  // mixed forward: steps left that start with the strain-accurate FP32 local step
+  // (set when a step's plain FP32 residual stopped halving above the tolerance)
+  int acc_steps = 0;
   EventTimer* solve_t = nullptr;
   int dev_flags = 0;
   EventTimer* local_t = nullptr;
@@ -400,7 +403,7 @@ namespace {
 
 cudaGraphExec_t iteration_graph(Ctx& c, int dir, int prec, bool with_act, int variant) {
   MeshImpl* m = c.m;
-  const int pi = prec == PD_PREC_MIXED ? 1 : 0;
+  const int pi = prec == PD_PREC_MIXED ? 1 : (prec == kPrecMixedAcc ? 2 : 0);
   const int iters = kGraphIters - variant;
   cudaGraphExec_t& g = m->iter_graph[dir][pi][variant];
   if (g && m->iter_graph_act[dir][pi][variant] == with_act) return g;
@@ -459,7 +462,8 @@ pd_status run_iterations(Ctx& c, int dir, int prec, const double* act, const dou
     const int variant = (c.solve_t || c.local_t) ? 1 : 0;
     cudaGraphExec_t g = iteration_graph(c, dir, prec, act != nullptr, variant);
     if (g) {
-      const int64_t* gc = c.m->iter_graph_counts[dir][prec == PD_PREC_MIXED ? 1 : 0][variant];
+      const int64_t* gc =
+          c.m->iter_graph_counts[dir][prec == PD_PREC_MIXED ? 1 : (prec == kPrecMixedAcc ? 2 : 0)][variant];
       for (; done + kGraphIters <= count; done += kGraphIters) {
         PD_CUDA_TRY(cudaGraphLaunch(g, c.s));
         c.launches += gc[0];
@@ -641,7 +645,12 @@ pd_status forward_step(Ctx& c, const double* act_t, const double* fext_int, doub
   // tolerance, re-evaluate the gradient at the accepted point with an FP64 local
   // step (the convergence check).  If it fails the FP32 iteration continues from
   // the FP64 gradient; after kMaxChecks failed checks the FP64 local step is used
-  // for the remaining iterations.
+  // for the remaining iterations.  When the FP32 residual stops halving above the
+  // tolerance (its rounding floor: under large rotations H = F - I is of the order
+  // of the rotation angle, and forming the strain from it in FP32 cancels bits),
+  // the iteration continues with the strain-accurate FP32 local step
+  // (kPrecMixedAcc), and only when that stalls too with FP64 local steps; the next
+  // steps then start with the strain-accurate one.
   const bool mixed = m->precision == PD_PREC_MIXED;
   int fp64_launched = 0;
   constexpr int kMaxChecks = 3;
@@ -652,9 +661,16 @@ pd_status forward_step(Ctx& c, const double* act_t, const double* fext_int, doub
     PD_CUDA_TRY(cudaMemcpyAsync(w.act_cur, act_t, sizeof(double) * m->h.e, cudaMemcpyDeviceToDevice, c.s));
     act_c = w.act_cur;
   }
+  // The first chunk of iterations is launched without polling; its length comes
+  // from the previous step: the iterations its FP32 phase took until it met the
+  // tolerance, or until the residual stopped halving (the start of the stall
+  // window, not the switch to FP64 after it).  Counting the whole previous step
+  // instead would feed every stall window into the next step's blind chunk.
+  int fp32_end = -1;
   // the PD + L-BFGS iteration from the trial in w.xt (iteration state reset)
+  bool used_acc = false;
   auto iterate = [&]() -> pd_status {
-    int prec = mixed ? PD_PREC_MIXED : PD_PREC_FP64;
+    int prec = mixed ? (c.acc_steps > 0 ? kPrecMixedAcc : PD_PREC_MIXED) : PD_PREC_FP64;
     int launched = 0, checks = 0, stall = 0;
     double best_rel = 1e300;
     int chunk = std::max(guess, 1);
@@ -676,8 +692,9 @@ pd_status forward_step(Ctx& c, const double* act_t, const double* fext_int, doub
         break;
       }
       if (sh.converged) {
-        if (mixed && prec == PD_PREC_MIXED && !sh.hit_max && !sh.fp64_checked) {
+        if (mixed && prec != PD_PREC_FP64 && !sh.hit_max && !sh.fp64_checked) {
           // FP64 convergence check at the accepted point
+          if (fp32_end < 0) fp32_end = sh.iters;
           ++checks;
           if (checks > kMaxChecks) prec = PD_PREC_FP64;
           force_accept_kernel<<<1, 1, 0, c.s>>>(w.st);
@@ -694,13 +711,21 @@ pd_status forward_step(Ctx& c, const double* act_t, const double* fext_int, doub
         break;
       }
       // FP32 floor above the tolerance: no halving of the residual over three polls
-      if (mixed && prec == PD_PREC_MIXED && sh.ref2 > 0) {
+      if (mixed && prec != PD_PREC_FP64 && sh.ref2 > 0) {
         const double rel = std::sqrt(sh.gn2_acc / sh.ref2);
         if (rel < 0.5 * best_rel) {
           best_rel = rel;
           stall = 0;
         } else if (++stall >= 3) {
-          prec = PD_PREC_FP64;
+          if (fp32_end < 0) fp32_end = std::max(1, sh.iters - 3 * c.o.check_every);
+          if (prec == PD_PREC_MIXED && m->h.rule == PD_ELEM_HEX8) {
+            prec = kPrecMixedAcc;
+            used_acc = true;
+          } else {
+            prec = PD_PREC_FP64;
+          }
+          best_rel = rel;
+          stall = 0;
         }
       }
       if (launched >= hard_cap) {
@@ -725,7 +750,10 @@ pd_status forward_step(Ctx& c, const double* act_t, const double* fext_int, doub
   info.ls = sh.ls_total;
   info.fp64_iters = fp64_launched;
   info.rel = sh.ref2 > 0 ? std::sqrt(sh.gn2_acc / sh.ref2) : 0.0;
-  guess = std::max(1, sh.iters - 1);
+  guess = std::max(1, (fp32_end >= 0 ? fp32_end : sh.iters) - 1);
+  // the strain-accurate local step stays on for the next 8 steps once it was needed
+  if (used_acc) c.acc_steps = 8;
+  else if (c.acc_steps > 0) --c.acc_steps;
   finalize_fwd_kernel<<<grid_for(c.n), 256, 0, c.s>>>(c.n, w.x, w.xprev, w.vprev, 1.0 / m->h_step,
                                                       m->kept_of_internal, traj_x, traj_v);
   c.launches += 1;
@@ -891,7 +919,7 @@ pd_status backward_step(Ctx& c, const double* xnext, const double* xt_, const do
   }
   // parameter gradients at x_{t+1} (per-element products in the factor's precision,
   // FP64 accumulation over steps), then the state adjoint of step t
-  LocalArgs la{m, nullptr, xnext, w.z, act_t, prec};
+  LocalArgs la{m, nullptr, xnext, w.z, act_t, prec == PD_PREC_MIXED ? kPrecMixedAcc : prec};
   PD_CUDA_TRY(launch_element_param_grads(la, g_wc, g_wv, g_wm, g_act_t, c.s));
   BwdStateParams bp{};
   bp.n = c.n;
@@ -1303,6 +1331,7 @@ pd_status pd_forward(pd_mesh mesh, const double* x0, const double* v0, const dou
     const Range step_range("forward step", t);
     pd_status e = forward_step(c, act_t, fext_int, mu, tx, tv, info, guess, t);
     if (o.step_ms) o.step_ms[t] = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - ts).count();
+    if (o.step_iters) o.step_iters[t] = info.iters;
     if (e != PD_OK) return e;
     accumulate(stats, info, true);
     if (!info.converged) all_ok = false;
@@ -1449,6 +1478,7 @@ pd_status pd_backward(pd_mesh mesh, const double* x_traj, const double* v_traj, 
                                    g_mu, info, guess_b, t);
       if (o.step_ms)
         o.step_ms[t] += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - ts).count();
+      if (o.step_iters) o.step_iters[t] = info.iters;
       if (er != PD_OK) return er;
       accumulate(stats, info, false);
       if (!info.converged) all_ok = false;
@@ -1483,6 +1513,10 @@ pd_status pd_local_step(pd_mesh mesh, const double* x, const double* act, int32_
     set_error("pd_local_step: x is required");
     return PD_ERR_INVALID_ARG;
   }
+  if (precision != PD_PREC_FP64 && precision != PD_PREC_MIXED && precision != PD_PREC_MIXED_STRAIN) {
+    set_error("pd_local_step: unknown precision");
+    return PD_ERR_INVALID_ARG;
+  }
   MeshImpl* m = &mesh->impl;
   DeviceGuard g(m->device);
   cudaStream_t s = (cudaStream_t)stream;
@@ -1497,7 +1531,7 @@ pd_status pd_local_step(pd_mesh mesh, const double* x, const double* act, int32_
   sum_partials_kernel<<<1, 256, 0, s>>>(pe, nbe, etot);
   double* gi = w.iov;
   const int gb = grid_for(n);
-  if (precision == PD_PREC_MIXED)
+  if (local_is_fp32(precision))
     gather_all_kernel<float><<<gb, 256, 0, s>>>(n, m->inc_ptr, m->inc, w.elembuf, w.iox,
                                                 m->k_contact > 0 ? m->contact : nullptr, m->k_contact, gi,
                                                 w.partials + nbe + 16, w.counters + 1, etot);
@@ -1517,6 +1551,10 @@ pd_status pd_hessian_vector(pd_mesh mesh, const double* x, const double* act, co
   if (ck != PD_OK) return ck;
   if (!x || !v || !Hv) {
     set_error("pd_hessian_vector: x, v and Hv are required");
+    return PD_ERR_INVALID_ARG;
+  }
+  if (precision != PD_PREC_FP64 && precision != PD_PREC_MIXED && precision != PD_PREC_MIXED_STRAIN) {
+    set_error("pd_hessian_vector: unknown precision");
     return PD_ERR_INVALID_ARG;
   }
   MeshImpl* m = &mesh->impl;

@@ -147,8 +147,9 @@ struct ElemParams {
   int* flags;
 };
 
-template <typename T, int MODE, int RULE = RULE_HEX8>
-__global__ void __launch_bounds__(kElemThreads, sizeof(T) == 8 ? 1 : (MODE == MODE_FORCE ? 3 : 2))
+// ACC (FP32 hexahedra only): H and the Green strain in FP64, the rest in FP32
+template <typename T, int MODE, int RULE = RULE_HEX8, bool ACC = false>
+__global__ void __launch_bounds__(kElemThreads, sizeof(T) == 8 ? 1 : (MODE == MODE_FORCE && !ACC ? 3 : 2))
 element_kernel(ElemParams p) {
   if (p.gate && p.gate->converged) return;
   __shared__ double wsum[kElemThreads / 32];
@@ -175,10 +176,12 @@ element_kernel(ElemParams p) {
     xk[2] = p.x[3 * (int64_t)node + 2];
   }
   T dk[3];
+  double dkd[3];
 #pragma unroll
   for (int i = 0; i < 3; ++i) {
     const double x0 = __shfl_sync(0xffffffffu, xk[i], base);
-    dk[i] = (T)((xk[i] - x0) - p.dx * (double)cbit(k, i));
+    dkd[i] = (xk[i] - x0) - p.dx * (double)cbit(k, i);
+    dk[i] = (T)dkd[i];
   }
   T vk[3] = {T(0), T(0), T(0)};
   if (MODE != MODE_FORCE && valid) {
@@ -190,7 +193,22 @@ element_kernel(ElemParams p) {
   // ---- per Gauss point (q = k): H = F - I and, when needed, dF = G_q v
   T H[3][3] = {{T(0), T(0), T(0)}, {T(0), T(0), T(0)}, {T(0), T(0), T(0)}};
   T dF[3][3] = {{T(0), T(0), T(0)}, {T(0), T(0), T(0)}, {T(0), T(0), T(0)}};
-  if constexpr (RULE == RULE_HEX8) {
+  // ACC: the Green strain of this point formed in FP64 (for the SVD below)
+  T Eacc[3][3];
+  if constexpr (RULE == RULE_HEX8 && ACC) {
+    double Hd[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+    hex_grad<double>(dkd, k, 1.0 / p.dx, Hd);
+    double Ed[3][3];
+    green_strain<double>(Hd, Ed);
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) {
+        H[i][j] = (T)Hd[i][j];
+        Eacc[i][j] = (T)Ed[i][j];
+      }
+    if (MODE != MODE_FORCE) hex_grad<T>(vk, k, inv_dx, dF);
+  } else if constexpr (RULE == RULE_HEX8) {
     hex_grad<T>(dk, k, inv_dx, H);
     if (MODE != MODE_FORCE) hex_grad<T>(vk, k, inv_dx, dF);
   } else {
@@ -224,7 +242,8 @@ element_kernel(ElemParams p) {
   T gwc = T(0), gwv = T(0), gwm = T(0), gact = T(0);
 
   SVD3<T> sv;
-  svd3_from_H<T>(H, sv);
+  if constexpr (RULE == RULE_HEX8 && ACC) svd3_from_HE<T>(H, Eacc, sv);
+  else svd3_from_H<T>(H, sv);
   if (valid && !(sv.sig[2] > T(0))) atomicOr(p.flags, DEV_ERR_INVERTED);
   T M[3][3];
   if (MODE != MODE_FORCE) rotate_in<T>(sv.U, dF, sv.V, M);
@@ -499,8 +518,9 @@ template <int MODE>
 void launch_elem(const MeshImpl* m, int precision, const ElemParams& p, cudaStream_t s) {
   const int nb = (int)((m->h.e * 8 + kElemThreads - 1) / kElemThreads);
   const bool tet = m->h.rule == PD_ELEM_TET6;
-  if (precision == PD_PREC_MIXED) {
+  if (local_is_fp32(precision)) {
     if (tet) element_kernel<float, MODE, RULE_TET6><<<nb, kElemThreads, 0, s>>>(p);
+    else if (precision == kPrecMixedAcc) element_kernel<float, MODE, RULE_HEX8, true><<<nb, kElemThreads, 0, s>>>(p);
     else element_kernel<float, MODE, RULE_HEX8><<<nb, kElemThreads, 0, s>>>(p);
   } else {
     if (tet) element_kernel<double, MODE, RULE_TET6><<<nb, kElemThreads, 0, s>>>(p);
@@ -574,7 +594,7 @@ cudaError_t launch_gather_grad(const MeshImpl* m, const IterState* gate, const v
   p.out = grad;
   p.partials = partials;
   const int nb = gather_blocks(m);
-  if (precision == PD_PREC_MIXED)
+  if (local_is_fp32(precision))
     gather_grad_kernel<float><<<nb, kGatherThreads, 0, s>>>(p);
   else
     gather_grad_kernel<double><<<nb, kGatherThreads, 0, s>>>(p);
@@ -593,7 +613,7 @@ cudaError_t launch_gather_hvp(const MeshImpl* m, const IterState* gate, const vo
   p.out = Hv;
   p.partials = partials;
   const int nb = gather_blocks(m);
-  if (precision == PD_PREC_MIXED)
+  if (local_is_fp32(precision))
     gather_hvp_kernel<float><<<nb, kGatherThreads, 0, s>>>(p);
   else
     gather_hvp_kernel<double><<<nb, kGatherThreads, 0, s>>>(p);

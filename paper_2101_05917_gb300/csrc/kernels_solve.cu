@@ -9,30 +9,24 @@
 //                               [u_s; w_s] = Q_s rhs,  W_s = w_s + (children
 //                               updates on the below rows)
 //   backward (root -> leaves):  x_s = Q_s^T [u_s; -x(below rows)]
-// The panels are cut into 2D tiles of at most 256 x 64 panel entries (64 KB in
-// FP32), shaped per supernode so that every thread issues all of its panel loads
-// (up to 64) before it uses any: a tile costs about one memory round trip, and a
-// level of the tree spreads over as many CTAs as it has tiles.  Forward tiles are
-// R rows x (256 / R) column groups of 64 columns (R = 256, 128 or 64, whichever
-// covers the supernode's columns with the fewest idle groups); backward tiles are
-// BC columns x min(16384 / BC, 1024) rows (BC = 64, 32, 16 or 8).  (Smaller CTAs of
-// 128 threads with 32 KB tiles were measured slower: 276 vs 224 us on the 32x32x64
-// beam.)  All-zero tiles of the
-// triangular L11^-1 block are skipped.
-// In FP32 every tile's panel values are also stored contiguously, in the order the
-// tile body reads them (MeshImpl::Qs, packed once per factorisation), and reach
-// shared memory by one bulk copy (cp.async.bulk, completion on an mbarrier) issued
-// before the tile waits for its dependencies: the copy engine keeps a whole 64 KB
-// tile in flight per CTA, where per-thread register loads were limited by the
-// requests an SM can have outstanding (a traced solve showed ~2.5 us just to issue
-// a tile's loads).  The stored layout adds zeros for the upper triangle of L11^-1
-// and for ragged tile edges (11 % more bytes than the structural entries on a
-// 32x32x64-cell beam, 30 % on a 24^3-cell cube, whose supernodes are smaller).
-// FP64 tiles keep the register loads.  Tiles sharing an output block write
-// partial sums; the last tile to finish (integer ticket) adds them in tile order,
-// so the result does not depend on scheduling and no float atomics run.  Both
-// sweeps run in one persistent launch scheduled by the supernodal tree
-// dependencies (below).
+// The panels are cut into 2D tiles of at most 256 x 48 panel entries (48 KB in
+// FP32), shaped per supernode so that each of the 256 tile-body threads owns up to
+// 48 entries: forward tiles are R rows x (256 / R) column groups of 48 columns
+// (R = 256, 128 or 64, whichever covers the supernode's columns with the fewest
+// idle groups); backward tiles are BC columns x min(12288 / BC, 1024) rows (BC =
+// 64, 32, 16 or 8).  All-zero tiles of the triangular L11^-1 block are skipped.
+// In FP32 every tile's panel values are also stored contiguously, in the order
+// the tile body reads them (MeshImpl::Qs, packed once per factorisation), and
+// reach shared memory by one bulk copy (cp.async.bulk, completion on an
+// mbarrier) issued by a producer warp into one of two stages per CTA while the
+// body warps work on the previous tile, so a CTA keeps the next tile's copy in
+// flight throughout (per-thread register loads are limited by the requests an SM
+// can have outstanding).  The stored layout adds zeros for the upper triangle of
+// L11^-1 and for ragged tile edges.  The FP64 kernel keeps per-thread register
+// loads.  Tiles sharing an output block write partial sums; the last tile to
+// finish (integer ticket) adds them in tile order, so the result does not depend
+// on scheduling and no float atomics run.  Both sweeps run in one persistent
+// launch scheduled by the supernodal tree dependencies (below).
 #include <algorithm>
 
 #include "pd_internal.cuh"
@@ -41,20 +35,22 @@ namespace pd {
 
 namespace {
 
-constexpr int kThreads = 256;         // threads per CTA (8 warps); 2 CTAs per SM
+constexpr int kThreads = 256;         // tile-body threads per CTA (8 warps); 2 CTAs per SM
 constexpr int kWarps = kThreads / 32;
-constexpr int kCols = 64;             // forward: columns per thread; backward: loads per lane
-constexpr int kTileElems = kThreads * kCols;   // panel entries per tile at most (32 KB in FP32)
+constexpr int kCols = 48;             // forward: columns per thread; backward: loads per lane
+constexpr int kTileElems = kThreads * kCols;   // panel entries per tile at most (48 KB in FP32)
 constexpr int kPart = kThreads * 3;   // partial-sum slots per tile
 constexpr int kMaxC = 4 * kCols;       // widest forward tile (4 column groups)
 // backward tile rows for BC columns: kTileElems / BC, at most 1024 (32 rows per lane)
 __host__ __device__ constexpr int bwd_tile_rows(int bc) { return kTileElems / bc < 1024 ? kTileElems / bc : 1024; }
 constexpr int kMaxBR = 1024;
 constexpr int kPreSlots = 4;          // W-row sources per position held in registers
-constexpr int kStreamBytes = kTileElems * 4;   // shared-memory tile buffer of the FP32 kernel
+constexpr int kStreamBytes = kTileElems * 4;   // one shared-memory stage of the FP32 kernel
+constexpr int kStages = 2;                     // FP32 kernel: stages per CTA (copy of the next tile in flight)
+constexpr int kPipeThreads = kThreads + 32;    // FP32 kernel: + one producer warp
 
-// loads issued back to back per thread: all 64 in FP32, four batches of 16 in FP64
-// (register budget of two CTAs per SM)
+// loads issued back to back per thread in the FP64 kernel: batches of 16 (register
+// budget); the FP32 kernel reads its panel values from shared memory
 template <typename T>
 struct Batch {
   static constexpr int kLoads = sizeof(T) == 4 ? 64 : 16;
@@ -139,48 +135,43 @@ __device__ __forceinline__ bool wait_count(const unsigned long long* c, unsigned
   return true;
 }
 
-// shared memory of one tile: forward rhs[kMaxC][3] + red[kThreads][3]; backward
-// v[kMaxBR][3] + res[64][3] (as T)
-struct __align__(16) PersistSmem {
-  double buf[(kMaxBR + 64) * 3];
+// Barrier of the 256 tile-body threads (named barrier 1).  In the FP32 kernel the
+// producer warp never joins it; the FP64 kernel has no producer and uses the same
+// barrier.
+__device__ __forceinline__ void body_sync() { asm volatile("bar.sync 1, 256;" ::: "memory"); }
+
+// shared memory of one tile body: forward rhs[kMaxC][3] + red[kThreads][3];
+// backward v[kMaxBR][3] + res[64][3] (as T)
+template <typename T>
+struct __align__(16) TileSmem {
+  T buf[(kMaxBR + 64) * 3];
   int flag;
 };
 
 // last of the tiles of an output block?  (then the partial sums are complete)
-__device__ __forceinline__ bool last_of_block(const SolveParams& p, const SolveTile& tl, PersistSmem& sm) {
-  __syncthreads();
+template <typename T>
+__device__ __forceinline__ bool last_of_block(const SolveParams& p, const SolveTile& tl, TileSmem<T>& sm) {
+  body_sync();
   if (threadIdx.x == 0) {
     const unsigned long long v = add_acq_rel(p.otick + tl.out);
     sm.flag = ((v + 1) % (unsigned long long)tl.ntile) == 0;
   }
-  __syncthreads();
+  body_sync();
   return sm.flag != 0;
 }
 
 __device__ __forceinline__ void signal_done(unsigned long long* c) {
-  __syncthreads();
+  body_sync();
   if (threadIdx.x == 0) add_release(c);
 }
 
-// ------------------------------------------------------------ bulk copies
-// One mbarrier per CTA tracks the tile copy: thread 0 arms it with the byte count
-// and issues the copy; every thread waits for the phase to complete (bounded), and
-// the parity flips once per streamed tile.
-struct StreamCtx {
-  float* tile;               // kStreamBytes of dynamic shared memory
-  unsigned long long* mbar;  // shared
-  int* state;                // shared: 0 = copy in flight, 1 = not issued (bad descriptor), 2 = wait gave up
-  unsigned phase;            // parity of the next completion
-};
-
+// ------------------------------------------------------------ mbarriers
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return (uint32_t)__cvta_generic_to_shared(p);
 }
 
-__device__ __forceinline__ void mbar_init(unsigned long long* bar) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar)) : "memory");
-  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+__device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
 }
 
 __device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, unsigned phase) {
@@ -199,44 +190,24 @@ __device__ __forceinline__ unsigned long long global_ns() {
   return t;
 }
 
-// thread 0: bulk copy of the tile's streamed panel values into sc.tile
-__device__ __forceinline__ void stream_issue(const SolveParams& p, const SolveTile& tl, StreamCtx& sc) {
-  if (threadIdx.x != 0) return;
-  const float* src = p.Qs + tl.soff;
-  const uint32_t bytes = (uint32_t)tl.sbytes;
-  const uint32_t dst = smem_u32(sc.tile), bar = smem_u32(sc.mbar);
-  if (bytes == 0u || bytes > (uint32_t)kStreamBytes || (bytes & 15u) || (dst & 15u) ||
-      (reinterpret_cast<uintptr_t>(src) & 15u)) {
-    atomicOr(p.err, DEV_ERR_LAYOUT);   // nothing issued: the tile skips its products
-    *sc.state = 1;
-    return;
+// waits (at most about limit_ns) for the phase with the given parity to complete
+__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned phase, unsigned long long limit_ns) {
+  if (mbar_try_wait(bar, phase)) return true;
+  const unsigned long long t0 = global_ns();
+  while (!mbar_try_wait(bar, phase)) {
+    if (global_ns() - t0 > limit_ns) return false;
   }
-  *sc.state = 0;
-  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
-  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
-               ::"r"(dst), "l"(src), "r"(bytes), "r"(bar)
-               : "memory");
+  return true;
 }
 
-// every thread: wait (at most about a second) for the tile copy, then flip its
-// parity.  Called after a CTA barrier that follows stream_issue (so *sc.state is
-// visible) and before the barrier that ends the tile (so thread 0 rewrites the
-// state only after every thread has read it).  A wait that gives up sets state 2:
-// the persistent loop then leaves after the tile.
-__device__ __forceinline__ void stream_wait(const SolveParams& p, StreamCtx& sc) {
-  if (*sc.state != 0) return;
-  if (!mbar_try_wait(sc.mbar, sc.phase)) {
-    const unsigned long long t0 = global_ns();
-    while (!mbar_try_wait(sc.mbar, sc.phase)) {
-      if (global_ns() - t0 > 1000000000ull) {
-        atomicOr(p.err, DEV_ERR_TIMEOUT);
-        *sc.state = 2;
-        return;
-      }
-    }
-  }
-  sc.phase ^= 1u;
+__device__ __forceinline__ void mbar_arrive(unsigned long long* bar) {
+  asm volatile("mbarrier.arrive.release.cta.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_tx(unsigned long long* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.release.cta.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
 }
 
 // W-row sources of a position, loaded before the dependency wait (they are static)
@@ -281,8 +252,8 @@ __device__ __forceinline__ void add_W(const SolveParams& p, const Slots& sl, int
 // are added in group order.
 template <typename T, int R>
 __device__ void fwd_tile_body(const SolveParams& p, const SolveTile& tl, int64_t tid_g, unsigned long long epoch,
-                              PersistSmem& sm, StreamCtx& stc) {
-  constexpr bool kStream = sizeof(T) == 4;   // FP32: panel values by bulk copy
+                              TileSmem<T>& sm, const float* stage) {
+  constexpr bool kStream = sizeof(T) == 4;   // FP32: panel values in the shared-memory stage (null: copy failed)
   constexpr int G = kThreads / R;
   constexpr int C = G * kCols;
   constexpr int B = Batch<T>::kLoads;
@@ -300,9 +271,7 @@ __device__ void fwd_tile_body(const SolveParams& p, const SolveTile& tl, int64_t
   const T* Qr = Q + r + cg0 * nr;
   // static data first: panel values, right-hand side, W-row sources
   T q[kStream ? 1 : B];
-  if constexpr (kStream) {
-    stream_issue(p, tl, stc);
-  } else {
+  if constexpr (!kStream) {
 #pragma unroll
     for (int k = 0; k < B; ++k) q[k] = (k < cnt) ? __ldg(Qr + (int64_t)k * nr) : T(0);
   }
@@ -336,7 +305,7 @@ __device__ void fwd_tile_body(const SolveParams& p, const SolveTile& tl, int64_t
       }
     }
   }
-  __syncthreads();
+  body_sync();
   // children's updates of the output row (below rows), read in the same round
   // trip as those of the right-hand side
   double o0 = 0, o1 = 0, o2 = 0;
@@ -354,20 +323,19 @@ __device__ void fwd_tile_body(const SolveParams& p, const SolveTile& tl, int64_t
     rhs[jj][1] = has_c ? (T)(bb[i][1] - w1) : T(0);
     rhs[jj][2] = has_c ? (T)(bb[i][2] - w2) : T(0);
   }
-  __syncthreads();
+  body_sync();
   T a0 = T(0), a1 = T(0), a2 = T(0);
   const T(*rg)[3] = rhs + g * kCols;
   if constexpr (kStream) {
     // stored layout [group][column k < kmax][row rl < rv], zeros past each row's
     // columns: the same products in the same order as the masked register loads of
-    // the FP64 path.  (Staging the 64 values into registers first, as the backward
+    // the FP64 path.  (Staging the values into registers first, as the backward
     // tile does, was measured slower here.)
-    stream_wait(p, stc);
     const int kmax = tl.sld;
     const int rv = (int)min((int64_t)R, nr - row0);
     // products only from a completed copy (a rejected or timed-out copy leaves zeros)
-    if (rl < rv && *stc.state == 0) {
-      const float* qs = stc.tile + g * kmax * rv + rl;
+    if (rl < rv && stage) {
+      const float* qs = stage + g * kmax * rv + rl;
 #pragma unroll 8
       for (int k = 0; k < kmax; ++k) {
         const float qk = qs[k * rv];
@@ -396,7 +364,7 @@ __device__ void fwd_tile_body(const SolveParams& p, const SolveTile& tl, int64_t
     red[threadIdx.x][0] = a0;
     red[threadIdx.x][1] = a1;
     red[threadIdx.x][2] = a2;
-    __syncthreads();
+    body_sync();
     if (g == 0) {
 #pragma unroll
       for (int k = 1; k < G; ++k) {
@@ -444,8 +412,8 @@ __device__ void fwd_tile_body(const SolveParams& p, const SolveTile& tl, int64_t
 // per column the lanes' sums are added by a fixed shuffle tree.
 template <typename T, int BC>
 __device__ void bwd_tile_body(const SolveParams& p, const SolveTile& tl, int64_t tid_g, unsigned long long epoch,
-                              PersistSmem& sm, StreamCtx& stc) {
-  constexpr bool kStream = sizeof(T) == 4;   // FP32: panel values by bulk copy
+                              TileSmem<T>& sm, const float* stage) {
+  constexpr bool kStream = sizeof(T) == 4;   // FP32: panel values in the shared-memory stage (null: copy failed)
   constexpr int CW = BC / kWarps;
   constexpr int BR = bwd_tile_rows(BC);
   constexpr int RL = BR / 32;           // rows per lane
@@ -475,10 +443,9 @@ __device__ void bwd_tile_body(const SolveParams& p, const SolveTile& tl, int64_t
       }
     }
   };
-  if constexpr (kStream) stream_issue(p, tl, stc);
-  else load_batch(0);
+  if constexpr (!kStream) load_batch(0);
   // global rows of the tile's below rows (static)
-  constexpr int VR = BR / kThreads > 0 ? BR / kThreads : 1;
+  constexpr int VR = (BR + kThreads - 1) / kThreads;   // rows of v per thread (BR need not divide)
   int32_t gidx[VR];
 #pragma unroll
   for (int k = 0; k < VR; ++k) {
@@ -492,7 +459,7 @@ __device__ void bwd_tile_body(const SolveParams& p, const SolveTile& tl, int64_t
     if (d >= 0) wait_count(p.bdone + d, (epoch + 1) * (unsigned long long)tl.dep_blocks[0], p.err, p.spin_limit);
     else wait_count(p.fdone + (-d - 1), (epoch + 1) * (unsigned long long)tl.dep_blocks[0], p.err, p.spin_limit);
   }
-  __syncthreads();
+  body_sync();
   // v = [u_s; -x(below rows)] on the tile's rows, zero past the panel
 #pragma unroll
   for (int k = 0; k < VR; ++k) {
@@ -511,7 +478,7 @@ __device__ void bwd_tile_body(const SolveParams& p, const SolveTile& tl, int64_t
     }
     v[rr][0] = v0; v[rr][1] = v1; v[rr][2] = v2;
   }
-  __syncthreads();
+  body_sync();
   T acc[CW][3];
 #pragma unroll
   for (int c = 0; c < CW; ++c) acc[c][0] = acc[c][1] = acc[c][2] = T(0);
@@ -521,17 +488,17 @@ __device__ void bwd_tile_body(const SolveParams& p, const SolveTile& tl, int64_t
     // reading them inside the product loop was measured ~2.5 us slower per tile),
     // then the same products in the same order as the masked register loads of the
     // FP64 path.
-    stream_wait(p, stc);
     const int rs = (int)rn;
     // products only from a completed copy (a rejected or timed-out copy leaves zeros)
-    const int bcv = *stc.state == 0 ? (int)min((int64_t)BC, nc - col0) : 0;
+    const int bcv = stage ? (int)min((int64_t)BC, nc - col0) : 0;
+    const float* tile = stage ? stage : reinterpret_cast<const float*>(sm.buf);
     T qq[CW][RL];
 #pragma unroll
     for (int c = 0; c < CW; ++c)
 #pragma unroll
       for (int i = 0; i < RL; ++i) {
         const int rr = lane + 32 * i, cc = warp * CW + c;
-        qq[c][i] = (rr < rs && cc < bcv) ? stc.tile[cc * rs + rr] : T(0);
+        qq[c][i] = (rr < rs && cc < bcv) ? tile[cc * rs + rr] : T(0);
       }
 #pragma unroll
     for (int i = 0; i < RL; ++i) {
@@ -573,7 +540,7 @@ __device__ void bwd_tile_body(const SolveParams& p, const SolveTile& tl, int64_t
       res[warp * CW + c][2] = acc[c][2];
     }
   }
-  __syncthreads();
+  body_sync();
   const int ntile = tl.ntile;
   if (ntile > 1) {
     T* part = reinterpret_cast<T*>(p.partial) + tid_g * kPart;
@@ -585,7 +552,7 @@ __device__ void bwd_tile_body(const SolveParams& p, const SolveTile& tl, int64_t
       for (int k = 0; k < ntile; ++k) t += __ldcg(parts + (int64_t)k * kPart + idx);
       res[idx / 3][idx % 3] = t;
     }
-    __syncthreads();
+    body_sync();
   }
   for (int jl = threadIdx.x; jl < BC; jl += kThreads) {
     const int64_t j = col0 + jl;
@@ -601,24 +568,29 @@ __device__ void bwd_tile_body(const SolveParams& p, const SolveTile& tl, int64_t
 // kThreads / 2, kThreads / 4 rows), backward with BC = 64 / 32 / 16 / 8 columns
 enum TileKind { kF1 = 0, kF2 = 1, kF4 = 2, kB64 = 3, kB32 = 4, kB16 = 5, kB8 = 6 };
 
-// dynamic shared memory of the FP32 kernel: the streamed tile
-extern __shared__ __align__(128) unsigned char solve_dsm[];
-
 template <typename T>
-__global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 2 : 1) solve_persistent_kernel(SolveParams p) {
-  if (p.gate && (p.gate->converged || !p.gate->accepted)) return;
-  __shared__ PersistSmem sm;
-  __shared__ unsigned long long tk[2];
-  __shared__ __align__(8) unsigned long long mbar;
-  __shared__ int sstate;
-  StreamCtx stc{reinterpret_cast<float*>(solve_dsm), &mbar, &sstate, 0u};
-  const unsigned long long per = (unsigned long long)p.ntiles + gridDim.x;
-  if (threadIdx.x == 0) {
-    tk[0] = atomicAdd(p.gticket, 1ull);
-    sstate = 0;
-    if (sizeof(T) == 4) mbar_init(&mbar);
+__device__ __forceinline__ void run_tile(const SolveParams& p, const SolveTile& tl, int64_t tile,
+                                         unsigned long long epoch, TileSmem<T>& sm, const float* stage) {
+  switch (tl.pad0) {
+    case kF1: fwd_tile_body<T, kThreads>(p, tl, tile, epoch, sm, stage); break;
+    case kF2: fwd_tile_body<T, kThreads / 2>(p, tl, tile, epoch, sm, stage); break;
+    case kF4: fwd_tile_body<T, kThreads / 4>(p, tl, tile, epoch, sm, stage); break;
+    case kB64: bwd_tile_body<T, 64>(p, tl, tile, epoch, sm, stage); break;
+    case kB32: bwd_tile_body<T, 32>(p, tl, tile, epoch, sm, stage); break;
+    case kB16: bwd_tile_body<T, 16>(p, tl, tile, epoch, sm, stage); break;
+    default: bwd_tile_body<T, 8>(p, tl, tile, epoch, sm, stage); break;
   }
-  __syncthreads();
+}
+
+// FP64 solve: every CTA draws its tickets itself and loads each tile's panel
+// values into registers (batches of 16 loads per thread).
+__global__ void __launch_bounds__(kThreads, 1) solve_persistent_kernel(SolveParams p) {
+  if (p.gate && (p.gate->converged || !p.gate->accepted)) return;
+  __shared__ TileSmem<double> sm;
+  __shared__ unsigned long long tk[2];
+  const unsigned long long per = (unsigned long long)p.ntiles + gridDim.x;
+  if (threadIdx.x == 0) tk[0] = atomicAdd(p.gticket, 1ull);
+  body_sync();
   int slot = 0;
   unsigned long long t = tk[0];
   while (true) {
@@ -633,29 +605,115 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 2 : 1) solve_persis
     // barrier that ended the previous tile.
     if (threadIdx.x == 0) tk[slot ^ 1] = atomicAdd(p.gticket, 1ull);
     const SolveTile tl = load_tile(p.tiles, tile);
-    switch (tl.pad0) {
-      case kF1: fwd_tile_body<T, kThreads>(p, tl, tile, epoch, sm, stc); break;
-      case kF2: fwd_tile_body<T, kThreads / 2>(p, tl, tile, epoch, sm, stc); break;
-      case kF4: fwd_tile_body<T, kThreads / 4>(p, tl, tile, epoch, sm, stc); break;
-      case kB64: bwd_tile_body<T, 64>(p, tl, tile, epoch, sm, stc); break;
-      case kB32: bwd_tile_body<T, 32>(p, tl, tile, epoch, sm, stc); break;
-      case kB16: bwd_tile_body<T, 16>(p, tl, tile, epoch, sm, stc); break;
-      default: bwd_tile_body<T, 8>(p, tl, tile, epoch, sm, stc); break;
-    }
-    __syncthreads();   // shared memory of this tile is free; the drawn ticket is visible
-    if (sizeof(T) == 4 && sstate == 2) {
-      // A copy wait gave up, so the copy may still be writing this CTA's shared
-      // memory.  Every issued copy reads a source range checked in stream_issue
-      // (16-byte aligned, inside the streamed panels), so it completes; wait for it
-      // once more, bounded like every other wait, before the CTA retires.  Every
-      // other issued copy completed inside its tile.
-      const unsigned long long t0 = global_ns();
-      while (!mbar_try_wait(&mbar, stc.phase) && global_ns() - t0 < 2000000000ull) {
-      }
-      return;
-    }
+    run_tile<double>(p, tl, tile, epoch, sm, nullptr);
+    body_sync();   // shared memory of this tile is free; the drawn ticket is visible
     slot ^= 1;
     t = tk[slot];
+  }
+}
+
+// FP32 solve: a producer warp and kStages shared-memory stages per CTA.  The
+// producer (one lane) draws the CTA's tickets in increasing order, loads each
+// tile's descriptor and starts one bulk copy (cp.async.bulk, completion on the
+// stage's "full" mbarrier) of the tile's streamed panel values into a free stage,
+// so the copies of the next tiles are in flight while the 8 body warps work on
+// the current one.  The body warps take the stages in the same order and return
+// each one on its "empty" mbarrier.  A CTA holds at most kStages tickets and
+// works on them in increasing order, so the lowest unfinished ticket is always the
+// one a CTA is working on, and the schedule cannot deadlock.  Every wait is
+// bounded: a dependency wait after SolveParams::spin_limit polls, a stage wait
+// after about a second (DEV_ERR_TIMEOUT); a rejected descriptor (DEV_ERR_LAYOUT)
+// is not copied and its tile skips its products.  A body wait that gives up
+// leaves after waiting once more, bounded, for that stage's copy; the producer
+// stops at the first stage wait that gives up.
+struct PipeStage {
+  SolveTile tl;
+  int64_t tile;                  // tile index, -1 = no more tiles
+  unsigned long long epoch;
+  int copied;                    // 1 = the stage holds the tile's panel values
+};
+
+// dynamic shared memory of the FP32 kernel: kStages stages of kStreamBytes
+extern __shared__ __align__(128) unsigned char solve_dsm[];
+
+__global__ void __launch_bounds__(kPipeThreads, 2) solve_pipe_kernel(SolveParams p) {
+  if (p.gate && (p.gate->converged || !p.gate->accepted)) return;
+  __shared__ TileSmem<float> sm;
+  __shared__ PipeStage stg[kStages];
+  __shared__ __align__(8) unsigned long long full[kStages], empty[kStages];
+  __shared__ int abort_flag;
+  float* stage_buf = reinterpret_cast<float*>(solve_dsm);
+  if (threadIdx.x == 0) {
+    for (int k = 0; k < kStages; ++k) {
+      mbar_init(&full[k], 1);
+      mbar_init(&empty[k], 1);
+    }
+    abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();   // the only barrier of all 288 threads: the mbarriers are ready
+  const unsigned long long per = (unsigned long long)p.ntiles + gridDim.x;
+  // stage waits outlast a dependency wait (~1 s), which a tile may sit in
+  constexpr unsigned long long kStageWaitNs = 4000000000ull;
+  if (threadIdx.x >= kThreads) {
+    // ---------------------------------------------------------------- producer
+    if (threadIdx.x != kThreads) return;
+    for (int k = 0;; ++k) {
+      const int st = k % kStages;
+      const unsigned ph = (unsigned)(k / kStages) & 1u;
+      if (k >= kStages && !mbar_wait(&empty[st], ph ^ 1u, kStageWaitNs)) {
+        atomicOr(p.err, DEV_ERR_TIMEOUT);
+        return;   // the body warps time out on this stage in turn
+      }
+      PipeStage& sg = stg[st];
+      const unsigned long long t = atomicAdd(p.gticket, 1ull);
+      const int64_t tile = (int64_t)(t % per);
+      if (tile >= p.ntiles || *(volatile int*)&abort_flag) {
+        sg.tile = -1;
+        mbar_arrive(&full[st]);
+        return;
+      }
+      sg.tl = load_tile(p.tiles, tile);
+      sg.tile = tile;
+      sg.epoch = t / per;
+      const float* src = p.Qs + sg.tl.soff;
+      const uint32_t bytes = (uint32_t)sg.tl.sbytes;
+      float* dst = stage_buf + (size_t)st * kTileElems;
+      const bool ok = bytes > 0u && bytes <= (uint32_t)kStreamBytes && !(bytes & 15u) &&
+                      !(smem_u32(dst) & 15u) && !(reinterpret_cast<uintptr_t>(src) & 15u);
+      sg.copied = ok ? 1 : 0;
+      if (!ok) {
+        atomicOr(p.err, DEV_ERR_LAYOUT);   // nothing copied: the tile skips its products
+        mbar_arrive(&full[st]);
+        continue;
+      }
+      mbar_arrive_tx(&full[st], bytes);
+      asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                   ::"r"(smem_u32(dst)), "l"(src), "r"(bytes), "r"(smem_u32(&full[st]))
+                   : "memory");
+    }
+  }
+  // ------------------------------------------------------------------ body warps
+  for (int k = 0;; ++k) {
+    const int st = k % kStages;
+    const unsigned ph = (unsigned)(k / kStages) & 1u;
+    if (!mbar_wait(&full[st], ph, kStageWaitNs)) {
+      // the stage's copy may still be writing shared memory: it reads a source
+      // range checked by the producer, so it completes; wait for it once more,
+      // bounded, before the CTA retires
+      if (threadIdx.x == 0) {
+        atomicOr(p.err, DEV_ERR_TIMEOUT);
+        abort_flag = 1;
+      }
+      mbar_wait(&full[st], ph, 2 * kStageWaitNs);
+      return;
+    }
+    const PipeStage& sg = stg[st];
+    if (sg.tile < 0) return;
+    const SolveTile tl = sg.tl;
+    run_tile<float>(p, tl, sg.tile, sg.epoch, sm, sg.copied ? stage_buf + (size_t)st * kTileElems : nullptr);
+    body_sync();   // every body thread is done with the stage and its descriptor
+    if (threadIdx.x == 0) mbar_arrive(&empty[st]);
   }
 }
 
@@ -852,16 +910,16 @@ size_t solve_partial_bytes(const SolveSchedule& S) {
   return (S.fwd.size() + S.bwd.size()) * (size_t)kPart * sizeof(double);
 }
 
-// CTAs per SM of the FP32 variant.  Both precisions launch this many CTAs per
-// SM, so every solve consumes the same number of tickets; the FP64 variant has
-// fewer resident at a time, which the ticket order tolerates (a CTA draws
-// tickets only once it runs).
+// CTAs per SM of the FP32 (pipelined) kernel.  Both precisions launch this many
+// CTAs per SM, so every solve consumes the same number of tickets; the FP64
+// kernel has fewer resident at a time, which the ticket order tolerates (a CTA
+// draws tickets only once it runs).
 int solve_persistent_occupancy() {
-  // the FP32 kernel's streamed tile buffer; set on the current device (meshes and
-  // servers call this on their device before any solve)
-  cudaFuncSetAttribute(solve_persistent_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, kStreamBytes);
+  // the FP32 kernel's stages; set on the current device (meshes and servers call
+  // this on their device before any solve)
+  cudaFuncSetAttribute(solve_pipe_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kStages * kStreamBytes);
   int occ = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, solve_persistent_kernel<float>, kThreads, kStreamBytes);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, solve_pipe_kernel, kPipeThreads, kStages * kStreamBytes);
   return std::max(1, occ);
 }
 
@@ -910,8 +968,8 @@ cudaError_t solve_A(const MeshImpl* m, const IterState* gate, const double* b, d
     --m->test_stall_solves;
   }
   const unsigned grid = (unsigned)std::min<int64_t>(m->solve_grid, ntiles);
-  if (f32) solve_persistent_kernel<float><<<grid, kThreads, kStreamBytes, st>>>(p);
-  else solve_persistent_kernel<double><<<grid, kThreads, 0, st>>>(p);
+  if (f32) solve_pipe_kernel<<<grid, kPipeThreads, kStages * kStreamBytes, st>>>(p);
+  else solve_persistent_kernel<<<grid, kThreads, 0, st>>>(p);
   return cudaGetLastError();
 }
 

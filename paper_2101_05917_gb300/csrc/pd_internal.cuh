@@ -31,6 +31,13 @@ size_t mesh_device_bytes(pd_mesh m);
     }                                                                            \
   } while (0)
 
+// Local-step precision beside PD_PREC_FP64 / PD_PREC_MIXED (internal): the FP32
+// local step with the displacement gradient H = F - I and the Green strain formed
+// in FP64, so its stresses stay accurate relative to the strain under large
+// rotations (hexahedra; the tetrahedral rule runs the plain FP32 step).
+constexpr int kPrecMixedAcc = PD_PREC_MIXED_STRAIN;
+inline bool local_is_fp32(int precision) { return precision == PD_PREC_MIXED || precision == kPrecMixedAcc; }
+
 // Device status bits raised by kernels (integer atomicOr; never on data).
 enum : int {
   DEV_ERR_NOT_SPD = 1,
@@ -159,9 +166,10 @@ struct MeshImpl {
   cudaStream_t cap_stream = nullptr;
   // [direction][precision][variant]: variant 1 holds one iteration fewer (profiled
   // chunks launch their first iteration directly, with timing events)
-  cudaGraphExec_t iter_graph[2][2][2] = {};
-  bool iter_graph_act[2][2][2] = {};
-  int64_t iter_graph_counts[2][2][2][3] = {};   // kernels, solves, local steps per replay
+  // [direction][local-step precision: FP64, MIXED, kPrecMixedAcc][variant]
+  cudaGraphExec_t iter_graph[2][3][2] = {};
+  bool iter_graph_act[2][3][2] = {};
+  int64_t iter_graph_counts[2][3][2][3] = {};   // kernels, solves, local steps per replay
   // complementarity contact (contact.cu): A^-1 columns of the candidate nodes and
   // the current contact set
   int64_t factor_gen = 0;              // bumped by every factorisation

@@ -84,18 +84,31 @@ struct SVD3 {
   T sm1[3];   // sig - 1, accurate at small strain
 };
 
-template <typename T>
-__device__ __forceinline__ void svd3_from_H(const T (&H)[3][3], SVD3<T>& o) {
-  T E[3][3];
+// Green strain E = F^T F - I = H + H^T + H^T H from H = F - I
+template <typename S>
+__device__ __forceinline__ void green_strain(const S (&H)[3][3], S (&E)[3][3]) {
 #pragma unroll
   for (int i = 0; i < 3; ++i)
 #pragma unroll
     for (int j = 0; j < 3; ++j) {
-      T v = H[i][j] + H[j][i];
+      S v = H[i][j] + H[j][i];
 #pragma unroll
       for (int k = 0; k < 3; ++k) v += H[k][i] * H[k][j];
       E[i][j] = v;
     }
+}
+
+// SVD of F = I + H given H and its Green strain E (which svd3_from_H forms in T;
+// a caller may form it in higher precision: under a large rotation H is of the
+// order of the rotation angle while E is of the order of the strain, and the
+// cancellation in H + H^T + H^T H then costs the bits that separate the two)
+template <typename T>
+__device__ __forceinline__ void svd3_from_HE(const T (&H)[3][3], const T (&Ein)[3][3], SVD3<T>& o) {
+  T E[3][3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) E[i][j] = Ein[i][j];
   T V[3][3] = {{T(1), T(0), T(0)}, {T(0), T(1), T(0)}, {T(0), T(0), T(1)}};
   const T nrm2 = E[0][0] * E[0][0] + E[1][1] * E[1][1] + E[2][2] * E[2][2] +
                  T(2) * (E[0][1] * E[0][1] + E[0][2] * E[0][2] + E[1][2] * E[1][2]);
@@ -152,6 +165,13 @@ __device__ __forceinline__ void svd3_from_H(const T (&H)[3][3], SVD3<T>& o) {
   for (int i = 0; i < 3; ++i)
 #pragma unroll
     for (int j = 0; j < 3; ++j) { o.U[i][j] = U[i][j]; o.V[i][j] = V[i][j]; }
+}
+
+template <typename T>
+__device__ __forceinline__ void svd3_from_H(const T (&H)[3][3], SVD3<T>& o) {
+  T E[3][3];
+  green_strain<T>(H, E);
+  svd3_from_HE<T>(H, E, o);
 }
 
 // out += c * U diag(d) V^T   (c scalar)

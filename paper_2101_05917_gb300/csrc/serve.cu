@@ -315,7 +315,8 @@ void run_job(pd_server s, Slot& sl, const Job& j, Done& d) {
   pd_solver_opts o = j.opts;
   o.checkpoint_every = 0;
   o.profile = 0;
-  o.step_ms = nullptr;   // the request's host pointer does not outlive the submit call
+  o.step_ms = nullptr;   // the request's host pointers do not outlive the submit call
+  o.step_iters = nullptr;
   pd_stats fs{}, bs{};
   st = pd_forward(m, sl.x0.p, sl.v0.p, fext, act, j.mu, j.T, &o, sl.xs.p, sl.vs.p, &fs, q);
   r.fwd_iters = fs.fwd_iters;

@@ -79,3 +79,35 @@ def test_c5_checkpoints_mixed_vs_fp64_and_fd(c5):
         an = float(np.sum(gd * d))
         print(f"C5 FD direction {k}: fd {fd:.10e} adjoint {an:.10e}")
         assert abs(fd - an) <= 1e-4 * abs(an)
+
+
+def test_c5_benchmark_configuration_matches_fp64_over_50_steps(c5):
+    """The configuration bench.py times (mixed precision, tol 1e-7, checkpoints every
+    25 steps) over the first 50 steps against the FP64 path at tol 1e-10 (the FP64
+    path is pinned to the oracle on the small meshes; no CPU oracle finishes at this
+    size).  Gates: relative position error 1e-5, displacement-relative error and
+    element-wise maximum (scaled by the largest displacement) 1e-4, relative
+    gradient error 1e-4 for the traction field and the initial velocity."""
+    sc, mesh, wc, _ = c5
+    T50 = 50
+    f, lw = _t(sc.f_ext), _t(sc.loss_w)
+
+    def run(prec, tol, K):
+        mesh.factorize(wc, None, None, None, h=sc.h, gravity=tuple(sc.gravity), precision=prec)
+        o = api.solver_opts(tol_fwd=tol, tol_bwd=tol, max_iter_fwd=5000, max_iter_bwd=5000, checkpoint_every=K)
+        r = mesh.forward(_t(sc.x0), _t(sc.v0), T50, f_ext=f, opts=o)
+        g = mesh.backward(r, T50, lw, f_ext=f, opts=o, want=("fext", "v0"))
+        return r.x[-1].cpu().numpy(), g["fext"].cpu().numpy(), g["v0"].cpu().numpy()
+    x_ref, gf_ref, gv_ref = run(N.PD_PREC_FP64, 1e-10, 0)
+    x, gf, gv = run(N.PD_PREC_MIXED, 1e-7, 25)
+    d = x - x_ref
+    u = x_ref - sc.x0
+    pos = np.linalg.norm(d) / np.linalg.norm(x_ref)
+    disp = np.linalg.norm(d) / np.linalg.norm(u)
+    emax = np.abs(d).max() / np.abs(u).max()
+    ef = np.linalg.norm(gf - gf_ref) / np.linalg.norm(gf_ref)
+    ev = np.linalg.norm(gv - gv_ref) / np.linalg.norm(gv_ref)
+    print(f"C5 50 steps, mixed tol 1e-7 vs FP64 tol 1e-10: position {pos:.2e}, displacement-relative {disp:.2e}, "
+          f"max {emax:.2e}; grad f_ext {ef:.2e}, grad v0 {ev:.2e}")
+    assert pos <= 1e-5 and disp <= 1e-4 and emax <= 1e-4
+    assert ef <= 1e-4 and ev <= 1e-4

@@ -85,3 +85,36 @@ def test_global_solve_matches_direct_solve(name, leaf, prec):
     torch.cuda.synchronize()
     assert rel(out.cpu().numpy(), ref) < TOL[prec]
     mesh.close()
+
+
+@pytest.mark.parametrize("name", ["c1", "beam_vol", "quad9"])
+def test_strain_accurate_local_step_under_large_rotation(name):
+    """A random rigid rotation with a strain of ~1e-4 on top: H = F - I is of the
+    order of the rotation while the stresses are of the order of the strain.  The
+    strain-accurate FP32 local step (F - I and the Green strain in FP64) matches the
+    oracle's gradient and Hessian product within the FP32 tolerance; the plain FP32
+    step's error is printed beside it (it grows with rotation / strain)."""
+    sc = _scenes()[name]
+    model = Model(sc)
+    mesh = make_mesh(sc, precision=N.PD_PREC_MIXED)
+    act = None if sc.act is None else sc.act[0]
+    x = deformed(sc, scale=1e-4, seed=11)
+    g_ref = model.grad_E(x, act)
+    e_ref = model.energy(x, act)
+    ta = None if act is None else T(act)
+    g_acc, e_acc = mesh.local_step(T(x), ta, precision=N.PD_PREC_MIXED_STRAIN)
+    g_32, _ = mesh.local_step(T(x), ta, precision=N.PD_PREC_MIXED)
+    torch.cuda.synchronize()
+    err_acc, err_32 = rel(g_acc.cpu().numpy(), g_ref), rel(g_32.cpu().numpy(), g_ref)
+    print(f"{name}: strain-accurate {err_acc:.2e}, plain FP32 {err_32:.2e}")
+    assert err_acc < TOL[N.PD_PREC_MIXED]
+    assert abs(e_acc.item() - e_ref) <= TOL[N.PD_PREC_MIXED] * abs(e_ref)
+    H = model.hessian(x, act)[model.free_dofs][:, model.free_dofs]
+    v = np.random.default_rng(3).standard_normal(x.shape)
+    v[model.dirichlet] = 0
+    ref = np.zeros_like(v)
+    ref[model.free_nodes] = (H @ v[model.free_nodes].ravel()).reshape(-1, 3)
+    out = mesh.hessian_vector(T(x), T(v), ta, precision=N.PD_PREC_MIXED_STRAIN)
+    torch.cuda.synchronize()
+    assert rel(out.cpu().numpy(), ref) < TOL[N.PD_PREC_MIXED]
+    mesh.close()

@@ -1,14 +1,14 @@
 """The triangular solve's tile schedule and its streamed FP32 layout, from the host
 analysis (no GPU).  Each tile's panel values reach shared memory by one bulk copy,
 which must start on a 16-byte boundary and move a multiple of 16 bytes, at most the
-64 KB tile buffer: a copy that breaks these rules is an illegal instruction on the
+48 KB tile stage: a copy that breaks these rules is an illegal instruction on the
 GPU, so they are checked here for every tile of every test mesh, together with the
 tiles lying back to back.  The schedule itself must equal a re-derivation from its
 definition: per supernode (nc columns, nr rows), forward tiles of R rows (R = 256
-for nc <= 64, 128 for nc <= 128, else 64) by 256/R column groups of 64, where a row
+for nc <= 48, 128 for nc <= 96, else 64) by 256/R column groups of 48, where a row
 block inside the triangular L11^-1 block only takes columns up to its last row;
 backward tiles of BC columns (the narrowest of 8/16/32/64 covering nc, 64 at most)
-by min(16384/BC, 1024) rows, starting at the row block that holds the tile's first
+by min(12288/BC, 1024) rows, starting at the row block that holds the tile's first
 column; forward tiles by ascending tree level, backward tiles by descending level,
 supernodes in level-list order.  Streamed copy per tile: forward [group][column <
 kmax][row < rv] with kmax the columns of the tile's last row inside its first
@@ -40,18 +40,18 @@ def _derive(m):
         lev_b = []
         for s in ll[lp[L]:lp[L + 1]]:
             nc, nr = int(sf[s + 1] - sf[s]), int(rp[s + 1] - rp[s])
-            R = 256 if nc <= 64 else (128 if nc <= 128 else 64)
+            R = 256 if nc <= 48 else (128 if nc <= 96 else 64)
             G = 256 // R
             for r0 in range(0, nr, R):
                 cmax = r0 + R if r0 + R <= nc else nc
                 rv = min(R, nr - r0)
                 rmax = r0 + rv - 1
                 cend = min(nc, rmax + 1) if rmax < nc else nc
-                for c0 in range(0, cmax, 64 * G):
-                    kmax = max(0, min(64, cend - c0))
+                for c0 in range(0, cmax, 48 * G):
+                    kmax = max(0, min(48, cend - c0))
                     fwd.append((s, KINDS_F[R], r0, c0, G * kmax * rv, kmax))
             BC = 64 if nc > 32 else (32 if nc > 16 else (16 if nc > 8 else 8))
-            BR = min(16384 // BC, 1024)
+            BR = min(12288 // BC, 1024)
             for c0 in range(0, nc, BC):
                 for r0 in range((c0 // BR) * BR, nr, BR):
                     rn = min(BR, nr - r0)
@@ -82,6 +82,6 @@ def test_solve_tiles_match_definition_and_copy_rules(native, case):
     assert np.array_equal(got, want)
     soff, sbytes = got[:, 4], got[:, 5]
     assert np.all(soff % 4 == 0)                          # 16-byte aligned starts (floats)
-    assert np.all(sbytes % 16 == 0) and np.all(sbytes > 0) and np.all(sbytes <= 65536)
+    assert np.all(sbytes % 16 == 0) and np.all(sbytes > 0) and np.all(sbytes <= 49152)
     assert np.array_equal(soff[1:], soff[:-1] + sbytes[:-1] // 4)   # back to back
     m.close()
