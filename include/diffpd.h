@@ -63,7 +63,13 @@ enum {
      that the stresses stay accurate relative to the strain under large rotations
      (hexahedra; the tetrahedral rule runs the plain FP32 step).  The mixed-precision
      rollouts switch to it when the plain FP32 residual stops decreasing. */
-  PD_PREC_MIXED_STRAIN = 2
+  PD_PREC_MIXED_STRAIN = 2,
+  /* pd_local_step / pd_hessian_vector only: FP64-accurate results from an FP32 SVD
+     of the FP64 strain whose rotation (and its derivative) is refined in FP64
+     without eigenvectors; hexahedra with the corotated and muscle energies (a mesh
+     with the volume energy, or the tetrahedral rule, runs the plain FP64 step).
+     The mixed-precision rollouts use it for their FP64 convergence checks. */
+  PD_PREC_FP64_REFINED = 3
 };
 
 typedef struct pd_mesh_s* pd_mesh;
@@ -128,14 +134,18 @@ enum {
   PD_EXPORT_REL = 8,       /* positions of each supernode's below rows in its parent */
   PD_EXPORT_LEVEL_PTR = 9, /* (n_levels+1) into PD_EXPORT_LEVEL_LIST */
   PD_EXPORT_LEVEL_LIST = 10, /* (n_snodes) supernodes grouped by level, ascending ids */
-  PD_EXPORT_SOLVE_TILES = 11 /* 7 per triangular-solve tile, in the persistent solve's order
+  PD_EXPORT_SOLVE_TILES = 11 /* 10 per triangular-solve tile, in the persistent solve's order
                                 (forward tiles by ascending level, then backward tiles by
-                                descending level): supernode, tile kind (0-2 forward tiles of
-                                256/128/64 rows, 3-6 backward tiles of 64/32/16/8 columns),
-                                first row (forward) or column (backward), first column or
-                                row, offset of its FP32 streamed copy in floats, its bytes,
-                                and the leading dimension of that copy (forward: columns
-                                per thread group; backward: rows) */
+                                descending level): supernode, kind (0-2 forward row blocks of
+                                256/128/64 rows, 3-6 backward column blocks of 64/32/16/8
+                                columns), first row (forward) or column (backward) of its
+                                block, index of its first chunk within the block, its chunks
+                                (forward: column ranges of 48 columns per row group; backward:
+                                row ranges of min(12288 / columns, 512) rows), offset of its
+                                first chunk in the FP32 streamed copy (floats), bytes of each
+                                chunk but its last, bytes of its last chunk, the last chunk's
+                                columns (forward; they fill the row groups in order) or rows
+                                (backward), and the tiles of its block */
 };
 pd_status pd_mesh_export(pd_mesh m, int32_t what, int64_t* host_out, int64_t capacity,
                          int64_t* count);
@@ -237,6 +247,16 @@ typedef struct {
 pd_status pd_forward(pd_mesh m, const double* x0, const double* v0, const double* f_ext,
                      const double* act, double mu, int32_t T, const pd_solver_opts* opts,
                      double* x_traj, double* v_traj, pd_stats* stats, void* stream);
+
+/* Checkpoint interval for a rollout of T steps (Sec. 4 back-propagates through
+ * every step; states that do not fit are recomputed per segment).  The budget is
+ * mem_cap_bytes, or (0) four fifths of the device's free memory.  *checkpoint_every
+ * = 0 when all T+1 states (x and v, 48 n bytes each) fit; otherwise the smallest
+ * K > 1 dividing T for which the T/K + 1 checkpointed states (the caller's x_traj,
+ * v_traj) plus the K + 1 states of one recomputed segment (pd_backward's buffer)
+ * fit.  PD_ERR_OOM when no K fits; PD_ERR_INVALID_ARG for a host-only mesh
+ * without a cap.  Does not allocate. */
+pd_status pd_plan_checkpoints(pd_mesh m, int32_t T, size_t mem_cap_bytes, int32_t* checkpoint_every);
 
 /* Backward rollout (Sec. 4, Alg. 2 with L-BFGS; Eqns 10-12 per step).
  * x_traj, v_traj, f_ext, act, mu, T: exactly as given to / produced by pd_forward

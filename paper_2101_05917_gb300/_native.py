@@ -30,6 +30,7 @@ STATUS_NAMES = {0: "PD_OK", 1: "PD_ERR_INVALID_ARG", 2: "PD_ERR_OOM", 3: "PD_ERR
 PD_PREC_FP64 = 0
 PD_PREC_MIXED = 1
 PD_PREC_MIXED_STRAIN = 2
+PD_PREC_FP64_REFINED = 3
 PD_ELEM_HEX8 = 0
 PD_ELEM_TET6 = 1
 ELEMENT_RULES = {"hex8": PD_ELEM_HEX8, "tet6": PD_ELEM_TET6}
@@ -109,7 +110,7 @@ class Result(ctypes.Structure):
 
 
 SYMBOLS = ["pd_create_mesh", "pd_mesh_destroy", "pd_mesh_query", "pd_mesh_export", "pd_factorize",
-           "pd_forward", "pd_backward", "pd_local_step", "pd_hessian_vector", "pd_solve_A",
+           "pd_forward", "pd_backward", "pd_plan_checkpoints", "pd_local_step", "pd_hessian_vector", "pd_solve_A",
            "pd_local_step_noalloc", "pd_contact_prepare", "pd_contact_set", "pd_solve_A_contact", "pd_contact_step_set", "pd_serve_create", "pd_serve_submit", "pd_serve_poll", "pd_serve_release", "pd_serve_drain",
            "pd_serve_destroy", "pd_last_error"]
 
@@ -143,6 +144,8 @@ def lib() -> ctypes.CDLL:
                               ctypes.POINTER(SolverOpts), vp, vp, vp, vp, vp, vp, vp, vp,
                               ctypes.POINTER(Stats), vp]
     L.pd_backward.restype = st
+    L.pd_plan_checkpoints.argtypes = [vp, ctypes.c_int32, ctypes.c_size_t, ctypes.POINTER(ctypes.c_int32)]
+    L.pd_plan_checkpoints.restype = st
     L.pd_local_step.argtypes = [vp, vp, vp, ctypes.c_int32, vp, vp, vp]
     L.pd_local_step.restype = st
     L.pd_hessian_vector.argtypes = [vp, vp, vp, vp, ctypes.c_int32, vp, vp]

@@ -46,7 +46,9 @@ def solver_opts(tol_fwd=1e-9, tol_bwd=1e-9, max_iter_fwd=500, max_iter_bwd=500, 
                 checkpoint_every=0, check_every=4, profile=False, warm_start=False, graphs=True,
                 complementarity=False, step_ms: Optional[np.ndarray] = None,
                 step_iters: Optional[np.ndarray] = None) -> N.SolverOpts:
-    """step_ms: optional float64 host array of T entries receiving the per-step
+    """checkpoint_every: 0 = every state stored, K > 0 = states 0, K, 2K, ..., -1 =
+    planned by PDMesh.forward from its mem_cap (pd_plan_checkpoints).
+    step_ms: optional float64 host array of T entries receiving the per-step
     wall time (forward, then the backward adds its own); step_iters: optional
     int32 host array of T entries receiving the per-step iterations (forward, then
     the backward's adjoint iterations); the caller keeps both alive."""
@@ -69,6 +71,7 @@ class Rollout:
     v: torch.Tensor
     stats: dict
     status: int
+    checkpoint_every: int = 0   # 0: every state stored; K: states 0, K, 2K, ...
 
 
 class PDMesh:
@@ -158,10 +161,25 @@ class PDMesh:
         N.check(N.lib().pd_factorize(self.handle, _ptr(w_corot), _ptr(w_vol), _ptr(w_muscle), _ptr(fiber),
                                      ctypes.byref(o), _stream(stream)), "pd_factorize")
 
+    def plan_checkpoints(self, T, mem_cap=0) -> int:
+        """Checkpoint interval for a T-step rollout: 0 when every state fits in
+        mem_cap bytes (0: four fifths of the free device memory), else the smallest
+        K dividing T whose checkpoints and one recomputed segment fit."""
+        K = ctypes.c_int32()
+        N.check(N.lib().pd_plan_checkpoints(self.handle, int(T), int(mem_cap), ctypes.byref(K)),
+                "pd_plan_checkpoints")
+        return K.value
+
     def forward(self, x0, v0, T, f_ext=None, act=None, mu=0.0, opts=None, stream=None,
-                allow_not_converged=False) -> Rollout:
+                allow_not_converged=False, mem_cap=0) -> Rollout:
+        """With opts.checkpoint_every < 0 the interval is planned from mem_cap
+        (pd_plan_checkpoints) and recorded in the returned Rollout."""
         opts = opts or solver_opts()
         K = opts.checkpoint_every
+        if K < 0:
+            K = self.plan_checkpoints(T, mem_cap)
+            opts = N.SolverOpts.from_buffer_copy(opts)
+            opts.checkpoint_every = K
         S = T + 1 if K <= 0 else T // K + 1
         xs = torch.empty((S, self.n, 3), dtype=torch.float64, device=x0.device)
         vs = torch.empty_like(xs)
@@ -169,12 +187,15 @@ class PDMesh:
         status = N.lib().pd_forward(self.handle, _ptr(x0), _ptr(v0), _ptr(f_ext), _ptr(act), mu, T,
                                     ctypes.byref(opts), _ptr(xs), _ptr(vs), ctypes.byref(st), _stream(stream))
         N.check(status, "pd_forward", allow=(N.PD_ERR_NOT_CONVERGED,) if allow_not_converged else ())
-        return Rollout(xs, vs, st.as_dict(), status)
+        return Rollout(xs, vs, st.as_dict(), status, K)
 
     def backward(self, roll: Rollout, T, dL_dx, dL_dv=None, loss_all_steps=False, f_ext=None, act=None,
                  mu=0.0, opts=None, stream=None, want=("x0", "v0", "fext", "w_corot", "w_vol", "w_muscle",
                                                         "act", "mu"), allow_not_converged=False):
         opts = opts or solver_opts()
+        if opts.checkpoint_every < 0:   # planned by forward: the rollout carries it
+            opts = N.SolverOpts.from_buffer_copy(opts)
+            opts.checkpoint_every = roll.checkpoint_every
         dev = roll.x.device
         out = {}
         # the library reads loss_states blocks of (n, 3): check the caller's shapes here

@@ -86,7 +86,7 @@ class _Rollout(torch.autograd.Function):
         sim.ensure_factor(wc, wv, wm, fib)
         opts = api.solver_opts(**sim.opts)
         roll = sim.mesh.forward(x0, v0, T, f_ext=f_ext, act=act, mu=float(mu), opts=opts)
-        ctx.sim, ctx.T = sim, T
+        ctx.sim, ctx.T, ctx.K = sim, T, roll.checkpoint_every
         ctx.has = tuple(t is not None for t in (f_ext, act, w_corot, w_vol, w_muscle))
         ctx.save_for_backward(roll.x, roll.v, f_ext if f_ext is not None else roll.x.new_empty(0),
                               act if act is not None else roll.x.new_empty(0), wc, wv, wm, fib, mu)
@@ -105,14 +105,14 @@ class _Rollout(torch.autograd.Function):
             gx = torch.zeros_like(xs)
         # with checkpointing the forward output holds states 0, K, 2K, ... only: their
         # gradients go to those steps of the (T+1)-state loss gradient, zeros elsewhere
-        K = int(sim.opts.get("checkpoint_every", 0) or 0)
+        K = ctx.K
         gx = _every_state(gx, T, K)
         gv = None if gv is None else _every_state(gv, T, K)
         need = ctx.needs_input_grad
         names = [(3, "x0"), (4, "v0"), (5, "fext"), (6, "act"), (7, "w_corot"), (8, "w_vol"), (9, "w_muscle"),
                  (10, "mu")]
         want = tuple(name for i, name in names if need[i])
-        roll = api.Rollout(xs, vs, {}, N.PD_OK)
+        roll = api.Rollout(xs, vs, {}, N.PD_OK, K)
         opts = api.solver_opts(**sim.opts)
         out = sim.mesh.backward(roll, T, gx, dL_dv=gv, loss_all_steps=True, f_ext=f_ext, act=act, mu=float(mu),
                                 opts=opts, want=want)

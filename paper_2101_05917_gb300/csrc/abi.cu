@@ -150,8 +150,6 @@ pd_status ensure_workspace(MeshImpl* m, int lbfgs_m) {
     PD_CUDA_TRY(dalloc(m, &w.flags, 4));
     PD_CUDA_TRY(cudaMemset(w.flags, 0, 4 * sizeof(int)));
     PD_CUDA_TRY(dalloc(m, (double**)&w.solve_u, (size_t)nf3));
-    const int64_t wrows = m->h.rel_ptr.empty() ? 0 : m->h.rel_ptr.back();
-    PD_CUDA_TRY(dalloc(m, (double**)&w.solve_W, (size_t)std::max<int64_t>(3 * wrows, 3)));
   }
   if (lbfgs_m > w.lbfgs_m) {
     // history buffers grow monotonically; old ones stay in the allocation list
@@ -165,7 +163,7 @@ pd_status ensure_workspace(MeshImpl* m, int lbfgs_m) {
 // The persistent solve counts tickets and finished blocks monotonically; a fresh
 // start at every public call also recovers from an aborted solve.
 cudaError_t reset_solve_counters(MeshImpl* m, cudaStream_t s) {
-  const size_t n = 1 + (size_t)(m->sched.n_fwd_out + m->sched.n_bwd_out) + 2 * (size_t)m->h.ns;
+  const size_t n = 1 + 2 * (size_t)m->h.ns + m->sched.all.size();
   return cudaMemsetAsync(m->solve_counters, 0, sizeof(unsigned long long) * n, s);
 }
 
@@ -403,7 +401,7 @@ namespace {
 
 cudaGraphExec_t iteration_graph(Ctx& c, int dir, int prec, bool with_act, int variant) {
   MeshImpl* m = c.m;
-  const int pi = prec == PD_PREC_MIXED ? 1 : (prec == kPrecMixedAcc ? 2 : 0);
+  const int pi = prec == PD_PREC_MIXED ? 1 : (prec == kPrecMixedAcc ? 2 : (prec == kPrecRefined ? 3 : 0));
   const int iters = kGraphIters - variant;
   cudaGraphExec_t& g = m->iter_graph[dir][pi][variant];
   if (g && m->iter_graph_act[dir][pi][variant] == with_act) return g;
@@ -463,7 +461,7 @@ pd_status run_iterations(Ctx& c, int dir, int prec, const double* act, const dou
     cudaGraphExec_t g = iteration_graph(c, dir, prec, act != nullptr, variant);
     if (g) {
       const int64_t* gc =
-          c.m->iter_graph_counts[dir][prec == PD_PREC_MIXED ? 1 : (prec == kPrecMixedAcc ? 2 : 0)][variant];
+          c.m->iter_graph_counts[dir][prec == PD_PREC_MIXED ? 1 : (prec == kPrecMixedAcc ? 2 : (prec == kPrecRefined ? 3 : 0))][variant];
       for (; done + kGraphIters <= count; done += kGraphIters) {
         PD_CUDA_TRY(cudaGraphLaunch(g, c.s));
         c.launches += gc[0];
@@ -643,7 +641,8 @@ pd_status forward_step(Ctx& c, const double* act_t, const double* fext_int, doub
   c.launches += 2;
   // MIXED: iterate with FP32 local steps; when the FP32 residual meets the
   // tolerance, re-evaluate the gradient at the accepted point with an FP64 local
-  // step (the convergence check).  If it fails the FP32 iteration continues from
+  // step (the convergence check; kPrecRefined: FP64-accurate from an FP32 SVD
+  // refined in FP64).  If it fails the FP32 iteration continues from
   // the FP64 gradient; after kMaxChecks failed checks the FP64 local step is used
   // for the remaining iterations.  When the FP32 residual stops halving above the
   // tolerance (its rounding floor: under large rotations H = F - I is of the order
@@ -678,7 +677,7 @@ pd_status forward_step(Ctx& c, const double* act_t, const double* fext_int, doub
       pd_status er = run_iterations(c, 0, prec, act_c, nullptr, chunk);
       if (er != PD_OK) return er;
       launched += chunk;
-      if (mixed && prec == PD_PREC_FP64) fp64_launched += chunk;
+      if (mixed && prec == kPrecRefined) fp64_launched += chunk;
       if (chunk > 0) {
         clear_checked_kernel<<<1, 1, 0, c.s>>>(w.st);
         c.launches += 1;
@@ -692,14 +691,14 @@ pd_status forward_step(Ctx& c, const double* act_t, const double* fext_int, doub
         break;
       }
       if (sh.converged) {
-        if (mixed && prec != PD_PREC_FP64 && !sh.hit_max && !sh.fp64_checked) {
+        if (mixed && prec != kPrecRefined && !sh.hit_max && !sh.fp64_checked) {
           // FP64 convergence check at the accepted point
           if (fp32_end < 0) fp32_end = sh.iters;
           ++checks;
-          if (checks > kMaxChecks) prec = PD_PREC_FP64;
+          if (checks > kMaxChecks) prec = kPrecRefined;
           force_accept_kernel<<<1, 1, 0, c.s>>>(w.st);
           copy_kernel<<<c.vb, 256, 0, c.s>>>(c.n3f, w.x, w.xt);
-          pd_status e2 = launch_fwd_iteration(c, PD_PREC_FP64, act_c);
+          pd_status e2 = launch_fwd_iteration(c, kPrecRefined, act_c);
           if (e2 != PD_OK) return e2;
           fp64_launched += 1;
           mark_checked_kernel<<<1, 1, 0, c.s>>>(w.st);
@@ -711,7 +710,7 @@ pd_status forward_step(Ctx& c, const double* act_t, const double* fext_int, doub
         break;
       }
       // FP32 floor above the tolerance: no halving of the residual over three polls
-      if (mixed && prec != PD_PREC_FP64 && sh.ref2 > 0) {
+      if (mixed && prec != kPrecRefined && sh.ref2 > 0) {
         const double rel = std::sqrt(sh.gn2_acc / sh.ref2);
         if (rel < 0.5 * best_rel) {
           best_rel = rel;
@@ -722,7 +721,7 @@ pd_status forward_step(Ctx& c, const double* act_t, const double* fext_int, doub
             prec = kPrecMixedAcc;
             used_acc = true;
           } else {
-            prec = PD_PREC_FP64;
+            prec = kPrecRefined;
           }
           best_rel = rel;
           stall = 0;
@@ -850,6 +849,8 @@ pd_status backward_step(Ctx& c, const double* xnext, const double* xt_, const do
   // product and replaces it (iterative refinement); the iteration continues
   // until the true residual meets the tolerance.
   const int prec = m->precision == PD_PREC_MIXED ? PD_PREC_MIXED : PD_PREC_FP64;
+  // the FP64 true residual: refined from the FP32 SVD in mixed precision
+  const int p64 = m->precision == PD_PREC_MIXED ? kPrecRefined : PD_PREC_FP64;
   int launched = 0, fp64_launched = 0, checks = 0;
   int chunk = std::max(guess, 1);
   const int hard_cap = 3 * c.o.max_iter_bwd + 64;
@@ -878,9 +879,9 @@ pd_status backward_step(Ctx& c, const double* xnext, const double* xt_, const do
         info.converged = false;
         break;
       }
-      LocalArgs la{m, nullptr, xnext, w.z, act_t, PD_PREC_FP64};
+      LocalArgs la{m, nullptr, xnext, w.z, act_t, p64};
       PD_CUDA_TRY(launch_element_hvp(la, w.elembuf, w.flags, c.s));
-      PD_CUDA_TRY(launch_gather_hvp(m, nullptr, w.elembuf, PD_PREC_FP64, xnext, w.z, nullptr, w.Hd, c.pg, c.s));
+      PD_CUDA_TRY(launch_gather_hvp(m, nullptr, w.elembuf, p64, xnext, w.z, nullptr, w.Hd, c.pg, c.s));
       residual_replace_kernel<<<c.vb, 256, 0, c.s>>>(c.vc, w.Hd, w.ax, w.av, inv_h, w.gs, w.q, held);
       fp64_launched += 1;
       c.launches += 3;
@@ -1059,20 +1060,28 @@ pd_status pd_create_mesh(const pd_mesh_desc* desc, pd_mesh* out) {
   build_solve_schedule(h, I.sched);
   {
     const SolveSchedule& S = I.sched;
-    // fixed-width gather slots (max fan-in of the forward-solve assembly)
+    // fixed-width slots per parent position (max fan-in of the forward-solve
+    // assembly): child update row gath[g] of position k goes to slot k w + (g - gath_ptr[k])
     int64_t w = 1;
     for (size_t k = 0; k + 1 < h.gath_ptr.size(); ++k) w = std::max<int64_t>(w, h.gath_ptr[k + 1] - h.gath_ptr[k]);
     I.slot_w = (int)w;
-    std::vector<int32_t> slots((h.gath_ptr.size() - 1) * w, -1);
+    const int64_t wrows = h.rel_ptr.empty() ? 0 : h.rel_ptr.back();
+    std::vector<int32_t> dest((size_t)std::max<int64_t>(wrows, 1), 0);
     for (size_t k = 0; k + 1 < h.gath_ptr.size(); ++k)
-      for (int64_t g = h.gath_ptr[k]; g < h.gath_ptr[k + 1]; ++g) slots[k * w + (g - h.gath_ptr[k])] = h.gath[g];
-    if ((e = upload(&I, &I.gath_slots, slots)) != cudaSuccess) return fail(e);
+      for (int64_t g = h.gath_ptr[k]; g < h.gath_ptr[k + 1]; ++g)
+        dest[h.gath[g]] = (int32_t)(k * w + (g - h.gath_ptr[k]));
+    if ((e = upload(&I, &I.wdest, dest)) != cudaSuccess) return fail(e);
+    const size_t nslot = 3 * (size_t)std::max<int64_t>((int64_t)(h.gath_ptr.size() - 1) * w, 1);
+    if ((e = dalloc(&I, &I.W32, nslot)) != cudaSuccess) return fail(e);
+    if ((e = dalloc(&I, &I.W64, nslot)) != cudaSuccess) return fail(e);
+    if ((e = cudaMemset(I.W32, 0, sizeof(float) * nslot)) != cudaSuccess) return fail(e);
+    if ((e = cudaMemset(I.W64, 0, sizeof(double) * nslot)) != cudaSuccess) return fail(e);
     if ((e = upload(&I, &I.nfb, S.nfb)) != cudaSuccess) return fail(e);
     if ((e = upload(&I, &I.nbb, S.nbb)) != cudaSuccess) return fail(e);
     if ((e = upload(&I, &I.parent, h.parent)) != cudaSuccess) return fail(e);
     if ((e = dalloc(&I, &I.all_tiles, S.all.size())) != cudaSuccess) return fail(e);
     if (!S.all.empty() && (e = cudaMemcpy(I.all_tiles, S.all.data(), sizeof(SolveTile) * S.all.size(), cudaMemcpyHostToDevice)) != cudaSuccess) return fail(e);
-    const size_t ncount = 1 + (size_t)(S.n_fwd_out + S.n_bwd_out) + 2 * (size_t)h.ns;
+    const size_t ncount = 1 + 2 * (size_t)h.ns + S.all.size();
     if ((e = dalloc(&I, &I.solve_counters, ncount)) != cudaSuccess) return fail(e);
     if ((e = cudaMemset(I.solve_counters, 0, sizeof(unsigned long long) * ncount)) != cudaSuccess) return fail(e);
     {
@@ -1082,6 +1091,8 @@ pd_status pd_create_mesh(const pd_mesh_desc* desc, pd_mesh* out) {
       I.solve_grid = sms * solve_persistent_occupancy();
       I.sms = std::max(1, sms);
     }
+    if ((e = dalloc(&I, (char**)&I.ws.solve_partial, std::max<size_t>(solve_partial_bytes(S), 16))) != cudaSuccess)
+      return fail(e);
     // bounded-wait settings and the test hook that makes one wait run out
     if (const char* ev = std::getenv("PD_SOLVE_SPIN_LIMIT")) {
       const long long v = std::atoll(ev);
@@ -1093,7 +1104,6 @@ pd_status pd_create_mesh(const pd_mesh_desc* desc, pd_mesh* out) {
         I.stall_tile = k;
         break;
       }
-    if ((e = dalloc(&I, (char**)&I.ws.solve_partial, solve_partial_bytes(S))) != cudaSuccess) return fail(e);
   }
   I.flevels.assign(h.nlev, FactorLevel{});
   for (int64_t L = 0; L < h.nlev; ++L) {
@@ -1159,6 +1169,42 @@ pd_status pd_mesh_query(pd_mesh m, pd_mesh_info* info) {
   return PD_OK;
 }
 
+pd_status pd_plan_checkpoints(pd_mesh m, int32_t T, size_t mem_cap_bytes, int32_t* checkpoint_every) {
+  if (!m || !checkpoint_every || T < 0) {
+    set_error("pd_plan_checkpoints: null argument or T < 0");
+    return PD_ERR_INVALID_ARG;
+  }
+  const MeshImpl& I = m->impl;
+  size_t budget = mem_cap_bytes;
+  if (budget == 0) {
+    if (I.device < 0) {
+      set_error("pd_plan_checkpoints: a host-only mesh needs an explicit memory cap");
+      return PD_ERR_INVALID_ARG;
+    }
+    DeviceGuard g(I.device);
+    size_t free_b = 0, total_b = 0;
+    PD_CUDA_TRY(cudaMemGetInfo(&free_b, &total_b));
+    budget = free_b / 10 * 8;   // leave a fifth of the free memory to everything else
+  }
+  // bytes of one stored state: x and v, (n, 3) doubles each
+  const double state = 2.0 * 3.0 * 8.0 * (double)I.h.n;
+  if ((double)(T + 1) * state <= (double)budget) {
+    *checkpoint_every = 0;
+    return PD_OK;
+  }
+  // smallest K dividing T whose checkpoints (T/K + 1 states, caller memory) and
+  // recomputed segment (K + 1 states, pd_backward's buffer) fit
+  for (int32_t K = 2; K <= T; ++K) {
+    if (T % K) continue;
+    if ((double)(T / K + 1 + K + 1) * state <= (double)budget) {
+      *checkpoint_every = K;
+      return PD_OK;
+    }
+  }
+  set_error("pd_plan_checkpoints: no checkpoint interval fits the memory cap");
+  return PD_ERR_OOM;
+}
+
 pd_status pd_mesh_export(pd_mesh m, int32_t what, int64_t* host_out, int64_t capacity, int64_t* count) {
   if (!m) {
     set_error("pd_mesh_export: null mesh");
@@ -1185,10 +1231,10 @@ pd_status pd_mesh_export(pd_mesh m, int32_t what, int64_t* host_out, int64_t cap
         build_solve_schedule(h, S);
         sp = &S;
       }
-      v.reserve(7 * sp->all.size());
+      v.reserve(10 * sp->all.size());
       for (const SolveTile& t : sp->all) {
-        const int64_t row[7] = {t.s, t.pad0, t.a, t.b, t.soff, t.sbytes, t.sld};
-        v.insert(v.end(), row, row + 7);
+        const int64_t row[10] = {t.s, t.kind, t.a, t.chunk0, t.nchunks, t.soff, t.cbytes, t.lbytes, t.lld, t.ntile};
+        v.insert(v.end(), row, row + 10);
       }
       break;
     }
@@ -1273,8 +1319,8 @@ pd_status pd_forward(pd_mesh mesh, const double* x0, const double* v0, const dou
     return PD_ERR_INVALID_ARG;
   }
   const pd_solver_opts o = fill_opts(opts);
-  if (o.checkpoint_every > 0 && T % o.checkpoint_every != 0) {
-    set_error("pd_forward: T must be a multiple of checkpoint_every");
+  if (o.checkpoint_every < 0 || (o.checkpoint_every > 0 && T % o.checkpoint_every != 0)) {
+    set_error("pd_forward: checkpoint_every must be >= 0 (pd_plan_checkpoints chooses one) and divide T");
     return PD_ERR_INVALID_ARG;
   }
   MeshImpl* m = &mesh->impl;
@@ -1375,8 +1421,8 @@ pd_status pd_backward(pd_mesh mesh, const double* x_traj, const double* v_traj, 
   const bool loss_all_steps = loss_states == T + 1 && T + 1 != 1;
   const pd_solver_opts o = fill_opts(opts);
   const int K = o.checkpoint_every;
-  if (K > 0 && T % K != 0) {
-    set_error("pd_backward: T must be a multiple of checkpoint_every");
+  if (K < 0 || (K > 0 && T % K != 0)) {
+    set_error("pd_backward: checkpoint_every must be >= 0 and divide T");
     return PD_ERR_INVALID_ARG;
   }
   MeshImpl* m = &mesh->impl;
@@ -1513,7 +1559,8 @@ pd_status pd_local_step(pd_mesh mesh, const double* x, const double* act, int32_
     set_error("pd_local_step: x is required");
     return PD_ERR_INVALID_ARG;
   }
-  if (precision != PD_PREC_FP64 && precision != PD_PREC_MIXED && precision != PD_PREC_MIXED_STRAIN) {
+  if (precision != PD_PREC_FP64 && precision != PD_PREC_MIXED && precision != PD_PREC_MIXED_STRAIN &&
+      precision != PD_PREC_FP64_REFINED) {
     set_error("pd_local_step: unknown precision");
     return PD_ERR_INVALID_ARG;
   }
@@ -1553,7 +1600,8 @@ pd_status pd_hessian_vector(pd_mesh mesh, const double* x, const double* act, co
     set_error("pd_hessian_vector: x, v and Hv are required");
     return PD_ERR_INVALID_ARG;
   }
-  if (precision != PD_PREC_FP64 && precision != PD_PREC_MIXED && precision != PD_PREC_MIXED_STRAIN) {
+  if (precision != PD_PREC_FP64 && precision != PD_PREC_MIXED && precision != PD_PREC_MIXED_STRAIN &&
+      precision != PD_PREC_FP64_REFINED) {
     set_error("pd_hessian_vector: unknown precision");
     return PD_ERR_INVALID_ARG;
   }

@@ -147,10 +147,15 @@ struct ElemParams {
   int* flags;
 };
 
-// ACC (FP32 hexahedra only): H and the Green strain in FP64, the rest in FP32
-template <typename T, int MODE, int RULE = RULE_HEX8, bool ACC = false>
+// ACC (FP32 hexahedra only): H and the Green strain in FP64, the rest in FP32.
+// REF (FP64 hexahedra with the corotated and muscle energies only): the SVD runs
+// in FP32 on the FP64 strain, and the rotation and its derivative are refined to
+// FP64 without eigenvectors (polar_refine / polar_solve); every quantity that
+// enters the gradient or the Hessian product is then FP64-accurate.
+template <typename T, int MODE, int RULE = RULE_HEX8, bool ACC = false, bool REF = false>
 __global__ void __launch_bounds__(kElemThreads, sizeof(T) == 8 ? 1 : (MODE == MODE_FORCE && !ACC ? 3 : 2))
 element_kernel(ElemParams p) {
+  static_assert(!REF || (sizeof(T) == 8 && RULE == RULE_HEX8 && MODE != MODE_PGRAD), "refined: FP64 hexahedra");
   if (p.gate && p.gate->converged) return;
   __shared__ double wsum[kElemThreads / 32];
   __shared__ unsigned arrived;
@@ -242,13 +247,66 @@ element_kernel(ElemParams p) {
   T gwc = T(0), gwv = T(0), gwm = T(0), gact = T(0);
 
   SVD3<T> sv;
-  if constexpr (RULE == RULE_HEX8 && ACC) svd3_from_HE<T>(H, Eacc, sv);
-  else svd3_from_H<T>(H, sv);
-  if (valid && !(sv.sig[2] > T(0))) atomicOr(p.flags, DEV_ERR_INVERTED);
+  double Rr[3][3], Sr[3][3];   // REF: refined rotation and symmetric factor
+  if constexpr (REF) {
+    double Ed[3][3];
+    green_strain<double>(H, Ed);
+    float H32[3][3], E32[3][3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) {
+        H32[i][j] = (float)H[i][j];
+        E32[i][j] = (float)Ed[i][j];
+      }
+    SVD3<float> s32;
+    svd3_from_HE<float>(H32, E32, s32);
+    const bool ok = polar_refine(s32.U, s32.V, H, Rr, Sr);
+    if (valid && (!(s32.sig[2] > 0.0f) || !ok)) atomicOr(p.flags, DEV_ERR_INVERTED);
+  } else {
+    if constexpr (RULE == RULE_HEX8 && ACC) svd3_from_HE<T>(H, Eacc, sv);
+    else svd3_from_H<T>(H, sv);
+    if (valid && !(sv.sig[2] > T(0))) atomicOr(p.flags, DEV_ERR_INVERTED);
+  }
   T M[3][3];
-  if (MODE != MODE_FORCE) rotate_in<T>(sv.U, dF, sv.V, M);
+  if (MODE != MODE_FORCE && !REF) rotate_in<T>(sv.U, dF, sv.V, M);
 
-  if (wc != T(0)) {
+  if constexpr (REF) {
+    if (wc != T(0)) {
+      if (MODE == MODE_FORCE) {
+        // F - R with F = I + H
+        T en = T(0);
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+#pragma unroll
+          for (int j = 0; j < 3; ++j) {
+            const double d = (i == j ? 1.0 : 0.0) + H[i][j] - Rr[i][j];
+            S[i][j] += wc * Vq * d;
+            en += d * d;
+          }
+        energy += T(0.5) * wc * Vq * en;
+      } else {
+        // dF - dR, dR = R skew(w), w = 2 (tr(S) I - S)^-1 axial(skew(R^T dF))
+        double RtdF[3][3], k[3], w[3];
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+#pragma unroll
+          for (int j = 0; j < 3; ++j) RtdF[i][j] = Rr[0][i] * dF[0][j] + Rr[1][i] * dF[1][j] + Rr[2][i] * dF[2][j];
+        skew_axial(RtdF, k);
+        polar_solve(Sr, k, w);
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+          // (R skew(w))_ij = sum_k R_ik skew(w)_kj
+          const double dR0 = Rr[i][1] * w[2] - Rr[i][2] * w[1];
+          const double dR1 = Rr[i][2] * w[0] - Rr[i][0] * w[2];
+          const double dR2 = Rr[i][0] * w[1] - Rr[i][1] * w[0];
+          S[i][0] += wc * Vq * (dF[i][0] - dR0);
+          S[i][1] += wc * Vq * (dF[i][1] - dR1);
+          S[i][2] += wc * Vq * (dF[i][2] - dR2);
+        }
+      }
+    }
+  } else if (wc != T(0)) {
     if (MODE == MODE_FORCE) {
       add_UdVt<T>(S, sv.U, sv.sm1, sv.V, wc * Vq);
       energy += T(0.5) * wc * Vq * (sv.sm1[0] * sv.sm1[0] + sv.sm1[1] * sv.sm1[1] + sv.sm1[2] * sv.sm1[2]);
@@ -260,7 +318,7 @@ element_kernel(ElemParams p) {
       gwc = -Vq * (M[0][0] * sv.sm1[0] + M[1][1] * sv.sm1[1] + M[2][2] * sv.sm1[2]);
     }
   }
-  if (__any_sync(0xffffffffu, wv != T(0))) {
+  if (!REF && __any_sync(0xffffffffu, wv != T(0))) {   // REF runs without the volume energy
     VolProj<T> vp;
     if (volume_project<T>(sv, vp, wv != T(0))) {
       if (MODE == MODE_FORCE) {
@@ -522,6 +580,9 @@ void launch_elem(const MeshImpl* m, int precision, const ElemParams& p, cudaStre
     if (tet) element_kernel<float, MODE, RULE_TET6><<<nb, kElemThreads, 0, s>>>(p);
     else if (precision == kPrecMixedAcc) element_kernel<float, MODE, RULE_HEX8, true><<<nb, kElemThreads, 0, s>>>(p);
     else element_kernel<float, MODE, RULE_HEX8><<<nb, kElemThreads, 0, s>>>(p);
+  } else if (MODE != MODE_PGRAD && precision == kPrecRefined && !tet && !p.wv) {
+    if constexpr (MODE != MODE_PGRAD)
+      element_kernel<double, MODE, RULE_HEX8, false, true><<<nb, kElemThreads, 0, s>>>(p);
   } else {
     if (tet) element_kernel<double, MODE, RULE_TET6><<<nb, kElemThreads, 0, s>>>(p);
     else element_kernel<double, MODE, RULE_HEX8><<<nb, kElemThreads, 0, s>>>(p);

@@ -36,6 +36,9 @@ size_t mesh_device_bytes(pd_mesh m);
 // in FP64, so its stresses stay accurate relative to the strain under large
 // rotations (hexahedra; the tetrahedral rule runs the plain FP32 step).
 constexpr int kPrecMixedAcc = PD_PREC_MIXED_STRAIN;
+// FP64-accurate local step from an FP32 SVD refined in FP64 (hexahedra, corotated +
+// muscle energies; otherwise the plain FP64 step runs)
+constexpr int kPrecRefined = PD_PREC_FP64_REFINED;
 inline bool local_is_fp32(int precision) { return precision == PD_PREC_MIXED || precision == kPrecMixedAcc; }
 
 // Device status bits raised by kernels (integer atomicOr; never on data).
@@ -54,45 +57,49 @@ struct DArr {
   size_t n = 0;
 };
 
-// Solve schedule: per level, ranges of 2D panel tiles.
+// Solve schedule: per level, ranges of tiles.  An output block is one row block
+// of a supernode's panel over all the columns it needs (forward) or one column
+// block over all its rows (backward); its panel values are streamed in chunks
+// (a chunk is what one shared-memory stage holds: at most 256 x 48 entries), and
+// a tile is a run of at most a level-dependent number of consecutive chunks of
+// one block.  A block split into several tiles adds their partial sums in tile
+// order (its last tile to finish does, after an integer ticket).
 struct SolveLevel {
   int64_t fwd_off = 0, fwd_cnt = 0;
   int64_t bwd_off = 0, bwd_cnt = 0;
 };
-// Everything one tile needs, loaded with four 16-byte loads.
+// Everything one tile needs, loaded with eight 16-byte loads.
 constexpr int kTileDeps = 6;   // dependencies carried inside a tile descriptor
 struct alignas(16) SolveTile {
-  int64_t panel_off;   // offset of the supernode's panel
-  int64_t part_base;   // first tile of the output block (partial-sum slots)
+  int64_t panel_off;   // offset of the supernode's panel (column-major nr x nc)
+  int64_t soff;        // FP32 streamed copy: offset (floats, 16-byte aligned) of the tile's first chunk
   int32_t s;           // supernode
-  int32_t a;           // forward: first row; backward: first column
-  int32_t b;           // forward: first column; backward: first row
-  int32_t out;         // output block (tiles of one block are contiguous)
+  int32_t kind;        // forward 0/1/2: 256/128/64 rows; backward 3/4/5/6: 64/32/16/8 columns
+  int32_t a;           // forward: first row of the row block; backward: first column of the block
   int32_t first, nc, nr;   // first column, columns, rows of the supernode
   int32_t pos;         // row_ptr[s]: start of its row structure / positions
   int32_t relp;        // rel_ptr[s]: start of its update-vector rows
-  int32_t ntile;       // tiles in the output block
-  int32_t pad0;        // tile kind: forward rows per tile / backward columns per tile
   int32_t ndep;        // dependencies: forward = children, backward = parent (root: itself)
+  int32_t nchunks;     // chunks of this tile (forward: column ranges, backward: row ranges)
+  int32_t cbytes;      // FP32 stream: bytes of every chunk but the tile's last
+  int32_t lbytes;      // FP32 stream: bytes of the tile's last chunk (a multiple of 16)
+  int32_t lld;         // the tile's last chunk's leading dimension: forward columns per group, backward rows
+  int32_t chunk0;      // index of the tile's first chunk within its block
   // the first kTileDeps dependencies inline: counter index (supernode id; backward
   // dependencies on a forward counter are stored as -(id + 1)) and the number of
   // output blocks that counter reaches per solve; more are read from the tree arrays
   int32_t dep[kTileDeps];
   int32_t dep_blocks[kTileDeps];
-  // FP32 streamed copy of the tile's panel values (one bulk copy into shared memory):
-  // offset in floats (16-byte aligned), bytes (multiple of 16), and the leading
-  // dimension of the tile's layout (forward: columns per thread group; backward: rows)
-  int64_t soff;
-  int32_t sbytes;
-  int32_t sld;
+  int32_t ntile;       // tiles of its block
+  int32_t tib;         // index of this tile within its block (the block's tiles are consecutive)
 };
 static_assert(sizeof(SolveTile) == 128, "tile descriptors are 128 bytes");
 struct SolveSchedule {
   std::vector<SolveTile> fwd, bwd;
   std::vector<SolveTile> all;      // persistent order: forward tiles, then backward tiles by descending level
-  int64_t n_fwd_out = 0, n_bwd_out = 0;
-  int64_t stream_elems = 0;        // floats of the streamed FP32 tiles (both sweeps)
-  std::vector<int32_t> nfb, nbb;   // per supernode: forward / backward output blocks
+  int64_t stream_elems = 0;        // floats of the streamed FP32 chunks (both sweeps)
+  int64_t chunks = 0;              // chunks of one solve (both sweeps)
+  std::vector<int32_t> nfb, nbb;   // per supernode: forward row blocks / backward column blocks
   std::vector<SolveLevel> levels;
 };
 
@@ -119,8 +126,7 @@ struct Workspace {
   IterState* st_host = nullptr;               // pinned mirror
   int* flags = nullptr;                       // device status bits
   void* solve_u = nullptr;                    // (3 nf) T
-  void* solve_W = nullptr;                    // (3 * below rows) T
-  void* solve_partial = nullptr;              // per-tile partial sums
+  void* solve_partial = nullptr;              // per tile partial sums of split blocks
   double* act_cur = nullptr;                  // (e) actuation of the current step
   double* xnext_cur = nullptr;                // (3n) x_{t+1} of the current adjoint step
   int lbfgs_m = 0;
@@ -142,7 +148,7 @@ struct MeshImpl {
   SolveTile* all_tiles = nullptr;
   int32_t *nfb = nullptr, *nbb = nullptr;
   int64_t* parent = nullptr;
-  unsigned long long* solve_counters = nullptr;   // gticket | otick[...] | fdone[ns] | bdone[ns]
+  unsigned long long* solve_counters = nullptr;   // gticket | fdone[ns] | bdone[ns] | otick[tiles]
   int solve_grid = 0;
   // polls of a solve dependency wait before it gives up (~1 s by default); the
   // environment variable PD_SOLVE_SPIN_LIMIT, read at mesh creation, lowers it
@@ -153,8 +159,13 @@ struct MeshImpl {
   mutable int test_stall_solves = 0;
   int64_t stall_tile = -1;         // the forward tile whose wait is raised
   int sms = 1;                     // SMs of the device
-  int32_t* gath_slots = nullptr;   // (sum nr) x slot_w update-row sources, -1 = none
+  // forward-solve update vectors in the parent's layout: child update row i (of
+  // rel_ptr.back()) goes to slot wdest[i] = position x slot_w + rank of the
+  // parent's positions (ranks in child order); unused slots stay zero
+  int32_t* wdest = nullptr;
   int slot_w = 1;
+  float* W32 = nullptr;            // (positions x slot_w x 3), zero-initialised
+  double* W64 = nullptr;
   SolveSchedule sched;
   std::vector<FactorLevel> flevels;
   // assembly map (device)
@@ -166,10 +177,10 @@ struct MeshImpl {
   cudaStream_t cap_stream = nullptr;
   // [direction][precision][variant]: variant 1 holds one iteration fewer (profiled
   // chunks launch their first iteration directly, with timing events)
-  // [direction][local-step precision: FP64, MIXED, kPrecMixedAcc][variant]
-  cudaGraphExec_t iter_graph[2][3][2] = {};
-  bool iter_graph_act[2][3][2] = {};
-  int64_t iter_graph_counts[2][3][2][3] = {};   // kernels, solves, local steps per replay
+  // [direction][local-step precision: FP64, MIXED, kPrecMixedAcc, kPrecRefined][variant]
+  cudaGraphExec_t iter_graph[2][4][2] = {};
+  bool iter_graph_act[2][4][2] = {};
+  int64_t iter_graph_counts[2][4][2][3] = {};   // kernels, solves, local steps per replay
   // complementarity contact (contact.cu): A^-1 columns of the candidate nodes and
   // the current contact set
   int64_t factor_gen = 0;              // bumped by every factorisation

@@ -174,6 +174,118 @@ __device__ __forceinline__ void svd3_from_H(const T (&H)[3][3], SVD3<T>& o) {
   svd3_from_HE<T>(H, E, o);
 }
 
+// ---------------------------------------------------------------- polar refinement
+// FP64 rotation of F = R S (S symmetric) from a rotation R0 accurate to FP32,
+// without eigenvectors.  Two identities carry it:
+//   * Newton-Schulz, R <- R (3 I - R^T R) / 2, squares the distance of R from the
+//     orthogonal matrices (1e-7 -> 1e-14);
+//   * for symmetric S and skew W = skew(w): W S + S W = skew((tr(S) I - S) w), so
+//     the rotation R exp(W) that makes (R exp(W))^T F symmetric to first order has
+//     w = 2 (tr(S0) I - S0)^-1 k with S0 = sym(R^T F), k = axial(skew(R^T F))
+//     (tr(S0) I - S0 has the eigenvalues s_i + s_j > 0 of S0's pairs);
+//     one step squares the error of R again.
+// The same 3 x 3 solve gives the derivative of the polar rotation:
+//   dR = R skew(w) with w = 2 (tr(S) I - S)^-1 axial(skew(R^T dF)).
+__device__ __forceinline__ void skew_axial(const double (&A)[3][3], double (&k)[3]) {
+  // axial vector of skew(A) = (A - A^T)/2: skew(k) has [2][1] = k0, [0][2] = k1, [1][0] = k2
+  k[0] = 0.5 * (A[2][1] - A[1][2]);
+  k[1] = 0.5 * (A[0][2] - A[2][0]);
+  k[2] = 0.5 * (A[1][0] - A[0][1]);
+}
+
+// w = 2 (tr(S) I - S)^-1 k for symmetric S (returns false when the matrix is singular)
+__device__ __forceinline__ bool polar_solve(const double (&S)[3][3], const double (&k)[3], double (&w)[3]) {
+  const double t = S[0][0] + S[1][1] + S[2][2];
+  const double a00 = t - S[0][0], a11 = t - S[1][1], a22 = t - S[2][2];
+  const double a01 = -0.5 * (S[0][1] + S[1][0]), a02 = -0.5 * (S[0][2] + S[2][0]), a12 = -0.5 * (S[1][2] + S[2][1]);
+  // adjugate of the symmetric matrix
+  const double c00 = a11 * a22 - a12 * a12, c01 = a02 * a12 - a01 * a22, c02 = a01 * a12 - a02 * a11;
+  const double c11 = a00 * a22 - a02 * a02, c12 = a01 * a02 - a00 * a12, c22 = a00 * a11 - a01 * a01;
+  const double det = a00 * c00 + a01 * c01 + a02 * c02;
+  if (!(fabs(det) > 1e-300)) {
+    w[0] = w[1] = w[2] = 0.0;
+    return false;
+  }
+  const double id = 2.0 / det;
+  w[0] = id * (c00 * k[0] + c01 * k[1] + c02 * k[2]);
+  w[1] = id * (c01 * k[0] + c11 * k[1] + c12 * k[2]);
+  w[2] = id * (c02 * k[0] + c12 * k[1] + c22 * k[2]);
+  return true;
+}
+
+// R <- R (I + skew(w) + skew(w)^2 / 2)
+__device__ __forceinline__ void rotate_by(double (&R)[3][3], const double (&w)[3]) {
+  const double W2 = w[0] * w[0] + w[1] * w[1] + w[2] * w[2];
+  double G[3][3];
+  G[0][0] = 1.0 + 0.5 * (w[0] * w[0] - W2);
+  G[1][1] = 1.0 + 0.5 * (w[1] * w[1] - W2);
+  G[2][2] = 1.0 + 0.5 * (w[2] * w[2] - W2);
+  G[0][1] = -w[2] + 0.5 * w[0] * w[1];
+  G[1][0] = w[2] + 0.5 * w[0] * w[1];
+  G[0][2] = w[1] + 0.5 * w[0] * w[2];
+  G[2][0] = -w[1] + 0.5 * w[0] * w[2];
+  G[1][2] = -w[0] + 0.5 * w[1] * w[2];
+  G[2][1] = w[0] + 0.5 * w[1] * w[2];
+  double T[3][3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) T[i][j] = R[i][0] * G[0][j] + R[i][1] * G[1][j] + R[i][2] * G[2][j];
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) R[i][j] = T[i][j];
+}
+
+// R from the FP32 rotation R0 and F = I + H (FP64), refined as above; S gets the
+// symmetric factor R^T F.  Returns false if a solve was singular (inverted or
+// degenerate elements).
+__device__ __forceinline__ bool polar_refine(const float (&U)[3][3], const float (&V)[3][3], const double (&H)[3][3],
+                                             double (&R)[3][3], double (&S)[3][3]) {
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j)
+      R[i][j] = (double)U[i][0] * (double)V[j][0] + (double)U[i][1] * (double)V[j][1] +
+                (double)U[i][2] * (double)V[j][2];
+  // Newton-Schulz
+  double RtR[3][3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) RtR[i][j] = R[0][i] * R[0][j] + R[1][i] * R[1][j] + R[2][i] * R[2][j];
+  double T[3][3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j)
+      T[i][j] = 1.5 * R[i][j] - 0.5 * (R[i][0] * RtR[0][j] + R[i][1] * RtR[1][j] + R[i][2] * RtR[2][j]);
+  // one polar correction: M = R^T F = R^T + R^T H
+  double M[3][3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) M[i][j] = T[j][i] + T[0][i] * H[0][j] + T[1][i] * H[1][j] + T[2][i] * H[2][j];
+  double k[3], w[3];
+  skew_axial(M, k);
+  const bool ok = polar_solve(M, k, w);
+  rotate_by(T, w);
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) R[i][j] = T[i][j];
+  // S = sym(R^T F)
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) M[i][j] = R[j][i] + R[0][i] * H[0][j] + R[1][i] * H[1][j] + R[2][i] * H[2][j];
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) S[i][j] = 0.5 * (M[i][j] + M[j][i]);
+  return ok;
+}
+
 // out += c * U diag(d) V^T   (c scalar)
 template <typename T>
 __device__ __forceinline__ void add_UdVt(T (&out)[3][3], const T (&U)[3][3], const T* d,

@@ -125,3 +125,24 @@ def test_backward_rejects_mismatched_loss_gradients(native):
         assert st == native.PD_ERR_INVALID_ARG
         assert b"loss_states" in L.pd_last_error()
     m.close()
+
+
+def test_checkpoint_plan_follows_the_memory_cap(native):
+    """pd_plan_checkpoints: every state stored when (T+1) states of x and v fit the
+    cap; otherwise the smallest K dividing T whose checkpoints plus one recomputed
+    segment fit; PD_ERR_OOM when none does (host arithmetic, no device)."""
+    from paper_2101_05917_gb300 import api
+    sc = small_beam(3, 2, 2, T=1)
+    m = api.PDMesh.from_scene(sc, device=None)
+    state = 48 * m.n                      # x and v of one state, bytes
+    T = 12
+    assert m.plan_checkpoints(T, (T + 1) * state) == 0
+    # K fits when (T/K + 1) + (K + 1) states fit: 12 states -> K = 2 (6+1+2+1 = 10),
+    # 9 states -> K = 3 (4+1+3+1 = 9), 8 states -> none (K = 3, 4, 6, 12 need 9, 9, 10, 15)
+    assert m.plan_checkpoints(T, 9 * state) == 3
+    assert m.plan_checkpoints(T, 12 * state) == 2
+    with pytest.raises(native.PDError):
+        m.plan_checkpoints(T, 8 * state)
+    with pytest.raises(native.PDError):   # host-only mesh: the cap is required
+        m.plan_checkpoints(T, 0)
+    m.close()

@@ -118,3 +118,50 @@ def test_strain_accurate_local_step_under_large_rotation(name):
     torch.cuda.synchronize()
     assert rel(out.cpu().numpy(), ref) < TOL[N.PD_PREC_MIXED]
     mesh.close()
+
+
+def _quad9_corot_muscle():
+    sc = quadruped(9, T=2)
+    sc.volume = False          # corotated + muscle + contact: the refined kernel's energies
+    return sc
+
+
+@pytest.mark.parametrize("name", ["c1", "quad9_corot_muscle", "quad9", "tiny_all"])
+@pytest.mark.parametrize("scale", [0.05, 1e-4])
+def test_refined_fp64_local_step_matches_oracle(name, scale):
+    """PD_PREC_FP64_REFINED (FP32 SVD of the FP64 strain, rotation and its
+    derivative refined in FP64 without eigenvectors) gives the gradient and the
+    Hessian product to FP64 accuracy: against the oracle within the FP64 tolerance
+    and against the plain FP64 kernel within 1e-12, at moderate strain (0.05) and
+    at a strain of 1e-4 under a random rotation.  Meshes with the volume energy run
+    the plain FP64 kernel through the same entry (checked for equality).  At a
+    strain of 1e-4 the gradient is 1e4 times smaller than the positions it comes
+    from, so two FP64 evaluations agree to ~1e-11 there: the gate is 1e-9."""
+    sc = _quad9_corot_muscle() if name == "quad9_corot_muscle" else _scenes()[name]
+    model = Model(sc)
+    mesh = make_mesh(sc, precision=N.PD_PREC_MIXED)
+    act = None if sc.act is None else sc.act[0]
+    ta = None if act is None else T(act)
+    x = deformed(sc, scale=scale, seed=13)
+    if sc.k_contact > 0:
+        x[:, 2] -= 0.3 * sc.dx
+    g_ref = model.grad_E(x, act)
+    g_r, e_r = mesh.local_step(T(x), ta, precision=N.PD_PREC_FP64_REFINED)
+    g_d, e_d = mesh.local_step(T(x), ta, precision=N.PD_PREC_FP64)
+    torch.cuda.synchronize()
+    gr, gd = g_r.cpu().numpy(), g_d.cpu().numpy()
+    tol = TOL[N.PD_PREC_FP64] if scale > 1e-3 else 1e-9
+    print(f"{name} strain {scale}: refined vs oracle {rel(gr, g_ref):.2e}, vs FP64 kernel {rel(gr, gd):.2e}")
+    assert rel(gr, g_ref) < tol
+    assert rel(gr, gd) < tol
+    assert abs(e_r.item() - e_d.item()) <= tol * abs(e_d.item())
+    H = model.hessian(x, act)[model.free_dofs][:, model.free_dofs]
+    v = np.random.default_rng(4).standard_normal(x.shape)
+    v[model.dirichlet] = 0
+    ref = np.zeros_like(v)
+    ref[model.free_nodes] = (H @ v[model.free_nodes].ravel()).reshape(-1, 3)
+    h_r = mesh.hessian_vector(T(x), T(v), ta, precision=N.PD_PREC_FP64_REFINED).cpu().numpy()
+    h_d = mesh.hessian_vector(T(x), T(v), ta, precision=N.PD_PREC_FP64).cpu().numpy()
+    assert rel(h_r, ref) < tol
+    assert rel(h_r, h_d) < tol
+    mesh.close()

@@ -1,7 +1,9 @@
 """Rollout parity through the C ABI: PD forward (Alg. 1 + L-BFGS) against the
 Newton oracle (Sec. 3) and the PD adjoint (Alg. 2 + L-BFGS) against the
 full-linearisation adjoint (Eqns 8-12).  Gates: 1e-5 relative position error
-(max over steps) and 1e-4 relative gradient error."""
+(max over steps), the same relative to the displacement |x_t - X| and, per
+component, relative to the largest displacement component; 1e-4 relative
+gradient error."""
 import os
 
 import numpy as np
@@ -27,6 +29,14 @@ def _pos_err(xs, ref):
     return max(np.linalg.norm(xs[t] - ref[t]) / np.linalg.norm(ref[t]) for t in range(ref.shape[0]))
 
 
+def _disp_errs(xs, ref):
+    """(|dx| / |x_t - X|, max|dx| / max|x_t - X|), worst over steps t >= 1."""
+    X = ref[0]
+    d = max(np.linalg.norm(xs[t] - ref[t]) / np.linalg.norm(ref[t] - X) for t in range(1, ref.shape[0]))
+    m = max(np.abs(xs[t] - ref[t]).max() / np.abs(ref[t] - X).max() for t in range(1, ref.shape[0]))
+    return float(d), float(m)
+
+
 def _run(sc, prec, opts, loss_all_steps=False):
     mesh = make_mesh(sc, precision=prec)
     f = T(sc.f_ext)
@@ -45,6 +55,9 @@ def test_c1_cantilever_fp64_matches_oracle():
     xs = roll.x.cpu().numpy()
     assert _pos_err(xs, gold["xs"]) < POS_TOL
     assert np.abs(xs - gold["xs"]).max() < 1e-8
+    d, m = _disp_errs(xs, gold["xs"])
+    print(f"C1 displacement-relative {d:.2e}, component max {m:.2e}")
+    assert d < POS_TOL and m < POS_TOL
     assert rel(g["v0"].cpu().numpy(), gold["g_v0"]) < GRAD_TOL
     assert rel(g["x0"].cpu().numpy(), gold["g_x0"]) < GRAD_TOL
     assert rel(g["w_corot"].cpu().numpy(), gold["g_wc"]) < GRAD_TOL
@@ -73,6 +86,9 @@ def test_rollout_matches_oracle(name, prec):
     mesh, roll, g = _run(sc, prec, opts)
     xs = roll.x.cpu().numpy()
     assert _pos_err(xs, xs_ref) < POS_TOL
+    d, m = _disp_errs(xs, xs_ref)
+    print(f"{name}: displacement-relative {d:.2e}, component max {m:.2e}")
+    assert d < POS_TOL and m < POS_TOL
     for key, rkey in (("v0", "g_v0"), ("x0", "g_x0"), ("fext", "g_fext")):
         assert rel(g[key].cpu().numpy(), ref[rkey]) < GRAD_TOL, key
     if sc.corotated:
@@ -113,3 +129,27 @@ def test_runs_are_deterministic():
         mesh.close()
     for a, b in zip(outs[0], outs[1]):
         assert torch.equal(a, b)
+
+
+def test_checkpointing_planned_from_a_memory_cap_is_bit_identical():
+    """A memory cap too small for all T+1 states makes the forward pass checkpoint
+    on its own (pd_plan_checkpoints picks the interval); the backward pass then
+    recomputes each segment and the gradients equal those over stored states bit
+    for bit (Sec. 4, back-propagation through every step)."""
+    steps = 8
+    sc = small_beam(4, 2, 2, T=steps)
+    mesh = make_mesh(sc)
+    state = 48 * mesh.n
+    want = ("x0", "v0", "fext", "w_corot", "w_vol")
+    outs = []
+    for every, cap in ((0, 0), (-1, 8 * state)):
+        o = api.solver_opts(tol_fwd=1e-11, tol_bwd=1e-11, max_iter_fwd=5000, max_iter_bwd=5000,
+                            checkpoint_every=every)
+        roll = mesh.forward(T(sc.x0), T(sc.v0), steps, f_ext=T(sc.f_ext), opts=o, mem_cap=cap)
+        g = mesh.backward(roll, steps, T(sc.loss_w), f_ext=T(sc.f_ext), opts=o, want=want)
+        outs.append((roll, g))
+    assert outs[0][0].checkpoint_every == 0 and outs[1][0].checkpoint_every == 2
+    assert torch.equal(outs[0][0].x[-1], outs[1][0].x[-1])
+    for k in want:
+        assert torch.equal(outs[0][1][k], outs[1][1][k]), k
+    mesh.close()

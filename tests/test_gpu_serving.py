@@ -81,6 +81,12 @@ def test_cache_reuse_and_release():
     c = srv.result(srv.submit_scene(sc2, opts=opts))
     assert (c["mesh_cached"], c["factor_cached"]) == (1, 0)
     assert not np.array_equal(a["x_final"], c["x_final"])
+    # another geometry key (fixed nodes) with the same box: a new mesh, compared in full
+    sc3 = quadruped(4, T=3, request=1)
+    sc3.dirichlet = sc3.dirichlet.copy()
+    sc3.dirichlet[0] = 1
+    d = srv.result(srv.submit_scene(sc3, opts=opts))
+    assert d["mesh_cached"] == 0
     with pytest.raises(N.PDError):
         srv.poll(t1)            # released by result()
     with pytest.raises(N.PDError):
@@ -99,3 +105,57 @@ def test_request_errors():
     assert r["status"] == N.PD_ERR_NOT_CONVERGED
     assert r["x_final"] is not None and np.all(np.isfinite(r["x_final"]))
     srv.close()
+
+
+def test_request_matches_newton_oracle():
+    """One served request (quadruped with muscles, ground contact and friction, 3
+    steps, mixed precision) against the FP64 oracle: Newton forward and the
+    full-linearisation adjoint of L = sum(loss_w x_T) (Sec. 3, Sec. 4)."""
+    from oracle import adjoint, newton
+    from oracle.model import Model
+    T = 3
+    sc = quadruped(5, T=T, request=2)
+    srv = api.PDServer(max_slots=2)
+    r = srv.result(srv.submit_scene(sc, precision=N.PD_PREC_MIXED, opts=api.solver_opts(**OPTS)))
+    srv.close()
+    assert r["status"] == N.PD_OK
+    model = Model(sc)
+    act = sc.act[:T]
+    xs, vs, _ = newton.rollout(model, sc.x0, sc.v0, sc.f_ext, act=act, mu=sc.mu, T=T)
+    loss, gx = adjoint.final_position_loss(model, xs, sc.loss_w)
+    g = adjoint.backward(model, xs, vs, gx, act=act, mu=sc.mu)
+    rel = lambda a, b: float(np.linalg.norm(a - b) / np.linalg.norm(b))
+    disp = np.linalg.norm(r["x_final"] - xs[-1]) / np.linalg.norm(xs[-1] - sc.x0)
+    print(f"served vs oracle: position {rel(r['x_final'], xs[-1]):.2e} (displacement-relative {disp:.2e}), "
+          f"g_v0 {rel(r['g_v0'], g['g_v0']):.2e}, g_act {rel(r['g_act'], g['g_act']):.2e}")
+    assert rel(r["x_final"], xs[-1]) <= 1e-5 and disp <= 1e-4
+    assert rel(r["g_v0"], g["g_v0"]) <= 1e-4 and rel(r["g_act"], g["g_act"]) <= 1e-4
+    assert abs(r["loss"] - loss) <= 1e-5 * abs(loss)
+
+
+@pytest.mark.parametrize("budget", ["tiny", "large"])
+def test_memory_budget_admission(budget):
+    """Admission by device memory: with a budget below any request's estimate every
+    request runs alone (a request that fits nowhere runs only when nothing else
+    does), so their run intervals do not overlap; with a large budget three slots
+    run them side by side.  Results are the same either way."""
+    import time
+    scenes = [quadruped(8, T=6, request=i) for i in range(3)]
+    opts = api.solver_opts(**OPTS)
+    srv = api.PDServer(max_slots=3, mem_budget=1 if budget == "tiny" else 16 << 30)
+    subs, tickets = [], []
+    for sc in scenes:
+        subs.append(time.perf_counter())
+        tickets.append(srv.submit_scene(sc, precision=N.PD_PREC_MIXED, opts=opts))
+    res = [srv.result(t) for t in tickets]
+    srv.close()
+    spans = sorted((s + 1e-3 * r["queue_ms"], s + 1e-3 * r["latency_ms"]) for s, r in zip(subs, res))
+    overlaps = sum(1 for a, b in zip(spans, spans[1:]) if b[0] < a[1] - 2e-3)
+    if budget == "tiny":
+        assert overlaps == 0, spans
+    else:
+        assert overlaps > 0, spans
+    ref = api.PDServer(max_slots=1)
+    for sc, r in zip(scenes, res):
+        _same(r, ref.result(ref.submit_scene(sc, precision=N.PD_PREC_MIXED, opts=opts)))
+    ref.close()

@@ -1,18 +1,22 @@
 """The triangular solve's tile schedule and its streamed FP32 layout, from the host
-analysis (no GPU).  Each tile's panel values reach shared memory by one bulk copy,
+analysis (no GPU).  Each chunk of a tile reaches shared memory by one bulk copy,
 which must start on a 16-byte boundary and move a multiple of 16 bytes, at most the
-48 KB tile stage: a copy that breaks these rules is an illegal instruction on the
-GPU, so they are checked here for every tile of every test mesh, together with the
-tiles lying back to back.  The schedule itself must equal a re-derivation from its
-definition: per supernode (nc columns, nr rows), forward tiles of R rows (R = 256
-for nc <= 48, 128 for nc <= 96, else 64) by 256/R column groups of 48, where a row
-block inside the triangular L11^-1 block only takes columns up to its last row;
-backward tiles of BC columns (the narrowest of 8/16/32/64 covering nc, 64 at most)
-by min(12288/BC, 1024) rows, starting at the row block that holds the tile's first
-column; forward tiles by ascending tree level, backward tiles by descending level,
-supernodes in level-list order.  Streamed copy per tile: forward [group][column <
-kmax][row < rv] with kmax the columns of the tile's last row inside its first
-group, backward [column < bcv][row < rn]; each padded to 16 bytes."""
+48 KB stage: a copy that breaks these rules is an illegal instruction on the GPU,
+so they are checked here for every chunk of every test mesh, together with the
+chunks lying back to back.  The schedule itself must equal a re-derivation from
+its definition: per supernode (nc columns, nr rows), forward tiles are row blocks
+of R rows (R = 256 for nc <= 48, 128 for nc <= 96, else 64) over the columns
+[0, cend) their rows need (a row block inside the triangular L11^-1 block only up
+to its last row), in chunks of 256/R column groups of 48 columns; backward tiles
+are column blocks of BC columns (the narrowest of 8/16/32/64 covering nc, 64 at
+most) over the rows from their first column down, in chunks of min(12288/BC, 512)
+rows; a level whose blocks number fewer than 1024 has them cut into runs of at
+most max(1, chunks of the level / 1024) consecutive chunks (a tile each);
+forward tiles by ascending tree level, backward tiles by descending level,
+supernodes in level-list order.  Streamed copy per chunk: forward [group][column <
+kmax_g][row < rv] with kmax_g = clamp(L - 48 g, 0, 48) for a chunk of L columns
+(the groups filled in order), backward [column < bcv][row < rn]; each padded to
+16 bytes."""
 import numpy as np
 import pytest
 
@@ -36,34 +40,60 @@ def _derive(m):
     ll = m.export("level_list")
     lp = m.export("level_ptr")
     fwd, bwd = [], []
+    LEVEL_TILES = 1024
+
+    def kc_of(blocks):
+        total = sum(b[3] for b in blocks)
+        most = max([b[3] for b in blocks] + [1])
+        if len(blocks) >= LEVEL_TILES:
+            return most
+        return max(1, min(most, total // LEVEL_TILES))
+
+    def split(blocks, kc, full_ld, out):
+        for s, kind, a, nch, full, last, lld in blocks:
+            nt = (nch + kc - 1) // kc
+            for k in range(nt):
+                c0 = k * kc
+                n = min(kc, nch - c0)
+                has_last = c0 + n == nch
+                ld = lld if has_last else full_ld(kind)
+                lastsz = last if has_last else full
+                out.append((s, kind, a, c0, n, full, lastsz, ld, nt))
+
     for L in range(len(lp) - 1):
-        lev_b = []
+        fb, bb = [], []
         for s in ll[lp[L]:lp[L + 1]]:
             nc, nr = int(sf[s + 1] - sf[s]), int(rp[s + 1] - rp[s])
             R = 256 if nc <= 48 else (128 if nc <= 96 else 64)
             G = 256 // R
+            CW = 48 * G
             for r0 in range(0, nr, R):
-                cmax = r0 + R if r0 + R <= nc else nc
                 rv = min(R, nr - r0)
                 rmax = r0 + rv - 1
                 cend = min(nc, rmax + 1) if rmax < nc else nc
-                for c0 in range(0, cmax, 48 * G):
-                    kmax = max(0, min(48, cend - c0))
-                    fwd.append((s, KINDS_F[R], r0, c0, G * kmax * rv, kmax))
+                nch = (cend + CW - 1) // CW
+                lld = cend - (nch - 1) * CW          # columns of the block's last chunk
+                fb.append((s, KINDS_F[R], r0, nch, G * 48 * rv, lld * rv, lld))
             BC = 64 if nc > 32 else (32 if nc > 16 else (16 if nc > 8 else 8))
-            BR = min(12288 // BC, 1024)
+            BR = min(12288 // BC, 512)
             for c0 in range(0, nc, BC):
-                for r0 in range((c0 // BR) * BR, nr, BR):
-                    rn = min(BR, nr - r0)
-                    lev_b.append((s, KINDS_B[BC], c0, r0, min(BC, nc - c0) * rn, rn))
+                rows = nr - c0
+                nch = (rows + BR - 1) // BR
+                lld = rows - (nch - 1) * BR
+                bcv = min(BC, nc - c0)
+                bb.append((s, KINDS_B[BC], c0, nch, bcv * BR, bcv * lld, lld))
+        split(fb, kc_of(fb), lambda kind: 48 * {0: 1, 1: 2, 2: 4}[kind], fwd)
+        lev_b = []
+        bc_of = {3: 64, 4: 32, 5: 16, 6: 8}
+        split(bb, kc_of(bb), lambda kind: min(12288 // bc_of[kind], 512), lev_b)
         bwd.append(lev_b)
     tiles = fwd + [t for lev in reversed(bwd) for t in lev]
     out, off = [], 0
-    for s, kind, a, b, elems, ld in tiles:
-        padded = (elems + 3) // 4 * 4
-        out.append((s, kind, a, b, off, 4 * padded, ld))
-        off += padded
-    return np.array(out, dtype=np.int64).reshape(-1, 7)
+    for s, kind, a, c0, n, full, last, ld, nt in tiles:
+        lpad = (last + 3) // 4 * 4
+        out.append((s, kind, a, c0, n, off, 4 * full, 4 * lpad, ld, nt))
+        off += full * (n - 1) + lpad
+    return np.array(out, dtype=np.int64).reshape(-1, 10)
 
 
 CASES = [(cantilever_c1, 64), (cantilever_c1, 8), (lambda: quadruped(9, T=1), 64),
@@ -77,11 +107,15 @@ def test_solve_tiles_match_definition_and_copy_rules(native, case):
     make, leaf = CASES[case]
     sc = make()
     m = api.PDMesh.from_scene(sc, leaf_max=leaf, device=None)
-    got = m.export("solve_tiles").reshape(-1, 7)
+    got = m.export("solve_tiles").reshape(-1, 10)
     want = _derive(m)
     assert np.array_equal(got, want)
-    soff, sbytes = got[:, 4], got[:, 5]
+    nch, soff, cbytes, lbytes = got[:, 4], got[:, 5], got[:, 6], got[:, 7]
+    assert np.all(nch >= 1)
     assert np.all(soff % 4 == 0)                          # 16-byte aligned starts (floats)
-    assert np.all(sbytes % 16 == 0) and np.all(sbytes > 0) and np.all(sbytes <= 49152)
-    assert np.array_equal(soff[1:], soff[:-1] + sbytes[:-1] // 4)   # back to back
+    for b in (cbytes, lbytes):
+        assert np.all(b % 16 == 0) and np.all(b > 0) and np.all(b <= 49152)
+    # chunks back to back: every chunk but a tile's last has cbytes, the last lbytes
+    ends = soff + (nch - 1) * (cbytes // 4) + lbytes // 4
+    assert np.array_equal(soff[1:], ends[:-1])
     m.close()
