@@ -492,7 +492,7 @@ def run_ours(args):
                               "solve" % (nnzq * 4 / 1e6)) if K > 0 else
                              "256 MB buffer written between timed rollouts",
                        "parallelism": "replicas"},
-            "roofline": {"bound": "hbm", "kernel": "triangular solve pair (solve_persistent_kernel)",
+            "roofline": {"bound": "hbm", "kernel": "triangular solve pair (solve_pipe_kernel, FP32 panels)",
                          "achieved": achieved, "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic, "traffic_source": traffic_src,
                          "bytes_per_launch": bytes_solve, "avg_solve_us": 1e6 * t_solve,

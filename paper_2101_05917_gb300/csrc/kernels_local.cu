@@ -140,7 +140,8 @@ struct ElemParams {
   const double* v;
   const double* act;
   const double *wc, *wv, *wm, *fiber;
-  double dx, Vq;
+  double dx, Vq, inv_dx;
+  float dx_f, Vq_f, inv_dx_f;   // the same in FP32 (the FP32 kernels take no FP64 arithmetic for them)
   void* out;            // elembuf (T) for FORCE/HVP
   double* energy;       // block partials (FORCE)
   double *g_wc, *g_wv, *g_wm, *g_act;   // PGRAD outputs
@@ -168,9 +169,9 @@ element_kernel(ElemParams p) {
   const int k = lane & 7;
   const int64_t e = ((int64_t)blockIdx.x * kElemThreads + threadIdx.x) >> 3;
   const bool valid = e < p.ne;
-  const T inv_dx = T(1.0 / p.dx);
+  const T inv_dx = sizeof(T) == 4 ? T(p.inv_dx_f) : T(p.inv_dx);
   // volume weight of this lane's point (the tetrahedral rule leaves lanes 6, 7 idle)
-  const T Vq = (RULE == RULE_TET6 && k >= 6) ? T(0) : T(p.Vq);
+  const T Vq = (RULE == RULE_TET6 && k >= 6) ? T(0) : (sizeof(T) == 4 ? T(p.Vq_f) : T(p.Vq));
 
   // ---- corner loads: relative displacement of corner k w.r.t. corner 0
   int node = valid ? p.elems[e * 8 + k] : 0;
@@ -185,7 +186,7 @@ element_kernel(ElemParams p) {
 #pragma unroll
   for (int i = 0; i < 3; ++i) {
     const double x0 = __shfl_sync(0xffffffffu, xk[i], base);
-    dkd[i] = (xk[i] - x0) - p.dx * (double)cbit(k, i);
+    dkd[i] = (xk[i] - x0) - (cbit(k, i) ? p.dx : 0.0);
     dk[i] = (T)dkd[i];
   }
   T vk[3] = {T(0), T(0), T(0)};
@@ -422,11 +423,15 @@ element_kernel(ElemParams p) {
     out[2] = fa[2];
   }
   if (MODE == MODE_FORCE) {
-    // block energy partial without a block barrier: each warp deposits its sum,
-    // the last warp to arrive adds the 8 deposits in warp order
-    double en = valid ? (double)energy : 0.0;
+    // block energy partial without a block barrier: the cell's 8 points are added
+    // in T, the warp's 4 cells in FP64; each warp deposits its sum, the last warp to
+    // arrive adds the 8 deposits in warp order
+    T ec = valid ? energy : T(0);
 #pragma unroll
-    for (int off = 16; off >= 1; off >>= 1) en += __shfl_xor_sync(0xffffffffu, en, off);
+    for (int off = 4; off >= 1; off >>= 1) ec += __shfl_xor_sync(0xffffffffu, ec, off);
+    double en = (double)ec;
+#pragma unroll
+    for (int off = 16; off >= 8; off >>= 1) en += __shfl_xor_sync(0xffffffffu, en, off);
     if (lane == 0) {
       wsum[threadIdx.x >> 5] = en;
       __threadfence_block();
@@ -478,6 +483,39 @@ struct GatherParams {
   const uint8_t* held;  // nodes held at contact targets: gradient / product rows are zero
 };
 
+// sum of a node's corner values in incidence order.  FP32 values are added in
+// FP32 with Kahan compensation (the sum of an FP64 accumulation without its FP64
+// additions, which GB300 runs at a small fraction of the FP32 rate), FP64 values
+// in FP64.
+template <typename T>
+__device__ __forceinline__ void corner_sum(const GatherParams& p, int64_t c, double (&g)[3]) {
+  const T* eb = reinterpret_cast<const T*>(p.elembuf);
+  const int32_t q0 = p.inc_ptr[c], q1 = p.inc_ptr[c + 1];
+  if constexpr (sizeof(T) == 8) {
+    g[0] = g[1] = g[2] = 0.0;
+    for (int32_t q = q0; q < q1; ++q) {
+      const int64_t slot = (int64_t)p.inc[q] * 3;
+      g[0] += eb[slot + 0];
+      g[1] += eb[slot + 1];
+      g[2] += eb[slot + 2];
+    }
+  } else {
+    float sm[3] = {0.f, 0.f, 0.f}, cp[3] = {0.f, 0.f, 0.f};
+    for (int32_t q = q0; q < q1; ++q) {
+      const int64_t slot = (int64_t)p.inc[q] * 3;
+#pragma unroll
+      for (int i = 0; i < 3; ++i) {
+        const float y = eb[slot + i] - cp[i];
+        const float t = sm[i] + y;
+        cp[i] = (t - sm[i]) - y;
+        sm[i] = t;
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < 3; ++i) g[i] = (double)sm[i] - (double)cp[i];
+  }
+}
+
 // grad g at x: partials = [kinetic + contact energy, |g|^2, g.dir, 0]
 template <typename T>
 __global__ void __launch_bounds__(kGatherThreads) gather_grad_kernel(GatherParams p) {
@@ -485,14 +523,8 @@ __global__ void __launch_bounds__(kGatherThreads) gather_grad_kernel(GatherParam
   const int64_t c = (int64_t)blockIdx.x * kGatherThreads + threadIdx.x;
   double acc[4] = {0, 0, 0, 0};
   if (c < p.nf) {
-    const T* eb = reinterpret_cast<const T*>(p.elembuf);
-    double g[3] = {0, 0, 0};
-    for (int32_t q = p.inc_ptr[c]; q < p.inc_ptr[c + 1]; ++q) {
-      const int64_t slot = (int64_t)p.inc[q] * 3;
-      g[0] += (double)eb[slot + 0];
-      g[1] += (double)eb[slot + 1];
-      g[2] += (double)eb[slot + 2];
-    }
+    double g[3];
+    corner_sum<T>(p, c, g);
     const double m = p.mass[c];
     double kin = 0;
 #pragma unroll
@@ -530,14 +562,8 @@ __global__ void __launch_bounds__(kGatherThreads) gather_hvp_kernel(GatherParams
   const int64_t c = (int64_t)blockIdx.x * kGatherThreads + threadIdx.x;
   double acc[4] = {0, 0, 0, 0};
   if (c < p.nf) {
-    const T* eb = reinterpret_cast<const T*>(p.elembuf);
-    double g[3] = {0, 0, 0};
-    for (int32_t q = p.inc_ptr[c]; q < p.inc_ptr[c + 1]; ++q) {
-      const int64_t slot = (int64_t)p.inc[q] * 3;
-      g[0] += (double)eb[slot + 0];
-      g[1] += (double)eb[slot + 1];
-      g[2] += (double)eb[slot + 2];
-    }
+    double g[3];
+    corner_sum<T>(p, c, g);
     const double m = p.mass[c];
 #pragma unroll
     for (int i = 0; i < 3; ++i) g[i] += m * p.v[3 * c + i] * p.inv_h2;
@@ -554,6 +580,15 @@ __global__ void __launch_bounds__(kGatherThreads) gather_hvp_kernel(GatherParams
   block_partials<4>(acc, p.partials);
 }
 
+void set_cell_size(ElemParams& p, double dx, double points_per_cell) {
+  p.dx = dx;
+  p.Vq = dx * dx * dx / points_per_cell;
+  p.inv_dx = 1.0 / dx;
+  p.dx_f = (float)p.dx;
+  p.Vq_f = (float)p.Vq;
+  p.inv_dx_f = (float)p.inv_dx;
+}
+
 ElemParams make_params(const LocalArgs& a) {
   ElemParams p{};
   p.gate = a.gate;
@@ -566,8 +601,7 @@ ElemParams make_params(const LocalArgs& a) {
   p.wv = a.m->wv;
   p.wm = a.m->wm;
   p.fiber = a.m->fiber;
-  p.dx = a.m->h.dx;
-  p.Vq = a.m->h.dx * a.m->h.dx * a.m->h.dx / (a.m->h.rule == PD_ELEM_TET6 ? 6.0 : 8.0);
+  set_cell_size(p, a.m->h.dx, a.m->h.rule == PD_ELEM_TET6 ? 6.0 : 8.0);
   return p;
 }
 
@@ -699,8 +733,7 @@ cudaError_t launch_element_forces_raw(int64_t ne, const int32_t* elems, const do
   p.wv = wv;
   p.wm = wm;
   p.fiber = fiber;
-  p.dx = dx;
-  p.Vq = dx * dx * dx / 8.0;
+  set_cell_size(p, dx, 8.0);
   p.out = elembuf;
   p.energy = energy_partials;
   p.flags = flags;

@@ -375,14 +375,21 @@ __device__ void fwd_tile(const SolveParams& p, const SolveTile& tl, int64_t tile
     const double* bp = p.b + 3 * (first + col_of(0));
     bb0 = __ldg(bp), bb1 = __ldg(bp + 1), bb2 = __ldg(bp + 2);
   }
-  if (threadIdx.x == 0) {
-    // the children's forward outputs (inline in the descriptor; more from the tree)
-    const int nd = tl.ndep;
-    for (int k = 0; k < nd && k < kTileDeps; ++k)
-      wait_count(p.fdone + tl.dep[k],
-                 (epoch + 1) * (unsigned long long)tl.dep_blocks[k] + (k == 0 && tile == p.stall_tile ? 1 : 0),
+  if (threadIdx.x < 32) {
+    // the children's forward outputs: those inline in the descriptor polled in
+    // parallel, one lane each; more (rare) from the tree by lane 0
+    const int nd = tl.ndep, lane = threadIdx.x;
+    int32_t dk = 0, bk = 0;
+#pragma unroll
+    for (int k = 0; k < kTileDeps; ++k)
+      if (lane == k) {
+        dk = tl.dep[k];
+        bk = tl.dep_blocks[k];
+      }
+    if (lane < nd && lane < kTileDeps)
+      wait_count(p.fdone + dk, (epoch + 1) * (unsigned long long)bk + (lane == 0 && tile == p.stall_tile ? 1 : 0),
                  p.err, p.spin_limit);
-    if (nd > kTileDeps) {
+    if (nd > kTileDeps && lane == 0) {
       for (int64_t ci = __ldg(p.child_ptr + tl.s) + kTileDeps; ci < __ldg(p.child_ptr + tl.s + 1); ++ci) {
         const int64_t c = __ldg(p.child_list + ci);
         wait_count(p.fdone + c, (epoch + 1) * (unsigned long long)__ldg(p.nfb + c), p.err, p.spin_limit);
