@@ -10,8 +10,8 @@ of R rows (R = 256 for nc <= 48, 128 for nc <= 96, else 64) over the columns
 to its last row), in chunks of 256/R column groups of 48 columns; backward tiles
 are column blocks of BC columns (the narrowest of 8/16/32/64 covering nc, 64 at
 most) over the rows from their first column down, in chunks of min(12288/BC, 512)
-rows; a level whose blocks number fewer than 1024 has them cut into runs of at
-most max(1, chunks of the level / 1024) consecutive chunks (a tile each);
+rows; a level whose blocks number fewer than 608 has them cut into runs of at
+most max(1, chunks of the level / 608) consecutive chunks (a tile each);
 forward tiles by ascending tree level, backward tiles by descending level,
 supernodes in level-list order.  Streamed copy per chunk: forward [group][column <
 kmax_g][row < rv] with kmax_g = clamp(L - 48 g, 0, 48) for a chunk of L columns
@@ -40,7 +40,7 @@ def _derive(m):
     ll = m.export("level_list")
     lp = m.export("level_ptr")
     fwd, bwd = [], []
-    LEVEL_TILES = 1024
+    LEVEL_TILES = 608
 
     def kc_of(blocks):
         total = sum(b[3] for b in blocks)
