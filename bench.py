@@ -68,6 +68,8 @@ def parse():
     ap.add_argument("--tol", type=float, default=None, help="PD / adjoint tolerance (default per workload)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 (4x4x8 cantilever) line")
+    ap.add_argument("--no-accuracy", action="store_true",
+                    help="skip the accuracy leg (the profiled mixed rollout against the FP64 path)")
     ap.add_argument("--serve", action="store_true",
                     help="serving workload instead: quadruped requests under Poisson arrivals")
     ap.add_argument("--serve-requests", type=int, default=24)
@@ -279,6 +281,35 @@ def _traffic(wl):
     return e.get("bytes_per_solve"), e.get("source")
 
 
+def accuracy_leg(mesh, sc, wc, wv, d, Tr, K, roll_m, g_m, want):
+    """The metric's error bound, measured: the profiled mixed rollout (the first Tr
+    steps of the timed configuration, its gradients included) against the plain FP64
+    path at tol 1e-10 on the same mesh, refactorised in FP64.  At the 64x64x128 beam
+    no CPU oracle finishes; the FP64 path is pinned to the oracle on smaller meshes
+    by the tests."""
+    import numpy as np
+    import torch
+    from paper_2101_05917_gb300 import api
+    from paper_2101_05917_gb300 import _native as N
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    mesh.factorize(wc, wv, None, None, h=sc.h, gravity=tuple(sc.gravity), precision=N.PD_PREC_FP64)
+    o = api.solver_opts(tol_fwd=1e-10, tol_bwd=1e-10, max_iter_fwd=5000, max_iter_bwd=5000, checkpoint_every=K)
+    r = mesh.forward(d["x0"], d["v0"], Tr, f_ext=d["f"], opts=o)
+    g = mesh.backward(r, Tr, d["lw"], f_ext=d["f"], opts=o, want=want)
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    x_ref, x = r.x[-1].cpu().numpy(), roll_m.x[-1].cpu().numpy()
+    dx, u = x - x_ref, x_ref - sc.x0
+    rel = lambda a, b: float(np.linalg.norm(a - b) / np.linalg.norm(b))
+    return {"reference": "plain FP64 path at tol 1e-10, same mesh (pinned to the CPU oracle on smaller meshes)",
+            "steps": Tr, "position_rel": float(np.linalg.norm(dx) / np.linalg.norm(x_ref)),
+            "displacement_rel": float(np.linalg.norm(dx) / np.linalg.norm(u)),
+            "component_max_rel": float(np.abs(dx).max() / np.abs(u).max()),
+            "grad_rel": {k: rel(g_m[k].cpu().numpy(), g[k].cpu().numpy()) for k in want},
+            "fp64_fwd_iters_per_step": r.stats["fwd_iters"] / Tr, "fp64_s": dt}
+
+
 def fp64_line(dev, steps=5):
     """Plain FP64 method on the 4x4x8 cantilever (675 DoFs, 50 steps, tol 1e-9):
     fwd+bwd sim steps/s with gradients w.r.t. E (through w_corot), nu and v0."""
@@ -467,6 +498,9 @@ def run_ours(args):
     d2h = sum(t.numel() * 8 for t in out_host)
     e2e_value = world * T_e / (e0.elapsed_time(e1) / 1e3)
 
+    accuracy = None
+    if rank == 0 and not args.no_accuracy:
+        accuracy = accuracy_leg(mesh, sc, wc, wv, d, prof_T, K, rp, gp, want)
     fp64 = None
     if rank == 0 and not args.no_fp64:
         fp64 = fp64_line(dev)
@@ -509,6 +543,7 @@ def run_ours(args):
                                 "max": float(lat.max()), "steps": int(lat.size),
                                 "what": "host wall time of one simulation step: forward + recomputation + "
                                         "adjoint"},
+            "accuracy": accuracy,
             "fp64": fp64,
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": "steps/s", "h2d_bytes_per_step": h2d,

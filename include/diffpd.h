@@ -211,6 +211,10 @@ typedef struct {
   int32_t* step_iters;          /* optional host array of T entries: pd_forward stores the
                                    iterations of each step, pd_backward those of each step's
                                    adjoint solve (it overwrites the entries); NULL = none */
+  int32_t fext_per_step;        /* nonzero: f_ext holds one external force per step, (T, n, 3)
+                                   (step t's predictor uses slice t), and pd_backward's g_fext
+                                   receives one gradient per step, (T, n, 3); 0: f_ext is (n, 3),
+                                   the same every step, and g_fext (n, 3) is summed over steps */
 } pd_solver_opts;
 
 typedef struct {
@@ -233,8 +237,10 @@ typedef struct {
 } pd_stats;
 
 /* Forward rollout of T implicit-Euler steps (Sec. 3 Eqns 1-4, Alg. 1).
- * x0, v0: (n,3).  f_ext: (n,3) constant external force added to gravity, or
- * NULL.  act: (T, e) muscle contraction per step, or NULL.  mu: friction
+ * x0, v0: (n,3).  f_ext: external force added to gravity, or NULL: (n,3) the
+ * same every step, or (T, n, 3) one per step with opts->fext_per_step (y of step t
+ * = x_t + h v_t + h^2 M^-1 (f_ext[t] + M g), Eqn 1).  act: (T, e) muscle
+ * contraction per step, or NULL.  mu: friction
  * coefficient of the ground penalty contact (Sec. 5.1).
  * x_traj, v_traj: ((S, n, 3)) with S = T+1, or with checkpointing
  * S = T/K + 1 (T must be a multiple of K) holding states 0, K, 2K, ...
@@ -266,7 +272,9 @@ pd_status pd_plan_checkpoints(pd_mesh m, int32_t T, size_t mem_cap_bytes, int32_
  * (T+1, n, 3), one block per state t = 0..T (with checkpointing as well: a loss
  * on the checkpointed states only puts zeros in the other blocks).  Any other
  * value returns PD_ERR_INVALID_ARG before anything is read.  dL_dv may be NULL.
- * Outputs (each may be NULL): g_x0, g_v0 (n,3); g_fext (n,3) summed over steps;
+ * Outputs (each may be NULL): g_x0, g_v0 (n,3); g_fext (n,3) summed over steps,
+ * or (T, n, 3) per step with opts->fext_per_step (dL/df_ext[t] = z_t, the adjoint
+ * of step t: y depends on f_ext through h^2 M^-1, dL/dy = M z / h^2);
  * g_w_corot, g_w_vol, g_w_muscle (e) = dL/dw per unit volume; g_act (T, e);
  * g_mu (1).  Status as pd_forward (PD_ERR_NOT_CONVERGED for an adjoint solve that
  * reached its cap, PD_ERR_NAN for a non-finite residual in any step). */

@@ -70,7 +70,7 @@ class SolverOpts(ctypes.Structure):
                 ("checkpoint_every", ctypes.c_int32), ("check_every", ctypes.c_int32),
                 ("profile", ctypes.c_int32), ("warm_start", ctypes.c_int32),
                 ("no_graphs", ctypes.c_int32), ("complementarity", ctypes.c_int32), ("step_ms", c_double_p),
-                ("step_iters", ctypes.POINTER(ctypes.c_int32))]
+                ("step_iters", ctypes.POINTER(ctypes.c_int32)), ("fext_per_step", ctypes.c_int32)]
 
 
 class Stats(ctypes.Structure):

@@ -74,6 +74,21 @@ class Rollout:
     checkpoint_every: int = 0   # 0: every state stored; K: states 0, K, 2K, ...
 
 
+def _with_fext_layout(opts, f_ext, T, n):
+    """opts with fext_per_step set from the shape of f_ext ((n, 3) or (T, n, 3));
+    the caller's opts are not modified."""
+    per_step = f_ext is not None and f_ext.dim() == 3
+    if f_ext is not None:
+        want = (T, n, 3) if per_step else (n, 3)
+        if tuple(f_ext.shape) != want:
+            raise ValueError(f"f_ext: expected shape (n, 3) or (T, n, 3) = {(T, n, 3)}, got {tuple(f_ext.shape)}")
+    if bool(opts.fext_per_step) == per_step:
+        return opts
+    o = N.SolverOpts.from_buffer_copy(opts)
+    o.fext_per_step = 1 if per_step else 0
+    return o
+
+
 class PDMesh:
     """A voxel mesh (hexahedra, or six tetrahedra per cell with element_rule
     "tet6") resident on one GPU (pd_create_mesh ... pd_mesh_destroy)."""
@@ -173,8 +188,9 @@ class PDMesh:
     def forward(self, x0, v0, T, f_ext=None, act=None, mu=0.0, opts=None, stream=None,
                 allow_not_converged=False, mem_cap=0) -> Rollout:
         """With opts.checkpoint_every < 0 the interval is planned from mem_cap
-        (pd_plan_checkpoints) and recorded in the returned Rollout."""
-        opts = opts or solver_opts()
+        (pd_plan_checkpoints) and recorded in the returned Rollout.  f_ext is (n, 3),
+        the same every step, or (T, n, 3), one external force per step."""
+        opts = _with_fext_layout(opts or solver_opts(), f_ext, T, self.n)
         K = opts.checkpoint_every
         if K < 0:
             K = self.plan_checkpoints(T, mem_cap)
@@ -192,7 +208,7 @@ class PDMesh:
     def backward(self, roll: Rollout, T, dL_dx, dL_dv=None, loss_all_steps=False, f_ext=None, act=None,
                  mu=0.0, opts=None, stream=None, want=("x0", "v0", "fext", "w_corot", "w_vol", "w_muscle",
                                                         "act", "mu"), allow_not_converged=False):
-        opts = opts or solver_opts()
+        opts = _with_fext_layout(opts or solver_opts(), f_ext, T, self.n)
         if opts.checkpoint_every < 0:   # planned by forward: the rollout carries it
             opts = N.SolverOpts.from_buffer_copy(opts)
             opts.checkpoint_every = roll.checkpoint_every
@@ -218,7 +234,7 @@ class PDMesh:
             return None
         gx0 = alloc("x0", (self.n, 3))
         gv0 = alloc("v0", (self.n, 3))
-        gf = alloc("fext", (self.n, 3))
+        gf = alloc("fext", (T, self.n, 3) if opts.fext_per_step else (self.n, 3))
         gwc = alloc("w_corot", (self.e,))
         gwv = alloc("w_vol", (self.e,))
         gwm = alloc("w_muscle", (self.e,))

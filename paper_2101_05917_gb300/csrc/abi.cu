@@ -1363,6 +1363,8 @@ pd_status pd_forward(pd_mesh mesh, const double* x0, const double* v0, const dou
   bool all_ok = true, any_nan = false;
   for (int t = 0; t < T; ++t) {
     const double* act_t = act ? act + (int64_t)t * m->h.e : nullptr;
+    if (f_ext && o.fext_per_step && t > 0)
+      kept_to_internal_kernel<<<grid_for(n), 256, 0, s>>>(n, m->kept_of_internal, f_ext + (int64_t)t * 3 * n, w.fext);
     double* tx = nullptr;
     double* tv = nullptr;
     if (K <= 0) {
@@ -1450,6 +1452,7 @@ pd_status pd_backward(pd_mesh mesh, const double* x_traj, const double* v_traj, 
   double* seg = nullptr;
   if (K > 0) PD_CUDA_TRY(cudaMallocAsync((void**)&seg, sizeof(double) * 6 * n * (size_t)(K + 1), s));
   double* gfext_int = w.gbar;   // reuse: accumulated dL/df_ext (internal order)
+  const bool per_step_g = g_fext && o.fext_per_step;   // one gradient block per step
   PD_CUDA_TRY(cudaMemsetAsync(gfext_int, 0, sizeof(double) * 3 * n, s));
   if (g_w_corot) PD_CUDA_TRY(cudaMemsetAsync(g_w_corot, 0, sizeof(double) * e, s));
   if (g_w_vol) PD_CUDA_TRY(cudaMemsetAsync(g_w_vol, 0, sizeof(double) * e, s));
@@ -1492,6 +1495,8 @@ pd_status pd_backward(pd_mesh mesh, const double* x_traj, const double* v_traj, 
       for (int t = ta; t < tb - 1; ++t) {
         StepInfo info;
         const double* act_t = act ? act + (int64_t)t * e : nullptr;
+        if (f_ext && o.fext_per_step)
+          kept_to_internal_kernel<<<grid_for(n), 256, 0, s>>>(n, m->kept_of_internal, f_ext + (int64_t)t * 3 * n, w.fext);
         const Range step_range("recompute step", t);
         const auto ts = std::chrono::steady_clock::now();
         pd_status er = forward_step(c, act_t, fext_int, mu, nullptr, nullptr, info, guess_f, t);
@@ -1519,6 +1524,7 @@ pd_status pd_backward(pd_mesh mesh, const double* x_traj, const double* v_traj, 
       StepInfo info;
       const auto ts = std::chrono::steady_clock::now();
       const Range step_range("adjoint step", t);
+      if (per_step_g) PD_CUDA_TRY(cudaMemsetAsync(gfext_int, 0, sizeof(double) * 3 * n, s));
       pd_status er = backward_step(c, xn_int, xt_int, vt_int, act_t, mu, loss_x(t), loss_v(t), gfext_int,
                                    g_w_corot, g_w_vol, g_w_muscle, g_act ? g_act + (int64_t)t * e : nullptr,
                                    g_mu, info, guess_b, t);
@@ -1526,6 +1532,9 @@ pd_status pd_backward(pd_mesh mesh, const double* x_traj, const double* v_traj, 
         o.step_ms[t] += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - ts).count();
       if (o.step_iters) o.step_iters[t] = info.iters;
       if (er != PD_OK) return er;
+      if (per_step_g)
+        internal_to_kept_kernel<<<grid_for(n), 256, 0, s>>>(n, n, m->kept_of_internal, gfext_int,
+                                                            g_fext + (int64_t)t * 3 * n);
       accumulate(stats, info, false);
       if (!info.converged) all_ok = false;
       if (info.nan) any_nan = true;
@@ -1533,7 +1542,8 @@ pd_status pd_backward(pd_mesh mesh, const double* x_traj, const double* v_traj, 
   }
   if (g_x0) internal_to_kept_kernel<<<grid_for(n), 256, 0, s>>>(n, n, m->kept_of_internal, w.ax, g_x0);
   if (g_v0) internal_to_kept_kernel<<<grid_for(n), 256, 0, s>>>(n, n, m->kept_of_internal, w.av, g_v0);
-  if (g_fext) internal_to_kept_kernel<<<grid_for(n), 256, 0, s>>>(n, n, m->kept_of_internal, gfext_int, g_fext);
+  if (g_fext && !per_step_g)
+    internal_to_kept_kernel<<<grid_for(n), 256, 0, s>>>(n, n, m->kept_of_internal, gfext_int, g_fext);
   if (seg) PD_CUDA_TRY(cudaFreeAsync(seg, s));
   PD_CUDA_TRY(cudaStreamSynchronize(s));
   check_flags(c, stats);

@@ -317,6 +317,7 @@ void run_job(pd_server s, Slot& sl, const Job& j, Done& d) {
   o.profile = 0;
   o.step_ms = nullptr;   // the request's host pointers do not outlive the submit call
   o.step_iters = nullptr;
+  o.fext_per_step = 0;   // a request carries one (n,3) force for the whole rollout
   pd_stats fs{}, bs{};
   st = pd_forward(m, sl.x0.p, sl.v0.p, fext, act, j.mu, j.T, &o, sl.xs.p, sl.vs.p, &fs, q);
   r.fwd_iters = fs.fwd_iters;

@@ -146,3 +146,19 @@ def test_checkpoint_plan_follows_the_memory_cap(native):
     with pytest.raises(native.PDError):   # host-only mesh: the cap is required
         m.plan_checkpoints(T, 0)
     m.close()
+
+
+def test_fext_layout_from_shape():
+    """The Python front end sets fext_per_step from f_ext's shape ((n, 3) or
+    (T, n, 3)) on a copy of the caller's options and rejects other shapes."""
+    import torch
+    from paper_2101_05917_gb300 import api
+    o = api.solver_opts()
+    n, T = 7, 4
+    assert api._with_fext_layout(o, None, T, n).fext_per_step == 0
+    assert api._with_fext_layout(o, torch.zeros((n, 3)), T, n).fext_per_step == 0
+    p = api._with_fext_layout(o, torch.zeros((T, n, 3)), T, n)
+    assert p.fext_per_step == 1 and o.fext_per_step == 0
+    for bad in ((T + 1, n, 3), (n, 2), (T, n)):
+        with pytest.raises(ValueError):
+            api._with_fext_layout(o, torch.zeros(bad), T, n)
