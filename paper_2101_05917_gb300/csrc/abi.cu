@@ -308,6 +308,23 @@ pd_status poll(Ctx& c) {
     } break;                         \
   }
 
+// runs the statement with MX bound as above and H to the L-BFGS history type: float
+// in mixed precision (the history buffers, allocated as doubles, hold floats then),
+// double otherwise
+#define PD_WITH_MX_H(c, ...)                        \
+  if ((c).m->precision == PD_PREC_MIXED) {          \
+    using H = float;                                \
+    PD_WITH_MX((c).mx, __VA_ARGS__);                \
+  } else {                                          \
+    using H = double;                               \
+    PD_WITH_MX((c).mx, __VA_ARGS__);                \
+  }
+
+template <typename H>
+H* hist(double* p) {
+  return reinterpret_cast<H*>(p);
+}
+
 // Complementarity contact: the global step of an iteration restricted to the free
 // nodes outside the held set (Alg. 3 / Alg. 5 global step, computed as in
 // kernels_contact.cu with zero targets: held rows of the direction stay zero).
@@ -332,14 +349,15 @@ pd_status launch_fwd_iteration(Ctx& c, int prec, const double* act_t) {
   if (timed) c.local_t->record(c.s);
   PD_CUDA_TRY(launch_gather_grad(m, st, w.elembuf, prec, w.xt, w.y, w.dir, w.gradt, c.pg, c.s));
   decide_fwd_kernel<<<1, 256, 0, c.s>>>(st, c.pe, c.nbe, c.pg, c.nbg);
-  PD_WITH_MX(c.mx, lbfgs_commit_fwd_kernel<MX><<<c.lb, 256, 0, c.s>>>(c.vc, w.x, w.xt, w.grad, w.gradt, w.S, w.Y));
-  PD_WITH_MX(c.mx, lbfgs_q_kernel<MX><<<c.lb, 256, 0, c.s>>>(c.vc, w.grad, w.Y, w.q));
+  PD_WITH_MX_H(c, lbfgs_commit_fwd_kernel<MX, H><<<c.lb, 256, 0, c.s>>>(c.vc, w.x, w.xt, w.grad, w.gradt,
+                                                                         hist<H>(w.S), hist<H>(w.Y)));
+  PD_WITH_MX_H(c, lbfgs_q_kernel<MX, H><<<c.lb, 256, 0, c.s>>>(c.vc, w.grad, hist<H>(w.Y), w.q));
   if (c.solve_t) c.solve_t->record(c.s);
   PD_CUDA_TRY(solve_A(m, st, w.q, w.r, m->precision, c.s));
   if (c.solve_t) c.solve_t->record(c.s);
   PD_CUDA_TRY(held_correction(m, w.r, c.s));
-  PD_WITH_MX(c.mx, lbfgs_post_dots_kernel<MX><<<c.lb, 256, 0, c.s>>>(c.vc, w.grad, w.Y, w.r));
-  PD_WITH_MX(c.mx, lbfgs_dir_kernel<MX><<<c.lb, 256, 0, c.s>>>(c.vc, w.S, w.r, w.dir, w.x, w.xt));
+  PD_WITH_MX_H(c, lbfgs_post_dots_kernel<MX, H><<<c.lb, 256, 0, c.s>>>(c.vc, w.grad, hist<H>(w.Y), w.r));
+  PD_WITH_MX_H(c, lbfgs_dir_kernel<MX, H><<<c.lb, 256, 0, c.s>>>(c.vc, hist<H>(w.S), w.r, w.dir, w.x, w.xt));
   c.launches += 9;
   c.solves += 1;
   c.locals += 1;
@@ -353,14 +371,15 @@ pd_status launch_bwd_iteration(Ctx& c, int prec, const double* xnext, const doub
   MeshImpl* m = c.m;
   Workspace& w = m->ws;
   IterState* st = w.st;
-  PD_WITH_MX(c.mx, lbfgs_commit_bwd_kernel<MX><<<c.lb, 256, 0, c.s>>>(c.vc, w.dir, w.Hd, w.z, w.gs, w.S, w.Y));
-  PD_WITH_MX(c.mx, lbfgs_q_kernel<MX><<<c.lb, 256, 0, c.s>>>(c.vc, w.gs, w.Y, w.q));
+  PD_WITH_MX_H(c, lbfgs_commit_bwd_kernel<MX, H><<<c.lb, 256, 0, c.s>>>(c.vc, w.dir, w.Hd, w.z, w.gs,
+                                                                         hist<H>(w.S), hist<H>(w.Y)));
+  PD_WITH_MX_H(c, lbfgs_q_kernel<MX, H><<<c.lb, 256, 0, c.s>>>(c.vc, w.gs, hist<H>(w.Y), w.q));
   if (c.solve_t) c.solve_t->record(c.s);
   PD_CUDA_TRY(solve_A(m, st, w.q, w.r, m->precision, c.s));
   if (c.solve_t) c.solve_t->record(c.s);
   PD_CUDA_TRY(held_correction(m, w.r, c.s));
-  PD_WITH_MX(c.mx, lbfgs_post_dots_kernel<MX><<<c.lb, 256, 0, c.s>>>(c.vc, w.gs, w.Y, w.r));
-  PD_WITH_MX(c.mx, lbfgs_dir_kernel<MX><<<c.lb, 256, 0, c.s>>>(c.vc, w.S, w.r, w.dir, nullptr, nullptr));
+  PD_WITH_MX_H(c, lbfgs_post_dots_kernel<MX, H><<<c.lb, 256, 0, c.s>>>(c.vc, w.gs, hist<H>(w.Y), w.r));
+  PD_WITH_MX_H(c, lbfgs_dir_kernel<MX, H><<<c.lb, 256, 0, c.s>>>(c.vc, hist<H>(w.S), w.r, w.dir, nullptr, nullptr));
   c.launches += 9;
   c.solves += 1;
   LocalArgs la{m, st, xnext, w.dir, act_t, prec};

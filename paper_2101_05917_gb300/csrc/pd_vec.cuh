@@ -421,45 +421,50 @@ __device__ __forceinline__ void first_loop_coefficients(LbfgsScalars& L) {
 // s_i . gn over the stored pairs (newest first) and, after a push into `slot`,
 // s_i . y_slot and s_slot . y_i.  The pushed pair's own entries (ss, ys) come from
 // registers; every other history entry was loaded before the entry's stores.
-template <int MX>
+template <int MX, typename H>
 __device__ __forceinline__ void accumulate_first_loop(const int* idx, int cnt, bool push, int slot,
-                                                      const double* si, const double* yi, double gn, double ss,
-                                                      double ys, double* sg, double* a, double* b) {
+                                                      const H* si, const H* yi, H gn, H ss,
+                                                      H ys, H* sg, H* a, H* b) {
 #pragma unroll
   for (int k = 0; k < MX; ++k) {
     const bool fresh = push && k < cnt && idx[k] == slot;
-    const double sk = fresh ? ss : si[k];
-    const double yk = fresh ? ys : yi[k];
+    const H sk = fresh ? ss : si[k];
+    const H yk = fresh ? ys : yi[k];
     sg[k] += sk * gn;
     a[k] += sk * ys;
     b[k] += ss * yk;
   }
 }
 
-template <int MX>
-__device__ __forceinline__ int first_loop_to_shared(int cnt, bool push, const double* sg, const double* a,
-                                                    const double* b, double (*sh)[kT / 32], int k0) {
+template <int MX, typename H>
+__device__ __forceinline__ int first_loop_to_shared(int cnt, bool push, const H* sg, const H* a,
+                                                    const H* b, double (*sh)[kT / 32], int k0) {
   int K = k0;
 #pragma unroll
   for (int k = 0; k < MX; ++k)
-    if (k < cnt) dot_to_shared(sg[k], sh, K++);
+    if (k < cnt) dot_to_shared((double)sg[k], sh, K++);
   if (push) {
 #pragma unroll
     for (int k = 0; k < MX; ++k) {
       if (k < cnt) {
-        dot_to_shared(a[k], sh, K++);
-        dot_to_shared(b[k], sh, K++);
+        dot_to_shared((double)a[k], sh, K++);
+        dot_to_shared((double)b[k], sh, K++);
       }
     }
   }
   return K;
 }
 
+// History storage H: double in FP64 meshes; float in mixed precision, where the
+// history only shapes the search direction (the iterate, gradient and convergence
+// test stay FP64) and the per-thread products are formed in FP32 (GB300's FP64
+// pipe is a small fraction of its FP32 pipe), then reduced in FP64.
+
 // forward, before the solve: commit an accepted trial (history pair, x, grad) and
 // form the first-loop products in the same pass; then the coefficients
-template <int MX>
+template <int MX, typename H>
 __global__ void __launch_bounds__(kT) lbfgs_commit_fwd_kernel(VecCtx c, double* x, const double* xt, double* grad,
-                                                             const double* gradt, double* S, double* Y) {
+                                                             const double* gradt, H* S, H* Y) {
   IterState* st = c.st;
   if (!st->accepted) return;
   const int64_t n3 = c.n3;
@@ -467,23 +472,24 @@ __global__ void __launch_bounds__(kT) lbfgs_commit_fwd_kernel(VecCtx c, double* 
   const bool conv = st->converged;
   int idx[MX];
   ring_newest<MX>(st, idx);
-  const double* sp[MX];
-  const double* yp[MX];
+  const H* sp[MX];
+  const H* yp[MX];
 #pragma unroll
-  for (int k = 0; k < MX; ++k) {   // unused entries read xt (a valid address)
-    sp[k] = k < cnt ? S + (int64_t)idx[k] * n3 : xt;
-    yp[k] = (k < cnt && push) ? Y + (int64_t)idx[k] * n3 : xt;
+  for (int k = 0; k < MX; ++k) {   // unused entries read slot 0 of S (a valid address)
+    sp[k] = k < cnt ? S + (int64_t)idx[k] * n3 : S;
+    yp[k] = (k < cnt && push) ? Y + (int64_t)idx[k] * n3 : S;
   }
-  double sg[MX], a[MX], b[MX];
+  H sg[MX], a[MX], b[MX];
 #pragma unroll
-  for (int k = 0; k < MX; ++k) sg[k] = a[k] = b[k] = 0.0;
+  for (int k = 0; k < MX; ++k) sg[k] = a[k] = b[k] = H(0);
   // two entries per iteration, every load of both issued before any store
   const int64_t stride = (int64_t)gridDim.x * kT;
   for (int64_t e0 = (int64_t)blockIdx.x * kT + threadIdx.x; e0 < n3; e0 += 2 * stride) {
     const int64_t e1 = e0 + stride;
     const bool v1 = e1 < n3;
     const int64_t f1 = v1 ? e1 : e0;
-    double xn[2], gn[2], xo[2], go[2], si[2][MX], yi[2][MX];
+    double xn[2], gn[2], xo[2], go[2];
+    H si[2][MX], yi[2][MX];
 #pragma unroll
     for (int u = 0; u < 2; ++u) {
       const int64_t e = u ? f1 : e0;
@@ -492,30 +498,30 @@ __global__ void __launch_bounds__(kT) lbfgs_commit_fwd_kernel(VecCtx c, double* 
       xo[u] = x[e];
       go[u] = grad[e];
 #pragma unroll
-      for (int k = 0; k < MX; ++k) {
-        si[u][k] = sp[k][e];
-        yi[u][k] = yp[k][e];
+      for (int k = 0; k < MX; ++k) {   // entries past the count are not used
+        si[u][k] = k < cnt ? sp[k][e] : H(0);
+        yi[u][k] = (k < cnt && push) ? yp[k][e] : H(0);
       }
     }
 #pragma unroll
     for (int u = 0; u < 2; ++u) {
       if (u == 1 && !v1) break;
       const int64_t e = u ? e1 : e0;
-      const double ss = xn[u] - xo[u], ys = gn[u] - go[u];
+      const H ss = (H)(xn[u] - xo[u]), ys = (H)(gn[u] - go[u]);
       if (push) {
         S[(int64_t)slot * n3 + e] = ss;
         Y[(int64_t)slot * n3 + e] = ys;
       }
       x[e] = xn[u];
       grad[e] = gn[u];
-      accumulate_first_loop<MX>(idx, cnt, push != 0, slot, si[u], yi[u], gn[u], ss, ys, sg, a, b);
+      accumulate_first_loop<MX, H>(idx, cnt, push != 0, slot, si[u], yi[u], (H)gn[u], ss, ys, sg, a, b);
     }
   }
   // a converged solve still records the new pair's products (history kept for the next step)
   if (conv && !push) return;
   __shared__ double sh[kMaxDots][kT / 32];
   __shared__ double tot[kMaxDots];
-  const int K = first_loop_to_shared<MX>(cnt, push != 0, sg, a, b, sh, 0);
+  const int K = first_loop_to_shared<MX, H>(cnt, push != 0, sg, a, b, sh, 0);
   if (!finish_dots(K, sh, c.lpart, c.lcounter, tot)) return;
   __shared__ LbfgsScalars L;
   scalars_load(st, L);
@@ -530,9 +536,9 @@ __global__ void __launch_bounds__(kT) lbfgs_commit_fwd_kernel(VecCtx c, double* 
 // gs += alpha Hd (history pair alpha (d, Hd)) and test |gs| for convergence, with
 // the first-loop products in the same pass; then the coefficients.  The first
 // iteration of a step (or the one after a residual replacement) has no step to apply.
-template <int MX>
+template <int MX, typename H>
 __global__ void __launch_bounds__(kT) lbfgs_commit_bwd_kernel(VecCtx c, const double* d, const double* Hd, double* z,
-                                                             double* gs, double* S, double* Y) {
+                                                             double* gs, H* S, H* Y) {
   IterState* st = c.st;
   if (st->converged) return;
   const int64_t n3 = c.n3;
@@ -541,23 +547,24 @@ __global__ void __launch_bounds__(kT) lbfgs_commit_bwd_kernel(VecCtx c, const do
   const double al = pending ? st->alpha : 0.0;
   int idx[MX];
   ring_newest<MX>(st, idx);
-  const double* sp[MX];
-  const double* yp[MX];
+  const H* sp[MX];
+  const H* yp[MX];
 #pragma unroll
   for (int k = 0; k < MX; ++k) {
-    sp[k] = k < cnt ? S + (int64_t)idx[k] * n3 : gs;
-    yp[k] = (k < cnt && push) ? Y + (int64_t)idx[k] * n3 : gs;
+    sp[k] = k < cnt ? S + (int64_t)idx[k] * n3 : S;
+    yp[k] = (k < cnt && push) ? Y + (int64_t)idx[k] * n3 : S;
   }
-  double sg[MX], a[MX], b[MX];
+  H sg[MX], a[MX], b[MX];
 #pragma unroll
-  for (int k = 0; k < MX; ++k) sg[k] = a[k] = b[k] = 0.0;
+  for (int k = 0; k < MX; ++k) sg[k] = a[k] = b[k] = H(0);
   double part = 0;
   const int64_t stride = (int64_t)gridDim.x * kT;
   for (int64_t e0 = (int64_t)blockIdx.x * kT + threadIdx.x; e0 < n3; e0 += 2 * stride) {
     const int64_t e1 = e0 + stride;
     const bool v1 = e1 < n3;
     const int64_t f1 = v1 ? e1 : e0;
-    double go[2], dd[2], hh[2], zz[2], si[2][MX], yi[2][MX];
+    double go[2], dd[2], hh[2], zz[2];
+    H si[2][MX], yi[2][MX];
 #pragma unroll
     for (int u = 0; u < 2; ++u) {
       const int64_t e = u ? f1 : e0;
@@ -566,9 +573,9 @@ __global__ void __launch_bounds__(kT) lbfgs_commit_bwd_kernel(VecCtx c, const do
       hh[u] = pending ? Hd[e] : 0.0;
       zz[u] = pending ? z[e] : 0.0;
 #pragma unroll
-      for (int k = 0; k < MX; ++k) {
-        si[u][k] = sp[k][e];
-        yi[u][k] = yp[k][e];
+      for (int k = 0; k < MX; ++k) {   // entries past the count are not used
+        si[u][k] = k < cnt ? sp[k][e] : H(0);
+        yi[u][k] = (k < cnt && push) ? yp[k][e] : H(0);
       }
     }
 #pragma unroll
@@ -583,12 +590,12 @@ __global__ void __launch_bounds__(kT) lbfgs_commit_bwd_kernel(VecCtx c, const do
         gn = go[u] + ah;
         gs[e] = gn;
         if (push) {
-          S[(int64_t)slot * n3 + e] = ad;
-          Y[(int64_t)slot * n3 + e] = ah;
+          S[(int64_t)slot * n3 + e] = (H)ad;
+          Y[(int64_t)slot * n3 + e] = (H)ah;
         }
         part += gn * gn;
       }
-      accumulate_first_loop<MX>(idx, cnt, push != 0, slot, si[u], yi[u], gn, ad, ah, sg, a, b);
+      accumulate_first_loop<MX, H>(idx, cnt, push != 0, slot, si[u], yi[u], (H)gn, (H)ad, (H)ah, sg, a, b);
     }
   }
   __shared__ double sh[kMaxDots][kT / 32];
@@ -598,7 +605,7 @@ __global__ void __launch_bounds__(kT) lbfgs_commit_bwd_kernel(VecCtx c, const do
     dot_to_shared(part, sh, 0);
     K0 = 1;
   }
-  const int K = first_loop_to_shared<MX>(cnt, push != 0, sg, a, b, sh, K0);
+  const int K = first_loop_to_shared<MX, H>(cnt, push != 0, sg, a, b, sh, K0);
   if (!finish_dots(K, sh, c.lpart, c.lcounter, tot)) return;
   __shared__ LbfgsScalars L;
   scalars_load(st, L);
@@ -624,36 +631,43 @@ __global__ void __launch_bounds__(kT) lbfgs_commit_bwd_kernel(VecCtx c, const do
 }
 
 // q = g - sum al_i y_i (newest first, as the first loop subtracts them)
-template <int MX>
-__global__ void __launch_bounds__(kT) lbfgs_q_kernel(VecCtx c, const double* g, const double* Y, double* q) {
+template <int MX, typename H>
+__global__ void __launch_bounds__(kT) lbfgs_q_kernel(VecCtx c, const double* g, const H* Y, double* q) {
   const IterState* st = c.st;
   if (st->converged || !st->accepted) return;
   const int64_t n3 = c.n3;
   const int cnt = st->count;
   int idx[MX];
-  double al[MX];
+  H al[MX];
   ring_newest<MX>(st, idx);
 #pragma unroll
-  for (int k = 0; k < MX; ++k) al[k] = k < cnt ? st->al[idx[k]] : 0.0;
-  const double* yp[MX];
+  for (int k = 0; k < MX; ++k) al[k] = k < cnt ? (H)st->al[idx[k]] : H(0);
+  const H* yp[MX];
 #pragma unroll
-  for (int k = 0; k < MX; ++k) yp[k] = k < cnt ? Y + (int64_t)idx[k] * n3 : g;   // al = 0 past the count
+  for (int k = 0; k < MX; ++k) yp[k] = k < cnt ? Y + (int64_t)idx[k] * n3 : Y;   // al = 0 past the count
   PD_FOR_MINE(e) {
-    double yv[MX];
+    H yv[MX];
 #pragma unroll
-    for (int k = 0; k < MX; ++k) yv[k] = yp[k][e];
-    double v = g[e];
+    for (int k = 0; k < MX; ++k) yv[k] = k < cnt ? yp[k][e] : H(0);
+    if constexpr (sizeof(H) == 8) {
+      double v = g[e];
 #pragma unroll
-    for (int k = 0; k < MX; ++k) v -= al[k] * yv[k];
-    q[e] = v;
+      for (int k = 0; k < MX; ++k) v -= al[k] * yv[k];
+      q[e] = v;
+    } else {
+      H u = H(0);
+#pragma unroll
+      for (int k = 0; k < MX; ++k) u += al[k] * yv[k];
+      q[e] = g[e] - (double)u;
+    }
   }
 }
 
 // after the solve r0 = A^-1 q: products y_i . r0 and r0 . g, then be_i oldest ->
 // newest, the coefficients cf_i = al_i - be_i and the slope d . g of
 // d = -(r0 + sum cf_i s_i)
-template <int MX>
-__global__ void __launch_bounds__(kT) lbfgs_post_dots_kernel(VecCtx c, const double* g, const double* Y,
+template <int MX, typename H>
+__global__ void __launch_bounds__(kT) lbfgs_post_dots_kernel(VecCtx c, const double* g, const H* Y,
                                                             const double* r) {
   IterState* st = c.st;
   if (st->converged || !st->accepted) return;
@@ -663,38 +677,40 @@ __global__ void __launch_bounds__(kT) lbfgs_post_dots_kernel(VecCtx c, const dou
   __shared__ double tot[kMaxDots];
   int idx[MX];
   ring_oldest<MX>(st, idx);
-  double yr[MX];
+  H yr[MX];
 #pragma unroll
-  for (int k = 0; k < MX; ++k) yr[k] = 0.0;
+  for (int k = 0; k < MX; ++k) yr[k] = H(0);
   double rg = 0.0;
-  const double* yp[MX];
+  const H* yp[MX];
 #pragma unroll
-  for (int k = 0; k < MX; ++k) yp[k] = k < cnt ? Y + (int64_t)idx[k] * n3 : g;
+  for (int k = 0; k < MX; ++k) yp[k] = k < cnt ? Y + (int64_t)idx[k] * n3 : Y;
   const int64_t stride = (int64_t)gridDim.x * kT;
   for (int64_t e0 = (int64_t)blockIdx.x * kT + threadIdx.x; e0 < n3; e0 += 2 * stride) {
     const int64_t e1 = e0 + stride;
     const bool v1 = e1 < n3;
     const int64_t f1 = v1 ? e1 : e0;
-    double re[2], ge[2], yv[2][MX];
+    double re[2], ge[2];
+    H yv[2][MX];
 #pragma unroll
     for (int u = 0; u < 2; ++u) {
       const int64_t e = u ? f1 : e0;
       re[u] = r[e];
       ge[u] = g[e];
 #pragma unroll
-      for (int k = 0; k < MX; ++k) yv[u][k] = yp[k][e];
+      for (int k = 0; k < MX; ++k) yv[u][k] = k < cnt ? yp[k][e] : H(0);
     }
 #pragma unroll
     for (int u = 0; u < 2; ++u) {
       if (u == 1 && !v1) break;
       rg += re[u] * ge[u];
+      const H rh = (H)re[u];
 #pragma unroll
-      for (int k = 0; k < MX; ++k) yr[k] += yv[u][k] * re[u];
+      for (int k = 0; k < MX; ++k) yr[k] += yv[u][k] * rh;
     }
   }
 #pragma unroll
   for (int k = 0; k < MX; ++k)
-    if (k < cnt) dot_to_shared(yr[k], sh, k);
+    if (k < cnt) dot_to_shared((double)yr[k], sh, k);
   dot_to_shared(rg, sh, cnt);
   if (!finish_dots(cnt + 1, sh, c.lpart, c.lcounter, tot)) return;
   __shared__ LbfgsScalars L;
@@ -718,8 +734,8 @@ __global__ void __launch_bounds__(kT) lbfgs_post_dots_kernel(VecCtx c, const dou
 
 // d = -(r0 + sum cf_i s_i) (oldest first, as the second loop adds them); forward:
 // trial xt = x + d, or xt = x + alpha d after a rejected trial
-template <int MX>
-__global__ void __launch_bounds__(kT) lbfgs_dir_kernel(VecCtx c, const double* S, const double* r, double* d,
+template <int MX, typename H>
+__global__ void __launch_bounds__(kT) lbfgs_dir_kernel(VecCtx c, const H* S, const double* r, double* d,
                                                       const double* x, double* xt) {
   const IterState* st = c.st;
   if (st->converged) return;
@@ -731,20 +747,28 @@ __global__ void __launch_bounds__(kT) lbfgs_dir_kernel(VecCtx c, const double* S
   }
   const int cnt = st->count;
   int idx[MX];
-  double cf[MX];
+  H cf[MX];
   ring_oldest<MX>(st, idx);
 #pragma unroll
-  for (int k = 0; k < MX; ++k) cf[k] = k < cnt ? st->cf[idx[k]] : 0.0;
-  const double* sp[MX];
+  for (int k = 0; k < MX; ++k) cf[k] = k < cnt ? (H)st->cf[idx[k]] : H(0);
+  const H* sp[MX];
 #pragma unroll
-  for (int k = 0; k < MX; ++k) sp[k] = k < cnt ? S + (int64_t)idx[k] * n3 : r;   // cf = 0 past the count
+  for (int k = 0; k < MX; ++k) sp[k] = k < cnt ? S + (int64_t)idx[k] * n3 : S;   // cf = 0 past the count
   PD_FOR_MINE(e) {
-    double sv[MX];
+    H sv[MX];
 #pragma unroll
-    for (int k = 0; k < MX; ++k) sv[k] = sp[k][e];
-    double v = r[e];
+    for (int k = 0; k < MX; ++k) sv[k] = k < cnt ? sp[k][e] : H(0);
+    double v;
+    if constexpr (sizeof(H) == 8) {
+      v = r[e];
 #pragma unroll
-    for (int k = 0; k < MX; ++k) v += cf[k] * sv[k];
+      for (int k = 0; k < MX; ++k) v += cf[k] * sv[k];
+    } else {
+      H u = H(0);
+#pragma unroll
+      for (int k = 0; k < MX; ++k) u += cf[k] * sv[k];
+      v = r[e] + (double)u;
+    }
     d[e] = -v;
     if (xt) xt[e] = x[e] - v;
   }
