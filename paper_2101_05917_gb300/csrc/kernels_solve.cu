@@ -330,9 +330,11 @@ __device__ __forceinline__ void sum_W(const SolveParams& p, int64_t position, bo
 
 // shared memory of one tile body (as T): forward rhs[2][kMaxC][3] (double buffer)
 // + red[kThreads][3]; backward v[2][kMaxBR][3] (double buffer) + res[64][3]
+constexpr int kTileSmemElems = (2 * kMaxBR + 64) * 3 > 2 * kMaxC * 4 + kThreads * 3
+                                   ? (2 * kMaxBR + 64) * 3 : 2 * kMaxC * 4 + kThreads * 3;
 template <typename T>
 struct __align__(16) TileSmem {
-  T buf[(2 * kMaxBR + 64) * 3];
+  T buf[kTileSmemElems];   // the larger of the backward and forward layouts above
   int flag;
 };
 
