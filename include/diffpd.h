@@ -140,8 +140,8 @@ enum {
                                 256/128/64 rows, 3-6 backward column blocks of 64/32/16/8
                                 columns), first row (forward) or column (backward) of its
                                 block, index of its first chunk within the block, its chunks
-                                (forward: column ranges of 48 columns per row group; backward:
-                                row ranges of min(12288 / columns, 512) rows), offset of its
+                                (forward: column ranges of 32 columns per row group; backward:
+                                row ranges of min(8192 / columns, 256) rows), offset of its
                                 first chunk in the FP32 streamed copy (floats), bytes of each
                                 chunk but its last, bytes of its last chunk, the last chunk's
                                 columns (forward; they fill the row groups in order) or rows

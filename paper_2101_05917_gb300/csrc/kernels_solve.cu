@@ -17,9 +17,9 @@
 // its first column down.  A tile is processed by one CTA from start to end, so its
 // sums never leave the CTA: there are no partial sums between CTAs and no
 // reductions across tiles, and the result does not depend on scheduling.  The
-// panel values of a tile flow through the CTA in chunks of at most 256 x 48
-// entries: forward chunks are ranges of 48 columns per row group (256 / R
-// groups), backward chunks ranges of 12288 / BC rows (at most 512).
+// panel values of a tile flow through the CTA in chunks of at most 256 x 32
+// entries: forward chunks are ranges of 32 columns per row group (256 / R
+// groups), backward chunks ranges of 8192 / BC rows (at most 256).
 //
 // FP32: every chunk is stored contiguously in the order the tile body reads it
 // (MeshImpl::Qs, packed once per factorisation; zeros for the upper triangle of
@@ -40,12 +40,12 @@ namespace {
 
 constexpr int kThreads = 256;         // tile-body threads per CTA (8 warps)
 constexpr int kWarps = kThreads / 32;
-constexpr int kCols = 48;             // forward: columns per thread and chunk
-constexpr int kChunkElems = kThreads * kCols;   // panel entries per chunk at most (48 KB in FP32)
+constexpr int kCols = 32;             // forward: columns per thread and chunk
+constexpr int kChunkElems = kThreads * kCols;   // panel entries per chunk at most (32 KB in FP32)
 constexpr int kMaxC = 4 * kCols;      // widest forward chunk (4 column groups)
-// backward chunk rows for BC columns: kChunkElems / BC, at most 512 (16 rows per lane;
-// the double-buffered right-hand side of two CTAs then fits beside their stages)
-constexpr int kMaxBR = 512;
+// backward chunk rows for BC columns: kChunkElems / BC, at most 256 (8 rows per lane;
+// the double-buffered right-hand side of three CTAs then fits beside their stages)
+constexpr int kMaxBR = 256;
 __host__ __device__ constexpr int bwd_chunk_rows(int bc) { return kChunkElems / bc < kMaxBR ? kChunkElems / bc : kMaxBR; }
 constexpr int kPreSlots = 4;          // W-row sources per position held in registers
 constexpr int kPart = kThreads * 3;   // partial-sum slots per tile (forward rows / backward columns x 3)
@@ -339,14 +339,14 @@ struct __align__(16) TileSmem {
 };
 
 // ------------------------------------------------------------ forward tile
-// Row block [a, a + rv) of panel s, rv <= R, over its chunks of G * 48 columns
+// Row block [a, a + rv) of panel s, rv <= R, over its chunks of G * 32 columns
 // (G = kThreads / R).  Thread (row rl, group g) owns row a + rl and, in a chunk,
-// the group's columns 48 g ... (fewer in a block's last chunk: its L columns fill
+// the group's columns 32 g ... (fewer in a block's last chunk: its L columns fill
 // the groups in order).  Chunks are added in order, the group sums in group order
 // at the end.
 //
 // The chunk's right-hand side rows rhs = b - (children's updates) are loaded one
-// chunk ahead: thread jj < G 48 owns column jj of the next chunk.
+// chunk ahead: thread jj < G 32 owns column jj of the next chunk.
 template <typename T, int R>
 __device__ void fwd_tile(const SolveParams& p, const SolveTile& tl, int64_t tile, unsigned long long epoch,
                          TileSmem<T>& sm, Ring* ring) {
@@ -436,7 +436,7 @@ __device__ void fwd_tile(const SolveParams& p, const SolveTile& tl, int64_t tile
     load_W<T>(p, pos + jn, has && kids, wc);
     if constexpr (kStream) {
       // stored layout [group][column k < kmax_g][row rl < rv]: group g holds
-      // kmax_g = clamp(L - 48 g, 0, 48) of the chunk's L columns; zeros past each
+      // kmax_g = clamp(L - 32 g, 0, 32) of the chunk's L columns; zeros past each
       // row's columns
       if (c > 0 && !ring->wait()) return;
       const float* stage = ring->data();
@@ -528,7 +528,7 @@ __device__ void fwd_tile(const SolveParams& p, const SolveTile& tl, int64_t tile
 
 // ------------------------------------------------------------ backward tile
 // Column block [a, a + bcv) of panel s, bcv <= BC, over rows [a, nr) in chunks of
-// BR = min(12288 / BC, 1024) rows.  Warp w owns columns a + w CW ... (CW = BC / 8),
+// BR = min(8192 / BC, 256) rows.  Warp w owns columns a + w CW ... (CW = BC / 8),
 // its lanes the chunk's rows lane + 32 i; per column the lanes' sums are added by
 // a fixed shuffle tree at the end.  v = [u_s; -x(below rows)] of the next chunk's
 // rows is gathered one chunk ahead (thread t owns rows t + 256 k of a chunk).
@@ -806,9 +806,11 @@ extern __shared__ __align__(128) unsigned char solve_dsm[];
 // skips its products.  A body wait that gives up leaves after waiting once more,
 // bounded, for that stage's copy; the producer stops at the first stage wait that
 // gives up, or when the body has given up.
-// Two CTAs of 288 threads per SM: 18 warps over the SM's four register-file
-// quarters leave at most 96 registers per thread.
-__global__ void __launch_bounds__(kPipeThreads, 2) solve_pipe_kernel(SolveParams p) {
+// Three CTAs of 288 threads per SM (72 registers per thread, 2 x 32 KB stages and
+// 7.4 KB of tile-body buffers each): more tiles in flight per SM hide more of each
+// tile's dependency, gather and release latency (the 64x64x128 beam's solve pair
+// took 11 % less time than with two CTAs of 2 x 48 KB stages).
+__global__ void __launch_bounds__(kPipeThreads, 3) solve_pipe_kernel(SolveParams p) {
   if (p.gate && (p.gate->converged || !p.gate->accepted)) return;
   __shared__ TileSmem<float> sm;
   __shared__ PipeStage stg[kStages];
@@ -1035,7 +1037,7 @@ void build_solve_schedule(const HostMesh& h, SolveSchedule& S) {
   }
   // streamed FP32 layout, tile after tile in persistent order, chunk after chunk,
   // each chunk 16-byte aligned: forward [group][column k < kmax_g][row < rv] with
-  // kmax_g = clamp(L - 48 g, 0, 48) for a chunk of L columns, backward [column <
+  // kmax_g = clamp(L - 32 g, 0, 32) for a chunk of L columns, backward [column <
   // bcv][row < rn]
   int64_t off = 0, chunks = 0;
   for (SolveTile& t : S.all) {
@@ -1085,7 +1087,7 @@ __global__ void pack_stream_kernel(const SolveTile* tiles, const float* Q, float
       const int64_t L = last ? tl.lld : (int64_t)G * kCols;
       total = L * rv;
       for (int64_t i = threadIdx.x; i < total; i += blockDim.x) {
-        // groups before the chunk's last nonempty one hold 48 columns each
+        // groups before the chunk's last nonempty one hold 32 columns each
         const int64_t g = i / (kCols * rv), j = i - g * kCols * rv;
         const int64_t k = j / rv, rl = j % rv;
         const int64_t r = tl.a + rl, col = (int64_t)(tl.chunk0 + c) * G * kCols + g * kCols + k;

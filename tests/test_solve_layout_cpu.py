@@ -1,20 +1,20 @@
 """The triangular solve's tile schedule and its streamed FP32 layout, from the host
 analysis (no GPU).  Each chunk of a tile reaches shared memory by one bulk copy,
 which must start on a 16-byte boundary and move a multiple of 16 bytes, at most the
-48 KB stage: a copy that breaks these rules is an illegal instruction on the GPU,
+32 KB stage: a copy that breaks these rules is an illegal instruction on the GPU,
 so they are checked here for every chunk of every test mesh, together with the
 chunks lying back to back.  The schedule itself must equal a re-derivation from
 its definition: per supernode (nc columns, nr rows), forward tiles are row blocks
-of R rows (R = 256 for nc <= 48, 128 for nc <= 96, else 64) over the columns
+of R rows (R = 256 for nc <= 32, 128 for nc <= 64, else 64) over the columns
 [0, cend) their rows need (a row block inside the triangular L11^-1 block only up
-to its last row), in chunks of 256/R column groups of 48 columns; backward tiles
+to its last row), in chunks of 256/R column groups of 32 columns; backward tiles
 are column blocks of BC columns (the narrowest of 8/16/32/64 covering nc, 64 at
-most) over the rows from their first column down, in chunks of min(12288/BC, 512)
+most) over the rows from their first column down, in chunks of min(8192/BC, 256)
 rows; a level whose blocks number fewer than 608 has them cut into runs of at
 most max(1, chunks of the level / 608) consecutive chunks (a tile each);
 forward tiles by ascending tree level, backward tiles by descending level,
 supernodes in level-list order.  Streamed copy per chunk: forward [group][column <
-kmax_g][row < rv] with kmax_g = clamp(L - 48 g, 0, 48) for a chunk of L columns
+kmax_g][row < rv] with kmax_g = clamp(L - 32 g, 0, 32) for a chunk of L columns
 (the groups filled in order), backward [column < bcv][row < rn]; each padded to
 16 bytes."""
 import numpy as np
@@ -64,28 +64,28 @@ def _derive(m):
         fb, bb = [], []
         for s in ll[lp[L]:lp[L + 1]]:
             nc, nr = int(sf[s + 1] - sf[s]), int(rp[s + 1] - rp[s])
-            R = 256 if nc <= 48 else (128 if nc <= 96 else 64)
+            R = 256 if nc <= 32 else (128 if nc <= 64 else 64)
             G = 256 // R
-            CW = 48 * G
+            CW = 32 * G
             for r0 in range(0, nr, R):
                 rv = min(R, nr - r0)
                 rmax = r0 + rv - 1
                 cend = min(nc, rmax + 1) if rmax < nc else nc
                 nch = (cend + CW - 1) // CW
                 lld = cend - (nch - 1) * CW          # columns of the block's last chunk
-                fb.append((s, KINDS_F[R], r0, nch, G * 48 * rv, lld * rv, lld))
+                fb.append((s, KINDS_F[R], r0, nch, G * 32 * rv, lld * rv, lld))
             BC = 64 if nc > 32 else (32 if nc > 16 else (16 if nc > 8 else 8))
-            BR = min(12288 // BC, 512)
+            BR = min(8192 // BC, 256)
             for c0 in range(0, nc, BC):
                 rows = nr - c0
                 nch = (rows + BR - 1) // BR
                 lld = rows - (nch - 1) * BR
                 bcv = min(BC, nc - c0)
                 bb.append((s, KINDS_B[BC], c0, nch, bcv * BR, bcv * lld, lld))
-        split(fb, kc_of(fb), lambda kind: 48 * {0: 1, 1: 2, 2: 4}[kind], fwd)
+        split(fb, kc_of(fb), lambda kind: 32 * {0: 1, 1: 2, 2: 4}[kind], fwd)
         lev_b = []
         bc_of = {3: 64, 4: 32, 5: 16, 6: 8}
-        split(bb, kc_of(bb), lambda kind: min(12288 // bc_of[kind], 512), lev_b)
+        split(bb, kc_of(bb), lambda kind: min(8192 // bc_of[kind], 256), lev_b)
         bwd.append(lev_b)
     tiles = fwd + [t for lev in reversed(bwd) for t in lev]
     out, off = [], 0
@@ -114,7 +114,7 @@ def test_solve_tiles_match_definition_and_copy_rules(native, case):
     assert np.all(nch >= 1)
     assert np.all(soff % 4 == 0)                          # 16-byte aligned starts (floats)
     for b in (cbytes, lbytes):
-        assert np.all(b % 16 == 0) and np.all(b > 0) and np.all(b <= 49152)
+        assert np.all(b % 16 == 0) and np.all(b > 0) and np.all(b <= 32768)
     # chunks back to back: every chunk but a tile's last has cbytes, the last lbytes
     ends = soff + (nch - 1) * (cbytes // 4) + lbytes // 4
     assert np.array_equal(soff[1:], ends[:-1])
