@@ -73,6 +73,12 @@ def backward(model: Model, xs, vs, gx, gv=None, act=None, mu=None):
             g_wc += -Vq * np.einsum("eqij,eqij->e", Gz, F - loc["R"])
         if "D" in loc:
             g_wv += -Vq * np.einsum("eqij,eqij->e", Gz, F - loc["D"])
+        if "P_nh" in loc:
+            # Neo-Hookean: dP/dw_corot = (F - F^-T)/2 (mu = w_corot/2), dP/dw_vol = log J F^-T
+            FinvT = np.swapaxes(np.linalg.inv(F), -1, -2)
+            logJ = np.log(np.linalg.det(F))
+            g_wc += -Vq * np.einsum("eqij,eqij->e", Gz, 0.5 * (F - FinvT))
+            g_wv += -Vq * np.einsum("eqij,eqij->e", Gz, logJ[..., None, None] * FinvT)
         if "f" in loc:
             Gzm = np.einsum("eqij,ej->eqi", Gz, model.fiber)
             g_wm += -Vq * np.einsum("eqi,eqi->e", Gzm, loc["f"] - loc["pm"])

@@ -12,6 +12,10 @@ V_q = dx^3/8 for hexahedra, dx^3/6 per tetrahedron of the tet6 rule): corotated 
 w = E nu/((1+nu)(1-2nu)) (= lambda), muscle w = E on fibre elements; penalty
 contact w = k per candidate node.  (Reading: the paper does not state the
 map from (E, nu) to w.)
+Neo-Hookean scenes (Sec. 8, `scene.neohookean`): the corotated and volume terms of
+E are replaced by the Neo-Hookean energy (oracle/neohookean.py) with mu = w_corot/2,
+lambda = w_vol; E is then not a PD energy, its Hessian is assembled from the
+Neo-Hookean tangent, and A keeps the PD matrix of the same weights.
 Penalty friction (Sec. 5.1) enters f_ext: reading, per candidate node j with
 z_j < 0 at the start of the step, f_n = k (-z_j), v_t = (v_x, v_y),
 f_t = -min(mu f_n, m_j |v_t| / h) v_t / |v_t| (zero when |v_t| = 0).
@@ -22,6 +26,7 @@ import numpy as np
 import scipy.sparse as sp
 
 from .mesh import VoxelMesh
+from . import neohookean as nh
 from . import projections as pj
 
 
@@ -61,16 +66,26 @@ class Model:
         self.free_nodes = np.flatnonzero(~self.dirichlet)
         self.free_dofs = (self.free_nodes[:, None] * 3 + np.arange(3)[None, :]).ravel()
         self.G = mesh.G_matrix()
+        self.neohookean = bool(getattr(s, "neohookean", False))
+        if self.neohookean:
+            self.nh_mu = 0.5 * wc
+            self.nh_lam = wv
 
     # ---------------------------------------------------------------- local
     def local(self, x, act=None):
         """Deformation gradients and projections at every Gauss point."""
         F = self.mesh.deformation_gradients(x)                 # (e, 8, 3, 3)
         out = {"F": F}
-        if np.any(self.w_corot):
-            out["R"] = pj.project_corotated(F)
-        if np.any(self.w_vol):
-            out["D"] = pj.project_volume(F)
+        if self.neohookean:
+            mu = np.broadcast_to(self.nh_mu[:, None], F.shape[:2])
+            lam = np.broadcast_to(self.nh_lam[:, None], F.shape[:2])
+            out["P_nh"] = nh.first_piola(F, mu, lam)
+            out["psi_nh"] = nh.energy_density(F, mu, lam)
+        else:
+            if np.any(self.w_corot):
+                out["R"] = pj.project_corotated(F)
+            if np.any(self.w_vol):
+                out["D"] = pj.project_volume(F)
         if np.any(self.w_musc):
             f = np.einsum("eqij,ej->eqi", F, self.fiber)
             a = np.zeros(self.mesh.e) if act is None else np.asarray(act, dtype=np.float64)
@@ -84,6 +99,8 @@ class Model:
         F = loc["F"]
         Vq = self.mesh.Vq
         E = 0.0
+        if "psi_nh" in loc:
+            E += Vq * np.sum(loc["psi_nh"])
         if "R" in loc:
             E += 0.5 * Vq * np.sum(self.w_corot[:, None] * np.sum((F - loc["R"]) ** 2, axis=(2, 3)))
         if "D" in loc:
@@ -101,6 +118,8 @@ class Model:
         F = loc["F"]
         Vq = self.mesh.Vq
         S = np.zeros_like(F)                                   # stress-like (e,q,3,3)
+        if "P_nh" in loc:
+            S += Vq * loc["P_nh"]
         if "R" in loc:
             S += (self.w_corot * Vq)[:, None, None, None] * (F - loc["R"])
         if "D" in loc:
@@ -124,7 +143,14 @@ class Model:
         G = self.G
         Vq = mesh.Vq
         GtG = np.einsum("qki,qkj->qij", G, G)                  # (8, 24, 24)
-        blocks = np.einsum("e,qij->eij", (self.w_corot + self.w_vol) * Vq, GtG)
+        if self.neohookean and linearised:
+            # Hess E of the Neo-Hookean terms: sum_q V_q G_q^T T_q G_q
+            F = mesh.deformation_gradients(x)
+            mu = np.broadcast_to(self.nh_mu[:, None], F.shape[:2])
+            lam = np.broadcast_to(self.nh_lam[:, None], F.shape[:2])
+            blocks = Vq * np.einsum("qki,eqkl,qlj->eij", G, nh.tangent(F, mu, lam), G)
+        else:
+            blocks = np.einsum("e,qij->eij", (self.w_corot + self.w_vol) * Vq, GtG)
         if np.any(self.w_musc):
             Q = G.shape[0]
             Gm = np.zeros((mesh.e, Q, 3, 24))
@@ -136,12 +162,13 @@ class Model:
             return blocks
         loc = self.local(x, act)
         F = loc["F"]
-        J = np.zeros((mesh.e, G.shape[0], 9, 9))
-        if np.any(self.w_corot):
-            J += self.w_corot[:, None, None, None] * pj.jacobian_corotated(F)
-        if np.any(self.w_vol):
-            J += self.w_vol[:, None, None, None] * pj.jacobian_volume(F)
-        blocks = blocks - Vq * np.einsum("qki,eqkl,qlj->eij", G, J, G)
+        if not self.neohookean:
+            J = np.zeros((mesh.e, G.shape[0], 9, 9))
+            if np.any(self.w_corot):
+                J += self.w_corot[:, None, None, None] * pj.jacobian_corotated(F)
+            if np.any(self.w_vol):
+                J += self.w_vol[:, None, None, None] * pj.jacobian_volume(F)
+            blocks = blocks - Vq * np.einsum("qki,eqkl,qlj->eij", G, J, G)
         if np.any(self.w_musc):
             f = loc["f"]
             nrm = np.linalg.norm(f, axis=2)

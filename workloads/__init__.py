@@ -31,5 +31,6 @@ from .scenes import (  # noqa: F401
     napkin,
     tet_beam,
     tet_ball,
+    neohookean_beam,
     SCENES,
 )

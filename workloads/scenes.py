@@ -45,6 +45,10 @@ class Scene:
     # element rule on the kept cells: "hex8" (trilinear hexahedra) or "tet6" (six
     # linear tetrahedra per cell); per-element arrays stay per cell either way
     element_rule: str = "hex8"
+    # Neo-Hookean material (Sec. 8): the corotated and volume energies are replaced by
+    # the compressible Neo-Hookean energy with mu = w_corot / 2 and lambda = w_vol;
+    # A stays the PD matrix of those weights
+    neohookean: bool = False
 
     @property
     def n_nodes(self) -> int:
@@ -137,6 +141,24 @@ def _beam(name, index, nx, ny, nz, dx, E, nu, rho, h, T, *, volume, e_sigma=0.0,
                  contact=np.zeros(n, dtype=np.uint8), gravity=np.array([0.0, 0.0, -9.81]),
                  h=h, T=T, x0=x0, v0=v0, f_ext=f_ext, act=None, k_contact=0.0, mu=0.0,
                  loss_w=loss_w, tol_fwd=tol, tol_bwd=tol)
+
+
+def neohookean_beam(nx=5, ny=3, nz=4, *, T=6, index=9, E=1e5, twist=0.0) -> Scene:
+    """Small cantilever of the Neo-Hookean material (Sec. 8): the small beam with
+    the corotated and volume weights read as (2 mu, lambda), seeded stiffness
+    variation and tractions; `twist` adds an initial angular velocity [rad/s] about
+    the beam axis (large rotations within a few steps)."""
+    sc = _beam(f"neohookean_beam_{nx}x{ny}x{nz}", index, nx, ny, nz, 0.01, E, 0.45, 1e3, 0.01, T,
+               volume=True, e_sigma=0.2, v0_sigma=0.01, traction=True, tol=1e-10)
+    if twist != 0.0:
+        c = sc.x0.mean(axis=0)
+        r = sc.x0 - c
+        w = np.array([twist, 0.0, 0.0])
+        v = np.cross(w[None, :], r)
+        v[sc.dirichlet.astype(bool)] = 0.0
+        sc.v0 = sc.v0 + v
+    sc.neohookean = True
+    return sc
 
 
 def cantilever_c1(T: int = 50) -> Scene:
