@@ -54,6 +54,10 @@ WORKLOADS = {
     "c5": dict(name="c5_beam_64x64x128_mixed_ckpt25", K=SEG, tol=1e-7, want=("fext", "v0"), iters_per_step=75.0),
     "c2": dict(name="c2_beam_32x32x64_mixed", K=0, tol=1e-8, want=("w_corot", "w_vol", "v0"),
                iters_per_step=150.0),
+    # the same beam of the Neo-Hookean material (Sec. 8): L-BFGS with the PD matrix as
+    # initial Hessian forward, the splitting iteration on the Neo-Hookean Hessian backward
+    "c2nh": dict(name="c2_beam_32x32x64_neohookean_mixed", K=0, tol=1e-8, want=("w_corot", "w_vol", "v0"),
+                 iters_per_step=150.0, nh=True),
 }
 
 
@@ -260,11 +264,14 @@ def whole_job_rate(elapsed_s, sim_steps_per_rank, world, device):
 
 def _scene(wl, T):
     from workloads import beam_c2, beam_c5
-    return beam_c5(T=T) if wl == "c5" else beam_c2(T=T)
+    sc = beam_c5(T=T) if wl == "c5" else beam_c2(T=T)
+    if wl == "c2nh":
+        sc.neohookean = True
+    return sc
 
 
 def _profile_key(wl):
-    return "c5_beam_64x64x128" if wl == "c5" else "c2_beam_32x32x64"
+    return {"c5": "c5_beam_64x64x128", "c2": "c2_beam_32x32x64", "c2nh": "c2nh_beam_32x32x64"}[wl]
 
 
 def _traffic(wl):
@@ -293,7 +300,8 @@ def accuracy_leg(mesh, sc, wc, wv, d, Tr, K, roll_m, g_m, want):
     from paper_2101_05917_gb300 import _native as N
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    mesh.factorize(wc, wv, None, None, h=sc.h, gravity=tuple(sc.gravity), precision=N.PD_PREC_FP64)
+    mesh.factorize(wc, wv, None, None, h=sc.h, gravity=tuple(sc.gravity), precision=N.PD_PREC_FP64,
+                   neohookean=sc.neohookean)
     o = api.solver_opts(tol_fwd=1e-10, tol_bwd=1e-10, max_iter_fwd=5000, max_iter_bwd=5000, checkpoint_every=K)
     r = mesh.forward(d["x0"], d["v0"], Tr, f_ext=d["f"], opts=o)
     g = mesh.backward(r, Tr, d["lw"], f_ext=d["f"], opts=o, want=want)
@@ -392,7 +400,8 @@ def run_ours(args):
     d = {"x0": tt(sc.x0), "v0": tt(sc.v0), "f": tt(sc.f_ext), "lw": tt(sc.loss_w)}
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    mesh.factorize(wc, wv, None, None, h=sc.h, gravity=tuple(sc.gravity), precision=N.PD_PREC_MIXED)
+    mesh.factorize(wc, wv, None, None, h=sc.h, gravity=tuple(sc.gravity), precision=N.PD_PREC_MIXED,
+                   neohookean=sc.neohookean)
     torch.cuda.synchronize()
     t_factor = time.perf_counter() - t0
     stream = torch.cuda.current_stream()
@@ -473,7 +482,7 @@ def run_ours(args):
     T_e = seg * max(1, args.steps // 4) if K > 0 else T
     host = {k: torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64).pin_memory()
             for k, a in (("x0", sc.x0), ("v0", sc.v0), ("f", sc.f_ext), ("lw", sc.loss_w),
-                         ("wc", wc.cpu().numpy()))}
+                         ("wc", wc.cpu().numpy())) + ((("wv", wv.cpu().numpy()),) if wv is not None else ())}
     h2d = sum(t.numel() * 8 for t in host.values())
     float((roll.x[-1] * d["lw"]).sum().cpu())   # lazily loaded torch kernels, outside the timed region
     torch.cuda.synchronize()
@@ -482,7 +491,8 @@ def run_ours(args):
     e0.record(stream)
     hp = [time.perf_counter()]
     dd = {k: t.to(dev, non_blocking=True) for k, t in host.items()}
-    mesh.factorize(dd["wc"], None, None, None, h=sc.h, gravity=tuple(sc.gravity), precision=N.PD_PREC_MIXED)
+    mesh.factorize(dd["wc"], dd.get("wv"), None, None, h=sc.h, gravity=tuple(sc.gravity),
+                   precision=N.PD_PREC_MIXED, neohookean=sc.neohookean)
     hp.append(time.perf_counter())
     o = opts_for()
     re_ = mesh.forward(dd["x0"], dd["v0"], T_e, f_ext=dd["f"], opts=o)
@@ -632,7 +642,7 @@ def run_probe(args):
     mesh = api.PDMesh.from_scene(sc)
     wc, wv, wm, fib = api.scene_weights(sc, dev)
     mesh.factorize(wc, wv, wm, fib, h=sc.h, gravity=tuple(sc.gravity), k_contact=sc.k_contact,
-                   precision=N.PD_PREC_MIXED)
+                   precision=N.PD_PREC_MIXED, neohookean=sc.neohookean)
     x = tt(sc.x0)
     v = tt(np.random.default_rng(1).standard_normal(sc.x0.shape))
     if args.probe == "solve":

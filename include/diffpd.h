@@ -164,6 +164,12 @@ typedef struct {
   double gravity[3];            /* [m/s^2] */
   double k_contact;             /* ground penalty stiffness [N/m] on contact candidates */
   int32_t precision;            /* PD_PREC_FP64 or PD_PREC_MIXED */
+  int32_t neohookean;           /* nonzero: Neo-Hookean material (Sec. 8, hexahedra only): the
+                                   local steps evaluate psi = mu/2 (tr F^T F - 3) - mu log J +
+                                   lambda/2 (log J)^2 with mu = w_corot / 2 and lambda = w_vol
+                                   (both required) instead of the corotated and volume energies;
+                                   A is still assembled from w_corot and w_vol (the PD matrix
+                                   of the same material, the L-BFGS initial Hessian) */
 } pd_factor_opts;
 
 pd_status pd_factorize(pd_mesh m, const double* w_corot, const double* w_vol,

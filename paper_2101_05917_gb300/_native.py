@@ -60,7 +60,7 @@ class MeshInfo(ctypes.Structure):
 
 class FactorOpts(ctypes.Structure):
     _fields_ = [("h", ctypes.c_double), ("gravity", ctypes.c_double * 3), ("k_contact", ctypes.c_double),
-                ("precision", ctypes.c_int32)]
+                ("precision", ctypes.c_int32), ("neohookean", ctypes.c_int32)]
 
 
 class SolverOpts(ctypes.Structure):

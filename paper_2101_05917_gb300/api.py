@@ -166,12 +166,15 @@ class PDMesh:
 
     # ------------------------------------------------------------------
     def factorize(self, w_corot=None, w_vol=None, w_muscle=None, fiber=None, h=0.01,
-                  gravity=(0.0, 0.0, -9.81), k_contact=0.0, precision=N.PD_PREC_FP64, stream=None):
+                  gravity=(0.0, 0.0, -9.81), k_contact=0.0, precision=N.PD_PREC_FP64, stream=None,
+                  neohookean=False):
+        """neohookean=True: Neo-Hookean material with mu = w_corot / 2, lambda = w_vol."""
         o = N.FactorOpts()
         o.h = h
         o.gravity = (ctypes.c_double * 3)(*gravity)
         o.k_contact = k_contact
         o.precision = precision
+        o.neohookean = 1 if neohookean else 0
         self.h = h
         N.check(N.lib().pd_factorize(self.handle, _ptr(w_corot), _ptr(w_vol), _ptr(w_muscle), _ptr(fiber),
                                      ctypes.byref(o), _stream(stream)), "pd_factorize")

@@ -736,7 +736,7 @@ pd_status forward_step(Ctx& c, const double* act_t, const double* fext_int, doub
           stall = 0;
         } else if (++stall >= 3) {
           if (fp32_end < 0) fp32_end = std::max(1, sh.iters - 3 * c.o.check_every);
-          if (prec == PD_PREC_MIXED && m->h.rule == PD_ELEM_HEX8) {
+          if (prec == PD_PREC_MIXED && m->h.rule == PD_ELEM_HEX8 && !m->neohookean) {
             prec = kPrecMixedAcc;
             used_acc = true;
           } else {
@@ -1293,6 +1293,14 @@ pd_status pd_factorize(pd_mesh mesh, const double* w_corot, const double* w_vol,
     set_error("pd_factorize: unknown precision");
     return PD_ERR_INVALID_ARG;
   }
+  if (opts->neohookean && (!w_corot || !w_vol)) {
+    set_error("pd_factorize: the Neo-Hookean material needs w_corot (2 mu) and w_vol (lambda)");
+    return PD_ERR_INVALID_ARG;
+  }
+  if (opts->neohookean && mesh->impl.h.rule != PD_ELEM_HEX8) {
+    set_error("pd_factorize: the Neo-Hookean material is implemented for hexahedra");
+    return PD_ERR_INVALID_ARG;
+  }
   MeshImpl& I = mesh->impl;
   DeviceGuard g(I.device);
   cudaStream_t s = (cudaStream_t)stream;
@@ -1315,6 +1323,7 @@ pd_status pd_factorize(pd_mesh mesh, const double* w_corot, const double* w_vol,
   for (int i = 0; i < 3; ++i) I.grav[i] = opts->gravity[i];
   I.k_contact = opts->k_contact;
   I.precision = opts->precision;
+  I.neohookean = opts->neohookean != 0;
   const int64_t nnz = I.h.factor_nnz();
   if (!I.Q64) PD_CUDA_TRY(dalloc(&I, &I.Q64, (size_t)nnz));
   if (I.precision == PD_PREC_MIXED && !I.Q32) PD_CUDA_TRY(dalloc(&I, &I.Q32, (size_t)nnz));

@@ -132,6 +132,123 @@ __device__ __forceinline__ T shape_grad(int a, int q, int d, T inv_dx) {
 
 enum { MODE_FORCE = 0, MODE_HVP = 1, MODE_PGRAD = 2 };
 
+// det(I + H) - 1 without the cancellation of forming det(I + H): the trace, the
+// principal 2x2 minors and det H
+template <typename T>
+__device__ __forceinline__ T det_minus_one(const T (&H)[3][3]) {
+  const T tr = H[0][0] + H[1][1] + H[2][2];
+  const T m2 = H[0][0] * H[1][1] - H[0][1] * H[1][0] + H[0][0] * H[2][2] - H[0][2] * H[2][0] +
+               H[1][1] * H[2][2] - H[1][2] * H[2][1];
+  const T d3 = H[0][0] * (H[1][1] * H[2][2] - H[1][2] * H[2][1]) - H[0][1] * (H[1][0] * H[2][2] - H[1][2] * H[2][0]) +
+               H[0][2] * (H[1][0] * H[2][1] - H[1][1] * H[2][0]);
+  return tr + m2 + d3;
+}
+
+// x - log(1 + x): its Taylor series for small |x| (the direct form cancels), else
+// directly
+template <typename T>
+__device__ __forceinline__ T x_minus_log1p(T x) {
+  const T lim = sizeof(T) == 4 ? T(0.1) : T(0.01);
+  if (fabs(x) < lim) {
+    // x^2/2 - x^3/3 + ... - x^11/11, Horner in x
+    T s = T(0);
+#pragma unroll
+    for (int k = 11; k >= 2; --k) s = s * x + ((k & 1) ? T(1) : T(-1)) * (T(1) / T(k)) * T(-1);
+    return s * x * x;
+  }
+  return x - (sizeof(T) == 4 ? (T)log1pf((float)x) : (T)log1p((double)x));
+}
+
+// One Gauss point of the Neo-Hookean material (Sec. 8),
+//   psi = mu/2 (tr F^T F - 3) - mu log J + lambda/2 (log J)^2,
+//   P   = mu (F - F^-T) + lambda log J F^-T,
+//   dP  = mu dF + (mu - lambda log J) F^-T dF^T F^-T + lambda tr(F^-1 dF) F^-T,
+// with F = I + H, in forms that keep the accuracy relative to the strain:
+// F - F^-T = (H + H^T + H H^T) F^-T, log J = log1p(det(I + H) - 1) and
+// tr F^T F - 3 - 2 log J = |H|^2 + 2 (tr H - log J).  FORCE adds V P to S and
+// V psi to energy, HVP adds V dP(dF), PGRAD sets the adjoint products of
+// dP/dw_corot = (F - F^-T)/2 and dP/dw_vol = log J F^-T with dF = G z.
+template <typename T, int MODE>
+__device__ __forceinline__ void neohookean_point(const T (&H)[3][3], const T (&dF)[3][3], T mu, T lam, T V,
+                                                 T (&S)[3][3], T& energy, T& gwc, T& gwv) {
+  const T F[3][3] = {{T(1) + H[0][0], H[0][1], H[0][2]},
+                     {H[1][0], T(1) + H[1][1], H[1][2]},
+                     {H[2][0], H[2][1], T(1) + H[2][2]}};
+  const T j1 = det_minus_one<T>(H);
+  const T invJ = T(1) / (T(1) + j1);
+  const T logJ = sizeof(T) == 4 ? (T)log1pf((float)j1) : (T)log1p((double)j1);
+  // F^-T = cof(F) / J
+  T Fit[3][3];
+  Fit[0][0] = (F[1][1] * F[2][2] - F[1][2] * F[2][1]) * invJ;
+  Fit[0][1] = (F[1][2] * F[2][0] - F[1][0] * F[2][2]) * invJ;
+  Fit[0][2] = (F[1][0] * F[2][1] - F[1][1] * F[2][0]) * invJ;
+  Fit[1][0] = (F[0][2] * F[2][1] - F[0][1] * F[2][2]) * invJ;
+  Fit[1][1] = (F[0][0] * F[2][2] - F[0][2] * F[2][0]) * invJ;
+  Fit[1][2] = (F[0][1] * F[2][0] - F[0][0] * F[2][1]) * invJ;
+  Fit[2][0] = (F[0][1] * F[1][2] - F[0][2] * F[1][1]) * invJ;
+  Fit[2][1] = (F[0][2] * F[1][0] - F[0][0] * F[1][2]) * invJ;
+  Fit[2][2] = (F[0][0] * F[1][1] - F[0][1] * F[1][0]) * invJ;
+  if constexpr (MODE == MODE_HVP) {
+    // tr(F^-1 dF) = F^-T : dF;  F^-T dF^T F^-T
+    T tr = T(0);
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) tr += Fit[i][j] * dF[i][j];
+    T A[3][3];   // dF^T F^-T
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) A[i][j] = dF[0][i] * Fit[0][j] + dF[1][i] * Fit[1][j] + dF[2][i] * Fit[2][j];
+    const T c1 = mu - lam * logJ, c2 = lam * tr;
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) {
+        const T FA = Fit[i][0] * A[0][j] + Fit[i][1] * A[1][j] + Fit[i][2] * A[2][j];
+        S[i][j] += V * (mu * dF[i][j] + c1 * FA + c2 * Fit[i][j]);
+      }
+  } else {
+    // B = H + H^T + H H^T = F F^T - I;  F - F^-T = B F^-T
+    T B[3][3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) B[i][j] = H[i][j] + H[j][i] + H[i][0] * H[j][0] + H[i][1] * H[j][1] + H[i][2] * H[j][2];
+    T D[3][3];   // F - F^-T
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) D[i][j] = B[i][0] * Fit[0][j] + B[i][1] * Fit[1][j] + B[i][2] * Fit[2][j];
+    if (MODE == MODE_FORCE) {
+#pragma unroll
+      for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) S[i][j] += V * (mu * D[i][j] + lam * logJ * Fit[i][j]);
+      // tr H - log J = (tr H - j1) + (j1 - log1p(j1))
+      const T trH = H[0][0] + H[1][1] + H[2][2];
+      T hh = T(0);
+#pragma unroll
+      for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) hh += H[i][j] * H[i][j];
+      const T trh_logj = (trH - j1) + x_minus_log1p<T>(j1);
+      energy += V * (T(0.5) * mu * hh + mu * trh_logj + T(0.5) * lam * logJ * logJ);
+    } else {
+      T a = T(0), b = T(0);
+#pragma unroll
+      for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+          a += dF[i][j] * D[i][j];
+          b += dF[i][j] * Fit[i][j];
+        }
+      gwc = -V * T(0.5) * a;
+      gwv = -V * logJ * b;
+    }
+  }
+}
+
 struct ElemParams {
   const IterState* gate;
   int64_t ne;
@@ -153,10 +270,13 @@ struct ElemParams {
 // in FP32 on the FP64 strain, and the rotation and its derivative are refined to
 // FP64 without eigenvectors (polar_refine / polar_solve); every quantity that
 // enters the gradient or the Hessian product is then FP64-accurate.
-template <typename T, int MODE, int RULE = RULE_HEX8, bool ACC = false, bool REF = false>
+// NH (hexahedra): the Neo-Hookean material (Sec. 8) with mu = w_corot / 2 and
+// lambda = w_vol in place of the corotated and volume energies; no SVD.
+template <typename T, int MODE, int RULE = RULE_HEX8, bool ACC = false, bool REF = false, bool NH = false>
 __global__ void __launch_bounds__(kElemThreads, sizeof(T) == 8 ? 1 : (MODE == MODE_FORCE && !ACC ? 3 : 2))
 element_kernel(ElemParams p) {
   static_assert(!REF || (sizeof(T) == 8 && RULE == RULE_HEX8 && MODE != MODE_PGRAD), "refined: FP64 hexahedra");
+  static_assert(!NH || (RULE == RULE_HEX8 && !ACC && !REF), "Neo-Hookean: hexahedra, plain FP32 / FP64");
   if (p.gate && p.gate->converged) return;
   __shared__ double wsum[kElemThreads / 32];
   __shared__ unsigned arrived;
@@ -249,7 +369,10 @@ element_kernel(ElemParams p) {
 
   SVD3<T> sv;
   double Rr[3][3], Sr[3][3];   // REF: refined rotation and symmetric factor
-  if constexpr (REF) {
+  if constexpr (NH) {
+    neohookean_point<T, MODE>(H, dF, T(0.5) * wc, wv, Vq, S, energy, gwc, gwv);
+    if (valid && !(T(1) + det_minus_one<T>(H) > T(0))) atomicOr(p.flags, DEV_ERR_INVERTED);
+  } else if constexpr (REF) {
     double Ed[3][3];
     green_strain<double>(H, Ed);
     float H32[3][3], E32[3][3];
@@ -270,9 +393,11 @@ element_kernel(ElemParams p) {
     if (valid && !(sv.sig[2] > T(0))) atomicOr(p.flags, DEV_ERR_INVERTED);
   }
   T M[3][3];
-  if (MODE != MODE_FORCE && !REF) rotate_in<T>(sv.U, dF, sv.V, M);
+  if (MODE != MODE_FORCE && !REF && !NH) rotate_in<T>(sv.U, dF, sv.V, M);
 
-  if constexpr (REF) {
+  if constexpr (NH) {
+    // done above
+  } else if constexpr (REF) {
     if (wc != T(0)) {
       if (MODE == MODE_FORCE) {
         // F - R with F = I + H
@@ -319,7 +444,7 @@ element_kernel(ElemParams p) {
       gwc = -Vq * (M[0][0] * sv.sm1[0] + M[1][1] * sv.sm1[1] + M[2][2] * sv.sm1[2]);
     }
   }
-  if (!REF && __any_sync(0xffffffffu, wv != T(0))) {   // REF runs without the volume energy
+  if (!REF && !NH && __any_sync(0xffffffffu, wv != T(0))) {   // REF runs without the volume energy
     VolProj<T> vp;
     if (volume_project<T>(sv, vp, wv != T(0))) {
       if (MODE == MODE_FORCE) {
@@ -610,6 +735,14 @@ template <int MODE>
 void launch_elem(const MeshImpl* m, int precision, const ElemParams& p, cudaStream_t s) {
   const int nb = (int)((m->h.e * 8 + kElemThreads - 1) / kElemThreads);
   const bool tet = m->h.rule == PD_ELEM_TET6;
+  if (m->neohookean && !tet) {
+    // Neo-Hookean: FP32 for the mixed tiers, FP64 for the FP64 and refined ones
+    if (local_is_fp32(precision))
+      element_kernel<float, MODE, RULE_HEX8, false, false, true><<<nb, kElemThreads, 0, s>>>(p);
+    else
+      element_kernel<double, MODE, RULE_HEX8, false, false, true><<<nb, kElemThreads, 0, s>>>(p);
+    return;
+  }
   if (local_is_fp32(precision)) {
     if (tet) element_kernel<float, MODE, RULE_TET6><<<nb, kElemThreads, 0, s>>>(p);
     else if (precision == kPrecMixedAcc) element_kernel<float, MODE, RULE_HEX8, true><<<nb, kElemThreads, 0, s>>>(p);

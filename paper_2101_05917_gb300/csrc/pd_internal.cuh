@@ -214,6 +214,7 @@ struct MeshImpl {
   // material state
   bool factorized = false;
   int precision = PD_PREC_FP64;
+  bool neohookean = false;   // Neo-Hookean material (mu = wc/2, lambda = wv) in the local steps
   double h_step = 0, grav[3] = {0, 0, 0}, k_contact = 0;
   double *wc = nullptr, *wv = nullptr, *wm = nullptr, *fiber = nullptr;   // null = energy absent
   double *wc_buf = nullptr, *wv_buf = nullptr, *wm_buf = nullptr, *fiber_buf = nullptr;

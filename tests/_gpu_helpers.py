@@ -17,7 +17,7 @@ def make_mesh(sc, precision=N.PD_PREC_FP64, leaf_max=64):
     mesh = api.PDMesh.from_scene(sc, leaf_max=leaf_max, device=0)
     wc, wv, wm, fib = api.scene_weights(sc, DEV)
     mesh.factorize(wc, wv, wm, fib, h=sc.h, gravity=tuple(sc.gravity), k_contact=sc.k_contact,
-                   precision=precision)
+                   precision=precision, neohookean=getattr(sc, "neohookean", False))
     return mesh
 
 
