@@ -48,6 +48,10 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 # (12), F V (27 FMA), its Givens QR (3 x 30), the stress U diag(sigma - 1) V^T
 # (63), the corner forces (72 FMA) and the energy (6).
 LOCAL_FLOPS_PER_GP = 144 + 42 + 4 * 3 * 40 + 12 + 54 + 90 + 63 + 144 + 6
+# The same for the Neo-Hookean material (no SVD): F - I (144), det(I + H) - 1 (27),
+# 1/J and log J (2), F^-T = cof(F)/J (36), H + H^T + H H^T (63), (F F^T - I) F^-T
+# (54), the stress (36), the energy (48) and the corner forces (144).
+LOCAL_FLOPS_PER_GP_NH = 144 + 27 + 2 + 36 + 63 + 54 + 36 + 48 + 144
 WORKLOADS = {
     # tol 1e-7: over 50 steps the mixed path at this tolerance stays within 2.5e-8
     # (positions) and 7e-8 (gradients) of the FP64 path at tol 1e-10
@@ -475,7 +479,8 @@ def run_ours(args):
     achieved = bytes_solve / t_solve / 1e9
     traffic, traffic_src = _traffic(args.workload)
     gps = 8 * int(mesh.e)
-    local_tflops = LOCAL_FLOPS_PER_GP * gps / t_local / 1e12 if locals_timed else None
+    flops_gp = LOCAL_FLOPS_PER_GP_NH if sc.neohookean else LOCAL_FLOPS_PER_GP
+    local_tflops = flops_gp * gps / t_local / 1e12 if locals_timed else None
 
     # end to end through the public API with host buffers: H2D of the inputs,
     # factorisation (the weights are inputs), forward, backward, D2H of the gradients
@@ -544,9 +549,10 @@ def run_ours(args):
                          "timing": "CUDA events on the launching stream around every directly launched solve "
                                    "of a profiled %d-step rollout run after the timed region (the timed rollout "
                                    "runs without events)" % prof_T},
-            "local_step": {"bound": "alu", "kernel": "element_kernel (forward, FP32)",
+            "local_step": {"bound": "alu", "kernel": "element_kernel (forward, FP32%s)" % (
+                               ", Neo-Hookean" if sc.neohookean else ""),
                            "avg_us": 1e6 * t_local, "launches_timed": locals_timed,
-                           "flops_per_gauss_point": LOCAL_FLOPS_PER_GP, "gauss_points": gps,
+                           "flops_per_gauss_point": flops_gp, "gauss_points": gps,
                            "achieved": local_tflops, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
                            "frac": (local_tflops / FP32_PEAK_TFLOPS) if local_tflops else None},
             "step_latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
