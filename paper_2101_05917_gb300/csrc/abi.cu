@@ -1458,6 +1458,18 @@ pd_status pd_backward(pd_mesh mesh, const double* x_traj, const double* v_traj, 
   MeshImpl* m = &mesh->impl;
   DeviceGuard g(m->device);
   const auto t0 = std::chrono::steady_clock::now();
+  {
+    // the Hessian products' SVD cache (before any iteration graph is captured); the
+    // adjoint solves run without it when it does not fit in memory
+    int64_t slots, fields;
+    svd_cache_layout(m, &slots, &fields);
+    if (fields > m->svd_cache_fields) {
+      dfree(m, &m->svd_cache);
+      m->svd_cache_fields = 0;
+      if (dalloc(m, &m->svd_cache, (size_t)(slots * fields)) == cudaSuccess) m->svd_cache_fields = fields;
+      else cudaGetLastError();
+    }
+  }
   pd_status ws = ensure_workspace(m, o.lbfgs_m);
   if (ws != PD_OK) return ws;
   cudaStream_t s = (cudaStream_t)stream;

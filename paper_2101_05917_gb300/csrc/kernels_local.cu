@@ -263,7 +263,15 @@ struct ElemParams {
   double* energy;       // block partials (FORCE)
   double *g_wc, *g_wv, *g_wm, *g_act;   // PGRAD outputs
   int* flags;
+  // FP32 hexahedral Hessian products inside an adjoint solve (gate set): the point
+  // SVDs (and volume projections) at x_{t+1}, shared by the solve's products;
+  // kSvdFields (+ kVolFields with the volume energy) fields of n_gp floats each
+  float* svd_cache;
+  int64_t n_gp;
 };
+
+constexpr int kSvdFields = 24;   // U, V, sigma, sigma - 1
+constexpr int kVolFields = 11;   // lambda, s, gap, a, and whether the projection applies
 
 // ACC (FP32 hexahedra only): H and the Green strain in FP64, the rest in FP32.
 // REF (FP64 hexahedra with the corotated and muscle energies only): the SVD runs
@@ -290,24 +298,38 @@ element_kernel(ElemParams p) {
   const int64_t e = ((int64_t)blockIdx.x * kElemThreads + threadIdx.x) >> 3;
   const bool valid = e < p.ne;
   const T inv_dx = sizeof(T) == 4 ? T(p.inv_dx_f) : T(p.inv_dx);
+  // The Hessian products of one adjoint solve are all taken at x_{t+1}: the solve's
+  // first product writes every point's SVD (and volume projection) to the cache, the
+  // later ones read it instead of forming H and the SVD again (same values, so the
+  // same results).  Uniform over the grid: 0 none, 1 write, 2 read.
+  constexpr bool kCache = MODE == MODE_HVP && sizeof(T) == 4 && RULE == RULE_HEX8 && !ACC && !REF && !NH;
+  int cmode = 0;
+  if constexpr (kCache) {
+    if (p.svd_cache && p.gate && !p.wm) cmode = p.gate->svd_cached ? 2 : 1;
+  }
+  // every thread of the grid owns a slot (n_gp = the grid's threads), tail threads too
+  float* cache = (kCache && cmode != 0) ? p.svd_cache + ((int64_t)blockIdx.x * kElemThreads + threadIdx.x) : nullptr;
+  const int64_t cs = p.n_gp;   // field stride
   // volume weight of this lane's point (the tetrahedral rule leaves lanes 6, 7 idle)
   const T Vq = (RULE == RULE_TET6 && k >= 6) ? T(0) : (sizeof(T) == 4 ? T(p.Vq_f) : T(p.Vq));
 
   // ---- corner loads: relative displacement of corner k w.r.t. corner 0
   int node = valid ? p.elems[e * 8 + k] : 0;
-  double xk[3] = {0, 0, 0};
-  if (valid) {
-    xk[0] = p.x[3 * (int64_t)node + 0];
-    xk[1] = p.x[3 * (int64_t)node + 1];
-    xk[2] = p.x[3 * (int64_t)node + 2];
-  }
-  T dk[3];
-  double dkd[3];
+  T dk[3] = {T(0), T(0), T(0)};
+  double dkd[3] = {0, 0, 0};
+  if (cmode != 2) {
+    double xk[3] = {0, 0, 0};
+    if (valid) {
+      xk[0] = p.x[3 * (int64_t)node + 0];
+      xk[1] = p.x[3 * (int64_t)node + 1];
+      xk[2] = p.x[3 * (int64_t)node + 2];
+    }
 #pragma unroll
-  for (int i = 0; i < 3; ++i) {
-    const double x0 = __shfl_sync(0xffffffffu, xk[i], base);
-    dkd[i] = (xk[i] - x0) - (cbit(k, i) ? p.dx : 0.0);
-    dk[i] = (T)dkd[i];
+    for (int i = 0; i < 3; ++i) {
+      const double x0 = __shfl_sync(0xffffffffu, xk[i], base);
+      dkd[i] = (xk[i] - x0) - (cbit(k, i) ? p.dx : 0.0);
+      dk[i] = (T)dkd[i];
+    }
   }
   T vk[3] = {T(0), T(0), T(0)};
   if (MODE != MODE_FORCE && valid) {
@@ -335,7 +357,7 @@ element_kernel(ElemParams p) {
       }
     if (MODE != MODE_FORCE) hex_grad<T>(vk, k, inv_dx, dF);
   } else if constexpr (RULE == RULE_HEX8) {
-    hex_grad<T>(dk, k, inv_dx, H);
+    if (cmode != 2) hex_grad<T>(dk, k, inv_dx, H);
     if (MODE != MODE_FORCE) hex_grad<T>(vk, k, inv_dx, dF);
   } else {
 #pragma unroll
@@ -387,10 +409,37 @@ element_kernel(ElemParams p) {
     svd3_from_HE<float>(H32, E32, s32);
     const bool ok = polar_refine(s32.U, s32.V, H, Rr, Sr);
     if (valid && (!(s32.sig[2] > 0.0f) || !ok)) atomicOr(p.flags, DEV_ERR_INVERTED);
+  } else if (cmode == 2) {
+    if constexpr (kCache) {
+#pragma unroll
+      for (int i = 0; i < 3; ++i) {
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+          sv.U[i][j] = (T)__ldcs(cache + (3 * i + j) * cs);
+          sv.V[i][j] = (T)__ldcs(cache + (9 + 3 * i + j) * cs);
+        }
+        sv.sig[i] = (T)__ldcs(cache + (18 + i) * cs);
+        sv.sm1[i] = (T)__ldcs(cache + (21 + i) * cs);
+      }
+    }
   } else {
     if constexpr (RULE == RULE_HEX8 && ACC) svd3_from_HE<T>(H, Eacc, sv);
     else svd3_from_H<T>(H, sv);
     if (valid && !(sv.sig[2] > T(0))) atomicOr(p.flags, DEV_ERR_INVERTED);
+    if constexpr (kCache) {
+      if (cmode == 1) {
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+#pragma unroll
+          for (int j = 0; j < 3; ++j) {
+            cache[(3 * i + j) * cs] = (float)sv.U[i][j];
+            cache[(9 + 3 * i + j) * cs] = (float)sv.V[i][j];
+          }
+          cache[(18 + i) * cs] = (float)sv.sig[i];
+          cache[(21 + i) * cs] = (float)sv.sm1[i];
+        }
+      }
+    }
   }
   T M[3][3];
   if (MODE != MODE_FORCE && !REF && !NH) rotate_in<T>(sv.U, dF, sv.V, M);
@@ -446,7 +495,32 @@ element_kernel(ElemParams p) {
   }
   if (!REF && !NH && __any_sync(0xffffffffu, wv != T(0))) {   // REF runs without the volume energy
     VolProj<T> vp;
-    if (volume_project<T>(sv, vp, wv != T(0))) {
+    bool vok;
+    if (cmode == 2) {
+      float* vc = cache + kSvdFields * cs;
+      vp.lam = (T)__ldcs(vc);
+#pragma unroll
+      for (int i = 0; i < 3; ++i) {
+        vp.s[i] = (T)__ldcs(vc + (1 + i) * cs);
+        vp.gap[i] = (T)__ldcs(vc + (4 + i) * cs);
+        vp.a[i] = (T)__ldcs(vc + (7 + i) * cs);
+      }
+      vok = __ldcs(vc + 10 * cs) != 0.0f;
+    } else {
+      vok = volume_project<T>(sv, vp, wv != T(0));
+      if (cmode == 1) {
+        float* vc = cache + kSvdFields * cs;
+        vc[0] = (float)vp.lam;
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+          vc[(1 + i) * cs] = (float)vp.s[i];
+          vc[(4 + i) * cs] = (float)vp.gap[i];
+          vc[(7 + i) * cs] = (float)vp.a[i];
+        }
+        vc[10 * cs] = vok ? 1.0f : 0.0f;
+      }
+    }
+    if (vok) {
       if (MODE == MODE_FORCE) {
         add_UdVt<T>(S, sv.U, vp.gap, sv.V, wv * Vq);
         energy += T(0.5) * wv * Vq * (vp.gap[0] * vp.gap[0] + vp.gap[1] * vp.gap[1] + vp.gap[2] * vp.gap[2]);
@@ -789,10 +863,23 @@ cudaError_t launch_element_forces(const LocalArgs& a, void* elembuf, double* ene
   return cudaGetLastError();
 }
 
+void svd_cache_layout(const MeshImpl* m, int64_t* slots, int64_t* fields) {
+  const int64_t nb = (m->h.e * 8 + kElemThreads - 1) / kElemThreads;
+  *slots = nb * kElemThreads;
+  const bool applies = m->precision == PD_PREC_MIXED && m->h.rule == PD_ELEM_HEX8 && !m->neohookean && !m->wm;
+  *fields = applies ? kSvdFields + (m->wv ? kVolFields : 0) : 0;
+}
+
 cudaError_t launch_element_hvp(const LocalArgs& a, void* elembuf, int* flags, cudaStream_t s) {
   ElemParams p = make_params(a);
   p.out = elembuf;
   p.flags = flags;
+  int64_t slots, fields;
+  svd_cache_layout(a.m, &slots, &fields);
+  if (a.gate && a.m->svd_cache && fields > 0 && a.m->svd_cache_fields >= fields && a.precision == PD_PREC_MIXED) {
+    p.svd_cache = a.m->svd_cache;
+    p.n_gp = slots;
+  }
   launch_elem<MODE_HVP>(a.m, a.precision, p, s);
   return cudaGetLastError();
 }

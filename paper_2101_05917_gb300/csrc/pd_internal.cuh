@@ -215,6 +215,10 @@ struct MeshImpl {
   bool factorized = false;
   int precision = PD_PREC_FP64;
   bool neohookean = false;   // Neo-Hookean material (mu = wc/2, lambda = wv) in the local steps
+  // point SVDs (and volume projections) shared by the FP32 Hessian products of one
+  // adjoint solve (svd_cache_layout); allocated by pd_backward when it applies
+  float* svd_cache = nullptr;
+  int64_t svd_cache_fields = 0;
   double h_step = 0, grav[3] = {0, 0, 0}, k_contact = 0;
   double *wc = nullptr, *wv = nullptr, *wm = nullptr, *fiber = nullptr;   // null = energy absent
   double *wc_buf = nullptr, *wv_buf = nullptr, *wm_buf = nullptr, *fiber_buf = nullptr;
@@ -242,6 +246,10 @@ struct LocalArgs {
 cudaError_t launch_element_forces(const LocalArgs& a, void* elembuf, double* energy_partials,
                                   int* flags, cudaStream_t s);
 cudaError_t launch_element_hvp(const LocalArgs& a, void* elembuf, int* flags, cudaStream_t s);
+// floats per field of the Hessian-product SVD cache (the element kernel's grid
+// threads) and the fields the mesh needs; 0 fields when the cache does not apply
+// (not FP32 hexahedra, the Neo-Hookean or the muscle energy)
+void svd_cache_layout(const MeshImpl* m, int64_t* slots, int64_t* fields);
 cudaError_t launch_element_param_grads(const LocalArgs& a, double* g_wc, double* g_wv,
                                        double* g_wm, double* g_act, cudaStream_t s);
 int element_blocks(const MeshImpl* m);

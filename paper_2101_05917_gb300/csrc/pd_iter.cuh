@@ -29,6 +29,7 @@ struct IterState {
   int iters, evals, ls_tries, ls_total, ls_max, max_iter;
   int accepted, converged, hit_max, force_accept, fp64_checked;
   int pending;           // backward: a step (alpha, d, Hd) waits to be applied
+  int svd_cached;        // backward: the step's FP32 point SVDs are in the mesh's cache
   int status;            // DEV_ERR_* bits
 };
 

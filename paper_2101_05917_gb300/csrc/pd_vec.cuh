@@ -154,6 +154,7 @@ __global__ void state_reset_kernel(IterState* st, StateCfg cfg) {
   st->fp64_checked = 0;
   st->pending = 0;
   st->status = 0;
+  st->svd_cached = 0;
 }
 
 // ---------------------------------------------------------------- forward
@@ -833,6 +834,7 @@ __global__ void decide_bwd_kernel(IterState* st, const double* gather_partials, 
   const double dHd = block_reduce_strided(gather_partials, nbg, 4, 0);
   if (threadIdx.x != 0) return;
   if (st->converged) return;
+  st->svd_cached = 1;   // this iteration's Hessian product ran: its point SVDs are cached
   st->dHd = dHd;
   st->evals += 1;
   st->pending = 1;
