@@ -51,8 +51,8 @@ constexpr int kPreSlots = 4;          // W-row sources per position held in regi
 constexpr int kPart = kThreads * 3;   // partial-sum slots per tile (forward rows / backward columns x 3)
 // tiles a level is cut into at least, where its blocks have enough chunks: blocks
 // are split into runs of consecutive chunks until the level has this many tiles
-// (two per resident CTA of a 152-SM part; each split costs its tiles a partial-sum
-// round trip, so a level is not cut finer than that)
+// (more than the 456 resident CTAs of a 152-SM part; each split costs its tiles a
+// partial-sum round trip, so a level is not cut finer than that)
 constexpr int64_t kLevelTiles = 608;
 constexpr int kStageBytes = kChunkElems * 4;   // one shared-memory stage of the FP32 kernel
 constexpr int kStages = 2;                     // FP32 kernel: stages per CTA
