@@ -1389,8 +1389,12 @@ pd_status pd_forward(pd_mesh mesh, const double* x0, const double* v0, const dou
   if (v_traj) PD_CUDA_TRY(cudaMemcpyAsync(v_traj, v0, sizeof(double) * 3 * n, cudaMemcpyDeviceToDevice, s));
   int guess = 4;
   bool all_ok = true, any_nan = false;
+  m->acc_log.assign((size_t)T, 0);
+  m->guess_log.assign((size_t)T, 0);
   for (int t = 0; t < T; ++t) {
     const double* act_t = act ? act + (int64_t)t * m->h.e : nullptr;
+    m->acc_log[t] = c.acc_steps;
+    m->guess_log[t] = guess;
     if (f_ext && o.fext_per_step && t > 0)
       kept_to_internal_kernel<<<grid_for(n), 256, 0, s>>>(n, m->kept_of_internal, f_ext + (int64_t)t * 3 * n, w.fext);
     double* tx = nullptr;
@@ -1535,6 +1539,11 @@ pd_status pd_backward(pd_mesh mesh, const double* x_traj, const double* v_traj, 
       for (int t = ta; t < tb - 1; ++t) {
         StepInfo info;
         const double* act_t = act ? act + (int64_t)t * e : nullptr;
+        // the forward pass's driver state at this step (bit-identical recomputation)
+        if ((int64_t)m->acc_log.size() == T) {
+          c.acc_steps = m->acc_log[t];
+          guess_f = m->guess_log[t];
+        }
         if (f_ext && o.fext_per_step)
           kept_to_internal_kernel<<<grid_for(n), 256, 0, s>>>(n, m->kept_of_internal, f_ext + (int64_t)t * 3 * n, w.fext);
         const Range step_range("recompute step", t);

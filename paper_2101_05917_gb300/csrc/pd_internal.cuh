@@ -211,6 +211,11 @@ struct MeshImpl {
   // target rule (1 = ray, 0 = drop) -- read by the backward pass
   std::vector<std::vector<int32_t>> contact_log_node;
   std::vector<std::vector<uint8_t>> contact_log_rule;
+  // per time step of the last pd_forward: the strain-accurate tier's remaining steps
+  // and the length of the first chunk of iterations at the start of the step, so that
+  // a checkpointed recomputation polls at the same iterations and takes the same
+  // local-step precision at every step as the forward pass did
+  std::vector<int32_t> acc_log, guess_log;
   // material state
   bool factorized = false;
   int precision = PD_PREC_FP64;

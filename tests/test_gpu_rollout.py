@@ -103,10 +103,14 @@ def test_rollout_matches_oracle(name, prec):
     mesh.close()
 
 
-def test_checkpointed_backward_is_bit_identical():
+@pytest.mark.parametrize("prec", [N.PD_PREC_FP64, N.PD_PREC_MIXED])
+def test_checkpointed_backward_is_bit_identical(prec):
+    """Mixed precision at tol 1e-10 sits below the FP32 floor: the forward steps
+    switch to the strain-accurate tier, which stays on for later steps and across
+    the checkpoint at step 4; the recomputation replays the forward's tier state."""
     sc = small_beam(4, 3, 3, T=8)
     opts = api.solver_opts(tol_fwd=1e-10, tol_bwd=1e-10)
-    mesh = make_mesh(sc)
+    mesh = make_mesh(sc, precision=prec)
     f = T(sc.f_ext)
     roll = mesh.forward(T(sc.x0), T(sc.v0), sc.T, f_ext=f, opts=opts)
     g_full = mesh.backward(roll, sc.T, T(sc.loss_w), f_ext=f, opts=opts)
