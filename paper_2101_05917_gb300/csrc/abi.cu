@@ -898,7 +898,9 @@ pd_status backward_step(Ctx& c, const double* xnext, const double* xt_, const do
         info.converged = false;
         break;
       }
-      LocalArgs la{m, nullptr, xnext, w.z, act_t, p64};
+      // the step's first refined check stores each point's refined rotation and
+      // stretch at x_{t+1}, the later ones reuse them (the same values)
+      LocalArgs la{m, nullptr, xnext, w.z, act_t, p64, checks == 0 ? 1 : 2};
       PD_CUDA_TRY(launch_element_hvp(la, w.elembuf, w.flags, c.s));
       PD_CUDA_TRY(launch_gather_hvp(m, nullptr, w.elembuf, p64, xnext, w.z, nullptr, w.Hd, c.pg, c.s));
       residual_replace_kernel<<<c.vb, 256, 0, c.s>>>(c.vc, w.Hd, w.ax, w.av, inv_h, w.gs, w.q, held);
@@ -1473,6 +1475,9 @@ pd_status pd_backward(pd_mesh mesh, const double* x_traj, const double* v_traj, 
       if (dalloc(m, &m->svd_cache, (size_t)(slots * fields)) == cudaSuccess) m->svd_cache_fields = fields;
       else cudaGetLastError();
     }
+    int64_t rd;
+    if (!m->ref_cache && ref_cache_applies(m, &rd) && dalloc(m, &m->ref_cache, (size_t)rd) != cudaSuccess)
+      cudaGetLastError();
   }
   pd_status ws = ensure_workspace(m, o.lbfgs_m);
   if (ws != PD_OK) return ws;

@@ -268,7 +268,14 @@ struct ElemParams {
   // kSvdFields (+ kVolFields with the volume energy) fields of n_gp floats each
   float* svd_cache;
   int64_t n_gp;
+  // refined FP64 Hessian products of one adjoint step (REF): each point's refined
+  // rotation and stretch (18 doubles, field stride n_gp), written by the step's first
+  // residual check (ref_mode 1) and read by the later ones (ref_mode 2)
+  double* ref_cache;
+  int ref_mode;
 };
+
+constexpr int kRefFields = 18;   // R (9), S (9)
 
 constexpr int kSvdFields = 24;   // U, V, sigma, sigma - 1
 constexpr int kVolFields = 11;   // lambda, s, gap, a, and whether the projection applies
@@ -310,6 +317,10 @@ element_kernel(ElemParams p) {
   // every thread of the grid owns a slot (n_gp = the grid's threads), tail threads too
   float* cache = (kCache && cmode != 0) ? p.svd_cache + ((int64_t)blockIdx.x * kElemThreads + threadIdx.x) : nullptr;
   const int64_t cs = p.n_gp;   // field stride
+  constexpr bool kRefCache = REF && MODE == MODE_HVP;
+  const int rmode = (kRefCache && p.ref_cache) ? p.ref_mode : 0;
+  double* rcache = rmode ? p.ref_cache + ((int64_t)blockIdx.x * kElemThreads + threadIdx.x) : nullptr;
+  const bool skip_x = cmode == 2 || rmode == 2;   // the cached point data replace x and H
   // volume weight of this lane's point (the tetrahedral rule leaves lanes 6, 7 idle)
   const T Vq = (RULE == RULE_TET6 && k >= 6) ? T(0) : (sizeof(T) == 4 ? T(p.Vq_f) : T(p.Vq));
 
@@ -317,7 +328,7 @@ element_kernel(ElemParams p) {
   int node = valid ? p.elems[e * 8 + k] : 0;
   T dk[3] = {T(0), T(0), T(0)};
   double dkd[3] = {0, 0, 0};
-  if (cmode != 2) {
+  if (!skip_x) {
     double xk[3] = {0, 0, 0};
     if (valid) {
       xk[0] = p.x[3 * (int64_t)node + 0];
@@ -357,7 +368,7 @@ element_kernel(ElemParams p) {
       }
     if (MODE != MODE_FORCE) hex_grad<T>(vk, k, inv_dx, dF);
   } else if constexpr (RULE == RULE_HEX8) {
-    if (cmode != 2) hex_grad<T>(dk, k, inv_dx, H);
+    if (!skip_x) hex_grad<T>(dk, k, inv_dx, H);
     if (MODE != MODE_FORCE) hex_grad<T>(vk, k, inv_dx, dF);
   } else {
 #pragma unroll
@@ -394,6 +405,14 @@ element_kernel(ElemParams p) {
   if constexpr (NH) {
     neohookean_point<T, MODE>(H, dF, T(0.5) * wc, wv, Vq, S, energy, gwc, gwv);
     if (valid && !(T(1) + det_minus_one<T>(H) > T(0))) atomicOr(p.flags, DEV_ERR_INVERTED);
+  } else if (REF && rmode == 2) {
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) {
+        Rr[i][j] = __ldcs(rcache + (3 * i + j) * cs);
+        Sr[i][j] = __ldcs(rcache + (9 + 3 * i + j) * cs);
+      }
   } else if constexpr (REF) {
     double Ed[3][3];
     green_strain<double>(H, Ed);
@@ -409,6 +428,15 @@ element_kernel(ElemParams p) {
     svd3_from_HE<float>(H32, E32, s32);
     const bool ok = polar_refine(s32.U, s32.V, H, Rr, Sr);
     if (valid && (!(s32.sig[2] > 0.0f) || !ok)) atomicOr(p.flags, DEV_ERR_INVERTED);
+    if (rmode == 1) {
+#pragma unroll
+      for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+          rcache[(3 * i + j) * cs] = Rr[i][j];
+          rcache[(9 + 3 * i + j) * cs] = Sr[i][j];
+        }
+    }
   } else if (cmode == 2) {
     if constexpr (kCache) {
 #pragma unroll
@@ -863,6 +891,12 @@ cudaError_t launch_element_forces(const LocalArgs& a, void* elembuf, double* ene
   return cudaGetLastError();
 }
 
+bool ref_cache_applies(const MeshImpl* m, int64_t* doubles) {
+  const int64_t nb = (m->h.e * 8 + kElemThreads - 1) / kElemThreads;
+  *doubles = nb * kElemThreads * kRefFields;
+  return m->precision == PD_PREC_MIXED && m->h.rule == PD_ELEM_HEX8 && !m->neohookean && !m->wv && !m->wm;
+}
+
 void svd_cache_layout(const MeshImpl* m, int64_t* slots, int64_t* fields) {
   const int64_t nb = (m->h.e * 8 + kElemThreads - 1) / kElemThreads;
   *slots = nb * kElemThreads;
@@ -878,6 +912,12 @@ cudaError_t launch_element_hvp(const LocalArgs& a, void* elembuf, int* flags, cu
   svd_cache_layout(a.m, &slots, &fields);
   if (a.gate && a.m->svd_cache && fields > 0 && a.m->svd_cache_fields >= fields && a.precision == PD_PREC_MIXED) {
     p.svd_cache = a.m->svd_cache;
+    p.n_gp = slots;
+  }
+  int64_t rd;
+  if (a.ref_cache && a.m->ref_cache && ref_cache_applies(a.m, &rd) && a.precision == kPrecRefined) {
+    p.ref_cache = a.m->ref_cache;
+    p.ref_mode = a.ref_cache;
     p.n_gp = slots;
   }
   launch_elem<MODE_HVP>(a.m, a.precision, p, s);

@@ -224,6 +224,9 @@ struct MeshImpl {
   // adjoint solve (svd_cache_layout); allocated by pd_backward when it applies
   float* svd_cache = nullptr;
   int64_t svd_cache_fields = 0;
+  // the refined FP64 rotation and stretch of every point (18 doubles), shared by the
+  // refined FP64 residual checks of one adjoint step (ref_cache_applies)
+  double* ref_cache = nullptr;
   double h_step = 0, grav[3] = {0, 0, 0}, k_contact = 0;
   double *wc = nullptr, *wv = nullptr, *wm = nullptr, *fiber = nullptr;   // null = energy absent
   double *wc_buf = nullptr, *wv_buf = nullptr, *wm_buf = nullptr, *fiber_buf = nullptr;
@@ -246,6 +249,7 @@ struct LocalArgs {
   const double* v;       // (n,3) direction for HVP / adjoint for param grads
   const double* act;     // (e) contraction or null
   int precision;         // PD_PREC_FP64 / PD_PREC_MIXED (float local step)
+  int ref_cache = 0;     // refined FP64 Hessian products: 1 write m->ref_cache, 2 read it
 };
 // forces into ws.elembuf; energy block partials into partials[0..nblk)
 cudaError_t launch_element_forces(const LocalArgs& a, void* elembuf, double* energy_partials,
@@ -255,6 +259,9 @@ cudaError_t launch_element_hvp(const LocalArgs& a, void* elembuf, int* flags, cu
 // threads) and the fields the mesh needs; 0 fields when the cache does not apply
 // (not FP32 hexahedra, the Neo-Hookean or the muscle energy)
 void svd_cache_layout(const MeshImpl* m, int64_t* slots, int64_t* fields);
+// whether the refined FP64 Hessian products of the mesh can share m->ref_cache
+// (mixed-precision hexahedra of the corotated energy alone), and its doubles
+bool ref_cache_applies(const MeshImpl* m, int64_t* doubles);
 cudaError_t launch_element_param_grads(const LocalArgs& a, double* g_wc, double* g_wv,
                                        double* g_wm, double* g_act, cudaStream_t s);
 int element_blocks(const MeshImpl* m);
