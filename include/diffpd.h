@@ -158,7 +158,8 @@ pd_status pd_mesh_export(pd_mesh m, int32_t what, int64_t* host_out, int64_t cap
  * (required when w_muscle is given).  The numeric supernodal Cholesky runs on
  * the device in FP64; with PD_PREC_MIXED an FP32 copy of the solve panels is kept
  * for the triangular solves.  Copies of the weights are kept for the local
- * steps.  Returns PD_ERR_NOT_SPD on a non-positive pivot. */
+ * steps.  Returns PD_ERR_NOT_SPD on a non-positive pivot; PD_ERR_INVALID_ARG for
+ * the Neo-Hookean option without both w_corot and w_vol or on a tetrahedral mesh. */
 typedef struct {
   double h;                     /* time step [s] */
   double gravity[3];            /* [m/s^2] */
