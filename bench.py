@@ -55,13 +55,13 @@ LOCAL_FLOPS_PER_GP_NH = 144 + 27 + 2 + 36 + 63 + 54 + 36 + 48 + 144
 WORKLOADS = {
     # tol 1e-7: over 50 steps the mixed path at this tolerance stays within 2.5e-8
     # (positions) and 7e-8 (gradients) of the FP64 path at tol 1e-10
-    "c5": dict(name="c5_beam_64x64x128_mixed_ckpt25", K=SEG, tol=1e-7, want=("fext", "v0"), iters_per_step=75.0),
+    "c5": dict(name="c5_beam_64x64x128_mixed_ckpt25", K=SEG, tol=1e-7, want=("fext", "v0"), iters_per_step=48.1),
     "c2": dict(name="c2_beam_32x32x64_mixed", K=0, tol=1e-8, want=("w_corot", "w_vol", "v0"),
-               iters_per_step=150.0),
+               iters_per_step=182.0),
     # the same beam of the Neo-Hookean material (Sec. 8): L-BFGS with the PD matrix as
     # initial Hessian forward, the splitting iteration on the Neo-Hookean Hessian backward
     "c2nh": dict(name="c2_beam_32x32x64_neohookean_mixed", K=0, tol=1e-8, want=("w_corot", "w_vol", "v0"),
-                 iters_per_step=150.0, nh=True),
+                 iters_per_step=234.0, nh=True),
 }
 
 
