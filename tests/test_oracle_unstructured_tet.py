@@ -1,0 +1,139 @@
+"""Pins for the oracle's unstructured tetrahedral meshes (oracle/tetmesh.py,
+oracle/tetstructure.py; Secs. 5.1 and 7 use tetrahedral meshes with their own node
+sets): partition of unity of the shape functions, the affine patch test, volumes
+that tile the box and the lumped mass, rest and rigid-motion invariants, the
+gradient and Hessian against central differences, the PD + L-BFGS fixed point
+against Newton's, the adjoint against differences of a rollout loss, and the graph
+nested dissection (a permutation whose separators disconnect their two sides, and a
+supernodal structure that holds the exact Cholesky fill of L_A)."""
+import numpy as np
+import pytest
+
+from oracle import adjoint, newton, pd_cpu
+from oracle.tetmesh import TetModel
+from oracle.tetstructure import analyse, free_adjacency
+from workloads import unstructured_tet_beam
+
+
+@pytest.fixture(scope="module")
+def beam():
+    return unstructured_tet_beam(6, 3, 3, T=2)
+
+
+def _rot(rng):
+    Q, _ = np.linalg.qr(rng.standard_normal((3, 3)))
+    if np.linalg.det(Q) < 0:
+        Q[:, 0] *= -1
+    return Q
+
+
+def test_shape_functions_volumes_and_mass(beam):
+    m = TetModel(beam)
+    g = m.mesh.gradN[:, 0]
+    assert np.abs(g.sum(axis=1)).max() <= 1e-9 * np.abs(g).max()          # partition of unity
+    rng = np.random.default_rng(1)
+    A = np.eye(3) + 0.1 * rng.standard_normal((3, 3))
+    b = rng.standard_normal(3)
+    F = m.mesh.deformation_gradients(beam.X @ A.T + b)
+    assert np.abs(F - A[None, None]).max() <= 1e-10                         # affine patch test
+    box = 6 * 3 * 3 * 0.01 ** 3
+    assert abs(m.mesh.Vq.sum() - box) <= 1e-12 * box                        # the tetrahedra tile the box
+    assert abs(m.m.sum() - beam.density * box) <= 1e-12 * beam.density * box
+
+
+def test_rest_and_rigid_motions_are_stress_free(beam):
+    m = TetModel(beam)
+    assert abs(m.energy(beam.X)) <= 1e-20
+    assert np.abs(m.grad_E(beam.X)).max() <= 1e-12
+    rng = np.random.default_rng(2)
+    x = beam.X @ _rot(rng).T + rng.standard_normal(3)
+    assert abs(m.energy(x)) <= 1e-18
+    assert np.abs(m.grad_E(x)).max() <= 1e-9
+
+
+def test_gradient_and_hessian_match_differences(beam):
+    m = TetModel(beam)
+    rng = np.random.default_rng(3)
+    x = beam.X + 0.1 * 0.01 * rng.standard_normal(beam.X.shape)
+    g = m.grad_E(x)
+    d = rng.standard_normal(x.shape)
+    eps = 1e-7
+    fd = (m.energy(x + eps * d) - m.energy(x - eps * d)) / (2 * eps)
+    assert abs(fd - np.sum(g * d)) <= 1e-6 * abs(fd)
+    H = m.hessian(x)
+    Hd = (H @ d.ravel()).reshape(x.shape) - (m.m / m.h ** 2)[:, None] * d
+    fdg = (m.grad_E(x + eps * d) - m.grad_E(x - eps * d)) / (2 * eps)
+    assert np.abs(fdg - Hd).max() <= 1e-5 * np.abs(Hd).max()
+
+
+def test_pd_lbfgs_reaches_the_newton_fixed_point(beam):
+    m = TetModel(beam)
+    xn, _, _ = newton.newton_step(m, beam.x0, beam.v0, beam.f_ext)
+    xp, _, _ = pd_cpu.pd_lbfgs_step(m, pd_cpu.ScalarA(m), beam.x0, beam.v0, beam.f_ext, None, None, 1e-12, 5, 5000)
+    assert np.linalg.norm(xp - xn) <= 1e-9 * np.linalg.norm(xn - beam.x0)
+
+
+def test_adjoint_matches_central_differences(beam):
+    m = TetModel(beam)
+    xs, vs, _ = newton.rollout(m, beam.x0, beam.v0, beam.f_ext, T=beam.T)
+    _, gx = adjoint.final_position_loss(m, xs, beam.loss_w)
+    g = adjoint.backward(m, xs, vs, gx)
+    rng = np.random.default_rng(4)
+    d = rng.standard_normal(beam.x0.shape)
+    d[m.dirichlet] = 0.0
+
+    def loss(v0=None, f=None, E=None):
+        mm = TetModel(beam, youngs=E)
+        out, _, _ = newton.rollout(mm, beam.x0, beam.v0 if v0 is None else v0,
+                                   beam.f_ext if f is None else f, T=beam.T)
+        return float(np.sum(beam.loss_w * out[-1]))
+    eps = 1e-6
+    fd_v = (loss(v0=beam.v0 + eps * d) - loss(v0=beam.v0 - eps * d)) / (2 * eps)
+    assert abs(fd_v - np.sum(g["g_v0"] * d)) <= 2e-6 * abs(fd_v)
+    fd_f = (loss(f=beam.f_ext + eps * d) - loss(f=beam.f_ext - eps * d)) / (2 * eps)
+    assert abs(fd_f - np.sum(g["g_fext"] * d)) <= 2e-6 * abs(fd_f)
+    gE, _ = adjoint.material_gradients(m, g)
+    dE = rng.standard_normal(m.mesh.e) * beam.youngs
+    fd_E = (loss(E=beam.youngs + eps * dE) - loss(E=beam.youngs - eps * dE)) / (2 * eps)
+    assert abs(fd_E - np.sum(gE * dE)) <= 2e-6 * abs(fd_E)
+
+
+@pytest.mark.parametrize("leaf", [8, 16, 64])
+def test_graph_nested_dissection(leaf):
+    sc = unstructured_tet_beam(8, 4, 4, T=1)
+    st = analyse(sc.X, sc.tets, sc.dirichlet, leaf_max=leaf)
+    perm, first = st["perm"], st["snode_first"]
+    free, adj = free_adjacency(sc.tets, sc.dirichlet)
+    assert np.array_equal(np.sort(perm), np.arange(free.size))              # a permutation of the free nodes
+    inv = np.empty_like(perm)
+    inv[perm] = np.arange(perm.size)
+    # every supernode's nodes are adjacent (in the permuted numbering) only to nodes
+    # of its own subtree or of its ancestors: the elimination tree is a tree
+    ns = first.size - 1
+    owner = np.repeat(np.arange(ns), np.diff(first))
+    parent = st["parent"]
+
+    def ancestors(s):
+        out = set()
+        while s >= 0:
+            out.add(int(s))
+            s = int(parent[s])
+        return out
+    anc = [ancestors(s) for s in range(ns)]
+    for k in range(perm.size):
+        for j in st["adj"][k]:
+            a, b = int(owner[k]), int(owner[j])
+            assert a in anc[b] or b in anc[a], (a, b)
+    # the exact Cholesky factor of L_A (x block of A on the free DoFs, permuted) has
+    # its nonzeros inside the supernodal row structure
+    m = TetModel(sc)
+    A = m.A_matrix().toarray()[np.ix_(m.free_dofs[0::3], m.free_dofs[0::3])]
+    Ap = A[np.ix_(perm, perm)]
+    L = np.linalg.cholesky(Ap)
+    rows, rp = st["rows"], st["row_ptr"]
+    allowed = np.zeros_like(L, dtype=bool)
+    for s in range(ns):
+        r = rows[rp[s]:rp[s + 1]]
+        for c in range(first[s], first[s + 1]):
+            allowed[r[r >= c], c] = True
+    assert np.abs(L[~allowed]).max(initial=0.0) <= 1e-12 * np.abs(L).max()
