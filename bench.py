@@ -52,6 +52,9 @@ LOCAL_FLOPS_PER_GP = 144 + 42 + 4 * 3 * 40 + 12 + 54 + 90 + 63 + 144 + 6
 # 1/J and log J (2), F^-T = cof(F)/J (36), H + H^T + H H^T (63), (F F^T - I) F^-T
 # (54), the stress (36), the energy (48) and the corner forces (144).
 LOCAL_FLOPS_PER_GP_NH = 144 + 27 + 2 + 36 + 63 + 54 + 36 + 48 + 144
+# A linear tetrahedron's one point: F - I and the vertex forces from 4 vertices (36
+# FMA each) instead of 8 corners, the rest as for a hexahedron's Gauss point.
+LOCAL_FLOPS_PER_TET = LOCAL_FLOPS_PER_GP - 72 - 72
 WORKLOADS = {
     # tol 1e-7: over 50 steps the mixed path at this tolerance stays within 2.5e-8
     # (positions) and 7e-8 (gradients) of the FP64 path at tol 1e-10
@@ -62,6 +65,10 @@ WORKLOADS = {
     # initial Hessian forward, the splitting iteration on the Neo-Hookean Hessian backward
     "c2nh": dict(name="c2_beam_32x32x64_neohookean_mixed", K=0, tol=1e-8, want=("w_corot", "w_vol", "v0"),
                  iters_per_step=234.0, nh=True),
+    # an unstructured tetrahedral beam (jittered 49x25x25 lattice, Delaunay; the
+    # material and tolerance of the C2 beam); no CPU baseline line
+    "tetu": dict(name="unstructured_tet_beam_48x24x24_mixed", K=0, tol=1e-8, want=("w_corot", "w_vol", "v0"),
+                 iters_per_step=None, tet=True),
 }
 
 
@@ -267,7 +274,11 @@ def whole_job_rate(elapsed_s, sim_steps_per_rank, world, device):
 
 
 def _scene(wl, T):
-    from workloads import beam_c2, beam_c5
+    from workloads import beam_c2, beam_c5, unstructured_tet_beam
+    if wl == "tetu":
+        sc = unstructured_tet_beam(48, 24, 24, T=T, index=21, E=1e6)
+        sc.neohookean = False
+        return sc
     sc = beam_c5(T=T) if wl == "c5" else beam_c2(T=T)
     if wl == "c2nh":
         sc.neohookean = True
@@ -275,7 +286,8 @@ def _scene(wl, T):
 
 
 def _profile_key(wl):
-    return {"c5": "c5_beam_64x64x128", "c2": "c2_beam_32x32x64", "c2nh": "c2nh_beam_32x32x64"}[wl]
+    return {"c5": "c5_beam_64x64x128", "c2": "c2_beam_32x32x64", "c2nh": "c2nh_beam_32x32x64",
+            "tetu": "tetu_beam_48x24x24"}[wl]
 
 
 def _traffic(wl):
@@ -397,7 +409,7 @@ def run_ours(args):
     T = seg * args.steps if K > 0 else args.T
     sc = _scene(args.workload, T)
     t0 = time.perf_counter()
-    mesh = api.PDMesh.from_scene(sc, device=local)
+    mesh = (api.PDMesh.from_tet_scene if wl.get("tet") else api.PDMesh.from_scene)(sc, device=local)
     t_mesh = time.perf_counter() - t0
     wc, wv, _, _ = api.scene_weights(sc, dev)
     tt = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device=dev)
@@ -478,8 +490,9 @@ def run_ours(args):
     peak, peak_kind = peaks()
     achieved = bytes_solve / t_solve / 1e9
     traffic, traffic_src = _traffic(args.workload)
-    gps = 8 * int(mesh.e)
-    flops_gp = LOCAL_FLOPS_PER_GP_NH if sc.neohookean else LOCAL_FLOPS_PER_GP
+    gps = int(mesh.e) if wl.get("tet") else 8 * int(mesh.e)
+    flops_gp = LOCAL_FLOPS_PER_TET if wl.get("tet") else (LOCAL_FLOPS_PER_GP_NH if sc.neohookean else
+                                                           LOCAL_FLOPS_PER_GP)
     local_tflops = flops_gp * gps / t_local / 1e12 if locals_timed else None
 
     # end to end through the public API with host buffers: H2D of the inputs
@@ -519,7 +532,7 @@ def run_ours(args):
     if rank == 0 and not args.no_fp64:
         fp64 = fp64_line(dev)
     cpu = None
-    if rank == 0 and not args.no_cpu_baseline:
+    if rank == 0 and not args.no_cpu_baseline and not wl.get("tet"):
         cpu = oracle_sample(args.workload, fwd_it + bwd_it)
 
     if rank == 0:
@@ -528,7 +541,8 @@ def run_ours(args):
             "warmup": args.warmup, "ms_per_step": 1e3 * elapsed / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "mixed-f32-f64",
             "data": "synthetic",
-            "config": {"workload": wl["name"], "cells": int(mesh.e), "nodes": int(mesh.n),
+            "config": {"workload": wl["name"], "element_rule": "tetu" if wl.get("tet") else "hex8",
+                       "cells": int(mesh.e), "nodes": int(mesh.n),
                        "dofs": 3 * int(mesh.n), "T": T, "sim_steps_per_bench_step": seg,
                        "checkpoint_every": K, "ms_per_sim_step": 1e3 * elapsed / sim_steps,
                        "tol_fwd": tol, "tol_bwd": tol, "lbfgs_m": 5,
@@ -549,7 +563,9 @@ def run_ours(args):
                                    "of a profiled %d-step rollout run after the timed region (the timed rollout "
                                    "runs without events)" % prof_T},
             "local_step": {"bound": "alu", "kernel": "element_kernel (forward, FP32%s)" % (
-                               ", Neo-Hookean" if sc.neohookean else ""),
+                               ", Neo-Hookean" if sc.neohookean else
+                               ", unstructured tetrahedra: one point per 8-lane element record" if wl.get("tet")
+                               else ""),
                            "avg_us": 1e6 * t_local, "launches_timed": locals_timed,
                            "flops_per_gauss_point": flops_gp, "gauss_points": gps,
                            "achieved": local_tflops, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",

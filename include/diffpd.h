@@ -2,7 +2,7 @@
  * diffpd.h -- C ABI of a GB300-native differentiable Projective Dynamics solver.
  *
  * The library simulates voxel meshes (hexahedra, or six tetrahedra per cell)
- * with implicit Euler solved by
+ * and unstructured tetrahedral meshes with implicit Euler solved by
  * Projective Dynamics (Sec. 3, Alg. 1 of "DiffPD: Differentiable Projective
  * Dynamics", arXiv 2101.05917) and back-propagates through the rollout with the
  * adjoint splitting iteration  A z_{k+1} = Delta A z_k + dL/dx  (Sec. 4, Eqn 23,
@@ -15,9 +15,11 @@
  *     frees caller memory and never keeps a caller pointer past the call.
  *   - Per-node arrays are node-major (n, 3) FP64 in kept-node order: the nodes
  *     touched by at least one kept cell, in increasing grid id, where grid node
- *     (i, j, k) has id (i*(ny+1)+j)*(nz+1)+k and i runs along x.
+ *     (i, j, k) has id (i*(ny+1)+j)*(nz+1)+k and i runs along x.  On an
+ *     unstructured tetrahedral mesh (pd_create_tet_mesh) the kept nodes are the
+ *     caller's nodes in the caller's order.
  *   - Per-element arrays follow kept-cell order (increasing cell id
- *     (ci*ny+cj)*nz+ck).
+ *     (ci*ny+cj)*nz+ck), or the caller's tetrahedron order.
  *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
  *     Calls are stream-ordered; entry points that return statistics synchronise
  *     the stream before returning.
@@ -74,17 +76,19 @@ enum {
 
 typedef struct pd_mesh_s* pd_mesh;
 
-/* Element rules on the kept cells of the voxel grid. */
+/* Element rules: the first two on the kept cells of the voxel grid. */
 enum {
   PD_ELEM_HEX8 = 0,  /* trilinear hexahedron, 2x2x2 Gauss points of weight dx^3/8 each;
                         lumped mass rho dx^3/8 per cell corner */
-  PD_ELEM_TET6 = 1   /* six linear tetrahedra per cell, one for each order of the axes
+  PD_ELEM_TET6 = 1,  /* six linear tetrahedra per cell, one for each order of the axes
                         along the path from corner (0,0,0) to corner (1,1,1) (conforming
                         between cells), one point of weight dx^3/6 each; lumped mass
                         rho V/4 per tetrahedron vertex.  Stands in for the tetrahedral
                         meshes of Secs. 5.1 and 7; per-element inputs (weights, fibres,
                         actuation, their gradients) stay per cell and are shared by its
                         six tetrahedra */
+  PD_ELEM_TETU = 2   /* unstructured linear tetrahedra (pd_create_tet_mesh): one point of
+                        weight V per tetrahedron, lumped mass rho V/4 per vertex */
 };
 
 /* Voxel mesh description.  All pointers are host memory, read during the call. */
@@ -116,6 +120,39 @@ typedef struct {
  * and the supernodal structure of A on the host (C++), and uploads them to
  * `device`.  Ownership of *out passes to the caller (pd_mesh_destroy). */
 pd_status pd_create_mesh(const pd_mesh_desc* desc, pd_mesh* out);
+
+/* Unstructured tetrahedral mesh (the tetrahedral meshes of Secs. 5.1 and 7, with
+ * their own node sets).  All pointers are host memory, read during the call. */
+typedef struct {
+  int64_t n_nodes, n_tets;      /* every node must be a vertex of a tetrahedron;
+                                   n_tets < 2^25 (32-bit assembly codes) */
+  const double* X;              /* (n_nodes, 3) rest positions [m] */
+  const int32_t* tets;          /* (n_tets, 4) vertex indices, either orientation;
+                                   four distinct nodes of non-zero volume */
+  double density;               /* [kg/m^3]; lumped mass rho V/4 per vertex */
+  const uint8_t* dirichlet;     /* per node: fixed at its rest position, NULL = none */
+  const uint8_t* contact;       /* per node: ground-penalty candidate, NULL = none */
+  int32_t leaf_max;             /* nested-dissection leaf size, 0 = 64 */
+  int32_t device;               /* CUDA device ordinal, -1 = host analysis only */
+} pd_tet_mesh_desc;
+
+/* Builds an unstructured tetrahedral mesh (element rule PD_ELEM_TETU): per
+ * tetrahedron the gradients of its barycentric coordinates (rows of the inverse
+ * of its edge matrix) and its volume, the node incidence, a nested-dissection
+ * ordering of the free nodes by coordinate bisection with vertex separators of
+ * the mesh graph (a set of more than leaf_max free nodes is sorted by its
+ * coordinate of largest extent -- ties x, y, z -- then by node index, and halved;
+ * the separator is the first half's nodes adjacent to the second half; the order
+ * is first half without the separator, second half, separator), and the
+ * supernodal structure of A as pd_create_mesh builds it for voxel meshes.  The
+ * mesh then serves every entry point that takes a pd_mesh, with per-element
+ * arrays per tetrahedron, except the muscle energy and the Neo-Hookean material
+ * (pd_factorize rejects them on this rule).  PD_EXPORT_INC entries are
+ * e*8 + vertex (vertex < 4): element records keep the stride of eight.
+ * Errors: PD_ERR_INVALID_ARG for a vertex out of range or repeated, a degenerate
+ * tetrahedron, a node in no tetrahedron or no free node; PD_ERR_OOM / PD_ERR_CUDA
+ * as pd_create_mesh.  Ownership of *out passes to the caller (pd_mesh_destroy). */
+pd_status pd_create_tet_mesh(const pd_tet_mesh_desc* desc, pd_mesh* out);
 void pd_mesh_destroy(pd_mesh m);
 pd_status pd_mesh_query(pd_mesh m, pd_mesh_info* info);
 

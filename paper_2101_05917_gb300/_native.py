@@ -33,6 +33,7 @@ PD_PREC_MIXED_STRAIN = 2
 PD_PREC_FP64_REFINED = 3
 PD_ELEM_HEX8 = 0
 PD_ELEM_TET6 = 1
+PD_ELEM_TETU = 2   # unstructured tetrahedra: pd_create_tet_mesh only
 ELEMENT_RULES = {"hex8": PD_ELEM_HEX8, "tet6": PD_ELEM_TET6}
 
 EXPORT = {"inc_ptr": 0, "inc": 1, "perm": 2, "snode_first": 3, "row_ptr": 4, "rows": 5, "parent": 6,
@@ -48,6 +49,13 @@ class MeshDesc(ctypes.Structure):
                 ("dx", ctypes.c_double), ("origin", ctypes.c_double * 3), ("density", ctypes.c_double),
                 ("cell_mask", c_u8_p), ("dirichlet", c_u8_p), ("contact", c_u8_p),
                 ("leaf_max", ctypes.c_int32), ("device", ctypes.c_int32), ("element_rule", ctypes.c_int32)]
+
+
+class TetMeshDesc(ctypes.Structure):
+    _fields_ = [("n_nodes", ctypes.c_int64), ("n_tets", ctypes.c_int64), ("X", c_double_p),
+                ("tets", ctypes.POINTER(ctypes.c_int32)), ("density", ctypes.c_double),
+                ("dirichlet", c_u8_p), ("contact", c_u8_p), ("leaf_max", ctypes.c_int32),
+                ("device", ctypes.c_int32)]
 
 
 class MeshInfo(ctypes.Structure):
@@ -109,7 +117,7 @@ class Result(ctypes.Structure):
                 ("slot", ctypes.c_int32), ("mesh_cached", ctypes.c_int32), ("factor_cached", ctypes.c_int32)]
 
 
-SYMBOLS = ["pd_create_mesh", "pd_mesh_destroy", "pd_mesh_query", "pd_mesh_export", "pd_factorize",
+SYMBOLS = ["pd_create_mesh", "pd_create_tet_mesh", "pd_mesh_destroy", "pd_mesh_query", "pd_mesh_export", "pd_factorize",
            "pd_forward", "pd_backward", "pd_plan_checkpoints", "pd_local_step", "pd_hessian_vector", "pd_solve_A",
            "pd_local_step_noalloc", "pd_contact_prepare", "pd_contact_set", "pd_solve_A_contact", "pd_contact_step_set", "pd_serve_create", "pd_serve_submit", "pd_serve_poll", "pd_serve_release", "pd_serve_drain",
            "pd_serve_destroy", "pd_last_error"]
@@ -129,6 +137,8 @@ def lib() -> ctypes.CDLL:
     st = ctypes.c_int32
     L.pd_create_mesh.argtypes = [ctypes.POINTER(MeshDesc), ctypes.POINTER(vp)]
     L.pd_create_mesh.restype = st
+    L.pd_create_tet_mesh.argtypes = [ctypes.POINTER(TetMeshDesc), ctypes.POINTER(vp)]
+    L.pd_create_tet_mesh.restype = st
     L.pd_mesh_destroy.argtypes = [vp]
     L.pd_mesh_destroy.restype = None
     L.pd_mesh_query.argtypes = [vp, ctypes.POINTER(MeshInfo)]

@@ -91,7 +91,8 @@ def _with_fext_layout(opts, f_ext, T, n):
 
 class PDMesh:
     """A voxel mesh (hexahedra, or six tetrahedra per cell with element_rule
-    "tet6") resident on one GPU (pd_create_mesh ... pd_mesh_destroy)."""
+    "tet6") or an unstructured tetrahedral mesh (from_tet_mesh) resident on one GPU
+    (pd_create_mesh / pd_create_tet_mesh ... pd_mesh_destroy)."""
 
     def __init__(self, nx, ny, nz, dx, density, origin=(0.0, 0.0, 0.0), cell_mask=None, dirichlet=None,
                  contact=None, leaf_max=64, device: Optional[int] = 0, element_rule: str = "hex8"):
@@ -132,6 +133,43 @@ class PDMesh:
         self.e = self.info["n_elems"]
         self.dx = dx
         self.h = None
+
+    @classmethod
+    def from_tet_mesh(cls, X, tets, density, dirichlet=None, contact=None, leaf_max=64,
+                      device: Optional[int] = 0):
+        """An unstructured tetrahedral mesh (pd_create_tet_mesh): X (n, 3) rest
+        positions, tets (e, 4) vertex indices; nodes and tetrahedra keep the
+        caller's order."""
+        L = N.lib()
+        self = cls.__new__(cls)
+        X = np.ascontiguousarray(X, dtype=np.float64).reshape(-1, 3)
+        tets = np.ascontiguousarray(tets, dtype=np.int32).reshape(-1, 4)
+        n = X.shape[0]
+        dir_arr, dir_p = _u8(dirichlet, n, "dirichlet")
+        con_arr, con_p = _u8(contact, n, "contact")
+        desc = N.TetMeshDesc()
+        desc.n_nodes, desc.n_tets = n, tets.shape[0]
+        desc.X = X.ctypes.data_as(N.c_double_p)
+        desc.tets = tets.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
+        desc.density = density
+        desc.dirichlet, desc.contact = dir_p, con_p
+        desc.leaf_max = leaf_max
+        desc.device = -1 if device is None else int(device)
+        self._keep = [X, tets, dir_arr, con_arr]
+        self.device = device
+        self.handle = ctypes.c_void_p()
+        N.check(L.pd_create_tet_mesh(ctypes.byref(desc), ctypes.byref(self.handle)), "pd_create_tet_mesh")
+        self.info = self.query()
+        self.n = self.info["n_nodes"]
+        self.e = self.info["n_elems"]
+        self.dx = None
+        self.h = None
+        return self
+
+    @classmethod
+    def from_tet_scene(cls, sc, leaf_max=64, device=0):
+        return cls.from_tet_mesh(sc.X, sc.tets, sc.density, sc.dirichlet,
+                                 getattr(sc, "contact", None) if sc.k_contact > 0 else None, leaf_max, device)
 
     @classmethod
     def from_scene(cls, sc, leaf_max=64, device=0):

@@ -1011,7 +1011,14 @@ extern "C" {
 
 const char* pd_last_error(void) { return g_last_error.c_str(); }
 
-pd_status pd_create_mesh(const pd_mesh_desc* desc, pd_mesh* out) {
+}  // extern "C"
+
+namespace {
+
+// Builds the host analysis with `analyse_fn`, then (device >= 0) uploads the mesh
+// and its solve structures: the common part of pd_create_mesh and pd_create_tet_mesh.
+template <typename Desc, typename AnalyseFn>
+pd_status create_mesh_common(const Desc* desc, pd_mesh* out, AnalyseFn analyse_fn) {
   if (!desc || !out) {
     set_error("pd_create_mesh: null argument");
     return PD_ERR_INVALID_ARG;
@@ -1025,7 +1032,7 @@ pd_status pd_create_mesh(const pd_mesh_desc* desc, pd_mesh* out) {
   MeshImpl& I = m->impl;
   std::string err;
   try {
-    err = analyse(*desc, I.h);
+    err = analyse_fn(*desc, I.h);
   } catch (const std::bad_alloc&) {
     err = "pd_create_mesh: host allocation failed";
   }
@@ -1077,6 +1084,12 @@ pd_status pd_create_mesh(const pd_mesh_desc* desc, pd_mesh* out) {
   UP(la_cptr, la_cptr);
   UP(la_diag_node, la_diag_node);
   UP(la_contrib, la_contrib);
+  if (h.rule == PD_ELEM_TETU) {
+    UP(tet_grad, tet_grad);
+    UP(tet_grad_f, tet_grad);
+    UP(tet_vol, tet_vol);
+    UP(tet_vol_f, tet_vol);
+  }
 #undef UP
   build_solve_schedule(h, I.sched);
   {
@@ -1150,6 +1163,18 @@ pd_status pd_create_mesh(const pd_mesh_desc* desc, pd_mesh* out) {
   }
   *out = m;
   return PD_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+pd_status pd_create_mesh(const pd_mesh_desc* desc, pd_mesh* out) {
+  return create_mesh_common(desc, out, [](const pd_mesh_desc& d, HostMesh& h) { return analyse(d, h); });
+}
+
+pd_status pd_create_tet_mesh(const pd_tet_mesh_desc* desc, pd_mesh* out) {
+  return create_mesh_common(desc, out, [](const pd_tet_mesh_desc& d, HostMesh& h) { return analyse_tet(d, h); });
 }
 
 void pd_mesh_destroy(pd_mesh m) {
@@ -1301,6 +1326,10 @@ pd_status pd_factorize(pd_mesh mesh, const double* w_corot, const double* w_vol,
   }
   if (opts->neohookean && mesh->impl.h.rule != PD_ELEM_HEX8) {
     set_error("pd_factorize: the Neo-Hookean material is implemented for hexahedra");
+    return PD_ERR_INVALID_ARG;
+  }
+  if (w_muscle && mesh->impl.h.rule == PD_ELEM_TETU) {
+    set_error("pd_factorize: the muscle energy is implemented for voxel meshes");
     return PD_ERR_INVALID_ARG;
   }
   MeshImpl& I = mesh->impl;

@@ -41,6 +41,9 @@ struct AsmParams {
   double Kref[64];
   double gN[8][8][3];   // dN_a/dX at Gauss point q: gN[q][a][d]
   double Vq;
+  // unstructured tetrahedra: per-element barycentric gradients (12, vertex-major) and
+  // volumes in place of the voxel rule's reference matrix Kref
+  const double *tet_grad, *tet_vol;
   double* front;
 };
 
@@ -52,7 +55,14 @@ __global__ void assemble_la_kernel(AsmParams p) {
     const int32_t code = p.contrib[c];
     const int32_t e = code >> 6, a = (code >> 3) & 7, b = code & 7;
     const double w = (p.wc ? p.wc[e] : 0.0) + (p.wv ? p.wv[e] : 0.0);
-    v += w * p.Kref[a * 8 + b];
+    if (p.tet_grad) {
+      // V_e w grad N_a . grad N_b (one point per tetrahedron; a, b < 4)
+      const double* ga = p.tet_grad + 12 * (int64_t)e + 3 * a;
+      const double* gb = p.tet_grad + 12 * (int64_t)e + 3 * b;
+      v += w * p.tet_vol[e] * (ga[0] * gb[0] + ga[1] * gb[1] + ga[2] * gb[2]);
+    } else {
+      v += w * p.Kref[a * 8 + b];
+    }
     if (p.wm && p.wm[e] != 0.0) {
       const double m0 = p.fiber[3 * e], m1 = p.fiber[3 * e + 1], m2 = p.fiber[3 * e + 2];
       double s = 0.0;
@@ -444,6 +454,10 @@ pd_status factorize_device(MeshImpl* m, cudaStream_t st) {
           for (int d = 0; d < 3; ++d) s += ap.gN[q][a][d] * ap.gN[q][b][d];
         ap.Kref[a * 8 + b] = ap.Vq * s;
       }
+  }
+  if (h.rule == PD_ELEM_TETU) {
+    ap.tet_grad = m->tet_grad;
+    ap.tet_vol = m->tet_vol;
   }
   ap.front = front;
   if (ap.nnz > 0) {

@@ -54,7 +54,10 @@ __device__ __forceinline__ T gradN_tet(int a, int q, int d, T inv_dx) {
   return T(g) * inv_dx;
 }
 
-enum { RULE_HEX8 = 0, RULE_TET6 = 1 };
+// RULE_TETU: unstructured linear tetrahedra, one per element record (vertices in
+// lanes 0..3, lanes 4..7 repeat vertex 0), with per-element barycentric gradients
+// and volume; the one point sits on lane 0, the other lanes carry zero weight.
+enum { RULE_HEX8 = 0, RULE_TET6 = 1, RULE_TETU = 2 };
 
 // Hexahedron: the shape gradients factor over the three axes, so the sums over
 // the 8 corners (F at a Gauss point) and over the 8 Gauss points (corner forces)
@@ -273,7 +276,25 @@ struct ElemParams {
   // residual check (ref_mode 1) and read by the later ones (ref_mode 2)
   double* ref_cache;
   int ref_mode;
+  // unstructured tetrahedra: node rest positions (internal order) and per element
+  // the barycentric gradients (12, vertex-major) and the volume
+  const double* Xrest;
+  const double *tgrad, *tvol;
+  const float *tgrad_f, *tvol_f;
 };
+
+// quadrature weight of lane k's point
+template <typename T, int RULE>
+__device__ __forceinline__ T point_weight(const ElemParams& p, int64_t e, int k, bool valid) {
+  if constexpr (RULE == RULE_TETU) {
+    if (!valid || k != 0) return T(0);
+    if constexpr (sizeof(T) == 4) return p.tvol_f[e];
+    else return p.tvol[e];
+  } else {
+    if (RULE == RULE_TET6 && k >= 6) return T(0);   // the tetrahedral rule leaves lanes 6, 7 idle
+    return sizeof(T) == 4 ? T(p.Vq_f) : T(p.Vq);
+  }
+}
 
 constexpr int kRefFields = 18;   // R (9), S (9)
 
@@ -321,8 +342,8 @@ element_kernel(ElemParams p) {
   const int rmode = (kRefCache && p.ref_cache) ? p.ref_mode : 0;
   double* rcache = rmode ? p.ref_cache + ((int64_t)blockIdx.x * kElemThreads + threadIdx.x) : nullptr;
   const bool skip_x = cmode == 2 || rmode == 2;   // the cached point data replace x and H
-  // volume weight of this lane's point (the tetrahedral rule leaves lanes 6, 7 idle)
-  const T Vq = (RULE == RULE_TET6 && k >= 6) ? T(0) : (sizeof(T) == 4 ? T(p.Vq_f) : T(p.Vq));
+  // volume weight of this lane's point
+  const T Vq = point_weight<T, RULE>(p, e, k, valid);
 
   // ---- corner loads: relative displacement of corner k w.r.t. corner 0
   int node = valid ? p.elems[e * 8 + k] : 0;
@@ -335,11 +356,38 @@ element_kernel(ElemParams p) {
       xk[1] = p.x[3 * (int64_t)node + 1];
       xk[2] = p.x[3 * (int64_t)node + 2];
     }
+    // rest offset of corner k from corner 0: the cell's edge vector, or from the
+    // node rest positions (unstructured tetrahedra)
+    double rk[3] = {0, 0, 0};
+    if constexpr (RULE == RULE_TETU) {
+      double Xk[3] = {0, 0, 0};
+      if (valid) {
+        Xk[0] = p.Xrest[3 * (int64_t)node + 0];
+        Xk[1] = p.Xrest[3 * (int64_t)node + 1];
+        Xk[2] = p.Xrest[3 * (int64_t)node + 2];
+      }
+#pragma unroll
+      for (int i = 0; i < 3; ++i) rk[i] = Xk[i] - __shfl_sync(0xffffffffu, Xk[i], base);
+    } else {
+#pragma unroll
+      for (int i = 0; i < 3; ++i) rk[i] = cbit(k, i) ? p.dx : 0.0;
+    }
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
       const double x0 = __shfl_sync(0xffffffffu, xk[i], base);
-      dkd[i] = (xk[i] - x0) - (cbit(k, i) ? p.dx : 0.0);
+      dkd[i] = (xk[i] - x0) - rk[i];
       dk[i] = (T)dkd[i];
+    }
+  }
+  // unstructured tetrahedra: lane k < 4 holds vertex k's barycentric gradient
+  T gk[3] = {T(0), T(0), T(0)};
+  if constexpr (RULE == RULE_TETU) {
+    if (valid && k < 4) {
+#pragma unroll
+      for (int j = 0; j < 3; ++j) {
+        if constexpr (sizeof(T) == 4) gk[j] = p.tgrad_f[12 * e + 3 * k + j];
+        else gk[j] = p.tgrad[12 * e + 3 * k + j];
+      }
     }
   }
   T vk[3] = {T(0), T(0), T(0)};
@@ -370,6 +418,25 @@ element_kernel(ElemParams p) {
   } else if constexpr (RULE == RULE_HEX8) {
     if (!skip_x) hex_grad<T>(dk, k, inv_dx, H);
     if (MODE != MODE_FORCE) hex_grad<T>(vk, k, inv_dx, dF);
+  } else if constexpr (RULE == RULE_TETU) {
+    // every lane forms the tetrahedron's F - I (and dF) from the four vertices
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+      T da[3], va[3], ga[3];
+#pragma unroll
+      for (int i = 0; i < 3; ++i) {
+        da[i] = __shfl_sync(0xffffffffu, dk[i], base + a);
+        if (MODE != MODE_FORCE) va[i] = __shfl_sync(0xffffffffu, vk[i], base + a);
+        ga[i] = __shfl_sync(0xffffffffu, gk[i], base + a);
+      }
+#pragma unroll
+      for (int j = 0; j < 3; ++j)
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+          H[i][j] += da[i] * ga[j];
+          if (MODE != MODE_FORCE) dF[i][j] += va[i] * ga[j];
+        }
+    }
   } else {
 #pragma unroll
     for (int a = 0; a < 8; ++a) {
@@ -627,6 +694,12 @@ element_kernel(ElemParams p) {
   T fa[3] = {T(0), T(0), T(0)};
   if constexpr (RULE == RULE_HEX8) {
     hex_forces<T>(S, k, inv_dx, fa);
+  } else if constexpr (RULE == RULE_TETU) {
+    // f_k = S grad N_k with the tetrahedron's stress (weight V included) from lane 0
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) fa[i] += __shfl_sync(0xffffffffu, S[i][j], base) * gk[j];
   } else {
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
@@ -829,6 +902,11 @@ ElemParams make_params(const LocalArgs& a) {
   p.wm = a.m->wm;
   p.fiber = a.m->fiber;
   set_cell_size(p, a.m->h.dx, a.m->h.rule == PD_ELEM_TET6 ? 6.0 : 8.0);
+  p.Xrest = a.m->X;
+  p.tgrad = a.m->tet_grad;
+  p.tvol = a.m->tet_vol;
+  p.tgrad_f = a.m->tet_grad_f;
+  p.tvol_f = a.m->tet_vol_f;
   return p;
 }
 
@@ -837,7 +915,8 @@ template <int MODE>
 void launch_elem(const MeshImpl* m, int precision, const ElemParams& p, cudaStream_t s) {
   const int nb = (int)((m->h.e * 8 + kElemThreads - 1) / kElemThreads);
   const bool tet = m->h.rule == PD_ELEM_TET6;
-  if (m->neohookean && !tet) {
+  const bool tetu = m->h.rule == PD_ELEM_TETU;
+  if (m->neohookean && m->h.rule == PD_ELEM_HEX8) {
     // Neo-Hookean: FP32 for the mixed tiers, FP64 for the FP64 and refined ones
     if (local_is_fp32(precision))
       element_kernel<float, MODE, RULE_HEX8, false, false, true><<<nb, kElemThreads, 0, s>>>(p);
@@ -846,14 +925,16 @@ void launch_elem(const MeshImpl* m, int precision, const ElemParams& p, cudaStre
     return;
   }
   if (local_is_fp32(precision)) {
-    if (tet) element_kernel<float, MODE, RULE_TET6><<<nb, kElemThreads, 0, s>>>(p);
+    if (tetu) element_kernel<float, MODE, RULE_TETU><<<nb, kElemThreads, 0, s>>>(p);
+    else if (tet) element_kernel<float, MODE, RULE_TET6><<<nb, kElemThreads, 0, s>>>(p);
     else if (precision == kPrecMixedAcc) element_kernel<float, MODE, RULE_HEX8, true><<<nb, kElemThreads, 0, s>>>(p);
     else element_kernel<float, MODE, RULE_HEX8><<<nb, kElemThreads, 0, s>>>(p);
-  } else if (MODE != MODE_PGRAD && precision == kPrecRefined && !tet && !p.wv) {
+  } else if (MODE != MODE_PGRAD && precision == kPrecRefined && m->h.rule == PD_ELEM_HEX8 && !p.wv) {
     if constexpr (MODE != MODE_PGRAD)
       element_kernel<double, MODE, RULE_HEX8, false, true><<<nb, kElemThreads, 0, s>>>(p);
   } else {
-    if (tet) element_kernel<double, MODE, RULE_TET6><<<nb, kElemThreads, 0, s>>>(p);
+    if (tetu) element_kernel<double, MODE, RULE_TETU><<<nb, kElemThreads, 0, s>>>(p);
+    else if (tet) element_kernel<double, MODE, RULE_TET6><<<nb, kElemThreads, 0, s>>>(p);
     else element_kernel<double, MODE, RULE_HEX8><<<nb, kElemThreads, 0, s>>>(p);
   }
 }

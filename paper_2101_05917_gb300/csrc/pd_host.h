@@ -1,4 +1,4 @@
-// Host-side mesh analysis: voxel mesh, incidence, nested-dissection ordering and
+// Host-side mesh analysis: voxel or tetrahedral mesh, incidence, nested-dissection ordering and
 // the supernodal structure of the scalar matrix L_A with A = I_3 (x) L_A
 // (Eqn 19: G_c maps each coordinate identically, so A never couples x, y, z).
 #pragma once
@@ -15,7 +15,11 @@ struct HostMesh {
   int nx = 0, ny = 0, nz = 0;
   double dx = 0, origin[3] = {0, 0, 0}, density = 0;
   int leaf_max = 64;
-  int rule = 0;                        // PD_ELEM_HEX8 / PD_ELEM_TET6
+  int rule = 0;                        // PD_ELEM_HEX8 / PD_ELEM_TET6 / PD_ELEM_TETU
+  // element corners in use; element records keep a stride of 8 entries (a
+  // tetrahedron of an unstructured mesh fills slots 0..3 and repeats vertex 0 in
+  // slots 4..7, which carry zero shape gradients and no incidence entries)
+  int corners = 8;
   int64_t n = 0, e = 0, nf = 0;       // kept nodes, kept cells, free nodes
 
   // kept order (increasing grid id / cell id)
@@ -34,6 +38,9 @@ struct HostMesh {
   std::vector<double> mass;            // (n) lumped mass, internal order
   std::vector<uint8_t> contact;        // (n) internal order
   std::vector<int32_t> inc_ptr, inc;   // incidence over internal nodes
+  // unstructured tetrahedra: per element the gradients of the four barycentric
+  // coordinates (12 doubles, vertex-major) and the volume
+  std::vector<double> tet_grad, tet_vol;
 
   // supernodes (ND-tree nodes: leaves and separator planes)
   int64_t ns = 0, nlev = 0;
@@ -70,5 +77,6 @@ struct HostMesh {
 
 // Returns "" on success, else an error message.
 std::string analyse(const pd_mesh_desc& d, HostMesh& m);
+std::string analyse_tet(const pd_tet_mesh_desc& d, HostMesh& m);
 
 }  // namespace pd

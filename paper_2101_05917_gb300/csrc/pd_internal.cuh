@@ -171,6 +171,10 @@ struct MeshImpl {
   // assembly map (device)
   int64_t *la_target = nullptr, *la_cptr = nullptr;
   int32_t *la_diag_node = nullptr, *la_contrib = nullptr;
+  // unstructured tetrahedra (PD_ELEM_TETU): barycentric gradients (12 per element,
+  // vertex-major) and volumes, in FP64 and FP32
+  double *tet_grad = nullptr, *tet_vol = nullptr;
+  float *tet_grad_f = nullptr, *tet_vol_f = nullptr;
   // iteration chunks replayed as CUDA graphs: [forward/backward][precision index],
   // captured on cap_stream with the per-step inputs read from ws.act_cur /
   // ws.xnext_cur; dropped whenever a captured argument could change

@@ -14,7 +14,7 @@ HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))
 
 SCALARS = {"int32_t": ctypes.c_int32, "int64_t": ctypes.c_int64, "double": ctypes.c_double,
            "pd_status": ctypes.c_int32}
-MIRRORS = {"pd_mesh_desc": N.MeshDesc, "pd_mesh_info": N.MeshInfo, "pd_factor_opts": N.FactorOpts,
+MIRRORS = {"pd_mesh_desc": N.MeshDesc, "pd_tet_mesh_desc": N.TetMeshDesc, "pd_mesh_info": N.MeshInfo, "pd_factor_opts": N.FactorOpts,
            "pd_solver_opts": N.SolverOpts, "pd_stats": N.Stats, "pd_request": N.Request, "pd_result": N.Result}
 
 
