@@ -562,10 +562,10 @@ def run_ours(args):
                          "timing": "CUDA events on the launching stream around every directly launched solve "
                                    "of a profiled %d-step rollout run after the timed region (the timed rollout "
                                    "runs without events)" % prof_T},
-            "local_step": {"bound": "alu", "kernel": "element_kernel (forward, FP32%s)" % (
-                               ", Neo-Hookean" if sc.neohookean else
-                               ", unstructured tetrahedra: one point per 8-lane element record" if wl.get("tet")
-                               else ""),
+            "local_step": {"bound": "alu", "kernel": (
+                               "tet_element_kernel (forward, FP32, one unstructured tetrahedron per thread)"
+                               if wl.get("tet") else "element_kernel (forward, FP32%s)" % (
+                                   ", Neo-Hookean" if sc.neohookean else "")),
                            "avg_us": 1e6 * t_local, "launches_timed": locals_timed,
                            "flops_per_gauss_point": flops_gp, "gauss_points": gps,
                            "achieved": local_tflops, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",

@@ -54,10 +54,7 @@ __device__ __forceinline__ T gradN_tet(int a, int q, int d, T inv_dx) {
   return T(g) * inv_dx;
 }
 
-// RULE_TETU: unstructured linear tetrahedra, one per element record (vertices in
-// lanes 0..3, lanes 4..7 repeat vertex 0), with per-element barycentric gradients
-// and volume; the one point sits on lane 0, the other lanes carry zero weight.
-enum { RULE_HEX8 = 0, RULE_TET6 = 1, RULE_TETU = 2 };
+enum { RULE_HEX8 = 0, RULE_TET6 = 1 };
 
 // Hexahedron: the shape gradients factor over the three axes, so the sums over
 // the 8 corners (F at a Gauss point) and over the 8 Gauss points (corner forces)
@@ -276,25 +273,12 @@ struct ElemParams {
   // residual check (ref_mode 1) and read by the later ones (ref_mode 2)
   double* ref_cache;
   int ref_mode;
-  // unstructured tetrahedra: node rest positions (internal order) and per element
-  // the barycentric gradients (12, vertex-major) and the volume
+  // unstructured tetrahedra (tet_element_kernel): node rest positions (internal
+  // order) and per element the barycentric gradients (12, vertex-major) and volume
   const double* Xrest;
   const double *tgrad, *tvol;
   const float *tgrad_f, *tvol_f;
 };
-
-// quadrature weight of lane k's point
-template <typename T, int RULE>
-__device__ __forceinline__ T point_weight(const ElemParams& p, int64_t e, int k, bool valid) {
-  if constexpr (RULE == RULE_TETU) {
-    if (!valid || k != 0) return T(0);
-    if constexpr (sizeof(T) == 4) return p.tvol_f[e];
-    else return p.tvol[e];
-  } else {
-    if (RULE == RULE_TET6 && k >= 6) return T(0);   // the tetrahedral rule leaves lanes 6, 7 idle
-    return sizeof(T) == 4 ? T(p.Vq_f) : T(p.Vq);
-  }
-}
 
 constexpr int kRefFields = 18;   // R (9), S (9)
 
@@ -342,8 +326,8 @@ element_kernel(ElemParams p) {
   const int rmode = (kRefCache && p.ref_cache) ? p.ref_mode : 0;
   double* rcache = rmode ? p.ref_cache + ((int64_t)blockIdx.x * kElemThreads + threadIdx.x) : nullptr;
   const bool skip_x = cmode == 2 || rmode == 2;   // the cached point data replace x and H
-  // volume weight of this lane's point
-  const T Vq = point_weight<T, RULE>(p, e, k, valid);
+  // volume weight of this lane's point (the tetrahedral rule leaves lanes 6, 7 idle)
+  const T Vq = (RULE == RULE_TET6 && k >= 6) ? T(0) : (sizeof(T) == 4 ? T(p.Vq_f) : T(p.Vq));
 
   // ---- corner loads: relative displacement of corner k w.r.t. corner 0
   int node = valid ? p.elems[e * 8 + k] : 0;
@@ -356,38 +340,11 @@ element_kernel(ElemParams p) {
       xk[1] = p.x[3 * (int64_t)node + 1];
       xk[2] = p.x[3 * (int64_t)node + 2];
     }
-    // rest offset of corner k from corner 0: the cell's edge vector, or from the
-    // node rest positions (unstructured tetrahedra)
-    double rk[3] = {0, 0, 0};
-    if constexpr (RULE == RULE_TETU) {
-      double Xk[3] = {0, 0, 0};
-      if (valid) {
-        Xk[0] = p.Xrest[3 * (int64_t)node + 0];
-        Xk[1] = p.Xrest[3 * (int64_t)node + 1];
-        Xk[2] = p.Xrest[3 * (int64_t)node + 2];
-      }
-#pragma unroll
-      for (int i = 0; i < 3; ++i) rk[i] = Xk[i] - __shfl_sync(0xffffffffu, Xk[i], base);
-    } else {
-#pragma unroll
-      for (int i = 0; i < 3; ++i) rk[i] = cbit(k, i) ? p.dx : 0.0;
-    }
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
       const double x0 = __shfl_sync(0xffffffffu, xk[i], base);
-      dkd[i] = (xk[i] - x0) - rk[i];
+      dkd[i] = (xk[i] - x0) - (cbit(k, i) ? p.dx : 0.0);
       dk[i] = (T)dkd[i];
-    }
-  }
-  // unstructured tetrahedra: lane k < 4 holds vertex k's barycentric gradient
-  T gk[3] = {T(0), T(0), T(0)};
-  if constexpr (RULE == RULE_TETU) {
-    if (valid && k < 4) {
-#pragma unroll
-      for (int j = 0; j < 3; ++j) {
-        if constexpr (sizeof(T) == 4) gk[j] = p.tgrad_f[12 * e + 3 * k + j];
-        else gk[j] = p.tgrad[12 * e + 3 * k + j];
-      }
     }
   }
   T vk[3] = {T(0), T(0), T(0)};
@@ -418,25 +375,6 @@ element_kernel(ElemParams p) {
   } else if constexpr (RULE == RULE_HEX8) {
     if (!skip_x) hex_grad<T>(dk, k, inv_dx, H);
     if (MODE != MODE_FORCE) hex_grad<T>(vk, k, inv_dx, dF);
-  } else if constexpr (RULE == RULE_TETU) {
-    // every lane forms the tetrahedron's F - I (and dF) from the four vertices
-#pragma unroll
-    for (int a = 0; a < 4; ++a) {
-      T da[3], va[3], ga[3];
-#pragma unroll
-      for (int i = 0; i < 3; ++i) {
-        da[i] = __shfl_sync(0xffffffffu, dk[i], base + a);
-        if (MODE != MODE_FORCE) va[i] = __shfl_sync(0xffffffffu, vk[i], base + a);
-        ga[i] = __shfl_sync(0xffffffffu, gk[i], base + a);
-      }
-#pragma unroll
-      for (int j = 0; j < 3; ++j)
-#pragma unroll
-        for (int i = 0; i < 3; ++i) {
-          H[i][j] += da[i] * ga[j];
-          if (MODE != MODE_FORCE) dF[i][j] += va[i] * ga[j];
-        }
-    }
   } else {
 #pragma unroll
     for (int a = 0; a < 8; ++a) {
@@ -694,12 +632,6 @@ element_kernel(ElemParams p) {
   T fa[3] = {T(0), T(0), T(0)};
   if constexpr (RULE == RULE_HEX8) {
     hex_forces<T>(S, k, inv_dx, fa);
-  } else if constexpr (RULE == RULE_TETU) {
-    // f_k = S grad N_k with the tetrahedron's stress (weight V included) from lane 0
-#pragma unroll
-    for (int i = 0; i < 3; ++i)
-#pragma unroll
-      for (int j = 0; j < 3; ++j) fa[i] += __shfl_sync(0xffffffffu, S[i][j], base) * gk[j];
   } else {
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
@@ -732,6 +664,150 @@ element_kernel(ElemParams p) {
     double en = (double)ec;
 #pragma unroll
     for (int off = 16; off >= 8; off >>= 1) en += __shfl_xor_sync(0xffffffffu, en, off);
+    if (lane == 0) {
+      wsum[threadIdx.x >> 5] = en;
+      __threadfence_block();
+      const unsigned t = atomicAdd(&arrived, 1u);
+      if (t == kElemThreads / 32 - 1) {
+        __threadfence_block();
+        double tot = 0;
+        for (int w = 0; w < kElemThreads / 32; ++w) tot += ((volatile double*)wsum)[w];
+        p.energy[blockIdx.x] = tot;
+      }
+    }
+  }
+}
+
+// Unstructured linear tetrahedra (PD_ELEM_TETU), one element per thread: F - I =
+// sum over vertices a = 1..3 of (x_a - x_0 - (X_a - X_0)) (outer) grad N_a with the
+// element's own barycentric gradients, dF = sum over a = 0..3 of v_a (outer) grad N_a,
+// the corotated and volume projections of element_kernel at the element's one
+// point (weight V), and the vertex forces f_a = S grad N_a into slots 0..3 of the
+// element's record (slots 4..7 have no incidence entries and are not written).
+// Every thread of the grid reaches the SVD and the volume projection (their
+// full-warp votes); tail threads carry F = I and zero weights.
+template <typename T, int MODE>
+__global__ void __launch_bounds__(kElemThreads, sizeof(T) == 8 ? 1 : 2)
+tet_element_kernel(ElemParams p) {
+  if (p.gate && p.gate->converged) return;
+  __shared__ double wsum[kElemThreads / 32];
+  __shared__ unsigned arrived;
+  if (MODE == MODE_FORCE) {
+    if (threadIdx.x == 0) arrived = 0u;
+    __syncthreads();   // at entry all warps are together: no wait
+  }
+  const int lane = threadIdx.x & 31;
+  const int64_t e = (int64_t)blockIdx.x * kElemThreads + threadIdx.x;
+  const bool valid = e < p.ne;
+  T g[4][3];
+  T H[3][3] = {{T(0), T(0), T(0)}, {T(0), T(0), T(0)}, {T(0), T(0), T(0)}};
+  T dF[3][3] = {{T(0), T(0), T(0)}, {T(0), T(0), T(0)}, {T(0), T(0), T(0)}};
+  T Vq = T(0);
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) g[a][j] = T(0);
+  if (valid) {
+    int node[4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a) node[a] = p.elems[e * 8 + a];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) {
+        if constexpr (sizeof(T) == 4) g[a][j] = p.tgrad_f[12 * e + 3 * a + j];
+        else g[a][j] = p.tgrad[12 * e + 3 * a + j];
+      }
+    if constexpr (sizeof(T) == 4) Vq = p.tvol_f[e];
+    else Vq = p.tvol[e];
+    double x0[3], X0[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      x0[i] = p.x[3 * (int64_t)node[0] + i];
+      X0[i] = p.Xrest[3 * (int64_t)node[0] + i];
+    }
+#pragma unroll
+    for (int a = 1; a < 4; ++a) {
+#pragma unroll
+      for (int i = 0; i < 3; ++i) {
+        const int64_t k = 3 * (int64_t)node[a] + i;
+        const T d = (T)((p.x[k] - x0[i]) - (p.Xrest[k] - X0[i]));
+#pragma unroll
+        for (int j = 0; j < 3; ++j) H[i][j] += d * g[a][j];
+      }
+    }
+    if (MODE != MODE_FORCE) {
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+          const T va = (T)p.v[3 * (int64_t)node[a] + i];
+#pragma unroll
+          for (int j = 0; j < 3; ++j) dF[i][j] += va * g[a][j];
+        }
+    }
+  }
+  const T wc = (valid && p.wc) ? (T)p.wc[e] : T(0);
+  const T wv = (valid && p.wv) ? (T)p.wv[e] : T(0);
+
+  T S[3][3] = {{T(0), T(0), T(0)}, {T(0), T(0), T(0)}, {T(0), T(0), T(0)}};
+  T energy = T(0);
+  T gwc = T(0), gwv = T(0);
+  SVD3<T> sv;
+  svd3_from_H<T>(H, sv);
+  if (valid && !(sv.sig[2] > T(0))) atomicOr(p.flags, DEV_ERR_INVERTED);
+  T M[3][3];
+  if (MODE != MODE_FORCE) rotate_in<T>(sv.U, dF, sv.V, M);
+  if (wc != T(0)) {
+    if (MODE == MODE_FORCE) {
+      add_UdVt<T>(S, sv.U, sv.sm1, sv.V, wc * Vq);
+      energy += T(0.5) * wc * Vq * (sv.sm1[0] * sv.sm1[0] + sv.sm1[1] * sv.sm1[1] + sv.sm1[2] * sv.sm1[2]);
+    } else if (MODE == MODE_HVP) {
+      T K[3][3];
+      corot_hvp_frame<T>(sv, M, K);
+      add_UKVt<T>(S, sv.U, K, sv.V, wc * Vq);
+    } else {
+      gwc = -Vq * (M[0][0] * sv.sm1[0] + M[1][1] * sv.sm1[1] + M[2][2] * sv.sm1[2]);
+    }
+  }
+  if (__any_sync(0xffffffffu, wv != T(0))) {
+    VolProj<T> vp;
+    if (volume_project<T>(sv, vp, wv != T(0))) {
+      if (MODE == MODE_FORCE) {
+        add_UdVt<T>(S, sv.U, vp.gap, sv.V, wv * Vq);
+        energy += T(0.5) * wv * Vq * (vp.gap[0] * vp.gap[0] + vp.gap[1] * vp.gap[1] + vp.gap[2] * vp.gap[2]);
+      } else if (MODE == MODE_HVP) {
+        T K[3][3];
+        vol_hvp_frame<T>(sv, vp, M, K);
+        add_UKVt<T>(S, sv.U, K, sv.V, wv * Vq);
+      } else {
+        gwv = -Vq * (M[0][0] * vp.gap[0] + M[1][1] * vp.gap[1] + M[2][2] * vp.gap[2]);
+      }
+    }
+  }
+
+  if (MODE == MODE_PGRAD) {
+    if (valid) {
+      if (p.g_wc) p.g_wc[e] += (double)gwc;
+      if (p.g_wv) p.g_wv[e] += (double)gwv;
+      if (p.g_act) p.g_act[e] = 0.0;   // no muscle energy on this rule
+    }
+    return;
+  }
+
+  if (valid) {
+    T* out = reinterpret_cast<T*>(p.out) + e * 8 * 3;
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int i = 0; i < 3; ++i) out[3 * a + i] = S[i][0] * g[a][0] + S[i][1] * g[a][1] + S[i][2] * g[a][2];
+  }
+  if (MODE == MODE_FORCE) {
+    // block energy partial as in element_kernel: the warp's 32 elements in FP64,
+    // each warp deposits its sum, the last warp to arrive adds the deposits in order
+    double en = valid ? (double)energy : 0.0;
+#pragma unroll
+    for (int off = 16; off >= 1; off >>= 1) en += __shfl_xor_sync(0xffffffffu, en, off);
     if (lane == 0) {
       wsum[threadIdx.x >> 5] = en;
       __threadfence_block();
@@ -911,12 +987,23 @@ ElemParams make_params(const LocalArgs& a) {
 }
 
 // element_kernel<T, MODE, rule of the mesh>
+// grid of the element kernels: 8 threads per element record (voxel rules), one
+// thread per element (unstructured tetrahedra)
+int64_t element_grid(const MeshImpl* m) {
+  const int64_t threads = m->h.rule == PD_ELEM_TETU ? m->h.e : m->h.e * 8;
+  return (threads + kElemThreads - 1) / kElemThreads;
+}
+
 template <int MODE>
 void launch_elem(const MeshImpl* m, int precision, const ElemParams& p, cudaStream_t s) {
-  const int nb = (int)((m->h.e * 8 + kElemThreads - 1) / kElemThreads);
+  const int nb = (int)element_grid(m);
+  if (m->h.rule == PD_ELEM_TETU) {   // corotated and volume energies only (no muscles, not Neo-Hookean)
+    if (local_is_fp32(precision)) tet_element_kernel<float, MODE><<<nb, kElemThreads, 0, s>>>(p);
+    else tet_element_kernel<double, MODE><<<nb, kElemThreads, 0, s>>>(p);
+    return;
+  }
   const bool tet = m->h.rule == PD_ELEM_TET6;
-  const bool tetu = m->h.rule == PD_ELEM_TETU;
-  if (m->neohookean && m->h.rule == PD_ELEM_HEX8) {
+  if (m->neohookean && !tet) {
     // Neo-Hookean: FP32 for the mixed tiers, FP64 for the FP64 and refined ones
     if (local_is_fp32(precision))
       element_kernel<float, MODE, RULE_HEX8, false, false, true><<<nb, kElemThreads, 0, s>>>(p);
@@ -925,16 +1012,14 @@ void launch_elem(const MeshImpl* m, int precision, const ElemParams& p, cudaStre
     return;
   }
   if (local_is_fp32(precision)) {
-    if (tetu) element_kernel<float, MODE, RULE_TETU><<<nb, kElemThreads, 0, s>>>(p);
-    else if (tet) element_kernel<float, MODE, RULE_TET6><<<nb, kElemThreads, 0, s>>>(p);
+    if (tet) element_kernel<float, MODE, RULE_TET6><<<nb, kElemThreads, 0, s>>>(p);
     else if (precision == kPrecMixedAcc) element_kernel<float, MODE, RULE_HEX8, true><<<nb, kElemThreads, 0, s>>>(p);
     else element_kernel<float, MODE, RULE_HEX8><<<nb, kElemThreads, 0, s>>>(p);
-  } else if (MODE != MODE_PGRAD && precision == kPrecRefined && m->h.rule == PD_ELEM_HEX8 && !p.wv) {
+  } else if (MODE != MODE_PGRAD && precision == kPrecRefined && !tet && !p.wv) {
     if constexpr (MODE != MODE_PGRAD)
       element_kernel<double, MODE, RULE_HEX8, false, true><<<nb, kElemThreads, 0, s>>>(p);
   } else {
-    if (tetu) element_kernel<double, MODE, RULE_TETU><<<nb, kElemThreads, 0, s>>>(p);
-    else if (tet) element_kernel<double, MODE, RULE_TET6><<<nb, kElemThreads, 0, s>>>(p);
+    if (tet) element_kernel<double, MODE, RULE_TET6><<<nb, kElemThreads, 0, s>>>(p);
     else element_kernel<double, MODE, RULE_HEX8><<<nb, kElemThreads, 0, s>>>(p);
   }
 }
@@ -954,9 +1039,7 @@ GatherParams make_gather(const MeshImpl* m) {
 
 }  // namespace
 
-int element_blocks(const MeshImpl* m) {
-  return (int)((m->h.e * 8 + kElemThreads - 1) / kElemThreads);
-}
+int element_blocks(const MeshImpl* m) { return (int)element_grid(m); }
 int element_energy_partials(const MeshImpl* m) { return element_blocks(m); }
 int gather_blocks(const MeshImpl* m) {
   return (int)((m->h.nf + kGatherThreads - 1) / kGatherThreads);
