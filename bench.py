@@ -52,9 +52,10 @@ LOCAL_FLOPS_PER_GP = 144 + 42 + 4 * 3 * 40 + 12 + 54 + 90 + 63 + 144 + 6
 # 1/J and log J (2), F^-T = cof(F)/J (36), H + H^T + H H^T (63), (F F^T - I) F^-T
 # (54), the stress (36), the energy (48) and the corner forces (144).
 LOCAL_FLOPS_PER_GP_NH = 144 + 27 + 2 + 36 + 63 + 54 + 36 + 48 + 144
-# A linear tetrahedron's one point: F - I and the vertex forces from 4 vertices (36
-# FMA each) instead of 8 corners, the rest as for a hexahedron's Gauss point.
-LOCAL_FLOPS_PER_TET = LOCAL_FLOPS_PER_GP - 72 - 72
+# A linear tetrahedron's one point: F - I from its 3 edge vectors (27 FMA) and the
+# forces of its 4 vertices (36 FMA) in place of the hexahedron's 8-corner sums
+# (72 FMA each), the rest as for a hexahedron's Gauss point.
+LOCAL_FLOPS_PER_TET = LOCAL_FLOPS_PER_GP - 144 - 144 + 54 + 72
 WORKLOADS = {
     # tol 1e-7: over 50 steps the mixed path at this tolerance stays within 2.5e-8
     # (positions) and 7e-8 (gradients) of the FP64 path at tol 1e-10
