@@ -137,3 +137,42 @@ def test_graph_nested_dissection(leaf):
         for c in range(first[s], first[s + 1]):
             allowed[r[r >= c], c] = True
     assert np.abs(L[~allowed]).max(initial=0.0) <= 1e-12 * np.abs(L).max()
+
+
+def test_voxel_split_agrees_with_the_voxel_rule():
+    """A voxel beam split six ways, handed to the unstructured model as a plain list
+    of tetrahedra (its nodes, the cells' Kuhn tetrahedra, each cell's Young's modulus
+    on its six tetrahedra), is the same discretisation as the voxel model's tet6
+    rule: same lumped mass, energy, forces, Hessian and A, and per-tetrahedron
+    material gradients that add up to the per-cell ones."""
+    from oracle.mesh import kuhn_tetrahedra
+    from oracle.model import Model
+    from workloads import TetScene, tet_beam
+    sv = tet_beam(4, 3, 2, T=2)
+    mv = Model(sv)
+    kt = np.array(kuhn_tetrahedra())
+    tets = mv.mesh.elems[:, kt].reshape(-1, 4)
+    st = TetScene(name="split", X=mv.mesh.X, tets=tets, density=sv.density,
+                  youngs=np.repeat(sv.youngs, 6), poisson=sv.poisson, corotated=sv.corotated,
+                  volume=sv.volume, dirichlet=sv.dirichlet, gravity=sv.gravity, h=sv.h, T=sv.T,
+                  x0=sv.x0, v0=sv.v0, f_ext=sv.f_ext, loss_w=sv.loss_w, tol_fwd=sv.tol_fwd,
+                  tol_bwd=sv.tol_bwd)
+    mt = TetModel(st)
+    assert np.allclose(mt.m, mv.m, rtol=1e-13, atol=0)
+    rng = np.random.default_rng(5)
+    x = sv.x0 + 0.02 * sv.dx * rng.standard_normal(sv.x0.shape)
+    assert abs(mt.energy(x) - mv.energy(x)) <= 1e-12 * abs(mv.energy(x))
+    g = mv.grad_E(x)
+    assert np.abs(mt.grad_E(x) - g).max() <= 1e-11 * np.abs(g).max()
+    Hv, Ht = mv.hessian(x).toarray(), mt.hessian(x).toarray()
+    assert np.abs(Ht - Hv).max() <= 1e-11 * np.abs(Hv).max()
+    Av, At = mv.A_matrix().toarray(), mt.A_matrix().toarray()
+    assert np.abs(At - Av).max() <= 1e-12 * np.abs(Av).max()
+    xs, vs, _ = newton.rollout(mv, sv.x0, sv.v0, sv.f_ext, T=sv.T)
+    _, gx = adjoint.final_position_loss(mv, xs, sv.loss_w)
+    gv = adjoint.backward(mv, xs, vs, gx)
+    gt = adjoint.backward(mt, xs, vs, gx)
+    for k in ("g_wc", "g_wv"):
+        cell = gt[k].reshape(-1, 6).sum(axis=1)
+        assert np.abs(cell - gv[k]).max() <= 1e-9 * np.abs(gv[k]).max(), k
+    assert np.abs(gt["g_v0"] - gv["g_v0"]).max() <= 1e-9 * np.abs(gv["g_v0"]).max()
