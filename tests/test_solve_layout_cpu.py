@@ -2,7 +2,9 @@
 analysis (no GPU).  Each chunk of a tile reaches shared memory by one bulk copy,
 which must start on a 16-byte boundary and move a multiple of 16 bytes, at most the
 32 KB stage: a copy that breaks these rules is an illegal instruction on the GPU,
-so they are checked here for every chunk of every test mesh, together with the
+so they are checked here for every chunk of every test mesh (voxel meshes, and
+unstructured tetrahedral meshes up to the bench's, whose graph-ordered supernodes
+have irregular sizes), together with the
 chunks lying back to back.  The schedule itself must equal a re-derivation from
 its definition: per supernode (nc columns, nr rows), forward tiles are row blocks
 of R rows (R = 256 for nc <= 32, 128 for nc <= 64, else 64) over the columns
@@ -101,12 +103,21 @@ CASES = [(cantilever_c1, 64), (cantilever_c1, 8), (lambda: quadruped(9, T=1), 64
          (lambda: tet_ball(T=1), 16), (lambda: beam_c2(T=1), 64)]
 
 
-@pytest.mark.parametrize("case", range(len(CASES)))
+# unstructured tetrahedral meshes: graph-ordered supernodes of irregular sizes
+TET_CASES = [((6, 3, 3), 16), ((8, 4, 4), 8), ((16, 8, 8), 64), ((24, 12, 12), 64), ((48, 24, 24), 64)]
+
+
+@pytest.mark.parametrize("case", range(len(CASES) + len(TET_CASES)))
 def test_solve_tiles_match_definition_and_copy_rules(native, case):
     from paper_2101_05917_gb300 import api
-    make, leaf = CASES[case]
-    sc = make()
-    m = api.PDMesh.from_scene(sc, leaf_max=leaf, device=None)
+    if case < len(CASES):
+        make, leaf = CASES[case]
+        m = api.PDMesh.from_scene(make(), leaf_max=leaf, device=None)
+    else:
+        from workloads import unstructured_tet_beam
+        (nx, ny, nz), leaf = TET_CASES[case - len(CASES)]
+        sc = unstructured_tet_beam(nx, ny, nz, T=1, index=21, E=1e6)
+        m = api.PDMesh.from_tet_scene(sc, leaf_max=leaf, device=None)
     got = m.export("solve_tiles").reshape(-1, 10)
     want = _derive(m)
     assert np.array_equal(got, want)
