@@ -63,13 +63,13 @@ enum {
   /* pd_local_step / pd_hessian_vector only: the FP32 local step with the
      displacement gradient F - I and the Green strain F^T F - I formed in FP64, so
      that the stresses stay accurate relative to the strain under large rotations
-     (hexahedra; the tetrahedral rule runs the plain FP32 step).  The mixed-precision
+     (hexahedra; the tetrahedral rules run the plain FP32 step).  The mixed-precision
      rollouts switch to it when the plain FP32 residual stops decreasing. */
   PD_PREC_MIXED_STRAIN = 2,
   /* pd_local_step / pd_hessian_vector only: FP64-accurate results from an FP32 SVD
      of the FP64 strain whose rotation (and its derivative) is refined in FP64
      without eigenvectors; hexahedra with the corotated and muscle energies (a mesh
-     with the volume energy, or the tetrahedral rule, runs the plain FP64 step).
+     with the volume energy, or a tetrahedral rule, runs the plain FP64 step).
      The mixed-precision rollouts use it for their FP64 convergence checks. */
   PD_PREC_FP64_REFINED = 3
 };
@@ -191,12 +191,14 @@ pd_status pd_mesh_export(pd_mesh m, int32_t what, int64_t* host_out, int64_t cap
  *   A = M/h^2 + sum_c w_c G_c^T G_c   (Sec. 3, Eqn 19).
  * w_corot, w_vol, w_muscle: (e) stiffness per unit volume [Pa] of the corotated,
  * volume-preserving and muscle-fibre energies (NULL = energy absent); each
- * Gauss point of a cell carries w * dx^3/8.  fiber: (e, 3) unit fibre directions
- * (required when w_muscle is given).  The numeric supernodal Cholesky runs on
+ * Gauss point of a cell carries w * dx^3/8 (w * dx^3/6 per tetrahedron of the
+ * six-way split, w * V per unstructured tetrahedron).  fiber: (e, 3) unit fibre
+ * directions (required when w_muscle is given).  The numeric supernodal Cholesky runs on
  * the device in FP64; with PD_PREC_MIXED an FP32 copy of the solve panels is kept
  * for the triangular solves.  Copies of the weights are kept for the local
  * steps.  Returns PD_ERR_NOT_SPD on a non-positive pivot; PD_ERR_INVALID_ARG for
- * the Neo-Hookean option without both w_corot and w_vol or on a tetrahedral mesh. */
+ * the Neo-Hookean option without both w_corot and w_vol or on a tetrahedral mesh,
+ * and for w_muscle on an unstructured tetrahedral mesh. */
 typedef struct {
   double h;                     /* time step [s] */
   double gravity[3];            /* [m/s^2] */
