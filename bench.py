@@ -67,9 +67,9 @@ WORKLOADS = {
     "c2nh": dict(name="c2_beam_32x32x64_neohookean_mixed", K=0, tol=1e-8, want=("w_corot", "w_vol", "v0"),
                  iters_per_step=234.0, nh=True),
     # an unstructured tetrahedral beam (jittered 49x25x25 lattice, Delaunay; the
-    # material and tolerance of the C2 beam); no CPU baseline line
+    # material and tolerance of the C2 beam)
     "tetu": dict(name="unstructured_tet_beam_48x24x24_mixed", K=0, tol=1e-8, want=("w_corot", "w_vol", "v0"),
-                 iters_per_step=None, tet=True),
+                 iters_per_step=186.8, tet=True),
 }
 
 
@@ -197,10 +197,11 @@ def oracle_sample(workload, iters_per_step, budget_s=20.0):
     import numpy as np
     from oracle import pd_cpu
     from oracle.model import Model
+    from oracle.tetmesh import TetModel
     sc = _scene(workload, 1)
     cores = os.cpu_count()
     t0 = time.perf_counter()
-    model = Model(sc)
+    model = TetModel(sc) if WORKLOADS[workload].get("tet") else Model(sc)
     if workload == "c5":
         t_setup = time.perf_counter() - t0
         n = 0
@@ -533,7 +534,7 @@ def run_ours(args):
     if rank == 0 and not args.no_fp64:
         fp64 = fp64_line(dev)
     cpu = None
-    if rank == 0 and not args.no_cpu_baseline and not wl.get("tet"):
+    if rank == 0 and not args.no_cpu_baseline:
         cpu = oracle_sample(args.workload, fwd_it + bwd_it)
 
     if rank == 0:
