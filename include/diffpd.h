@@ -161,7 +161,8 @@ pd_status pd_mesh_query(pd_mesh m, pd_mesh_info* info);
  * bit for bit against an independent re-derivation. */
 enum {
   PD_EXPORT_INC_PTR = 0,   /* (n+1): kept-node -> (element, corner) CSR pointers */
-  PD_EXPORT_INC = 1,       /* (8e): entries e*8+corner, ascending per node */
+  PD_EXPORT_INC = 1,       /* (8e; 4e on an unstructured tetrahedral mesh): entries
+                              e*8+corner, ascending per node */
   PD_EXPORT_PERM = 2,      /* (n_free): column -> free-node index (free nodes in kept order) */
   PD_EXPORT_SNODE_FIRST = 3, /* (n_snodes+1): first column of each supernode */
   PD_EXPORT_ROW_PTR = 4,   /* (n_snodes+1) */
