@@ -128,7 +128,8 @@ typedef struct {
                                    n_tets < 2^25 (32-bit assembly codes) */
   const double* X;              /* (n_nodes, 3) rest positions [m] */
   const int32_t* tets;          /* (n_tets, 4) vertex indices, either orientation;
-                                   four distinct nodes of non-zero volume */
+                                   four distinct nodes, |det(edge matrix)| above
+                                   1e-12 x (longest edge from vertex 0)^3 */
   double density;               /* [kg/m^3]; lumped mass rho V/4 per vertex */
   const uint8_t* dirichlet;     /* per node: fixed at its rest position, NULL = none */
   const uint8_t* contact;       /* per node: ground-penalty candidate, NULL = none */

@@ -10,6 +10,11 @@
 //              grid-id order.  Boxes with 1..leaf_max free nodes are leaves in
 //              grid-id order.
 //  supernodes  every leaf and every non-empty separator plane.
+//  unstructured tetrahedral meshes (analyse_tet): kept nodes and elements are the
+//              caller's; incidence entries e*8+a for vertices a < 4; ordering by
+//              coordinate bisection of free-node sets with vertex separators of
+//              the mesh graph (GraphNDBuilder); supernodes every leaf and every
+//              non-empty separator.
 //  structure   rows(s) = cols(s) + {r >= first(s) adjacent to a column of s} +
 //              below(t) of every child t; parent(s) = owner of min below(s).
 //  levels      0 for supernodes without children, else 1 + max over children.
@@ -308,7 +313,11 @@ std::string analyse_tet(const pd_tet_mesh_desc& d, HostMesh& m) {
     const double C01 = D[1][2] * D[2][0] - D[1][0] * D[2][2];
     const double C02 = D[1][0] * D[2][1] - D[1][1] * D[2][0];
     const double det = D[0][0] * C00 + D[0][1] * C01 + D[0][2] * C02;
-    if (!(std::fabs(det) > 0.0) || !std::isfinite(det))
+    // degenerate: a volume below 1e-12 of the cube of its longest edge from vertex 0
+    // (the barycentric gradients would then overflow the FP32 tables)
+    double L2 = 0.0;
+    for (int c = 0; c < 3; ++c) L2 = std::max(L2, D[0][c] * D[0][c] + D[1][c] * D[1][c] + D[2][c] * D[2][c]);
+    if (!std::isfinite(det) || !(std::fabs(det) > 1e-12 * L2 * std::sqrt(L2)))
       return "tet mesh: degenerate tetrahedron " + std::to_string(t);
     double inv[3][3];   // inv = adj(D) / det, adj(D)[i][j] = cofactor C_ji
     inv[0][0] = C00 / det;
