@@ -62,6 +62,12 @@ def test_tet_mesh_rejects_malformed_input(api):
     t = sc.tets[2]
     X[t[3]] = X[t[0]] + 0.5 * (X[t[1]] - X[t[0]])  # vertex 3 on edge 0-1: zero volume
     assert status(X, sc.tets) == N.PD_ERR_INVALID_ARG
+    X = sc.X.copy()
+    p0, p1, p2 = X[t[0]], X[t[1]], X[t[2]]
+    nrm = np.cross(p1 - p0, p2 - p0)
+    nrm /= np.linalg.norm(nrm)
+    X[t[3]] = (p0 + p1 + p2) / 3 + 1e-15 * nrm      # a sliver of volume ~1e-15 of its edge cubed
+    assert status(X, sc.tets) == N.PD_ERR_INVALID_ARG
     X = np.vstack([sc.X, [[1.0, 1.0, 1.0]]])        # a node in no tetrahedron
     assert status(X, sc.tets) == N.PD_ERR_INVALID_ARG
     assert status(sc.X, sc.tets, np.ones(sc.X.shape[0])) == N.PD_ERR_INVALID_ARG   # nothing free
