@@ -44,6 +44,20 @@ def test_tet_structures_bit_exact(api, case):
     m.close()
 
 
+@pytest.mark.parametrize("jitter", [0.0, 0.05, 0.45])
+@pytest.mark.parametrize("leaf", [3, 8])
+def test_tet_ordering_bit_exact_under_coordinate_ties(api, jitter, leaf):
+    """jitter 0 puts every node on the lattice (whole planes of equal coordinates,
+    so the ordering's ties are broken by node index throughout)."""
+    for index in (3, 4):
+        sc = unstructured_tet_beam(5, 4, 3, T=1, index=index, jitter=jitter)
+        m = api.PDMesh.from_tet_scene(sc, leaf_max=leaf, device=None)
+        st = tetstructure.analyse(sc.X, sc.tets, sc.dirichlet, leaf_max=leaf)
+        for key in ("perm", "snode_first", "row_ptr", "rows", "parent", "level", "rel"):
+            assert np.array_equal(m.export(key), st[key]), (key, index)
+        m.close()
+
+
 def test_tet_mesh_rejects_malformed_input(api):
     from paper_2101_05917_gb300 import _native as N
     sc = unstructured_tet_beam(3, 2, 2, T=1)
