@@ -14,9 +14,11 @@
 // whichever covers the supernode's columns with the fewest idle column groups)
 // over every column its rows need; a backward tile is one column block (BC = 64,
 // 32, 16 or 8 columns, the narrowest covering the supernode) over every row from
-// its first column down.  A tile is processed by one CTA from start to end, so its
-// sums never leave the CTA: there are no partial sums between CTAs and no
-// reductions across tiles, and the result does not depend on scheduling.  The
+// its first column down.  A tile is processed by one CTA from start to end.  In a
+// level with few blocks (the top of the tree) a block is split into several tiles,
+// runs of its consecutive chunks: each writes its partial sums to its own slots and
+// the last to arrive (an arrival counter) adds them in tile order, so the result
+// does not depend on scheduling either way.  The
 // panel values of a tile flow through the CTA in chunks of at most 256 x 32
 // entries: forward chunks are ranges of 32 columns per row group (256 / R
 // groups), backward chunks ranges of 8192 / BC rows (at most 256).
