@@ -8,7 +8,9 @@
 // (2x2x2 rule).  Corner data moves between the two roles with warp shuffles,
 // so there is no shared memory and no atomics: each cell writes its 8 corner
 // forces to an element buffer, and the gather sums them per node in the fixed
-// incidence order (bit-reproducible).
+// incidence order (bit-reproducible).  Unstructured tetrahedra (one point each)
+// take one thread per element instead (tet_element_kernel), with the same element
+// buffer layout and gathers.
 #include "pd_internal.cuh"
 #include "pd_math.cuh"
 

@@ -268,8 +268,11 @@ void svd_cache_layout(const MeshImpl* m, int64_t* slots, int64_t* fields);
 bool ref_cache_applies(const MeshImpl* m, int64_t* doubles);
 cudaError_t launch_element_param_grads(const LocalArgs& a, double* g_wc, double* g_wv,
                                        double* g_wm, double* g_act, cudaStream_t s);
+// blocks of the element kernels: 8 threads per element record (voxel rules) or one
+// thread per element (unstructured tetrahedra); each force launch writes one
+// energy partial per block
 int element_blocks(const MeshImpl* m);
-int element_energy_partials(const MeshImpl* m);   // one per warp
+int element_energy_partials(const MeshImpl* m);
 
 // Gathers (K2): out[c] = sum over incidence of elembuf + node terms, for c < nf
 // (gradient mode: + m (x - y)/h^2 + contact force; hvp mode: + m v/h^2 + contact).
