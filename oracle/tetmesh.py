@@ -13,12 +13,16 @@ so), lumped mass rho V / 4 per vertex (reading, as for the voxel split).
 TetModel is the PD model of oracle/model.py (corotated and volume energies, the PD
 matrix A, gravity, external force; no muscles and no contact) on such a mesh; it
 keeps Model's interface so that newton.py, pd_cpu.py and adjoint.py run on it.
+With `scene.neohookean` the corotated and volume terms give way to the Neo-Hookean
+energy of oracle/neohookean.py (Sec. 8; the paper's Armadillo is such a mesh) with
+mu = w_corot/2, lambda = w_vol, as in oracle/model.py.
 """
 from __future__ import annotations
 
 import numpy as np
 import scipy.sparse as sp
 
+from . import neohookean as nh
 from . import projections as pj
 from .model import Model, lame_weights
 
@@ -99,13 +103,18 @@ class TetModel(Model):
         self.free_nodes = np.flatnonzero(~self.dirichlet)
         self.free_dofs = (self.free_nodes[:, None] * 3 + np.arange(3)[None, :]).ravel()
         self.G = mesh.G_matrices()
-        self.neohookean = False
+        self.neohookean = bool(getattr(s, "neohookean", False))
+        if self.neohookean:
+            self.nh_mu = 0.5 * wc
+            self.nh_lam = wv
 
     def energy(self, x, act=None, loc=None):
         loc = self.local(x, act) if loc is None else loc
         F = loc["F"]
         V = self.mesh.Vq[:, None]
         E = 0.0
+        if "psi_nh" in loc:
+            E += np.sum(V * loc["psi_nh"])
         if "R" in loc:
             E += 0.5 * np.sum(self.w_corot[:, None] * V * np.sum((F - loc["R"]) ** 2, axis=(2, 3)))
         if "D" in loc:
@@ -116,6 +125,8 @@ class TetModel(Model):
         loc = self.local(x, act) if loc is None else loc
         F = loc["F"]
         S = np.zeros_like(F)
+        if "P_nh" in loc:
+            S += self.mesh.Vq[:, None, None, None] * loc["P_nh"]
         if "R" in loc:
             S += (self.w_corot * self.mesh.Vq)[:, None, None, None] * (F - loc["R"])
         if "D" in loc:
@@ -126,9 +137,15 @@ class TetModel(Model):
         return g
 
     def _element_blocks(self, x, act=None, linearised=True):
-        """Per-element 12x12: V w G^T (I - J) G (or V w G^T G when linearised=False)."""
+        """Per-element 12x12: V w G^T (I - J) G (or V w G^T G when linearised=False);
+        Neo-Hookean: V G^T T G with the tangent T = dP/dF."""
         G = self.G                                         # (e, 1, 9, 12)
         V = self.mesh.Vq
+        if self.neohookean and linearised:
+            F = self.mesh.deformation_gradients(x)
+            mu = np.broadcast_to(self.nh_mu[:, None], F.shape[:2])
+            lam = np.broadcast_to(self.nh_lam[:, None], F.shape[:2])
+            return np.einsum("e,eqki,eqkl,eqlj->eij", V, G, nh.tangent(F, mu, lam), G)
         blocks = np.einsum("e,eqki,eqkj->eij", (self.w_corot + self.w_vol) * V, G, G)
         if not linearised:
             return blocks

@@ -176,3 +176,62 @@ def test_voxel_split_agrees_with_the_voxel_rule():
         cell = gt[k].reshape(-1, 6).sum(axis=1)
         assert np.abs(cell - gv[k]).max() <= 1e-9 * np.abs(gv[k]).max(), k
     assert np.abs(gt["g_v0"] - gv["g_v0"]).max() <= 1e-9 * np.abs(gv["g_v0"]).max()
+
+
+@pytest.fixture(scope="module")
+def nh_beam():
+    import dataclasses
+    return dataclasses.replace(unstructured_tet_beam(6, 3, 3, T=2), neohookean=True)
+
+
+def test_neohookean_rest_rigid_and_derivatives(nh_beam):
+    """Neo-Hookean tetrahedra (the paper's Armadillo): stress-free at rest and under
+    rigid motions, gradient and Hessian against central differences."""
+    m = TetModel(nh_beam)
+    X = nh_beam.X
+    scale = np.sum(m.nh_mu * m.mesh.Vq)                  # energy of a unit strain, roughly
+    fscale = scale / 0.01                                # force of a unit strain at dx = 1 cm
+    assert abs(m.energy(X)) <= 1e-14 * scale and np.abs(m.grad_E(X)).max() <= 1e-12 * fscale
+    rng = np.random.default_rng(8)
+    xr = X @ _rot(rng).T + rng.standard_normal(3)
+    assert abs(m.energy(xr)) <= 1e-12 * scale and np.abs(m.grad_E(xr)).max() <= 1e-10 * fscale
+    x = X + 0.01 * 0.01 * rng.standard_normal(X.shape)
+    assert np.linalg.det(m.mesh.deformation_gradients(x)[:, 0]).min() > 0.25
+    g = m.grad_E(x)
+    d = rng.standard_normal(X.shape)
+    eps = 1e-8
+    fd = (m.energy(x + eps * d) - m.energy(x - eps * d)) / (2 * eps)
+    assert abs(fd - np.sum(g * d)) <= 1e-6 * abs(fd)
+    Hd = (m.hessian(x) @ d.ravel()).reshape(x.shape) - (m.m / m.h ** 2)[:, None] * d
+    fdg = (m.grad_E(x + eps * d) - m.grad_E(x - eps * d)) / (2 * eps)
+    assert np.abs(fdg - Hd).max() <= 1e-5 * np.abs(Hd).max()
+
+
+def test_neohookean_pd_and_adjoint(nh_beam):
+    """L-BFGS with the PD matrix A as initial Hessian reaches Newton's fixed point,
+    and the adjoint matches central differences of a rollout loss in v0 and E."""
+    import dataclasses
+    m = TetModel(nh_beam)
+    xn, _, _ = newton.newton_step(m, nh_beam.x0, nh_beam.v0, nh_beam.f_ext)
+    xp, _, _ = pd_cpu.pd_lbfgs_step(m, pd_cpu.ScalarA(m), nh_beam.x0, nh_beam.v0, nh_beam.f_ext,
+                                    None, None, 1e-12, 5, 5000)
+    assert np.linalg.norm(xp - xn) <= 1e-9 * np.linalg.norm(xn - nh_beam.x0)
+    xs, vs, _ = newton.rollout(m, nh_beam.x0, nh_beam.v0, nh_beam.f_ext, T=nh_beam.T)
+    _, gx = adjoint.final_position_loss(m, xs, nh_beam.loss_w)
+    g = adjoint.backward(m, xs, vs, gx)
+    rng = np.random.default_rng(9)
+    d = rng.standard_normal(nh_beam.x0.shape)
+    d[m.dirichlet] = 0.0
+
+    def loss(v0=None, E=None):
+        mm = TetModel(nh_beam, youngs=E)
+        out, _, _ = newton.rollout(mm, nh_beam.x0, nh_beam.v0 if v0 is None else v0, nh_beam.f_ext,
+                                   T=nh_beam.T)
+        return float(np.sum(nh_beam.loss_w * out[-1]))
+    eps = 1e-6
+    fd_v = (loss(v0=nh_beam.v0 + eps * d) - loss(v0=nh_beam.v0 - eps * d)) / (2 * eps)
+    assert abs(fd_v - np.sum(g["g_v0"] * d)) <= 2e-6 * abs(fd_v)
+    gE, _ = adjoint.material_gradients(m, g)
+    dE = rng.standard_normal(m.mesh.e) * nh_beam.youngs
+    fd_E = (loss(E=nh_beam.youngs + eps * dE) - loss(E=nh_beam.youngs - eps * dE)) / (2 * eps)
+    assert abs(fd_E - np.sum(gE * dE)) <= 2e-6 * abs(fd_E)

@@ -37,6 +37,7 @@ class TetScene:
     tol_bwd: float
     act: Optional[np.ndarray] = None
     muscle: Optional[np.ndarray] = None   # no muscle fibres on these meshes
+    neohookean: bool = False              # Neo-Hookean material in place of corotated + volume
     k_contact: float = 0.0
     mu: float = 0.0
 
