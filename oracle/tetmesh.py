@@ -11,7 +11,8 @@ constant on the element, one point of weight V = det(D) / 6 (> 0: vertices order
 so), lumped mass rho V / 4 per vertex (reading, as for the voxel split).
 
 TetModel is the PD model of oracle/model.py (corotated and volume energies, the PD
-matrix A, gravity, external force; no muscles and no contact) on such a mesh; it
+matrix A, gravity, external force, penalty ground contact with friction on the
+scene's candidate nodes; no muscles) on such a mesh; it
 keeps Model's interface so that newton.py, pd_cpu.py and adjoint.py run on it.
 With `scene.neohookean` the corotated and volume terms give way to the Neo-Hookean
 energy of oracle/neohookean.py (Sec. 8; the paper's Armadillo is such a mesh) with
@@ -96,9 +97,10 @@ class TetModel(Model):
         self.m = mesh.lumped_mass(s.density)
         self.h = float(s.h)
         self.gravity = np.asarray(s.gravity, dtype=np.float64)
-        self.k = 0.0
-        self.mu = 0.0
-        self.contact = np.zeros(mesh.n, dtype=bool)
+        self.k = float(getattr(s, "k_contact", 0.0))
+        self.mu = float(getattr(s, "mu", 0.0) if mu is None else mu)
+        c = getattr(s, "contact", None)
+        self.contact = np.zeros(mesh.n, dtype=bool) if c is None else np.asarray(c, dtype=bool)
         self.dirichlet = np.asarray(s.dirichlet, dtype=bool)
         self.free_nodes = np.flatnonzero(~self.dirichlet)
         self.free_dofs = (self.free_nodes[:, None] * 3 + np.arange(3)[None, :]).ravel()
@@ -119,6 +121,8 @@ class TetModel(Model):
             E += 0.5 * np.sum(self.w_corot[:, None] * V * np.sum((F - loc["R"]) ** 2, axis=(2, 3)))
         if "D" in loc:
             E += 0.5 * np.sum(self.w_vol[:, None] * V * np.sum((F - loc["D"]) ** 2, axis=(2, 3)))
+        if self.k > 0:   # k/2 |x_j - p(x_j)|^2, p = (x, y, max(z, 0)) on the candidates
+            E += 0.5 * self.k * np.sum(np.minimum(x[self.contact, 2], 0.0) ** 2)
         return E
 
     def grad_E(self, x, act=None, loc=None):
@@ -134,6 +138,8 @@ class TetModel(Model):
         fe = np.einsum("eqij,eqaj->eai", S, self.mesh.gradN)    # (e, 4, 3)
         g = np.zeros_like(x)
         np.add.at(g, self.mesh.elems.ravel(), fe.reshape(-1, 3))
+        if self.k > 0:
+            g[:, 2] += np.where(self.contact, self.k * np.minimum(x[:, 2], 0.0), 0.0)
         return g
 
     def _element_blocks(self, x, act=None, linearised=True):

@@ -235,3 +235,57 @@ def test_neohookean_pd_and_adjoint(nh_beam):
     dE = rng.standard_normal(m.mesh.e) * nh_beam.youngs
     fd_E = (loss(E=nh_beam.youngs + eps * dE) - loss(E=nh_beam.youngs - eps * dE)) / (2 * eps)
     assert abs(fd_E - np.sum(gE * dE)) <= 2e-6 * abs(fd_E)
+
+
+@pytest.fixture(scope="module")
+def ball():
+    from workloads import unstructured_tet_ball
+    return unstructured_tet_ball(T=8)
+
+
+def test_contact_ball_derivatives_and_pd(ball):
+    """Penalty ground contact on an unstructured ball (the tennis balls of Sec. 7):
+    the contact term's gradient and Hessian against central differences (candidates
+    kept clear of z = 0, where the penalty has its kink), and PD + L-BFGS = Newton on
+    a step that starts in contact."""
+    m = TetModel(ball)
+    assert m.contact.sum() > 0 and m.k > 0
+    rng = np.random.default_rng(10)
+    x = ball.X + 0.005 * 0.01 * rng.standard_normal(ball.X.shape)
+    x[:, 2] -= 0.004                                    # the lowest candidates 2 mm below ground
+    zc = x[m.contact, 2]
+    assert (zc < 0).sum() >= 3 and np.abs(zc).min() > 1e-5
+    g = m.grad_E(x)
+    d = rng.standard_normal(x.shape)
+    eps = 1e-8
+    fd = (m.energy(x + eps * d) - m.energy(x - eps * d)) / (2 * eps)
+    assert abs(fd - np.sum(g * d)) <= 1e-6 * abs(fd)
+    Hd = (m.hessian(x) @ d.ravel()).reshape(x.shape) - (m.m / m.h ** 2)[:, None] * d
+    fdg = (m.grad_E(x + eps * d) - m.grad_E(x - eps * d)) / (2 * eps)
+    assert np.abs(fdg - Hd).max() <= 1e-5 * np.abs(Hd).max()
+    v = np.zeros_like(x)
+    xn, _, _ = newton.newton_step(m, x, v, ball.f_ext)
+    xp, _, _ = pd_cpu.pd_lbfgs_step(m, pd_cpu.ScalarA(m), x, v, ball.f_ext, None, None, 1e-12, 5, 5000)
+    assert np.linalg.norm(xp - xn) <= 1e-8 * np.linalg.norm(xn - x)
+
+
+def test_contact_ball_adjoint_matches_differences(ball):
+    """The adjoint through penalty contact and Coulomb friction against central
+    differences of a rollout loss in v0 and in the friction coefficient."""
+    m = TetModel(ball)
+    xs, vs, _ = newton.rollout(m, ball.x0, ball.v0, ball.f_ext, T=ball.T)
+    assert np.any(xs[:, m.contact, 2] < 0)              # the ball reaches the ground
+    _, gx = adjoint.final_position_loss(m, xs, ball.loss_w)
+    g = adjoint.backward(m, xs, vs, gx)
+    rng = np.random.default_rng(11)
+    d = rng.standard_normal(ball.x0.shape)
+
+    def loss(v0=None, mu=None):
+        mm = TetModel(ball, mu=mu)
+        out, _, _ = newton.rollout(mm, ball.x0, ball.v0 if v0 is None else v0, ball.f_ext, T=ball.T)
+        return float(np.sum(ball.loss_w * out[-1]))
+    eps = 1e-7
+    fd_v = (loss(v0=ball.v0 + eps * d) - loss(v0=ball.v0 - eps * d)) / (2 * eps)
+    assert abs(fd_v - np.sum(g["g_v0"] * d)) <= 1e-5 * abs(fd_v)
+    fd_mu = (loss(mu=ball.mu + 1e-6) - loss(mu=ball.mu - 1e-6)) / 2e-6
+    assert abs(fd_mu - g["g_mu"]) <= 1e-4 * max(abs(fd_mu), 1e-12)

@@ -34,4 +34,4 @@ from .scenes import (  # noqa: F401
     neohookean_beam,
     SCENES,
 )
-from .tetscenes import TetScene, unstructured_tet_beam  # noqa: F401
+from .tetscenes import TetScene, unstructured_tet_ball, unstructured_tet_beam  # noqa: F401
