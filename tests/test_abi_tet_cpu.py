@@ -91,3 +91,17 @@ def test_tet_mesh_rejects_malformed_input(api):
     b = api.PDMesh.from_tet_mesh(sc.X, flipped, 1e3, sc.dirichlet, device=None)
     for key in ("perm", "rows", "parent"):
         assert np.array_equal(a.export(key), b.export(key))
+
+
+@pytest.mark.parametrize("leaf", [8, 64])
+def test_tet_ball_without_fixed_nodes(api, leaf):
+    """A free-floating contact ball (no fixed node, a contact mask): ordering and
+    structure as the oracle's, every node free."""
+    from workloads import unstructured_tet_ball
+    sc = unstructured_tet_ball(T=1)
+    m = api.PDMesh.from_tet_scene(sc, leaf_max=leaf, device=None)
+    st = tetstructure.analyse(sc.X, sc.tets, sc.dirichlet, leaf_max=leaf)
+    for key in ("perm", "snode_first", "row_ptr", "rows", "parent", "level", "rel"):
+        assert np.array_equal(m.export(key), st[key]), key
+    assert m.query()["n_free"] == sc.X.shape[0]
+    m.close()
