@@ -57,6 +57,12 @@ class TetMesh:
     def e(self) -> int:
         return self.elems.shape[0]
 
+    @property
+    def dx(self) -> float:
+        """A length scale for tolerances that voxel meshes take from their cell edge:
+        the edge of a cube of six times the mean tetrahedron volume."""
+        return float(np.cbrt(6.0 * self.Vq.mean()))
+
     def lumped_mass(self, rho: float) -> np.ndarray:
         m = np.zeros(self.n)
         for a in range(4):

@@ -289,3 +289,55 @@ def test_contact_ball_adjoint_matches_differences(ball):
     assert abs(fd_v - np.sum(g["g_v0"] * d)) <= 1e-5 * abs(fd_v)
     fd_mu = (loss(mu=ball.mu + 1e-6) - loss(mu=ball.mu - 1e-6)) / 2e-6
     assert abs(fd_mu - g["g_mu"]) <= 1e-4 * max(abs(fd_mu), 1e-12)
+
+
+def _complementarity_ball(T):
+    import dataclasses
+    from workloads import unstructured_tet_ball
+    sc = unstructured_tet_ball(T=T)
+    return dataclasses.replace(sc, k_contact=0.0, mu=0.0)
+
+
+def test_complementarity_contact_on_the_ball():
+    """Complementarity contact (Sec. 5.2, Algs 3-5; the tennis balls' ball-ground
+    contact in Sec. 7) on the unstructured ball: held nodes at their targets on the
+    ground, contact forces pushing, no candidate below the ground, the contact
+    forces carrying the momentum change; the adjoint against central differences
+    in v0 with the contact sets unchanged along the direction."""
+    from oracle import contact
+    sc = _complementarity_ball(4)
+    model = TetModel(sc)
+    cand = np.flatnonzero(sc.contact)
+    xs, vs, infos = contact.rollout_complementarity(model, sc.x0, sc.v0, sc.f_ext, sc.contact, sc.T)
+    assert any(i["C"].size for i in infos)
+    for t, i in enumerate(infos):
+        x, y = xs[t + 1], i["y"]
+        assert np.array_equal(x[i["C"]], i["xstar"])
+        assert np.all(i["xstar"][:, 2] == 0.0)
+        assert i["rounds"] < 64
+        free_set = ~np.isin(i["C"], i["locked"])
+        assert np.all(i["force"][free_set, 2] >= -i["tau_r"])
+        assert np.all(x[np.setdiff1d(cand, i["C"]), 2] >= -i["tau_z"])
+        total = (model.m[:, None] * (x - y) / model.h ** 2).sum(axis=0)
+        weight = model.m.sum() * np.linalg.norm(model.gravity)
+        assert np.allclose(i["force"].sum(axis=0), total, rtol=1e-9, atol=1e-12 * weight)
+    T = 3
+    rng = np.random.default_rng(12)
+    w = rng.standard_normal(sc.x0.shape)
+
+    def run(v0):
+        xr, vr, ir = contact.rollout_complementarity(model, sc.x0, v0, sc.f_ext, sc.contact, T)
+        return float(np.sum(w * xr[-1])), xr, vr, ir
+    _, xr, vr, ir = run(sc.v0)
+    gx = np.zeros_like(xr)
+    gx[-1] = w
+    g = contact.backward_complementarity(model, xr, vr, ir, gx)
+    d = rng.standard_normal(sc.v0.shape)
+    eps = 1e-7
+    Lp, _, _, ip = run(sc.v0 + eps * d)
+    Lm, _, _, im = run(sc.v0 - eps * d)
+    for a, b in zip(ip, im):
+        assert np.array_equal(a["C"], b["C"]) and a["rules"] == b["rules"]
+    fd = (Lp - Lm) / (2 * eps)
+    an = float(np.sum(g["g_v0"] * d))
+    assert abs(fd - an) <= 1e-6 * max(abs(an), 1e-12)
